@@ -1,0 +1,201 @@
+/*
+ * ctgraph.h -- exact fixed-radius near-neighbour graphs (ε-graphs) with a
+ * cover tree on one GB300 GPU (sm_103a).
+ *
+ * Problem (paper Sec. III, "ε-graph"): given n points P with a metric d and a
+ * threshold eps, output every ordered pair (i, j), i != j, with
+ * d(p_i, p_j) <= eps (closed ball).  The output is a CSR matrix whose row i
+ * lists the original indices j in ascending order; it is symmetric, and nnz
+ * counts both directions of every undirected edge, as Table I does.
+ *
+ * Method: a cover tree built level by level by vertex splitting
+ * (Algorithms 1 and 2, Sec. IV-A), queried in batches (Algorithm 3 and the
+ * batching remark of Sec. IV-B): each leaf block of the tree is one query
+ * group; its candidate leaf blocks are found by a triangle-inequality walk of
+ * the tree, then every (query, candidate point) pair is decided exactly.
+ *
+ * Conventions for every entry point:
+ *  - Device pointers are CUDA device addresses on the current device; host
+ *    pointers are ordinary process memory.  `stream` is a cudaStream_t (NULL
+ *    is the legacy default stream).
+ *  - Inputs are borrowed: the caller keeps them valid until the work enqueued
+ *    on `stream` has completed.
+ *  - Outputs are owned by the library and are released only by csr_free /
+ *    ct_tree_free.  Device buffers are allocated stream-ordered on `stream`.
+ *  - Every call returns a status and never aborts, traps or exits.  On error
+ *    the out-parameters are zeroed and ct_last_error() describes the failure;
+ *    a CUDA error maps to CT_ECUDA with the CUDA error string.
+ *  - Calls synchronise `stream` where the size of an output must be known on
+ *    the host (the edge count before the CSR is allocated).
+ */
+#ifndef CTGRAPH_H
+#define CTGRAPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CT_OK = 0,
+    CT_EINVAL = 1,        /* invalid argument (null pointer, negative size, eps < 0, ...) */
+    CT_ENOMEM = 2,        /* a device or host allocation failed */
+    CT_ECUDA = 3,         /* a CUDA call or kernel failed; see ct_last_error() */
+    CT_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+    CT_EOVERFLOW = 5,     /* a size does not fit the index types (e.g. n >= 2^31) */
+    CT_EUNSUPPORTED = 6   /* valid but unsupported input (e.g. a string above the length limit) */
+} ct_status;
+
+typedef enum {
+    CT_L2_F32 = 0,        /* Euclidean distance over fp32 coordinates */
+    CT_LEVENSHTEIN_U8 = 1 /* edit distance, unit costs, over byte strings */
+} ct_metric;
+
+/* A cudaStream_t, passed as an opaque pointer so this header needs no CUDA headers. */
+typedef void *ct_stream;
+
+/* The point set P (paper Sec. III: a finite metric space).
+ *  CT_L2_F32:         data    = device, n*dim fp32, row-major, rows contiguous;
+ *                     offsets = NULL; 1 <= dim <= 4096.
+ *  CT_LEVENSHTEIN_U8: data    = device, concatenated byte strings;
+ *                     offsets = device, n+1 int64, string i is
+ *                     data[offsets[i] .. offsets[i+1]); dim ignored;
+ *                     every string at most CT_MAX_STRING_LEN bytes.
+ *  n may be 0.  n must be below 2^31 - 1. */
+typedef struct {
+    int32_t metric;
+    int32_t dim;
+    int64_t n;
+    const void *data;
+    const int64_t *offsets;
+} ct_points;
+
+#define CT_MAX_STRING_LEN 1024
+
+/* Build options.  leaf_size is ζ of Algorithm 2: a vertex with at most ζ
+ * points becomes a leaf block (<= 0 selects 32).  root is the index of the
+ * root point (the paper selects one point as the root; default 0). */
+typedef struct {
+    int32_t leaf_size;
+    int32_t root;
+} ct_build_opts;
+
+/* Query options.
+ *  precision:     0 = plain FP32 direct-difference leaf tiles;
+ *                 1 = BF16 tensor-core filter (tcgen05) with FP32 recheck.
+ *                 Both give the same edge set.
+ *  use_predictor: 0 = two-pass count -> scan -> emit;
+ *                 1 = one-pass emit into capacities predicted by `predictor`,
+ *                     with exact recount of overflowing rows.  Same output.
+ *  include_self:  1 adds the pair (i, i) to every row (d(p, p) = 0 <= eps).
+ *  predictor:     a ct_predictor* when use_predictor = 1, else NULL. */
+typedef struct {
+    int32_t precision;
+    int32_t use_predictor;
+    int32_t include_self;
+    int32_t reserved;
+    const void *predictor;
+} ct_query_opts;
+
+/* CSR output.  row_ptr: device int64[n_rows + 1]; col: device int32[nnz]
+ * (original point indices, ascending within a row); dist: device fp32[nnz]
+ * (the distance; within 1e-6 relative of the FP64 value for L2, exact
+ * integers for edit distance).  Pointers may be NULL when nnz == 0 (col,
+ * dist) or n_rows == 0 is still given a one-entry row_ptr. */
+typedef struct {
+    int64_t n_rows;
+    int64_t nnz;
+    int64_t *row_ptr;
+    int32_t *col;
+    float *dist;
+    void *priv;           /* library-owned; do not touch */
+} ct_csr;
+
+/* Counters of one query, read back with ct_csr_stats. */
+typedef struct {
+    int64_t traversal_evals;  /* distance evaluations in the tree walk (count pass) */
+    int64_t leaf_pairs;       /* (query, candidate point) pairs decided (count pass) */
+    int64_t guard_fp64;       /* pairs re-decided in FP64 (|d - eps| <= 1e-3 eps) */
+    int64_t recheck_fp32;     /* pairs re-evaluated in FP32 after the BF16 filter */
+    int64_t candidates;       /* (group, candidate leaf block) entries */
+    int64_t overflow_rows;    /* rows recounted after a predicted capacity overflowed */
+    int64_t kernel_launches;  /* kernels this library launched for the query */
+    int64_t reserved;
+} ct_query_stats;
+
+typedef struct ct_tree ct_tree;           /* opaque, device-resident */
+
+/* Cover-tree construction (Algorithms 1 and 2): level-wise vertex splitting on
+ * the GPU.  The points are copied into tree order, so the tree does not alias
+ * `points`.  Synchronises `stream` a few times per level (loop control).
+ * Errors: CT_EINVAL (null pointers, n < 0, bad metric or dim),
+ * CT_EUNSUPPORTED (string too long), CT_ENOMEM, CT_ECUDA. */
+ct_status ct_build(const ct_points *points, const ct_build_opts *opts, ct_stream stream,
+                   ct_tree **out);
+
+/* The ε-graph of the tree's point set (Sec. III definition; query by
+ * Algorithm 3 with batching, Sec. IV-B).  eps >= 0; for edit distance only
+ * floor(eps) matters.  On success *out holds a CSR in library-owned device
+ * memory (release with csr_free).  Synchronises `stream` once to learn nnz.
+ * Errors: CT_EINVAL (null pointers, eps < 0 or NaN, precision 1 with a
+ * non-L2 tree, use_predictor without predictor), CT_ENOMEM, CT_ECUDA. */
+ct_status eps_graph_query(const ct_tree *tree, double eps, const ct_query_opts *opts,
+                          ct_stream stream, ct_csr *out);
+
+/* Many point clouds in one call: outs[c] is the ε-graph of trees[c] with
+ * radius eps[c] (host array).  Work items of all clouds share one persistent
+ * launch per stage.  Same output as n_clouds calls of eps_graph_query. */
+ct_status eps_graph_query_batched(int32_t n_clouds, const ct_tree *const *trees,
+                                  const double *eps, const ct_query_opts *opts,
+                                  ct_stream stream, ct_csr *outs);
+
+/* Releases a CSR (stream-ordered on the stream it was produced on; that
+ * stream must still exist).  Idempotent and NULL-safe: zeroes *csr. */
+void csr_free(ct_csr *csr);
+
+/* Host copy of the counters recorded with `csr`. */
+ct_status ct_csr_stats(const ct_csr *csr, ct_query_stats *out);
+
+/* Releases a tree (synchronises the device).  NULL-safe. */
+void ct_tree_free(ct_tree *tree);
+
+/* Sizes of a tree: number of vertices (internal + leaf blocks) and points. */
+ct_status ct_tree_shape(const ct_tree *tree, int64_t *n_nodes, int64_t *n_points);
+
+/* Copies the tree to host arrays in the flat format (vertex 0 is the root;
+ * children of a vertex are consecutive ids; a leaf block lists its points
+ * in leaf_pts[pts_begin .. pts_begin + pts_count)).  Every array is host
+ * memory sized by ct_tree_shape: center, radius, level, child_begin,
+ * child_count, pts_begin, pts_count have n_nodes entries; leaf_pts has
+ * n_points.  Point ids are original indices.  Synchronises the device. */
+ct_status ct_tree_export(const ct_tree *tree, int64_t *center, double *radius, int32_t *level,
+                         int64_t *child_begin, int64_t *child_count, int64_t *pts_begin,
+                         int64_t *pts_count, int64_t *leaf_pts);
+
+/* Stage timing.  When enabled, every later ct_build / eps_graph_query call
+ * records a CUDA event pair around each of its stages on the caller's stream
+ * and adds the elapsed device time to a process-wide table (stage name ->
+ * total milliseconds, calls).  ct_profile_count() snapshots the table's names;
+ * ct_profile_entry(i, ...) reads entry i of that snapshot (the name stays
+ * valid until the next ct_profile_count).  Timing costs a few microseconds of
+ * host time per stage. */
+void ct_profile_enable(int32_t on);
+void ct_profile_reset(void);
+int32_t ct_profile_count(void);
+ct_status ct_profile_entry(int32_t i, const char **name, double *total_ms, int64_t *calls);
+
+/* Number of kernels this library has launched in this process so far. */
+int64_t ct_kernel_launches(void);
+
+/* Thread-local message for the last non-OK status of this thread. */
+const char *ct_last_error(void);
+
+/* Library version string. */
+const char *ct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTGRAPH_H */

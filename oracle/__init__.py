@@ -85,10 +85,15 @@ def _load():
             lib.orc_lev_banded.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32]
             lib.orc_brute_force.restype = C.POINTER(_Csr)
             lib.orc_brute_force.argtypes = [C.POINTER(_Space), C.c_double, C.c_int32]
+            lib.orc_brute_rows.restype = C.POINTER(_Csr)
+            lib.orc_brute_rows.argtypes = [C.POINTER(_Space), C.c_double, C.c_int32, C.c_void_p, C.c_int64]
             lib.orc_build_tree.restype = C.POINTER(_Tree)
             lib.orc_build_tree.argtypes = [C.POINTER(_Space), C.c_int32, C.c_int64]
             lib.orc_tree_query.restype = C.POINTER(_Csr)
             lib.orc_tree_query.argtypes = [C.POINTER(_Space), C.POINTER(_Tree), C.c_double, C.c_int32]
+            lib.orc_tree_query_rows.restype = C.POINTER(_Csr)
+            lib.orc_tree_query_rows.argtypes = [C.POINTER(_Space), C.POINTER(_Tree), C.c_double, C.c_int32,
+                                                C.c_void_p, C.c_int64]
             lib.orc_check_tree.restype = C.c_int32
             lib.orc_check_tree.argtypes = [C.POINTER(_Space), C.POINTER(_Tree), C.c_double,
                                            C.c_char_p, C.c_int32]
@@ -174,6 +179,14 @@ def brute_force(space: Space, eps: float, include_self: bool = False) -> dict:
     return _take_csr(_load().orc_brute_force(C.byref(space.c), float(eps), int(include_self)))
 
 
+def brute_rows(space: Space, eps: float, rows, include_self: bool = False) -> dict:
+    """Brute force for the given query rows only (row r lists the neighbours of
+    point rows[r])."""
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    return _take_csr(_load().orc_brute_rows(C.byref(space.c), float(eps), int(include_self),
+                                            r.ctypes.data, r.size))
+
+
 class Tree:
     """A cover tree in the flat export format (node 0 is the root; children are
     contiguous node ids; leaf blocks list their points in ``leaf_pts``)."""
@@ -234,6 +247,15 @@ def tree_query(space: Space, tree: Tree, eps: float, include_self: bool = False)
     ct = tree._c()
     return _take_csr(_load().orc_tree_query(C.byref(space.c), C.byref(ct), float(eps),
                                             int(include_self)))
+
+
+def tree_query_rows(space: Space, tree: Tree, eps: float, rows, include_self: bool = False) -> dict:
+    """Algorithm 3 for the given query rows only (row r lists the neighbours of
+    point rows[r])."""
+    ct = tree._c()
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    return _take_csr(_load().orc_tree_query_rows(C.byref(space.c), C.byref(ct), float(eps),
+                                                 int(include_self), r.ctypes.data, r.size))
 
 
 def check_tree(space: Space, tree: Tree, tol: float = 0.0):

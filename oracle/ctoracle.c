@@ -255,6 +255,28 @@ orc_csr *orc_brute_force(const orc_space *sp, double eps, int32_t include_self)
     return o;
 }
 
+/* Brute force restricted to the query rows `rows[0..k)` (ascending columns);
+ * row r of the result is the neighbour list of point rows[r]. */
+orc_csr *orc_brute_rows(const orc_space *sp, double eps, int32_t include_self, const int64_t *rows,
+                        int64_t k)
+{
+    int64_t n = sp->n;
+    double eps2 = eps * eps;
+    vec_t *out = (vec_t *)calloc((size_t)(k ? k : 1), sizeof(vec_t));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t r = 0; r < k; ++r) {
+        int64_t i = rows[r];
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i && !include_self) continue;
+            double d;
+            if (edge_pred(sp, i, j, eps, eps2, &d)) vec_push(&out[r], j, d);
+        }
+    }
+    orc_csr *o = assemble(k, out);
+    o->dist_evals = k * n;
+    return o;
+}
+
 /* ------------------------------------------------------------- cover tree */
 
 /* Flat tree export, shared format between this oracle and the GPU library's
@@ -449,12 +471,12 @@ void orc_tree_free(orc_tree *t)
  * root.  A child vertex v is pushed iff d(q, v) <= radius(v) + eps; the points
  * of a leaf block are leaf vertices B(p, 0), reported iff d(q, p) <= eps (the
  * pinned predicate). */
-orc_csr *orc_tree_query(const orc_space *sp, const orc_tree *t, double eps,
-                        int32_t include_self)
+orc_csr *orc_tree_query_rows(const orc_space *sp, const orc_tree *t, double eps,
+                             int32_t include_self, const int64_t *rows, int64_t n_rows)
 {
-    int64_t n = sp->n;
+    int64_t n = n_rows;
     double eps2 = eps * eps;
-    vec_t *rows = (vec_t *)calloc((size_t)(n ? n : 1), sizeof(vec_t));
+    vec_t *rows_out = (vec_t *)calloc((size_t)(n ? n : 1), sizeof(vec_t));
     int64_t evals = 0;
     if (n > 0) {
 #pragma omp parallel reduction(+ : evals)
@@ -462,7 +484,9 @@ orc_csr *orc_tree_query(const orc_space *sp, const orc_tree *t, double eps,
             int64_t scap = 256;
             int64_t *stack = (int64_t *)malloc(sizeof(int64_t) * (size_t)scap);
 #pragma omp for schedule(dynamic, 64)
-            for (int64_t q = 0; q < n; ++q) {
+            for (int64_t qr = 0; qr < n; ++qr) {
+                int64_t q = rows ? rows[qr] : qr;
+                vec_t *row = &rows_out[qr];
                 int64_t sp_top = 0;
                 stack[sp_top++] = 0;
                 while (sp_top > 0) {
@@ -474,7 +498,7 @@ orc_csr *orc_tree_query(const orc_space *sp, const orc_tree *t, double eps,
                             if (p == q && !include_self) continue;
                             double d;
                             evals++;
-                            if (edge_pred(sp, q, p, eps, eps2, &d)) vec_push(&rows[q], p, d);
+                            if (edge_pred(sp, q, p, eps, eps2, &d)) vec_push(row, p, d);
                         }
                         continue;
                     }
@@ -503,9 +527,14 @@ orc_csr *orc_tree_query(const orc_space *sp, const orc_tree *t, double eps,
             free(stack);
         }
     }
-    orc_csr *o = assemble(n, rows);
+    orc_csr *o = assemble(n, rows_out);
     o->dist_evals = evals;
     return o;
+}
+
+orc_csr *orc_tree_query(const orc_space *sp, const orc_tree *t, double eps, int32_t include_self)
+{
+    return orc_tree_query_rows(sp, t, eps, include_self, NULL, sp->n);
 }
 
 /* ---------------------------------------------------------- invariant check */

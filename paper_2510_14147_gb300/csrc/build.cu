@@ -1,0 +1,879 @@
+// build.cu -- cover-tree construction on the GPU (Algorithm 1 SplitVertex and
+// Algorithm 2 BuildLevel of the paper, Sec. IV-A).
+//
+// All hubs created in one round are split together.  One split iteration is
+// two launches over every hub of the round:
+//   k_hub_step      -- per hub: take the farthest point found by the previous
+//                      pass (largest D, lowest position on ties, as the strict
+//                      comparison of Algorithm 1 in scan order); stop the hub
+//                      once it lies within 2^(l-1), else make it the next centre;
+//   k_dist_update   -- per point of an active hub: d = d(p, newest centre);
+//                      if d < D[p] then D[p] = d, L[p] = new label (strict <);
+//                      then the hub's argmax of D by a packed 64-bit atomicMax.
+// When every hub has stopped, the round's points are partitioned by
+// (hub, label) with a stable radix sort; each child's centre is moved to the
+// front of its range, its radius is the max of D over its range, and a child
+// with more than zeta points and positive radius becomes a hub of the next
+// round at level ceil(log2 r) (levels with a single nested child are skipped);
+// the others become leaf blocks.  Radii are stored rounded up so that they
+// bound every descendant's exact distance.
+//
+// Distances are fp32 for L2 (direct differences) and exact integers for edit
+// distance (bit-parallel, lev.cuh).
+#include <climits>
+#include <cstdio>
+#include <memory>
+#include <vector>
+#include <algorithm>
+
+#include "common.cuh"
+#include "lev.cuh"
+#include "profile.cuh"
+
+namespace ct {
+
+namespace {
+
+constexpr int BT = 256;  // threads per block in the build kernels
+constexpr int32_t kNone = 0x7f7f7f7f;  // byte-fill 0x7f: "no position yet"
+
+// ceil(log2 r) for finite r > 0 (exact at powers of two).
+__device__ __forceinline__ int ceil_log2f(float r) {
+    int e;
+    float m = frexpf(r, &e);  // r = m * 2^e, m in [0.5, 1)
+    return m == 0.5f ? e - 1 : e;
+}
+
+// Rounded-up radius: bounds the exact distance of every point whose fp32
+// distance was at most r (fp32 relative error of the distance sums here is
+// below 2^-17 for rows up to 4096 floats; absolute slack covers underflow).
+__device__ __forceinline__ float round_radius_up(float r, int metric) {
+    if (metric != CT_L2_F32) return r;
+    if (r == 0.0f) return 0.0f;
+    float t = __fmul_ru(r, 1.0f + 0x1p-16f);
+    return __fadd_ru(t, 0x1p-64f);
+}
+
+// ---- L2 distance of a point row to a centre row held in shared memory.
+// TPD threads cooperate on one distance; lane j reads float4s j, j+TPD, ...
+template <int TPD>
+__device__ __forceinline__ float group_sqdist(const float4 *__restrict__ row, const float4 *cen,
+                                              int nq, int j) {
+    float acc = 0.f;
+    for (int k = j; k < nq; k += TPD) {
+        float4 a = __ldg(row + k);
+        float4 b = cen[k];
+        float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
+        acc = fmaf(dx, dx, acc);
+        acc = fmaf(dy, dy, acc);
+        acc = fmaf(dz, dz, acc);
+        acc = fmaf(dw, dw, acc);
+    }
+#pragma unroll
+    for (int o = TPD / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPD);
+    return acc;
+}
+
+struct Hubs {
+    int32_t *begin, *count, *node, *nc, *cur, *done, *level;
+    float *thr;
+    unsigned long long *key;
+};
+
+template <int TPD>
+__global__ void __launch_bounds__(BT) k_dist_update_l2(
+    const float *__restrict__ X, int dp, const int32_t *__restrict__ ids, float *__restrict__ D,
+    int32_t *__restrict__ lab, const int32_t *__restrict__ chunk_hub,
+    const int32_t *__restrict__ chunk_start, int chunk_len, Hubs hb) {
+    extern __shared__ float4 cen[];
+    int c = blockIdx.x;
+    int h = chunk_hub[c];
+    if (hb.done[h]) return;
+    int start = chunk_start[c];
+    int end = min(start + chunk_len, hb.begin[h] + hb.count[h]);
+    int cpos = hb.cur[h];
+    int lbl = hb.nc[h] - 1;
+    int nq = dp >> 2;
+    const float4 *crow = reinterpret_cast<const float4 *>(X + (size_t)ids[cpos] * dp);
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) cen[i] = crow[i];
+    __syncthreads();
+    constexpr int G = BT / TPD;
+    int g = threadIdx.x / TPD, j = threadIdx.x % TPD;
+    unsigned long long best = 0ull;
+    for (int base = start; base < end; base += G) {
+        int pos = base + g;
+        bool valid = pos < end;
+        int row_id = valid ? ids[pos] : ids[start];
+        float s = group_sqdist<TPD>(reinterpret_cast<const float4 *>(X + (size_t)row_id * dp), cen,
+                                    nq, j);
+        if (valid && j == 0) {
+            float d = sqrtf(s);
+            float cur = D[pos];
+            if (d < cur) {
+                D[pos] = d;
+                lab[pos] = lbl;
+                cur = d;
+            }
+            unsigned long long k = pack_max_key(cur, (uint32_t)pos);
+            best = k > best ? k : best;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+        best = v > best ? v : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(&hb.key[h], best);
+}
+
+// Edit distance: one thread per point; the newest centre is the pattern of
+// the bit-parallel recurrence, its match masks in shared memory.
+template <int W>
+__global__ void __launch_bounds__(BT) k_dist_update_lev(
+    const uint8_t *__restrict__ S, const int64_t *__restrict__ off, const int32_t *__restrict__ ids,
+    float *__restrict__ D, int32_t *__restrict__ lab, const int32_t *__restrict__ chunk_hub,
+    const int32_t *__restrict__ chunk_start, int chunk_len, Hubs hb) {
+    __shared__ uint64_t peq[256 * W];
+    int c = blockIdx.x;
+    int h = chunk_hub[c];
+    if (hb.done[h]) return;
+    int start = chunk_start[c];
+    int end = min(start + chunk_len, hb.begin[h] + hb.count[h]);
+    int cid = ids[hb.cur[h]];
+    int lbl = hb.nc[h] - 1;
+    const uint8_t *pat = S + off[cid];
+    int m = (int)(off[cid + 1] - off[cid]);
+    lev_build_peq<W>(peq, pat, m);
+    __syncthreads();
+    unsigned long long best = 0ull;
+    for (int base = start; base < end; base += blockDim.x) {
+        int pos = base + threadIdx.x;
+        if (pos < end) {
+            int id = ids[pos];
+            const uint8_t *txt = S + off[id];
+            int n = (int)(off[id + 1] - off[id]);
+            float cur = D[pos];
+            int cutoff = isinf(cur) ? INT_MAX / 2 : (int)cur - 1;
+            int d = lev_myers<W>(peq, m, txt, n, cutoff);
+            if (d <= cutoff && (float)d < cur) {
+                D[pos] = (float)d;
+                lab[pos] = lbl;
+                cur = (float)d;
+            }
+            unsigned long long k = pack_max_key(cur, (uint32_t)pos);
+            best = k > best ? k : best;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+        best = v > best ? v : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(&hb.key[h], best);
+}
+
+// One thread per hub: decide termination or choose the next centre.
+__global__ void k_hub_step(int nh, Hubs hb, int32_t *__restrict__ active_out) {
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    int act = 0;
+    if (h < nh && !hb.done[h]) {
+        unsigned long long k = hb.key[h];
+        float v = key_value(k);
+        if (k == 0ull || !(v > hb.thr[h])) {
+            hb.done[h] = 1;
+        } else {
+            hb.cur[h] = (int32_t)key_pos(k);
+            hb.nc[h] += 1;
+            hb.key[h] = 0ull;
+            act = 1;
+        }
+    }
+    unsigned b = __ballot_sync(0xffffffffu, act);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(active_out, __popc(b));
+}
+
+// Chunk table of a round: chunk -> (hub, first position).
+__global__ void k_chunk_counts(int nh, const int32_t *__restrict__ count, int chunk_len,
+                               int32_t *__restrict__ out) {
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h < nh) out[h] = (count[h] + chunk_len - 1) / chunk_len;
+}
+__global__ void k_chunk_fill(int nh, const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+                             const int64_t *__restrict__ coff, int chunk_len,
+                             int32_t *__restrict__ chunk_hub, int32_t *__restrict__ chunk_start) {
+    int h = blockIdx.x;
+    if (h >= nh) return;
+    int nchunks = (count[h] + chunk_len - 1) / chunk_len;
+    for (int i = threadIdx.x; i < nchunks; i += blockDim.x) {
+        chunk_hub[coff[h] + i] = h;
+        chunk_start[coff[h] + i] = begin[h] + i * chunk_len;
+    }
+}
+
+// Partition keys for the round: key = child_base[hub] + label, value = round index.
+__global__ void k_part_keys(int nh, const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+                            const int64_t *__restrict__ round_off, const int64_t *__restrict__ child_base,
+                            const int32_t *__restrict__ lab, uint32_t *__restrict__ keys,
+                            uint32_t *__restrict__ vals, int32_t *__restrict__ rpos) {
+    int h = blockIdx.x;
+    int b = begin[h], cnt = count[h];
+    int64_t ro = round_off[h], cb = child_base[h];
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        int64_t r = ro + i;
+        keys[r] = (uint32_t)(cb + lab[b + i]);
+        vals[r] = (uint32_t)r;
+        rpos[r] = b + i;
+    }
+}
+
+// Gather the round in sorted order into temporaries; per child: count, first
+// position, first zero-distance position (its centre or a duplicate of it).
+__global__ void k_part_gather(int64_t R, const uint32_t *__restrict__ skeys, const uint32_t *__restrict__ svals,
+                              const int32_t *__restrict__ rpos, const int32_t *__restrict__ ids,
+                              const float *__restrict__ D, int32_t *__restrict__ tids,
+                              float *__restrict__ tD, int32_t *__restrict__ ccount,
+                              int32_t *__restrict__ cbegin, int32_t *__restrict__ czero) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R) return;
+    int src = rpos[svals[i]];
+    int dst = rpos[i];
+    uint32_t gc = skeys[i];
+    float d = D[src];
+    tids[i] = ids[src];
+    tD[i] = d;
+    atomicAdd(&ccount[gc], 1);
+    atomicMin(&cbegin[gc], dst);
+    if (d == 0.0f) atomicMin(&czero[gc], dst);
+}
+
+// Writes the sorted round back; every point starts the next round labelled 0
+// (the centre of the child it now belongs to).
+__global__ void k_part_scatter(int64_t R, const int32_t *__restrict__ rpos, const int32_t *__restrict__ tids,
+                               const float *__restrict__ tD, int32_t *__restrict__ ids,
+                               float *__restrict__ D, int32_t *__restrict__ lab) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R) return;
+    int dst = rpos[i];
+    ids[dst] = tids[i];
+    D[dst] = tD[i];
+    lab[dst] = 0;
+}
+
+// Move each child's centre to the front of its range.
+__global__ void k_centre_front(int64_t T, const int32_t *__restrict__ cbegin, const int32_t *__restrict__ czero,
+                               int32_t *__restrict__ ids, float *__restrict__ D, int32_t *__restrict__ err) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= T) return;
+    int b = cbegin[c], z = czero[c];
+    if (z == kNone) { atomicOr(err, 1); return; }
+    if (z != b) {
+        int ti = ids[b]; ids[b] = ids[z]; ids[z] = ti;
+        float td = D[b]; D[b] = D[z]; D[z] = td;
+    }
+}
+
+__global__ void k_child_keys(int64_t R, const uint32_t *__restrict__ skeys, const int32_t *__restrict__ rpos,
+                             const float *__restrict__ D, unsigned long long *__restrict__ ckey) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R) return;
+    int pos = rpos[i];
+    atomicMax(&ckey[skeys[i]], pack_max_key(D[pos], (uint32_t)pos));
+}
+
+// Link every hub to its children (consecutive node ids).
+__global__ void k_link_children(int nh, Hubs hb, const int64_t *__restrict__ child_base, int node_base,
+                                int32_t *__restrict__ child_begin, int32_t *__restrict__ child_count,
+                                int32_t *__restrict__ node_level, int32_t *__restrict__ parent) {
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= nh) return;
+    int u = hb.node[h];
+    int first = node_base + (int32_t)child_base[h];
+    child_begin[u] = first;
+    child_count[u] = hb.nc[h];
+    node_level[u] = hb.level[h];
+    for (int c = 0; c < hb.nc[h]; ++c) parent[first + c] = u;
+}
+
+// New vertices of the round; flags children that become next-round hubs.
+__global__ void k_make_nodes(int64_t T, int node_base, int zeta, int metric,
+                             const int32_t *__restrict__ cbegin, const int32_t *__restrict__ ccount,
+                             const unsigned long long *__restrict__ ckey, int32_t *__restrict__ node_begin,
+                             int32_t *__restrict__ node_count, int32_t *__restrict__ child_begin,
+                             int32_t *__restrict__ child_count, float *__restrict__ radius,
+                             int32_t *__restrict__ level, int32_t *__restrict__ is_hub) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= T) return;
+    int v = node_base + (int)c;
+    float r = key_value(ckey[c]);
+    node_begin[v] = cbegin[c];
+    node_count[v] = ccount[c];
+    child_begin[v] = 0;
+    child_count[v] = 0;
+    radius[v] = round_radius_up(r, metric);
+    level[v] = r > 0.0f ? ceil_log2f(r) : INT_MIN;
+    is_hub[c] = (ccount[c] > zeta && r > 0.0f) ? 1 : 0;
+}
+
+// Next round's hubs from the flagged children (order preserved).
+__global__ void k_next_hubs(int64_t T, int node_base, const int32_t *__restrict__ is_hub,
+                            const int64_t *__restrict__ hub_off, const int32_t *__restrict__ cbegin,
+                            const int32_t *__restrict__ ccount, const unsigned long long *__restrict__ ckey,
+                            const int32_t *__restrict__ level, Hubs nh) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= T || !is_hub[c]) return;
+    int64_t h = hub_off[c];
+    int v = node_base + (int)c;
+    nh.begin[h] = cbegin[c];
+    nh.count[h] = ccount[c];
+    nh.node[h] = v;
+    nh.nc[h] = 1;
+    nh.cur[h] = cbegin[c];
+    nh.done[h] = 0;
+    nh.key[h] = ckey[c];
+    int l = level[v];
+    nh.level[h] = l;
+    nh.thr[h] = ldexpf(1.0f, l - 1);
+}
+
+__global__ void k_root_init(int64_t n, int root, int32_t *__restrict__ ids, float *__restrict__ D,
+                            int32_t *__restrict__ lab) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    ids[i] = i == 0 ? root : (i <= root ? (int32_t)i - 1 : (int32_t)i);
+    D[i] = INFINITY;
+    lab[i] = 0;
+}
+
+__global__ void k_root_node(int64_t n, int zeta, int metric, const unsigned long long *__restrict__ key,
+                            int32_t *__restrict__ node_begin, int32_t *__restrict__ node_count,
+                            int32_t *__restrict__ child_begin, int32_t *__restrict__ child_count,
+                            float *__restrict__ radius, int32_t *__restrict__ level, Hubs hb,
+                            int32_t *__restrict__ is_hub) {
+    float r = key_value(key[0]);
+    node_begin[0] = 0;
+    node_count[0] = (int32_t)n;
+    child_begin[0] = 0;
+    child_count[0] = 0;
+    radius[0] = round_radius_up(r, metric);
+    int l = r > 0.0f ? ceil_log2f(r) : INT_MIN;
+    level[0] = l;
+    int hub = (n > zeta && r > 0.0f) ? 1 : 0;
+    *is_hub = hub;
+    // the root hub for the first round
+    hb.begin[0] = 0;
+    hb.count[0] = (int32_t)n;
+    hb.node[0] = 0;
+    hb.nc[0] = 1;
+    hb.cur[0] = 0;
+    hb.done[0] = 0;
+    hb.key[0] = key[0];
+    hb.level[0] = l;
+    hb.thr[0] = hub ? ldexpf(1.0f, l - 1) : 0.0f;
+}
+
+// Pad rows to dp floats (original order) and check the coordinate range.
+__global__ void k_pad_rows(const float *__restrict__ src, int64_t n, int dim, int dp,
+                           float *__restrict__ dst, int32_t *__restrict__ bad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * dp) return;
+    int64_t r = i / dp;
+    int k = (int)(i - r * dp);
+    float v = k < dim ? src[r * dim + k] : 0.0f;
+    if (!(fabsf(v) <= 0x1p50f)) atomicOr(bad, 1);
+    dst[i] = v;
+}
+
+__global__ void k_gather_rows(const float *__restrict__ Xp, int dp, const int32_t *__restrict__ perm,
+                              int64_t n, float *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int nq = dp >> 2;
+    if (i >= n * nq) return;
+    int64_t r = i / nq;
+    int k = (int)(i - r * nq);
+    reinterpret_cast<float4 *>(out)[i] = reinterpret_cast<const float4 *>(Xp + (size_t)perm[r] * dp)[k];
+}
+
+__global__ void k_node_centres(int nn, const int32_t *__restrict__ node_begin, const float *__restrict__ pts,
+                               int dp, float *__restrict__ ctr) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int nq = dp >> 2;
+    if (i >= (int64_t)nn * nq) return;
+    int64_t v = i / nq;
+    int k = (int)(i - v * nq);
+    reinterpret_cast<float4 *>(ctr)[i] =
+        reinterpret_cast<const float4 *>(pts + (size_t)node_begin[v] * dp)[k];
+}
+
+__global__ void k_leaf_keys(int nn, const int32_t *__restrict__ child_count, const int32_t *__restrict__ node_begin,
+                            const int32_t *__restrict__ node_count, uint32_t *__restrict__ keys,
+                            uint32_t *__restrict__ vals, int32_t *__restrict__ nleaf,
+                            int32_t *__restrict__ maxcnt) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nn || child_count[v] != 0) return;
+    int slot = atomicAdd(nleaf, 1);
+    keys[slot] = (uint32_t)node_begin[v];
+    vals[slot] = (uint32_t)v;
+    atomicMax(maxcnt, node_count[v]);
+}
+
+__global__ void k_string_lengths(int64_t n, const int32_t *__restrict__ perm, const int64_t *__restrict__ off,
+                                 int64_t *__restrict__ len_out, int32_t *__restrict__ maxlen) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t id = perm ? perm[i] : i;
+    int64_t l = off[id + 1] - off[id];
+    len_out[i] = l;
+    atomicMax(maxlen, (int32_t)(l < INT_MAX ? l : INT_MAX));
+}
+
+__global__ void k_gather_strings(int64_t n, const int32_t *__restrict__ perm, const uint8_t *__restrict__ S,
+                                 const int64_t *__restrict__ off, const int64_t *__restrict__ noff,
+                                 uint8_t *__restrict__ out) {
+    int64_t i = blockIdx.x;
+    if (i >= n) return;
+    int64_t id = perm[i];
+    int64_t b = off[id], l = off[id + 1] - b, o = noff[i];
+    for (int64_t k = threadIdx.x; k < l; k += blockDim.x) out[o + k] = S[b + k];
+}
+
+// Radius of each query group: max distance from its first point (rounded up).
+// One warp per group, one lane per point.
+__global__ void k_group_radius_l2(int ng, const int32_t *__restrict__ gbeg, const int32_t *__restrict__ gcnt,
+                                  const float *__restrict__ pts, int dp, float *__restrict__ grad) {
+    int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (g >= ng) return;
+    const float4 *c = reinterpret_cast<const float4 *>(pts + (size_t)gbeg[g] * dp);
+    float r = 0.f;
+    for (int i = lane; i < gcnt[g]; i += 32) {
+        const float4 *p = reinterpret_cast<const float4 *>(pts + (size_t)(gbeg[g] + i) * dp);
+        float acc = 0.f;
+        for (int k = 0; k < dp / 4; ++k) {
+            float4 a = __ldg(c + k), b = __ldg(p + k);
+            float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
+            acc = fmaf(dx, dx, acc); acc = fmaf(dy, dy, acc); acc = fmaf(dz, dz, acc); acc = fmaf(dw, dw, acc);
+        }
+        r = fmaxf(r, sqrtf(acc));
+    }
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (lane == 0) grad[g] = round_radius_up(r, CT_L2_F32);
+}
+
+template <int W>
+__global__ void __launch_bounds__(32) k_group_radius_lev(int ng, const int32_t *__restrict__ gbeg,
+                                                         const int32_t *__restrict__ gcnt,
+                                                         const uint8_t *__restrict__ S,
+                                                         const int64_t *__restrict__ off, float *__restrict__ grad) {
+    __shared__ uint64_t peq[256 * W];
+    int g = blockIdx.x;
+    if (g >= ng) return;
+    int cpos = gbeg[g];
+    const uint8_t *pat = S + off[cpos];
+    int m = (int)(off[cpos + 1] - off[cpos]);
+    lev_build_peq<W>(peq, pat, m);
+    __syncthreads();
+    int r = 0;
+    for (int i = threadIdx.x; i < gcnt[g]; i += 32) {
+        int p = cpos + i;
+        int d = lev_myers<W>(peq, m, S + off[p], (int)(off[p + 1] - off[p]), INT_MAX / 2);
+        r = max(r, d);
+    }
+    for (int o = 16; o > 0; o >>= 1) r = max(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (threadIdx.x == 0) grad[g] = (float)r;
+}
+
+inline unsigned grid_for(int64_t n, int t = BT) { return (unsigned)ceil_div(n > 0 ? n : 1, t); }
+
+int bits_for(int64_t v) {
+    int b = 0;
+    while ((int64_t(1) << b) <= v && b < 62) ++b;
+    return b;
+}
+
+}  // namespace
+
+// Builds the tree; on failure throws ct::Error after freeing what it allocated.
+void free_tree(ct_tree *t);
+
+namespace {
+struct TreeGuard {
+    ct_tree *t;
+    ~TreeGuard() { if (t) free_tree(t); }
+};
+}  // namespace
+
+ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
+    const int64_t n = pts->n;
+    TreeGuard tg{new ct_tree()};
+    ct_tree *t = tg.t;
+    struct Flush { ~Flush() { prof_flush(); } } flush_at_exit;
+    ProfScope prof_all("build", s);
+    t->metric = pts->metric;
+    t->n = n;
+    t->leaf_size = zeta;
+    t->stream = s;
+    CT_CHECK_CUDA(cudaGetDevice(&t->device));
+    const bool l2 = pts->metric == CT_L2_F32;
+    t->dim = l2 ? pts->dim : 0;
+    t->dp = l2 ? (int)ceil_div(pts->dim, 4) * 4 : 0;
+    const int dp = t->dp;
+
+    DBuf<int32_t> err(2, s);
+    CT_CHECK_CUDA(cudaMemsetAsync(err.p, 0, 2 * sizeof(int32_t), s));
+
+    // padded copy of the input (original order) / string lengths
+    DBuf<float> Xp;
+    int W = 1;
+    if (l2) {
+        Xp = DBuf<float>((size_t)n * dp, s);
+        if (n) {
+            k_pad_rows<<<grid_for(n * dp), BT, 0, s>>>((const float *)pts->data, n, pts->dim, dp, Xp.p, err.p);
+            CT_COUNT_LAUNCH();
+        }
+    } else {
+        DBuf<int64_t> lens(n > 0 ? n : 1, s);
+        if (n) {
+            k_string_lengths<<<grid_for(n), BT, 0, s>>>(n, nullptr, pts->offsets, lens.p, err.p + 1);
+            CT_COUNT_LAUNCH();
+        }
+    }
+    CT_LAUNCH_CHECK();
+    int32_t herr[2] = {0, 0};
+    to_host(herr, err.p, 2, s);
+    if (herr[0]) CT_FAIL(CT_EUNSUPPORTED, "coordinates must be finite with |x| <= 2^50");
+    if (!l2) {
+        if (herr[1] > CT_MAX_STRING_LEN)
+            CT_FAIL(CT_EUNSUPPORTED, "string of length %d above the limit %d", herr[1], CT_MAX_STRING_LEN);
+        t->max_len = herr[1];
+        W = lev_words_for(t->max_len);
+    }
+
+    // tree arrays: a tree whose internal vertices have >= 2 children has < 2n vertices
+    const int64_t cap = 2 * n + 1;
+    DBuf<int32_t> nb(cap, s), ncnt(cap, s), cbeg(cap, s), ccnt(cap, s), lvl(cap, s), par(cap, s);
+    CT_CHECK_CUDA(cudaMemsetAsync(par.p, 0xff, cap * sizeof(int32_t), s));
+    DBuf<float> rad(cap, s);
+    DBuf<int32_t> ids(n ? n : 1, s), lab(n ? n : 1, s);
+    DBuf<float> D(n ? n : 1, s);
+
+    int n_nodes = 0, depth = 0;
+    if (n > 0) {
+        if (root < 0 || root >= n) CT_FAIL(CT_EINVAL, "root %d out of range", root);
+        // ---- round 0: distances to the root
+        const int64_t cap_h = n;  // hubs per round never exceed n / (zeta+1) + 1
+        DBuf<int32_t> hbuf(7 * (cap_h + 1), s);
+        DBuf<float> hthr(cap_h + 1, s);
+        DBuf<unsigned long long> hkey(cap_h + 1, s);
+        DBuf<int32_t> hbuf2(7 * (cap_h + 1), s);
+        DBuf<float> hthr2(cap_h + 1, s);
+        DBuf<unsigned long long> hkey2(cap_h + 1, s);
+        auto make_hubs = [&](DBuf<int32_t> &b, DBuf<float> &th, DBuf<unsigned long long> &k) {
+            Hubs h;
+            int64_t st = cap_h + 1;
+            h.begin = b.p; h.count = b.p + st; h.node = b.p + 2 * st; h.nc = b.p + 3 * st;
+            h.cur = b.p + 4 * st; h.done = b.p + 5 * st; h.level = b.p + 6 * st;
+            h.thr = th.p; h.key = k.p;
+            return h;
+        };
+        Hubs H = make_hubs(hbuf, hthr, hkey), H2 = make_hubs(hbuf2, hthr2, hkey2);
+
+        k_root_init<<<grid_for(n), BT, 0, s>>>(n, root, ids.p, D.p, lab.p);
+        CT_COUNT_LAUNCH();
+        // one pass of the update kernel with the root as the only centre
+        const int tpd = l2 ? (dp >= 128 ? 32 : dp >= 64 ? 16 : dp >= 32 ? 8 : dp >= 16 ? 4 : dp >= 8 ? 2 : 1) : 1;
+        const int chunk_len = l2 ? 32 * (BT / tpd) : 4 * BT;
+        auto update = [&](Hubs &hb, int64_t nchunks, const int32_t *chub, const int32_t *cst) {
+            if (!nchunks) return;
+            if (l2) {
+                size_t sm = (size_t)dp * sizeof(float);
+                switch (tpd) {
+#define CT_UPD(T) case T: k_dist_update_l2<T><<<(unsigned)nchunks, BT, sm, s>>>(Xp.p, dp, ids.p, D.p, lab.p, chub, cst, chunk_len, hb); break;
+                    CT_UPD(1) CT_UPD(2) CT_UPD(4) CT_UPD(8) CT_UPD(16) CT_UPD(32)
+#undef CT_UPD
+                }
+            } else {
+                const uint8_t *S = (const uint8_t *)pts->data;
+                switch (W) {
+#define CT_UPDL(WW) case WW: k_dist_update_lev<WW><<<(unsigned)nchunks, BT, 0, s>>>(S, pts->offsets, ids.p, D.p, lab.p, chub, cst, chunk_len, hb); break;
+                    CT_UPDL(1) CT_UPDL(2) CT_UPDL(4) CT_UPDL(8) CT_UPDL(16)
+#undef CT_UPDL
+                }
+            }
+            CT_COUNT_LAUNCH();
+            CT_LAUNCH_CHECK();
+        };
+        // root hub state for the initial pass: centre = position 0, label 0
+        {
+            int32_t one = 1;
+            int32_t zero = 0;
+            unsigned long long z = 0;
+            CT_CHECK_CUDA(cudaMemcpyAsync(H.begin, &zero, 4, cudaMemcpyHostToDevice, s));
+            int32_t cnt = (int32_t)n;
+            CT_CHECK_CUDA(cudaMemcpyAsync(H.count, &cnt, 4, cudaMemcpyHostToDevice, s));
+            CT_CHECK_CUDA(cudaMemcpyAsync(H.nc, &one, 4, cudaMemcpyHostToDevice, s));
+            CT_CHECK_CUDA(cudaMemcpyAsync(H.cur, &zero, 4, cudaMemcpyHostToDevice, s));
+            CT_CHECK_CUDA(cudaMemcpyAsync(H.done, &zero, 4, cudaMemcpyHostToDevice, s));
+            CT_CHECK_CUDA(cudaMemcpyAsync(H.key, &z, 8, cudaMemcpyHostToDevice, s));
+            CT_CHECK_CUDA(cudaStreamSynchronize(s));  // host values above are on the stack
+        }
+        int64_t nchunks0 = ceil_div(n, chunk_len);
+        DBuf<int32_t> chub(nchunks0, s), cst(nchunks0, s);
+        {
+            DBuf<int64_t> coff(1, s);
+            CT_CHECK_CUDA(cudaMemsetAsync(coff.p, 0, sizeof(int64_t), s));
+            k_chunk_fill<<<1, BT, 0, s>>>(1, H.begin, H.count, coff.p, chunk_len, chub.p, cst.p);
+            CT_COUNT_LAUNCH();
+            update(H, nchunks0, chub.p, cst.p);
+        }
+        DBuf<int32_t> is_root_hub(1, s);
+        k_root_node<<<1, 1, 0, s>>>(n, zeta, pts->metric, H.key, nb.p, ncnt.p, cbeg.p, ccnt.p, rad.p, lvl.p, H,
+                                    is_root_hub.p);
+        CT_COUNT_LAUNCH();
+        CT_LAUNCH_CHECK();
+        int32_t root_hub = 0;
+        to_host(&root_hub, is_root_hub.p, 1, s);
+        n_nodes = 1;
+        int64_t nh = root_hub ? 1 : 0;
+
+        // scratch for partitioning
+        DBuf<uint32_t> pk(n, s), pv(n, s), tk(n, s), tv(n, s);
+        DBuf<int32_t> rpos(n, s), tids(n, s);
+        DBuf<float> tD(n, s);
+        DBuf<int32_t> active(1, s);
+        DBuf<int64_t> i64tmp(2, s);
+
+        while (nh > 0) {
+            ++depth;
+            // chunk table of this round
+            DBuf<int32_t> ccounts(nh, s);
+            DBuf<int64_t> coff(nh, s);
+            k_chunk_counts<<<grid_for(nh), BT, 0, s>>>((int)nh, H.count, chunk_len, ccounts.p);
+            CT_COUNT_LAUNCH();
+            exclusive_scan_i32_to_i64(ccounts.p, coff.p, nh, i64tmp.p, s);
+            int64_t nchunks = 0;
+            to_host(&nchunks, i64tmp.p, 1, s);
+            chub.grow(nchunks);
+            cst.grow(nchunks);
+            k_chunk_fill<<<(unsigned)nh, 64, 0, s>>>((int)nh, H.begin, H.count, coff.p, chunk_len, chub.p, cst.p);
+            CT_COUNT_LAUNCH();
+            CT_LAUNCH_CHECK();
+
+            // split iterations (Algorithm 1) for every hub of the round
+            {
+                ProfScope prof_split("build_split", s);
+                int burst = 1;
+                int64_t iters = 0;
+                for (;;) {
+                    // every iteration adds a distinct centre to some hub
+                    if (iters > n + 2) CT_FAIL(CT_ECUDA, "split loop did not terminate");
+                    iters += burst;
+                    CT_CHECK_CUDA(cudaMemsetAsync(active.p, 0, sizeof(int32_t), s));
+                    for (int it = 0; it < burst; ++it) {
+                        k_hub_step<<<grid_for(nh), BT, 0, s>>>((int)nh, H, active.p);
+                        CT_COUNT_LAUNCH();
+                        update(H, nchunks, chub.p, cst.p);
+                    }
+                    int32_t act = 0;
+                    to_host(&act, active.p, 1, s);
+                    if (act == 0) break;
+                    burst = burst < 16 ? burst * 2 : 16;
+                }
+            }
+
+            // partition the round's points by (hub, label)
+            DBuf<int32_t> ncs(nh, s);
+            DBuf<int64_t> child_base(nh, s), round_off(nh, s);
+            CT_CHECK_CUDA(cudaMemcpyAsync(ncs.p, H.nc, nh * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+            exclusive_scan_i32_to_i64(ncs.p, child_base.p, nh, i64tmp.p, s);
+            exclusive_scan_i32_to_i64(H.count, round_off.p, nh, i64tmp.p + 1, s);
+            int64_t tot[2];
+            to_host(tot, i64tmp.p, 2, s);
+            const int64_t T = tot[0], R = tot[1];
+            if (n_nodes + T > cap) CT_FAIL(CT_ECUDA, "vertex capacity exceeded");
+            k_part_keys<<<(unsigned)nh, BT, 0, s>>>((int)nh, H.begin, H.count, round_off.p, child_base.p, lab.p,
+                                                    pk.p, pv.p, rpos.p);
+            CT_COUNT_LAUNCH();
+            radix_sort_pairs(pk.p, pv.p, tk.p, tv.p, R, bits_for(T), s);
+            DBuf<int32_t> ccount(T, s), cbegin(T, s), czero(T, s), is_hub(T, s);
+            DBuf<unsigned long long> ckey(T, s);
+            CT_CHECK_CUDA(cudaMemsetAsync(ccount.p, 0, T * sizeof(int32_t), s));
+            CT_CHECK_CUDA(cudaMemsetAsync(cbegin.p, 0x7f, T * sizeof(int32_t), s));
+            CT_CHECK_CUDA(cudaMemsetAsync(czero.p, 0x7f, T * sizeof(int32_t), s));
+            CT_CHECK_CUDA(cudaMemsetAsync(ckey.p, 0, T * sizeof(unsigned long long), s));
+            k_part_gather<<<grid_for(R), BT, 0, s>>>(R, pk.p, pv.p, rpos.p, ids.p, D.p, tids.p, tD.p, ccount.p,
+                                                     cbegin.p, czero.p);
+            CT_COUNT_LAUNCH();
+            k_part_scatter<<<grid_for(R), BT, 0, s>>>(R, rpos.p, tids.p, tD.p, ids.p, D.p, lab.p);
+            CT_COUNT_LAUNCH();
+            k_centre_front<<<grid_for(T), BT, 0, s>>>(T, cbegin.p, czero.p, ids.p, D.p, err.p);
+            CT_COUNT_LAUNCH();
+            k_child_keys<<<grid_for(R), BT, 0, s>>>(R, pk.p, rpos.p, D.p, ckey.p);
+            CT_COUNT_LAUNCH();
+            k_link_children<<<grid_for(nh), BT, 0, s>>>((int)nh, H, child_base.p, n_nodes, cbeg.p, ccnt.p, lvl.p, par.p);
+            CT_COUNT_LAUNCH();
+            k_make_nodes<<<grid_for(T), BT, 0, s>>>(T, n_nodes, zeta, pts->metric, cbegin.p, ccount.p, ckey.p,
+                                                    nb.p, ncnt.p, cbeg.p, ccnt.p, rad.p, lvl.p, is_hub.p);
+            CT_COUNT_LAUNCH();
+            DBuf<int64_t> hub_off(T, s);
+            exclusive_scan_i32_to_i64(is_hub.p, hub_off.p, T, i64tmp.p, s);
+            int64_t nh2 = 0;
+            to_host(&nh2, i64tmp.p, 1, s);
+            if (nh2 > cap_h) CT_FAIL(CT_ECUDA, "hub capacity exceeded");
+            k_next_hubs<<<grid_for(T), BT, 0, s>>>(T, n_nodes, is_hub.p, hub_off.p, cbegin.p, ccount.p, ckey.p, lvl.p,
+                                                   H2);
+            CT_COUNT_LAUNCH();
+            CT_LAUNCH_CHECK();
+            n_nodes += (int)T;
+            std::swap(H, H2);
+            nh = nh2;
+        }
+        int32_t e2 = 0;
+        to_host(&e2, err.p, 1, s);
+        if (e2) CT_FAIL(CT_ECUDA, "internal: a child without a zero-distance centre");
+    }
+
+    // ---- final layout
+    t->n_nodes = n_nodes;
+    t->depth = depth;
+    t->perm = ids.release();
+    t->dcen = D.release();
+    lab.reset();
+    if (n == 0) {
+        // empty tree: keep valid (non-null) small allocations
+        t->perm = (int32_t *)dmalloc(sizeof(int32_t), s);
+        t->dcen = (float *)dmalloc(sizeof(float), s);
+    }
+    if (l2) {
+        t->pts = (float *)dmalloc((size_t)(n ? n : 1) * dp * sizeof(float) + 16, s);
+        if (n) {
+            k_gather_rows<<<grid_for(n * (dp / 4)), BT, 0, s>>>(Xp.p, dp, t->perm, n, t->pts);
+            CT_COUNT_LAUNCH();
+        }
+        Xp.reset();
+    } else {
+        DBuf<int64_t> lens(n + 1, s);
+        DBuf<int32_t> ml(1, s);
+        CT_CHECK_CUDA(cudaMemsetAsync(ml.p, 0, sizeof(int32_t), s));
+        if (n) {
+            k_string_lengths<<<grid_for(n), BT, 0, s>>>(n, t->perm, pts->offsets, lens.p, ml.p);
+            CT_COUNT_LAUNCH();
+        }
+        t->soff = (int64_t *)dmalloc((size_t)(n + 1) * sizeof(int64_t), s);
+        DBuf<int64_t> tot(1, s);
+        exclusive_scan_i64(lens.p, t->soff, n, tot.p, s);
+        CT_CHECK_CUDA(cudaMemcpyAsync(t->soff + n, tot.p, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+        int64_t total = 0;
+        to_host(&total, tot.p, 1, s);
+        t->sbytes = total;
+        t->sdata = (uint8_t *)dmalloc((size_t)total + 16, s);
+        if (n) {
+            k_gather_strings<<<(unsigned)n, 128, 0, s>>>(n, t->perm, (const uint8_t *)pts->data, pts->offsets,
+                                                         t->soff, t->sdata);
+            CT_COUNT_LAUNCH();
+        }
+    }
+    // shrink vertex arrays to n_nodes
+    auto shrink_i = [&](DBuf<int32_t> &b) {
+        int32_t *p = (int32_t *)dmalloc(sizeof(int32_t) * (size_t)(n_nodes ? n_nodes : 1), s);
+        if (n_nodes) CT_CHECK_CUDA(cudaMemcpyAsync(p, b.p, sizeof(int32_t) * n_nodes, cudaMemcpyDeviceToDevice, s));
+        b.reset();
+        return p;
+    };
+    t->node_begin = shrink_i(nb);
+    t->node_count = shrink_i(ncnt);
+    t->child_begin = shrink_i(cbeg);
+    t->child_count = shrink_i(ccnt);
+    t->level = shrink_i(lvl);
+    t->parent = shrink_i(par);
+    t->radius = (float *)dmalloc(sizeof(float) * (size_t)(n_nodes ? n_nodes : 1), s);
+    if (n_nodes) CT_CHECK_CUDA(cudaMemcpyAsync(t->radius, rad.p, sizeof(float) * n_nodes, cudaMemcpyDeviceToDevice, s));
+    rad.reset();
+    if (l2) {
+        t->node_ctr = (float *)dmalloc(sizeof(float) * (size_t)(n_nodes ? n_nodes : 1) * dp + 16, s);
+        if (n_nodes) {
+            k_node_centres<<<grid_for((int64_t)n_nodes * (dp / 4)), BT, 0, s>>>(n_nodes, t->node_begin, t->pts, dp,
+                                                                               t->node_ctr);
+            CT_COUNT_LAUNCH();
+        }
+    }
+    // leaf blocks in position order
+    {
+        int64_t nn = n_nodes ? n_nodes : 1;
+        DBuf<uint32_t> k1(nn, s), v1(nn, s), k2(nn, s), v2(nn, s);
+        DBuf<int32_t> cnts(2, s);
+        CT_CHECK_CUDA(cudaMemsetAsync(cnts.p, 0, 2 * sizeof(int32_t), s));
+        if (n_nodes) {
+            k_leaf_keys<<<grid_for(n_nodes), BT, 0, s>>>(n_nodes, t->child_count, t->node_begin, t->node_count, k1.p,
+                                                         v1.p, cnts.p, cnts.p + 1);
+            CT_COUNT_LAUNCH();
+        }
+        int32_t hc[2];
+        to_host(hc, cnts.p, 2, s);
+        t->n_leaves = hc[0];
+        t->max_leaf_count = hc[1];
+        radix_sort_pairs(k1.p, v1.p, k2.p, v2.p, hc[0], bits_for(n), s);
+        t->leaf_ids = (int32_t *)dmalloc(sizeof(int32_t) * (size_t)(hc[0] ? hc[0] : 1), s);
+        if (hc[0]) CT_CHECK_CUDA(cudaMemcpyAsync(t->leaf_ids, v1.p, sizeof(int32_t) * hc[0], cudaMemcpyDeviceToDevice, s));
+    }
+    // query groups: greedy runs of consecutive sibling leaf blocks (host side)
+    {
+        const int L = t->n_leaves;
+        std::vector<int32_t> lid(L), nbh(n_nodes), nch(n_nodes), parh(n_nodes);
+        to_host(lid.data(), t->leaf_ids, L, s);
+        to_host(nbh.data(), t->node_begin, n_nodes, s);
+        to_host(nch.data(), t->node_count, n_nodes, s);
+        to_host(parh.data(), t->parent, n_nodes, s);
+        std::vector<int32_t> gb, gc;
+        gb.reserve(L);
+        gc.reserve(L);
+        int cur_par = -2, maxc = 0;
+        for (int i = 0; i < L; ++i) {
+            int v = lid[i], b = nbh[v], c = nch[v], p = parh[v];
+            if (!gc.empty() && p == cur_par && gc.back() + c <= kGroupSize) {
+                gc.back() += c;
+            } else {
+                gb.push_back(b);
+                gc.push_back(c);
+                cur_par = p;
+            }
+            maxc = std::max(maxc, gc.back());
+        }
+        const int G = (int)gb.size();
+        t->n_groups = G;
+        t->max_group_count = maxc;
+        t->group_begin = (int32_t *)dmalloc(sizeof(int32_t) * (size_t)(G ? G : 1), s);
+        t->group_count = (int32_t *)dmalloc(sizeof(int32_t) * (size_t)(G ? G : 1), s);
+        t->group_radius = (float *)dmalloc(sizeof(float) * (size_t)(G ? G : 1), s);
+        if (G) {
+            CT_CHECK_CUDA(cudaMemcpyAsync(t->group_begin, gb.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s));
+            CT_CHECK_CUDA(cudaMemcpyAsync(t->group_count, gc.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s));
+            if (l2) {
+                k_group_radius_l2<<<grid_for((int64_t)G * 32), BT, 0, s>>>(G, t->group_begin, t->group_count, t->pts,
+                                                                          dp, t->group_radius);
+            } else {
+                switch (W) {
+#define CT_GR(WW) case WW: k_group_radius_lev<WW><<<G, 32, 0, s>>>(G, t->group_begin, t->group_count, t->sdata, t->soff, t->group_radius); break;
+                    CT_GR(1) CT_GR(2) CT_GR(4) CT_GR(8) CT_GR(16)
+#undef CT_GR
+                }
+            }
+            CT_COUNT_LAUNCH();
+        }
+        CT_CHECK_CUDA(cudaStreamSynchronize(s));  // host vectors above must outlive the copies
+    }
+    CT_LAUNCH_CHECK();
+    CT_CHECK_CUDA(cudaStreamSynchronize(s));
+    tg.t = nullptr;
+    return t;
+}
+
+void free_tree(ct_tree *t) {
+    if (!t) return;
+    cudaStream_t s = t->stream;
+    void *ptrs[] = {t->pts, t->sdata, t->soff, t->perm, t->dcen, t->node_begin, t->node_count,
+                    t->child_begin, t->child_count, t->radius, t->level, t->node_ctr, t->leaf_ids,
+                    t->parent, t->group_begin, t->group_count, t->group_radius};
+    for (void *p : ptrs)
+        if (p) cudaFreeAsync(p, s);
+    cudaStreamSynchronize(s);
+    delete t;
+}
+
+}  // namespace ct

@@ -1,0 +1,245 @@
+// capi.cu -- the C-ABI of include/ctgraph.h: argument checks, status codes,
+// ownership of trees and CSR outputs.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "query.cuh"
+
+namespace ct {
+ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s);
+void free_tree(ct_tree *t);
+void query_tc(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out);
+void query_predicted(const ct_tree *t, const QParams &qp, const void *predictor, int precision,
+                     cudaStream_t s, QueryOut &out);
+void query_batched(int n_clouds, const ct_tree *const *trees, const QParams *qps, const ct_query_opts *opts,
+                   cudaStream_t s, QueryOut *outs);
+}  // namespace ct
+
+namespace {
+
+struct CsrPriv {
+    cudaStream_t stream;
+    ct_query_stats stats;
+};
+
+template <class F>
+ct_status guarded(F &&f) {
+    try {
+        f();
+        return CT_OK;
+    } catch (const ct::Error &e) {
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        ct::set_error("host allocation failed");
+        return CT_ENOMEM;
+    } catch (...) {
+        ct::set_error("unexpected internal error");
+        return CT_ECUDA;
+    }
+}
+
+void check_device(const ct_tree *t) {
+    int dev = -1;
+    CT_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev != t->device) CT_FAIL(CT_EINVAL, "tree lives on device %d, current device is %d", t->device, dev);
+}
+
+ct_query_opts default_query_opts() {
+    ct_query_opts o;
+    std::memset(&o, 0, sizeof(o));
+    return o;
+}
+
+void validate_query(const ct_tree *tree, double eps, const ct_query_opts &o) {
+    if (!tree) CT_FAIL(CT_EINVAL, "tree is NULL");
+    if (!(eps >= 0.0)) CT_FAIL(CT_EINVAL, "eps must be >= 0 (got %g)", eps);
+    if (o.precision != 0 && o.precision != 1) CT_FAIL(CT_EINVAL, "precision must be 0 or 1");
+    if (o.precision == 1 && tree->metric != CT_L2_F32)
+        CT_FAIL(CT_EINVAL, "the BF16 filter applies to L2 trees only");
+    if (o.use_predictor && !o.predictor) CT_FAIL(CT_EINVAL, "use_predictor set without a predictor");
+    if (o.include_self != 0 && o.include_self != 1) CT_FAIL(CT_EINVAL, "include_self must be 0 or 1");
+}
+
+void fill_csr(ct_csr *out, int64_t n, ct::QueryOut &q, cudaStream_t s) {
+    CsrPriv *p = new CsrPriv();
+    p->stream = s;
+    p->stats = q.stats;
+    out->n_rows = n;
+    out->nnz = q.nnz;
+    out->row_ptr = q.row_ptr;
+    out->col = q.col;
+    out->dist = q.dist;
+    out->priv = p;
+}
+
+void release_query_out(ct::QueryOut &q, cudaStream_t s) {
+    ct::dfree(q.row_ptr, s);
+    ct::dfree(q.col, s);
+    ct::dfree(q.dist, s);
+    q.row_ptr = nullptr;
+    q.col = nullptr;
+    q.dist = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+ct_status ct_build(const ct_points *points, const ct_build_opts *opts, ct_stream stream, ct_tree **out) {
+    if (out) *out = nullptr;
+    return guarded([&] {
+        if (!points || !out) CT_FAIL(CT_EINVAL, "points and out must not be NULL");
+        const ct_points &p = *points;
+        if (p.n < 0) CT_FAIL(CT_EINVAL, "n must be >= 0");
+        if (p.n >= 0x7f7f7f00LL) CT_FAIL(CT_EOVERFLOW, "n = %lld is above the supported limit", (long long)p.n);
+        if (p.metric == CT_L2_F32) {
+            if (p.dim < 1 || p.dim > 4096) CT_FAIL(CT_EINVAL, "dim must be in [1, 4096] (got %d)", p.dim);
+            if (p.n > 0 && !p.data) CT_FAIL(CT_EINVAL, "data is NULL");
+            if ((double)p.n * (double)((p.dim + 3) / 4 * 4) > 4.0e9 * 4)
+                CT_FAIL(CT_EOVERFLOW, "n * dim too large");
+        } else if (p.metric == CT_LEVENSHTEIN_U8) {
+            if (p.n > 0 && (!p.data || !p.offsets)) CT_FAIL(CT_EINVAL, "data and offsets must not be NULL");
+        } else {
+            CT_FAIL(CT_EINVAL, "unknown metric %d", p.metric);
+        }
+        int zeta = opts && opts->leaf_size > 0 ? opts->leaf_size : 32;
+        int root = opts ? opts->root : 0;
+        if (p.n > 0 && (root < 0 || root >= p.n)) CT_FAIL(CT_EINVAL, "root %d out of range", root);
+        ct::g_launches = 0;
+        *out = ct::build_tree(&p, zeta, root, (cudaStream_t)stream);
+    });
+}
+
+ct_status eps_graph_query(const ct_tree *tree, double eps, const ct_query_opts *opts, ct_stream stream,
+                          ct_csr *out) {
+    if (out) std::memset(out, 0, sizeof(*out));
+    cudaStream_t s = (cudaStream_t)stream;
+    ct::QueryOut q;
+    ct_status st = guarded([&] {
+        if (!out) CT_FAIL(CT_EINVAL, "out is NULL");
+        ct_query_opts o = opts ? *opts : default_query_opts();
+        validate_query(tree, eps, o);
+        check_device(tree);
+        ct::g_launches = 0;
+        ct::QParams qp = ct::make_qparams(tree, eps, o.include_self);
+        if (o.use_predictor)
+            ct::query_predicted(tree, qp, o.predictor, o.precision, s, q);
+        else if (o.precision == 1)
+            ct::query_tc(tree, qp, s, q);
+        else
+            ct::query_plain(tree, qp, s, q);
+        q.stats.kernel_launches = ct::g_launches;
+        fill_csr(out, tree->n, q, s);
+    });
+    if (st != CT_OK) {
+        release_query_out(q, s);
+        if (out) std::memset(out, 0, sizeof(*out));
+    }
+    return st;
+}
+
+ct_status eps_graph_query_batched(int32_t n_clouds, const ct_tree *const *trees, const double *eps,
+                                  const ct_query_opts *opts, ct_stream stream, ct_csr *outs) {
+    if (outs && n_clouds > 0) std::memset(outs, 0, sizeof(ct_csr) * (size_t)n_clouds);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<ct::QueryOut> q((size_t)(n_clouds > 0 ? n_clouds : 0));
+    ct_status st = guarded([&] {
+        if (n_clouds < 0) CT_FAIL(CT_EINVAL, "n_clouds must be >= 0");
+        if (n_clouds == 0) return;
+        if (!trees || !eps || !outs) CT_FAIL(CT_EINVAL, "trees, eps and outs must not be NULL");
+        ct_query_opts o = opts ? *opts : default_query_opts();
+        std::vector<ct::QParams> qps((size_t)n_clouds);
+        for (int c = 0; c < n_clouds; ++c) {
+            validate_query(trees[c], eps[c], o);
+            check_device(trees[c]);
+            qps[c] = ct::make_qparams(trees[c], eps[c], o.include_self);
+        }
+        ct::g_launches = 0;
+        ct::query_batched(n_clouds, trees, qps.data(), &o, s, q.data());
+        for (int c = 0; c < n_clouds; ++c) {
+            q[c].stats.kernel_launches = ct::g_launches;
+            fill_csr(&outs[c], trees[c]->n, q[c], s);
+            q[c] = ct::QueryOut();
+        }
+    });
+    if (st != CT_OK) {
+        for (auto &x : q) release_query_out(x, s);
+        if (outs && n_clouds > 0) {
+            for (int c = 0; c < n_clouds; ++c) csr_free(&outs[c]);
+        }
+    }
+    return st;
+}
+
+void csr_free(ct_csr *csr) {
+    if (!csr) return;
+    CsrPriv *p = (CsrPriv *)csr->priv;
+    cudaStream_t s = p ? p->stream : (cudaStream_t)0;
+    if (csr->row_ptr) cudaFreeAsync(csr->row_ptr, s);
+    if (csr->col) cudaFreeAsync(csr->col, s);
+    if (csr->dist) cudaFreeAsync(csr->dist, s);
+    delete p;
+    std::memset(csr, 0, sizeof(*csr));
+}
+
+ct_status ct_csr_stats(const ct_csr *csr, ct_query_stats *out) {
+    return guarded([&] {
+        if (!csr || !out) CT_FAIL(CT_EINVAL, "csr and out must not be NULL");
+        if (!csr->priv) CT_FAIL(CT_EINVAL, "csr holds no query");
+        *out = ((CsrPriv *)csr->priv)->stats;
+    });
+}
+
+void ct_tree_free(ct_tree *tree) { ct::free_tree(tree); }
+
+ct_status ct_tree_shape(const ct_tree *tree, int64_t *n_nodes, int64_t *n_points) {
+    return guarded([&] {
+        if (!tree || !n_nodes || !n_points) CT_FAIL(CT_EINVAL, "NULL argument");
+        *n_nodes = tree->n_nodes;
+        *n_points = tree->n;
+    });
+}
+
+ct_status ct_tree_export(const ct_tree *tree, int64_t *center, double *radius, int32_t *level,
+                         int64_t *child_begin, int64_t *child_count, int64_t *pts_begin, int64_t *pts_count,
+                         int64_t *leaf_pts) {
+    return guarded([&] {
+        if (!tree) CT_FAIL(CT_EINVAL, "tree is NULL");
+        const int N = tree->n_nodes;
+        const int64_t n = tree->n;
+        if (N > 0 && (!center || !radius || !level || !child_begin || !child_count || !pts_begin || !pts_count))
+            CT_FAIL(CT_EINVAL, "NULL output array");
+        if (n > 0 && !leaf_pts) CT_FAIL(CT_EINVAL, "NULL leaf_pts");
+        check_device(tree);
+        CT_CHECK_CUDA(cudaDeviceSynchronize());
+        std::vector<int32_t> nb(N), nc(N), cb(N), cc(N), lv(N), perm(n);
+        std::vector<float> rd(N);
+        auto get = [&](void *h, const void *d, size_t bytes) {
+            if (bytes) CT_CHECK_CUDA(cudaMemcpy(h, d, bytes, cudaMemcpyDeviceToHost));
+        };
+        get(nb.data(), tree->node_begin, N * sizeof(int32_t));
+        get(nc.data(), tree->node_count, N * sizeof(int32_t));
+        get(cb.data(), tree->child_begin, N * sizeof(int32_t));
+        get(cc.data(), tree->child_count, N * sizeof(int32_t));
+        get(lv.data(), tree->level, N * sizeof(int32_t));
+        get(rd.data(), tree->radius, N * sizeof(float));
+        get(perm.data(), tree->perm, n * sizeof(int32_t));
+        for (int v = 0; v < N; ++v) {
+            center[v] = perm[nb[v]];
+            radius[v] = (double)rd[v];
+            level[v] = lv[v];
+            child_begin[v] = cb[v];
+            child_count[v] = cc[v];
+            pts_begin[v] = cc[v] == 0 ? nb[v] : 0;
+            pts_count[v] = cc[v] == 0 ? nc[v] : 0;
+        }
+        for (int64_t i = 0; i < n; ++i) leaf_pts[i] = perm[i];
+    });
+}
+
+const char *ct_last_error(void) { return ct::get_error(); }
+
+const char *ct_version(void) { return "ctgraph 0.1 (sm_103a)"; }
+
+}  // extern "C"

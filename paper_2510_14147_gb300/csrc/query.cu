@@ -1,0 +1,1035 @@
+// query.cu -- the batched ε query (Algorithm 3 with the batching of Sec. IV-B)
+// as a two-pass count -> scan -> emit pipeline, plus the CSR row sort.
+//
+// Query groups are the tree's leaf blocks (<= zeta points, contiguous in tree
+// order, centre c_g, radius r_g).  Stages:
+//   1. traversal (k_traverse_*): one warp per group walks the tree from the
+//      root with a stack of sibling ranges; 32 vertices are tested at a time,
+//      one per lane.  A vertex v survives iff d(c_g, v) <= r(v) + eps + r_g
+//      (every query q of the group has d(q, c_g) <= r_g, so no descendant of a
+//      pruned v is within eps of any q: triangle inequality).  Survivors are
+//      compacted with ballots: leaf blocks are candidates, internal vertices
+//      push their child range.  Run twice: count, then fill a CSR of
+//      candidates per group.
+//   2. leaf tiles (k_leaf_*): one CTA per group evaluates every (query,
+//      candidate point) pair and decides d(q, p) <= eps exactly (see QParams).
+//      Count pass: per-query degree, and a flag on every candidate block that
+//      produced an edge.  Emit pass: flagged blocks only; writes col/dist at
+//      the row offsets.
+//   3. scan of degrees to row_ptr (int64), then a per-row sort by column.
+#include <cfloat>
+#include <climits>
+#include <cmath>
+
+#include "lev.cuh"
+#include "profile.cuh"
+#include "query.cuh"
+
+namespace ct {
+
+namespace {
+
+constexpr int TRAV_WARPS = 4;              // warps per traversal block
+constexpr int LEAF_T = 128;                // threads per leaf-tile block
+constexpr int KC = 128;                    // floats per K chunk of a tile
+constexpr int KS4 = KC / 4 + 1;            // padded row stride in float4
+constexpr uint32_t FLAG = 0x80000000u;     // candidate produced an edge
+constexpr float PRUNE_REL = 1.0f + 0x1p-10f;
+constexpr float PRUNE_ABS = 0x1p-60f;
+
+__device__ __forceinline__ void stat_add(unsigned long long *st, int slot, unsigned long long v) {
+    if (v) atomicAdd(st + slot, v);
+}
+
+// Pinned FP64 sum of squared differences: fp32 inputs widened exactly,
+// t = x - y, s = s + t*t in ascending index order, every op rounded to
+// nearest and never contracted.
+__device__ __noinline__ double sq_l2_exact(const float *__restrict__ x, const float *__restrict__ y,
+                                           int dim) {
+    double s = 0.0;
+    for (int k = 0; k < dim; ++k) {
+        double t = __dsub_rn((double)x[k], (double)y[k]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return s;
+}
+
+// Lane-per-vertex fp32 squared distance from a centre in shared memory.
+__device__ __forceinline__ float lane_sqdist(const float4 *__restrict__ c, const float4 *__restrict__ v,
+                                             int nq) {
+    float a0 = 0.f, a1 = 0.f;
+    int k = 0;
+    for (; k + 1 < nq; k += 2) {
+        float4 x = c[k], y = __ldg(v + k);
+        float4 x2 = c[k + 1], y2 = __ldg(v + k + 1);
+        float dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z, dw = x.w - y.w;
+        a0 = fmaf(dx, dx, a0); a0 = fmaf(dy, dy, a0); a0 = fmaf(dz, dz, a0); a0 = fmaf(dw, dw, a0);
+        dx = x2.x - y2.x; dy = x2.y - y2.y; dz = x2.z - y2.z; dw = x2.w - y2.w;
+        a1 = fmaf(dx, dx, a1); a1 = fmaf(dy, dy, a1); a1 = fmaf(dz, dz, a1); a1 = fmaf(dw, dw, a1);
+    }
+    if (k < nq) {
+        float4 x = c[k], y = __ldg(v + k);
+        float dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z, dw = x.w - y.w;
+        a0 = fmaf(dx, dx, a0); a0 = fmaf(dy, dy, a0); a0 = fmaf(dz, dz, a0); a0 = fmaf(dw, dw, a0);
+    }
+    return a0 + a1;
+}
+
+struct TreeView {
+    const float *pts, *node_ctr, *radius, *dcen, *group_radius;
+    const int32_t *perm, *node_begin, *node_count, *child_begin, *child_count, *leaf_ids;
+    const int32_t *group_begin, *group_count;
+    const uint8_t *sdata;
+    const int64_t *soff;
+    int dp, dim, n_leaves, n_groups;
+};
+
+TreeView view_of(const ct_tree *t) {
+    TreeView v;
+    v.pts = t->pts; v.node_ctr = t->node_ctr; v.radius = t->radius; v.dcen = t->dcen;
+    v.perm = t->perm; v.node_begin = t->node_begin; v.node_count = t->node_count;
+    v.child_begin = t->child_begin; v.child_count = t->child_count; v.leaf_ids = t->leaf_ids;
+    v.sdata = t->sdata; v.soff = t->soff; v.dp = t->dp; v.dim = t->dim; v.n_leaves = t->n_leaves;
+    v.group_begin = t->group_begin; v.group_count = t->group_count; v.group_radius = t->group_radius;
+    v.n_groups = t->n_groups;
+    return v;
+}
+
+// ------------------------------------------------------------ traversal
+
+// Shared DFS machinery: pops up to 32 vertices from the top range; `test`
+// decides a vertex (lane-parallel); survivors are compacted by ballots.
+template <bool FILL, class Test>
+__device__ __forceinline__ int64_t walk_group(const TreeView &tv, int2 *__restrict__ stack, int cap,
+                                              int64_t out_base, int out_cap, uint32_t *__restrict__ cand,
+                                              int &n_cand, unsigned long long &evals,
+                                              int32_t *__restrict__ err, Test test) {
+    const int lane = threadIdx.x & 31;
+    n_cand = 0;
+    if (tv.child_count[0] == 0) {  // the root is a leaf block: it is the only candidate
+        if (FILL && out_cap < 1) {
+            if (lane == 0) atomicOr(err, 16);
+            return -1;
+        }
+        if (FILL && lane == 0) cand[out_base] = 0u;
+        n_cand = 1;
+        return 0;
+    }
+    int top = 0;
+    if (lane == 0) stack[0] = make_int2(tv.child_begin[0], tv.child_count[0]);
+    top = 1;
+    __syncwarp();
+    while (top > 0) {
+        int2 r = stack[top - 1];
+        int take = r.y < 32 ? r.y : 32;
+        __syncwarp();
+        if (lane == 0) {
+            if (r.y > take) stack[top - 1] = make_int2(r.x + take, r.y - take);
+        }
+        if (r.y <= take) --top;
+        if (lane < take) ++evals;
+        bool keep = false, leaf = false;
+        int v = r.x + lane;
+        if (lane < take) {
+            keep = test(v);
+            leaf = tv.child_count[v] == 0;
+        }
+        unsigned ml = __ballot_sync(0xffffffffu, keep && leaf);
+        unsigned mi = __ballot_sync(0xffffffffu, keep && !leaf);
+        if (FILL && n_cand + __popc(ml) > out_cap) {  // the fill walk must repeat the count walk
+            if (lane == 0) atomicOr(err, 16);
+            return -1;
+        }
+        if (FILL && keep && leaf) cand[out_base + n_cand + __popc(ml & lanemask_lt())] = (uint32_t)v;
+        n_cand += __popc(ml);
+        int np = __popc(mi);
+        if (top + np > cap) {  // cannot happen for a stack of 32 * (depth + 2) ranges
+            if (lane == 0) atomicOr(err, 2);
+            return -1;
+        }
+        if (keep && !leaf) {
+            // reverse lane order so the lowest lane's children are on top (DFS order)
+            int slot = top + __popc(mi & ~lanemask_lt() & ~(1u << lane));
+            stack[slot] = make_int2(tv.child_begin[v], tv.child_count[v]);
+        }
+        top += np;
+        __syncwarp();
+    }
+    return 0;
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(TRAV_WARPS * 32) k_traverse_l2(
+    TreeView tv, QParams qp, int32_t *__restrict__ cand_cnt, const int64_t *__restrict__ cand_off,
+    uint32_t *__restrict__ cand, int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st,
+    int32_t *__restrict__ err) {
+    extern __shared__ float4 sc[];  // TRAV_WARPS x (dp/4)
+    const int nq = tv.dp >> 2;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4 *cen = sc + wib * nq;
+    const int gw = blockIdx.x * TRAV_WARPS + wib;
+    const int nw = gridDim.x * TRAV_WARPS;
+    int2 *stack = stacks + (int64_t)gw * cap;
+    unsigned long long evals = 0;
+    for (int g = gw; g < tv.n_groups; g += nw) {
+        const float4 *crow = reinterpret_cast<const float4 *>(tv.pts + (size_t)tv.group_begin[g] * tv.dp);
+        for (int k = lane; k < nq; k += 32) cen[k] = crow[k];
+        __syncwarp();
+        const float add = qp.eps_up + tv.group_radius[g];
+        int n_cand = 0;
+        auto test = [&](int v) {
+            float s = lane_sqdist(cen, reinterpret_cast<const float4 *>(tv.node_ctr + (size_t)v * tv.dp), nq);
+            float d = sqrtf(s);
+            float bound = fmaf(tv.radius[v] + add, PRUNE_REL, PRUNE_ABS);
+            return !(d > bound);
+        };
+        int64_t base = FILL ? cand_off[g] : 0;
+        int ocap = FILL ? cand_cnt[g] : 0;
+        if (walk_group<FILL>(tv, stack, cap, base, ocap, cand, n_cand, evals, err, test) < 0) return;
+        if (!FILL && lane == 0) cand_cnt[g] = n_cand;
+        __syncwarp();
+    }
+    if (!FILL) {
+        for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
+        if (lane == 0) stat_add(st, ST_TRAV, evals);
+    }
+}
+
+// Edit distance: a vertex survives iff lev(c_g, v) <= r(v) + eps + r_g
+// (integers, exact).  One warp per block; the group centre's match masks are
+// in shared memory.
+template <bool FILL, int W>
+__global__ void __launch_bounds__(32) k_traverse_lev(
+    TreeView tv, QParams qp, int32_t *__restrict__ cand_cnt, const int64_t *__restrict__ cand_off,
+    uint32_t *__restrict__ cand, int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st,
+    int32_t *__restrict__ err) {
+    __shared__ uint64_t peq[256 * W];
+    const int lane = threadIdx.x;
+    int2 *stack = stacks + (int64_t)blockIdx.x * cap;
+    unsigned long long evals = 0;
+    for (int g = blockIdx.x; g < tv.n_groups; g += gridDim.x) {
+        int cpos = tv.group_begin[g];
+        const uint8_t *pat = tv.sdata + tv.soff[cpos];
+        int m = (int)(tv.soff[cpos + 1] - tv.soff[cpos]);
+        __syncwarp();
+        lev_build_peq<W>(peq, pat, m);
+        __syncwarp();
+        const int add = qp.lev_k + (int)tv.group_radius[g];
+        int n_cand = 0;
+        auto test = [&](int v) {
+            int vp = tv.node_begin[v];
+            int k = add + (int)tv.radius[v];
+            const uint8_t *txt = tv.sdata + tv.soff[vp];
+            int n = (int)(tv.soff[vp + 1] - tv.soff[vp]);
+            return lev_myers<W>(peq, m, txt, n, k) <= k;
+        };
+        int64_t base = FILL ? cand_off[g] : 0;
+        int ocap = FILL ? cand_cnt[g] : 0;
+        if (walk_group<FILL>(tv, stack, cap, base, ocap, cand, n_cand, evals, err, test) < 0) return;
+        if (!FILL && lane == 0) cand_cnt[g] = n_cand;
+    }
+    if (!FILL) {
+        for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
+        if (lane == 0) stat_add(st, ST_TRAV, evals);
+    }
+}
+
+// ------------------------------------------------------------ leaf tiles
+
+// Packs the next run of candidate points into a tile of up to 32 rows.  The
+// candidates of a group are leaf blocks of a few points each; rows of
+// consecutive candidates are concatenated so that every tile is full.
+// Called by warp 0; (s_ci, s_off) is the cursor: candidate index and the number
+// of its points already consumed.  In the emit pass, candidates without the
+// "produced an edge" flag are skipped.
+__device__ __forceinline__ void fill_tile(const TreeView &tv, const uint32_t *__restrict__ cand, int64_t c1,
+                                          bool flagged_only, int64_t *s_ci, int *s_off, int *s_rows,
+                                          int *tpos, int64_t *tcand) {
+    const int lane = threadIdx.x & 31;
+    const int64_t ci = *s_ci;
+    const int off = *s_off;
+    const int64_t c = ci + lane;
+    int beg = 0, cnt = 0;
+    if (c < c1) {
+        uint32_t e = cand[c];
+        if (!flagged_only || (e & FLAG)) {
+            int v = (int)(e & ~FLAG);
+            beg = tv.node_begin[v];
+            cnt = tv.node_count[v];
+        }
+    }
+    if (lane == 0) {
+        beg += off;
+        cnt -= off;
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int excl = incl - cnt;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int rows = total < 32 ? total : 32;
+    // owner of row r = lane: number of candidates whose inclusive end is <= r
+    int L = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        int probe = __shfl_sync(0xffffffffu, incl, L + step - 1);
+        if (probe <= lane) L += step;
+    }
+    const int bl = __shfl_sync(0xffffffffu, beg, L);
+    const int el = __shfl_sync(0xffffffffu, excl, L);
+    if (lane < rows) {
+        tpos[lane] = bl + (lane - el);
+        tcand[lane] = ci + L;
+    }
+    const int L31 = __shfl_sync(0xffffffffu, L, 31);
+    const int e31 = __shfl_sync(0xffffffffu, excl, L31);
+    const int n31 = __shfl_sync(0xffffffffu, cnt, L31);
+    if (lane == 0) {
+        if (total <= 32) {
+            int64_t nx = ci + 32;
+            *s_ci = nx < c1 ? nx : c1;
+            *s_off = 0;
+        } else {
+            int used = 32 - e31;
+            if (used == n31) {
+                *s_ci = ci + L31 + 1;
+                *s_off = 0;
+            } else {
+                *s_ci = ci + L31;
+                *s_off = (L31 == 0 ? off : 0) + used;
+            }
+        }
+        *s_rows = rows;
+    }
+}
+
+// Loads rows (K chunk kc0 .. kc0 + 4 kq floats) into a padded shared tile;
+// row r comes from position pos[r] (or first + r when pos is null); rows
+// beyond `rows` are zero.
+__device__ __forceinline__ void load_rows(float4 *__restrict__ tile, const float *__restrict__ pts, int dp,
+                                          const int *pos, int first, int rows, int kc0, int kq) {
+    for (int i = threadIdx.x; i < 32 * kq; i += LEAF_T) {
+        int r = i / kq, k = i - r * kq;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < rows) {
+            int p = pos ? pos[r] : first + r;
+            v = __ldg(reinterpret_cast<const float4 *>(pts + (size_t)p * dp + kc0) + k);
+        }
+        tile[r * KS4 + k] = v;
+    }
+}
+
+// Decides one pair; returns 1 for an edge and sets *dist.
+__device__ __forceinline__ int decide_l2(const QParams &qp, float s, const float *__restrict__ x,
+                                         const float *__restrict__ y, int dim, bool fp32_dist_ok,
+                                         float *dist, unsigned &guard) {
+    int edge = 0;
+    bool exact = false;
+    if (qp.mode == 0) {
+        if (s < qp.lo2) edge = 1;
+        else if (s > qp.hi2) edge = 0;
+        else exact = true;
+    } else if (qp.mode == 1) {
+        edge = s == 0.0f;
+    } else if (qp.mode == 3) {
+        edge = 1;
+    } else {
+        exact = true;
+    }
+    if (exact) {
+        ++guard;
+        double s64 = sq_l2_exact(x, y, dim);
+        edge = s64 <= qp.eps2_64;
+        if (edge) *dist = (float)sqrt(s64);
+        return edge;
+    }
+    if (edge) {
+        if (fp32_dist_ok) *dist = sqrtf(s);
+        else *dist = (float)sqrt(sq_l2_exact(x, y, dim));
+    }
+    return edge;
+}
+
+// One CTA per query group.  Q tile: the group's points (32 rows at a time);
+// P tiles: packed candidate points.  Each thread owns a 2 x 4 block of pairs
+// (queries qi, qi+16; points pj, pj+8, pj+16, pj+24) and accumulates the
+// squared differences over the row in chunks of 16 coordinates (chunk sums
+// added into a running total), which bounds the fp32 error of the sum by
+// about 26 units of roundoff for rows of up to 128 floats.
+template <bool EMIT>
+__global__ void __launch_bounds__(LEAF_T) k_leaf_l2(
+    TreeView tv, QParams qp, const int64_t *__restrict__ cand_off, uint32_t *__restrict__ cand,
+    int32_t *__restrict__ deg, const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col,
+    float *__restrict__ dist, unsigned long long *__restrict__ st, int32_t *__restrict__ err) {
+    __shared__ float4 Qs[32 * KS4];
+    __shared__ float4 Ps[32 * KS4];
+    __shared__ int cursor[32];
+    __shared__ int64_t rowb[32], rowe[32];
+    __shared__ int tpos[32];
+    __shared__ int64_t tcand[32];
+    __shared__ int64_t s_ci;
+    __shared__ int s_off, s_rows;
+    __shared__ unsigned s_hit;
+    const int g = blockIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int qi = tid >> 3, pj = tid & 7;
+    const int dp = tv.dp, dim = tv.dim;
+    const int nkc = (dp + KC - 1) / KC;
+    const bool fp32_dist_ok = dp <= 128;
+    const int qb = tv.group_begin[g], qn = tv.group_count[g];
+    const int64_t c0 = cand_off[g], c1 = cand_off[g + 1];
+    unsigned long long pairs = 0;
+    unsigned guard = 0;
+
+    for (int q0 = 0; q0 < qn; q0 += 32) {
+        const int nqr = min(32, qn - q0);
+        __syncthreads();
+        if (tid < 32) {
+            cursor[tid] = 0;
+            if (EMIT && tid < nqr) {
+                int o = tv.perm[qb + q0 + tid];
+                rowb[tid] = row_ptr[o];
+                rowe[tid] = row_ptr[o + 1];
+            }
+        }
+        if (tid == 0) {
+            s_ci = c0;
+            s_off = 0;
+            s_hit = 0u;
+        }
+        int cnt0 = 0, cnt1 = 0;
+        if (nkc == 1) load_rows(Qs, tv.pts, dp, nullptr, qb + q0, nqr, 0, dp >> 2);
+        for (;;) {
+            __syncthreads();
+            if (warp == 0) fill_tile(tv, cand, c1, EMIT, &s_ci, &s_off, &s_rows, tpos, tcand);
+            __syncthreads();
+            const int npr = s_rows;
+            const bool last = s_ci >= c1;
+            if (npr > 0) {
+                float tot[2][4];
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) tot[i][j] = 0.f;
+                for (int kc = 0; kc < nkc; ++kc) {
+                    const int k0 = kc * KC;
+                    const int kq = min(KC, dp - k0) >> 2;
+                    if (kc > 0) __syncthreads();
+                    if (nkc > 1) load_rows(Qs, tv.pts, dp, nullptr, qb + q0, nqr, k0, kq);
+                    load_rows(Ps, tv.pts, dp, tpos, 0, npr, k0, kq);
+                    __syncthreads();
+                    const float4 *qa = Qs + qi * KS4, *qb2 = Qs + (qi + 16) * KS4;
+                    const float4 *pr0 = Ps + pj * KS4, *pr1 = Ps + (pj + 8) * KS4;
+                    const float4 *pr2 = Ps + (pj + 16) * KS4, *pr3 = Ps + (pj + 24) * KS4;
+                    for (int k4 = 0; k4 < kq; k4 += 4) {
+                        float acc[2][4];
+#pragma unroll
+                        for (int i = 0; i < 2; ++i)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+                        const int ke = min(k4 + 4, kq);
+                        for (int k = k4; k < ke; ++k) {
+                            float4 a[2] = {qa[k], qb2[k]};
+                            float4 b[4] = {pr0[k], pr1[k], pr2[k], pr3[k]};
+#pragma unroll
+                            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    float dx = a[i].x - b[j].x, dy = a[i].y - b[j].y;
+                                    float dz = a[i].z - b[j].z, dw = a[i].w - b[j].w;
+                                    acc[i][j] = fmaf(dx, dx, acc[i][j]);
+                                    acc[i][j] = fmaf(dy, dy, acc[i][j]);
+                                    acc[i][j] = fmaf(dz, dz, acc[i][j]);
+                                    acc[i][j] = fmaf(dw, dw, acc[i][j]);
+                                }
+                        }
+#pragma unroll
+                        for (int i = 0; i < 2; ++i)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) tot[i][j] += acc[i][j];
+                    }
+                }
+                unsigned hit = 0u;
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int q = qi + 16 * i;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int p = pj + 8 * j;
+                        if (q >= nqr || p >= npr) continue;
+                        const int qpos = qb + q0 + q, ppos = tpos[p];
+                        if (qpos == ppos && !qp.include_self) continue;
+                        if (!EMIT) ++pairs;
+                        float dv = 0.f;
+                        unsigned gcount = 0;
+                        int e = decide_l2(qp, tot[i][j], tv.pts + (size_t)qpos * dp, tv.pts + (size_t)ppos * dp,
+                                          dim, fp32_dist_ok, &dv, gcount);
+                        if (!EMIT) guard += gcount;
+                        if (!e) continue;
+                        if (!EMIT) {
+                            hit |= 1u << p;
+                            if (i == 0) ++cnt0; else ++cnt1;
+                        } else {
+                            int slot = atomicAdd(&cursor[q], 1);
+                            int64_t at = rowb[q] + slot;
+                            if (at < rowe[q]) {
+                                col[at] = tv.perm[ppos];
+                                dist[at] = dv;
+                            } else {
+                                atomicOr(err, 4);
+                            }
+                        }
+                    }
+                }
+                if (!EMIT) {
+                    if (hit) atomicOr(&s_hit, hit);
+                    __syncthreads();
+                    if (tid < npr && ((s_hit >> tid) & 1u)) atomicOr(&cand[tcand[tid]], FLAG);
+                    __syncthreads();
+                    if (tid == 0) s_hit = 0u;
+                }
+            }
+            if (last) break;
+        }
+        if (!EMIT) {
+            for (int o = 1; o < 8; o <<= 1) {
+                cnt0 += __shfl_xor_sync(0xffffffffu, cnt0, o);
+                cnt1 += __shfl_xor_sync(0xffffffffu, cnt1, o);
+            }
+            if (pj == 0) {
+                if (qi < nqr) deg[tv.perm[qb + q0 + qi]] = cnt0;
+                if (qi + 16 < nqr) deg[tv.perm[qb + q0 + qi + 16]] = cnt1;
+            }
+        } else {
+            __syncthreads();
+            if (tid < nqr && rowb[tid] + cursor[tid] != rowe[tid]) atomicOr(err, 8);
+        }
+    }
+    if (!EMIT) {
+        for (int o = 16; o > 0; o >>= 1) {
+            pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+            guard += __shfl_xor_sync(0xffffffffu, guard, o);
+        }
+        if ((tid & 31) == 0) {
+            stat_add(st, ST_PAIRS, pairs);
+            stat_add(st, ST_GUARD, guard);
+        }
+    }
+}
+
+// Edit distance of one (pattern, text) pair over alphabet-mapped symbols;
+// the distance if <= k, else k + 1.
+template <int W>
+__device__ __forceinline__ int lev_mapped(const uint64_t *__restrict__ pq, const uint8_t *__restrict__ amap, int m,
+                                          const uint8_t *__restrict__ txt, int n, int k) {
+    if (k < 0) return (m == 0 && n == 0) ? 0 : k + 1;
+    if ((m > n ? m - n : n - m) > k) return k + 1;
+    if (m == 0) return n;
+    if (n == 0) return m;
+    const int nw = (m + 63) >> 6, hw = (m - 1) >> 6;
+    const uint64_t hbit = 1ull << ((m - 1) & 63);
+    uint64_t Pv[W], Mv[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        Pv[w] = ~0ull;
+        Mv[w] = 0ull;
+    }
+    int score = m;
+    for (int j = 0; j < n; ++j) {
+        const uint64_t *eqr = pq + (int)amap[txt[j]] * W;
+        uint64_t carry = 0ull, hp_in = 1ull, hn_in = 0ull;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            if (w < nw) {
+                uint64_t Eq = eqr[w], pv = Pv[w], mv = Mv[w];
+                uint64_t Xv = Eq | mv, tt = Eq & pv;
+                uint64_t s1 = tt + pv, c1b = s1 < tt ? 1ull : 0ull;
+                uint64_t s2 = s1 + carry, c2b = s2 < s1 ? 1ull : 0ull;
+                carry = c1b | c2b;
+                uint64_t Xh = (s2 ^ pv) | Eq;
+                uint64_t Ph = mv | ~(Xh | pv), Mh = pv & Xh;
+                if (w == hw) {
+                    if (Ph & hbit) ++score;
+                    else if (Mh & hbit) --score;
+                }
+                uint64_t po = Ph >> 63, mo = Mh >> 63;
+                Ph = (Ph << 1) | hp_in;
+                Mh = (Mh << 1) | hn_in;
+                hp_in = po;
+                hn_in = mo;
+                Pv[w] = Mh | ~(Xv | Ph);
+                Mv[w] = Ph & Xv;
+            }
+        }
+        if (score - (n - 1 - j) > k) return k + 1;
+    }
+    return score;
+}
+
+// Edit distance leaf stage: one CTA per group; packed candidate tiles as in
+// the L2 kernel; each thread decides (query, candidate point) pairs with the
+// query as the bit-parallel pattern.  The queries' match masks cover only the
+// bytes that occur in the data (alphabet map amap, A symbols).
+template <bool EMIT, int W>
+__global__ void __launch_bounds__(LEAF_T) k_leaf_lev(
+    TreeView tv, QParams qp, const uint8_t *__restrict__ amap_g, int A, int qchunk,
+    const int64_t *__restrict__ cand_off, uint32_t *__restrict__ cand, int32_t *__restrict__ deg,
+    const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col, float *__restrict__ dist,
+    unsigned long long *__restrict__ st, int32_t *__restrict__ err) {
+    extern __shared__ uint64_t speq[];  // qchunk x A x W
+    __shared__ uint8_t amap[256];
+    __shared__ int cnt[32], cursor[32], qlen[32];
+    __shared__ int64_t rowb[32], rowe[32];
+    __shared__ int tpos[32];
+    __shared__ int64_t tcand[32];
+    __shared__ int64_t s_ci;
+    __shared__ int s_off, s_rows;
+    __shared__ unsigned s_hit;
+    const int g = blockIdx.x, tid = threadIdx.x, warp = tid >> 5;
+    const int qb = tv.group_begin[g], qn = tv.group_count[g];
+    const int64_t c0 = cand_off[g], c1 = cand_off[g + 1];
+    const int k = qp.lev_k;
+    for (int i = tid; i < 256; i += LEAF_T) amap[i] = amap_g[i];
+    unsigned long long pairs = 0;
+    for (int q0 = 0; q0 < qn; q0 += qchunk) {
+        const int nqr = min(qchunk, qn - q0);
+        __syncthreads();
+        for (int i = tid; i < qchunk * A * W; i += LEAF_T) speq[i] = 0ull;
+        if (tid < 32) {
+            cnt[tid] = 0;
+            cursor[tid] = 0;
+            if (tid < nqr) {
+                int qpos = qb + q0 + tid;
+                qlen[tid] = (int)(tv.soff[qpos + 1] - tv.soff[qpos]);
+                if (EMIT) {
+                    int o = tv.perm[qpos];
+                    rowb[tid] = row_ptr[o];
+                    rowe[tid] = row_ptr[o + 1];
+                }
+            }
+        }
+        if (tid == 0) {
+            s_ci = c0;
+            s_off = 0;
+            s_hit = 0u;
+        }
+        __syncthreads();
+        for (int q = 0; q < nqr; ++q) {
+            int qpos = qb + q0 + q;
+            const uint8_t *sq = tv.sdata + tv.soff[qpos];
+            int m = qlen[q];
+            for (int j = tid; j < m; j += LEAF_T)
+                atomicOr((unsigned long long *)&speq[((size_t)q * A + amap[sq[j]]) * W + (j >> 6)], 1ull << (j & 63));
+        }
+        for (;;) {
+            __syncthreads();
+            if (warp == 0) fill_tile(tv, cand, c1, EMIT, &s_ci, &s_off, &s_rows, tpos, tcand);
+            __syncthreads();
+            const int npr = s_rows;
+            const bool last = s_ci >= c1;
+            if (npr > 0) {
+                unsigned hit = 0u;
+                for (int t = tid; t < nqr * npr; t += LEAF_T) {
+                    int q = t / npr, p = t - q * npr;
+                    int qpos = qb + q0 + q, ppos = tpos[p];
+                    if (qpos == ppos && !qp.include_self) continue;
+                    if (!EMIT) ++pairs;
+                    const uint8_t *txt = tv.sdata + tv.soff[ppos];
+                    int n = (int)(tv.soff[ppos + 1] - tv.soff[ppos]);
+                    int d = lev_mapped<W>(speq + (size_t)q * A * W, amap, qlen[q], txt, n, k);
+                    if (d > k) continue;
+                    if (!EMIT) {
+                        hit |= 1u << p;
+                        atomicAdd(&cnt[q], 1);
+                    } else {
+                        int slot = atomicAdd(&cursor[q], 1);
+                        int64_t at = rowb[q] + slot;
+                        if (at < rowe[q]) {
+                            col[at] = tv.perm[ppos];
+                            dist[at] = (float)d;
+                        } else {
+                            atomicOr(err, 4);
+                        }
+                    }
+                }
+                if (!EMIT) {
+                    if (hit) atomicOr(&s_hit, hit);
+                    __syncthreads();
+                    if (tid < npr && ((s_hit >> tid) & 1u)) atomicOr(&cand[tcand[tid]], FLAG);
+                    __syncthreads();
+                    if (tid == 0) s_hit = 0u;
+                }
+            }
+            if (last) break;
+        }
+        __syncthreads();
+        if (tid < nqr) {
+            if (!EMIT) deg[tv.perm[qb + q0 + tid]] = cnt[tid];
+            else if (rowb[tid] + cursor[tid] != rowe[tid]) atomicOr(err, 8);
+        }
+    }
+    if (!EMIT) {
+        for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        if ((tid & 31) == 0) stat_add(st, ST_PAIRS, pairs);
+    }
+}
+
+__global__ void k_alphabet(const uint8_t *__restrict__ s, int64_t nbytes, int32_t *__restrict__ present) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nbytes) present[s[i]] = 1;
+}
+
+// ------------------------------------------------------------- row sort
+
+constexpr int SORT_MID = 4096;  // rows up to this length are sorted in one CTA
+
+__global__ void k_row_classes(const int64_t *__restrict__ row_ptr, int64_t n, int32_t *__restrict__ lists,
+                              int32_t *__restrict__ counts) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t len = row_ptr[i + 1] - row_ptr[i];
+    int cls = len <= 1 ? -1 : len <= 32 ? 0 : len <= SORT_MID ? 1 : 2;
+    if (cls < 0) return;
+    int slot = atomicAdd(&counts[cls], 1);
+    lists[(int64_t)cls * n + slot] = (int32_t)i;
+}
+
+// Warp per row, <= 32 entries: bitonic network across lanes.
+__global__ void k_sort_small(const int32_t *__restrict__ rows, const int32_t *__restrict__ count,
+                             const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col,
+                             float *__restrict__ dist) {
+    int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= *count) return;
+    int r = rows[w];
+    int64_t b = row_ptr[r];
+    int len = (int)(row_ptr[r + 1] - b);
+    int key = lane < len ? col[b + lane] : INT_MAX;
+    float val = lane < len ? dist[b + lane] : 0.f;
+    for (int k = 2; k <= 32; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            int ok = __shfl_xor_sync(0xffffffffu, key, j);
+            float ov = __shfl_xor_sync(0xffffffffu, val, j);
+            bool up = (lane & k) == 0;
+            bool lower = (lane & j) == 0;
+            bool take_min = lower == up;
+            bool swap = take_min ? (ok < key) : (ok > key);
+            if (swap) { key = ok; val = ov; }
+        }
+    }
+    if (lane < len) {
+        col[b + lane] = key;
+        dist[b + lane] = val;
+    }
+}
+
+// CTA per row, 33..SORT_MID entries: bitonic sort in shared memory.
+__global__ void __launch_bounds__(512) k_sort_mid(const int32_t *__restrict__ rows, const int32_t *__restrict__ count,
+                                                  const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col,
+                                                  float *__restrict__ dist) {
+    __shared__ int sk[SORT_MID];
+    __shared__ float sv[SORT_MID];
+    for (int w = blockIdx.x; w < *count; w += gridDim.x) {
+        int r = rows[w];
+        int64_t b = row_ptr[r];
+        int len = (int)(row_ptr[r + 1] - b);
+        int P = 64;
+        while (P < len) P <<= 1;
+        __syncthreads();
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            sk[i] = i < len ? col[b + i] : INT_MAX;
+            sv[i] = i < len ? dist[b + i] : 0.f;
+        }
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                    int ix = i ^ j;
+                    if (ix > i) {
+                        bool up = (i & k) == 0;
+                        int a = sk[i], c = sk[ix];
+                        if ((a > c) == up) {
+                            sk[i] = c; sk[ix] = a;
+                            float t = sv[i]; sv[i] = sv[ix]; sv[ix] = t;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < len; i += blockDim.x) {
+            col[b + i] = sk[i];
+            dist[b + i] = sv[i];
+        }
+    }
+}
+
+// Long rows: gather (row rank, col) keys and sort them globally.
+__global__ void k_big_gather(const int32_t *__restrict__ rows, int nbig, const int64_t *__restrict__ row_ptr,
+                             const int64_t *__restrict__ big_off, const int32_t *__restrict__ col,
+                             uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    int w = blockIdx.x;
+    if (w >= nbig) return;
+    int r = rows[w];
+    int64_t b = row_ptr[r], len = row_ptr[r + 1] - b, o = big_off[w];
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+        keys[o + i] = ((uint64_t)w << 32) | (uint32_t)col[b + i];
+        vals[o + i] = (uint32_t)i;
+    }
+}
+__global__ void k_big_apply(const int32_t *__restrict__ rows, int nbig, const int64_t *__restrict__ row_ptr,
+                            const int64_t *__restrict__ big_off, const uint64_t *__restrict__ keys,
+                            const uint32_t *__restrict__ vals, int32_t *__restrict__ col, float *__restrict__ dist,
+                            float *__restrict__ tmpd) {
+    int w = blockIdx.x;
+    if (w >= nbig) return;
+    int r = rows[w];
+    int64_t b = row_ptr[r], len = row_ptr[r + 1] - b, o = big_off[w];
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) tmpd[o + i] = dist[b + vals[o + i]];
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+        col[b + i] = (int32_t)(uint32_t)(keys[o + i] & 0xffffffffull);
+        dist[b + i] = tmpd[o + i];
+    }
+}
+__global__ void k_big_lengths(const int32_t *__restrict__ rows, int nbig, const int64_t *__restrict__ row_ptr,
+                              int64_t *__restrict__ lens) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < nbig) lens[w] = row_ptr[rows[w] + 1] - row_ptr[rows[w]];
+}
+
+inline unsigned grid_for(int64_t n, int t) { return (unsigned)ceil_div(n > 0 ? n : 1, t); }
+
+}  // namespace
+
+void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int64_t nnz, cudaStream_t s) {
+    if (n <= 0 || nnz <= 0) return;
+    DBuf<int32_t> lists(3 * n, s), counts(3, s);
+    CT_CHECK_CUDA(cudaMemsetAsync(counts.p, 0, 3 * sizeof(int32_t), s));
+    k_row_classes<<<grid_for(n, 256), 256, 0, s>>>(row_ptr, n, lists.p, counts.p);
+    CT_COUNT_LAUNCH();
+    int32_t hc[3];
+    to_host(hc, counts.p, 3, s);
+    if (hc[0]) {
+        k_sort_small<<<grid_for((int64_t)hc[0] * 32, 256), 256, 0, s>>>(lists.p, counts.p, row_ptr, col, dist);
+        CT_COUNT_LAUNCH();
+    }
+    if (hc[1]) {
+        int blocks = (int)std::min<int64_t>(hc[1], (int64_t)num_sms() * 8);
+        k_sort_mid<<<blocks, 512, 0, s>>>(lists.p + n, counts.p + 1, row_ptr, col, dist);
+        CT_COUNT_LAUNCH();
+    }
+    if (hc[2]) {
+        int nb = hc[2];
+        const int32_t *big = lists.p + 2 * n;
+        DBuf<int64_t> lens(nb, s), off(nb, s), tot(1, s);
+        k_big_lengths<<<grid_for(nb, 256), 256, 0, s>>>(big, nb, row_ptr, lens.p);
+        CT_COUNT_LAUNCH();
+        exclusive_scan_i64(lens.p, off.p, nb, tot.p, s);
+        int64_t total = 0;
+        to_host(&total, tot.p, 1, s);
+        DBuf<uint64_t> k1(total, s), k2(total, s);
+        DBuf<uint32_t> v1(total, s), v2(total, s);
+        DBuf<float> td(total, s);
+        k_big_gather<<<nb, 256, 0, s>>>(big, nb, row_ptr, off.p, col, k1.p, v1.p);
+        CT_COUNT_LAUNCH();
+        int bits = 32;
+        while ((int64_t(1) << (bits - 32)) < nb) ++bits;
+        radix_sort_pairs64(k1.p, v1.p, k2.p, v2.p, total, bits, s);
+        k_big_apply<<<nb, 256, 0, s>>>(big, nb, row_ptr, off.p, k1.p, v1.p, col, dist, td.p);
+        CT_COUNT_LAUNCH();
+    }
+    CT_LAUNCH_CHECK();
+}
+
+QParams make_qparams(const ct_tree *t, double eps, int include_self) {
+    QParams q;
+    q.eps64 = eps;
+    q.eps2_64 = eps * eps;
+    q.include_self = include_self;
+    float ef = (float)eps;
+    if ((double)ef < eps) ef = nextafterf(ef, INFINITY);
+    q.eps_up = ef;
+    if (t->metric == CT_LEVENSHTEIN_U8) {
+        double fl = floor(eps);
+        q.lev_k = fl > 1e9 ? 1000000000 : (int)fl;
+        return q;
+    }
+    const double e2 = q.eps2_64;
+    if (eps == 0.0) {
+        q.mode = 1;
+    } else if (e2 >= 0x1p115) {
+        q.mode = 3;
+    } else if (e2 < 0x1p-100 || e2 > 0x1p100) {
+        q.mode = 2;
+    } else {
+        q.mode = 0;
+        double lo = eps * (1.0 - 1e-3), hi = eps * (1.0 + 1e-3);
+        double lo2 = lo * lo, hi2 = hi * hi;
+        float l = (float)lo2, h = (float)hi2;
+        if ((double)l > lo2) l = nextafterf(l, 0.0f);
+        if ((double)h < hi2) h = nextafterf(h, INFINITY);
+        q.lo2 = l;
+        q.hi2 = h;
+    }
+    return q;
+}
+
+void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out) {
+    const int64_t n = t->n;
+    const int G = t->n_groups;
+    const bool l2 = t->metric == CT_L2_F32;
+    TreeView tv = view_of(t);
+    DBuf<unsigned long long> st(ST_N, s);
+    CT_CHECK_CUDA(cudaMemsetAsync(st.p, 0, ST_N * sizeof(unsigned long long), s));
+    int32_t *err = reinterpret_cast<int32_t *>(st.p + ST_ERR);
+
+    // 1. traversal: count, scan, fill
+    const int cap = 32 * (t->depth + 2);
+    int blocks, warps_total;
+    int W = l2 ? 1 : lev_words_for(t->max_len);
+    if (l2) {
+        blocks = (int)std::min<int64_t>(ceil_div(G, TRAV_WARPS), (int64_t)num_sms() * 8);
+        warps_total = blocks * TRAV_WARPS;
+    } else {
+        blocks = (int)std::min<int64_t>(G, (int64_t)num_sms() * 16);
+        warps_total = blocks;
+    }
+    blocks = std::max(blocks, 1);
+    warps_total = std::max(warps_total, 1);
+    DBuf<int2> stacks((size_t)warps_total * cap, s);
+    DBuf<int32_t> ccnt(G + 1, s);
+    DBuf<int64_t> coff(G + 1, s);
+    size_t tsm = l2 ? (size_t)TRAV_WARPS * t->dp * sizeof(float) : 0;
+    if (tsm > 48 * 1024) {
+        CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+        CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    }
+    auto traverse = [&](bool fill, uint32_t *cand) {
+        if (l2) {
+            if (fill)
+                k_traverse_l2<true><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err);
+            else
+                k_traverse_l2<false><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err);
+        } else {
+            switch (W) {
+#define CT_TL(WW)                                                                                           \
+    case WW:                                                                                                \
+        if (fill) k_traverse_lev<true, WW><<<blocks, 32, 0, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err); \
+        else k_traverse_lev<false, WW><<<blocks, 32, 0, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err);    \
+        break;
+                CT_TL(1) CT_TL(2) CT_TL(4) CT_TL(8) CT_TL(16)
+#undef CT_TL
+            }
+        }
+        CT_COUNT_LAUNCH();
+        CT_LAUNCH_CHECK();
+    };
+    {
+        ProfScope ps("traverse_count", s);
+        traverse(false, nullptr);
+    }
+    exclusive_scan_i32_to_i64(ccnt.p, coff.p, G, coff.p + G, s);
+    int64_t n_cand = 0;
+    to_host(&n_cand, coff.p + G, 1, s);
+    DBuf<uint32_t> cand(n_cand ? n_cand : 1, s);
+    {
+        ProfScope ps("traverse_fill", s);
+        traverse(true, cand.p);
+    }
+
+    // alphabet of the strings (edit distance)
+    DBuf<uint8_t> amap;
+    int A = 0, qchunk = 32;
+    if (!l2) {
+        DBuf<int32_t> present(256, s);
+        CT_CHECK_CUDA(cudaMemsetAsync(present.p, 0, 256 * sizeof(int32_t), s));
+        if (t->sbytes) {
+            k_alphabet<<<grid_for(t->sbytes, 256), 256, 0, s>>>(t->sdata, t->sbytes, present.p);
+            CT_COUNT_LAUNCH();
+        }
+        int32_t hp[256];
+        to_host(hp, present.p, 256, s);
+        uint8_t hm[256];
+        for (int c = 0; c < 256; ++c) hm[c] = 0;
+        int a = 1;  // slot 0: bytes absent from the data (never matched)
+        for (int c = 0; c < 256; ++c)
+            if (hp[c]) hm[c] = (uint8_t)std::min(a++, 255);
+        A = std::min(a, 256);
+        if (a > 256) {  // every byte value occurs: identity map
+            for (int c = 0; c < 256; ++c) hm[c] = (uint8_t)c;
+            A = 256;
+        }
+        amap = DBuf<uint8_t>(256, s);
+        CT_CHECK_CUDA(cudaMemcpyAsync(amap.p, hm, 256, cudaMemcpyHostToDevice, s));
+        CT_CHECK_CUDA(cudaStreamSynchronize(s));
+        size_t per_q = (size_t)A * W * sizeof(uint64_t);
+        qchunk = (int)std::max<size_t>(1, std::min<size_t>(32, (96 * 1024) / per_q));
+    }
+    size_t lsm = l2 ? 0 : (size_t)qchunk * A * W * sizeof(uint64_t);
+
+    // 2. count pass
+    DBuf<int32_t> deg(n + 1, s);
+    CT_CHECK_CUDA(cudaMemsetAsync(deg.p, 0, (n + 1) * sizeof(int32_t), s));
+    auto leaf = [&](bool emit, int64_t *row_ptr, int32_t *col, float *dist) {
+        if (G == 0) return;
+        if (l2) {
+            if (emit)
+                k_leaf_l2<true><<<G, LEAF_T, 0, s>>>(tv, qp, coff.p, cand.p, deg.p, row_ptr, col, dist, st.p, err);
+            else
+                k_leaf_l2<false><<<G, LEAF_T, 0, s>>>(tv, qp, coff.p, cand.p, deg.p, row_ptr, col, dist, st.p, err);
+        } else {
+            switch (W) {
+#define CT_LL(WW)                                                                                                      \
+    case WW:                                                                                                           \
+        if (lsm > 48 * 1024) {                                                                                         \
+            CT_CHECK_CUDA(cudaFuncSetAttribute(k_leaf_lev<true, WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm)); \
+            CT_CHECK_CUDA(cudaFuncSetAttribute(k_leaf_lev<false, WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm)); \
+        }                                                                                                              \
+        if (emit) k_leaf_lev<true, WW><<<G, LEAF_T, lsm, s>>>(tv, qp, amap.p, A, qchunk, coff.p, cand.p, deg.p, row_ptr, col, dist, st.p, err); \
+        else k_leaf_lev<false, WW><<<G, LEAF_T, lsm, s>>>(tv, qp, amap.p, A, qchunk, coff.p, cand.p, deg.p, row_ptr, col, dist, st.p, err);    \
+        break;
+                CT_LL(1) CT_LL(2) CT_LL(4) CT_LL(8) CT_LL(16)
+#undef CT_LL
+            }
+        }
+        CT_COUNT_LAUNCH();
+        CT_LAUNCH_CHECK();
+    };
+    {
+        ProfScope ps("leaf_count", s);
+        leaf(false, nullptr, nullptr, nullptr);
+    }
+
+    // 3. scan -> row_ptr, then emit
+    int64_t *row_ptr = (int64_t *)dmalloc((size_t)(n + 1) * sizeof(int64_t), s);
+    out.row_ptr = row_ptr;
+    exclusive_scan_i32_to_i64(deg.p, row_ptr, n + 1, nullptr, s);
+    int64_t nnz = 0;
+    to_host(&nnz, row_ptr + n, 1, s);
+    out.nnz = nnz;
+    out.col = (int32_t *)dmalloc((size_t)(nnz ? nnz : 1) * sizeof(int32_t), s);
+    out.dist = (float *)dmalloc((size_t)(nnz ? nnz : 1) * sizeof(float), s);
+    if (nnz) {
+        ProfScope ps("leaf_emit", s);
+        leaf(true, row_ptr, out.col, out.dist);
+    }
+    {
+        ProfScope ps("row_sort", s);
+        sort_rows(row_ptr, n, out.col, out.dist, nnz, s);
+    }
+
+    unsigned long long hs[ST_N];
+    to_host(hs, st.p, ST_N, s);
+    prof_flush();
+    if (hs[ST_ERR]) CT_FAIL(CT_ECUDA, "internal consistency check failed in the query (code %llu)", hs[ST_ERR]);
+    out.stats.traversal_evals = (int64_t)hs[ST_TRAV];
+    out.stats.leaf_pairs = (int64_t)hs[ST_PAIRS];
+    out.stats.guard_fp64 = (int64_t)hs[ST_GUARD];
+    out.stats.recheck_fp32 = (int64_t)hs[ST_RECHECK];
+    out.stats.candidates = n_cand;
+}
+
+}  // namespace ct

@@ -1,0 +1,44 @@
+// query.cuh -- shared declarations of the query stages.
+#pragma once
+
+#include "common.cuh"
+
+namespace ct {
+
+// Decision parameters of the L2 predicate d(q, p) <= eps.
+//  mode 0: fp32 decides outside the guard band |d - eps| <= 1e-3 eps, FP64
+//          (the pinned sequential sum) inside it;
+//  mode 1: eps == 0: an edge iff the fp32 sum is exactly 0 (iff x == y);
+//  mode 2: every pair in FP64 (eps^2 outside [2^-100, 2^100]);
+//  mode 3: every pair is an edge (eps^2 above any representable sum).
+struct QParams {
+    double eps64 = 0, eps2_64 = 0;
+    float eps_up = 0;      // eps rounded up to fp32 (traversal bound)
+    float lo2 = 0, hi2 = 0;  // guard band in squared distance, rounded outwards
+    int mode = 0;
+    int include_self = 0;
+    int lev_k = 0;         // edit distance: floor(eps)
+};
+
+QParams make_qparams(const ct_tree *t, double eps, int include_self);
+
+// Per-query output and counters of one query.
+struct QueryOut {
+    int64_t nnz = 0;
+    int64_t *row_ptr = nullptr;
+    int32_t *col = nullptr;
+    float *dist = nullptr;
+    ct_query_stats stats{};
+};
+
+// The plain FP32 path (precision 0) and the edit-distance path.
+void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out);
+
+// Sorts every CSR row by column, moving dist along.
+void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int64_t nnz,
+               cudaStream_t s);
+
+// Stats slots accumulated on the device.
+enum { ST_TRAV = 0, ST_PAIRS, ST_GUARD, ST_RECHECK, ST_CAND, ST_OVERFLOW, ST_ERR, ST_N };
+
+}  // namespace ct

@@ -1,0 +1,340 @@
+"""Python binding of the C-ABI in ``include/ctgraph.h`` (ctypes; argument
+marshalling only -- every step of the computation runs in the CUDA library).
+
+PyTorch supplies device memory and streams.  Functions keep the C names:
+
+    tree = ct_build(points)                      # torch.cuda fp32 (n, dim)
+    tree = ct_build(strings=(data, offsets))     # torch.cuda uint8 / int64
+    csr = eps_graph_query(tree, eps)             # CSR with torch views
+    csrs = eps_graph_query_batched(trees, eps)
+    csr_free(csr); ct_tree_free(tree)
+
+There is no CPU fallback: if the library is not built, or no GPU is present,
+these calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _buildmod
+
+CT_OK, CT_EINVAL, CT_ENOMEM, CT_ECUDA, CT_ETIMEOUT, CT_EOVERFLOW, CT_EUNSUPPORTED = range(7)
+STATUS_NAMES = {0: "CT_OK", 1: "CT_EINVAL", 2: "CT_ENOMEM", 3: "CT_ECUDA", 4: "CT_ETIMEOUT",
+                5: "CT_EOVERFLOW", 6: "CT_EUNSUPPORTED"}
+CT_L2_F32, CT_LEVENSHTEIN_U8 = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class CtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class ct_points(C.Structure):
+    _fields_ = [("metric", C.c_int32), ("dim", C.c_int32), ("n", C.c_int64),
+                ("data", C.c_void_p), ("offsets", C.c_void_p)]
+
+
+class ct_build_opts(C.Structure):
+    _fields_ = [("leaf_size", C.c_int32), ("root", C.c_int32)]
+
+
+class ct_query_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("use_predictor", C.c_int32),
+                ("include_self", C.c_int32), ("reserved", C.c_int32), ("predictor", C.c_void_p)]
+
+
+class ct_csr(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col", C.c_void_p), ("dist", C.c_void_p), ("priv", C.c_void_p)]
+
+
+class ct_query_stats(C.Structure):
+    _fields_ = [(f, C.c_int64) for f in ("traversal_evals", "leaf_pairs", "guard_fp64",
+                                           "recheck_fp32", "candidates", "overflow_rows",
+                                           "kernel_launches", "reserved")]
+
+
+def library_path() -> str:
+    return _buildmod.LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _buildmod.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("CUDA library %s is not built; call paper_2510_14147_gb300.build.build()" % path)
+        lib = C.CDLL(path)
+        P = C.POINTER
+        lib.ct_build.restype = C.c_int
+        lib.ct_build.argtypes = [P(ct_points), P(ct_build_opts), C.c_void_p, P(C.c_void_p)]
+        lib.eps_graph_query.restype = C.c_int
+        lib.eps_graph_query.argtypes = [C.c_void_p, C.c_double, P(ct_query_opts), C.c_void_p, P(ct_csr)]
+        lib.eps_graph_query_batched.restype = C.c_int
+        lib.eps_graph_query_batched.argtypes = [C.c_int32, P(C.c_void_p), P(C.c_double), P(ct_query_opts),
+                                                C.c_void_p, P(ct_csr)]
+        lib.csr_free.restype = None
+        lib.csr_free.argtypes = [P(ct_csr)]
+        lib.ct_csr_stats.restype = C.c_int
+        lib.ct_csr_stats.argtypes = [P(ct_csr), P(ct_query_stats)]
+        lib.ct_tree_free.restype = None
+        lib.ct_tree_free.argtypes = [C.c_void_p]
+        lib.ct_tree_shape.restype = C.c_int
+        lib.ct_tree_shape.argtypes = [C.c_void_p, P(C.c_int64), P(C.c_int64)]
+        lib.ct_tree_export.restype = C.c_int
+        lib.ct_tree_export.argtypes = [C.c_void_p] + [C.c_void_p] * 8
+        lib.ct_last_error.restype = C.c_char_p
+        lib.ct_last_error.argtypes = []
+        lib.ct_version.restype = C.c_char_p
+        lib.ct_version.argtypes = []
+        lib.ct_profile_enable.restype = None
+        lib.ct_profile_enable.argtypes = [C.c_int32]
+        lib.ct_profile_reset.restype = None
+        lib.ct_profile_reset.argtypes = []
+        lib.ct_profile_count.restype = C.c_int32
+        lib.ct_profile_count.argtypes = []
+        lib.ct_profile_entry.restype = C.c_int
+        lib.ct_profile_entry.argtypes = [C.c_int32, P(C.c_char_p), P(C.c_double), P(C.c_int64)]
+        lib.ct_kernel_launches.restype = C.c_int64
+        lib.ct_kernel_launches.argtypes = []
+        _lib = lib
+        return lib
+
+
+def ct_last_error() -> str:
+    return _load().ct_last_error().decode(errors="replace")
+
+
+def _check(status: int):
+    if status != CT_OK:
+        raise CtError(status, ct_last_error())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class _CudaArray:
+    """__cuda_array_interface__ view of library-owned memory; holds `owner`."""
+
+    def __init__(self, ptr: int, shape, typestr: str, owner):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr or 0), False), "version": 3,
+                                         "strides": None}
+        self._owner = owner
+
+
+def _view(ptr, count, typestr, owner, torch_dtype):
+    import torch
+    if count == 0 or not ptr:
+        return torch.empty(0, dtype=torch_dtype, device="cuda")
+    return torch.as_tensor(_CudaArray(ptr, (count,), typestr, owner), device="cuda")
+
+
+class Tree:
+    """Owning handle of a device-resident cover tree."""
+
+    def __init__(self, handle: int, n: int, metric: int):
+        self.handle = C.c_void_p(handle)
+        self.n = n
+        self.metric = metric
+
+    def free(self):
+        if self.handle and self.handle.value:
+            _load().ct_tree_free(self.handle)
+            self.handle = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class _CsrOwner:
+    """Holds one library CSR; releases it when the last reference goes."""
+
+    def __init__(self, c: ct_csr):
+        self.c = c
+
+    def free(self):
+        if self.c.priv:
+            _load().csr_free(C.byref(self.c))
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class CSR:
+    """A library-allocated CSR.  ``row_ptr``/``col``/``dist`` are zero-copy
+    torch views; each keeps the memory alive until it is dropped, unless
+    :meth:`free` releases it first (views taken earlier become invalid)."""
+
+    def __init__(self, c: ct_csr):
+        self._owner = _CsrOwner(c)
+        self.n_rows = int(c.n_rows)
+        self.nnz = int(c.nnz)
+
+    @property
+    def c(self) -> ct_csr:
+        return self._owner.c
+
+    @property
+    def row_ptr(self):
+        import torch
+        return _view(self.c.row_ptr, self.n_rows + 1, "<i8", self._owner, torch.int64)
+
+    @property
+    def col(self):
+        import torch
+        return _view(self.c.col, self.nnz, "<i4", self._owner, torch.int32)
+
+    @property
+    def dist(self):
+        import torch
+        return _view(self.c.dist, self.nnz, "<f4", self._owner, torch.float32)
+
+    def stats(self) -> dict:
+        st = ct_query_stats()
+        _check(_load().ct_csr_stats(C.byref(self.c), C.byref(st)))
+        return {f: int(getattr(st, f)) for f, _ in ct_query_stats._fields_ if f != "reserved"}
+
+    def to_numpy(self) -> dict:
+        return {"row_ptr": self.row_ptr.cpu().numpy(), "col": self.col.cpu().numpy(),
+                "dist": self.dist.cpu().numpy()}
+
+    def free(self):
+        self._owner.free()
+
+
+def ct_build(points=None, strings=None, leaf_size: int = 32, root: int = 0, stream=None) -> Tree:
+    """Cover-tree construction (Algorithms 1-2).  ``points``: CUDA fp32 tensor
+    (n, dim); or ``strings=(data, offsets)``: CUDA uint8 and int64 tensors."""
+    import torch
+    lib = _load()
+    if (points is None) == (strings is None):
+        raise ValueError("give exactly one of points= or strings=")
+    p = ct_points()
+    if points is not None:
+        if not (points.is_cuda and points.dtype == torch.float32 and points.dim() == 2):
+            raise ValueError("points must be a CUDA float32 tensor of shape (n, dim)")
+        points = points.contiguous()
+        p.metric, p.dim, p.n = CT_L2_F32, points.shape[1], points.shape[0]
+        p.data, p.offsets = points.data_ptr() or None, None
+        keep = (points,)
+    else:
+        data, off = strings
+        if not (data.is_cuda and off.is_cuda and data.dtype == torch.uint8 and off.dtype == torch.int64):
+            raise ValueError("strings must be (CUDA uint8 data, CUDA int64 offsets)")
+        data, off = data.contiguous(), off.contiguous()
+        p.metric, p.dim, p.n = CT_LEVENSHTEIN_U8, 0, off.numel() - 1
+        p.data, p.offsets = data.data_ptr() or None, off.data_ptr() or None
+        keep = (data, off)
+    o = ct_build_opts(leaf_size, root)
+    h = C.c_void_p()
+    st = lib.ct_build(C.byref(p), C.byref(o), C.c_void_p(_stream(stream)), C.byref(h))
+    del keep
+    _check(st)
+    return Tree(h.value, int(p.n), int(p.metric))
+
+
+def _opts(precision, use_predictor, include_self, predictor):
+    o = ct_query_opts()
+    o.precision = int(precision)
+    o.use_predictor = int(bool(use_predictor))
+    o.include_self = int(bool(include_self))
+    o.predictor = predictor.handle.value if predictor is not None else None
+    return o
+
+
+def eps_graph_query(tree: Tree, eps: float, precision: int = 0, use_predictor: bool = False,
+                    include_self: bool = False, predictor=None, stream=None) -> CSR:
+    """The exact ε-graph of the tree's points as a CSR (rows ascending)."""
+    lib = _load()
+    out = ct_csr()
+    o = _opts(precision, use_predictor, include_self, predictor)
+    _check(lib.eps_graph_query(tree.handle, float(eps), C.byref(o), C.c_void_p(_stream(stream)),
+                               C.byref(out)))
+    return CSR(out)
+
+
+def eps_graph_query_batched(trees, eps, precision: int = 0, use_predictor: bool = False,
+                            include_self: bool = False, predictor=None, stream=None):
+    lib = _load()
+    k = len(trees)
+    arr = (C.c_void_p * max(k, 1))(*[t.handle.value for t in trees])
+    ea = (C.c_double * max(k, 1))(*[float(e) for e in eps])
+    outs = (ct_csr * max(k, 1))()
+    o = _opts(precision, use_predictor, include_self, predictor)
+    _check(lib.eps_graph_query_batched(k, arr, ea, C.byref(o), C.c_void_p(_stream(stream)), outs))
+    return [CSR(outs[i]) for i in range(k)]
+
+
+def csr_free(csr: CSR):
+    csr.free()
+
+
+def ct_tree_free(tree: Tree):
+    tree.free()
+
+
+def ct_tree_export(tree: Tree) -> dict:
+    """Host copy of the tree in the flat format (numpy arrays)."""
+    lib = _load()
+    nn, npnt = C.c_int64(), C.c_int64()
+    _check(lib.ct_tree_shape(tree.handle, C.byref(nn), C.byref(npnt)))
+    N, n = nn.value, npnt.value
+    a = {"center": np.zeros(max(N, 1), np.int64), "radius": np.zeros(max(N, 1), np.float64),
+         "level": np.zeros(max(N, 1), np.int32), "child_begin": np.zeros(max(N, 1), np.int64),
+         "child_count": np.zeros(max(N, 1), np.int64), "pts_begin": np.zeros(max(N, 1), np.int64),
+         "pts_count": np.zeros(max(N, 1), np.int64), "leaf_pts": np.zeros(max(n, 1), np.int64)}
+    order = ("center", "radius", "level", "child_begin", "child_count", "pts_begin", "pts_count", "leaf_pts")
+    _check(lib.ct_tree_export(tree.handle, *[a[k].ctypes.data for k in order]))
+    for k in order:
+        a[k] = a[k][:n] if k == "leaf_pts" else a[k][:N]
+    return a
+
+
+def ct_profile_enable(on: bool = True):
+    _load().ct_profile_enable(int(bool(on)))
+
+
+def ct_profile_reset():
+    _load().ct_profile_reset()
+
+
+def ct_profile_read() -> dict:
+    """{stage: (total_ms, calls)} accumulated since the last reset."""
+    lib = _load()
+    out = {}
+    for i in range(lib.ct_profile_count()):
+        name, ms, calls = C.c_char_p(), C.c_double(), C.c_int64()
+        _check(lib.ct_profile_entry(i, C.byref(name), C.byref(ms), C.byref(calls)))
+        out[name.value.decode()] = (ms.value, calls.value)
+    return out
+
+
+def ct_kernel_launches() -> int:
+    return int(_load().ct_kernel_launches())
+
+
+def version() -> str:
+    return _load().ct_version().decode()

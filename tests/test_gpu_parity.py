@@ -1,0 +1,206 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle: exact
+row_ptr/col, dist within 1e-6 relative of FP64, GPU-built trees checked by
+the oracle's invariant checker."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_14147_gb300 import inputs as I
+from helpers import assert_csr_matches, gpu_graph, tree_from_export
+
+pytestmark = pytest.mark.gpu
+
+TREE_TOL = 1e-4   # fp32-built trees: relative tolerance of the net properties
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_14147_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _check_tree(space, out):
+    code, msg = oracle.check_tree(space, tree_from_export(out["tree"]), TREE_TOL)
+    assert code == 0, msg
+
+
+def test_small_3d_workload_exact():
+    """n=2000 uniform [0,1]^3, eps=0.08, zeta=32 (the small configuration)."""
+    x = I.uniform_cube(2000, 3, seed=0)
+    sp = oracle.Space(points=x)
+    ref = oracle.brute_force(sp, 0.08)
+    out = gpu_graph(points=x, eps=0.08, export=True)
+    assert_csr_matches(out, ref)
+    _check_tree(sp, out)
+    assert out["stats"]["leaf_pairs"] > 0 and out["stats"]["traversal_evals"] > 0
+
+
+@pytest.mark.parametrize("dim,n,zeta,seed", [
+    (1, 1500, 8, 0), (2, 2500, 16, 1), (3, 3000, 32, 2), (5, 2000, 32, 3), (8, 2600, 32, 4),
+    (16, 2200, 17, 5), (33, 1800, 32, 6), (64, 2100, 32, 7), (128, 2300, 32, 8),
+    (130, 1200, 32, 9), (300, 900, 24, 10), (7, 2000, 1, 11), (12, 1000, 100, 12)])
+def test_parity_dims_and_leaf_sizes(dim, n, zeta, seed):
+    """Several tiles per group and candidate, ragged tails (n, dim, zeta not
+    multiples of the tile sizes), K-chunked rows above 128 floats."""
+    x = I.gmm_embedded(n, dim=dim, intrinsic=min(dim, 6), n_centres=5, seed=seed) if dim > 3 \
+        else I.uniform_cube(n, dim, seed=seed)
+    sp = oracle.Space(points=x)
+    rng = np.random.default_rng(seed)
+    sample = oracle.brute_rows(sp, 1e30, rng.integers(0, n, size=8))["dist"]
+    for q in (0.003, 0.03, 0.15):
+        eps = float(np.float32(np.quantile(sample, q)))
+        ref = oracle.brute_force(sp, eps)
+        out = gpu_graph(points=x, eps=eps, leaf_size=zeta, export=(q == 0.03))
+        assert_csr_matches(out, ref)
+        if q == 0.03:
+            _check_tree(sp, out)
+
+
+def test_degenerate_sizes():
+    for n in (0, 1, 2, 3, 33):
+        x = I.uniform_cube(n, 3, seed=n)
+        sp = oracle.Space(points=x)
+        for eps in (0.0, 0.3, 10.0):
+            out = gpu_graph(points=x, eps=eps, export=True)
+            assert_csr_matches(out, oracle.brute_force(sp, eps))
+            if n:
+                _check_tree(sp, out)
+            else:
+                assert out["row_ptr"].tolist() == [0]
+
+
+def test_duplicates_above_leaf_size_and_eps_zero():
+    rng = np.random.default_rng(3)
+    distinct = rng.random((40, 6)).astype(np.float32)
+    x = distinct[rng.integers(0, 40, size=3000)]
+    x[:200] = x[0]                      # one class far above zeta
+    sp = oracle.Space(points=x)
+    for eps in (0.0, 0.05, 0.4):
+        out = gpu_graph(points=x, eps=eps, leaf_size=16, export=True)
+        assert_csr_matches(out, oracle.brute_force(sp, eps))
+    _check_tree(sp, out)
+
+
+def test_complete_graph_and_include_self():
+    x = I.uniform_cube(700, 4, seed=1)
+    sp = oracle.Space(points=x)
+    out = gpu_graph(points=x, eps=5.0)
+    assert out["row_ptr"][-1] == 700 * 699
+    assert_csr_matches(out, oracle.brute_force(sp, 5.0))
+    out = gpu_graph(points=x, eps=0.2, include_self=True)
+    assert_csr_matches(out, oracle.brute_force(sp, 0.2, include_self=True))
+
+
+def test_lattice_ties_exactly_at_eps():
+    """Every edge of the lattice lies exactly at eps (or at sqrt 2 rounded to
+    fp32 either way): the decision at the boundary is the FP64 one."""
+    g = np.arange(9, dtype=np.float32)
+    x = np.array(list(itertools.product(g, g, g)), dtype=np.float32)
+    sp = oracle.Space(points=x)
+    up = float(np.nextafter(np.float32(math.sqrt(2)), np.float32(np.inf)))
+    dn = float(np.float32(math.sqrt(2)))
+    for eps in (1.0, up, dn, math.sqrt(3)):
+        out = gpu_graph(points=x, eps=eps, leaf_size=8)
+        ref = oracle.brute_force(sp, eps)
+        assert_csr_matches(out, ref)
+        assert out["stats"]["guard_fp64"] > 0 or eps == math.sqrt(3)
+
+
+def test_large_offsets_no_cancellation():
+    """Points far from the origin with small separations: direct differences
+    keep full relative accuracy."""
+    base = I.uniform_cube(2500, 16, seed=4).astype(np.float64)
+    x = (base + 3000.0).astype(np.float32)      # |x|^2 ~ 1.4e8 against d^2 ~ 1
+    sp = oracle.Space(points=x)
+    sample = oracle.brute_rows(sp, 1e30, [0, 1, 2])["dist"]
+    eps = float(np.quantile(sample[sample > 0], 0.02))
+    assert_csr_matches(gpu_graph(points=x, eps=eps), oracle.brute_force(sp, eps))
+
+
+def test_root_choice_does_not_change_output():
+    x = I.uniform_cube(1500, 5, seed=8)
+    a = gpu_graph(points=x, eps=0.2, root=0)
+    b = gpu_graph(points=x, eps=0.2, root=777)
+    assert np.array_equal(a["row_ptr"], b["row_ptr"]) and np.array_equal(a["col"], b["col"])
+
+
+def test_near_boundary_pairs_random():
+    """Pairs placed at eps * (1 +- 1e-7 .. 1e-3): inside the guard band the FP64
+    decision must match the oracle bit for bit."""
+    rng = np.random.default_rng(0)
+    n, dim, eps = 1200, 24, 0.75
+    a = rng.standard_normal((n // 2, dim)).astype(np.float32) * 3
+    u = rng.standard_normal((n // 2, dim))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    scale = eps * (1 + rng.choice([-1, 1], n // 2) * 10 ** rng.uniform(-7.5, -3, n // 2))
+    b = (a + u * scale[:, None]).astype(np.float32)
+    x = np.concatenate([a, b])
+    sp = oracle.Space(points=x)
+    out = gpu_graph(points=x, eps=eps)
+    assert_csr_matches(out, oracle.brute_force(sp, eps))
+    assert out["stats"]["guard_fp64"] >= n // 4
+
+
+# ------------------------------------------------------------ edit distance
+
+@pytest.mark.parametrize("eps", [0, 3, 8, 15])
+def test_levenshtein_dna(eps):
+    data, off = I.dna_strings(n_seeds=12, per_seed=60, seed=5)
+    sp = oracle.Space(strings=(data, off))
+    out = gpu_graph(strings=(data, off), eps=eps, leaf_size=16, export=(eps == 8))
+    assert_csr_matches(out, oracle.brute_force(sp, eps), integer_dist=True)
+    if eps == 8:
+        code, msg = oracle.check_tree(sp, tree_from_export(out["tree"]), 0.0)
+        assert code == 0, msg
+
+
+def test_levenshtein_mixed_lengths_and_alphabet():
+    d1, o1 = I.random_strings(500, 0, 150, alphabet=b"ACGTN", seed=1)
+    d2, o2 = I.random_strings(300, 60, 70, alphabet=bytes(range(32, 127)), seed=2)
+    data = np.concatenate([d1, d2])
+    off = np.concatenate([o1, o2[1:] + o1[-1]])
+    # a few near-duplicates so that some edges exist
+    sp = oracle.Space(strings=(data, off))
+    for eps in (2, 40, 300):
+        out = gpu_graph(strings=(data, off), eps=eps, leaf_size=8)
+        assert_csr_matches(out, oracle.brute_force(sp, eps), integer_dist=True)
+
+
+def test_levenshtein_long_strings_multiword():
+    data, off = I.dna_strings(n_seeds=4, per_seed=40, seed_len=700, min_len=600, max_len=800, seed=9)
+    sp = oracle.Space(strings=(data, off))
+    out = gpu_graph(strings=(data, off), eps=60, leaf_size=8)
+    assert_csr_matches(out, oracle.brute_force(sp, 60), integer_dist=True)
+
+
+# ------------------------------------------------------------ full size
+
+@pytest.mark.parametrize("key", ["gmm_1m_k70"])
+def test_full_size_sampled_rows(key):
+    """1M x 128 points at the calibrated eps: sampled rows equal the oracle's
+    brute force; the whole output is symmetric with sorted rows."""
+    wl = I.load_workloads()[key]
+    x = I.gmm_embedded(wl["n"], dim=wl["dim"], seed=wl["seed"])
+    out = gpu_graph(points=x, eps=wl["eps"])
+    rp, col = out["row_ptr"], out["col"].astype(np.int64)
+    n = x.shape[0]
+    mean_deg = rp[-1] / n
+    assert 0.5 * wl["target_degree"] < mean_deg < 2.0 * wl["target_degree"]
+    rows_ok = np.all((np.diff(col) > 0) | (np.diff(np.repeat(np.arange(n), np.diff(rp))) != 0))
+    assert rows_ok
+    assert oracle.csr_symmetric({"row_ptr": rp, "col": col})
+    rng = np.random.default_rng(1)
+    rows = np.sort(rng.choice(n, size=48, replace=False))
+    sp = oracle.Space(points=x)
+    ref = oracle.brute_rows(sp, wl["eps"], rows)
+    sub = {"row_ptr": np.concatenate([[0], np.cumsum(rp[rows + 1] - rp[rows])]),
+           "col": np.concatenate([col[rp[r]:rp[r + 1]] for r in rows]),
+           "dist": np.concatenate([out["dist"][rp[r]:rp[r + 1]] for r in rows])}
+    assert_csr_matches(sub, ref)
