@@ -150,6 +150,32 @@ ct_status eps_graph_query_batched(int32_t n_clouds, const ct_tree *const *trees,
                                   const double *eps, const ct_query_opts *opts,
                                   ct_stream stream, ct_csr *outs);
 
+/* Size of the fixed device array used by eps_graph_degrees_noalloc. */
+#define CT_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Degree of every point of the ε-graph, without allocating device memory.
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot let a library allocate on the device (an application whose own
+ * allocator owns the device and hands out fixed budgets, or a latency-bound
+ * loop that cannot take an allocation's implicit synchronisation or its
+ * possible failure).
+ *  degrees: device int32[n], written by the call: degrees[i] is the number of
+ *           j (j != i unless include_self) with d(p_i, p_j) <= eps, i.e.
+ *           row_ptr[i+1] - row_ptr[i] of eps_graph_query with the same eps.
+ * All temporaries live in one fixed array of CT_NOALLOC_SCRATCH_BYTES bytes
+ * inside the library (every GPU that loads the library holds it until the
+ * process exits).  The first call on a device looks up that array's device
+ * address; make that first call before any stream capture.  Calls never
+ * allocate or free device memory; they synchronise `stream` twice.
+ * Every call reuses the same array and clears what must start at zero; calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on
+ * it and must be serialised by the caller.
+ * L2 trees only.  Errors: CT_EINVAL (null pointers, eps < 0 or NaN),
+ * CT_EUNSUPPORTED (an edit-distance tree, or a problem whose temporaries do
+ * not fit the fixed array: the message gives the need), CT_ECUDA. */
+ct_status eps_graph_degrees_noalloc(const ct_tree *tree, double eps, int32_t include_self,
+                                    int32_t *degrees, ct_stream stream);
+
 /* Releases a CSR (stream-ordered on the stream it was produced on; that
  * stream must still exist).  Idempotent and NULL-safe: zeroes *csr. */
 void csr_free(ct_csr *csr);

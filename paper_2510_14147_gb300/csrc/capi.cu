@@ -14,6 +14,7 @@ void query_predicted(const ct_tree *t, const QParams &qp, const void *predictor,
                      cudaStream_t s, QueryOut &out);
 void query_batched(int n_clouds, const ct_tree *const *trees, const QParams *qps, const ct_query_opts *opts,
                    cudaStream_t s, QueryOut *outs);
+void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cudaStream_t s);
 }  // namespace ct
 
 namespace {
@@ -170,6 +171,19 @@ ct_status eps_graph_query_batched(int32_t n_clouds, const ct_tree *const *trees,
         }
     }
     return st;
+}
+
+ct_status eps_graph_degrees_noalloc(const ct_tree *tree, double eps, int32_t include_self, int32_t *degrees,
+                                    ct_stream stream) {
+    return guarded([&] {
+        if (!tree) CT_FAIL(CT_EINVAL, "tree is NULL");
+        if (tree->n > 0 && !degrees) CT_FAIL(CT_EINVAL, "degrees is NULL");
+        if (!(eps >= 0.0)) CT_FAIL(CT_EINVAL, "eps must be >= 0 (got %g)", eps);
+        if (include_self != 0 && include_self != 1) CT_FAIL(CT_EINVAL, "include_self must be 0 or 1");
+        check_device(tree);
+        ct::QParams qp = ct::make_qparams(tree, eps, include_self);
+        ct::degrees_noalloc(tree, qp, degrees, (cudaStream_t)stream);
+    });
 }
 
 void csr_free(ct_csr *csr) {

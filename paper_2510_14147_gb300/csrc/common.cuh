@@ -104,6 +104,10 @@ void exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64
                                cudaStream_t s);
 void exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev,
                         cudaStream_t s);
+// The same scan with caller-provided tile sums (scan_scratch_entries(n) int64).
+int64_t scan_scratch_entries(int64_t n);
+void exclusive_scan_i32_to_i64_into(const int32_t *in, int64_t *out, int64_t n, int64_t *total_dev,
+                                    int64_t *tile_sums, cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits of
 // the key.  Sorted output returned in keys/vals (tmp buffers of n entries).

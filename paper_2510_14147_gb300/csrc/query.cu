@@ -20,6 +20,7 @@
 #include <cfloat>
 #include <climits>
 #include <cmath>
+#include <mutex>
 
 #include "lev.cuh"
 #include "profile.cuh"
@@ -1030,6 +1031,112 @@ void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &
     out.stats.guard_fp64 = (int64_t)hs[ST_GUARD];
     out.stats.recheck_fp32 = (int64_t)hs[ST_RECHECK];
     out.stats.candidates = n_cand;
+}
+
+}  // namespace ct
+
+// ----------------------------------------------------------------------
+// Degrees without device allocation.
+//
+// Some callers cannot let a library allocate device memory: an application
+// whose own allocator owns the whole device and hands out fixed budgets, or a
+// latency-bound loop where an allocation's implicit synchronisation, or its
+// possible failure, is not acceptable.  For them the count pass (tree walk +
+// FP32 leaf tiles with the FP64 guard band) also runs with every temporary
+// buffer placed in one fixed device array of this translation unit.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CT_NOALLOC_SCRATCH_BYTES];
+
+namespace ct {
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[64] = {};
+
+// Device address of the fixed array on the current device, looked up once per
+// device (the host-side symbol is not a device address).
+unsigned char *noalloc_scratch() {
+    int dev = 0;
+    CT_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) CT_FAIL(CT_EUNSUPPORTED, "device ordinal %d above 63", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            CT_FAIL(CT_ECUDA, "cudaGetSymbolAddress of the fixed scratch failed: %s", cudaGetErrorString(e));
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    return (unsigned char *)g_noalloc_addr[dev];
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+}  // namespace
+
+void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cudaStream_t s) {
+    if (t->metric != CT_L2_F32) CT_FAIL(CT_EUNSUPPORTED, "the allocation-free degree count supports L2 trees only");
+    const int64_t n = t->n;
+    const int G = t->n_groups;
+    if (n == 0) return;
+    unsigned char *base = noalloc_scratch();
+    const size_t cap_bytes = CT_NOALLOC_SCRATCH_BYTES;
+    const int cap = 32 * (t->depth + 2);
+    // fixed part: counters, per-group counts and offsets, scan tile sums
+    size_t off = 0;
+    unsigned long long *st = (unsigned long long *)(base + off);
+    off = align256(off + ST_N * sizeof(unsigned long long));
+    int32_t *ccnt = (int32_t *)(base + off);
+    off = align256(off + (size_t)(G + 1) * sizeof(int32_t));
+    int64_t *coff = (int64_t *)(base + off);
+    off = align256(off + (size_t)(G + 1) * sizeof(int64_t));
+    int64_t *sums = (int64_t *)(base + off);
+    off = align256(off + (size_t)std::max<int64_t>(scan_scratch_entries(G), 1) * sizeof(int64_t));
+    const size_t stack_per_block = (size_t)TRAV_WARPS * cap * sizeof(int2);
+    if (off + stack_per_block > cap_bytes)
+        CT_FAIL(CT_EUNSUPPORTED, "tree with %d query groups and depth %d needs more than the fixed %zu-byte scratch",
+                G, t->depth, cap_bytes);
+    // traversal blocks: as in the allocating path, capped so that the stacks
+    // take at most a quarter of the array
+    int64_t want = std::min<int64_t>(ceil_div(G, TRAV_WARPS), (int64_t)num_sms() * 8);
+    int64_t fit = (int64_t)std::max<size_t>(1, (cap_bytes / 4) / stack_per_block);
+    const int blocks = (int)std::max<int64_t>(1, std::min(want, fit));
+    int2 *stacks = (int2 *)(base + off);
+    off = align256(off + (size_t)blocks * stack_per_block);
+    uint32_t *cand = (uint32_t *)(base + off);
+    if (off >= cap_bytes) CT_FAIL(CT_EUNSUPPORTED, "problem too large for the fixed scratch");
+    const int64_t cand_cap = (int64_t)((cap_bytes - off) / sizeof(uint32_t));
+
+    TreeView tv = view_of(t);
+    int32_t *err = reinterpret_cast<int32_t *>(st + ST_ERR);
+    const size_t tsm = (size_t)TRAV_WARPS * t->dp * sizeof(float);
+    if (tsm > 48 * 1024) {
+        CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+        CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    }
+    // the array keeps the previous call's contents: clear the counters
+    CT_CHECK_CUDA(cudaMemsetAsync(st, 0, ST_N * sizeof(unsigned long long), s));
+    k_traverse_l2<false><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt, coff, nullptr, stacks, cap, st, err);
+    CT_COUNT_LAUNCH();
+    CT_LAUNCH_CHECK();
+    exclusive_scan_i32_to_i64_into(ccnt, coff, G, coff + G, sums, s);
+    int64_t total = 0;
+    CT_CHECK_CUDA(cudaMemcpyAsync(&total, coff + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CT_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (total > cand_cap)
+        CT_FAIL(CT_EUNSUPPORTED, "%lld candidate blocks exceed the fixed scratch (room for %lld); use eps_graph_query",
+                (long long)total, (long long)cand_cap);
+    k_traverse_l2<true><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt, coff, cand, stacks, cap, st, err);
+    CT_COUNT_LAUNCH();
+    if (G) {
+        k_leaf_l2<false><<<G, LEAF_T, 0, s>>>(tv, qp, coff, cand, degrees, nullptr, nullptr, nullptr, st, err);
+        CT_COUNT_LAUNCH();
+    }
+    CT_LAUNCH_CHECK();
+    unsigned long long e = 0;
+    CT_CHECK_CUDA(cudaMemcpyAsync(&e, st + ST_ERR, sizeof(e), cudaMemcpyDeviceToHost, s));
+    CT_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (e) CT_FAIL(CT_ECUDA, "internal consistency check failed in the degree count (code %llu)", e);
 }
 
 }  // namespace ct

@@ -188,6 +188,24 @@ void exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64
                                cudaStream_t s) {
     exclusive_scan_impl<int32_t>(in, out, n, total_dev, s);
 }
+
+int64_t scan_scratch_entries(int64_t n) { return n > 0 ? ceil_div(n, SCAN_TILE) : 0; }
+
+void exclusive_scan_i32_to_i64_into(const int32_t *in, int64_t *out, int64_t n, int64_t *total_dev,
+                                    int64_t *tile_sums, cudaStream_t s) {
+    if (n <= 0) {
+        if (total_dev) CT_CHECK_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(int64_t), s));
+        return;
+    }
+    int64_t tiles = ceil_div(n, SCAN_TILE);
+    k_tile_sums<int32_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, tile_sums);
+    CT_COUNT_LAUNCH();
+    k_scan_single<<<1, 1024, 0, s>>>(tile_sums, tiles, total_dev);
+    CT_COUNT_LAUNCH();
+    k_tile_scan<int32_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, tile_sums);
+    CT_COUNT_LAUNCH();
+    CT_LAUNCH_CHECK();
+}
 void exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev,
                         cudaStream_t s) {
     exclusive_scan_impl<int64_t>(in, out, n, total_dev, s);

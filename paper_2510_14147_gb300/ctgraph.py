@@ -105,6 +105,8 @@ def _load():
         lib.ct_profile_count.argtypes = []
         lib.ct_profile_entry.restype = C.c_int
         lib.ct_profile_entry.argtypes = [C.c_int32, P(C.c_char_p), P(C.c_double), P(C.c_int64)]
+        lib.eps_graph_degrees_noalloc.restype = C.c_int
+        lib.eps_graph_degrees_noalloc.argtypes = [C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p]
         lib.ct_kernel_launches.restype = C.c_int64
         lib.ct_kernel_launches.argtypes = []
         _lib = lib
@@ -286,6 +288,19 @@ def eps_graph_query_batched(trees, eps, precision: int = 0, use_predictor: bool 
     o = _opts(precision, use_predictor, include_self, predictor)
     _check(lib.eps_graph_query_batched(k, arr, ea, C.byref(o), C.c_void_p(_stream(stream)), outs))
     return [CSR(outs[i]) for i in range(k)]
+
+
+def eps_graph_degrees_noalloc(tree: Tree, eps: float, degrees, include_self: bool = False, stream=None):
+    """Writes the ε-graph degree of every point into ``degrees`` (a CUDA int32
+    tensor of n entries owned by the caller) without any device allocation by
+    the library; the library's temporaries live in its fixed device array."""
+    import torch
+    if tree.n and not (degrees.is_cuda and degrees.dtype == torch.int32 and degrees.is_contiguous()
+                       and degrees.numel() >= tree.n):
+        raise ValueError("degrees must be a contiguous CUDA int32 tensor with n entries")
+    _check(_load().eps_graph_degrees_noalloc(tree.handle, float(eps), int(bool(include_self)),
+                                             degrees.data_ptr() if tree.n else None,
+                                             C.c_void_p(_stream(stream))))
 
 
 def csr_free(csr: CSR):
