@@ -25,6 +25,10 @@ from paper_2510_14147_gb300 import inputs as I  # noqa: E402
 OUT = os.path.join(_ROOT, "paper_2510_14147_gb300", "workloads.json")
 
 
+PROFILE_SIZE = {"kind": "gmm", "n": 300_000, "dim": 128, "seed": 0, "target_degree": 70.0, "zeta": 32,
+                "note": "profiling size of the 1M generator (154 MB of points, above the 129 MB L2)"}
+
+
 def calibrate(x: np.ndarray, target_degree: float, n_queries: int = 4096, seed: int = 12345) -> float:
     n = x.shape[0]
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -52,6 +56,22 @@ def calibrate(x: np.ndarray, target_degree: float, n_queries: int = 4096, seed: 
 
 
 def main():
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--only", default=None, help="recompute one workload and keep the others")
+    args = ap.parse_args()
+    if args.only:
+        with open(OUT) as f:
+            wl = json.load(f)
+        key = args.only
+        spec = dict(PROFILE_SIZE) if key == "gmm_300k_k70" else wl[key]
+        x = I.gmm_embedded(spec["n"], dim=spec["dim"], seed=spec["seed"])
+        spec["eps"] = calibrate(x, spec["target_degree"])
+        wl[key] = spec
+        print(key, spec["eps"])
+        with open(OUT, "w") as f:
+            json.dump(wl, f, indent=1)
+        return
     wl = {
         "small_3d": {"kind": "uniform", "n": 2000, "dim": 3, "seed": 0, "eps": 0.08,
                      "zeta": 32, "note": "uniform [0,1]^3, eps=0.08"},
@@ -65,6 +85,10 @@ def main():
                     "seed": 0, "eps": 8, "zeta": 32,
                     "note": "Levenshtein; 4% substitution, 0.5% insertion, 0.5% deletion per site"},
     }
+    wl["gmm_300k_k70"] = dict(PROFILE_SIZE)
+    x3 = I.gmm_embedded(300_000, seed=0)
+    wl["gmm_300k_k70"]["eps"] = calibrate(x3, 70.0)
+    del x3
     x = I.gmm_embedded(1_000_000, seed=0)
     for key in ("gmm_1m_k70", "gmm_1m_k500"):
         wl[key]["eps"] = calibrate(x, wl[key]["target_degree"])
