@@ -163,7 +163,7 @@ template <bool FILL>
 __global__ void __launch_bounds__(TRAV_WARPS * 32) k_traverse_l2(
     TreeView tv, QParams qp, int32_t *__restrict__ cand_cnt, const int64_t *__restrict__ cand_off,
     uint32_t *__restrict__ cand, int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st,
-    int32_t *__restrict__ err) {
+    int32_t *__restrict__ err, int32_t *__restrict__ next_group) {
     extern __shared__ float4 sc[];  // TRAV_WARPS x (dp/4)
     const int nq = tv.dp >> 2;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -172,7 +172,13 @@ __global__ void __launch_bounds__(TRAV_WARPS * 32) k_traverse_l2(
     const int nw = gridDim.x * TRAV_WARPS;
     int2 *stack = stacks + (int64_t)gw * cap;
     unsigned long long evals = 0;
-    for (int g = gw; g < tv.n_groups; g += nw) {
+    (void)nw;
+    for (;;) {
+        // groups are taken dynamically: their walks differ widely in length
+        int g = 0;
+        if (lane == 0) g = atomicAdd(next_group, 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= tv.n_groups) break;
         const float4 *crow = reinterpret_cast<const float4 *>(tv.pts + (size_t)tv.group_begin[g] * tv.dp);
         for (int k = lane; k < nq; k += 32) cen[k] = crow[k];
         __syncwarp();
@@ -203,12 +209,16 @@ template <bool FILL, int W>
 __global__ void __launch_bounds__(32) k_traverse_lev(
     TreeView tv, QParams qp, int32_t *__restrict__ cand_cnt, const int64_t *__restrict__ cand_off,
     uint32_t *__restrict__ cand, int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st,
-    int32_t *__restrict__ err) {
+    int32_t *__restrict__ err, int32_t *__restrict__ next_group) {
     __shared__ uint64_t peq[256 * W];
     const int lane = threadIdx.x;
     int2 *stack = stacks + (int64_t)blockIdx.x * cap;
     unsigned long long evals = 0;
-    for (int g = blockIdx.x; g < tv.n_groups; g += gridDim.x) {
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(next_group, 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= tv.n_groups) break;
         int cpos = tv.group_begin[g];
         const uint8_t *pat = tv.sdata + tv.soff[cpos];
         int m = (int)(tv.soff[cpos + 1] - tv.soff[cpos]);
@@ -354,171 +364,581 @@ __device__ __forceinline__ int decide_l2(const QParams &qp, float s, const float
     return edge;
 }
 
-// One CTA per query group.  Q tile: the group's points (32 rows at a time);
-// P tiles: packed candidate points.  Each thread owns a 2 x 4 block of pairs
-// (queries qi, qi+16; points pj, pj+8, pj+16, pj+24) and accumulates the
-// squared differences over the row in chunks of 16 coordinates (chunk sums
-// added into a running total), which bounds the fp32 error of the sum by
-// about 26 units of roundoff for rows of up to 128 floats.
-template <bool EMIT>
-__global__ void __launch_bounds__(LEAF_T) k_leaf_l2(
-    TreeView tv, QParams qp, const int64_t *__restrict__ cand_off, uint32_t *__restrict__ cand,
-    int32_t *__restrict__ deg, const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col,
-    float *__restrict__ dist, unsigned long long *__restrict__ st, int32_t *__restrict__ err) {
-    __shared__ float4 Qs[32 * KS4];
-    __shared__ float4 Ps[32 * KS4];
-    __shared__ int cursor[32];
-    __shared__ int64_t rowb[32], rowe[32];
-    __shared__ int tpos[32];
-    __shared__ int64_t tcand[32];
-    __shared__ int64_t s_ci;
-    __shared__ int s_off, s_rows;
-    __shared__ unsigned s_hit;
-    const int g = blockIdx.x;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int qi = tid >> 3, pj = tid & 7;
-    const int dp = tv.dp, dim = tv.dim;
-    const int nkc = (dp + KC - 1) / KC;
-    const bool fp32_dist_ok = dp <= 128;
-    const int qb = tv.group_begin[g], qn = tv.group_count[g];
-    const int64_t c0 = cand_off[g], c1 = cand_off[g + 1];
-    unsigned long long pairs = 0;
-    unsigned guard = 0;
+constexpr int NB = 128;       // candidate leaf blocks per batch
+constexpr int GQ_CAP = 1088;  // guard-band queue: <= 63 carried + 1024 from one tile
+constexpr int RCAP = 512;     // packed rows mapped to positions at a time
 
-    for (int q0 = 0; q0 < qn; q0 += 32) {
-        const int nqr = min(32, qn - q0);
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    int n = valid ? 16 : 0;  // 0: the 16 bytes are zero-filled, nothing is read
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Squared distances of the 2 x 4 pairs owned by this thread: queries qi and
+// qi + 16 of the Q tile against rows pj, pj+8, pj+16, pj+24 of the P tile,
+// whose positions are prow[0..npr).  Coordinates are summed in chunks of 16
+// (FMA per term) and the chunk sums added into the total.  Contains barriers;
+// every thread of the block calls it.  On return the P tile is loaded and
+// every thread is past its last read of Qs/Ps for this call.
+__device__ __forceinline__ void tile_sqdist(const TreeView &tv, float4 *Qs, float4 *Ps, const int *prow, int npr,
+                                            int qfirst, int nqr, int nkc, float (&tot)[2][4]) {
+    const int tid = threadIdx.x, qi = tid >> 3, pj = tid & 7;
+    const int dp = tv.dp;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tot[i][j] = 0.f;
+    for (int kc = 0; kc < nkc; ++kc) {
+        const int k0 = kc * KC;
+        const int kq = min(KC, dp - k0) >> 2;
+        if (kc > 0) __syncthreads();
+        if (nkc > 1) load_rows(Qs, tv.pts, dp, nullptr, qfirst, nqr, k0, kq);
+        load_rows(Ps, tv.pts, dp, prow, 0, npr, k0, kq);
         __syncthreads();
-        if (tid < 32) {
-            cursor[tid] = 0;
-            if (EMIT && tid < nqr) {
-                int o = tv.perm[qb + q0 + tid];
-                rowb[tid] = row_ptr[o];
-                rowe[tid] = row_ptr[o + 1];
-            }
-        }
-        if (tid == 0) {
-            s_ci = c0;
-            s_off = 0;
-            s_hit = 0u;
-        }
-        int cnt0 = 0, cnt1 = 0;
-        if (nkc == 1) load_rows(Qs, tv.pts, dp, nullptr, qb + q0, nqr, 0, dp >> 2);
-        for (;;) {
-            __syncthreads();
-            if (warp == 0) fill_tile(tv, cand, c1, EMIT, &s_ci, &s_off, &s_rows, tpos, tcand);
-            __syncthreads();
-            const int npr = s_rows;
-            const bool last = s_ci >= c1;
-            if (npr > 0) {
-                float tot[2][4];
+        const float4 *qa = Qs + qi * KS4, *qb2 = Qs + (qi + 16) * KS4;
+        const float4 *pr0 = Ps + pj * KS4, *pr1 = Ps + (pj + 8) * KS4;
+        const float4 *pr2 = Ps + (pj + 16) * KS4, *pr3 = Ps + (pj + 24) * KS4;
+        for (int k4 = 0; k4 < kq; k4 += 4) {
+            float acc[2][4];
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+            const int ke = min(k4 + 4, kq);
+            for (int k = k4; k < ke; ++k) {
+                float4 a[2] = {qa[k], qb2[k]};
+                float4 b[4] = {pr0[k], pr1[k], pr2[k], pr3[k]};
 #pragma unroll
                 for (int i = 0; i < 2; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) tot[i][j] = 0.f;
-                for (int kc = 0; kc < nkc; ++kc) {
-                    const int k0 = kc * KC;
-                    const int kq = min(KC, dp - k0) >> 2;
-                    if (kc > 0) __syncthreads();
-                    if (nkc > 1) load_rows(Qs, tv.pts, dp, nullptr, qb + q0, nqr, k0, kq);
-                    load_rows(Ps, tv.pts, dp, tpos, 0, npr, k0, kq);
-                    __syncthreads();
-                    const float4 *qa = Qs + qi * KS4, *qb2 = Qs + (qi + 16) * KS4;
-                    const float4 *pr0 = Ps + pj * KS4, *pr1 = Ps + (pj + 8) * KS4;
-                    const float4 *pr2 = Ps + (pj + 16) * KS4, *pr3 = Ps + (pj + 24) * KS4;
-                    for (int k4 = 0; k4 < kq; k4 += 4) {
-                        float acc[2][4];
+                    for (int j = 0; j < 4; ++j) {
+                        float dx = a[i].x - b[j].x, dy = a[i].y - b[j].y;
+                        float dz = a[i].z - b[j].z, dw = a[i].w - b[j].w;
+                        acc[i][j] = fmaf(dx, dx, acc[i][j]);
+                        acc[i][j] = fmaf(dy, dy, acc[i][j]);
+                        acc[i][j] = fmaf(dz, dz, acc[i][j]);
+                        acc[i][j] = fmaf(dw, dw, acc[i][j]);
+                    }
+            }
 #pragma unroll
-                        for (int i = 0; i < 2; ++i)
+            for (int i = 0; i < 2; ++i)
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-                        const int ke = min(k4 + 4, kq);
-                        for (int k = k4; k < ke; ++k) {
-                            float4 a[2] = {qa[k], qb2[k]};
-                            float4 b[4] = {pr0[k], pr1[k], pr2[k], pr3[k]};
+                for (int j = 0; j < 4; ++j) tot[i][j] += acc[i][j];
+        }
+    }
+}
+
+// Packed fp32 pairs (sm_100+ f32x2 instructions): two independent IEEE
+// round-to-nearest operations per instruction.
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_sqacc(unsigned long long d, unsigned long long acc) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(d), "l"(acc));
+    return r;
+}
+__device__ __forceinline__ float f2_sum(unsigned long long v) {
+    return __uint_as_float((uint32_t)v) + __uint_as_float((uint32_t)(v >> 32));
+}
+
+// 2 x 4 micro-tile from tiles already in shared memory (rows of kq float4).
+// Per chunk of 16 coordinates two packed partial sums of 8 terms each (even
+// and odd coordinates) are formed with FMA, added, and the chunk sum is added
+// into the running total: fp32 error of the squared distance <= ~19 u for
+// rows of 128 floats (u = 2^-24).
+__device__ __forceinline__ void tile_sqdist_smem(const float4 *Qs, const float4 *Ps, int kq, float (&tot)[2][4]) {
+    const int tid = threadIdx.x, qi = tid >> 3, pj = tid & 7;
 #pragma unroll
-                            for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-                                for (int j = 0; j < 4; ++j) {
-                                    float dx = a[i].x - b[j].x, dy = a[i].y - b[j].y;
-                                    float dz = a[i].z - b[j].z, dw = a[i].w - b[j].w;
-                                    acc[i][j] = fmaf(dx, dx, acc[i][j]);
-                                    acc[i][j] = fmaf(dy, dy, acc[i][j]);
-                                    acc[i][j] = fmaf(dz, dz, acc[i][j]);
-                                    acc[i][j] = fmaf(dw, dw, acc[i][j]);
-                                }
+        for (int j = 0; j < 4; ++j) tot[i][j] = 0.f;
+    const ulonglong2 *qa[2] = {reinterpret_cast<const ulonglong2 *>(Qs + qi * KS4),
+                               reinterpret_cast<const ulonglong2 *>(Qs + (qi + 16) * KS4)};
+    const ulonglong2 *pr[4] = {reinterpret_cast<const ulonglong2 *>(Ps + pj * KS4),
+                               reinterpret_cast<const ulonglong2 *>(Ps + (pj + 8) * KS4),
+                               reinterpret_cast<const ulonglong2 *>(Ps + (pj + 16) * KS4),
+                               reinterpret_cast<const ulonglong2 *>(Ps + (pj + 24) * KS4)};
+    int k4 = 0;
+    for (; k4 + 4 <= kq; k4 += 4) {
+        unsigned long long acc[2][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0ull;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const ulonglong2 a0 = qa[0][k4 + u], a1 = qa[1][k4 + u];
+            const ulonglong2 b[4] = {pr[0][k4 + u], pr[1][k4 + u], pr[2][k4 + u], pr[3][k4 + u]};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                acc[0][j] = f2_sqacc(f2_sub(a0.x, b[j].x), acc[0][j]);
+                acc[0][j] = f2_sqacc(f2_sub(a0.y, b[j].y), acc[0][j]);
+                acc[1][j] = f2_sqacc(f2_sub(a1.x, b[j].x), acc[1][j]);
+                acc[1][j] = f2_sqacc(f2_sub(a1.y, b[j].y), acc[1][j]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) tot[i][j] += f2_sum(acc[i][j]);
+    }
+    if (k4 < kq) {  // rows whose length is not a multiple of 16 floats
+        unsigned long long acc[2][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0ull;
+        for (int k = k4; k < kq; ++k) {
+            const ulonglong2 a0 = qa[0][k], a1 = qa[1][k];
+            const ulonglong2 b[4] = {pr[0][k], pr[1][k], pr[2][k], pr[3][k]};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                acc[0][j] = f2_sqacc(f2_sub(a0.x, b[j].x), acc[0][j]);
+                acc[0][j] = f2_sqacc(f2_sub(a0.y, b[j].y), acc[0][j]);
+                acc[1][j] = f2_sqacc(f2_sub(a1.x, b[j].x), acc[1][j]);
+                acc[1][j] = f2_sqacc(f2_sub(a1.y, b[j].y), acc[1][j]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) tot[i][j] += f2_sum(acc[i][j]);
+    }
+}
+
+struct LeafShared {
+    float4 Qs[32 * KS4];
+    float4 Ps[2][32 * KS4];
+    int bbeg[NB], bcnt[NB], bpre[NB + 1];
+    uint32_t bmask[NB], bem[NB];
+    float brad[NB];
+    int64_t bci[NB];
+    int rpos[RCAP];
+    uint8_t rli[RCAP];
+    int64_t rowb[32], rowe[32];
+    int cursor[32], qcnt[32];
+    int gpos[GQ_CAP];
+    uint8_t gq[GQ_CAP], gb[GQ_CAP];
+    int gn, nb_fill, scan_tmp[LEAF_T / 32];
+    int64_t next_ci;
+};
+constexpr size_t kLeafSmem = sizeof(LeafShared);
+
+// One CTA per query group; queries in chunks of 32 (Q tile), candidate leaf
+// blocks in batches of NB.  Per batch:
+//  stage 1 (count pass) -- Algorithm 3's own test per query,
+//             d(q, c_v) <= r(v) + eps, for every (query, candidate block) pair,
+//             as dense 32 x 32 tiles of query rows against block centres; it
+//             gives each block the mask of queries that still need it (a
+//             pruned pair cannot hold an edge);
+//  stage 2 -- the points of blocks with a non-empty mask, packed into 32-row
+//             tiles (double buffered with cp.async); pairs outside the block's
+//             mask are skipped.
+// The emit pass skips stage 1: the count pass leaves, per candidate block,
+// the mask of queries that found an edge in it, and the emit pass batches only
+// blocks whose mask is non-empty.  Pairs inside the guard band are queued and
+// decided in FP64 by whole warps.
+// A work item: a slice of at most kItem candidate blocks of one query group.
+// Heavy groups (large candidate lists) are spread over several CTAs.
+constexpr int kItem = 512;
+struct Items {
+    const int32_t *group;
+    const int64_t *begin, *end;
+    const int32_t *count;  // device: number of items
+};
+
+template <bool EMIT>
+__global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
+    TreeView tv, QParams qp, Items items, const uint32_t *__restrict__ cand,
+    uint32_t *__restrict__ emask, int32_t *__restrict__ deg, const int64_t *__restrict__ row_ptr,
+    int32_t *__restrict__ rowcur, int32_t *__restrict__ col, float *__restrict__ dist,
+    unsigned long long *__restrict__ st, int32_t *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
+    const int it = blockIdx.x;
+    if (it >= *items.count) return;
+    const int g = items.group[it];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int qi = tid >> 3, pj = tid & 7;
+    const int dp = tv.dp, dim = tv.dim;
+    const int nkc = (dp + KC - 1) / KC;
+    const int kq = dp >> 2;  // float4 per row when nkc == 1
+    const bool fp32_dist_ok = dp <= 128;
+    const int qb = tv.group_begin[g], qn = tv.group_count[g];
+    const int64_t c0 = items.begin[it], c1 = items.end[it];
+    unsigned long long pairs = 0, s1evals = 0, guard = 0;
+
+    for (int q0 = 0; q0 < qn; q0 += 32) {
+        const int nqr = min(32, qn - q0);
+        const int qfirst = qb + q0;
+        __syncthreads();
+        if (tid < 32) {
+            S.qcnt[tid] = 0;
+            if (tid < nqr) {
+                int o = tv.perm[qfirst + tid];
+                S.cursor[tid] = o;  // original id of the query (row of the CSR)
+                if (EMIT) {
+                    S.rowb[tid] = row_ptr[o];
+                    S.rowe[tid] = row_ptr[o + 1];
+                }
+            }
+        }
+        if (tid == 0) S.gn = 0;
+        int cnt0 = 0, cnt1 = 0;
+        if (nkc == 1) load_rows(S.Qs, tv.pts, dp, nullptr, qfirst, nqr, 0, kq);
+
+        // decides the queued guard-band pairs; `all` drains everything, else
+        // whole warps' worth and keeps the rest
+        auto drain = [&](bool all) {
+            __syncthreads();
+            const int n = S.gn;
+            const int m = all ? n : (n & ~31);
+            for (int i = tid; i < m; i += LEAF_T) {
+                const int q = S.gq[i], ppos = S.gpos[i], li = S.gb[i];
+                if (!EMIT) ++guard;
+                double s64 = sq_l2_exact(tv.pts + (size_t)(qfirst + q) * dp, tv.pts + (size_t)ppos * dp, dim);
+                if (s64 <= qp.eps2_64) {
+                    if (!EMIT) {
+                        atomicAdd(&S.qcnt[q], 1);
+                        atomicOr(&S.bem[li], 1u << q);
+                    } else {
+                        int slot = atomicAdd(&rowcur[S.cursor[q]], 1);
+                        int64_t at = S.rowb[q] + slot;
+                        if (at < S.rowe[q]) {
+                            col[at] = tv.perm[ppos];
+                            dist[at] = (float)sqrt(s64);
+                        } else {
+                            atomicOr(err, 4);
                         }
-#pragma unroll
-                        for (int i = 0; i < 2; ++i)
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) tot[i][j] += acc[i][j];
                     }
                 }
-                unsigned hit = 0u;
+            }
+            __syncthreads();
+            const int rest = n - m;
+            int rp = 0, rq = 0, rb = 0;
+            if (tid < rest) {
+                rp = S.gpos[m + tid];
+                rq = S.gq[m + tid];
+                rb = S.gb[m + tid];
+            }
+            __syncthreads();
+            if (tid < rest) {
+                S.gpos[tid] = rp;
+                S.gq[tid] = (uint8_t)rq;
+                S.gb[tid] = (uint8_t)rb;
+            }
+            if (tid == 0) S.gn = rest;
+            __syncthreads();
+        };
+
+        // issues the cp.async copies of tile t (rows rowsrc[32t ..]) into buffer buf
+        auto issue = [&](int t, int buf, const int *rowsrc, int nrows) {
+            if (nkc != 1) return;
+            const int r0 = 32 * t;
+            const int rows = min(32, nrows - r0);
+            float4 *dst = S.Ps[buf];
+            for (int i = tid; i < 32 * kq; i += LEAF_T) {
+                const int r = i / kq, k = i - r * kq;
+                const bool valid = r < rows;
+                const int pos = valid ? rowsrc[r0 + r] : qfirst;
+                cp_async16(dst + r * KS4 + k, tv.pts + (size_t)pos * dp + 4 * k, valid);
+            }
+            cp_async_commit();
+        };
+        auto compute = [&](int t, int buf, const int *rowsrc, int nrows, float (&tot)[2][4]) {
+            if (nkc == 1) {
+                tile_sqdist_smem(S.Qs, S.Ps[buf], kq, tot);
+            } else {
+                const int r0 = 32 * t;
+                tile_sqdist(tv, S.Qs, S.Ps[0], rowsrc + r0, min(32, nrows - r0), qfirst, nqr, nkc, tot);
+            }
+        };
+
+        int64_t ci = c0;
+        while (ci < c1) {
+            // ---- batch of candidate blocks
+            int bn;
+            if (EMIT) {
+                __syncthreads();
+                if (tid == 0) S.nb_fill = 0;
+                __syncthreads();
+                for (;;) {
+                    const int nf = S.nb_fill;
+                    if (nf >= NB || ci >= c1) break;
+                    const int64_t idx = ci + tid;
+                    const uint32_t m = idx < c1 ? emask[idx] : 0u;
+                    const bool f = m != 0u;
+                    const unsigned bal = __ballot_sync(0xffffffffu, f);
+                    if (lane == 0) S.scan_tmp[warp] = __popc(bal);
+                    __syncthreads();
+                    int off = 0, tot = 0;
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int q = qi + 16 * i;
+                    for (int w = 0; w < LEAF_T / 32; ++w) {
+                        if (w < warp) off += S.scan_tmp[w];
+                        tot += S.scan_tmp[w];
+                    }
+                    const int rank = off + __popc(bal & lanemask_lt());
+                    const int room = NB - nf;
+                    if (f && rank < room) {
+                        S.bci[nf + rank] = idx;
+                        S.bmask[nf + rank] = m;
+                    }
+                    if (f && rank == room) S.next_ci = idx;
+                    __syncthreads();
+                    if (tot <= room) ci = ci + LEAF_T < c1 ? ci + LEAF_T : c1;
+                    else ci = S.next_ci;
+                    if (tid == 0) S.nb_fill = nf + (tot < room ? tot : room);
+                    __syncthreads();
+                }
+                bn = S.nb_fill;
+                if (bn == 0) break;
+            } else {
+                bn = (int)((c1 - ci) < NB ? (c1 - ci) : NB);
+                if (tid < NB) S.bci[tid] = ci + tid;
+                ci += bn;
+            }
+            __syncthreads();
+            for (int i = tid; i < bn; i += LEAF_T) {
+                const int v = (int)cand[S.bci[i]];
+                S.bbeg[i] = tv.node_begin[v];
+                S.bcnt[i] = tv.node_count[v];
+                S.brad[i] = tv.radius[v];
+                if (!EMIT) S.bmask[i] = 0u;
+                S.bem[i] = 0u;
+            }
+            __syncthreads();
+
+            // ---- stage 1 (count pass): per-query test against the block centres
+            if (!EMIT) {
+                const int nt = (bn + 31) >> 5;
+                issue(0, 0, S.bbeg, bn);
+                for (int t = 0; t < nt; ++t) {
+                    if (t + 1 < nt) {
+                        issue(t + 1, (t + 1) & 1, S.bbeg, bn);
+                        cp_async_wait<1>();
+                    } else {
+                        cp_async_wait<0>();
+                    }
+                    __syncthreads();
+                    float tot[2][4];
+                    compute(t, t & 1, S.bbeg, bn, tot);
+                    const int rows = min(32, bn - 32 * t);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const int p = pj + 8 * j;
-                        if (q >= nqr || p >= npr) continue;
-                        const int qpos = qb + q0 + q, ppos = tpos[p];
-                        if (qpos == ppos && !qp.include_self) continue;
-                        if (!EMIT) ++pairs;
-                        float dv = 0.f;
-                        unsigned gcount = 0;
-                        int e = decide_l2(qp, tot[i][j], tv.pts + (size_t)qpos * dp, tv.pts + (size_t)ppos * dp,
-                                          dim, fp32_dist_ok, &dv, gcount);
-                        if (!EMIT) guard += gcount;
-                        if (!e) continue;
-                        if (!EMIT) {
-                            hit |= 1u << p;
-                            if (i == 0) ++cnt0; else ++cnt1;
-                        } else {
-                            int slot = atomicAdd(&cursor[q], 1);
-                            int64_t at = rowb[q] + slot;
-                            if (at < rowe[q]) {
-                                col[at] = tv.perm[ppos];
-                                dist[at] = dv;
+                        if (p >= rows) continue;
+                        const int li = 32 * t + p;
+                        const float bound = fmaf(S.brad[li] + qp.eps_up, PRUNE_REL, PRUNE_ABS);
+                        uint32_t m = 0u;
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const int q = qi + 16 * i;
+                            if (q >= nqr) continue;
+                            ++s1evals;
+                            if (!(sqrtf(tot[i][j]) > bound)) m |= 1u << q;
+                        }
+                        if (m) atomicOr(&S.bmask[li], m);
+                    }
+                    __syncthreads();
+                }
+            }
+
+            // ---- prefix of the surviving blocks' point counts (warp 0)
+            if (warp == 0) {
+                int loc[4], sum = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int i = 4 * lane + k;
+                    loc[k] = (i < bn && S.bmask[i] != 0u) ? S.bcnt[i] : 0;
+                    sum += loc[k];
+                }
+                int incl = sum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                int run = incl - sum;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    S.bpre[4 * lane + k] = run;
+                    run += loc[k];
+                }
+                if (lane == 31) S.bpre[NB] = incl;
+            }
+            __syncthreads();
+            const int T = S.bpre[NB];
+
+            // ---- stage 2: packed points of the surviving blocks
+            for (int R0 = 0; R0 < T; R0 += RCAP) {
+                const int RN = min(RCAP, T - R0);
+                __syncthreads();
+                for (int r = tid; r < RN; r += LEAF_T) {
+                    const int R = R0 + r;
+                    int lo = 0, hi = NB;  // last li with bpre[li] <= R (and a non-empty block)
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (S.bpre[mid] <= R) lo = mid; else hi = mid;
+                    }
+                    S.rpos[r] = S.bbeg[lo] + (R - S.bpre[lo]);
+                    S.rli[r] = (uint8_t)lo;
+                }
+                __syncthreads();
+                const int nt = (RN + 31) >> 5;
+                issue(0, 0, S.rpos, RN);
+                for (int t = 0; t < nt; ++t) {
+                    if (t + 1 < nt) {
+                        issue(t + 1, (t + 1) & 1, S.rpos, RN);
+                        cp_async_wait<1>();
+                    } else {
+                        cp_async_wait<0>();
+                    }
+                    __syncthreads();
+                    float tot[2][4];
+                    compute(t, t & 1, S.rpos, RN, tot);
+                    const int npr = min(32, RN - 32 * t);
+                    uint32_t hitrow = 0u;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int p = pj + 8 * j;
+                        if (p >= npr) continue;
+                        const int r = 32 * t + p;
+                        const int li = S.rli[r];
+                        const uint32_t mask = S.bmask[li];
+                        const int ppos = S.rpos[r];
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const int q = qi + 16 * i;
+                            if (q >= nqr || !((mask >> q) & 1u)) continue;
+                            const int qpos = qfirst + q;
+                            if (qpos == ppos && !qp.include_self) continue;
+                            if (!EMIT) ++pairs;
+                            const float sv = tot[i][j];
+                            int edge;
+                            if (qp.mode == 0) {
+                                if (sv < qp.lo2) edge = 1;
+                                else if (sv > qp.hi2) edge = 0;
+                                else edge = -1;
+                            } else if (qp.mode == 1) {
+                                edge = sv == 0.0f;
+                            } else if (qp.mode == 3) {
+                                edge = 1;
                             } else {
-                                atomicOr(err, 4);
+                                edge = -1;
+                            }
+                            if (edge < 0) {  // guard band: queue for the FP64 decision
+                                const int slot = atomicAdd(&S.gn, 1);
+                                S.gpos[slot] = ppos;
+                                S.gq[slot] = (uint8_t)q;
+                                S.gb[slot] = (uint8_t)li;
+                                continue;
+                            }
+                            if (!edge) continue;
+                            if (!EMIT) {
+                                if (i == 0) ++cnt0; else ++cnt1;
+                                hitrow |= 1u << (4 * j + i);
+                            } else {
+                                const int slot = atomicAdd(&rowcur[S.cursor[q]], 1);
+                                const int64_t at = S.rowb[q] + slot;
+                                if (at < S.rowe[q]) {
+                                    col[at] = tv.perm[ppos];
+                                    dist[at] = fp32_dist_ok ? sqrtf(sv)
+                                                            : (float)sqrt(sq_l2_exact(tv.pts + (size_t)qpos * dp,
+                                                                                      tv.pts + (size_t)ppos * dp, dim));
+                                } else {
+                                    atomicOr(err, 4);
+                                }
                             }
                         }
                     }
-                }
-                if (!EMIT) {
-                    if (hit) atomicOr(&s_hit, hit);
+                    if (!EMIT && hitrow) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint32_t qm = (hitrow >> (4 * j)) & 3u;
+                            if (!qm) continue;
+                            uint32_t bits = 0u;
+                            if (qm & 1u) bits |= 1u << qi;
+                            if (qm & 2u) bits |= 1u << (qi + 16);
+                            atomicOr(&S.bem[S.rli[32 * t + pj + 8 * j]], bits);
+                        }
+                    }
                     __syncthreads();
-                    if (tid < npr && ((s_hit >> tid) & 1u)) atomicOr(&cand[tcand[tid]], FLAG);
-                    __syncthreads();
-                    if (tid == 0) s_hit = 0u;
+                    if (S.gn >= 64) drain(false);
                 }
             }
-            if (last) break;
+            drain(true);
+            // count pass: queries that found an edge in each block (all queries
+            // for a group above 32 points), read by the emit pass
+            if (!EMIT && emask) {
+                for (int i = tid; i < bn; i += LEAF_T) emask[S.bci[i]] = qn <= 32 ? S.bem[i] : ~0u;
+            }
         }
         if (!EMIT) {
             for (int o = 1; o < 8; o <<= 1) {
                 cnt0 += __shfl_xor_sync(0xffffffffu, cnt0, o);
                 cnt1 += __shfl_xor_sync(0xffffffffu, cnt1, o);
             }
-            if (pj == 0) {
-                if (qi < nqr) deg[tv.perm[qb + q0 + qi]] = cnt0;
-                if (qi + 16 < nqr) deg[tv.perm[qb + q0 + qi + 16]] = cnt1;
-            }
-        } else {
             __syncthreads();
-            if (tid < nqr && rowb[tid] + cursor[tid] != rowe[tid]) atomicOr(err, 8);
+            if (pj == 0) {
+                if (qi < nqr && cnt0 + S.qcnt[qi]) atomicAdd(&deg[S.cursor[qi]], cnt0 + S.qcnt[qi]);
+                if (qi + 16 < nqr && cnt1 + S.qcnt[qi + 16])
+                    atomicAdd(&deg[S.cursor[qi + 16]], cnt1 + S.qcnt[qi + 16]);
+            }
         }
     }
     if (!EMIT) {
         for (int o = 16; o > 0; o >>= 1) {
             pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+            s1evals += __shfl_xor_sync(0xffffffffu, s1evals, o);
             guard += __shfl_xor_sync(0xffffffffu, guard, o);
         }
         if ((tid & 31) == 0) {
             stat_add(st, ST_PAIRS, pairs);
+            stat_add(st, ST_TRAV, s1evals);
             stat_add(st, ST_GUARD, guard);
         }
     }
+}
+
+// Work items of every group: ceil(candidates / kItem) slices.
+__global__ void k_item_counts(int G, const int32_t *__restrict__ ccnt, int32_t *__restrict__ icnt) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < G) icnt[g] = (ccnt[g] + kItem - 1) / kItem;
+}
+__global__ void k_item_fill(int G, const int64_t *__restrict__ coff, const int64_t *__restrict__ ioff,
+                            int32_t *__restrict__ ig, int64_t *__restrict__ ib, int64_t *__restrict__ ie,
+                            int32_t *__restrict__ nitems) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g == 0) *nitems = (int32_t)ioff[G];
+    if (g >= G) return;
+    const int64_t a = coff[g], b = coff[g + 1];
+    int64_t k = ioff[g];
+    for (int64_t c = a; c < b; c += kItem, ++k) {
+        ig[k] = g;
+        ib[k] = c;
+        ie[k] = c + kItem < b ? c + kItem : b;
+    }
+}
+// Every row received exactly its counted number of entries.
+__global__ void k_check_rows(int64_t n, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ rowcur,
+                             int32_t *__restrict__ err) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && row_ptr[i] + rowcur[i] != row_ptr[i + 1]) atomicOr(err, 8);
+}
+
+// Dynamic shared memory of the L2 leaf kernel (set once per process).
+void leaf_l2_prepare() {
+    static bool done = false;
+    if (done) return;
+    CT_CHECK_CUDA(cudaFuncSetAttribute(k_leaf_l2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafSmem));
+    CT_CHECK_CUDA(cudaFuncSetAttribute(k_leaf_l2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafSmem));
+    done = true;
 }
 
 // Edit distance of one (pattern, text) pair over alphabet-mapped symbols;
@@ -908,18 +1328,20 @@ void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &
         CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
         CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
     }
+    DBuf<int32_t> next_group(1, s);
     auto traverse = [&](bool fill, uint32_t *cand) {
+        CT_CHECK_CUDA(cudaMemsetAsync(next_group.p, 0, sizeof(int32_t), s));
         if (l2) {
             if (fill)
-                k_traverse_l2<true><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err);
+                k_traverse_l2<true><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err, next_group.p);
             else
-                k_traverse_l2<false><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err);
+                k_traverse_l2<false><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err, next_group.p);
         } else {
             switch (W) {
 #define CT_TL(WW)                                                                                           \
     case WW:                                                                                                \
-        if (fill) k_traverse_lev<true, WW><<<blocks, 32, 0, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err); \
-        else k_traverse_lev<false, WW><<<blocks, 32, 0, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err);    \
+        if (fill) k_traverse_lev<true, WW><<<blocks, 32, 0, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err, next_group.p); \
+        else k_traverse_lev<false, WW><<<blocks, 32, 0, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err, next_group.p);    \
         break;
                 CT_TL(1) CT_TL(2) CT_TL(4) CT_TL(8) CT_TL(16)
 #undef CT_TL
@@ -936,6 +1358,21 @@ void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &
     int64_t n_cand = 0;
     to_host(&n_cand, coff.p + G, 1, s);
     DBuf<uint32_t> cand(n_cand ? n_cand : 1, s);
+    DBuf<uint32_t> emask(l2 ? (n_cand ? n_cand : 1) : 0, s);
+    // work items of the L2 leaf stage
+    const int64_t max_items = G + n_cand / kItem + 1;
+    DBuf<int32_t> icnt(l2 ? G + 1 : 0, s), igroup(l2 ? max_items : 0, s), nitems(1, s);
+    DBuf<int64_t> ioff(l2 ? G + 1 : 0, s), ibeg(l2 ? max_items : 0, s), iend(l2 ? max_items : 0, s);
+    Items items{igroup.p, ibeg.p, iend.p, nitems.p};
+    if (l2 && G) {
+        k_item_counts<<<grid_for(G, 256), 256, 0, s>>>(G, ccnt.p, icnt.p);
+        CT_COUNT_LAUNCH();
+        exclusive_scan_i32_to_i64(icnt.p, ioff.p, G, ioff.p + G, s);
+        k_item_fill<<<grid_for(G, 256), 256, 0, s>>>(G, coff.p, ioff.p, igroup.p, ibeg.p, iend.p, nitems.p);
+        CT_COUNT_LAUNCH();
+        CT_LAUNCH_CHECK();
+    }
+    DBuf<int32_t> rowcur(l2 ? n + 1 : 0, s);
     {
         ProfScope ps("traverse_fill", s);
         traverse(true, cand.p);
@@ -977,10 +1414,11 @@ void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &
     auto leaf = [&](bool emit, int64_t *row_ptr, int32_t *col, float *dist) {
         if (G == 0) return;
         if (l2) {
+            leaf_l2_prepare();
             if (emit)
-                k_leaf_l2<true><<<G, LEAF_T, 0, s>>>(tv, qp, coff.p, cand.p, deg.p, row_ptr, col, dist, st.p, err);
+                k_leaf_l2<true><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand.p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err);
             else
-                k_leaf_l2<false><<<G, LEAF_T, 0, s>>>(tv, qp, coff.p, cand.p, deg.p, row_ptr, col, dist, st.p, err);
+                k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand.p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err);
         } else {
             switch (W) {
 #define CT_LL(WW)                                                                                                      \
@@ -1015,7 +1453,12 @@ void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &
     out.dist = (float *)dmalloc((size_t)(nnz ? nnz : 1) * sizeof(float), s);
     if (nnz) {
         ProfScope ps("leaf_emit", s);
+        if (l2) CT_CHECK_CUDA(cudaMemsetAsync(rowcur.p, 0, (n + 1) * sizeof(int32_t), s));
         leaf(true, row_ptr, out.col, out.dist);
+        if (l2) {
+            k_check_rows<<<grid_for(n, 256), 256, 0, s>>>(n, row_ptr, rowcur.p, err);
+            CT_COUNT_LAUNCH();
+        }
     }
     {
         ProfScope ps("row_sort", s);
@@ -1082,16 +1525,21 @@ void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cuda
     unsigned char *base = noalloc_scratch();
     const size_t cap_bytes = CT_NOALLOC_SCRATCH_BYTES;
     const int cap = 32 * (t->depth + 2);
-    // fixed part: counters, per-group counts and offsets, scan tile sums
+    // fixed part: counters, per-group counts and offsets, scan tile sums, work-item counts
     size_t off = 0;
-    unsigned long long *st = (unsigned long long *)(base + off);
-    off = align256(off + ST_N * sizeof(unsigned long long));
-    int32_t *ccnt = (int32_t *)(base + off);
-    off = align256(off + (size_t)(G + 1) * sizeof(int32_t));
-    int64_t *coff = (int64_t *)(base + off);
-    off = align256(off + (size_t)(G + 1) * sizeof(int64_t));
-    int64_t *sums = (int64_t *)(base + off);
-    off = align256(off + (size_t)std::max<int64_t>(scan_scratch_entries(G), 1) * sizeof(int64_t));
+    auto take = [&](size_t bytes) {
+        unsigned char *p = base + off;
+        off = align256(off + bytes);
+        return p;
+    };
+    unsigned long long *st = (unsigned long long *)take(ST_N * sizeof(unsigned long long));
+    int32_t *next_group = (int32_t *)take(sizeof(int32_t));
+    int32_t *nitems = (int32_t *)take(sizeof(int32_t));
+    int32_t *ccnt = (int32_t *)take((size_t)(G + 1) * sizeof(int32_t));
+    int64_t *coff = (int64_t *)take((size_t)(G + 1) * sizeof(int64_t));
+    int32_t *icnt = (int32_t *)take((size_t)(G + 1) * sizeof(int32_t));
+    int64_t *ioff = (int64_t *)take((size_t)(G + 1) * sizeof(int64_t));
+    int64_t *sums = (int64_t *)take((size_t)std::max<int64_t>(scan_scratch_entries(G), 1) * sizeof(int64_t));
     const size_t stack_per_block = (size_t)TRAV_WARPS * cap * sizeof(int2);
     if (off + stack_per_block > cap_bytes)
         CT_FAIL(CT_EUNSUPPORTED, "tree with %d query groups and depth %d needs more than the fixed %zu-byte scratch",
@@ -1101,11 +1549,9 @@ void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cuda
     int64_t want = std::min<int64_t>(ceil_div(G, TRAV_WARPS), (int64_t)num_sms() * 8);
     int64_t fit = (int64_t)std::max<size_t>(1, (cap_bytes / 4) / stack_per_block);
     const int blocks = (int)std::max<int64_t>(1, std::min(want, fit));
-    int2 *stacks = (int2 *)(base + off);
-    off = align256(off + (size_t)blocks * stack_per_block);
-    uint32_t *cand = (uint32_t *)(base + off);
+    int2 *stacks = (int2 *)take((size_t)blocks * stack_per_block);
     if (off >= cap_bytes) CT_FAIL(CT_EUNSUPPORTED, "problem too large for the fixed scratch");
-    const int64_t cand_cap = (int64_t)((cap_bytes - off) / sizeof(uint32_t));
+    const size_t room = cap_bytes - off;  // candidates and work items share the rest
 
     TreeView tv = view_of(t);
     int32_t *err = reinterpret_cast<int32_t *>(st + ST_ERR);
@@ -1114,22 +1560,42 @@ void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cuda
         CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
         CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
     }
-    // the array keeps the previous call's contents: clear the counters
+    // the array keeps the previous call's contents: clear what must start at zero
     CT_CHECK_CUDA(cudaMemsetAsync(st, 0, ST_N * sizeof(unsigned long long), s));
-    k_traverse_l2<false><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt, coff, nullptr, stacks, cap, st, err);
+    CT_CHECK_CUDA(cudaMemsetAsync(next_group, 0, sizeof(int32_t), s));
+    k_traverse_l2<false><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt, coff, nullptr, stacks, cap, st, err,
+                                                              next_group);
     CT_COUNT_LAUNCH();
     CT_LAUNCH_CHECK();
     exclusive_scan_i32_to_i64_into(ccnt, coff, G, coff + G, sums, s);
     int64_t total = 0;
     CT_CHECK_CUDA(cudaMemcpyAsync(&total, coff + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CT_CHECK_CUDA(cudaStreamSynchronize(s));
-    if (total > cand_cap)
-        CT_FAIL(CT_EUNSUPPORTED, "%lld candidate blocks exceed the fixed scratch (room for %lld); use eps_graph_query",
-                (long long)total, (long long)cand_cap);
-    k_traverse_l2<true><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt, coff, cand, stacks, cap, st, err);
+    const int64_t max_items = G + total / kItem + 1;
+    const size_t need = align256((size_t)total * sizeof(uint32_t)) + align256((size_t)max_items * sizeof(int32_t)) +
+                        2 * align256((size_t)max_items * sizeof(int64_t));
+    if (need > room)
+        CT_FAIL(CT_EUNSUPPORTED, "%lld candidate blocks need %zu bytes of the fixed scratch (room for %zu); use eps_graph_query",
+                (long long)total, need, room);
+    uint32_t *cand = (uint32_t *)take((size_t)total * sizeof(uint32_t));
+    int32_t *igroup = (int32_t *)take((size_t)max_items * sizeof(int32_t));
+    int64_t *ibeg = (int64_t *)take((size_t)max_items * sizeof(int64_t));
+    int64_t *iend = (int64_t *)take((size_t)max_items * sizeof(int64_t));
+    CT_CHECK_CUDA(cudaMemsetAsync(next_group, 0, sizeof(int32_t), s));
+    k_traverse_l2<true><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt, coff, cand, stacks, cap, st, err,
+                                                             next_group);
     CT_COUNT_LAUNCH();
+    CT_CHECK_CUDA(cudaMemsetAsync(degrees, 0, (size_t)n * sizeof(int32_t), s));
     if (G) {
-        k_leaf_l2<false><<<G, LEAF_T, 0, s>>>(tv, qp, coff, cand, degrees, nullptr, nullptr, nullptr, st, err);
+        k_item_counts<<<grid_for(G, 256), 256, 0, s>>>(G, ccnt, icnt);
+        CT_COUNT_LAUNCH();
+        exclusive_scan_i32_to_i64_into(icnt, ioff, G, ioff + G, sums, s);
+        k_item_fill<<<grid_for(G, 256), 256, 0, s>>>(G, coff, ioff, igroup, ibeg, iend, nitems);
+        CT_COUNT_LAUNCH();
+        Items items{igroup, ibeg, iend, nitems};
+        leaf_l2_prepare();
+        k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand, nullptr, degrees, nullptr,
+                                                                          nullptr, nullptr, nullptr, st, err);
         CT_COUNT_LAUNCH();
     }
     CT_LAUNCH_CHECK();
