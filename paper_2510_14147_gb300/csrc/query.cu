@@ -55,27 +55,6 @@ __device__ __noinline__ double sq_l2_exact(const float *__restrict__ x, const fl
     return s;
 }
 
-// Lane-per-vertex fp32 squared distance from a centre in shared memory.
-__device__ __forceinline__ float lane_sqdist(const float4 *__restrict__ c, const float4 *__restrict__ v,
-                                             int nq) {
-    float a0 = 0.f, a1 = 0.f;
-    int k = 0;
-    for (; k + 1 < nq; k += 2) {
-        float4 x = c[k], y = __ldg(v + k);
-        float4 x2 = c[k + 1], y2 = __ldg(v + k + 1);
-        float dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z, dw = x.w - y.w;
-        a0 = fmaf(dx, dx, a0); a0 = fmaf(dy, dy, a0); a0 = fmaf(dz, dz, a0); a0 = fmaf(dw, dw, a0);
-        dx = x2.x - y2.x; dy = x2.y - y2.y; dz = x2.z - y2.z; dw = x2.w - y2.w;
-        a1 = fmaf(dx, dx, a1); a1 = fmaf(dy, dy, a1); a1 = fmaf(dz, dz, a1); a1 = fmaf(dw, dw, a1);
-    }
-    if (k < nq) {
-        float4 x = c[k], y = __ldg(v + k);
-        float dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z, dw = x.w - y.w;
-        a0 = fmaf(dx, dx, a0); a0 = fmaf(dy, dy, a0); a0 = fmaf(dz, dz, a0); a0 = fmaf(dw, dw, a0);
-    }
-    return a0 + a1;
-}
-
 struct TreeView {
     const float *pts, *node_ctr, *radius, *dcen, *group_radius;
     const int32_t *perm, *node_begin, *node_count, *child_begin, *child_count, *leaf_ids;
@@ -97,82 +76,184 @@ TreeView view_of(const ct_tree *t) {
 }
 
 // ------------------------------------------------------------ traversal
+//
+// One pass: every warp appends the candidate leaf blocks of its groups to
+// private chunks of a shared pool; a group's candidates form one or more
+// segments (group, pool offset, count).  If the pool runs out, the host reruns
+// the pass with the exact size.
 
-// Shared DFS machinery: pops up to 32 vertices from the top range; `test`
-// decides a vertex (lane-parallel); survivors are compacted by ballots.
-template <bool FILL, class Test>
-__device__ __forceinline__ int64_t walk_group(const TreeView &tv, int2 *__restrict__ stack, int cap,
-                                              int64_t out_base, int out_cap, uint32_t *__restrict__ cand,
-                                              int &n_cand, unsigned long long &evals,
-                                              int32_t *__restrict__ err, Test test) {
+constexpr int POOL_CHUNK = 2048;
+
+struct Pool {
+    uint32_t *data;
+    int64_t cap;
+    unsigned long long *next;  // chunk allocator
+    int32_t *seg_group, *seg_count;
+    int64_t *seg_begin;
+    int32_t *nseg;
+    int64_t seg_cap;
+    unsigned long long *total;  // candidates of all groups
+    int32_t *overflow;
+};
+
+// Warp-uniform write cursor: current chunk, its fill, the open segment.
+struct PoolCursor {
+    int64_t cur;
+    int fill;
+    int64_t seg_begin;
+    int seg_count;
+};
+
+__device__ __forceinline__ void pool_close(const Pool &P, int g, PoolCursor &pc) {
+    if (pc.seg_count > 0 && (threadIdx.x & 31) == 0) {
+        int idx = atomicAdd(P.nseg, 1);
+        if (idx < P.seg_cap) {
+            P.seg_group[idx] = g;
+            P.seg_begin[idx] = pc.seg_begin;
+            P.seg_count[idx] = pc.seg_count;
+        } else {
+            atomicOr(P.overflow, 1);
+        }
+    }
+    pc.seg_count = 0;
+}
+
+// Appends the values of the lanes with `flag` set, in lane order.
+__device__ __forceinline__ void pool_append(const Pool &P, int g, PoolCursor &pc, bool flag, uint32_t v) {
     const int lane = threadIdx.x & 31;
-    n_cand = 0;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    const int n = __popc(m);
+    if (!n) return;
+    const int rank = __popc(m & lanemask_lt());
+    const int room = pc.cur >= 0 ? POOL_CHUNK - pc.fill : 0;
+    if (n <= room) {
+        if (flag) P.data[pc.cur + pc.fill + rank] = v;
+        pc.fill += n;
+        pc.seg_count += n;
+        return;
+    }
+    if (flag && rank < room) P.data[pc.cur + pc.fill + rank] = v;
+    pc.seg_count += room;
+    pool_close(P, g, pc);
+    unsigned long long c = 0ull;
+    if (lane == 0) c = atomicAdd(P.next, (unsigned long long)POOL_CHUNK);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if ((int64_t)c + POOL_CHUNK > P.cap) {  // out of pool: keep counting, write nothing
+        if (lane == 0) atomicOr(P.overflow, 1);
+        pc.cur = -1;
+        pc.fill = POOL_CHUNK;
+        pc.seg_begin = 0;
+        pc.seg_count = 0;
+        return;
+    }
+    pc.cur = (int64_t)c;
+    pc.fill = n - room;
+    pc.seg_begin = pc.cur;
+    pc.seg_count = n - room;
+    if (flag && rank >= room) P.data[pc.cur + rank - room] = v;
+}
+
+// DFS over ranges of sibling vertices: up to 32 vertices are tested per step,
+// vertex i of the step by lane i (`tester(first, take)` returns the lane's
+// keep flag); survivors are compacted with ballots -- leaf blocks are
+// appended to the pool, internal vertices push their child range.
+template <class Tester>
+__device__ __forceinline__ int walk_group(const TreeView &tv, int2 *__restrict__ stack, int cap, int g,
+                                          const Pool &P, PoolCursor &pc, unsigned long long &evals,
+                                          int32_t *__restrict__ err, Tester tester) {
+    const int lane = threadIdx.x & 31;
+    int n_cand = 0;
+    pc.seg_begin = pc.cur + pc.fill;
+    pc.seg_count = 0;
     if (tv.child_count[0] == 0) {  // the root is a leaf block: it is the only candidate
-        if (FILL && out_cap < 1) {
-            if (lane == 0) atomicOr(err, 16);
-            return -1;
-        }
-        if (FILL && lane == 0) cand[out_base] = 0u;
+        pool_append(P, g, pc, lane == 0, 0u);
         n_cand = 1;
-        return 0;
-    }
-    int top = 0;
-    if (lane == 0) stack[0] = make_int2(tv.child_begin[0], tv.child_count[0]);
-    top = 1;
-    __syncwarp();
-    while (top > 0) {
-        int2 r = stack[top - 1];
-        int take = r.y < 32 ? r.y : 32;
+    } else {
+        int top = 0;
+        if (lane == 0) stack[0] = make_int2(tv.child_begin[0], tv.child_count[0]);
+        top = 1;
         __syncwarp();
-        if (lane == 0) {
-            if (r.y > take) stack[top - 1] = make_int2(r.x + take, r.y - take);
+        while (top > 0) {
+            int2 r = stack[top - 1];
+            int take = r.y < 32 ? r.y : 32;
+            __syncwarp();
+            if (lane == 0) {
+                if (r.y > take) stack[top - 1] = make_int2(r.x + take, r.y - take);
+            }
+            if (r.y <= take) --top;
+            if (lane < take) ++evals;
+            const bool keep = tester(r.x, take);
+            const int v = r.x + lane;
+            const bool leaf = keep && tv.child_count[v] == 0;
+            pool_append(P, g, pc, keep && leaf, (uint32_t)v);
+            n_cand += __popc(__ballot_sync(0xffffffffu, keep && leaf));
+            const unsigned mi = __ballot_sync(0xffffffffu, keep && !leaf);
+            const int np = __popc(mi);
+            if (top + np > cap) {  // cannot happen for a stack of 32 * (depth + 2) ranges
+                if (lane == 0) atomicOr(err, 2);
+                return -1;
+            }
+            if (keep && !leaf) {
+                // reverse lane order so the lowest lane's children are on top (DFS order)
+                int slot = top + __popc(mi & ~lanemask_lt() & ~(1u << lane));
+                stack[slot] = make_int2(tv.child_begin[v], tv.child_count[v]);
+            }
+            top += np;
+            __syncwarp();
         }
-        if (r.y <= take) --top;
-        if (lane < take) ++evals;
-        bool keep = false, leaf = false;
-        int v = r.x + lane;
-        if (lane < take) {
-            keep = test(v);
-            leaf = tv.child_count[v] == 0;
-        }
-        unsigned ml = __ballot_sync(0xffffffffu, keep && leaf);
-        unsigned mi = __ballot_sync(0xffffffffu, keep && !leaf);
-        if (FILL && n_cand + __popc(ml) > out_cap) {  // the fill walk must repeat the count walk
-            if (lane == 0) atomicOr(err, 16);
-            return -1;
-        }
-        if (FILL && keep && leaf) cand[out_base + n_cand + __popc(ml & lanemask_lt())] = (uint32_t)v;
-        n_cand += __popc(ml);
-        int np = __popc(mi);
-        if (top + np > cap) {  // cannot happen for a stack of 32 * (depth + 2) ranges
-            if (lane == 0) atomicOr(err, 2);
-            return -1;
-        }
-        if (keep && !leaf) {
-            // reverse lane order so the lowest lane's children are on top (DFS order)
-            int slot = top + __popc(mi & ~lanemask_lt() & ~(1u << lane));
-            stack[slot] = make_int2(tv.child_begin[v], tv.child_count[v]);
-        }
-        top += np;
-        __syncwarp();
     }
+    pool_close(P, g, pc);
+    if (lane == 0) atomicAdd(P.total, (unsigned long long)n_cand);
     return 0;
 }
 
-template <bool FILL>
+// L2 test of `take` consecutive vertices against the group centre (shared
+// memory): TPD lanes share one vertex and read its centre row in coalesced
+// 16-byte pieces; the partial sums are reduced by shuffles and lane i gets
+// vertex i's squared distance.  Keep v unless d > (r(v) + eps + r_g)(1 + 2^-10).
+template <int TPD>
+__device__ __forceinline__ bool l2_keep(const TreeView &tv, const float4 *cen, int nq4, int first, int take,
+                                        float add) {
+    constexpr int NPR = 32 / TPD;
+    const int lane = threadIdx.x & 31, sub = lane / TPD, j = lane % TPD;
+    float mine = 0.f;
+    for (int r0 = 0; r0 < take; r0 += NPR) {
+        const int i = r0 + sub;
+        float acc = 0.f;
+        if (i < take) {
+            const float4 *row = reinterpret_cast<const float4 *>(tv.node_ctr) + (size_t)(first + i) * nq4;
+            for (int k = j; k < nq4; k += TPD) {
+                const float4 a = cen[k], b = __ldg(row + k);
+                const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
+                acc = fmaf(dx, dx, acc);
+                acc = fmaf(dy, dy, acc);
+                acc = fmaf(dz, dz, acc);
+                acc = fmaf(dw, dw, acc);
+            }
+        }
+#pragma unroll
+        for (int o = TPD / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const int src = ((lane - r0) & (NPR - 1)) * TPD;
+        const float v = __shfl_sync(0xffffffffu, acc, src);
+        if (lane >= r0 && lane < r0 + NPR) mine = v;
+    }
+    if (lane >= take) return false;
+    const float bound = fmaf(tv.radius[first + lane] + add, PRUNE_REL, PRUNE_ABS);
+    return !(sqrtf(mine) > bound);
+}
+
+template <int TPD>
 __global__ void __launch_bounds__(TRAV_WARPS * 32) k_traverse_l2(
-    TreeView tv, QParams qp, int32_t *__restrict__ cand_cnt, const int64_t *__restrict__ cand_off,
-    uint32_t *__restrict__ cand, int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st,
+    TreeView tv, QParams qp, Pool P, int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st,
     int32_t *__restrict__ err, int32_t *__restrict__ next_group) {
     extern __shared__ float4 sc[];  // TRAV_WARPS x (dp/4)
-    const int nq = tv.dp >> 2;
+    const int nq4 = tv.dp >> 2;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4 *cen = sc + wib * nq;
+    float4 *cen = sc + wib * nq4;
     const int gw = blockIdx.x * TRAV_WARPS + wib;
-    const int nw = gridDim.x * TRAV_WARPS;
     int2 *stack = stacks + (int64_t)gw * cap;
     unsigned long long evals = 0;
-    (void)nw;
+    PoolCursor pc{-1, POOL_CHUNK, 0, 0};
     for (;;) {
         // groups are taken dynamically: their walks differ widely in length
         int g = 0;
@@ -180,40 +261,29 @@ __global__ void __launch_bounds__(TRAV_WARPS * 32) k_traverse_l2(
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= tv.n_groups) break;
         const float4 *crow = reinterpret_cast<const float4 *>(tv.pts + (size_t)tv.group_begin[g] * tv.dp);
-        for (int k = lane; k < nq; k += 32) cen[k] = crow[k];
+        for (int k = lane; k < nq4; k += 32) cen[k] = crow[k];
         __syncwarp();
         const float add = qp.eps_up + tv.group_radius[g];
-        int n_cand = 0;
-        auto test = [&](int v) {
-            float s = lane_sqdist(cen, reinterpret_cast<const float4 *>(tv.node_ctr + (size_t)v * tv.dp), nq);
-            float d = sqrtf(s);
-            float bound = fmaf(tv.radius[v] + add, PRUNE_REL, PRUNE_ABS);
-            return !(d > bound);
-        };
-        int64_t base = FILL ? cand_off[g] : 0;
-        int ocap = FILL ? cand_cnt[g] : 0;
-        if (walk_group<FILL>(tv, stack, cap, base, ocap, cand, n_cand, evals, err, test) < 0) return;
-        if (!FILL && lane == 0) cand_cnt[g] = n_cand;
+        auto tester = [&](int first, int take) { return l2_keep<TPD>(tv, cen, nq4, first, take, add); };
+        if (walk_group(tv, stack, cap, g, P, pc, evals, err, tester) < 0) return;
         __syncwarp();
     }
-    if (!FILL) {
-        for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
-        if (lane == 0) stat_add(st, ST_TRAV, evals);
-    }
+    for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
+    if (lane == 0) stat_add(st, ST_TRAV, evals);
 }
 
 // Edit distance: a vertex survives iff lev(c_g, v) <= r(v) + eps + r_g
 // (integers, exact).  One warp per block; the group centre's match masks are
 // in shared memory.
-template <bool FILL, int W>
+template <int W>
 __global__ void __launch_bounds__(32) k_traverse_lev(
-    TreeView tv, QParams qp, int32_t *__restrict__ cand_cnt, const int64_t *__restrict__ cand_off,
-    uint32_t *__restrict__ cand, int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st,
+    TreeView tv, QParams qp, Pool P, int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st,
     int32_t *__restrict__ err, int32_t *__restrict__ next_group) {
     __shared__ uint64_t peq[256 * W];
     const int lane = threadIdx.x;
     int2 *stack = stacks + (int64_t)blockIdx.x * cap;
     unsigned long long evals = 0;
+    PoolCursor pc{-1, POOL_CHUNK, 0, 0};
     for (;;) {
         int g = 0;
         if (lane == 0) g = atomicAdd(next_group, 1);
@@ -226,23 +296,19 @@ __global__ void __launch_bounds__(32) k_traverse_lev(
         lev_build_peq<W>(peq, pat, m);
         __syncwarp();
         const int add = qp.lev_k + (int)tv.group_radius[g];
-        int n_cand = 0;
-        auto test = [&](int v) {
-            int vp = tv.node_begin[v];
-            int k = add + (int)tv.radius[v];
+        auto tester = [&](int first, int take) {
+            if (lane >= take) return false;
+            const int v = first + lane;
+            const int vp = tv.node_begin[v];
+            const int k = add + (int)tv.radius[v];
             const uint8_t *txt = tv.sdata + tv.soff[vp];
-            int n = (int)(tv.soff[vp + 1] - tv.soff[vp]);
+            const int n = (int)(tv.soff[vp + 1] - tv.soff[vp]);
             return lev_myers<W>(peq, m, txt, n, k) <= k;
         };
-        int64_t base = FILL ? cand_off[g] : 0;
-        int ocap = FILL ? cand_cnt[g] : 0;
-        if (walk_group<FILL>(tv, stack, cap, base, ocap, cand, n_cand, evals, err, test) < 0) return;
-        if (!FILL && lane == 0) cand_cnt[g] = n_cand;
+        if (walk_group(tv, stack, cap, g, P, pc, evals, err, tester) < 0) return;
     }
-    if (!FILL) {
-        for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
-        if (lane == 0) stat_add(st, ST_TRAV, evals);
-    }
+    for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
+    if (lane == 0) stat_add(st, ST_TRAV, evals);
 }
 
 // ------------------------------------------------------------ leaf tiles
@@ -331,37 +397,6 @@ __device__ __forceinline__ void load_rows(float4 *__restrict__ tile, const float
         }
         tile[r * KS4 + k] = v;
     }
-}
-
-// Decides one pair; returns 1 for an edge and sets *dist.
-__device__ __forceinline__ int decide_l2(const QParams &qp, float s, const float *__restrict__ x,
-                                         const float *__restrict__ y, int dim, bool fp32_dist_ok,
-                                         float *dist, unsigned &guard) {
-    int edge = 0;
-    bool exact = false;
-    if (qp.mode == 0) {
-        if (s < qp.lo2) edge = 1;
-        else if (s > qp.hi2) edge = 0;
-        else exact = true;
-    } else if (qp.mode == 1) {
-        edge = s == 0.0f;
-    } else if (qp.mode == 3) {
-        edge = 1;
-    } else {
-        exact = true;
-    }
-    if (exact) {
-        ++guard;
-        double s64 = sq_l2_exact(x, y, dim);
-        edge = s64 <= qp.eps2_64;
-        if (edge) *dist = (float)sqrt(s64);
-        return edge;
-    }
-    if (edge) {
-        if (fp32_dist_ok) *dist = sqrtf(s);
-        else *dist = (float)sqrt(sq_l2_exact(x, y, dim));
-    }
-    return edge;
 }
 
 constexpr int NB = 128;       // candidate leaf blocks per batch
@@ -906,21 +941,22 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
     }
 }
 
-// Work items of every group: ceil(candidates / kItem) slices.
-__global__ void k_item_counts(int G, const int32_t *__restrict__ ccnt, int32_t *__restrict__ icnt) {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < G) icnt[g] = (ccnt[g] + kItem - 1) / kItem;
+// Work items: every pool segment split into slices of at most kItem blocks.
+__global__ void k_item_counts(int nseg, const int32_t *__restrict__ seg_count, int32_t *__restrict__ icnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nseg) icnt[i] = (seg_count[i] + kItem - 1) / kItem;
 }
-__global__ void k_item_fill(int G, const int64_t *__restrict__ coff, const int64_t *__restrict__ ioff,
+__global__ void k_item_fill(int nseg, const int32_t *__restrict__ seg_group, const int64_t *__restrict__ seg_begin,
+                            const int32_t *__restrict__ seg_count, const int64_t *__restrict__ ioff,
                             int32_t *__restrict__ ig, int64_t *__restrict__ ib, int64_t *__restrict__ ie,
                             int32_t *__restrict__ nitems) {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g == 0) *nitems = (int32_t)ioff[G];
-    if (g >= G) return;
-    const int64_t a = coff[g], b = coff[g + 1];
-    int64_t k = ioff[g];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *nitems = (int32_t)ioff[nseg];
+    if (i >= nseg) return;
+    const int64_t a = seg_begin[i], b = a + seg_count[i];
+    int64_t k = ioff[i];
     for (int64_t c = a; c < b; c += kItem, ++k) {
-        ig[k] = g;
+        ig[k] = seg_group[i];
         ib[k] = c;
         ie[k] = c + kItem < b ? c + kItem : b;
     }
@@ -996,9 +1032,9 @@ __device__ __forceinline__ int lev_mapped(const uint64_t *__restrict__ pq, const
 // bytes that occur in the data (alphabet map amap, A symbols).
 template <bool EMIT, int W>
 __global__ void __launch_bounds__(LEAF_T) k_leaf_lev(
-    TreeView tv, QParams qp, const uint8_t *__restrict__ amap_g, int A, int qchunk,
-    const int64_t *__restrict__ cand_off, uint32_t *__restrict__ cand, int32_t *__restrict__ deg,
-    const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col, float *__restrict__ dist,
+    TreeView tv, QParams qp, const uint8_t *__restrict__ amap_g, int A, int qchunk, Items items,
+    uint32_t *__restrict__ cand, int32_t *__restrict__ deg, const int64_t *__restrict__ row_ptr,
+    int32_t *__restrict__ rowcur, int32_t *__restrict__ col, float *__restrict__ dist,
     unsigned long long *__restrict__ st, int32_t *__restrict__ err) {
     extern __shared__ uint64_t speq[];  // qchunk x A x W
     __shared__ uint8_t amap[256];
@@ -1009,9 +1045,11 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf_lev(
     __shared__ int64_t s_ci;
     __shared__ int s_off, s_rows;
     __shared__ unsigned s_hit;
-    const int g = blockIdx.x, tid = threadIdx.x, warp = tid >> 5;
+    const int it = blockIdx.x, tid = threadIdx.x, warp = tid >> 5;
+    if (it >= *items.count) return;
+    const int g = items.group[it];
     const int qb = tv.group_begin[g], qn = tv.group_count[g];
-    const int64_t c0 = cand_off[g], c1 = cand_off[g + 1];
+    const int64_t c0 = items.begin[it], c1 = items.end[it];
     const int k = qp.lev_k;
     for (int i = tid; i < 256; i += LEAF_T) amap[i] = amap_g[i];
     unsigned long long pairs = 0;
@@ -1021,12 +1059,12 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf_lev(
         for (int i = tid; i < qchunk * A * W; i += LEAF_T) speq[i] = 0ull;
         if (tid < 32) {
             cnt[tid] = 0;
-            cursor[tid] = 0;
             if (tid < nqr) {
                 int qpos = qb + q0 + tid;
                 qlen[tid] = (int)(tv.soff[qpos + 1] - tv.soff[qpos]);
+                int o = tv.perm[qpos];
+                cursor[tid] = o;  // original id of the query (row of the CSR)
                 if (EMIT) {
-                    int o = tv.perm[qpos];
                     rowb[tid] = row_ptr[o];
                     rowe[tid] = row_ptr[o + 1];
                 }
@@ -1066,7 +1104,7 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf_lev(
                         hit |= 1u << p;
                         atomicAdd(&cnt[q], 1);
                     } else {
-                        int slot = atomicAdd(&cursor[q], 1);
+                        int slot = atomicAdd(&rowcur[cursor[q]], 1);
                         int64_t at = rowb[q] + slot;
                         if (at < rowe[q]) {
                             col[at] = tv.perm[ppos];
@@ -1087,10 +1125,7 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf_lev(
             if (last) break;
         }
         __syncthreads();
-        if (tid < nqr) {
-            if (!EMIT) deg[tv.perm[qb + q0 + tid]] = cnt[tid];
-            else if (rowb[tid] + cursor[tid] != rowe[tid]) atomicOr(err, 8);
-        }
+        if (!EMIT && tid < nqr && cnt[tid]) atomicAdd(&deg[cursor[tid]], cnt[tid]);
     }
     if (!EMIT) {
         for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
@@ -1298,6 +1333,73 @@ QParams make_qparams(const ct_tree *t, double eps, int include_self) {
     return q;
 }
 
+// Traversal launch shape: L2 uses blocks of TRAV_WARPS warps, edit distance
+// one warp per block; both are capped at a resident-sized grid.
+struct TravLaunch {
+    int blocks, warps;
+};
+TravLaunch trav_launch_config(const ct_tree *t) {
+    const int G = t->n_groups;
+    TravLaunch tl;
+    if (t->metric == CT_L2_F32) {
+        tl.blocks = (int)std::min<int64_t>(ceil_div(G, TRAV_WARPS), (int64_t)num_sms() * 8);
+        tl.blocks = std::max(tl.blocks, 1);
+        tl.warps = tl.blocks * TRAV_WARPS;
+    } else {
+        tl.blocks = (int)std::max<int64_t>(1, std::min<int64_t>(G, (int64_t)num_sms() * 16));
+        tl.warps = tl.blocks;
+    }
+    return tl;
+}
+
+// First pool size: 256 candidate blocks per point (or 512 per group), at most
+// a quarter of the free device memory, plus one chunk per warp.
+int64_t pool_capacity_guess(const ct_tree *t, const TravLaunch &tl) {
+    int64_t want = std::max<int64_t>(256 * t->n, (int64_t)t->n_groups * 512);
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+        int64_t lim = (int64_t)(fr / 4 / sizeof(uint32_t));
+        if (lim > 0 && want > lim) want = lim;
+    } else {
+        cudaGetLastError();
+    }
+    return want + (int64_t)(tl.warps + 1) * POOL_CHUNK;
+}
+
+// Clears the pool counters and launches the traversal (allocates nothing).
+void launch_traversal(const ct_tree *t, const TreeView &tv, const QParams &qp, const Pool &P, int2 *stacks, int cap,
+                      const TravLaunch &tl, unsigned long long *st, int32_t *err, int32_t *next_group,
+                      cudaStream_t s) {
+    // P.next .. P.overflow are the four 64-bit words of one counter block
+    CT_CHECK_CUDA(cudaMemsetAsync(next_group, 0, sizeof(int32_t), s));
+    CT_CHECK_CUDA(cudaMemsetAsync(P.next, 0, 4 * sizeof(unsigned long long), s));
+    if (t->n_groups == 0) return;
+    if (t->metric == CT_L2_F32) {
+        const int nq4 = t->dp >> 2;
+        const size_t tsm = (size_t)TRAV_WARPS * t->dp * sizeof(float);
+        const int tpd = nq4 >= 16 ? 8 : nq4 >= 8 ? 4 : nq4 >= 4 ? 2 : 1;
+        switch (tpd) {
+#define CT_TRL(T)                                                                                               \
+    case T:                                                                                                     \
+        if (tsm > 48 * 1024)                                                                                    \
+            CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)); \
+        k_traverse_l2<T><<<tl.blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, P, stacks, cap, st, err, next_group); \
+        break;
+            CT_TRL(1) CT_TRL(2) CT_TRL(4) CT_TRL(8)
+#undef CT_TRL
+        }
+    } else {
+        switch (lev_words_for(t->max_len)) {
+#define CT_TL(WW) \
+    case WW: k_traverse_lev<WW><<<tl.blocks, 32, 0, s>>>(tv, qp, P, stacks, cap, st, err, next_group); break;
+            CT_TL(1) CT_TL(2) CT_TL(4) CT_TL(8) CT_TL(16)
+#undef CT_TL
+        }
+    }
+    CT_COUNT_LAUNCH();
+    CT_LAUNCH_CHECK();
+}
+
 void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out) {
     const int64_t n = t->n;
     const int G = t->n_groups;
@@ -1307,76 +1409,58 @@ void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &
     CT_CHECK_CUDA(cudaMemsetAsync(st.p, 0, ST_N * sizeof(unsigned long long), s));
     int32_t *err = reinterpret_cast<int32_t *>(st.p + ST_ERR);
 
-    // 1. traversal: count, scan, fill
+    const int W = l2 ? 1 : lev_words_for(t->max_len);
+    // 1. traversal: one pass into the candidate pool (rerun once if it overflows)
     const int cap = 32 * (t->depth + 2);
-    int blocks, warps_total;
-    int W = l2 ? 1 : lev_words_for(t->max_len);
-    if (l2) {
-        blocks = (int)std::min<int64_t>(ceil_div(G, TRAV_WARPS), (int64_t)num_sms() * 8);
-        warps_total = blocks * TRAV_WARPS;
-    } else {
-        blocks = (int)std::min<int64_t>(G, (int64_t)num_sms() * 16);
-        warps_total = blocks;
-    }
-    blocks = std::max(blocks, 1);
-    warps_total = std::max(warps_total, 1);
-    DBuf<int2> stacks((size_t)warps_total * cap, s);
-    DBuf<int32_t> ccnt(G + 1, s);
-    DBuf<int64_t> coff(G + 1, s);
-    size_t tsm = l2 ? (size_t)TRAV_WARPS * t->dp * sizeof(float) : 0;
-    if (tsm > 48 * 1024) {
-        CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
-        CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
-    }
+    TravLaunch tl = trav_launch_config(t);
+    DBuf<int2> stacks((size_t)tl.warps * cap, s);
+    DBuf<unsigned long long> ctr(4, s);
     DBuf<int32_t> next_group(1, s);
-    auto traverse = [&](bool fill, uint32_t *cand) {
-        CT_CHECK_CUDA(cudaMemsetAsync(next_group.p, 0, sizeof(int32_t), s));
-        if (l2) {
-            if (fill)
-                k_traverse_l2<true><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err, next_group.p);
-            else
-                k_traverse_l2<false><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err, next_group.p);
-        } else {
-            switch (W) {
-#define CT_TL(WW)                                                                                           \
-    case WW:                                                                                                \
-        if (fill) k_traverse_lev<true, WW><<<blocks, 32, 0, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err, next_group.p); \
-        else k_traverse_lev<false, WW><<<blocks, 32, 0, s>>>(tv, qp, ccnt.p, coff.p, cand, stacks.p, cap, st.p, err, next_group.p);    \
-        break;
-                CT_TL(1) CT_TL(2) CT_TL(4) CT_TL(8) CT_TL(16)
-#undef CT_TL
-            }
+    int64_t pool_cap = pool_capacity_guess(t, tl);
+    DBuf<uint32_t> pool;
+    DBuf<int32_t> seg_group, seg_count;
+    DBuf<int64_t> seg_begin;
+    unsigned long long hc[4] = {0, 0, 0, 0};
+    Pool P{};
+    for (int attempt = 0;; ++attempt) {
+        const int64_t seg_cap = G + pool_cap / POOL_CHUNK + tl.warps + 16;
+        pool = DBuf<uint32_t>(pool_cap, s);
+        seg_group = DBuf<int32_t>(seg_cap, s);
+        seg_count = DBuf<int32_t>(seg_cap, s);
+        seg_begin = DBuf<int64_t>(seg_cap, s);
+        P = Pool{pool.p, pool_cap, ctr.p, seg_group.p, seg_count.p, seg_begin.p,
+                 reinterpret_cast<int32_t *>(ctr.p + 1), seg_cap, ctr.p + 2, reinterpret_cast<int32_t *>(ctr.p + 3)};
+        {
+            ProfScope ps("traverse", s);
+            launch_traversal(t, tv, qp, P, stacks.p, cap, tl, st.p, err, next_group.p, s);
         }
-        CT_COUNT_LAUNCH();
-        CT_LAUNCH_CHECK();
-    };
-    {
-        ProfScope ps("traverse_count", s);
-        traverse(false, nullptr);
+        to_host(hc, ctr.p, 4, s);
+        if (!(uint32_t)hc[3]) break;
+        if (attempt >= 1) CT_FAIL(CT_ECUDA, "candidate pool overflowed twice");
+        pool_cap = (int64_t)hc[2] + 2LL * tl.warps * POOL_CHUNK + POOL_CHUNK;
+        CT_CHECK_CUDA(cudaMemsetAsync(st.p, 0, ST_N * sizeof(unsigned long long), s));
     }
-    exclusive_scan_i32_to_i64(ccnt.p, coff.p, G, coff.p + G, s);
-    int64_t n_cand = 0;
-    to_host(&n_cand, coff.p + G, 1, s);
-    DBuf<uint32_t> cand(n_cand ? n_cand : 1, s);
-    DBuf<uint32_t> emask(l2 ? (n_cand ? n_cand : 1) : 0, s);
-    // work items of the L2 leaf stage
-    const int64_t max_items = G + n_cand / kItem + 1;
-    DBuf<int32_t> icnt(l2 ? G + 1 : 0, s), igroup(l2 ? max_items : 0, s), nitems(1, s);
-    DBuf<int64_t> ioff(l2 ? G + 1 : 0, s), ibeg(l2 ? max_items : 0, s), iend(l2 ? max_items : 0, s);
+    const int64_t n_cand = (int64_t)hc[2];
+    const int nseg = (int)(uint32_t)hc[1];
+    const int64_t pool_used = (int64_t)hc[0] < pool_cap ? (int64_t)hc[0] : pool_cap;
+    DBuf<uint32_t> emask(l2 ? (pool_used ? pool_used : 1) : 0, s);
+    // work items: pool segments in slices of at most kItem candidate blocks
+    const int64_t max_items = nseg + n_cand / kItem + 1;
+    DBuf<int32_t> icnt(nseg + 1, s), igroup(max_items, s), nitems(1, s);
+    DBuf<int64_t> ioff(nseg + 1, s), ibeg(max_items, s), iend(max_items, s);
     Items items{igroup.p, ibeg.p, iend.p, nitems.p};
-    if (l2 && G) {
-        k_item_counts<<<grid_for(G, 256), 256, 0, s>>>(G, ccnt.p, icnt.p);
+    CT_CHECK_CUDA(cudaMemsetAsync(nitems.p, 0, sizeof(int32_t), s));
+    if (nseg) {
+        k_item_counts<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_count.p, icnt.p);
         CT_COUNT_LAUNCH();
-        exclusive_scan_i32_to_i64(icnt.p, ioff.p, G, ioff.p + G, s);
-        k_item_fill<<<grid_for(G, 256), 256, 0, s>>>(G, coff.p, ioff.p, igroup.p, ibeg.p, iend.p, nitems.p);
+        exclusive_scan_i32_to_i64(icnt.p, ioff.p, nseg, ioff.p + nseg, s);
+        k_item_fill<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_group.p, seg_begin.p, seg_count.p, ioff.p,
+                                                       igroup.p, ibeg.p, iend.p, nitems.p);
         CT_COUNT_LAUNCH();
         CT_LAUNCH_CHECK();
     }
-    DBuf<int32_t> rowcur(l2 ? n + 1 : 0, s);
-    {
-        ProfScope ps("traverse_fill", s);
-        traverse(true, cand.p);
-    }
+    DBuf<int32_t> rowcur(n + 1, s);
+    uint32_t *cand_p = pool.p;
 
     // alphabet of the strings (edit distance)
     DBuf<uint8_t> amap;
@@ -1412,13 +1496,13 @@ void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &
     DBuf<int32_t> deg(n + 1, s);
     CT_CHECK_CUDA(cudaMemsetAsync(deg.p, 0, (n + 1) * sizeof(int32_t), s));
     auto leaf = [&](bool emit, int64_t *row_ptr, int32_t *col, float *dist) {
-        if (G == 0) return;
+        if (G == 0 || nseg == 0) return;
         if (l2) {
             leaf_l2_prepare();
             if (emit)
-                k_leaf_l2<true><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand.p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err);
+                k_leaf_l2<true><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err);
             else
-                k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand.p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err);
+                k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err);
         } else {
             switch (W) {
 #define CT_LL(WW)                                                                                                      \
@@ -1427,8 +1511,8 @@ void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &
             CT_CHECK_CUDA(cudaFuncSetAttribute(k_leaf_lev<true, WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm)); \
             CT_CHECK_CUDA(cudaFuncSetAttribute(k_leaf_lev<false, WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm)); \
         }                                                                                                              \
-        if (emit) k_leaf_lev<true, WW><<<G, LEAF_T, lsm, s>>>(tv, qp, amap.p, A, qchunk, coff.p, cand.p, deg.p, row_ptr, col, dist, st.p, err); \
-        else k_leaf_lev<false, WW><<<G, LEAF_T, lsm, s>>>(tv, qp, amap.p, A, qchunk, coff.p, cand.p, deg.p, row_ptr, col, dist, st.p, err);    \
+        if (emit) k_leaf_lev<true, WW><<<(unsigned)max_items, LEAF_T, lsm, s>>>(tv, qp, amap.p, A, qchunk, items, cand_p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err); \
+        else k_leaf_lev<false, WW><<<(unsigned)max_items, LEAF_T, lsm, s>>>(tv, qp, amap.p, A, qchunk, items, cand_p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err);    \
         break;
                 CT_LL(1) CT_LL(2) CT_LL(4) CT_LL(8) CT_LL(16)
 #undef CT_LL
@@ -1453,12 +1537,10 @@ void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &
     out.dist = (float *)dmalloc((size_t)(nnz ? nnz : 1) * sizeof(float), s);
     if (nnz) {
         ProfScope ps("leaf_emit", s);
-        if (l2) CT_CHECK_CUDA(cudaMemsetAsync(rowcur.p, 0, (n + 1) * sizeof(int32_t), s));
+        CT_CHECK_CUDA(cudaMemsetAsync(rowcur.p, 0, (n + 1) * sizeof(int32_t), s));
         leaf(true, row_ptr, out.col, out.dist);
-        if (l2) {
-            k_check_rows<<<grid_for(n, 256), 256, 0, s>>>(n, row_ptr, rowcur.p, err);
-            CT_COUNT_LAUNCH();
-        }
+        k_check_rows<<<grid_for(n, 256), 256, 0, s>>>(n, row_ptr, rowcur.p, err);
+        CT_COUNT_LAUNCH();
     }
     {
         ProfScope ps("row_sort", s);
@@ -1520,81 +1602,86 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cudaStream_t s) {
     if (t->metric != CT_L2_F32) CT_FAIL(CT_EUNSUPPORTED, "the allocation-free degree count supports L2 trees only");
     const int64_t n = t->n;
-    const int G = t->n_groups;
     if (n == 0) return;
     unsigned char *base = noalloc_scratch();
     const size_t cap_bytes = CT_NOALLOC_SCRATCH_BYTES;
     const int cap = 32 * (t->depth + 2);
-    // fixed part: counters, per-group counts and offsets, scan tile sums, work-item counts
     size_t off = 0;
     auto take = [&](size_t bytes) {
         unsigned char *p = base + off;
         off = align256(off + bytes);
         return p;
     };
+    // fixed part: counters, scan tile sums, traversal stacks
     unsigned long long *st = (unsigned long long *)take(ST_N * sizeof(unsigned long long));
+    unsigned long long *ctr = (unsigned long long *)take(4 * sizeof(unsigned long long));
     int32_t *next_group = (int32_t *)take(sizeof(int32_t));
     int32_t *nitems = (int32_t *)take(sizeof(int32_t));
-    int32_t *ccnt = (int32_t *)take((size_t)(G + 1) * sizeof(int32_t));
-    int64_t *coff = (int64_t *)take((size_t)(G + 1) * sizeof(int64_t));
-    int32_t *icnt = (int32_t *)take((size_t)(G + 1) * sizeof(int32_t));
-    int64_t *ioff = (int64_t *)take((size_t)(G + 1) * sizeof(int64_t));
-    int64_t *sums = (int64_t *)take((size_t)std::max<int64_t>(scan_scratch_entries(G), 1) * sizeof(int64_t));
+    TravLaunch tl = trav_launch_config(t);
     const size_t stack_per_block = (size_t)TRAV_WARPS * cap * sizeof(int2);
-    if (off + stack_per_block > cap_bytes)
-        CT_FAIL(CT_EUNSUPPORTED, "tree with %d query groups and depth %d needs more than the fixed %zu-byte scratch",
-                G, t->depth, cap_bytes);
-    // traversal blocks: as in the allocating path, capped so that the stacks
-    // take at most a quarter of the array
-    int64_t want = std::min<int64_t>(ceil_div(G, TRAV_WARPS), (int64_t)num_sms() * 8);
-    int64_t fit = (int64_t)std::max<size_t>(1, (cap_bytes / 4) / stack_per_block);
-    const int blocks = (int)std::max<int64_t>(1, std::min(want, fit));
-    int2 *stacks = (int2 *)take((size_t)blocks * stack_per_block);
+    if (off + stack_per_block > cap_bytes / 2)
+        CT_FAIL(CT_EUNSUPPORTED, "a tree of depth %d needs more than the fixed %zu-byte scratch", t->depth, cap_bytes);
+    // stacks take at most a quarter of the array, and the warps' partly filled
+    // pool chunks at most a quarter of it
+    const int64_t chunk_blocks = (int64_t)(cap_bytes / 4 / sizeof(uint32_t)) / ((int64_t)TRAV_WARPS * POOL_CHUNK);
+    tl.blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>(std::min<int64_t>(tl.blocks, (cap_bytes / 4) / stack_per_block), chunk_blocks));
+    tl.warps = tl.blocks * TRAV_WARPS;
+    int2 *stacks = (int2 *)take((size_t)tl.blocks * stack_per_block);
+    // the rest: segments (one third of it, at most one per group and chunk) and the pool
+    const size_t rest = cap_bytes > off ? cap_bytes - off : 0;
+    const int64_t seg_cap = (int64_t)(rest / 3 / (sizeof(int32_t) * 2 + sizeof(int64_t) + 16));
+    int32_t *seg_group = (int32_t *)take((size_t)seg_cap * sizeof(int32_t));
+    int32_t *seg_count = (int32_t *)take((size_t)seg_cap * sizeof(int32_t));
+    int64_t *seg_begin = (int64_t *)take((size_t)seg_cap * sizeof(int64_t));
     if (off >= cap_bytes) CT_FAIL(CT_EUNSUPPORTED, "problem too large for the fixed scratch");
-    const size_t room = cap_bytes - off;  // candidates and work items share the rest
+    const int64_t pool_cap = (int64_t)((cap_bytes - off) / sizeof(uint32_t));
+    uint32_t *pool = (uint32_t *)take((size_t)pool_cap * sizeof(uint32_t));
+    Pool P{pool, pool_cap, ctr, seg_group, seg_count, seg_begin, reinterpret_cast<int32_t *>(ctr + 1), seg_cap,
+           ctr + 2, reinterpret_cast<int32_t *>(ctr + 3)};
 
     TreeView tv = view_of(t);
     int32_t *err = reinterpret_cast<int32_t *>(st + ST_ERR);
-    const size_t tsm = (size_t)TRAV_WARPS * t->dp * sizeof(float);
-    if (tsm > 48 * 1024) {
-        CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
-        CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
-    }
     // the array keeps the previous call's contents: clear what must start at zero
     CT_CHECK_CUDA(cudaMemsetAsync(st, 0, ST_N * sizeof(unsigned long long), s));
-    CT_CHECK_CUDA(cudaMemsetAsync(next_group, 0, sizeof(int32_t), s));
-    k_traverse_l2<false><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt, coff, nullptr, stacks, cap, st, err,
-                                                              next_group);
-    CT_COUNT_LAUNCH();
-    CT_LAUNCH_CHECK();
-    exclusive_scan_i32_to_i64_into(ccnt, coff, G, coff + G, sums, s);
-    int64_t total = 0;
-    CT_CHECK_CUDA(cudaMemcpyAsync(&total, coff + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    launch_traversal(t, tv, qp, P, stacks, cap, tl, st, err, next_group, s);
+    unsigned long long hc[4] = {0, 0, 0, 0};
+    CT_CHECK_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
     CT_CHECK_CUDA(cudaStreamSynchronize(s));
-    const int64_t max_items = G + total / kItem + 1;
-    const size_t need = align256((size_t)total * sizeof(uint32_t)) + align256((size_t)max_items * sizeof(int32_t)) +
-                        2 * align256((size_t)max_items * sizeof(int64_t));
-    if (need > room)
-        CT_FAIL(CT_EUNSUPPORTED, "%lld candidate blocks need %zu bytes of the fixed scratch (room for %zu); use eps_graph_query",
-                (long long)total, need, room);
-    uint32_t *cand = (uint32_t *)take((size_t)total * sizeof(uint32_t));
-    int32_t *igroup = (int32_t *)take((size_t)max_items * sizeof(int32_t));
-    int64_t *ibeg = (int64_t *)take((size_t)max_items * sizeof(int64_t));
-    int64_t *iend = (int64_t *)take((size_t)max_items * sizeof(int64_t));
-    CT_CHECK_CUDA(cudaMemsetAsync(next_group, 0, sizeof(int32_t), s));
-    k_traverse_l2<true><<<blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, ccnt, coff, cand, stacks, cap, st, err,
-                                                             next_group);
-    CT_COUNT_LAUNCH();
+    if ((uint32_t)hc[3])
+        CT_FAIL(CT_EUNSUPPORTED, "%llu candidate blocks do not fit the fixed %zu-byte scratch (room for %lld); use eps_graph_query",
+                hc[2], cap_bytes, (long long)pool_cap);
+    const int nseg = (int)(uint32_t)hc[1];
+    // work items live in the unused tail of the pool
+    const int64_t used = (int64_t)hc[0] < pool_cap ? (int64_t)hc[0] : pool_cap;
+    const int64_t max_items = nseg + (int64_t)hc[2] / kItem + 1;
+    size_t toff = align256((size_t)used * sizeof(uint32_t));
+    auto ttake = [&](size_t bytes) {
+        unsigned char *p = (unsigned char *)pool + toff;
+        toff = align256(toff + bytes);
+        return p;
+    };
+    int32_t *icnt = (int32_t *)ttake((size_t)(nseg + 1) * sizeof(int32_t));
+    int64_t *ioff = (int64_t *)ttake((size_t)(nseg + 1) * sizeof(int64_t));
+    int64_t *sums = (int64_t *)ttake((size_t)std::max<int64_t>(scan_scratch_entries(nseg), 1) * sizeof(int64_t));
+    int32_t *igroup = (int32_t *)ttake((size_t)max_items * sizeof(int32_t));
+    int64_t *ibeg = (int64_t *)ttake((size_t)max_items * sizeof(int64_t));
+    int64_t *iend = (int64_t *)ttake((size_t)max_items * sizeof(int64_t));
+    if (toff > (size_t)pool_cap * sizeof(uint32_t))
+        CT_FAIL(CT_EUNSUPPORTED, "work items of %llu candidate blocks do not fit the fixed scratch; use eps_graph_query",
+                hc[2]);
     CT_CHECK_CUDA(cudaMemsetAsync(degrees, 0, (size_t)n * sizeof(int32_t), s));
-    if (G) {
-        k_item_counts<<<grid_for(G, 256), 256, 0, s>>>(G, ccnt, icnt);
+    CT_CHECK_CUDA(cudaMemsetAsync(nitems, 0, sizeof(int32_t), s));
+    if (nseg) {
+        k_item_counts<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_count, icnt);
         CT_COUNT_LAUNCH();
-        exclusive_scan_i32_to_i64_into(icnt, ioff, G, ioff + G, sums, s);
-        k_item_fill<<<grid_for(G, 256), 256, 0, s>>>(G, coff, ioff, igroup, ibeg, iend, nitems);
+        exclusive_scan_i32_to_i64_into(icnt, ioff, nseg, ioff + nseg, sums, s);
+        k_item_fill<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_group, seg_begin, seg_count, ioff, igroup, ibeg,
+                                                       iend, nitems);
         CT_COUNT_LAUNCH();
         Items items{igroup, ibeg, iend, nitems};
         leaf_l2_prepare();
-        k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand, nullptr, degrees, nullptr,
+        k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, pool, nullptr, degrees, nullptr,
                                                                           nullptr, nullptr, nullptr, st, err);
         CT_COUNT_LAUNCH();
     }
