@@ -412,60 +412,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Squared distances of the 2 x 4 pairs owned by this thread: queries qi and
-// qi + 16 of the Q tile against rows pj, pj+8, pj+16, pj+24 of the P tile,
-// whose positions are prow[0..npr).  Coordinates are summed in chunks of 16
-// (FMA per term) and the chunk sums added into the total.  Contains barriers;
-// every thread of the block calls it.  On return the P tile is loaded and
-// every thread is past its last read of Qs/Ps for this call.
-__device__ __forceinline__ void tile_sqdist(const TreeView &tv, float4 *Qs, float4 *Ps, const int *prow, int npr,
-                                            int qfirst, int nqr, int nkc, float (&tot)[2][4]) {
-    const int tid = threadIdx.x, qi = tid >> 3, pj = tid & 7;
-    const int dp = tv.dp;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) tot[i][j] = 0.f;
-    for (int kc = 0; kc < nkc; ++kc) {
-        const int k0 = kc * KC;
-        const int kq = min(KC, dp - k0) >> 2;
-        if (kc > 0) __syncthreads();
-        if (nkc > 1) load_rows(Qs, tv.pts, dp, nullptr, qfirst, nqr, k0, kq);
-        load_rows(Ps, tv.pts, dp, prow, 0, npr, k0, kq);
-        __syncthreads();
-        const float4 *qa = Qs + qi * KS4, *qb2 = Qs + (qi + 16) * KS4;
-        const float4 *pr0 = Ps + pj * KS4, *pr1 = Ps + (pj + 8) * KS4;
-        const float4 *pr2 = Ps + (pj + 16) * KS4, *pr3 = Ps + (pj + 24) * KS4;
-        for (int k4 = 0; k4 < kq; k4 += 4) {
-            float acc[2][4];
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-            const int ke = min(k4 + 4, kq);
-            for (int k = k4; k < ke; ++k) {
-                float4 a[2] = {qa[k], qb2[k]};
-                float4 b[4] = {pr0[k], pr1[k], pr2[k], pr3[k]};
-#pragma unroll
-                for (int i = 0; i < 2; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        float dx = a[i].x - b[j].x, dy = a[i].y - b[j].y;
-                        float dz = a[i].z - b[j].z, dw = a[i].w - b[j].w;
-                        acc[i][j] = fmaf(dx, dx, acc[i][j]);
-                        acc[i][j] = fmaf(dy, dy, acc[i][j]);
-                        acc[i][j] = fmaf(dz, dz, acc[i][j]);
-                        acc[i][j] = fmaf(dw, dw, acc[i][j]);
-                    }
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) tot[i][j] += acc[i][j];
-        }
-    }
-}
-
 // Packed fp32 pairs (sm_100+ f32x2 instructions): two independent IEEE
 // round-to-nearest operations per instruction.
 __device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
@@ -482,17 +428,39 @@ __device__ __forceinline__ float f2_sum(unsigned long long v) {
     return __uint_as_float((uint32_t)v) + __uint_as_float((uint32_t)(v >> 32));
 }
 
+// Squared distances of the 2 x 4 pairs owned by this thread: queries qi and
+// qi + 16 of the Q tile against rows pj, pj+8, pj+16, pj+24 of the P tile,
+// whose positions are prow[0..npr).  Coordinates are summed in chunks of 16
+// (FMA per term) and the chunk sums added into the total.  Contains barriers;
+// every thread of the block calls it.  On return the P tile is loaded and
+// every thread is past its last read of Qs/Ps for this call.
+__device__ __forceinline__ void tile_accumulate(const float4 *Qs, const float4 *Ps, int kq, float (&tot)[2][4]);
+
+__device__ __forceinline__ void tile_sqdist(const TreeView &tv, float4 *Qs, float4 *Ps, const int *prow, int npr,
+                                            int qfirst, int nqr, int nkc, float (&tot)[2][4]) {
+    const int dp = tv.dp;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tot[i][j] = 0.f;
+    for (int kc = 0; kc < nkc; ++kc) {
+        const int k0 = kc * KC;
+        const int kq = min(KC, dp - k0) >> 2;
+        if (kc > 0) __syncthreads();
+        if (nkc > 1) load_rows(Qs, tv.pts, dp, nullptr, qfirst, nqr, k0, kq);
+        load_rows(Ps, tv.pts, dp, prow, 0, npr, k0, kq);
+        __syncthreads();
+        tile_accumulate(Qs, Ps, kq, tot);  // KC is a multiple of 16: chunks line up across K chunks
+    }
+}
+
 // 2 x 4 micro-tile from tiles already in shared memory (rows of kq float4).
 // Per chunk of 16 coordinates two packed partial sums of 8 terms each (even
 // and odd coordinates) are formed with FMA, added, and the chunk sum is added
 // into the running total: fp32 error of the squared distance <= ~19 u for
 // rows of 128 floats (u = 2^-24).
-__device__ __forceinline__ void tile_sqdist_smem(const float4 *Qs, const float4 *Ps, int kq, float (&tot)[2][4]) {
+__device__ __forceinline__ void tile_accumulate(const float4 *Qs, const float4 *Ps, int kq, float (&tot)[2][4]) {
     const int tid = threadIdx.x, qi = tid >> 3, pj = tid & 7;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) tot[i][j] = 0.f;
     const ulonglong2 *qa[2] = {reinterpret_cast<const ulonglong2 *>(Qs + qi * KS4),
                                reinterpret_cast<const ulonglong2 *>(Qs + (qi + 16) * KS4)};
     const ulonglong2 *pr[4] = {reinterpret_cast<const ulonglong2 *>(Ps + pj * KS4),
@@ -545,6 +513,49 @@ __device__ __forceinline__ void tile_sqdist_smem(const float4 *Qs, const float4 
 #pragma unroll
             for (int j = 0; j < 4; ++j) tot[i][j] += f2_sum(acc[i][j]);
     }
+}
+
+__device__ __forceinline__ void tile_sqdist_smem(const float4 *Qs, const float4 *Ps, int kq, float (&tot)[2][4]) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tot[i][j] = 0.f;
+    tile_accumulate(Qs, Ps, kq, tot);
+}
+
+// The same squared distance for one pair, scalar, in the same operation order
+// as the tiles (per 16 coordinates: x and z terms into one FMA chain, y and w
+// into another; chain sums added; chunk sums added into the total), so that
+// its decisions equal the tiles' bit for bit.
+__device__ __forceinline__ float pair_sqdist(const float4 *__restrict__ x, const float4 *__restrict__ y, int nq4) {
+    float tot = 0.f;
+    int k = 0;
+    for (; k + 4 <= nq4; k += 4) {
+        float lo = 0.f, hi = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 a = __ldg(x + k + u), b = __ldg(y + k + u);
+            const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
+            lo = fmaf(dx, dx, lo);
+            hi = fmaf(dy, dy, hi);
+            lo = fmaf(dz, dz, lo);
+            hi = fmaf(dw, dw, hi);
+        }
+        tot += lo + hi;
+    }
+    if (k < nq4) {
+        float lo = 0.f, hi = 0.f;
+        for (; k < nq4; ++k) {
+            const float4 a = __ldg(x + k), b = __ldg(y + k);
+            const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
+            lo = fmaf(dx, dx, lo);
+            hi = fmaf(dy, dy, hi);
+            lo = fmaf(dz, dz, lo);
+            hi = fmaf(dw, dw, hi);
+        }
+        tot += lo + hi;
+    }
+    return tot;
 }
 
 struct LeafShared {
@@ -784,13 +795,16 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
                 }
             }
 
-            // ---- prefix of the surviving blocks' point counts (warp 0)
+            // ---- prefix over the batch (warp 0): count pass -- points of the
+            // surviving blocks; emit pass -- (query, point) pairs to evaluate
+            const uint32_t qvalid = nqr >= 32 ? 0xffffffffu : ((1u << nqr) - 1u);
             if (warp == 0) {
                 int loc[4], sum = 0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int i = 4 * lane + k;
-                    loc[k] = (i < bn && S.bmask[i] != 0u) ? S.bcnt[i] : 0;
+                    if (EMIT) loc[k] = i < bn ? __popc(S.bmask[i] & qvalid) * S.bcnt[i] : 0;
+                    else loc[k] = (i < bn && S.bmask[i] != 0u) ? S.bcnt[i] : 0;
                     sum += loc[k];
                 }
                 int incl = sum;
@@ -810,8 +824,61 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
             __syncthreads();
             const int T = S.bpre[NB];
 
-            // ---- stage 2: packed points of the surviving blocks
-            for (int R0 = 0; R0 < T; R0 += RCAP) {
+            // ---- emit pass: one thread per (query, point) pair of the blocks in
+            // which the query found an edge; same arithmetic as the tiles
+            if (EMIT) {
+                for (int r0 = 0; r0 < T; r0 += LEAF_T) {
+                    const int r = r0 + tid;
+                    if (r >= T) continue;
+                    int lo = 0, hi = NB;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (S.bpre[mid] <= r) lo = mid; else hi = mid;
+                    }
+                    const int idx = r - S.bpre[lo], cnt = S.bcnt[lo];
+                    const int qr = idx / cnt, pidx = idx - qr * cnt;
+                    const int q = (int)__fns(S.bmask[lo] & qvalid, 0u, qr + 1);
+                    const int qpos = qfirst + q, ppos = S.bbeg[lo] + pidx;
+                    if (qpos == ppos && !qp.include_self) continue;
+                    const float sv = pair_sqdist(reinterpret_cast<const float4 *>(tv.pts + (size_t)qpos * dp),
+                                                 reinterpret_cast<const float4 *>(tv.pts + (size_t)ppos * dp), dp >> 2);
+                    int edge;
+                    float dv = 0.f;
+                    bool exact = false;
+                    if (qp.mode == 0) {
+                        if (sv < qp.lo2) edge = 1;
+                        else if (sv > qp.hi2) edge = 0;
+                        else exact = true;
+                    } else if (qp.mode == 1) {
+                        edge = sv == 0.0f;
+                    } else if (qp.mode == 3) {
+                        edge = 1;
+                    } else {
+                        exact = true;
+                    }
+                    if (exact) {
+                        const double s64 = sq_l2_exact(tv.pts + (size_t)qpos * dp, tv.pts + (size_t)ppos * dp, dim);
+                        edge = s64 <= qp.eps2_64;
+                        dv = (float)sqrt(s64);
+                    } else if (edge) {
+                        dv = fp32_dist_ok ? sqrtf(sv)
+                                          : (float)sqrt(sq_l2_exact(tv.pts + (size_t)qpos * dp,
+                                                                    tv.pts + (size_t)ppos * dp, dim));
+                    }
+                    if (!edge) continue;
+                    const int slot = atomicAdd(&rowcur[S.cursor[q]], 1);
+                    const int64_t at = S.rowb[q] + slot;
+                    if (at < S.rowe[q]) {
+                        col[at] = tv.perm[ppos];
+                        dist[at] = dv;
+                    } else {
+                        atomicOr(err, 4);
+                    }
+                }
+            }
+
+            // ---- stage 2 (count pass): packed points of the surviving blocks
+            for (int R0 = 0; !EMIT && R0 < T; R0 += RCAP) {
                 const int RN = min(RCAP, T - R0);
                 __syncthreads();
                 for (int r = tid; r < RN; r += LEAF_T) {
