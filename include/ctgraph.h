@@ -121,7 +121,7 @@ typedef struct {
     int64_t candidates;       /* (group, candidate leaf block) entries */
     int64_t overflow_rows;    /* rows recounted after a predicted capacity overflowed */
     int64_t kernel_launches;  /* kernels this library launched for the query */
-    int64_t reserved;
+    int64_t emit_pairs;       /* pairs evaluated again by the emit pass */
 } ct_query_stats;
 
 typedef struct ct_tree ct_tree;           /* opaque, device-resident */

@@ -434,6 +434,15 @@ __global__ void k_gather_strings(int64_t n, const int32_t *__restrict__ perm, co
     for (int64_t k = threadIdx.x; k < l; k += blockDim.x) out[o + k] = S[b + k];
 }
 
+// Sort keys putting larger radii first (radii are non-negative floats).
+__global__ void k_radius_desc_keys(int ng, const float *__restrict__ r, uint32_t *__restrict__ keys,
+                                   uint32_t *__restrict__ vals) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    keys[g] = 0xFFFFFFFFu - __float_as_uint(r[g]);
+    vals[g] = (uint32_t)g;
+}
+
 // Radius of each query group: max distance from its first point (rounded up).
 // One warp per group, one lane per point.
 __global__ void k_group_radius_l2(int ng, const int32_t *__restrict__ gbeg, const int32_t *__restrict__ gcnt,
@@ -856,6 +865,16 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
             }
             CT_COUNT_LAUNCH();
         }
+        // traversal order: groups with larger balls walk more of the tree; taking
+        // them first shortens the tail of the dynamically scheduled walk
+        t->group_order = (int32_t *)dmalloc(sizeof(int32_t) * (size_t)(G ? G : 1), s);
+        if (G) {
+            DBuf<uint32_t> ok(G, s), ov(G, s), tk2(G, s), tv2(G, s);
+            k_radius_desc_keys<<<grid_for(G), BT, 0, s>>>(G, t->group_radius, ok.p, ov.p);
+            CT_COUNT_LAUNCH();
+            radix_sort_pairs(ok.p, ov.p, tk2.p, tv2.p, G, 32, s);
+            CT_CHECK_CUDA(cudaMemcpyAsync(t->group_order, ov.p, sizeof(int32_t) * G, cudaMemcpyDeviceToDevice, s));
+        }
         CT_CHECK_CUDA(cudaStreamSynchronize(s));  // host vectors above must outlive the copies
     }
     CT_LAUNCH_CHECK();
@@ -869,7 +888,7 @@ void free_tree(ct_tree *t) {
     cudaStream_t s = t->stream;
     void *ptrs[] = {t->pts, t->sdata, t->soff, t->perm, t->dcen, t->node_begin, t->node_count,
                     t->child_begin, t->child_count, t->radius, t->level, t->node_ctr, t->leaf_ids,
-                    t->parent, t->group_begin, t->group_count, t->group_radius};
+                    t->parent, t->group_begin, t->group_count, t->group_radius, t->group_order};
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, s);
     cudaStreamSynchronize(s);

@@ -185,6 +185,7 @@ struct ct_tree {
     int32_t *group_begin = nullptr;
     int32_t *group_count = nullptr;
     float *group_radius = nullptr;
+    int32_t *group_order = nullptr;  // groups by decreasing radius (longest walks first)
 };
 
 namespace ct {

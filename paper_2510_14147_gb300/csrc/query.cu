@@ -58,7 +58,7 @@ __device__ __noinline__ double sq_l2_exact(const float *__restrict__ x, const fl
 struct TreeView {
     const float *pts, *node_ctr, *radius, *dcen, *group_radius;
     const int32_t *perm, *node_begin, *node_count, *child_begin, *child_count, *leaf_ids;
-    const int32_t *group_begin, *group_count;
+    const int32_t *group_begin, *group_count, *group_order;
     const uint8_t *sdata;
     const int64_t *soff;
     int dp, dim, n_leaves, n_groups;
@@ -71,6 +71,7 @@ TreeView view_of(const ct_tree *t) {
     v.child_begin = t->child_begin; v.child_count = t->child_count; v.leaf_ids = t->leaf_ids;
     v.sdata = t->sdata; v.soff = t->soff; v.dp = t->dp; v.dim = t->dim; v.n_leaves = t->n_leaves;
     v.group_begin = t->group_begin; v.group_count = t->group_count; v.group_radius = t->group_radius;
+    v.group_order = t->group_order;
     v.n_groups = t->n_groups;
     return v;
 }
@@ -256,10 +257,11 @@ __global__ void __launch_bounds__(TRAV_WARPS * 32) k_traverse_l2(
     PoolCursor pc{-1, POOL_CHUNK, 0, 0};
     for (;;) {
         // groups are taken dynamically: their walks differ widely in length
-        int g = 0;
-        if (lane == 0) g = atomicAdd(next_group, 1);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= tv.n_groups) break;
+        int gi = 0;
+        if (lane == 0) gi = atomicAdd(next_group, 1);
+        gi = __shfl_sync(0xffffffffu, gi, 0);
+        if (gi >= tv.n_groups) break;
+        const int g = tv.group_order[gi];
         const float4 *crow = reinterpret_cast<const float4 *>(tv.pts + (size_t)tv.group_begin[g] * tv.dp);
         for (int k = lane; k < nq4; k += 32) cen[k] = crow[k];
         __syncwarp();
@@ -285,10 +287,11 @@ __global__ void __launch_bounds__(32) k_traverse_lev(
     unsigned long long evals = 0;
     PoolCursor pc{-1, POOL_CHUNK, 0, 0};
     for (;;) {
-        int g = 0;
-        if (lane == 0) g = atomicAdd(next_group, 1);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= tv.n_groups) break;
+        int gi = 0;
+        if (lane == 0) gi = atomicAdd(next_group, 1);
+        gi = __shfl_sync(0xffffffffu, gi, 0);
+        if (gi >= tv.n_groups) break;
+        const int g = tv.group_order[gi];
         int cpos = tv.group_begin[g];
         const uint8_t *pat = tv.sdata + tv.soff[cpos];
         int m = (int)(tv.soff[cpos + 1] - tv.soff[cpos]);
@@ -526,15 +529,16 @@ __device__ __forceinline__ void tile_sqdist_smem(const float4 *Qs, const float4 
 // The same squared distance for one pair, scalar, in the same operation order
 // as the tiles (per 16 coordinates: x and z terms into one FMA chain, y and w
 // into another; chain sums added; chunk sums added into the total), so that
-// its decisions equal the tiles' bit for bit.
-__device__ __forceinline__ float pair_sqdist(const float4 *__restrict__ x, const float4 *__restrict__ y, int nq4) {
+// its decisions equal the tiles' bit for bit.  x may point to shared or
+// global memory (generic loads); y is a global row.
+__device__ __forceinline__ float pair_sqdist(const float4 *x, const float4 *__restrict__ y, int nq4) {
     float tot = 0.f;
     int k = 0;
     for (; k + 4 <= nq4; k += 4) {
         float lo = 0.f, hi = 0.f;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const float4 a = __ldg(x + k + u), b = __ldg(y + k + u);
+            const float4 a = x[k + u], b = __ldg(y + k + u);
             const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
             lo = fmaf(dx, dx, lo);
             hi = fmaf(dy, dy, hi);
@@ -546,7 +550,39 @@ __device__ __forceinline__ float pair_sqdist(const float4 *__restrict__ x, const
     if (k < nq4) {
         float lo = 0.f, hi = 0.f;
         for (; k < nq4; ++k) {
-            const float4 a = __ldg(x + k), b = __ldg(y + k);
+            const float4 a = x[k], b = __ldg(y + k);
+            const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
+            lo = fmaf(dx, dx, lo);
+            hi = fmaf(dy, dy, hi);
+            lo = fmaf(dz, dz, lo);
+            hi = fmaf(dw, dw, hi);
+        }
+        tot += lo + hi;
+    }
+    return tot;
+}
+
+// pair_sqdist with both rows in shared memory (plain loads).
+__device__ __forceinline__ float pair_sqdist_smem(const float4 *x, const float4 *y, int nq4) {
+    float tot = 0.f;
+    int k = 0;
+    for (; k + 4 <= nq4; k += 4) {
+        float lo = 0.f, hi = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 a = x[k + u], b = y[k + u];
+            const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
+            lo = fmaf(dx, dx, lo);
+            hi = fmaf(dy, dy, hi);
+            lo = fmaf(dz, dz, lo);
+            hi = fmaf(dw, dw, hi);
+        }
+        tot += lo + hi;
+    }
+    if (k < nq4) {
+        float lo = 0.f, hi = 0.f;
+        for (; k < nq4; ++k) {
+            const float4 a = x[k], b = y[k];
             const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
             lo = fmaf(dx, dx, lo);
             hi = fmaf(dy, dy, hi);
@@ -573,6 +609,7 @@ struct LeafShared {
     uint8_t gq[GQ_CAP], gb[GQ_CAP];
     int gn, nb_fill, scan_tmp[LEAF_T / 32];
     int64_t next_ci;
+    int tpre[33];  // emit pass: pairs per row of the current tile (exclusive prefix)
 };
 constexpr size_t kLeafSmem = sizeof(LeafShared);
 
@@ -803,8 +840,8 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int i = 4 * lane + k;
-                    if (EMIT) loc[k] = i < bn ? __popc(S.bmask[i] & qvalid) * S.bcnt[i] : 0;
-                    else loc[k] = (i < bn && S.bmask[i] != 0u) ? S.bcnt[i] : 0;
+                    if (EMIT && nkc > 1) loc[k] = i < bn ? __popc(S.bmask[i] & qvalid) * S.bcnt[i] : 0;
+                    else loc[k] = (i < bn && (S.bmask[i] & qvalid) != 0u) ? S.bcnt[i] : 0;
                     sum += loc[k];
                 }
                 int incl = sum;
@@ -825,60 +862,59 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
             const int T = S.bpre[NB];
 
             // ---- emit pass: one thread per (query, point) pair of the blocks in
-            // which the query found an edge; same arithmetic as the tiles
-            if (EMIT) {
+            // which the query found an edge; same arithmetic as the tiles;
+            // guard-band pairs go through the FP64 queue
+            if (EMIT && nkc > 1) {
                 for (int r0 = 0; r0 < T; r0 += LEAF_T) {
                     const int r = r0 + tid;
-                    if (r >= T) continue;
-                    int lo = 0, hi = NB;
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (S.bpre[mid] <= r) lo = mid; else hi = mid;
+                    if (r < T) {
+                        int lo = 0, hi = NB;
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (S.bpre[mid] <= r) lo = mid; else hi = mid;
+                        }
+                        const int idx = r - S.bpre[lo], cnt = S.bcnt[lo];
+                        const int qr = idx / cnt, pidx = idx - qr * cnt;
+                        const int q = (int)__fns(S.bmask[lo] & qvalid, 0u, qr + 1);
+                        const int qpos = qfirst + q, ppos = S.bbeg[lo] + pidx;
+                        if (qpos != ppos || qp.include_self) {
+                            ++pairs;
+                            const float4 *qrow = reinterpret_cast<const float4 *>(tv.pts + (size_t)qpos * dp);
+                            const float sv = pair_sqdist(qrow, reinterpret_cast<const float4 *>(tv.pts + (size_t)ppos * dp),
+                                                         dp >> 2);
+                            int edge;
+                            if (qp.mode == 0) edge = sv < qp.lo2 ? 1 : (sv > qp.hi2 ? 0 : -1);
+                            else if (qp.mode == 1) edge = sv == 0.0f;
+                            else if (qp.mode == 3) edge = 1;
+                            else edge = -1;
+                            if (edge < 0) {
+                                const int slot = atomicAdd(&S.gn, 1);
+                                S.gpos[slot] = ppos;
+                                S.gq[slot] = (uint8_t)q;
+                                S.gb[slot] = (uint8_t)lo;
+                            } else if (edge) {
+                                const int slot = atomicAdd(&rowcur[S.cursor[q]], 1);
+                                const int64_t at = S.rowb[q] + slot;
+                                if (at < S.rowe[q]) {
+                                    col[at] = tv.perm[ppos];
+                                    dist[at] = fp32_dist_ok ? sqrtf(sv)
+                                                            : (float)sqrt(sq_l2_exact(tv.pts + (size_t)qpos * dp,
+                                                                                      tv.pts + (size_t)ppos * dp, dim));
+                                } else {
+                                    atomicOr(err, 4);
+                                }
+                            }
+                        }
                     }
-                    const int idx = r - S.bpre[lo], cnt = S.bcnt[lo];
-                    const int qr = idx / cnt, pidx = idx - qr * cnt;
-                    const int q = (int)__fns(S.bmask[lo] & qvalid, 0u, qr + 1);
-                    const int qpos = qfirst + q, ppos = S.bbeg[lo] + pidx;
-                    if (qpos == ppos && !qp.include_self) continue;
-                    const float sv = pair_sqdist(reinterpret_cast<const float4 *>(tv.pts + (size_t)qpos * dp),
-                                                 reinterpret_cast<const float4 *>(tv.pts + (size_t)ppos * dp), dp >> 2);
-                    int edge;
-                    float dv = 0.f;
-                    bool exact = false;
-                    if (qp.mode == 0) {
-                        if (sv < qp.lo2) edge = 1;
-                        else if (sv > qp.hi2) edge = 0;
-                        else exact = true;
-                    } else if (qp.mode == 1) {
-                        edge = sv == 0.0f;
-                    } else if (qp.mode == 3) {
-                        edge = 1;
-                    } else {
-                        exact = true;
-                    }
-                    if (exact) {
-                        const double s64 = sq_l2_exact(tv.pts + (size_t)qpos * dp, tv.pts + (size_t)ppos * dp, dim);
-                        edge = s64 <= qp.eps2_64;
-                        dv = (float)sqrt(s64);
-                    } else if (edge) {
-                        dv = fp32_dist_ok ? sqrtf(sv)
-                                          : (float)sqrt(sq_l2_exact(tv.pts + (size_t)qpos * dp,
-                                                                    tv.pts + (size_t)ppos * dp, dim));
-                    }
-                    if (!edge) continue;
-                    const int slot = atomicAdd(&rowcur[S.cursor[q]], 1);
-                    const int64_t at = S.rowb[q] + slot;
-                    if (at < S.rowe[q]) {
-                        col[at] = tv.perm[ppos];
-                        dist[at] = dv;
-                    } else {
-                        atomicOr(err, 4);
-                    }
+                    __syncthreads();
+                    if (S.gn >= 64) drain(false);
                 }
             }
 
-            // ---- stage 2 (count pass): packed points of the surviving blocks
-            for (int R0 = 0; !EMIT && R0 < T; R0 += RCAP) {
+            // ---- stage 2: packed points of the surviving blocks (count pass: dense
+            // 32 x 32 tiles; emit pass: only the (query, row) pairs of each tile
+            // whose block holds an edge of the query)
+            for (int R0 = 0; (!EMIT || nkc == 1) && R0 < T; R0 += RCAP) {
                 const int RN = min(RCAP, T - R0);
                 __syncthreads();
                 for (int r = tid; r < RN; r += LEAF_T) {
@@ -902,9 +938,63 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
                         cp_async_wait<0>();
                     }
                     __syncthreads();
+                    const int npr = min(32, RN - 32 * t);
+                    if (EMIT) {
+                        // pairs of this tile: row r pairs with the queries of its block's mask
+                        if (warp == 0) {
+                            const int c = lane < npr ? __popc(S.bmask[S.rli[32 * t + lane]] & qvalid) : 0;
+                            int incl = c;
+#pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                int y = __shfl_up_sync(0xffffffffu, incl, o);
+                                if (lane >= o) incl += y;
+                            }
+                            S.tpre[lane] = incl - c;
+                            if (lane == 31) S.tpre[32] = incl;
+                        }
+                        __syncthreads();
+                        const int TP = S.tpre[32];
+                        const float4 *Pb = S.Ps[t & 1];
+                        for (int pi = tid; pi < TP; pi += LEAF_T) {
+                            int lo = 0, hi = 32;
+                            while (hi - lo > 1) {
+                                const int mid = (lo + hi) >> 1;
+                                if (S.tpre[mid] <= pi) lo = mid; else hi = mid;
+                            }
+                            const int r = 32 * t + lo;
+                            const int li = S.rli[r];
+                            const int q = (int)__fns(S.bmask[li] & qvalid, 0u, pi - S.tpre[lo] + 1);
+                            const int qpos = qfirst + q, ppos = S.rpos[r];
+                            if (qpos == ppos && !qp.include_self) continue;
+                            ++pairs;
+                            const float sv = pair_sqdist_smem(S.Qs + q * KS4, Pb + lo * KS4, kq);
+                            int edge;
+                            if (qp.mode == 0) edge = sv < qp.lo2 ? 1 : (sv > qp.hi2 ? 0 : -1);
+                            else if (qp.mode == 1) edge = sv == 0.0f;
+                            else if (qp.mode == 3) edge = 1;
+                            else edge = -1;
+                            if (edge < 0) {
+                                const int slot = atomicAdd(&S.gn, 1);
+                                S.gpos[slot] = ppos;
+                                S.gq[slot] = (uint8_t)q;
+                                S.gb[slot] = (uint8_t)li;
+                            } else if (edge) {
+                                const int slot = atomicAdd(&rowcur[S.cursor[q]], 1);
+                                const int64_t at = S.rowb[q] + slot;
+                                if (at < S.rowe[q]) {
+                                    col[at] = tv.perm[ppos];
+                                    dist[at] = sqrtf(sv);
+                                } else {
+                                    atomicOr(err, 4);
+                                }
+                            }
+                        }
+                        __syncthreads();
+                        if (S.gn >= 64) drain(false);
+                        continue;
+                    }
                     float tot[2][4];
                     compute(t, t & 1, S.rpos, RN, tot);
-                    const int npr = min(32, RN - 32 * t);
                     uint32_t hitrow = 0u;
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
@@ -994,16 +1084,18 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
             }
         }
     }
-    if (!EMIT) {
-        for (int o = 16; o > 0; o >>= 1) {
-            pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
-            s1evals += __shfl_xor_sync(0xffffffffu, s1evals, o);
-            guard += __shfl_xor_sync(0xffffffffu, guard, o);
-        }
-        if ((tid & 31) == 0) {
+    for (int o = 16; o > 0; o >>= 1) {
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        s1evals += __shfl_xor_sync(0xffffffffu, s1evals, o);
+        guard += __shfl_xor_sync(0xffffffffu, guard, o);
+    }
+    if ((tid & 31) == 0) {
+        if (!EMIT) {
             stat_add(st, ST_PAIRS, pairs);
             stat_add(st, ST_TRAV, s1evals);
             stat_add(st, ST_GUARD, guard);
+        } else {
+            stat_add(st, ST_EMIT, pairs);
         }
     }
 }
@@ -1622,6 +1714,7 @@ void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &
     out.stats.leaf_pairs = (int64_t)hs[ST_PAIRS];
     out.stats.guard_fp64 = (int64_t)hs[ST_GUARD];
     out.stats.recheck_fp32 = (int64_t)hs[ST_RECHECK];
+    out.stats.emit_pairs = (int64_t)hs[ST_EMIT];
     out.stats.candidates = n_cand;
 }
 

@@ -59,7 +59,7 @@ class ct_csr(C.Structure):
 class ct_query_stats(C.Structure):
     _fields_ = [(f, C.c_int64) for f in ("traversal_evals", "leaf_pairs", "guard_fp64",
                                            "recheck_fp32", "candidates", "overflow_rows",
-                                           "kernel_launches", "reserved")]
+                                           "kernel_launches", "emit_pairs")]
 
 
 def library_path() -> str:
@@ -217,7 +217,7 @@ class CSR:
     def stats(self) -> dict:
         st = ct_query_stats()
         _check(_load().ct_csr_stats(C.byref(self.c), C.byref(st)))
-        return {f: int(getattr(st, f)) for f, _ in ct_query_stats._fields_ if f != "reserved"}
+        return {f: int(getattr(st, f)) for f, _ in ct_query_stats._fields_}
 
     def to_numpy(self) -> dict:
         return {"row_ptr": self.row_ptr.cpu().numpy(), "col": self.col.cpu().numpy(),
