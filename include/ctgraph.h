@@ -214,6 +214,14 @@ ct_status ct_profile_entry(int32_t i, const char **name, double *total_ms, int64
 /* Number of kernels this library has launched in this process so far. */
 int64_t ct_kernel_launches(void);
 
+/* Tensor-core self-test (a diagnostic; the paper has none): D = A * B^T for
+ * A (128 x 128) and B (32 x 128) bf16 row-major device matrices and D
+ * (128 x 32) fp32 row-major device output, through one tcgen05 BF16 MMA chain
+ * with the accumulator in tensor memory -- the primitive of the precision-1
+ * leaf filter.  Synchronises `stream`.  CT_ETIMEOUT if the bounded wait for
+ * the MMA's completion gives up. */
+ct_status ct_selftest_tc_gemm(const void *A, const void *B, float *D, ct_stream stream);
+
 /* Thread-local message for the last non-OK status of this thread. */
 const char *ct_last_error(void);
 

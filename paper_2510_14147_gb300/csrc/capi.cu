@@ -15,6 +15,7 @@ void query_predicted(const ct_tree *t, const QParams &qp, const void *predictor,
 void query_batched(int n_clouds, const ct_tree *const *trees, const QParams *qps, const ct_query_opts *opts,
                    cudaStream_t s, QueryOut *outs);
 void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cudaStream_t s);
+void tc_selftest(const void *A, const void *B, float *D, cudaStream_t s);
 }  // namespace ct
 
 namespace {
@@ -183,6 +184,13 @@ ct_status eps_graph_degrees_noalloc(const ct_tree *tree, double eps, int32_t inc
         check_device(tree);
         ct::QParams qp = ct::make_qparams(tree, eps, include_self);
         ct::degrees_noalloc(tree, qp, degrees, (cudaStream_t)stream);
+    });
+}
+
+ct_status ct_selftest_tc_gemm(const void *A, const void *B, float *D, ct_stream stream) {
+    return guarded([&] {
+        if (!A || !B || !D) CT_FAIL(CT_EINVAL, "NULL argument");
+        ct::tc_selftest(A, B, D, (cudaStream_t)stream);
     });
 }
 

@@ -25,6 +25,7 @@
 #include "lev.cuh"
 #include "profile.cuh"
 #include "query.cuh"
+#include "tc.cuh"
 
 namespace ct {
 
@@ -1127,6 +1128,337 @@ __global__ void k_check_rows(int64_t n, const int64_t *__restrict__ row_ptr, con
     if (i < n && row_ptr[i] + rowcur[i] != row_ptr[i + 1]) atomicOr(err, 8);
 }
 
+// ---------------------------------------------------------------------------
+// Precision 1: BF16 tensor-core filter, FP32 recheck, FP64 guard band.
+//
+// Count pass per work item: the group's queries (B, N = 32) and 128-row tiles
+// of packed candidate points (A, M = 128) are centred on the group centre c,
+// rounded to bf16 and multiplied by tcgen05 MMAs (K = 16 per instruction) into
+// a 128 x 32 fp32 accumulator in tensor memory.  With x~ = x - c, y~ = y - c
+// (fp32) and x^ = bf16(x~), y^ = bf16(y~):
+//   |x^_k - x~_k| <= 2^-9 |x~_k|, so ||x^ - y^|| <= d(x, y) + 2^-8.9 (|x~| + |y~|);
+//   d^2 = |x^|^2 + |y^|^2 - 2 x^.y^ is formed from exact bf16 products with fp32
+//   sums, |d^2 - ||x^ - y^||^2| <= 2^-12 (|x~|^2 + |y~|^2) (sums of 128 terms
+//   with a few ulps per addition, generously).
+// A pair is kept iff d^2 <= (eps + 2^-8 (|x~| + |y~|))^2 + 2^-12 (|x~|^2 + |y~|^2),
+// which keeps every edge.  Kept pairs are decided like the FP32 path: the
+// canonical fp32 direct-difference sum outside the guard band, FP64 inside it.
+// The emit pass is the FP32 path's, driven by the same per-block edge masks.
+constexpr int TC_ROWS = 128;
+constexpr float TC_REL = 0x1p-8f, TC_ABS2 = 0x1p-12f;
+
+struct __align__(1024) TcShared {
+    unsigned char A[TC_ROWS * 256];  // bf16 candidate rows, core-matrix layout
+    unsigned char B[32 * 256];       // bf16 query rows
+    float4 Qf[32 * KS4];             // fp32 query rows (recheck)
+    float4 cen[32];                  // group centre
+    float qn2[32], qabs[32];
+    float pn2[TC_ROWS], pabs[TC_ROWS];
+    int rpos[TC_ROWS];
+    uint8_t rli[TC_ROWS];
+    int bbeg[NB], bcnt[NB], bpre[NB + 1];
+    uint32_t bem[NB];
+    int qcnt[32];
+    int gpos[GQ_CAP];
+    uint8_t gq[GQ_CAP], gb[GQ_CAP];
+    int gn;
+    uint32_t tslot;
+    uint64_t mbar;
+};
+constexpr size_t kTcSmem = sizeof(TcShared) + 1024;
+
+// Thread-per-row conversion of a whole row (dp4 float4, zero beyond) to
+// centred bf16 in the core-matrix layout; returns both squared norms.  Eight
+// loads are kept in flight.
+__device__ __forceinline__ void tc_convert_row_thread(unsigned char *tile, int r, const float4 *__restrict__ row,
+                                                      const float4 *cen, int dp4, bool valid, float &n2, float &a2) {
+    float bn = 0.f, an = 0.f;
+#pragma unroll
+    for (int k0 = 0; k0 < 32; k0 += 8) {
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + u;
+            v[u] = (valid && k < dp4) ? __ldg(row + k) : cen[k];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            const int k = k0 + u;
+            const float4 c0 = cen[k], c1 = cen[k + 1];
+            const float x0 = v[u].x - c0.x, x1 = v[u].y - c0.y, x2 = v[u].z - c0.z, x3 = v[u].w - c0.w;
+            const float x4 = v[u + 1].x - c1.x, x5 = v[u + 1].y - c1.y, x6 = v[u + 1].z - c1.z,
+                        x7 = v[u + 1].w - c1.w;
+            const __nv_bfloat162 b01 = __floats2bfloat162_rn(x0, x1), b23 = __floats2bfloat162_rn(x2, x3);
+            const __nv_bfloat162 b45 = __floats2bfloat162_rn(x4, x5), b67 = __floats2bfloat162_rn(x6, x7);
+            uint4 pk;
+            pk.x = *reinterpret_cast<const uint32_t *>(&b01);
+            pk.y = *reinterpret_cast<const uint32_t *>(&b23);
+            pk.z = *reinterpret_cast<const uint32_t *>(&b45);
+            pk.w = *reinterpret_cast<const uint32_t *>(&b67);
+            *reinterpret_cast<uint4 *>(tile + tc::core_offset(r, k >> 1)) = pk;
+            const float2 f01 = __bfloat1622float2(b01), f23 = __bfloat1622float2(b23);
+            const float2 f45 = __bfloat1622float2(b45), f67 = __bfloat1622float2(b67);
+            bn = fmaf(f01.x, f01.x, bn); bn = fmaf(f01.y, f01.y, bn);
+            bn = fmaf(f23.x, f23.x, bn); bn = fmaf(f23.y, f23.y, bn);
+            bn = fmaf(f45.x, f45.x, bn); bn = fmaf(f45.y, f45.y, bn);
+            bn = fmaf(f67.x, f67.x, bn); bn = fmaf(f67.y, f67.y, bn);
+            an = fmaf(x0, x0, an); an = fmaf(x1, x1, an); an = fmaf(x2, x2, an); an = fmaf(x3, x3, an);
+            an = fmaf(x4, x4, an); an = fmaf(x5, x5, an); an = fmaf(x6, x6, an); an = fmaf(x7, x7, an);
+        }
+    }
+    n2 = bn;
+    a2 = an;
+}
+
+__global__ void __launch_bounds__(LEAF_T, 3) k_leaf_tc(TreeView tv, QParams qp, Items items,
+                                                    const uint32_t *__restrict__ cand, uint32_t *__restrict__ emask,
+                                                    int32_t *__restrict__ deg, unsigned long long *__restrict__ st,
+                                                    int32_t *__restrict__ err) {
+    extern __shared__ unsigned char tc_raw[];
+    TcShared &S = *reinterpret_cast<TcShared *>(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+    const int it = blockIdx.x;
+    if (it >= *items.count) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = items.group[it];
+    const int dp = tv.dp, dim = tv.dim, dp4 = dp >> 2;
+    const int ksteps = (dp + 15) >> 4;
+    const int qb = tv.group_begin[g], qn = tv.group_count[g];
+    const int64_t c0 = items.begin[it], c1 = items.end[it];
+    unsigned long long pairs = 0, kept = 0, guard = 0;
+    bool failed = false;
+
+    if (warp == 0) tc::tmem_alloc(&S.tslot, 32);
+    if (tid == 0) tc::mbar_init(&S.mbar, 1);
+    if (tid < 32) S.cen[tid] = tid < dp4 ? __ldg(reinterpret_cast<const float4 *>(tv.pts + (size_t)qb * dp) + tid)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = S.tslot;
+    const uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, 32);
+    uint32_t phase = 0;
+
+    for (int q0 = 0; q0 < qn && !failed; q0 += 32) {
+        const int nqr = min(32, qn - q0);
+        const int qfirst = qb + q0;
+        __syncthreads();
+        // queries: fp32 copy (recheck) by all threads, bf16 conversion by thread q
+        for (int i = tid; i < 32 * 32; i += LEAF_T) {
+            const int q = i >> 5, k = i & 31;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q < nqr && k < dp4) v = __ldg(reinterpret_cast<const float4 *>(tv.pts + (size_t)(qfirst + q) * dp) + k);
+            S.Qf[q * KS4 + k] = v;
+        }
+        if (tid < 32) {
+            const int q = tid;
+            float n2, a2;
+            tc_convert_row_thread(S.B, q, reinterpret_cast<const float4 *>(tv.pts + (size_t)(qfirst + min(q, nqr - 1)) * dp),
+                                  S.cen, dp4, q < nqr, n2, a2);
+            S.qn2[q] = n2;
+            S.qabs[q] = sqrtf(a2);
+            S.qcnt[q] = 0;
+        }
+        if (tid == 0) S.gn = 0;
+
+        auto drain = [&](bool all) {
+            __syncthreads();
+            const int n = S.gn;
+            const int m = all ? n : (n & ~31);
+            for (int i = tid; i < m; i += LEAF_T) {
+                const int q = S.gq[i], ppos = S.gpos[i], li = S.gb[i];
+                ++guard;
+                const double s64 = sq_l2_exact(tv.pts + (size_t)(qfirst + q) * dp, tv.pts + (size_t)ppos * dp, dim);
+                if (s64 <= qp.eps2_64) {
+                    atomicAdd(&S.qcnt[q], 1);
+                    atomicOr(&S.bem[li], 1u << q);
+                }
+            }
+            __syncthreads();
+            const int rest = n - m;
+            int rp = 0, rq = 0, rb = 0;
+            if (tid < rest) {
+                rp = S.gpos[m + tid];
+                rq = S.gq[m + tid];
+                rb = S.gb[m + tid];
+            }
+            __syncthreads();
+            if (tid < rest) {
+                S.gpos[tid] = rp;
+                S.gq[tid] = (uint8_t)rq;
+                S.gb[tid] = (uint8_t)rb;
+            }
+            if (tid == 0) S.gn = rest;
+            __syncthreads();
+        };
+
+        for (int64_t b0 = c0; b0 < c1 && !failed; b0 += NB) {
+            const int bn = (int)((c1 - b0) < NB ? (c1 - b0) : NB);
+            __syncthreads();
+            for (int i = tid; i < NB; i += LEAF_T) {
+                int beg = 0, cnt = 0;
+                if (i < bn) {
+                    const int v = (int)cand[b0 + i];
+                    beg = tv.node_begin[v];
+                    cnt = tv.node_count[v];
+                }
+                S.bbeg[i] = beg;
+                S.bcnt[i] = cnt;
+                S.bem[i] = 0u;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                int loc[4], sum = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    loc[k] = S.bcnt[4 * lane + k];
+                    sum += loc[k];
+                }
+                int incl = sum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                int run = incl - sum;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    S.bpre[4 * lane + k] = run;
+                    run += loc[k];
+                }
+                if (lane == 31) S.bpre[NB] = incl;
+            }
+            __syncthreads();
+            const int T = S.bpre[NB];
+            for (int R0 = 0; R0 < T && !failed; R0 += TC_ROWS) {
+                const int rows = min(TC_ROWS, T - R0);
+                // row -> (position, block) for this tile
+                {
+                    const int r = tid;
+                    if (r < rows) {
+                        const int R = R0 + r;
+                        int lo = 0, hi = NB;
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (S.bpre[mid] <= R) lo = mid; else hi = mid;
+                        }
+                        S.rpos[r] = S.bbeg[lo] + (R - S.bpre[lo]);
+                        S.rli[r] = (uint8_t)lo;
+                    }
+                }
+                __syncthreads();
+                // A tile: thread r converts row r
+                {
+                    const int r = tid;
+                    const bool valid = r < rows;
+                    float n2, a2;
+                    tc_convert_row_thread(S.A, r,
+                                          reinterpret_cast<const float4 *>(tv.pts + (size_t)(valid ? S.rpos[r] : qb) * dp),
+                                          S.cen, dp4, valid, n2, a2);
+                    S.pn2[r] = n2;
+                    S.pabs[r] = sqrtf(a2);
+                }
+                tc::fence_smem_to_async();
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+                if (tid == 0) {
+                    for (int ks = 0; ks < ksteps; ++ks) {
+                        const uint64_t ad = tc::smem_desc(tc::smem_u32(S.A) + ks * 256, tc::kLBO, tc::kSBO);
+                        const uint64_t bd = tc::smem_desc(tc::smem_u32(S.B) + ks * 256, tc::kLBO, tc::kSBO);
+                        tc::mma_bf16(tmem, ad, bd, idesc, ks > 0);
+                    }
+                    tc::mma_commit(&S.mbar);
+                }
+                const bool ok = tc::mbar_wait(&S.mbar, phase, 1u << 22);
+                phase ^= 1u;
+                if (!__syncthreads_and(ok)) {
+                    if (tid == 0) atomicOr(err, 32);
+                    failed = true;
+                    break;
+                }
+                tc::fence_after_sync();
+                float dot[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), dot);
+                const int r = 32 * warp + lane;
+                if (r < rows) {
+                    const int ppos = S.rpos[r], li = S.rli[r];
+                    const float pa = S.pabs[r], pn = S.pn2[r];
+                    uint32_t keepm = 0u, validm = 0u;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        if (q >= nqr) continue;
+                        if (qfirst + q == ppos && !qp.include_self) continue;
+                        validm |= 1u << q;
+                        const float qa = S.qabs[q];
+                        const float d2 = fmaf(-2.0f, dot[q], S.qn2[q] + pn);
+                        const float e = fmaf(TC_REL, qa + pa, qp.eps_up);
+                        const float bound = fmaf(e, e, TC_ABS2 * fmaf(qa, qa, pa * pa)) + 0x1p-60f;
+                        if (!(d2 > bound)) keepm |= 1u << q;  // NaN keeps the pair
+                    }
+                    pairs += __popc(validm);
+                    kept += __popc(keepm);
+                    while (keepm) {
+                        const int q = __ffs(keepm) - 1;
+                        keepm &= keepm - 1u;
+                        const float sv = pair_sqdist(S.Qf + q * KS4,
+                                                     reinterpret_cast<const float4 *>(tv.pts + (size_t)ppos * dp), dp4);
+                        int edge;
+                        if (qp.mode == 0) edge = sv < qp.lo2 ? 1 : (sv > qp.hi2 ? 0 : -1);
+                        else if (qp.mode == 1) edge = sv == 0.0f;
+                        else if (qp.mode == 3) edge = 1;
+                        else edge = -1;
+                        if (edge < 0) {
+                            const int slot = atomicAdd(&S.gn, 1);
+                            if (slot < GQ_CAP) {
+                                S.gpos[slot] = ppos;
+                                S.gq[slot] = (uint8_t)q;
+                                S.gb[slot] = (uint8_t)li;
+                            } else {  // queue full (many pairs at eps): decide here
+                                atomicSub(&S.gn, 1);
+                                ++guard;
+                                const double s64 = sq_l2_exact(tv.pts + (size_t)(qfirst + q) * dp,
+                                                               tv.pts + (size_t)ppos * dp, dim);
+                                if (s64 <= qp.eps2_64) {
+                                    atomicAdd(&S.qcnt[q], 1);
+                                    atomicOr(&S.bem[li], 1u << q);
+                                }
+                            }
+                        } else if (edge) {
+                            atomicAdd(&S.qcnt[q], 1);
+                            atomicOr(&S.bem[li], 1u << q);
+                        }
+                    }
+                }
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+                if (S.gn >= 64) drain(false);
+            }
+            if (failed) break;
+            drain(true);
+            if (emask)
+                for (int i = tid; i < bn; i += LEAF_T) emask[b0 + i] = qn <= 32 ? S.bem[i] : ~0u;
+        }
+        __syncthreads();
+        if (!failed && tid < nqr && S.qcnt[tid]) atomicAdd(&deg[tv.perm[qfirst + tid]], S.qcnt[tid]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        kept += __shfl_xor_sync(0xffffffffu, kept, o);
+        guard += __shfl_xor_sync(0xffffffffu, guard, o);
+    }
+    if (lane == 0) {
+        stat_add(st, ST_PAIRS, pairs);
+        stat_add(st, ST_RECHECK, kept);
+        stat_add(st, ST_GUARD, guard);
+    }
+    if (failed) tc::mbar_wait(&S.mbar, phase ^ 1u, 1u << 22);  // let an outstanding MMA finish
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 32);
+}
+
 // Dynamic shared memory of the L2 leaf kernel (set once per process).
 void leaf_l2_prepare() {
     static bool done = false;
@@ -1559,7 +1891,7 @@ void launch_traversal(const ct_tree *t, const TreeView &tv, const QParams &qp, c
     CT_LAUNCH_CHECK();
 }
 
-void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out) {
+void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out, int precision) {
     const int64_t n = t->n;
     const int G = t->n_groups;
     const bool l2 = t->metric == CT_L2_F32;
@@ -1680,7 +2012,22 @@ void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &
         CT_COUNT_LAUNCH();
         CT_LAUNCH_CHECK();
     };
-    {
+    // the tensor-core filter applies to L2 rows of at most 128 floats; wider
+    // rows use the FP32 tiles (same output)
+    const bool use_tc = precision == 1 && l2 && t->dp <= 128;
+    if (use_tc) {
+        ProfScope ps("leaf_count_tc", s);
+        static bool tc_ready = false;
+        if (!tc_ready) {
+            CT_CHECK_CUDA(cudaFuncSetAttribute(k_leaf_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+            tc_ready = true;
+        }
+        if (G && nseg) {
+            k_leaf_tc<<<(unsigned)max_items, LEAF_T, kTcSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, st.p, err);
+            CT_COUNT_LAUNCH();
+            CT_LAUNCH_CHECK();
+        }
+    } else {
         ProfScope ps("leaf_count", s);
         leaf(false, nullptr, nullptr, nullptr);
     }
@@ -1716,6 +2063,14 @@ void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &
     out.stats.recheck_fp32 = (int64_t)hs[ST_RECHECK];
     out.stats.emit_pairs = (int64_t)hs[ST_EMIT];
     out.stats.candidates = n_cand;
+}
+
+void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out) {
+    query_impl(t, qp, s, out, 0);
+}
+
+void query_tc(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out) {
+    query_impl(t, qp, s, out, 1);
 }
 
 }  // namespace ct

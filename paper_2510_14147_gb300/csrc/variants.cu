@@ -4,10 +4,7 @@
 
 namespace ct {
 
-void query_tc(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out) {
-    (void)t; (void)qp; (void)s; (void)out;
-    CT_FAIL(CT_EUNSUPPORTED, "precision 1 is not available in this build");
-}
+void query_tc(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out);
 
 void query_predicted(const ct_tree *t, const QParams &qp, const void *predictor, int precision,
                      cudaStream_t s, QueryOut &out) {

@@ -107,6 +107,8 @@ def _load():
         lib.ct_profile_entry.argtypes = [C.c_int32, P(C.c_char_p), P(C.c_double), P(C.c_int64)]
         lib.eps_graph_degrees_noalloc.restype = C.c_int
         lib.eps_graph_degrees_noalloc.argtypes = [C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p]
+        lib.ct_selftest_tc_gemm.restype = C.c_int
+        lib.ct_selftest_tc_gemm.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.ct_kernel_launches.restype = C.c_int64
         lib.ct_kernel_launches.argtypes = []
         _lib = lib
@@ -349,6 +351,19 @@ def ct_profile_read() -> dict:
 
 def ct_kernel_launches() -> int:
     return int(_load().ct_kernel_launches())
+
+
+def ct_selftest_tc_gemm(A, B, stream=None):
+    """D = A @ B.T through one tcgen05 BF16 MMA chain: A (128, 128) and B (32, 128)
+    CUDA bfloat16 tensors; returns D (128, 32) float32."""
+    import torch
+    if not (A.shape == (128, 128) and B.shape == (32, 128) and A.dtype == torch.bfloat16
+            and B.dtype == torch.bfloat16 and A.is_cuda and B.is_cuda):
+        raise ValueError("A must be (128, 128) and B (32, 128) CUDA bfloat16")
+    A, B = A.contiguous(), B.contiguous()
+    D = torch.empty(128, 32, dtype=torch.float32, device=A.device)
+    _check(_load().ct_selftest_tc_gemm(A.data_ptr(), B.data_ptr(), D.data_ptr(), C.c_void_p(_stream(stream))))
+    return D
 
 
 def version() -> str:
