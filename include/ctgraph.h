@@ -86,8 +86,11 @@ typedef struct {
  *                 1 = BF16 tensor-core filter (tcgen05) with FP32 recheck.
  *                 Both give the same edge set.
  *  use_predictor: 0 = two-pass count -> scan -> emit;
- *                 1 = one-pass emit into capacities predicted by `predictor`,
- *                     with exact recount of overflowing rows.  Same output.
+ *                 1 = one-pass emit into row capacities predicted by
+ *                     `predictor` (a fitted ct_predictor on the tree's
+ *                     device); entries past a row's capacity go to an
+ *                     overflow arena, rows that overflow the arena too are
+ *                     emitted again exactly.  Same output.
  *  include_self:  1 adds the pair (i, i) to every row (d(p, p) = 0 <= eps).
  *  predictor:     a ct_predictor* when use_predictor = 1, else NULL. */
 typedef struct {
@@ -119,9 +122,10 @@ typedef struct {
     int64_t guard_fp64;       /* pairs re-decided in FP64 (|d - eps| <= 1e-3 eps) */
     int64_t recheck_fp32;     /* pairs re-evaluated in FP32 after the BF16 filter */
     int64_t candidates;       /* (group, candidate leaf block) entries */
-    int64_t overflow_rows;    /* rows recounted after a predicted capacity overflowed */
+    int64_t overflow_rows;    /* learned form: rows whose degree exceeded the predicted capacity */
     int64_t kernel_launches;  /* kernels this library launched for the query */
     int64_t emit_pairs;       /* pairs evaluated again by the emit pass */
+    int64_t reemit_rows;      /* learned form: rows emitted again (overflow arena was full) */
 } ct_query_stats;
 
 typedef struct ct_tree ct_tree;           /* opaque, device-resident */
@@ -198,6 +202,99 @@ ct_status ct_tree_shape(const ct_tree *tree, int64_t *n_nodes, int64_t *n_points
 ct_status ct_tree_export(const ct_tree *tree, int64_t *center, double *radius, int32_t *level,
                          int64_t *child_begin, int64_t *child_count, int64_t *pts_begin,
                          int64_t *pts_count, int64_t *leaf_pts);
+
+/* ------------------------------------------------------------------------
+ * Degree/work predictor of the learned form.  The paper has no learned
+ * component: this is an extension that sizes the one-pass emit and orders the
+ * leaf work.  A small multilayer perceptron, CT_MLP_IN -> 64 -> 64 -> 2 with
+ * ReLU after both hidden layers, maps 16 features of a query, taken after the
+ * traversal (e = max(eps, 1e-20)):
+ *    0 log1p(d(q, leaf-block centre)/e)   1 log1p(d(q, group centre)/e)
+ *                                           (L2; 0 for edit distance)
+ *    2 log1p(group radius/e)              3 log2(points of the group)
+ *    4 log1p(candidate leaf blocks of the group)
+ *    5 log1p(points of those blocks)
+ *    6..11 leaf block, parent, grandparent (the root repeats):
+ *          log1p(points below), log1p(radius/e)
+ *    12..15 log1p(points below the lowest ancestor of the leaf block,
+ *          itself included, with radius >= e, 2e, 4e, 16e; the root if none)
+ * (the group: the query's run of sibling leaf blocks, at most 32 points or a
+ * single larger block; its centre is its first point) to
+ *    output 0: log(1 + degree of the query),
+ *    output 1: log(1 + points the query evaluates in the leaf stage after
+ *              the per-query leaf-centre test of Algorithm 3; for edit
+ *              distance, the group's candidate points).
+ * Inputs and targets are standardised with the mean and deviation of the
+ * training set.  Parameters are one fp32 vector, W1 (64 x 16, row-major),
+ * b1, W2 (64 x 64), b2, W3 (2 x 64), b3: CT_MLP_NPARAMS values.  Inference
+ * uses fp16 copies of the weights with fp32 sums.
+ * A predictor lives on the device that was current when it was created. */
+#define CT_MLP_IN 16
+#define CT_MLP_NPARAMS 5378
+#define CT_MLP_NORM 36  /* feature mean[16], feature std[16], target mean[2], target std[2] */
+
+typedef struct ct_predictor ct_predictor;
+
+/* Fit options (zero fields select the defaults). */
+typedef struct {
+    int32_t steps;         /* Adam steps (default 1500) */
+    int32_t batch;         /* samples per step, drawn uniformly (default 4096) */
+    float lr;              /* initial learning rate, cosine-decayed to lr/10 (default 2e-3) */
+    int32_t include_self;  /* the degrees to learn count the point itself */
+    uint64_t seed;         /* batch sampling */
+} ct_fit_opts;
+
+/* New predictor with He-initialised weights drawn from `seed`.
+ * Errors: CT_EINVAL (out NULL), CT_ENOMEM, CT_ECUDA. */
+ct_status ct_predictor_create(uint64_t seed, ct_predictor **out);
+/* Releases a predictor (synchronises its device).  NULL-safe. */
+void ct_predictor_free(ct_predictor *p);
+
+/* Labels every point of `tree` with its exact degree at `eps` and its leaf
+ * work (one traversal and one FP32 count pass of eps_graph_query), then
+ * trains on the GPU (mean squared error, Adam).  *final_loss (may be NULL) receives the
+ * mean standardised loss of the last 10% of the steps.  Synchronises `stream`.
+ * Errors: CT_EINVAL (null pointers, eps < 0 or NaN, empty tree, predictor on
+ * another device), CT_ENOMEM, CT_ECUDA. */
+ct_status ct_predictor_fit(ct_predictor *p, const ct_tree *tree, double eps, const ct_fit_opts *opts,
+                           ct_stream stream, double *final_loss);
+
+/* Row capacity of the one-pass emit: ceil(predicted degree * (1 + margin)) +
+ * pad (at most n); overflow arena: arena_frac * (sum of capacities) +
+ * arena_min entries.  Defaults 0.5, 16, 0.25, 65536.  margin >= -1, pad >= 0,
+ * arena_frac >= 0, arena_min >= 0, else CT_EINVAL. */
+ct_status ct_predictor_set_capacity(ct_predictor *p, float margin, int32_t pad, float arena_frac,
+                                    int64_t arena_min);
+
+/* Host copies of the parameters (CT_MLP_NPARAMS floats) and the
+ * standardisation (CT_MLP_NORM floats); either pointer may be NULL.  set
+ * marks the predictor fitted.  Errors: CT_EINVAL, CT_ECUDA. */
+ct_status ct_predictor_get_params(const ct_predictor *p, float *params, float *norm);
+ct_status ct_predictor_set_params(ct_predictor *p, const float *params, const float *norm);
+
+/* Raw (unstandardised) features of every point of `tree` at `eps` (runs the
+ * traversal): device fp32 [n x CT_MLP_IN], 16-byte aligned, row i for the
+ * point at tree position i (the order of ct_tree_export's leaf_pts).
+ * Errors: CT_EINVAL, CT_ENOMEM, CT_ECUDA. */
+ct_status ct_predictor_features(const ct_tree *tree, double eps, float *x, ct_stream stream);
+
+/* Predicted degree and leaf work of every point (device fp32 [n] each, by
+ * original index; either may be NULL).  Requires a fitted predictor.
+ * Errors: CT_EINVAL, CT_ENOMEM, CT_ECUDA. */
+ct_status ct_predictor_predict(const ct_predictor *p, const ct_tree *tree, double eps, float *degree,
+                               float *work, ct_stream stream);
+
+/* The perceptron itself, for checking (device buffers):
+ * ct_mlp_loss_grad: loss = (1/n) sum over samples and both outputs of
+ *   (y - t)^2 for x [n x 16], t [n x 2]; grad [CT_MLP_NPARAMS] is overwritten
+ *   with d loss / d params (fp32 kernels); *loss (host, may be NULL) gets the
+ *   loss.  Synchronises `stream`.
+ * ct_mlp_forward_f16: y [n x 2] = forward pass with the parameters rounded
+ *   to fp16 and fp32 sums (the inference kernel).
+ * Errors: CT_EINVAL (null pointers, n < 0), CT_ENOMEM, CT_ECUDA. */
+ct_status ct_mlp_loss_grad(const float *params, const float *x, const float *t, int64_t n, float *grad,
+                           double *loss, ct_stream stream);
+ct_status ct_mlp_forward_f16(const float *params, const float *x, int64_t n, float *y, ct_stream stream);
 
 /* Stage timing.  When enabled, every later ct_build / eps_graph_query call
  * records a CUDA event pair around each of its stages on the caller's stream

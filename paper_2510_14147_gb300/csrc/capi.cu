@@ -4,6 +4,7 @@
 #include <cstring>
 #include <new>
 
+#include "mlp.cuh"
 #include "query.cuh"
 
 namespace ct {
@@ -257,6 +258,155 @@ ct_status ct_tree_export(const ct_tree *tree, int64_t *center, double *radius, i
             pts_count[v] = cc[v] == 0 ? nc[v] : 0;
         }
         for (int64_t i = 0; i < n; ++i) leaf_pts[i] = perm[i];
+    });
+}
+
+ct_status ct_predictor_create(uint64_t seed, ct_predictor **out) {
+    if (out) *out = nullptr;
+    ct_predictor *p = nullptr;
+    ct_status st = guarded([&] {
+        if (!out) CT_FAIL(CT_EINVAL, "out is NULL");
+        p = new ct_predictor();
+        CT_CHECK_CUDA(cudaGetDevice(&p->device));
+        ct::predictor_init(p, seed);
+        *out = p;
+    });
+    if (st != CT_OK && p) {
+        ct::predictor_release(p);
+        delete p;
+    }
+    return st;
+}
+
+void ct_predictor_free(ct_predictor *p) {
+    if (!p) return;
+    ct::predictor_release(p);
+    delete p;
+}
+
+namespace {
+void check_predictor_device(const ct_predictor *p) {
+    int dev = -1;
+    CT_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev != p->device) CT_FAIL(CT_EINVAL, "predictor lives on device %d, current device is %d", p->device, dev);
+}
+}  // namespace
+
+ct_status ct_predictor_fit(ct_predictor *p, const ct_tree *tree, double eps, const ct_fit_opts *opts,
+                           ct_stream stream, double *final_loss) {
+    return guarded([&] {
+        if (!p || !tree) CT_FAIL(CT_EINVAL, "predictor and tree must not be NULL");
+        if (!(eps >= 0.0)) CT_FAIL(CT_EINVAL, "eps must be >= 0 (got %g)", eps);
+        if (tree->n == 0) CT_FAIL(CT_EINVAL, "cannot fit on an empty tree");
+        check_device(tree);
+        check_predictor_device(p);
+        ct_fit_opts o;
+        std::memset(&o, 0, sizeof(o));
+        if (opts) o = *opts;
+        if (o.include_self != 0 && o.include_self != 1) CT_FAIL(CT_EINVAL, "include_self must be 0 or 1");
+        if (o.steps < 0 || o.batch < 0 || !(o.lr >= 0.f)) CT_FAIL(CT_EINVAL, "steps, batch and lr must be >= 0");
+        ct::g_launches = 0;
+        const double l = ct::predictor_fit(p, tree, eps, o, (cudaStream_t)stream);
+        if (final_loss) *final_loss = l;
+    });
+}
+
+ct_status ct_predictor_set_capacity(ct_predictor *p, float margin, int32_t pad, float arena_frac,
+                                    int64_t arena_min) {
+    return guarded([&] {
+        if (!p) CT_FAIL(CT_EINVAL, "predictor is NULL");
+        if (!(margin >= -1.0f) || pad < 0 || !(arena_frac >= 0.0f) || arena_min < 0 || !std::isfinite(margin) ||
+            !std::isfinite(arena_frac))
+            CT_FAIL(CT_EINVAL, "need margin >= -1, pad >= 0, arena_frac >= 0, arena_min >= 0");
+        p->margin = margin;
+        p->pad = pad;
+        p->arena_frac = arena_frac;
+        p->arena_min = arena_min;
+    });
+}
+
+ct_status ct_predictor_get_params(const ct_predictor *p, float *params, float *norm) {
+    return guarded([&] {
+        if (!p) CT_FAIL(CT_EINVAL, "predictor is NULL");
+        check_predictor_device(p);
+        if (params) {
+            CT_CHECK_CUDA(cudaDeviceSynchronize());
+            CT_CHECK_CUDA(cudaMemcpy(params, p->w, sizeof(float) * ct::MLP_NPARAMS, cudaMemcpyDeviceToHost));
+        }
+        if (norm) {
+            std::memcpy(norm, p->fmean, sizeof(float) * ct::MLP_IN);
+            std::memcpy(norm + ct::MLP_IN, p->fstd, sizeof(float) * ct::MLP_IN);
+            std::memcpy(norm + 2 * ct::MLP_IN, p->tmean, sizeof(float) * ct::MLP_OUT);
+            std::memcpy(norm + 2 * ct::MLP_IN + ct::MLP_OUT, p->tstd, sizeof(float) * ct::MLP_OUT);
+        }
+    });
+}
+
+ct_status ct_predictor_set_params(ct_predictor *p, const float *params, const float *norm) {
+    return guarded([&] {
+        if (!p) CT_FAIL(CT_EINVAL, "predictor is NULL");
+        check_predictor_device(p);
+        if (params) {
+            CT_CHECK_CUDA(cudaDeviceSynchronize());
+            CT_CHECK_CUDA(cudaMemcpy(p->w, params, sizeof(float) * ct::MLP_NPARAMS, cudaMemcpyHostToDevice));
+            ct::mlp_to_half(p->w, p->wh, 0);
+            CT_CHECK_CUDA(cudaDeviceSynchronize());
+        }
+        if (norm) {
+            std::memcpy(p->fmean, norm, sizeof(float) * ct::MLP_IN);
+            std::memcpy(p->fstd, norm + ct::MLP_IN, sizeof(float) * ct::MLP_IN);
+            std::memcpy(p->tmean, norm + 2 * ct::MLP_IN, sizeof(float) * ct::MLP_OUT);
+            std::memcpy(p->tstd, norm + 2 * ct::MLP_IN + ct::MLP_OUT, sizeof(float) * ct::MLP_OUT);
+        }
+        p->fitted = true;
+    });
+}
+
+ct_status ct_predictor_features(const ct_tree *tree, double eps, float *x, ct_stream stream) {
+    return guarded([&] {
+        if (!tree) CT_FAIL(CT_EINVAL, "tree is NULL");
+        if (!(eps >= 0.0)) CT_FAIL(CT_EINVAL, "eps must be >= 0 (got %g)", eps);
+        if (tree->n > 0 && (!x || ((uintptr_t)x & 15))) CT_FAIL(CT_EINVAL, "x must be a 16-byte aligned device pointer");
+        check_device(tree);
+        ct::predictor_features(tree, eps, x, (cudaStream_t)stream);
+    });
+}
+
+ct_status ct_predictor_predict(const ct_predictor *p, const ct_tree *tree, double eps, float *degree, float *work,
+                               ct_stream stream) {
+    return guarded([&] {
+        if (!p || !tree) CT_FAIL(CT_EINVAL, "predictor and tree must not be NULL");
+        if (!(eps >= 0.0)) CT_FAIL(CT_EINVAL, "eps must be >= 0 (got %g)", eps);
+        if (!p->fitted) CT_FAIL(CT_EINVAL, "the predictor has not been fitted");
+        check_device(tree);
+        check_predictor_device(p);
+        ct::predictor_predict(p, tree, eps, degree, work, (cudaStream_t)stream);
+    });
+}
+
+ct_status ct_mlp_loss_grad(const float *params, const float *x, const float *t, int64_t n, float *grad,
+                           double *loss, ct_stream stream) {
+    return guarded([&] {
+        if (!params || !grad || n < 0 || (n > 0 && (!x || !t))) CT_FAIL(CT_EINVAL, "bad argument");
+        cudaStream_t s = (cudaStream_t)stream;
+        CT_CHECK_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * ct::MLP_NPARAMS, s));
+        ct::DBuf<double> acc(1, s);
+        CT_CHECK_CUDA(cudaMemsetAsync(acc.p, 0, sizeof(double), s));
+        ct::mlp_accumulate_grad(params, x, t, n, (double)(n > 0 ? n : 1), grad, acc.p, s);
+        double h = 0.0;
+        ct::to_host(&h, acc.p, 1, s);
+        if (loss) *loss = h / (double)(n > 0 ? n : 1);
+    });
+}
+
+ct_status ct_mlp_forward_f16(const float *params, const float *x, int64_t n, float *y, ct_stream stream) {
+    return guarded([&] {
+        if (!params || n < 0 || (n > 0 && (!x || !y))) CT_FAIL(CT_EINVAL, "bad argument");
+        cudaStream_t s = (cudaStream_t)stream;
+        ct::DBuf<__half> wh(ct::MLP_NPARAMS, s);
+        ct::mlp_to_half(params, wh.p, s);
+        ct::mlp_predict(wh.p, x, n, y, s);
+        CT_CHECK_CUDA(cudaStreamSynchronize(s));
     });
 }
 

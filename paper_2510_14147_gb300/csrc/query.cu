@@ -605,10 +605,11 @@ struct LeafShared {
     int rpos[RCAP];
     uint8_t rli[RCAP];
     int64_t rowb[32], rowe[32];
-    int cursor[32], qcnt[32];
+    int cursor[32], qcnt[32], qwk[32];
     int gpos[GQ_CAP];
     uint8_t gq[GQ_CAP], gb[GQ_CAP];
     int gn, nb_fill, scan_tmp[LEAF_T / 32];
+    uint32_t selm;
     int64_t next_ci;
     int tpre[33];  // emit pass: pairs per row of the current tile (exclusive prefix)
 };
@@ -635,18 +636,59 @@ struct Items {
     const int32_t *group;
     const int64_t *begin, *end;
     const int32_t *count;  // device: number of items
+    const int32_t *order;  // launch order of the items (nullptr: as built)
 };
+__device__ __forceinline__ int item_of_block(const Items &items) {
+    return items.order ? items.order[blockIdx.x] : (int)blockIdx.x;
+}
+
+// One-pass emit (learned form): the count pass also writes every edge into a
+// per-row capacity region sized from the predicted degree.  A row's entries
+// past its capacity go to an overflow arena as (row, slot, col, dist); once
+// the arena is full the row is marked lost and re-emitted exactly later.
+// off == nullptr: plain count pass.
+struct CapOut {
+    const int64_t *off;      // n + 1 capacity offsets by original id
+    int32_t *fill;           // entries produced per row (ends equal to the degree)
+    int32_t *col;
+    float *dist;             // capacity region
+    int32_t *ovf_row, *ovf_slot, *ovf_col;
+    float *ovf_dist;
+    unsigned long long *ovf_n;
+    int64_t ovf_cap;
+    uint8_t *lost;
+};
+
+__device__ __forceinline__ void cap_put(const CapOut &co, int o, int32_t c, float d) {
+    const int slot = atomicAdd(&co.fill[o], 1);
+    const int64_t b = co.off[o];
+    if (slot < co.off[o + 1] - b) {
+        co.col[b + slot] = c;
+        co.dist[b + slot] = d;
+        return;
+    }
+    const unsigned long long k = atomicAdd(co.ovf_n, 1ull);
+    if ((int64_t)k < co.ovf_cap) {
+        co.ovf_row[k] = o;
+        co.ovf_slot[k] = slot;
+        co.ovf_col[k] = c;
+        co.ovf_dist[k] = d;
+    } else {
+        co.lost[o] = 1;
+    }
+}
 
 template <bool EMIT>
 __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
     TreeView tv, QParams qp, Items items, const uint32_t *__restrict__ cand,
     uint32_t *__restrict__ emask, int32_t *__restrict__ deg, const int64_t *__restrict__ row_ptr,
     int32_t *__restrict__ rowcur, int32_t *__restrict__ col, float *__restrict__ dist,
-    unsigned long long *__restrict__ st, int32_t *__restrict__ err) {
+    unsigned long long *__restrict__ st, int32_t *__restrict__ err, CapOut co, const uint8_t *__restrict__ rowsel,
+    int32_t *__restrict__ qwork) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
-    const int it = blockIdx.x;
-    if (it >= *items.count) return;
+    if ((int)blockIdx.x >= *items.count) return;
+    const int it = item_of_block(items);
     const int g = items.group[it];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int qi = tid >> 3, pj = tid & 7;
@@ -664,14 +706,20 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
         __syncthreads();
         if (tid < 32) {
             S.qcnt[tid] = 0;
+            S.qwk[tid] = 0;
+            bool sel = false;
             if (tid < nqr) {
                 int o = tv.perm[qfirst + tid];
                 S.cursor[tid] = o;  // original id of the query (row of the CSR)
                 if (EMIT) {
                     S.rowb[tid] = row_ptr[o];
                     S.rowe[tid] = row_ptr[o + 1];
+                    sel = rowsel == nullptr || rowsel[o] != 0;
                 }
             }
+            // emit pass: queries whose rows are written (all, or the selected ones)
+            const unsigned sm = __ballot_sync(0xffffffffu, sel);
+            if (tid == 0) S.selm = sm;
         }
         if (tid == 0) S.gn = 0;
         int cnt0 = 0, cnt1 = 0;
@@ -691,6 +739,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
                     if (!EMIT) {
                         atomicAdd(&S.qcnt[q], 1);
                         atomicOr(&S.bem[li], 1u << q);
+                        if (co.off) cap_put(co, S.cursor[q], tv.perm[ppos], (float)sqrt(s64));
                     } else {
                         int slot = atomicAdd(&rowcur[S.cursor[q]], 1);
                         int64_t at = S.rowb[q] + slot;
@@ -756,7 +805,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
                     const int nf = S.nb_fill;
                     if (nf >= NB || ci >= c1) break;
                     const int64_t idx = ci + tid;
-                    const uint32_t m = idx < c1 ? emask[idx] : 0u;
+                    const uint32_t m = idx < c1 ? (emask[idx] & S.selm) : 0u;
                     const bool f = m != 0u;
                     const unsigned bal = __ballot_sync(0xffffffffu, f);
                     if (lane == 0) S.scan_tmp[warp] = __popc(bal);
@@ -861,6 +910,17 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
             }
             __syncthreads();
             const int T = S.bpre[NB];
+            // fitting the predictor: points each query evaluates after stage 1
+            if (!EMIT && qwork) {
+                for (int li = tid; li < bn; li += LEAF_T) {
+                    uint32_t m = S.bmask[li] & qvalid;
+                    while (m) {
+                        const int q = __ffs(m) - 1;
+                        m &= m - 1u;
+                        atomicAdd(&S.qwk[q], S.bcnt[li]);
+                    }
+                }
+            }
 
             // ---- emit pass: one thread per (query, point) pair of the blocks in
             // which the query found an edge; same arithmetic as the tiles;
@@ -1036,6 +1096,11 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
                             if (!EMIT) {
                                 if (i == 0) ++cnt0; else ++cnt1;
                                 hitrow |= 1u << (4 * j + i);
+                                if (co.off)
+                                    cap_put(co, S.cursor[q], tv.perm[ppos],
+                                            fp32_dist_ok ? sqrtf(sv)
+                                                         : (float)sqrt(sq_l2_exact(tv.pts + (size_t)qpos * dp,
+                                                                                   tv.pts + (size_t)ppos * dp, dim)));
                             } else {
                                 const int slot = atomicAdd(&rowcur[S.cursor[q]], 1);
                                 const int64_t at = S.rowb[q] + slot;
@@ -1083,6 +1148,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
                 if (qi + 16 < nqr && cnt1 + S.qcnt[qi + 16])
                     atomicAdd(&deg[S.cursor[qi + 16]], cnt1 + S.qcnt[qi + 16]);
             }
+            if (qwork && tid < nqr && S.qwk[tid]) atomicAdd(&qwork[S.cursor[tid]], S.qwk[tid]);
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -1127,6 +1193,90 @@ __global__ void k_check_rows(int64_t n, const int64_t *__restrict__ row_ptr, con
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && row_ptr[i] + rowcur[i] != row_ptr[i + 1]) atomicOr(err, 8);
 }
+// rowsel != nullptr: only the selected rows were written.
+__global__ void k_check_rows_sel(int64_t n, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ rowcur,
+                                 const uint8_t *__restrict__ rowsel, int32_t *__restrict__ err) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && rowsel[i] && row_ptr[i] + rowcur[i] != row_ptr[i + 1]) atomicOr(err, 8);
+}
+
+// Candidate points of every work item, and candidate blocks and points per
+// group (block per item).
+__global__ void k_item_stats(Items items, const uint32_t *__restrict__ cand, const int32_t *__restrict__ node_count,
+                             int32_t *__restrict__ ipoints, int32_t *__restrict__ gblocks,
+                             int32_t *__restrict__ gpoints) {
+    if ((int)blockIdx.x >= *items.count) return;
+    const int it = blockIdx.x;
+    const int64_t b = items.begin[it], e = items.end[it];
+    int sum = 0;
+    for (int64_t k = b + threadIdx.x; k < e; k += blockDim.x) sum += node_count[cand[k] & ~FLAG];
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    __shared__ int part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += part[w];
+        ipoints[it] = tot;
+        const int g = items.group[it];
+        atomicAdd(&gpoints[g], tot);
+        atomicAdd(&gblocks[g], (int)(e - b));
+    }
+}
+
+// One-pass emit, after the count pass: every row's produced entries must
+// equal its degree; counts rows past their capacity (cnt[0]) and lost rows
+// (cnt[1]).
+__global__ void k_cap_rows(int64_t n, const int64_t *__restrict__ row_ptr, const int64_t *__restrict__ off,
+                           const int32_t *__restrict__ fill, const uint8_t *__restrict__ lost,
+                           unsigned long long *__restrict__ cnt, int32_t *__restrict__ err) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool ov = false, ls = false;
+    if (o < n) {
+        const int64_t deg = row_ptr[o + 1] - row_ptr[o];
+        if ((int64_t)fill[o] != deg) atomicOr(err, 64);
+        ov = deg > off[o + 1] - off[o];
+        ls = lost[o] != 0;
+    }
+    const unsigned a = __ballot_sync(0xffffffffu, ov), b = __ballot_sync(0xffffffffu, ls);
+    if ((threadIdx.x & 31) == 0) {
+        if (a) atomicAdd(cnt, (unsigned long long)__popc(a));
+        if (b) atomicAdd(cnt + 1, (unsigned long long)__popc(b));
+    }
+}
+
+// Copies each kept row's capacity-region entries into the CSR (warp per row).
+__global__ void k_compact(int64_t n, const int64_t *__restrict__ row_ptr, const int64_t *__restrict__ off,
+                          const uint8_t *__restrict__ lost, const int32_t *__restrict__ ccol,
+                          const float *__restrict__ cdist, int32_t *__restrict__ col, float *__restrict__ dist) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n || lost[w]) return;
+    const int64_t b = off[w], cap = off[w + 1] - b, d0 = row_ptr[w], deg = row_ptr[w + 1] - d0;
+    const int64_t m = deg < cap ? deg : cap;
+    for (int64_t j = lane; j < m; j += 32) {
+        col[d0 + j] = ccol[b + j];
+        dist[d0 + j] = cdist[b + j];
+    }
+}
+
+// Places the overflow arena's entries of kept rows at their slots.
+__global__ void k_ovf_scatter(int64_t used, const int32_t *__restrict__ orow, const int32_t *__restrict__ oslot,
+                              const int32_t *__restrict__ ocol, const float *__restrict__ odist,
+                              const uint8_t *__restrict__ lost, const int64_t *__restrict__ row_ptr,
+                              int32_t *__restrict__ col, float *__restrict__ dist, int32_t *__restrict__ err) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= used) return;
+    const int r = orow[k];
+    if (lost[r]) return;
+    const int64_t at = row_ptr[r] + oslot[k];
+    if (at >= row_ptr[r + 1]) {
+        atomicOr(err, 128);
+        return;
+    }
+    col[at] = ocol[k];
+    dist[at] = odist[k];
+}
 
 // ---------------------------------------------------------------------------
 // Precision 1: BF16 tensor-core filter, FP32 recheck, FP64 guard band.
@@ -1158,7 +1308,7 @@ struct __align__(1024) TcShared {
     uint8_t rli[TC_ROWS];
     int bbeg[NB], bcnt[NB], bpre[NB + 1];
     uint32_t bem[NB];
-    int qcnt[32];
+    int qcnt[32], orig[32];
     int gpos[GQ_CAP];
     uint8_t gq[GQ_CAP], gb[GQ_CAP];
     int gn;
@@ -1213,11 +1363,11 @@ __device__ __forceinline__ void tc_convert_row_thread(unsigned char *tile, int r
 __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_tc(TreeView tv, QParams qp, Items items,
                                                     const uint32_t *__restrict__ cand, uint32_t *__restrict__ emask,
                                                     int32_t *__restrict__ deg, unsigned long long *__restrict__ st,
-                                                    int32_t *__restrict__ err) {
+                                                    int32_t *__restrict__ err, CapOut co) {
     extern __shared__ unsigned char tc_raw[];
     TcShared &S = *reinterpret_cast<TcShared *>(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
-    const int it = blockIdx.x;
-    if (it >= *items.count) return;
+    if ((int)blockIdx.x >= *items.count) return;
+    const int it = item_of_block(items);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = items.group[it];
     const int dp = tv.dp, dim = tv.dim, dp4 = dp >> 2;
@@ -1257,6 +1407,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_tc(TreeView tv, QParams qp, 
             S.qn2[q] = n2;
             S.qabs[q] = sqrtf(a2);
             S.qcnt[q] = 0;
+            S.orig[q] = q < nqr ? tv.perm[qfirst + q] : 0;
         }
         if (tid == 0) S.gn = 0;
 
@@ -1271,6 +1422,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_tc(TreeView tv, QParams qp, 
                 if (s64 <= qp.eps2_64) {
                     atomicAdd(&S.qcnt[q], 1);
                     atomicOr(&S.bem[li], 1u << q);
+                    if (co.off) cap_put(co, S.orig[q], tv.perm[ppos], (float)sqrt(s64));
                 }
             }
             __syncthreads();
@@ -1421,11 +1573,13 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_tc(TreeView tv, QParams qp, 
                                 if (s64 <= qp.eps2_64) {
                                     atomicAdd(&S.qcnt[q], 1);
                                     atomicOr(&S.bem[li], 1u << q);
+                                    if (co.off) cap_put(co, S.orig[q], tv.perm[ppos], (float)sqrt(s64));
                                 }
                             }
                         } else if (edge) {
                             atomicAdd(&S.qcnt[q], 1);
                             atomicOr(&S.bem[li], 1u << q);
+                            if (co.off) cap_put(co, S.orig[q], tv.perm[ppos], sqrtf(sv));
                         }
                     }
                 }
@@ -1440,7 +1594,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_tc(TreeView tv, QParams qp, 
                 for (int i = tid; i < bn; i += LEAF_T) emask[b0 + i] = qn <= 32 ? S.bem[i] : ~0u;
         }
         __syncthreads();
-        if (!failed && tid < nqr && S.qcnt[tid]) atomicAdd(&deg[tv.perm[qfirst + tid]], S.qcnt[tid]);
+        if (!failed && tid < nqr && S.qcnt[tid]) atomicAdd(&deg[S.orig[tid]], S.qcnt[tid]);
     }
     for (int o = 16; o > 0; o >>= 1) {
         pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
@@ -1526,18 +1680,19 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf_lev(
     TreeView tv, QParams qp, const uint8_t *__restrict__ amap_g, int A, int qchunk, Items items,
     uint32_t *__restrict__ cand, int32_t *__restrict__ deg, const int64_t *__restrict__ row_ptr,
     int32_t *__restrict__ rowcur, int32_t *__restrict__ col, float *__restrict__ dist,
-    unsigned long long *__restrict__ st, int32_t *__restrict__ err) {
+    unsigned long long *__restrict__ st, int32_t *__restrict__ err, CapOut co, const uint8_t *__restrict__ rowsel) {
     extern __shared__ uint64_t speq[];  // qchunk x A x W
     __shared__ uint8_t amap[256];
-    __shared__ int cnt[32], cursor[32], qlen[32];
+    __shared__ int cnt[32], cursor[32], qlen[32], sel[32];
     __shared__ int64_t rowb[32], rowe[32];
     __shared__ int tpos[32];
     __shared__ int64_t tcand[32];
     __shared__ int64_t s_ci;
     __shared__ int s_off, s_rows;
     __shared__ unsigned s_hit;
-    const int it = blockIdx.x, tid = threadIdx.x, warp = tid >> 5;
-    if (it >= *items.count) return;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if ((int)blockIdx.x >= *items.count) return;
+    const int it = item_of_block(items);
     const int g = items.group[it];
     const int qb = tv.group_begin[g], qn = tv.group_count[g];
     const int64_t c0 = items.begin[it], c1 = items.end[it];
@@ -1555,6 +1710,7 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf_lev(
                 qlen[tid] = (int)(tv.soff[qpos + 1] - tv.soff[qpos]);
                 int o = tv.perm[qpos];
                 cursor[tid] = o;  // original id of the query (row of the CSR)
+                sel[tid] = rowsel == nullptr || rowsel[o] != 0;
                 if (EMIT) {
                     rowb[tid] = row_ptr[o];
                     rowe[tid] = row_ptr[o + 1];
@@ -1586,6 +1742,7 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf_lev(
                     int q = t / npr, p = t - q * npr;
                     int qpos = qb + q0 + q, ppos = tpos[p];
                     if (qpos == ppos && !qp.include_self) continue;
+                    if (EMIT && !sel[q]) continue;
                     if (!EMIT) ++pairs;
                     const uint8_t *txt = tv.sdata + tv.soff[ppos];
                     int n = (int)(tv.soff[ppos + 1] - tv.soff[ppos]);
@@ -1594,6 +1751,7 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf_lev(
                     if (!EMIT) {
                         hit |= 1u << p;
                         atomicAdd(&cnt[q], 1);
+                        if (co.off) cap_put(co, cursor[q], tv.perm[ppos], (float)d);
                     } else {
                         int slot = atomicAdd(&rowcur[cursor[q]], 1);
                         int64_t at = rowb[q] + slot;
@@ -1891,7 +2049,8 @@ void launch_traversal(const ct_tree *t, const TreeView &tv, const QParams &qp, c
     CT_LAUNCH_CHECK();
 }
 
-void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out, int precision) {
+void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out, int precision,
+                const ct_predictor *pred, Probe *probe) {
     const int64_t n = t->n;
     const int G = t->n_groups;
     const bool l2 = t->metric == CT_L2_F32;
@@ -1931,6 +2090,7 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
         pool_cap = (int64_t)hc[2] + 2LL * tl.warps * POOL_CHUNK + POOL_CHUNK;
         CT_CHECK_CUDA(cudaMemsetAsync(st.p, 0, ST_N * sizeof(unsigned long long), s));
     }
+    stacks.reset();
     const int64_t n_cand = (int64_t)hc[2];
     const int nseg = (int)(uint32_t)hc[1];
     const int64_t pool_used = (int64_t)hc[0] < pool_cap ? (int64_t)hc[0] : pool_cap;
@@ -1939,7 +2099,7 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
     const int64_t max_items = nseg + n_cand / kItem + 1;
     DBuf<int32_t> icnt(nseg + 1, s), igroup(max_items, s), nitems(1, s);
     DBuf<int64_t> ioff(nseg + 1, s), ibeg(max_items, s), iend(max_items, s);
-    Items items{igroup.p, ibeg.p, iend.p, nitems.p};
+    Items items{igroup.p, ibeg.p, iend.p, nitems.p, nullptr};
     CT_CHECK_CUDA(cudaMemsetAsync(nitems.p, 0, sizeof(int32_t), s));
     if (nseg) {
         k_item_counts<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_count.p, icnt.p);
@@ -1952,6 +2112,33 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
     }
     DBuf<int32_t> rowcur(n + 1, s);
     uint32_t *cand_p = pool.p;
+
+    // learned form: candidate counts per group and item, features, the plan
+    LearnedPlan lp;
+    if (pred || probe) {
+        DBuf<int32_t> gb_own, gp_own;
+        int32_t *gbl = probe && probe->gblocks ? probe->gblocks : (gb_own = DBuf<int32_t>(G ? G : 1, s)).p;
+        int32_t *gpt = probe && probe->gpoints ? probe->gpoints : (gp_own = DBuf<int32_t>(G ? G : 1, s)).p;
+        DBuf<int32_t> ipts(max_items, s);
+        CT_CHECK_CUDA(cudaMemsetAsync(gbl, 0, (G ? G : 1) * sizeof(int32_t), s));
+        CT_CHECK_CUDA(cudaMemsetAsync(gpt, 0, (G ? G : 1) * sizeof(int32_t), s));
+        if (nseg) {
+            k_item_stats<<<(unsigned)max_items, 128, 0, s>>>(items, cand_p, t->node_count, ipts.p, gbl, gpt);
+            CT_COUNT_LAUNCH();
+            CT_LAUNCH_CHECK();
+        }
+        if (probe) {
+            if (probe->x) features_from_groups(t, qp.eps64, gbl, gpt, nullptr, probe->x, s);
+            if (!probe->deg) {
+                out.stats.candidates = n_cand;
+                return;
+            }
+        } else if (n > 0) {
+            ProfScope ps("predict", s);
+            learned_plan(pred, t, qp, gbl, gpt, igroup.p, ipts.p, nitems.p, s, lp);
+            if (lp.item_order.p) items.order = lp.item_order.p;
+        }
+    }
 
     // alphabet of the strings (edit distance)
     DBuf<uint8_t> amap;
@@ -1983,17 +2170,48 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
     }
     size_t lsm = l2 ? 0 : (size_t)qchunk * A * W * sizeof(uint64_t);
 
+    // one-pass emit: capacity region and overflow arena
+    const bool capmode = pred && !probe && lp.one_pass;
+    CapOut co{};
+    DBuf<int32_t> c_fill, c_col, o_row, o_slot, o_col;
+    DBuf<float> c_dist, o_dist;
+    DBuf<unsigned long long> o_n;
+    DBuf<uint8_t> lost;
+    if (capmode) {
+        const int64_t ct = lp.cap_total > 0 ? lp.cap_total : 1, oc = lp.arena > 0 ? lp.arena : 1;
+        c_fill = DBuf<int32_t>(n + 1, s);
+        c_col = DBuf<int32_t>(ct, s);
+        c_dist = DBuf<float>(ct, s);
+        o_row = DBuf<int32_t>(oc, s);
+        o_slot = DBuf<int32_t>(oc, s);
+        o_col = DBuf<int32_t>(oc, s);
+        o_dist = DBuf<float>(oc, s);
+        o_n = DBuf<unsigned long long>(3, s);
+        lost = DBuf<uint8_t>(n + 1, s);
+        CT_CHECK_CUDA(cudaMemsetAsync(c_fill.p, 0, (n + 1) * sizeof(int32_t), s));
+        CT_CHECK_CUDA(cudaMemsetAsync(o_n.p, 0, 3 * sizeof(unsigned long long), s));
+        CT_CHECK_CUDA(cudaMemsetAsync(lost.p, 0, n + 1, s));
+        co = CapOut{lp.cap_off.p, c_fill.p, c_col.p, c_dist.p, o_row.p, o_slot.p, o_col.p, o_dist.p,
+                    o_n.p, lp.arena > 0 ? lp.arena : 0, lost.p};
+    }
+
     // 2. count pass
     DBuf<int32_t> deg(n + 1, s);
     CT_CHECK_CUDA(cudaMemsetAsync(deg.p, 0, (n + 1) * sizeof(int32_t), s));
-    auto leaf = [&](bool emit, int64_t *row_ptr, int32_t *col, float *dist) {
+    int32_t *qwork = probe && probe->work && l2 ? probe->work : nullptr;
+    if (qwork) {
+        CT_CHECK_CUDA(cudaMemsetAsync(qwork, 0, n * sizeof(int32_t), s));
+        probe->work_valid = true;
+    }
+    auto leaf = [&](bool emit, int64_t *row_ptr, int32_t *col, float *dist, const uint8_t *rowsel) {
         if (G == 0 || nseg == 0) return;
+        const CapOut cw = emit ? CapOut{} : co;
         if (l2) {
             leaf_l2_prepare();
             if (emit)
-                k_leaf_l2<true><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err);
+                k_leaf_l2<true><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel, nullptr);
             else
-                k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err);
+                k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel, emit ? nullptr : qwork);
         } else {
             switch (W) {
 #define CT_LL(WW)                                                                                                      \
@@ -2002,8 +2220,8 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
             CT_CHECK_CUDA(cudaFuncSetAttribute(k_leaf_lev<true, WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm)); \
             CT_CHECK_CUDA(cudaFuncSetAttribute(k_leaf_lev<false, WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm)); \
         }                                                                                                              \
-        if (emit) k_leaf_lev<true, WW><<<(unsigned)max_items, LEAF_T, lsm, s>>>(tv, qp, amap.p, A, qchunk, items, cand_p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err); \
-        else k_leaf_lev<false, WW><<<(unsigned)max_items, LEAF_T, lsm, s>>>(tv, qp, amap.p, A, qchunk, items, cand_p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err);    \
+        if (emit) k_leaf_lev<true, WW><<<(unsigned)max_items, LEAF_T, lsm, s>>>(tv, qp, amap.p, A, qchunk, items, cand_p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel); \
+        else k_leaf_lev<false, WW><<<(unsigned)max_items, LEAF_T, lsm, s>>>(tv, qp, amap.p, A, qchunk, items, cand_p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel);    \
         break;
                 CT_LL(1) CT_LL(2) CT_LL(4) CT_LL(8) CT_LL(16)
 #undef CT_LL
@@ -2014,7 +2232,7 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
     };
     // the tensor-core filter applies to L2 rows of at most 128 floats; wider
     // rows use the FP32 tiles (same output)
-    const bool use_tc = precision == 1 && l2 && t->dp <= 128;
+    const bool use_tc = precision == 1 && l2 && t->dp <= 128 && !qwork;
     if (use_tc) {
         ProfScope ps("leaf_count_tc", s);
         static bool tc_ready = false;
@@ -2023,13 +2241,32 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
             tc_ready = true;
         }
         if (G && nseg) {
-            k_leaf_tc<<<(unsigned)max_items, LEAF_T, kTcSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, st.p, err);
+            k_leaf_tc<<<(unsigned)max_items, LEAF_T, kTcSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, st.p, err, co);
             CT_COUNT_LAUNCH();
             CT_LAUNCH_CHECK();
         }
     } else {
         ProfScope ps("leaf_count", s);
-        leaf(false, nullptr, nullptr, nullptr);
+        leaf(false, nullptr, nullptr, nullptr, nullptr);
+    }
+
+    auto finish_stats = [&]() {
+        unsigned long long hs[ST_N];
+        to_host(hs, st.p, ST_N, s);
+        prof_flush();
+        if (hs[ST_ERR]) CT_FAIL(CT_ECUDA, "internal consistency check failed in the query (code %llu)", hs[ST_ERR]);
+        out.stats.traversal_evals = (int64_t)hs[ST_TRAV];
+        out.stats.leaf_pairs = (int64_t)hs[ST_PAIRS];
+        out.stats.guard_fp64 = (int64_t)hs[ST_GUARD];
+        out.stats.recheck_fp32 = (int64_t)hs[ST_RECHECK];
+        out.stats.emit_pairs = (int64_t)hs[ST_EMIT];
+        out.stats.candidates = n_cand;
+    };
+
+    if (probe) {  // labels for fitting the predictor
+        if (n) CT_CHECK_CUDA(cudaMemcpyAsync(probe->deg, deg.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        finish_stats();
+        return;
     }
 
     // 3. scan -> row_ptr, then emit
@@ -2041,10 +2278,44 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
     out.nnz = nnz;
     out.col = (int32_t *)dmalloc((size_t)(nnz ? nnz : 1) * sizeof(int32_t), s);
     out.dist = (float *)dmalloc((size_t)(nnz ? nnz : 1) * sizeof(float), s);
-    if (nnz) {
+    if (capmode) {
+        // one-pass emit: move the capacity region and the arena into the CSR;
+        // rows that lost entries are emitted again, exactly
+        unsigned long long hv[3] = {0, 0, 0};
+        {
+            ProfScope ps("compact", s);
+            if (n) {
+                k_cap_rows<<<grid_for(n, 256), 256, 0, s>>>(n, row_ptr, lp.cap_off.p, c_fill.p, lost.p, o_n.p + 1, err);
+                CT_COUNT_LAUNCH();
+                k_compact<<<grid_for(n * 32, 256), 256, 0, s>>>(n, row_ptr, lp.cap_off.p, lost.p, c_col.p, c_dist.p,
+                                                                out.col, out.dist);
+                CT_COUNT_LAUNCH();
+                CT_LAUNCH_CHECK();
+            }
+            to_host(hv, o_n.p, 3, s);
+            const int64_t used = std::min<int64_t>((int64_t)hv[0], co.ovf_cap);
+            if (used > 0) {
+                k_ovf_scatter<<<grid_for(used, 256), 256, 0, s>>>(used, o_row.p, o_slot.p, o_col.p, o_dist.p, lost.p,
+                                                                  row_ptr, out.col, out.dist, err);
+                CT_COUNT_LAUNCH();
+                CT_LAUNCH_CHECK();
+            }
+        }
+        out.stats.overflow_rows = (int64_t)hv[1];
+        out.stats.reemit_rows = (int64_t)hv[2];
+        c_col.reset();
+        c_dist.reset();
+        if (hv[2]) {
+            ProfScope ps("reemit", s);
+            CT_CHECK_CUDA(cudaMemsetAsync(rowcur.p, 0, (n + 1) * sizeof(int32_t), s));
+            leaf(true, row_ptr, out.col, out.dist, lost.p);
+            k_check_rows_sel<<<grid_for(n, 256), 256, 0, s>>>(n, row_ptr, rowcur.p, lost.p, err);
+            CT_COUNT_LAUNCH();
+        }
+    } else if (nnz) {
         ProfScope ps("leaf_emit", s);
         CT_CHECK_CUDA(cudaMemsetAsync(rowcur.p, 0, (n + 1) * sizeof(int32_t), s));
-        leaf(true, row_ptr, out.col, out.dist);
+        leaf(true, row_ptr, out.col, out.dist, nullptr);
         k_check_rows<<<grid_for(n, 256), 256, 0, s>>>(n, row_ptr, rowcur.p, err);
         CT_COUNT_LAUNCH();
     }
@@ -2052,25 +2323,15 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
         ProfScope ps("row_sort", s);
         sort_rows(row_ptr, n, out.col, out.dist, nnz, s);
     }
-
-    unsigned long long hs[ST_N];
-    to_host(hs, st.p, ST_N, s);
-    prof_flush();
-    if (hs[ST_ERR]) CT_FAIL(CT_ECUDA, "internal consistency check failed in the query (code %llu)", hs[ST_ERR]);
-    out.stats.traversal_evals = (int64_t)hs[ST_TRAV];
-    out.stats.leaf_pairs = (int64_t)hs[ST_PAIRS];
-    out.stats.guard_fp64 = (int64_t)hs[ST_GUARD];
-    out.stats.recheck_fp32 = (int64_t)hs[ST_RECHECK];
-    out.stats.emit_pairs = (int64_t)hs[ST_EMIT];
-    out.stats.candidates = n_cand;
+    finish_stats();
 }
 
 void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out) {
-    query_impl(t, qp, s, out, 0);
+    query_impl(t, qp, s, out, 0, nullptr, nullptr);
 }
 
 void query_tc(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out) {
-    query_impl(t, qp, s, out, 1);
+    query_impl(t, qp, s, out, 1, nullptr, nullptr);
 }
 
 }  // namespace ct
@@ -2194,10 +2455,11 @@ void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cuda
         k_item_fill<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_group, seg_begin, seg_count, ioff, igroup, ibeg,
                                                        iend, nitems);
         CT_COUNT_LAUNCH();
-        Items items{igroup, ibeg, iend, nitems};
+        Items items{igroup, ibeg, iend, nitems, nullptr};
         leaf_l2_prepare();
         k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, pool, nullptr, degrees, nullptr,
-                                                                          nullptr, nullptr, nullptr, st, err);
+                                                                          nullptr, nullptr, nullptr, st, err, CapOut{},
+                                                                          nullptr, nullptr);
         CT_COUNT_LAUNCH();
     }
     CT_LAUNCH_CHECK();

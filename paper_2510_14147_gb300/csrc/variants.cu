@@ -4,18 +4,14 @@
 
 namespace ct {
 
-void query_tc(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out);
-
 void query_predicted(const ct_tree *t, const QParams &qp, const void *predictor, int precision,
-                     cudaStream_t s, QueryOut &out) {
-    (void)t; (void)qp; (void)predictor; (void)precision; (void)s; (void)out;
-    CT_FAIL(CT_EUNSUPPORTED, "use_predictor is not available in this build");
-}
+                     cudaStream_t s, QueryOut &out);
 
 void query_batched(int n_clouds, const ct_tree *const *trees, const QParams *qps, const ct_query_opts *opts,
                    cudaStream_t s, QueryOut *outs) {
     for (int c = 0; c < n_clouds; ++c) {
-        if (opts->precision == 1) query_tc(trees[c], qps[c], s, outs[c]);
+        if (opts->use_predictor) query_predicted(trees[c], qps[c], opts->predictor, opts->precision, s, outs[c]);
+        else if (opts->precision == 1) query_tc(trees[c], qps[c], s, outs[c]);
         else query_plain(trees[c], qps[c], s, outs[c]);
     }
 }

@@ -59,7 +59,15 @@ class ct_csr(C.Structure):
 class ct_query_stats(C.Structure):
     _fields_ = [(f, C.c_int64) for f in ("traversal_evals", "leaf_pairs", "guard_fp64",
                                            "recheck_fp32", "candidates", "overflow_rows",
-                                           "kernel_launches", "emit_pairs")]
+                                           "kernel_launches", "emit_pairs", "reemit_rows")]
+
+
+class ct_fit_opts(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("include_self", C.c_int32),
+                ("seed", C.c_uint64)]
+
+
+CT_MLP_IN, CT_MLP_NPARAMS, CT_MLP_NORM = 16, 5378, 36
 
 
 def library_path() -> str:
@@ -111,6 +119,29 @@ def _load():
         lib.ct_selftest_tc_gemm.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.ct_kernel_launches.restype = C.c_int64
         lib.ct_kernel_launches.argtypes = []
+        lib.ct_predictor_create.restype = C.c_int
+        lib.ct_predictor_create.argtypes = [C.c_uint64, P(C.c_void_p)]
+        lib.ct_predictor_free.restype = None
+        lib.ct_predictor_free.argtypes = [C.c_void_p]
+        lib.ct_predictor_fit.restype = C.c_int
+        lib.ct_predictor_fit.argtypes = [C.c_void_p, C.c_void_p, C.c_double, P(ct_fit_opts), C.c_void_p,
+                                         P(C.c_double)]
+        lib.ct_predictor_set_capacity.restype = C.c_int
+        lib.ct_predictor_set_capacity.argtypes = [C.c_void_p, C.c_float, C.c_int32, C.c_float, C.c_int64]
+        lib.ct_predictor_get_params.restype = C.c_int
+        lib.ct_predictor_get_params.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.ct_predictor_set_params.restype = C.c_int
+        lib.ct_predictor_set_params.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.ct_predictor_features.restype = C.c_int
+        lib.ct_predictor_features.argtypes = [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]
+        lib.ct_predictor_predict.restype = C.c_int
+        lib.ct_predictor_predict.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
+                                             C.c_void_p]
+        lib.ct_mlp_loss_grad.restype = C.c_int
+        lib.ct_mlp_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                         P(C.c_double), C.c_void_p]
+        lib.ct_mlp_forward_f16.restype = C.c_int
+        lib.ct_mlp_forward_f16.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
         _lib = lib
         return lib
 
@@ -364,6 +395,110 @@ def ct_selftest_tc_gemm(A, B, stream=None):
     D = torch.empty(128, 32, dtype=torch.float32, device=A.device)
     _check(_load().ct_selftest_tc_gemm(A.data_ptr(), B.data_ptr(), D.data_ptr(), C.c_void_p(_stream(stream))))
     return D
+
+
+class Predictor:
+    """Owning handle of a degree/work predictor (the learned form's MLP)."""
+
+    def __init__(self, seed: int = 0):
+        h = C.c_void_p()
+        _check(_load().ct_predictor_create(C.c_uint64(seed), C.byref(h)))
+        self.handle = h
+
+    def free(self):
+        if self.handle and self.handle.value:
+            _load().ct_predictor_free(self.handle)
+            self.handle = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def ct_predictor_create(seed: int = 0) -> Predictor:
+    return Predictor(seed)
+
+
+def ct_predictor_free(p: Predictor):
+    p.free()
+
+
+def ct_predictor_fit(p: Predictor, tree: Tree, eps: float, steps: int = 0, batch: int = 0, lr: float = 0.0,
+                     include_self: bool = False, seed: int = 0, stream=None) -> float:
+    """Labels the tree's points with their exact degrees and leaf work and
+    trains the MLP; returns the mean standardised loss of the last tenth of
+    the steps."""
+    o = ct_fit_opts(int(steps), int(batch), float(lr), int(bool(include_self)), int(seed))
+    loss = C.c_double()
+    _check(_load().ct_predictor_fit(p.handle, tree.handle, float(eps), C.byref(o), C.c_void_p(_stream(stream)),
+                                    C.byref(loss)))
+    return float(loss.value)
+
+
+def ct_predictor_set_capacity(p: Predictor, margin: float = 0.5, pad: int = 16, arena_frac: float = 0.25,
+                              arena_min: int = 65536):
+    _check(_load().ct_predictor_set_capacity(p.handle, float(margin), int(pad), float(arena_frac),
+                                             int(arena_min)))
+
+
+def ct_predictor_get_params(p: Predictor):
+    """(params [5378] float32, norm [36] float32) host copies."""
+    params = np.zeros(CT_MLP_NPARAMS, np.float32)
+    norm = np.zeros(CT_MLP_NORM, np.float32)
+    _check(_load().ct_predictor_get_params(p.handle, params.ctypes.data, norm.ctypes.data))
+    return params, norm
+
+
+def ct_predictor_set_params(p: Predictor, params=None, norm=None):
+    a = None if params is None else np.ascontiguousarray(params, np.float32)
+    b = None if norm is None else np.ascontiguousarray(norm, np.float32)
+    if a is not None and a.size != CT_MLP_NPARAMS:
+        raise ValueError("params must hold %d values" % CT_MLP_NPARAMS)
+    if b is not None and b.size != CT_MLP_NORM:
+        raise ValueError("norm must hold %d values" % CT_MLP_NORM)
+    _check(_load().ct_predictor_set_params(p.handle, None if a is None else a.ctypes.data,
+                                           None if b is None else b.ctypes.data))
+
+
+def ct_predictor_features(tree: Tree, eps: float, stream=None):
+    """Raw features (n, 16) float32 CUDA tensor, row i = tree position i."""
+    import torch
+    x = torch.empty(max(tree.n, 1), CT_MLP_IN, dtype=torch.float32, device="cuda")
+    _check(_load().ct_predictor_features(tree.handle, float(eps), x.data_ptr(), C.c_void_p(_stream(stream))))
+    return x[:tree.n]
+
+
+def ct_predictor_predict(p: Predictor, tree: Tree, eps: float, stream=None):
+    """(predicted degree, predicted leaf work), CUDA float32 by original id."""
+    import torch
+    d = torch.empty(max(tree.n, 1), dtype=torch.float32, device="cuda")
+    b = torch.empty(max(tree.n, 1), dtype=torch.float32, device="cuda")
+    _check(_load().ct_predictor_predict(p.handle, tree.handle, float(eps), d.data_ptr(), b.data_ptr(),
+                                        C.c_void_p(_stream(stream))))
+    return d[:tree.n], b[:tree.n]
+
+
+def ct_mlp_loss_grad(params, x, t, stream=None):
+    """(loss, grad) of the MLP for CUDA float32 params [5378], x (n, 16), t (n, 2)."""
+    import torch
+    params, x, t = params.contiguous(), x.contiguous(), t.contiguous()
+    g = torch.empty(CT_MLP_NPARAMS, dtype=torch.float32, device="cuda")
+    loss = C.c_double()
+    _check(_load().ct_mlp_loss_grad(params.data_ptr(), x.data_ptr(), t.data_ptr(), x.shape[0], g.data_ptr(),
+                                    C.byref(loss), C.c_void_p(_stream(stream))))
+    return float(loss.value), g
+
+
+def ct_mlp_forward_f16(params, x, stream=None):
+    """y (n, 2): forward pass with fp16-rounded parameters, fp32 sums."""
+    import torch
+    params, x = params.contiguous(), x.contiguous()
+    y = torch.empty(max(x.shape[0], 1), 2, dtype=torch.float32, device="cuda")
+    _check(_load().ct_mlp_forward_f16(params.data_ptr(), x.data_ptr(), x.shape[0], y.data_ptr(),
+                                      C.c_void_p(_stream(stream))))
+    return y[:x.shape[0]]
 
 
 def version() -> str:

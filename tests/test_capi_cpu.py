@@ -64,6 +64,17 @@ def test_invalid_arguments_without_gpu():
     assert lib.eps_graph_query_batched(0, None, None, None, None, None) == cg.CT_OK
     st = cg.ct_query_stats()
     assert lib.ct_csr_stats(C.byref(csr), C.byref(st)) == cg.CT_EINVAL
+    # predictor entry points
+    assert lib.ct_predictor_create(0, None) == cg.CT_EINVAL
+    lib.ct_predictor_free(None)
+    assert lib.ct_predictor_fit(None, None, 1.0, None, None, None) == cg.CT_EINVAL
+    assert lib.ct_predictor_set_capacity(None, 0.5, 16, 0.25, 0) == cg.CT_EINVAL
+    assert lib.ct_predictor_get_params(None, None, None) == cg.CT_EINVAL
+    assert lib.ct_predictor_set_params(None, None, None) == cg.CT_EINVAL
+    assert lib.ct_predictor_features(None, 1.0, None, None) == cg.CT_EINVAL
+    assert lib.ct_predictor_predict(None, None, 1.0, None, None, None) == cg.CT_EINVAL
+    assert lib.ct_mlp_loss_grad(None, None, None, 4, None, None, None) == cg.CT_EINVAL
+    assert lib.ct_mlp_forward_f16(None, None, -1, None, None) == cg.CT_EINVAL
 
 
 def test_product_path_has_no_cpu_fallback():
