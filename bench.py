@@ -233,6 +233,8 @@ def main():
     ap.add_argument("--learned", action="store_true",
                     help="one-pass emit into capacities from a predictor fitted on another draw")
     ap.add_argument("--fit-steps", type=int, default=1500)
+    ap.add_argument("--order-radius", action="store_true",
+                    help="learned form: walk groups by radius instead of predicted walk length")
     args = ap.parse_args()
     wl = I.load_workloads()[args.workload]
 
@@ -274,9 +276,12 @@ def main():
                                        stream=stream)
             fit_s = time.perf_counter() - t0
             tf.free()
+            if args.order_radius:
+                cg.ct_predictor_set_order(pred, False)
         del xf
         fit_info = {"fit_on": "seed %d draw" % wl_fit["seed"], "fit_steps": args.fit_steps,
-                    "final_loss": loss, "fit_s": fit_s}
+                    "final_loss": loss, "fit_s": fit_s,
+                    "walk_order": "radius" if args.order_radius else "predicted walk length"}
 
     def step(points):
         t = cg.ct_build(points=points, leaf_size=zeta, stream=stream)

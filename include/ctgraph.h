@@ -206,28 +206,26 @@ ct_status ct_tree_export(const ct_tree *tree, int64_t *center, double *radius, i
 /* ------------------------------------------------------------------------
  * Degree/work predictor of the learned form.  The paper has no learned
  * component: this is an extension that sizes the one-pass emit and orders the
- * leaf work.  A small multilayer perceptron, CT_MLP_IN -> 64 -> 64 -> 2 with
- * ReLU after both hidden layers, maps 16 features of a query, taken after the
- * traversal (e = max(eps, 1e-20)):
+ * traversal.  A small multilayer perceptron, CT_MLP_IN -> 64 -> 64 -> 2 with
+ * ReLU after both hidden layers, maps 16 features of a query, read from the
+ * tree before the query runs (e = max(eps, 1e-20)):
  *    0 log1p(d(q, leaf-block centre)/e)   1 log1p(d(q, group centre)/e)
  *                                           (L2; 0 for edit distance)
  *    2 log1p(group radius/e)              3 log2(points of the group)
- *    4 log1p(candidate leaf blocks of the group)
- *    5 log1p(points of those blocks)
- *    6..11 leaf block, parent, grandparent (the root repeats):
+ *    4..11 leaf block and its first three ancestors (the root repeats):
  *          log1p(points below), log1p(radius/e)
  *    12..15 log1p(points below the lowest ancestor of the leaf block,
  *          itself included, with radius >= e, 2e, 4e, 16e; the root if none)
  * (the group: the query's run of sibling leaf blocks, at most 32 points or a
  * single larger block; its centre is its first point) to
  *    output 0: log(1 + degree of the query),
- *    output 1: log(1 + points the query evaluates in the leaf stage after
- *              the per-query leaf-centre test of Algorithm 3; for edit
- *              distance, the group's candidate points).
- * Inputs and targets are standardised with the mean and deviation of the
- * training set.  Parameters are one fp32 vector, W1 (64 x 16, row-major),
- * b1, W2 (64 x 64), b2, W3 (2 x 64), b3: CT_MLP_NPARAMS values.  Inference
- * uses fp16 copies of the weights with fp32 sums.
+ *    output 1: log(1 + vertices tested by the tree walk of its group).
+ * Output 0 sizes the rows of the one-pass emit; output 1, averaged over a
+ * group, orders the walks longest first.  Inputs and targets are
+ * standardised with the mean and deviation of the training set.  Parameters
+ * are one fp32 vector, W1 (64 x 16, row-major), b1, W2 (64 x 64), b2,
+ * W3 (2 x 64), b3: CT_MLP_NPARAMS values.  Inference uses fp16 copies of the
+ * weights with fp32 sums.
  * A predictor lives on the device that was current when it was created. */
 #define CT_MLP_IN 16
 #define CT_MLP_NPARAMS 5378
@@ -250,9 +248,9 @@ ct_status ct_predictor_create(uint64_t seed, ct_predictor **out);
 /* Releases a predictor (synchronises its device).  NULL-safe. */
 void ct_predictor_free(ct_predictor *p);
 
-/* Labels every point of `tree` with its exact degree at `eps` and its leaf
- * work (one traversal and one FP32 count pass of eps_graph_query), then
- * trains on the GPU (mean squared error, Adam).  *final_loss (may be NULL) receives the
+/* Labels every point of `tree` with its exact degree at `eps` and its group's
+ * walk length (one traversal and one FP32 count pass of eps_graph_query),
+ * then trains on the GPU (mean squared error, Adam).  *final_loss (may be NULL) receives the
  * mean standardised loss of the last 10% of the steps.  Synchronises `stream`.
  * Errors: CT_EINVAL (null pointers, eps < 0 or NaN, empty tree, predictor on
  * another device), CT_ENOMEM, CT_ECUDA. */
@@ -266,23 +264,28 @@ ct_status ct_predictor_fit(ct_predictor *p, const ct_tree *tree, double eps, con
 ct_status ct_predictor_set_capacity(ct_predictor *p, float margin, int32_t pad, float arena_frac,
                                     int64_t arena_min);
 
+/* Order of the tree walks: 1 (default) = groups by decreasing predicted walk
+ * length, 0 = by decreasing group radius (the order without a predictor).
+ * Errors: CT_EINVAL. */
+ct_status ct_predictor_set_order(ct_predictor *p, int32_t by_predicted_work);
+
 /* Host copies of the parameters (CT_MLP_NPARAMS floats) and the
  * standardisation (CT_MLP_NORM floats); either pointer may be NULL.  set
  * marks the predictor fitted.  Errors: CT_EINVAL, CT_ECUDA. */
 ct_status ct_predictor_get_params(const ct_predictor *p, float *params, float *norm);
 ct_status ct_predictor_set_params(ct_predictor *p, const float *params, const float *norm);
 
-/* Raw (unstandardised) features of every point of `tree` at `eps` (runs the
- * traversal): device fp32 [n x CT_MLP_IN], 16-byte aligned, row i for the
- * point at tree position i (the order of ct_tree_export's leaf_pts).
+/* Raw (unstandardised) features of every point of `tree` at `eps`: device
+ * fp32 [n x CT_MLP_IN], 16-byte aligned, row i for the point at tree
+ * position i (the order of ct_tree_export's leaf_pts).
  * Errors: CT_EINVAL, CT_ENOMEM, CT_ECUDA. */
 ct_status ct_predictor_features(const ct_tree *tree, double eps, float *x, ct_stream stream);
 
-/* Predicted degree and leaf work of every point (device fp32 [n] each, by
- * original index; either may be NULL).  Requires a fitted predictor.
- * Errors: CT_EINVAL, CT_ENOMEM, CT_ECUDA. */
+/* Predicted degree and group walk length of every point (device fp32 [n]
+ * each, by original index; either may be NULL).  Requires a fitted
+ * predictor.  Errors: CT_EINVAL, CT_ENOMEM, CT_ECUDA. */
 ct_status ct_predictor_predict(const ct_predictor *p, const ct_tree *tree, double eps, float *degree,
-                               float *work, ct_stream stream);
+                               float *walk, ct_stream stream);
 
 /* The perceptron itself, for checking (device buffers):
  * ct_mlp_loss_grad: loss = (1/n) sum over samples and both outputs of

@@ -104,19 +104,17 @@ def query_groups(tree):
     return np.array(gb, np.int64), np.array(gc, np.int64), parent
 
 
-def features(tree, points, eps, gblocks=None, gpoints=None):
+def features(tree, points, eps):
     """The predictor's 16 features of every tree position, in float64, from
     the definition (the library computes them in fp32), e = max(eps, 1e-20):
       0 log1p(d(q, leaf-block centre)/e)   1 log1p(d(q, group centre)/e)
       2 log1p(group radius/e)              3 log2(group size)
-      4 log1p(candidate blocks of the group)   5 log1p(their points)
-      6..11 leaf block, parent, grandparent (the root repeats):
+      4..11 leaf block and its first three ancestors (the root repeats):
             log1p(points below), log1p(radius/e)
       12..15 log1p(points below the lowest ancestor, starting at the leaf
             block, with radius >= e, 2e, 4e, 16e; the root if none)
     Group centre = its first point, group radius = the largest distance of
-    its points to that centre.  Columns 4 and 5 come from the traversal's
-    candidate lists (gblocks, gpoints per group); NaN when not given."""
+    its points to that centre."""
     x = np.asarray(points, dtype=np.float64)
     e = max(float(eps), 1e-20)
     N = len(tree["center"])
@@ -150,13 +148,11 @@ def features(tree, points, eps, gblocks=None, gpoints=None):
         F[i, 1] = np.log1p(np.sqrt(((q - x[pos[gb[g]]]) ** 2).sum()) / e)
         F[i, 2] = np.log1p(grad_[g] / e)
         F[i, 3] = np.log2(gc[g])
-        F[i, 4] = np.log1p(gblocks[g]) if gblocks is not None else np.nan
-        F[i, 5] = np.log1p(gpoints[g]) if gpoints is not None else np.nan
         a = v
-        for k in range(3):
-            F[i, 6 + 2 * k] = np.log1p(below[a])
-            F[i, 7 + 2 * k] = np.log1p(radius[a] / e)
-            if k < 2 and parent[a] >= 0:
+        for k in range(4):
+            F[i, 4 + 2 * k] = np.log1p(below[a])
+            F[i, 5 + 2 * k] = np.log1p(radius[a] / e)
+            if k < 3 and parent[a] >= 0:
                 a = int(parent[a])
         for col, f in ((12, 1.0), (13, 2.0), (14, 4.0), (15, 16.0)):
             a = v

@@ -325,6 +325,14 @@ ct_status ct_predictor_set_capacity(ct_predictor *p, float margin, int32_t pad, 
     });
 }
 
+ct_status ct_predictor_set_order(ct_predictor *p, int32_t by_predicted_work) {
+    return guarded([&] {
+        if (!p) CT_FAIL(CT_EINVAL, "predictor is NULL");
+        if (by_predicted_work != 0 && by_predicted_work != 1) CT_FAIL(CT_EINVAL, "by_predicted_work must be 0 or 1");
+        p->order_by_work = by_predicted_work;
+    });
+}
+
 ct_status ct_predictor_get_params(const ct_predictor *p, float *params, float *norm) {
     return guarded([&] {
         if (!p) CT_FAIL(CT_EINVAL, "predictor is NULL");
@@ -368,11 +376,11 @@ ct_status ct_predictor_features(const ct_tree *tree, double eps, float *x, ct_st
         if (!(eps >= 0.0)) CT_FAIL(CT_EINVAL, "eps must be >= 0 (got %g)", eps);
         if (tree->n > 0 && (!x || ((uintptr_t)x & 15))) CT_FAIL(CT_EINVAL, "x must be a 16-byte aligned device pointer");
         check_device(tree);
-        ct::predictor_features(tree, eps, x, (cudaStream_t)stream);
+        ct::predictor_features(tree, eps, nullptr, x, (cudaStream_t)stream);
     });
 }
 
-ct_status ct_predictor_predict(const ct_predictor *p, const ct_tree *tree, double eps, float *degree, float *work,
+ct_status ct_predictor_predict(const ct_predictor *p, const ct_tree *tree, double eps, float *degree, float *walk,
                                ct_stream stream) {
     return guarded([&] {
         if (!p || !tree) CT_FAIL(CT_EINVAL, "predictor and tree must not be NULL");
@@ -380,7 +388,7 @@ ct_status ct_predictor_predict(const ct_predictor *p, const ct_tree *tree, doubl
         if (!p->fitted) CT_FAIL(CT_EINVAL, "the predictor has not been fitted");
         check_device(tree);
         check_predictor_device(p);
-        ct::predictor_predict(p, tree, eps, degree, work, (cudaStream_t)stream);
+        ct::predictor_predict(p, tree, eps, degree, walk, (cudaStream_t)stream);
     });
 }
 

@@ -1,8 +1,9 @@
 // learned.cu -- the learned form of the query: per-query features, fitting of
-// the degree/work predictor on the GPU, and the one-pass emit plan (row
-// capacities, overflow arena, order of the leaf work items by predicted work).
-// The paper has no learned component; the output is the same edge set as the
-// two-pass form whatever the predictions are.
+// the degree/work predictor on the GPU, and the plan it makes before the
+// traversal (row capacities and overflow arena of the one-pass emit; groups
+// walked in order of decreasing predicted walk length).  The paper has no
+// learned component; the output is the same edge set as the two-pass form
+// whatever the predictions are.
 #include <cmath>
 #include <random>
 #include <vector>
@@ -35,20 +36,20 @@ __global__ void k_pos_group(int64_t n, int G, const int32_t *__restrict__ group_
 
 __device__ __forceinline__ float rel_log(float r, double eps) { return (float)log1p((double)r / eps); }
 
-// The 16 features of the query at tree position i, taken after the traversal
-// (see ct_predictor_features); e = max(eps, 1e-20):
+// The 16 features of the query at tree position i (see
+// ct_predictor_features); e = max(eps, 1e-20):
 //  0 log1p(d(q, leaf centre)/e)      1 log1p(d(q, group centre)/e) (L2; 0 else)
 //  2 log1p(group radius/e)           3 log2(group size)
-//  4 log1p(group candidate blocks)   5 log1p(group candidate points)
-//  6..11 leaf block, parent, grandparent: log1p(points below), log1p(radius/e)
+//  4..11 leaf block and its first three ancestors: log1p(points below),
+//        log1p(radius/e)
 //  12..15 log1p(points below the lowest ancestor with radius >= e, 2e, 4e, 16e)
 __global__ void __launch_bounds__(256) k_features(
     int64_t n, int dp, int l2, const float *__restrict__ pts, const float *__restrict__ dcen,
     const int32_t *__restrict__ leaf_ids, int n_leaves, const int32_t *__restrict__ node_begin,
     const int32_t *__restrict__ node_count, const float *__restrict__ radius, const int32_t *__restrict__ parent,
     const int32_t *__restrict__ group_begin, const int32_t *__restrict__ group_count,
-    const float *__restrict__ group_radius, const int32_t *__restrict__ gof, const int32_t *__restrict__ gblocks,
-    const int32_t *__restrict__ gpoints, double e, Norm nm, float *__restrict__ x) {
+    const float *__restrict__ group_radius, const int32_t *__restrict__ gof, double e, Norm nm,
+    float *__restrict__ x) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int lo = 0, hi = n_leaves;  // leaf block holding position i
@@ -77,14 +78,12 @@ __global__ void __launch_bounds__(256) k_features(
     }
     f[2] = rel_log(group_radius[g], e);
     f[3] = log2f((float)group_count[g]);
-    f[4] = log1pf((float)gblocks[g]);
-    f[5] = log1pf((float)gpoints[g]);
     int v = leaf;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        f[6 + 2 * k] = log1pf((float)node_count[v]);
-        f[7 + 2 * k] = rel_log(radius[v], e);
-        if (k < 2 && parent[v] >= 0) v = parent[v];
+    for (int k = 0; k < 4; ++k) {
+        f[4 + 2 * k] = log1pf((float)node_count[v]);
+        f[5 + 2 * k] = rel_log(radius[v], e);
+        if (k < 3 && parent[v] >= 0) v = parent[v];
     }
     const double mult[4] = {1.0, 2.0, 4.0, 16.0};
     int found = 0;
@@ -105,17 +104,14 @@ __global__ void __launch_bounds__(256) k_features(
     for (int k = 0; k < MLP_IN / 4; ++k) out[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
 }
 
-// Training targets at position i: log1p(degree), log1p(leaf work) where the
-// leaf work is the points the query evaluates after the leaf-centre test, or
-// its group's candidate points when that test was not measured.
+// Training targets at position i: log1p(degree), log1p(vertices tested by
+// the walk of the query's group).
 __global__ void k_targets(int64_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ gof,
-                          const int32_t *__restrict__ deg, const int32_t *__restrict__ work,
-                          const int32_t *__restrict__ gpoints, float *__restrict__ t) {
+                          const int32_t *__restrict__ deg, const int32_t *__restrict__ gvisit, float *__restrict__ t) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int o = perm[i];
-    t[2 * i] = log1pf((float)deg[o]);
-    t[2 * i + 1] = log1pf((float)(work ? work[o] : gpoints[gof[i]]));
+    t[2 * i] = log1pf((float)deg[perm[i]]);
+    t[2 * i + 1] = log1pf((float)gvisit[gof[i]]);
 }
 
 // Column sums and sums of squares of an n x d matrix (d <= 16), in FP64.
@@ -203,24 +199,18 @@ __global__ void k_capacity(int64_t n, const float *__restrict__ y, const int32_t
     }
 }
 
-// Predicted leaf work summed per group (position i adds its query's share).
-__global__ void k_group_work(int64_t n, const float *__restrict__ y, const int32_t *__restrict__ gof, TargetNorm tn,
-                             float *__restrict__ gwork) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicAdd(&gwork[gof[i]], predicted(y, i, 1, tn));
-}
-
-// Sort keys of the work items: the group's predicted work in proportion to
-// the item's share of the group's candidate points; larger first.
-__global__ void k_item_keys(int m, const int32_t *__restrict__ item_group, const int32_t *__restrict__ item_points,
-                            const int32_t *__restrict__ gpoints, const float *__restrict__ gwork,
-                            uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    const int it = blockIdx.x * blockDim.x + threadIdx.x;
-    if (it >= m) return;
-    const int g = item_group[it];
-    const float w = gwork[g] * (float)item_points[it] / (float)max(gpoints[g], 1);
-    keys[it] = ~__float_as_uint(fmaxf(w, 0.f));
-    vals[it] = (uint32_t)it;
+// Traversal order: per group the mean predicted walk length of its queries;
+// sort key larger first.
+__global__ void k_group_keys(int G, const int32_t *__restrict__ group_begin, const int32_t *__restrict__ group_count,
+                             const float *__restrict__ y, TargetNorm tn, uint32_t *__restrict__ keys,
+                             uint32_t *__restrict__ vals) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const int qb = group_begin[g], qn = group_count[g];
+    float s = 0.f;
+    for (int q = 0; q < qn; ++q) s += predicted(y, qb + q, 1, tn);
+    keys[g] = ~__float_as_uint(fmaxf(s / (float)max(qn, 1), 0.f));
+    vals[g] = (uint32_t)g;
 }
 
 Norm make_norm(const float *mean, const float *std_, int d, bool on) {
@@ -253,8 +243,8 @@ void moments(const float *x, int64_t n, int d, float *mean, float *std_, cudaStr
 
 }  // namespace
 
-void features_from_groups(const ct_tree *t, double eps, const int32_t *gblocks, const int32_t *gpoints,
-                          const ct_predictor *P, float *x, cudaStream_t s) {
+// Raw (P == nullptr) or standardised features of every tree position.
+void predictor_features(const ct_tree *t, double eps, const ct_predictor *P, float *x, cudaStream_t s) {
     const int64_t n = t->n;
     if (n == 0) return;
     DBuf<int32_t> gof(n, s);
@@ -264,8 +254,7 @@ void features_from_groups(const ct_tree *t, double eps, const int32_t *gblocks, 
     const double e = eps > 1e-20 ? eps : 1e-20;
     k_features<<<grid_of(n, 256), 256, 0, s>>>(n, t->dp, t->metric == CT_L2_F32, t->pts, t->dcen, t->leaf_ids,
                                                t->n_leaves, t->node_begin, t->node_count, t->radius, t->parent,
-                                               t->group_begin, t->group_count, t->group_radius, gof.p, gblocks,
-                                               gpoints, e, nm, x);
+                                               t->group_begin, t->group_count, t->group_radius, gof.p, e, nm, x);
     CT_COUNT_LAUNCH();
     CT_LAUNCH_CHECK();
 }
@@ -299,34 +288,22 @@ void predictor_release(ct_predictor *P) {
         if (p) cudaFree(p);
 }
 
-// Raw features of every position (one traversal).
-void predictor_features(const ct_tree *t, double eps, float *x, cudaStream_t s) {
-    if (t->n == 0) return;
-    Probe pr;
-    pr.x = x;
-    QueryOut tmp;
-    query_impl(t, make_qparams(t, eps, 0), s, tmp, 0, nullptr, &pr);
-}
-
 double predictor_fit(ct_predictor *P, const ct_tree *t, double eps, const ct_fit_opts &o, cudaStream_t s) {
     const int64_t n = t->n;
     const int G = t->n_groups;
-    // one traversal and one FP32 count pass: features and labels
+    // labels from one traversal and one count pass of the plain query
     const QParams qp = make_qparams(t, eps, o.include_self);
-    DBuf<int32_t> deg(n, s), work(n, s), gbl(G ? G : 1, s), gpt(G ? G : 1, s), gof(n, s);
+    DBuf<int32_t> deg(n, s), gvisit(G ? G : 1, s), gof(n, s);
     DBuf<float> x(n * MLP_IN, s), y(n * MLP_OUT, s);
     Probe pr;
-    pr.x = x.p;
     pr.deg = deg.p;
-    pr.work = work.p;
-    pr.gblocks = gbl.p;
-    pr.gpoints = gpt.p;
+    pr.gvisit = gvisit.p;
     QueryOut tmp;
     query_impl(t, qp, s, tmp, 0, nullptr, &pr);
+    predictor_features(t, eps, nullptr, x.p, s);
     k_pos_group<<<grid_of(n, 256), 256, 0, s>>>(n, G, t->group_begin, gof.p);
     CT_COUNT_LAUNCH();
-    k_targets<<<grid_of(n, 256), 256, 0, s>>>(n, t->perm, gof.p, deg.p, pr.work_valid ? work.p : nullptr, gpt.p,
-                                              y.p);
+    k_targets<<<grid_of(n, 256), 256, 0, s>>>(n, t->perm, gof.p, deg.p, gvisit.p, y.p);
     CT_COUNT_LAUNCH();
     CT_LAUNCH_CHECK();
     moments(x.p, n, MLP_IN, P->fmean, P->fstd, s);
@@ -362,35 +339,26 @@ double predictor_fit(ct_predictor *P, const ct_tree *t, double eps, const ct_fit
     return l / ((double)batch * tail);
 }
 
-// Predicted degree and leaf work by original id.
-void predictor_predict(const ct_predictor *P, const ct_tree *t, double eps, float *pdeg, float *pwork,
+// Predicted degree and walk length by original id.
+void predictor_predict(const ct_predictor *P, const ct_tree *t, double eps, float *pdeg, float *pvisit,
                        cudaStream_t s) {
     const int64_t n = t->n;
     if (n == 0) return;
-    const int G = t->n_groups;
     DBuf<float> x(n * MLP_IN, s), y(n * MLP_OUT, s);
-    DBuf<int32_t> gbl(G ? G : 1, s), gpt(G ? G : 1, s);
-    Probe pr;
-    pr.gblocks = gbl.p;
-    pr.gpoints = gpt.p;
-    QueryOut tmp;
-    query_impl(t, make_qparams(t, eps, 0), s, tmp, 0, nullptr, &pr);
-    features_from_groups(t, eps, gbl.p, gpt.p, P, x.p, s);
+    predictor_features(t, eps, P, x.p, s);
     mlp_predict(P->wh, x.p, n, y.p, s);
     TargetNorm tn{{P->tmean[0], P->tmean[1]}, {P->tstd[0], P->tstd[1]}};
-    k_capacity<<<grid_of(n, 256), 256, 0, s>>>(n, y.p, t->perm, tn, 0.f, 0, nullptr, pdeg, pwork);
+    k_capacity<<<grid_of(n, 256), 256, 0, s>>>(n, y.p, t->perm, tn, 0.f, 0, nullptr, pdeg, pvisit);
     CT_COUNT_LAUNCH();
     CT_LAUNCH_CHECK();
 }
 
-void learned_plan(const ct_predictor *P, const ct_tree *t, const QParams &qp, const int32_t *gblocks,
-                  const int32_t *gpoints, const int32_t *item_group, const int32_t *item_points,
-                  const int32_t *nitems_dev, cudaStream_t s, LearnedPlan &lp) {
+void learned_plan(const ct_predictor *P, const ct_tree *t, const QParams &qp, cudaStream_t s, LearnedPlan &lp) {
     if (!P->fitted) CT_FAIL(CT_EINVAL, "the predictor has not been fitted");
     const int64_t n = t->n;
     const int G = t->n_groups;
     DBuf<float> x(n * MLP_IN, s), y(n * MLP_OUT, s);
-    features_from_groups(t, qp.eps64, gblocks, gpoints, P, x.p, s);
+    predictor_features(t, qp.eps64, P, x.p, s);
     mlp_predict(P->wh, x.p, n, y.p, s);
     x.reset();
     const TargetNorm tn{{P->tmean[0], P->tmean[1]}, {P->tstd[0], P->tstd[1]}};
@@ -401,28 +369,18 @@ void learned_plan(const ct_predictor *P, const ct_tree *t, const QParams &qp, co
     CT_COUNT_LAUNCH();
     CT_LAUNCH_CHECK();
     exclusive_scan_i32_to_i64(cap.p, lp.cap_off.p, n + 1, nullptr, s);
-    // items by decreasing predicted work
-    DBuf<int32_t> gof(n, s);
-    DBuf<float> gwork(G ? G : 1, s);
-    CT_CHECK_CUDA(cudaMemsetAsync(gwork.p, 0, (G ? G : 1) * sizeof(float), s));
-    k_pos_group<<<grid_of(n, 256), 256, 0, s>>>(n, G, t->group_begin, gof.p);
-    CT_COUNT_LAUNCH();
-    k_group_work<<<grid_of(n, 256), 256, 0, s>>>(n, y.p, gof.p, tn, gwork.p);
-    CT_COUNT_LAUNCH();
-    CT_LAUNCH_CHECK();
-    int32_t m = 0;
-    int64_t total = 0;
-    to_host(&m, nitems_dev, 1, s);
-    to_host(&total, lp.cap_off.p + n, 1, s);
-    if (m > 1 && P->order_by_work) {
-        DBuf<uint32_t> keys(m, s), vals(m, s), tk(m, s), tv(m, s);
-        k_item_keys<<<grid_of(m, 256), 256, 0, s>>>(m, item_group, item_points, gpoints, gwork.p, keys.p, vals.p);
+    // groups by decreasing predicted walk length
+    if (G > 1 && P->order_by_work) {
+        DBuf<uint32_t> keys(G, s), vals(G, s), tk(G, s), tv(G, s);
+        k_group_keys<<<grid_of(G, 256), 256, 0, s>>>(G, t->group_begin, t->group_count, y.p, tn, keys.p, vals.p);
         CT_COUNT_LAUNCH();
         CT_LAUNCH_CHECK();
-        radix_sort_pairs(keys.p, vals.p, tk.p, tv.p, m, 32, s);
-        lp.item_order = DBuf<int32_t>(m, s);
-        CT_CHECK_CUDA(cudaMemcpyAsync(lp.item_order.p, vals.p, m * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        radix_sort_pairs(keys.p, vals.p, tk.p, tv.p, G, 32, s);
+        lp.group_order = DBuf<int32_t>(G, s);
+        CT_CHECK_CUDA(cudaMemcpyAsync(lp.group_order.p, vals.p, G * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     }
+    int64_t total = 0;
+    to_host(&total, lp.cap_off.p + n, 1, s);
     lp.cap_total = total;
     lp.arena = (int64_t)std::ceil((double)P->arena_frac * (double)total) + P->arena_min;
     // the one-pass buffers must fit comfortably; else the two-pass form

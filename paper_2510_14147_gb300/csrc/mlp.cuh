@@ -40,7 +40,8 @@ struct ct_predictor {
     int32_t pad = 16;
     float arena_frac = 0.25f;
     int64_t arena_min = 65536;
-    // launch the leaf work items in order of decreasing predicted work
+    // walk the groups in order of decreasing predicted walk length (else by
+    // decreasing group radius)
     int32_t order_by_work = 1;
 };
 
@@ -50,8 +51,8 @@ void predictor_release(ct_predictor *P);
 // Trains on the tree's exact labels; returns the mean standardised loss of
 // the last tenth of the steps.
 double predictor_fit(ct_predictor *P, const ct_tree *t, double eps, const ct_fit_opts &o, cudaStream_t s);
-// Raw features of every tree position (runs the traversal).
-void predictor_features(const ct_tree *t, double eps, float *x, cudaStream_t s);
-void predictor_predict(const ct_predictor *P, const ct_tree *t, double eps, float *pdeg, float *pwork,
+// Features of every tree position (raw when P is null, else standardised).
+void predictor_features(const ct_tree *t, double eps, const ct_predictor *P, float *x, cudaStream_t s);
+void predictor_predict(const ct_predictor *P, const ct_tree *t, double eps, float *pdeg, float *pvisit,
                        cudaStream_t s);
 }  // namespace ct

@@ -209,6 +209,13 @@ __device__ __forceinline__ int walk_group(const TreeView &tv, int2 *__restrict__
     return 0;
 }
 
+// Vertices the warp tested for group g (for fitting the predictor).
+__device__ __forceinline__ void group_visits(int32_t *gvisit, int g, unsigned long long mine) {
+    unsigned long long v = mine;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) gvisit[g] = (int32_t)(v < 0x7fffffffull ? v : 0x7fffffffull);
+}
+
 // L2 test of `take` consecutive vertices against the group centre (shared
 // memory): TPD lanes share one vertex and read its centre row in coalesced
 // 16-byte pieces; the partial sums are reduced by shuffles and lane i gets
@@ -247,7 +254,7 @@ __device__ __forceinline__ bool l2_keep(const TreeView &tv, const float4 *cen, i
 template <int TPD>
 __global__ void __launch_bounds__(TRAV_WARPS * 32) k_traverse_l2(
     TreeView tv, QParams qp, Pool P, int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st,
-    int32_t *__restrict__ err, int32_t *__restrict__ next_group) {
+    int32_t *__restrict__ err, int32_t *__restrict__ next_group, int32_t *__restrict__ gvisit) {
     extern __shared__ float4 sc[];  // TRAV_WARPS x (dp/4)
     const int nq4 = tv.dp >> 2;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -268,7 +275,9 @@ __global__ void __launch_bounds__(TRAV_WARPS * 32) k_traverse_l2(
         __syncwarp();
         const float add = qp.eps_up + tv.group_radius[g];
         auto tester = [&](int first, int take) { return l2_keep<TPD>(tv, cen, nq4, first, take, add); };
+        const unsigned long long e0 = evals;
         if (walk_group(tv, stack, cap, g, P, pc, evals, err, tester) < 0) return;
+        if (gvisit) group_visits(gvisit, g, evals - e0);
         __syncwarp();
     }
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
@@ -281,7 +290,7 @@ __global__ void __launch_bounds__(TRAV_WARPS * 32) k_traverse_l2(
 template <int W>
 __global__ void __launch_bounds__(32) k_traverse_lev(
     TreeView tv, QParams qp, Pool P, int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st,
-    int32_t *__restrict__ err, int32_t *__restrict__ next_group) {
+    int32_t *__restrict__ err, int32_t *__restrict__ next_group, int32_t *__restrict__ gvisit) {
     __shared__ uint64_t peq[256 * W];
     const int lane = threadIdx.x;
     int2 *stack = stacks + (int64_t)blockIdx.x * cap;
@@ -309,7 +318,9 @@ __global__ void __launch_bounds__(32) k_traverse_lev(
             const int n = (int)(tv.soff[vp + 1] - tv.soff[vp]);
             return lev_myers<W>(peq, m, txt, n, k) <= k;
         };
+        const unsigned long long e0 = evals;
         if (walk_group(tv, stack, cap, g, P, pc, evals, err, tester) < 0) return;
+        if (gvisit) group_visits(gvisit, g, evals - e0);
     }
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
     if (lane == 0) stat_add(st, ST_TRAV, evals);
@@ -605,7 +616,7 @@ struct LeafShared {
     int rpos[RCAP];
     uint8_t rli[RCAP];
     int64_t rowb[32], rowe[32];
-    int cursor[32], qcnt[32], qwk[32];
+    int cursor[32], qcnt[32];
     int gpos[GQ_CAP];
     uint8_t gq[GQ_CAP], gb[GQ_CAP];
     int gn, nb_fill, scan_tmp[LEAF_T / 32];
@@ -636,11 +647,7 @@ struct Items {
     const int32_t *group;
     const int64_t *begin, *end;
     const int32_t *count;  // device: number of items
-    const int32_t *order;  // launch order of the items (nullptr: as built)
 };
-__device__ __forceinline__ int item_of_block(const Items &items) {
-    return items.order ? items.order[blockIdx.x] : (int)blockIdx.x;
-}
 
 // One-pass emit (learned form): the count pass also writes every edge into a
 // per-row capacity region sized from the predicted degree.  A row's entries
@@ -683,12 +690,11 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
     TreeView tv, QParams qp, Items items, const uint32_t *__restrict__ cand,
     uint32_t *__restrict__ emask, int32_t *__restrict__ deg, const int64_t *__restrict__ row_ptr,
     int32_t *__restrict__ rowcur, int32_t *__restrict__ col, float *__restrict__ dist,
-    unsigned long long *__restrict__ st, int32_t *__restrict__ err, CapOut co, const uint8_t *__restrict__ rowsel,
-    int32_t *__restrict__ qwork) {
+    unsigned long long *__restrict__ st, int32_t *__restrict__ err, CapOut co, const uint8_t *__restrict__ rowsel) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
-    if ((int)blockIdx.x >= *items.count) return;
-    const int it = item_of_block(items);
+    const int it = blockIdx.x;
+    if (it >= *items.count) return;
     const int g = items.group[it];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int qi = tid >> 3, pj = tid & 7;
@@ -706,7 +712,6 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
         __syncthreads();
         if (tid < 32) {
             S.qcnt[tid] = 0;
-            S.qwk[tid] = 0;
             bool sel = false;
             if (tid < nqr) {
                 int o = tv.perm[qfirst + tid];
@@ -910,17 +915,6 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
             }
             __syncthreads();
             const int T = S.bpre[NB];
-            // fitting the predictor: points each query evaluates after stage 1
-            if (!EMIT && qwork) {
-                for (int li = tid; li < bn; li += LEAF_T) {
-                    uint32_t m = S.bmask[li] & qvalid;
-                    while (m) {
-                        const int q = __ffs(m) - 1;
-                        m &= m - 1u;
-                        atomicAdd(&S.qwk[q], S.bcnt[li]);
-                    }
-                }
-            }
 
             // ---- emit pass: one thread per (query, point) pair of the blocks in
             // which the query found an edge; same arithmetic as the tiles;
@@ -1148,7 +1142,6 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
                 if (qi + 16 < nqr && cnt1 + S.qcnt[qi + 16])
                     atomicAdd(&deg[S.cursor[qi + 16]], cnt1 + S.qcnt[qi + 16]);
             }
-            if (qwork && tid < nqr && S.qwk[tid]) atomicAdd(&qwork[S.cursor[tid]], S.qwk[tid]);
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -1198,30 +1191,6 @@ __global__ void k_check_rows_sel(int64_t n, const int64_t *__restrict__ row_ptr,
                                  const uint8_t *__restrict__ rowsel, int32_t *__restrict__ err) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && rowsel[i] && row_ptr[i] + rowcur[i] != row_ptr[i + 1]) atomicOr(err, 8);
-}
-
-// Candidate points of every work item, and candidate blocks and points per
-// group (block per item).
-__global__ void k_item_stats(Items items, const uint32_t *__restrict__ cand, const int32_t *__restrict__ node_count,
-                             int32_t *__restrict__ ipoints, int32_t *__restrict__ gblocks,
-                             int32_t *__restrict__ gpoints) {
-    if ((int)blockIdx.x >= *items.count) return;
-    const int it = blockIdx.x;
-    const int64_t b = items.begin[it], e = items.end[it];
-    int sum = 0;
-    for (int64_t k = b + threadIdx.x; k < e; k += blockDim.x) sum += node_count[cand[k] & ~FLAG];
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    __shared__ int part[32];
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int tot = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += part[w];
-        ipoints[it] = tot;
-        const int g = items.group[it];
-        atomicAdd(&gpoints[g], tot);
-        atomicAdd(&gblocks[g], (int)(e - b));
-    }
 }
 
 // One-pass emit, after the count pass: every row's produced entries must
@@ -1366,8 +1335,8 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_tc(TreeView tv, QParams qp, 
                                                     int32_t *__restrict__ err, CapOut co) {
     extern __shared__ unsigned char tc_raw[];
     TcShared &S = *reinterpret_cast<TcShared *>(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
-    if ((int)blockIdx.x >= *items.count) return;
-    const int it = item_of_block(items);
+    const int it = blockIdx.x;
+    if (it >= *items.count) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = items.group[it];
     const int dp = tv.dp, dim = tv.dim, dp4 = dp >> 2;
@@ -1691,8 +1660,8 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf_lev(
     __shared__ int s_off, s_rows;
     __shared__ unsigned s_hit;
     const int tid = threadIdx.x, warp = tid >> 5;
-    if ((int)blockIdx.x >= *items.count) return;
-    const int it = item_of_block(items);
+    const int it = blockIdx.x;
+    if (it >= *items.count) return;
     const int g = items.group[it];
     const int qb = tv.group_begin[g], qn = tv.group_count[g];
     const int64_t c0 = items.begin[it], c1 = items.end[it];
@@ -2018,7 +1987,7 @@ int64_t pool_capacity_guess(const ct_tree *t, const TravLaunch &tl) {
 // Clears the pool counters and launches the traversal (allocates nothing).
 void launch_traversal(const ct_tree *t, const TreeView &tv, const QParams &qp, const Pool &P, int2 *stacks, int cap,
                       const TravLaunch &tl, unsigned long long *st, int32_t *err, int32_t *next_group,
-                      cudaStream_t s) {
+                      cudaStream_t s, int32_t *gvisit = nullptr) {
     // P.next .. P.overflow are the four 64-bit words of one counter block
     CT_CHECK_CUDA(cudaMemsetAsync(next_group, 0, sizeof(int32_t), s));
     CT_CHECK_CUDA(cudaMemsetAsync(P.next, 0, 4 * sizeof(unsigned long long), s));
@@ -2032,7 +2001,7 @@ void launch_traversal(const ct_tree *t, const TreeView &tv, const QParams &qp, c
     case T:                                                                                                     \
         if (tsm > 48 * 1024)                                                                                    \
             CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)); \
-        k_traverse_l2<T><<<tl.blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, P, stacks, cap, st, err, next_group); \
+        k_traverse_l2<T><<<tl.blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, P, stacks, cap, st, err, next_group, gvisit); \
         break;
             CT_TRL(1) CT_TRL(2) CT_TRL(4) CT_TRL(8)
 #undef CT_TRL
@@ -2040,7 +2009,7 @@ void launch_traversal(const ct_tree *t, const TreeView &tv, const QParams &qp, c
     } else {
         switch (lev_words_for(t->max_len)) {
 #define CT_TL(WW) \
-    case WW: k_traverse_lev<WW><<<tl.blocks, 32, 0, s>>>(tv, qp, P, stacks, cap, st, err, next_group); break;
+    case WW: k_traverse_lev<WW><<<tl.blocks, 32, 0, s>>>(tv, qp, P, stacks, cap, st, err, next_group, gvisit); break;
             CT_TL(1) CT_TL(2) CT_TL(4) CT_TL(8) CT_TL(16)
 #undef CT_TL
         }
@@ -2058,6 +2027,15 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
     DBuf<unsigned long long> st(ST_N, s);
     CT_CHECK_CUDA(cudaMemsetAsync(st.p, 0, ST_N * sizeof(unsigned long long), s));
     int32_t *err = reinterpret_cast<int32_t *>(st.p + ST_ERR);
+
+    // learned form: row capacities and the traversal order from the predictor
+    LearnedPlan lp;
+    if (pred && !probe && n > 0) {
+        ProfScope ps("predict", s);
+        learned_plan(pred, t, qp, s, lp);
+        if (lp.group_order.p) tv.group_order = lp.group_order.p;
+    }
+    int32_t *gvisit = probe ? probe->gvisit : nullptr;
 
     const int W = l2 ? 1 : lev_words_for(t->max_len);
     // 1. traversal: one pass into the candidate pool (rerun once if it overflows)
@@ -2082,7 +2060,7 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
                  reinterpret_cast<int32_t *>(ctr.p + 1), seg_cap, ctr.p + 2, reinterpret_cast<int32_t *>(ctr.p + 3)};
         {
             ProfScope ps("traverse", s);
-            launch_traversal(t, tv, qp, P, stacks.p, cap, tl, st.p, err, next_group.p, s);
+            launch_traversal(t, tv, qp, P, stacks.p, cap, tl, st.p, err, next_group.p, s, gvisit);
         }
         to_host(hc, ctr.p, 4, s);
         if (!(uint32_t)hc[3]) break;
@@ -2099,7 +2077,7 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
     const int64_t max_items = nseg + n_cand / kItem + 1;
     DBuf<int32_t> icnt(nseg + 1, s), igroup(max_items, s), nitems(1, s);
     DBuf<int64_t> ioff(nseg + 1, s), ibeg(max_items, s), iend(max_items, s);
-    Items items{igroup.p, ibeg.p, iend.p, nitems.p, nullptr};
+    Items items{igroup.p, ibeg.p, iend.p, nitems.p};
     CT_CHECK_CUDA(cudaMemsetAsync(nitems.p, 0, sizeof(int32_t), s));
     if (nseg) {
         k_item_counts<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_count.p, icnt.p);
@@ -2112,33 +2090,6 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
     }
     DBuf<int32_t> rowcur(n + 1, s);
     uint32_t *cand_p = pool.p;
-
-    // learned form: candidate counts per group and item, features, the plan
-    LearnedPlan lp;
-    if (pred || probe) {
-        DBuf<int32_t> gb_own, gp_own;
-        int32_t *gbl = probe && probe->gblocks ? probe->gblocks : (gb_own = DBuf<int32_t>(G ? G : 1, s)).p;
-        int32_t *gpt = probe && probe->gpoints ? probe->gpoints : (gp_own = DBuf<int32_t>(G ? G : 1, s)).p;
-        DBuf<int32_t> ipts(max_items, s);
-        CT_CHECK_CUDA(cudaMemsetAsync(gbl, 0, (G ? G : 1) * sizeof(int32_t), s));
-        CT_CHECK_CUDA(cudaMemsetAsync(gpt, 0, (G ? G : 1) * sizeof(int32_t), s));
-        if (nseg) {
-            k_item_stats<<<(unsigned)max_items, 128, 0, s>>>(items, cand_p, t->node_count, ipts.p, gbl, gpt);
-            CT_COUNT_LAUNCH();
-            CT_LAUNCH_CHECK();
-        }
-        if (probe) {
-            if (probe->x) features_from_groups(t, qp.eps64, gbl, gpt, nullptr, probe->x, s);
-            if (!probe->deg) {
-                out.stats.candidates = n_cand;
-                return;
-            }
-        } else if (n > 0) {
-            ProfScope ps("predict", s);
-            learned_plan(pred, t, qp, gbl, gpt, igroup.p, ipts.p, nitems.p, s, lp);
-            if (lp.item_order.p) items.order = lp.item_order.p;
-        }
-    }
 
     // alphabet of the strings (edit distance)
     DBuf<uint8_t> amap;
@@ -2198,20 +2149,15 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
     // 2. count pass
     DBuf<int32_t> deg(n + 1, s);
     CT_CHECK_CUDA(cudaMemsetAsync(deg.p, 0, (n + 1) * sizeof(int32_t), s));
-    int32_t *qwork = probe && probe->work && l2 ? probe->work : nullptr;
-    if (qwork) {
-        CT_CHECK_CUDA(cudaMemsetAsync(qwork, 0, n * sizeof(int32_t), s));
-        probe->work_valid = true;
-    }
     auto leaf = [&](bool emit, int64_t *row_ptr, int32_t *col, float *dist, const uint8_t *rowsel) {
         if (G == 0 || nseg == 0) return;
         const CapOut cw = emit ? CapOut{} : co;
         if (l2) {
             leaf_l2_prepare();
             if (emit)
-                k_leaf_l2<true><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel, nullptr);
+                k_leaf_l2<true><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel);
             else
-                k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel, emit ? nullptr : qwork);
+                k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel);
         } else {
             switch (W) {
 #define CT_LL(WW)                                                                                                      \
@@ -2232,7 +2178,7 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
     };
     // the tensor-core filter applies to L2 rows of at most 128 floats; wider
     // rows use the FP32 tiles (same output)
-    const bool use_tc = precision == 1 && l2 && t->dp <= 128 && !qwork;
+    const bool use_tc = precision == 1 && l2 && t->dp <= 128;
     if (use_tc) {
         ProfScope ps("leaf_count_tc", s);
         static bool tc_ready = false;
@@ -2264,7 +2210,7 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
     };
 
     if (probe) {  // labels for fitting the predictor
-        if (n) CT_CHECK_CUDA(cudaMemcpyAsync(probe->deg, deg.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        if (n && probe->deg) CT_CHECK_CUDA(cudaMemcpyAsync(probe->deg, deg.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
         finish_stats();
         return;
     }
@@ -2455,11 +2401,11 @@ void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cuda
         k_item_fill<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_group, seg_begin, seg_count, ioff, igroup, ibeg,
                                                        iend, nitems);
         CT_COUNT_LAUNCH();
-        Items items{igroup, ibeg, iend, nitems, nullptr};
+        Items items{igroup, ibeg, iend, nitems};
         leaf_l2_prepare();
         k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, pool, nullptr, degrees, nullptr,
                                                                           nullptr, nullptr, nullptr, st, err, CapOut{},
-                                                                          nullptr, nullptr);
+                                                                          nullptr);
         CT_COUNT_LAUNCH();
     }
     CT_LAUNCH_CHECK();

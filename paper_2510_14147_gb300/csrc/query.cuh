@@ -37,33 +37,23 @@ struct QueryOut {
 void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out);
 void query_tc(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out);
 
-// Learned form.  A probe stops the query early and hands out what the
-// predictor needs: after the traversal the per-group candidate counts and the
-// raw features (x), after the count pass the labels (deg, work).
+// Learned form.  A probe collects the labels for fitting the predictor: the
+// query stops after the count pass.
 struct Probe {
-    float *x = nullptr;         // n x 16 raw features by tree position
     int32_t *deg = nullptr;     // n, by original id: degree
-    int32_t *work = nullptr;    // n, by original id: points evaluated after the leaf-centre test
-    int32_t *gblocks = nullptr; // G: candidate leaf blocks per group
-    int32_t *gpoints = nullptr; // G: points of those blocks
-    bool work_valid = false;    // set when the count pass measured `work`
+    int32_t *gvisit = nullptr;  // G: vertices tested by each group's walk
 };
-// What the predictor decided after the traversal.
+// What the predictor decided before the traversal.
 struct LearnedPlan {
     DBuf<int64_t> cap_off;      // n + 1 row capacity offsets by original id
     int64_t cap_total = 0;
     int64_t arena = 0;          // overflow arena entries
-    DBuf<int32_t> item_order;   // work items by decreasing predicted work
+    DBuf<int32_t> group_order;  // groups by decreasing predicted walk length
     bool one_pass = false;
 };
 void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out, int precision,
                 const ct_predictor *P, Probe *probe);
-// Raw (P == nullptr) or standardised features from the group candidate counts.
-void features_from_groups(const ct_tree *t, double eps, const int32_t *gblocks, const int32_t *gpoints,
-                          const ct_predictor *P, float *x, cudaStream_t s);
-void learned_plan(const ct_predictor *P, const ct_tree *t, const QParams &qp, const int32_t *gblocks,
-                  const int32_t *gpoints, const int32_t *item_group, const int32_t *item_points,
-                  const int32_t *nitems_dev, cudaStream_t s, LearnedPlan &lp);
+void learned_plan(const ct_predictor *P, const ct_tree *t, const QParams &qp, cudaStream_t s, LearnedPlan &lp);
 
 // Sorts every CSR row by column, moving dist along.
 void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int64_t nnz,

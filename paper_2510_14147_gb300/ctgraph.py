@@ -128,6 +128,8 @@ def _load():
                                          P(C.c_double)]
         lib.ct_predictor_set_capacity.restype = C.c_int
         lib.ct_predictor_set_capacity.argtypes = [C.c_void_p, C.c_float, C.c_int32, C.c_float, C.c_int64]
+        lib.ct_predictor_set_order.restype = C.c_int
+        lib.ct_predictor_set_order.argtypes = [C.c_void_p, C.c_int32]
         lib.ct_predictor_get_params.restype = C.c_int
         lib.ct_predictor_get_params.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         lib.ct_predictor_set_params.restype = C.c_int
@@ -427,9 +429,9 @@ def ct_predictor_free(p: Predictor):
 
 def ct_predictor_fit(p: Predictor, tree: Tree, eps: float, steps: int = 0, batch: int = 0, lr: float = 0.0,
                      include_self: bool = False, seed: int = 0, stream=None) -> float:
-    """Labels the tree's points with their exact degrees and leaf work and
-    trains the MLP; returns the mean standardised loss of the last tenth of
-    the steps."""
+    """Labels the tree's points with their exact degrees and group walk
+    lengths and trains the MLP; returns the mean standardised loss of the
+    last tenth of the steps."""
     o = ct_fit_opts(int(steps), int(batch), float(lr), int(bool(include_self)), int(seed))
     loss = C.c_double()
     _check(_load().ct_predictor_fit(p.handle, tree.handle, float(eps), C.byref(o), C.c_void_p(_stream(stream)),
@@ -441,6 +443,10 @@ def ct_predictor_set_capacity(p: Predictor, margin: float = 0.5, pad: int = 16, 
                               arena_min: int = 65536):
     _check(_load().ct_predictor_set_capacity(p.handle, float(margin), int(pad), float(arena_frac),
                                              int(arena_min)))
+
+
+def ct_predictor_set_order(p: Predictor, by_predicted_work: bool = True):
+    _check(_load().ct_predictor_set_order(p.handle, int(bool(by_predicted_work))))
 
 
 def ct_predictor_get_params(p: Predictor):
@@ -471,7 +477,7 @@ def ct_predictor_features(tree: Tree, eps: float, stream=None):
 
 
 def ct_predictor_predict(p: Predictor, tree: Tree, eps: float, stream=None):
-    """(predicted degree, predicted leaf work), CUDA float32 by original id."""
+    """(predicted degree, predicted group walk length), CUDA float32 by original id."""
     import torch
     d = torch.empty(max(tree.n, 1), dtype=torch.float32, device="cuda")
     b = torch.empty(max(tree.n, 1), dtype=torch.float32, device="cuda")

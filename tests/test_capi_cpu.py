@@ -69,6 +69,7 @@ def test_invalid_arguments_without_gpu():
     lib.ct_predictor_free(None)
     assert lib.ct_predictor_fit(None, None, 1.0, None, None, None) == cg.CT_EINVAL
     assert lib.ct_predictor_set_capacity(None, 0.5, 16, 0.25, 0) == cg.CT_EINVAL
+    assert lib.ct_predictor_set_order(None, 1) == cg.CT_EINVAL
     assert lib.ct_predictor_get_params(None, None, None) == cg.CT_EINVAL
     assert lib.ct_predictor_set_params(None, None, None) == cg.CT_EINVAL
     assert lib.ct_predictor_features(None, 1.0, None, None) == cg.CT_EINVAL

@@ -87,16 +87,16 @@ def test_features_hand_computed():
     tree, pts = _two_leaf_tree()
     gb, gc, parent = mlp.query_groups(tree)
     assert list(gb) == [0] and list(gc) == [4] and list(parent) == [-1, 0, 0]
-    F = mlp.features(tree, pts, 1.0, gblocks=[2], gpoints=[4])
+    F = mlp.features(tree, pts, 1.0)
     L = np.log1p
-    want1 = [L(1), L(1), L(11), 2.0, L(2), L(4), L(2), L(1), L(4), L(11), L(4), L(11), L(2), L(4), L(4), L(4)]
-    want2 = [0.0, L(10), L(11), 2.0, L(2), L(4), L(2), L(1), L(4), L(11), L(4), L(11), L(2), L(4), L(4), L(4)]
+    anc = [L(2), L(1), L(4), L(11), L(4), L(11), L(4), L(11)]   # leaf, root, root, root
+    want1 = [L(1), L(1), L(11), 2.0] + anc + [L(2), L(4), L(4), L(4)]
+    want2 = [0.0, L(10), L(11), 2.0] + anc + [L(2), L(4), L(4), L(4)]
     assert np.allclose(F[1], want1, rtol=0, atol=1e-15)
     assert np.allclose(F[2], want2, rtol=0, atol=1e-15)
     # eps = 0.5: the leaf block (radius 1) already has radius >= e and >= 2e
     F = mlp.features(tree, pts, 0.5)
     assert list(F[0, 12:16]) == [L(2), L(2), L(4), L(4)]
-    assert np.isnan(F[0, 4]) and np.isnan(F[0, 5])
 
 
 def test_query_groups_split_at_32_points():
