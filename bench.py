@@ -7,7 +7,11 @@ Default workload: 1,000,000 points, 128-D, 100-component Gaussian mixture in
 sift eps=175 shape).  Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                  [--workload gmm_1m_k70] [--precision 0|1] [--no-cpu-baseline]
+                  [--workload gmm_1m_k70] [--form tc+learned|tc|learned|plain]
+                  [--no-compare] [--no-cpu-baseline] [--no-e2e]
+
+The default form is the BF16-filtered, learned one; the plain FP32 two-pass
+form is timed beside it on the same input ("plain" in the JSON line).
 
 With N > 1 (torchrun) every rank runs an independent replica of the workload
 (nothing is sharded; weak scaling) and the time is the max over ranks.
@@ -208,12 +212,16 @@ def run_reference(args, wl):
     return 0
 
 
+FORMS = {"plain": (0, False), "tc": (1, False), "learned": (0, True), "tc+learned": (1, True)}
+
+
 def config_of(args, wl, world):
+    prec, learned = FORMS[args.form]
     return {"workload": args.workload, "n": wl["n"], "dim": wl["dim"], "eps": wl["eps"],
             "zeta": wl.get("zeta", 32), "target_degree": wl.get("target_degree"),
-            "precision": args.precision, "parallelism": "replicas%d" % world if world > 1 else "single",
+            "form": args.form, "precision": prec, "learned": learned,
+            "parallelism": "replicas%d" % world if world > 1 else "single",
             "l2": "inputs (%.0f MB) larger than L2 (129 MB); no flush" % (wl["n"] * wl["dim"] * 4 / 1e6),
-            "learned": bool(args.learned),
             "step": "ct_build + eps_graph_query + csr_free"}
 
 
@@ -226,17 +234,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="gmm_1m_k70")
-    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--form", default="tc+learned", choices=sorted(FORMS),
+                    help="plain: FP32 two-pass; tc: BF16 tensor-core filter; learned: one-pass emit "
+                         "sized by the predictor; tc+learned: both")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the plain form beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-queries", type=int, default=4000)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--learned", action="store_true",
-                    help="one-pass emit into capacities from a predictor fitted on another draw")
     ap.add_argument("--fit-steps", type=int, default=1500)
     ap.add_argument("--order-radius", action="store_true",
-                    help="learned form: walk groups by radius instead of predicted walk length")
+                    help="learned forms: walk groups by radius instead of predicted walk length")
     args = ap.parse_args()
     wl = I.load_workloads()[args.workload]
+    precision, learned = FORMS[args.form]
 
     if args.impl == "reference":
         return run_reference(args, wl)
@@ -263,30 +273,28 @@ def main():
     last = {}
     pred = None
     fit_info = None
-    if args.learned:
+    if learned:
         # fitted once, outside the timed region, on another draw of the recipe
-        import time
         wl_fit = dict(wl, seed=wl["seed"] + 1)
         xf = torch.from_numpy(load_points(wl_fit)).cuda()
         with torch.cuda.stream(stream):
             tf = cg.ct_build(points=xf, leaf_size=zeta, stream=stream)
             pred = cg.ct_predictor_create(seed=1)
             t0 = time.perf_counter()
-            loss = cg.ct_predictor_fit(pred, tf, eps, steps=args.fit_steps, seed=2,
-                                       stream=stream)
+            loss = cg.ct_predictor_fit(pred, tf, eps, steps=args.fit_steps, seed=2, stream=stream)
             fit_s = time.perf_counter() - t0
             tf.free()
             if args.order_radius:
                 cg.ct_predictor_set_order(pred, False)
         del xf
-        fit_info = {"fit_on": "seed %d draw" % wl_fit["seed"], "fit_steps": args.fit_steps,
-                    "final_loss": loss, "fit_s": fit_s,
+        fit_info = {"fit_on": "another draw of the recipe (seed %d)" % wl_fit["seed"],
+                    "fit_steps": args.fit_steps, "final_loss": loss, "fit_s": fit_s,
                     "walk_order": "radius" if args.order_radius else "predicted walk length"}
 
-    def step(points):
+    def step(points, prec=precision, use_pred=learned):
         t = cg.ct_build(points=points, leaf_size=zeta, stream=stream)
-        c = cg.eps_graph_query(t, eps, precision=args.precision, stream=stream, use_predictor=args.learned,
-                               predictor=pred)
+        c = cg.eps_graph_query(t, eps, precision=prec, stream=stream, use_predictor=use_pred,
+                               predictor=pred if use_pred else None)
         last["nnz"] = c.nnz
         last["stats"] = c.stats()
         c.free()
@@ -298,7 +306,6 @@ def main():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step(xd)
@@ -337,6 +344,31 @@ def main():
     st = last["stats"]
     nnz = last["nnz"]
 
+    # the plain form on the same input, for the comparison
+    plain = None
+    if args.form != "plain" and not args.no_compare:
+        with torch.cuda.stream(stream):
+            step(xd, 0, False)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tot = 0
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                tot += step(xd, 0, False)
+        b.record(stream)
+        barrier()
+        tp = a.elapsed_time(b)
+        if dist:
+            tt = torch.tensor([tp], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            tp = float(tt.item())
+            tot *= world
+        if not dist and tot != nnz_total:
+            raise RuntimeError("plain form produced a different edge count")
+        plain = {"form": "plain", "value": tot / (tp / 1e3), "ms_per_step": tp / args.steps,
+                 "speedup_of_form": value / (tot / (tp / 1e3))}
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -349,8 +381,8 @@ def main():
         def e2e_step():
             xdev.copy_(xh, non_blocking=True)
             t = cg.ct_build(points=xdev, leaf_size=zeta, stream=stream)
-            c = cg.eps_graph_query(t, eps, precision=args.precision, stream=stream,
-                                   use_predictor=args.learned, predictor=pred)
+            c = cg.eps_graph_query(t, eps, precision=precision, stream=stream,
+                                   use_predictor=learned, predictor=pred)
             rp_h.copy_(c.row_ptr, non_blocking=True)
             col_h[:c.nnz].copy_(c.col, non_blocking=True)
             dist_h[:c.nnz].copy_(c.dist, non_blocking=True)
@@ -390,18 +422,20 @@ def main():
     dom = max(kernel_stages, key=lambda k: kernel_stages[k][0]) if kernel_stages else None
     roof = None
     if "leaf_count_tc" in prof:
-        # precision 1: the BF16 MMA of every (query, candidate) pair is the
-        # contraction; FP32 rechecks are extra ALU work beside it
+        # BF16 form: 32 queries x 128 dims x 2 flops per 512-byte candidate row is
+        # 16 flop/B, far below the tensor ridge (~250 flop/B): the tiles are
+        # bound by streaming the candidate rows, so the roofline is HBM
         t_launch = prof["leaf_count_tc"][0] / prof["leaf_count_tc"][1] / 1e3
-        kdim = (wl["dim"] + 15) // 16 * 16
-        flops = st["leaf_pairs"] * 2.0 * kdim
-        bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops") or 1700.0
-        ach = flops / t_launch / 1e12
-        roof = {"kernel": "k_leaf_tc", "bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
-                "frac": ach / bf16, "traffic": profile_traffic("k_leaf_tc", args.workload),
-                "peak_note": "measured cuBLAS bf16 (sustained) from MEASURED_PEAKS.json" if peaks
-                             else "fallback 1.7 PFLOP/s sustained",
-                "flops_per_launch": flops, "ms_per_launch": t_launch * 1e3,
+        nbytes = st["leaf_rows"] * wl["dim"] * 4.0
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        ach = nbytes / t_launch / 1e9
+        roof = {"kernel": "k_leaf_tc", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": profile_traffic("k_leaf_tc", args.workload),
+                "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)" if peaks else "fallback 6.8 TB/s",
+                "bytes_per_launch": nbytes, "bytes_rule": "candidate point rows loaded x dim x 4 B",
+                "ms_per_launch": t_launch * 1e3, "tensor_flops_per_launch": st["leaf_pairs"] * 2.0 * wl["dim"],
+                "tensor_frac_of_sustained_bf16": st["leaf_pairs"] * 2.0 * wl["dim"] / t_launch / 1e12
+                / peaks.get("bf16_tflops_sustained", 1700.0),
                 "recheck_fp32_pairs": st["recheck_fp32"], "dominant_stage": dom}
     elif "leaf_count" in prof:
         t_launch = prof["leaf_count"][0] / prof["leaf_count"][1] / 1e3
@@ -421,7 +455,7 @@ def main():
             "config": config_of(args, wl, world), "nnz": nnz, "edges_undirected": nnz // 2,
             "dist_evals_per_s": (st["traversal_evals"] + st["leaf_pairs"]) * world * args.steps / (t_ms / 1e3),
             "query_stats": st, "stage_ms": stage_ms, "roofline": roof, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks, "library": cg.library_path()}
+            "gpu_launches": launches, "clocks": clocks, "library": cg.library_path(), "plain": plain}
     if fit_info:
         line["learned"] = fit_info
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -126,6 +126,7 @@ typedef struct {
     int64_t kernel_launches;  /* kernels this library launched for the query */
     int64_t emit_pairs;       /* pairs evaluated again by the emit pass */
     int64_t reemit_rows;      /* learned form: rows emitted again (overflow arena was full) */
+    int64_t leaf_rows;        /* point rows loaded into the count pass's leaf tiles (L2) */
 } ct_query_stats;
 
 typedef struct ct_tree ct_tree;           /* opaque, device-resident */

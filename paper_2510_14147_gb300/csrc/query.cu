@@ -704,7 +704,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
     const bool fp32_dist_ok = dp <= 128;
     const int qb = tv.group_begin[g], qn = tv.group_count[g];
     const int64_t c0 = items.begin[it], c1 = items.end[it];
-    unsigned long long pairs = 0, s1evals = 0, guard = 0;
+    unsigned long long pairs = 0, s1evals = 0, guard = 0, rows_ld = 0;  // rows_ld: thread 0
 
     for (int q0 = 0; q0 < qn; q0 += 32) {
         const int nqr = min(32, qn - q0);
@@ -855,6 +855,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
             // ---- stage 1 (count pass): per-query test against the block centres
             if (!EMIT) {
                 const int nt = (bn + 31) >> 5;
+                if (tid == 0) rows_ld += bn;
                 issue(0, 0, S.bbeg, bn);
                 for (int t = 0; t < nt; ++t) {
                     if (t + 1 < nt) {
@@ -971,6 +972,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
             // whose block holds an edge of the query)
             for (int R0 = 0; (!EMIT || nkc == 1) && R0 < T; R0 += RCAP) {
                 const int RN = min(RCAP, T - R0);
+                if (!EMIT && tid == 0) rows_ld += RN;
                 __syncthreads();
                 for (int r = tid; r < RN; r += LEAF_T) {
                     const int R = R0 + r;
@@ -1154,6 +1156,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
             stat_add(st, ST_PAIRS, pairs);
             stat_add(st, ST_TRAV, s1evals);
             stat_add(st, ST_GUARD, guard);
+            if (tid == 0) stat_add(st, ST_ROWS, rows_ld);
         } else {
             stat_add(st, ST_EMIT, pairs);
         }
@@ -1343,7 +1346,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_tc(TreeView tv, QParams qp, 
     const int ksteps = (dp + 15) >> 4;
     const int qb = tv.group_begin[g], qn = tv.group_count[g];
     const int64_t c0 = items.begin[it], c1 = items.end[it];
-    unsigned long long pairs = 0, kept = 0, guard = 0;
+    unsigned long long pairs = 0, kept = 0, guard = 0, rows_ld = 0;  // rows_ld: thread 0
     bool failed = false;
 
     if (warp == 0) tc::tmem_alloc(&S.tslot, 32);
@@ -1452,6 +1455,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_tc(TreeView tv, QParams qp, 
             const int T = S.bpre[NB];
             for (int R0 = 0; R0 < T && !failed; R0 += TC_ROWS) {
                 const int rows = min(TC_ROWS, T - R0);
+                if (tid == 0) rows_ld += rows;
                 // row -> (position, block) for this tile
                 {
                     const int r = tid;
@@ -1574,6 +1578,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_tc(TreeView tv, QParams qp, 
         stat_add(st, ST_PAIRS, pairs);
         stat_add(st, ST_RECHECK, kept);
         stat_add(st, ST_GUARD, guard);
+        if (tid == 0) stat_add(st, ST_ROWS, rows_ld);
     }
     if (failed) tc::mbar_wait(&S.mbar, phase ^ 1u, 1u << 22);  // let an outstanding MMA finish
     tc::fence_before_sync();
@@ -2206,6 +2211,7 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
         out.stats.guard_fp64 = (int64_t)hs[ST_GUARD];
         out.stats.recheck_fp32 = (int64_t)hs[ST_RECHECK];
         out.stats.emit_pairs = (int64_t)hs[ST_EMIT];
+        out.stats.leaf_rows = (int64_t)hs[ST_ROWS];
         out.stats.candidates = n_cand;
     };
 

@@ -60,6 +60,6 @@ void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int
                cudaStream_t s);
 
 // Stats slots accumulated on the device.
-enum { ST_TRAV = 0, ST_PAIRS, ST_GUARD, ST_RECHECK, ST_CAND, ST_OVERFLOW, ST_ERR, ST_EMIT, ST_N };
+enum { ST_TRAV = 0, ST_PAIRS, ST_GUARD, ST_RECHECK, ST_CAND, ST_OVERFLOW, ST_ERR, ST_EMIT, ST_ROWS, ST_N };
 
 }  // namespace ct

@@ -59,7 +59,8 @@ class ct_csr(C.Structure):
 class ct_query_stats(C.Structure):
     _fields_ = [(f, C.c_int64) for f in ("traversal_evals", "leaf_pairs", "guard_fp64",
                                            "recheck_fp32", "candidates", "overflow_rows",
-                                           "kernel_launches", "emit_pairs", "reemit_rows")]
+                                           "kernel_launches", "emit_pairs", "reemit_rows",
+                                           "leaf_rows")]
 
 
 class ct_fit_opts(C.Structure):
