@@ -119,7 +119,7 @@ typedef struct {
 typedef struct {
     int64_t traversal_evals;  /* distance evaluations in the tree walk (count pass) */
     int64_t leaf_pairs;       /* (query, candidate point) pairs decided (count pass) */
-    int64_t guard_fp64;       /* pairs re-decided in FP64 (|d - eps| <= 1e-3 eps) */
+    int64_t guard_fp64;       /* pairs decided by the pinned FP64 sum */
     int64_t recheck_fp32;     /* pairs re-evaluated in FP32 after the BF16 filter */
     int64_t candidates;       /* (group, candidate leaf block) entries */
     int64_t overflow_rows;    /* learned form: rows whose degree exceeded the predicted capacity */
@@ -127,6 +127,9 @@ typedef struct {
     int64_t emit_pairs;       /* pairs evaluated again by the emit pass */
     int64_t reemit_rows;      /* learned form: rows emitted again (overflow arena was full) */
     int64_t leaf_rows;        /* point rows loaded into the count pass's leaf tiles (L2) */
+    int64_t guard_band;       /* pairs in the guard band |d - eps| <= 1e-3 eps (FP32 value); of
+                                 these, only those the fp32 error bound cannot place on one side
+                                 of eps go to FP64 */
 } ct_query_stats;
 
 typedef struct ct_tree ct_tree;           /* opaque, device-resident */

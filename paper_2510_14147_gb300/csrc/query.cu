@@ -43,17 +43,54 @@ __device__ __forceinline__ void stat_add(unsigned long long *st, int slot, unsig
     if (v) atomicAdd(st + slot, v);
 }
 
+// Edge decision from the canonical fp32 squared distance sv: 1 edge, 0 none,
+// -1 the pinned FP64 sum decides.  Mode 0: outside the guard band
+// |d - eps| <= 1e-3 eps the fp32 value decides; inside it (counted in band)
+// the fp32 value still decides when its rigorous error bound (c_lo, c_hi)
+// puts the exact sum -- and so the pinned FP64 sum -- on one side of eps^2.
+// Mode 1 (eps = 0): sv > 0 means x != y; sv == 0 can also be an underflowed
+// square, so FP64 decides.  Mode 3: every pair.  Mode 2: always FP64.
+__device__ __forceinline__ int decide32(const QParams &qp, float sv, unsigned long long &band) {
+    if (qp.mode == 0) {
+        if (sv < qp.lo2) return 1;
+        if (sv > qp.hi2) return 0;
+        ++band;
+        return sv < qp.c_lo ? 1 : (sv > qp.c_hi ? 0 : -1);
+    }
+    if (qp.mode == 1) return sv > 0.0f ? 0 : -1;
+    if (qp.mode == 3) return 1;
+    return -1;
+}
+
 // Pinned FP64 sum of squared differences: fp32 inputs widened exactly,
 // t = x - y, s = s + t*t in ascending index order, every op rounded to
 // nearest and never contracted.
-__device__ __noinline__ double sq_l2_exact(const float *__restrict__ x, const float *__restrict__ y,
-                                           int dim) {
+// Rows start on 16-byte boundaries (global or shared memory): the loads go
+// four floats at a time, the sum stays in ascending index order.
+__device__ __noinline__ double sq_l2_exact4(const float4 *x, const float4 *y, int dim) {
     double s = 0.0;
-    for (int k = 0; k < dim; ++k) {
-        double t = __dsub_rn((double)x[k], (double)y[k]);
+    const int n4 = dim >> 2;
+#pragma unroll 4
+    for (int k = 0; k < n4; ++k) {
+        const float4 a = x[k], b = y[k];
+        double t = __dsub_rn((double)a.x, (double)b.x);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+        t = __dsub_rn((double)a.y, (double)b.y);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+        t = __dsub_rn((double)a.z, (double)b.z);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+        t = __dsub_rn((double)a.w, (double)b.w);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    const float *xs = reinterpret_cast<const float *>(x), *ys = reinterpret_cast<const float *>(y);
+    for (int k = 4 * n4; k < dim; ++k) {
+        const double t = __dsub_rn((double)xs[k], (double)ys[k]);
         s = __dadd_rn(s, __dmul_rn(t, t));
     }
     return s;
+}
+__device__ __forceinline__ double sq_l2_exact(const float *x, const float *y, int dim) {
+    return sq_l2_exact4(reinterpret_cast<const float4 *>(x), reinterpret_cast<const float4 *>(y), dim);
 }
 
 struct TreeView {
@@ -638,8 +675,8 @@ constexpr size_t kLeafSmem = sizeof(LeafShared);
 //             mask are skipped.
 // The emit pass skips stage 1: the count pass leaves, per candidate block,
 // the mask of queries that found an edge in it, and the emit pass batches only
-// blocks whose mask is non-empty.  Pairs inside the guard band are queued and
-// decided in FP64 by whole warps.
+// blocks whose mask is non-empty.  Pairs that the fp32 value cannot decide
+// (decide32) are queued and decided in FP64 by whole warps.
 // A work item: a slice of at most kItem candidate blocks of one query group.
 // Heavy groups (large candidate lists) are spread over several CTAs.
 constexpr int kItem = 512;
@@ -666,8 +703,8 @@ struct CapOut {
     uint8_t *lost;
 };
 
-__device__ __forceinline__ void cap_put(const CapOut &co, int o, int32_t c, float d) {
-    const int slot = atomicAdd(&co.fill[o], 1);
+// Writes entry `slot` of row o: in the row's capacity, else in the arena.
+__device__ __forceinline__ void cap_place(const CapOut &co, int o, int slot, int32_t c, float d) {
     const int64_t b = co.off[o];
     if (slot < co.off[o + 1] - b) {
         co.col[b + slot] = c;
@@ -683,6 +720,10 @@ __device__ __forceinline__ void cap_put(const CapOut &co, int o, int32_t c, floa
     } else {
         co.lost[o] = 1;
     }
+}
+
+__device__ __forceinline__ void cap_put(const CapOut &co, int o, int32_t c, float d) {
+    cap_place(co, o, atomicAdd(&co.fill[o], 1), c, d);
 }
 
 template <bool EMIT>
@@ -704,7 +745,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
     const bool fp32_dist_ok = dp <= 128;
     const int qb = tv.group_begin[g], qn = tv.group_count[g];
     const int64_t c0 = items.begin[it], c1 = items.end[it];
-    unsigned long long pairs = 0, s1evals = 0, guard = 0, rows_ld = 0;  // rows_ld: thread 0
+    unsigned long long pairs = 0, s1evals = 0, guard = 0, band = 0, rows_ld = 0;  // rows_ld: thread 0
 
     for (int q0 = 0; q0 < qn; q0 += 32) {
         const int nqr = min(32, qn - q0);
@@ -919,7 +960,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
 
             // ---- emit pass: one thread per (query, point) pair of the blocks in
             // which the query found an edge; same arithmetic as the tiles;
-            // guard-band pairs go through the FP64 queue
+            // undecided pairs go through the FP64 queue
             if (EMIT && nkc > 1) {
                 for (int r0 = 0; r0 < T; r0 += LEAF_T) {
                     const int r = r0 + tid;
@@ -938,11 +979,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
                             const float4 *qrow = reinterpret_cast<const float4 *>(tv.pts + (size_t)qpos * dp);
                             const float sv = pair_sqdist(qrow, reinterpret_cast<const float4 *>(tv.pts + (size_t)ppos * dp),
                                                          dp >> 2);
-                            int edge;
-                            if (qp.mode == 0) edge = sv < qp.lo2 ? 1 : (sv > qp.hi2 ? 0 : -1);
-                            else if (qp.mode == 1) edge = sv == 0.0f;
-                            else if (qp.mode == 3) edge = 1;
-                            else edge = -1;
+                            const int edge = decide32(qp, sv, band);
                             if (edge < 0) {
                                 const int slot = atomicAdd(&S.gn, 1);
                                 S.gpos[slot] = ppos;
@@ -1025,11 +1062,7 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
                             if (qpos == ppos && !qp.include_self) continue;
                             ++pairs;
                             const float sv = pair_sqdist_smem(S.Qs + q * KS4, Pb + lo * KS4, kq);
-                            int edge;
-                            if (qp.mode == 0) edge = sv < qp.lo2 ? 1 : (sv > qp.hi2 ? 0 : -1);
-                            else if (qp.mode == 1) edge = sv == 0.0f;
-                            else if (qp.mode == 3) edge = 1;
-                            else edge = -1;
+                            const int edge = decide32(qp, sv, band);
                             if (edge < 0) {
                                 const int slot = atomicAdd(&S.gn, 1);
                                 S.gpos[slot] = ppos;
@@ -1069,19 +1102,8 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
                             if (qpos == ppos && !qp.include_self) continue;
                             if (!EMIT) ++pairs;
                             const float sv = tot[i][j];
-                            int edge;
-                            if (qp.mode == 0) {
-                                if (sv < qp.lo2) edge = 1;
-                                else if (sv > qp.hi2) edge = 0;
-                                else edge = -1;
-                            } else if (qp.mode == 1) {
-                                edge = sv == 0.0f;
-                            } else if (qp.mode == 3) {
-                                edge = 1;
-                            } else {
-                                edge = -1;
-                            }
-                            if (edge < 0) {  // guard band: queue for the FP64 decision
+                            const int edge = decide32(qp, sv, band);
+                            if (edge < 0) {  // undecided in fp32: queue for the FP64 decision
                                 const int slot = atomicAdd(&S.gn, 1);
                                 S.gpos[slot] = ppos;
                                 S.gq[slot] = (uint8_t)q;
@@ -1150,12 +1172,14 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
         pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
         s1evals += __shfl_xor_sync(0xffffffffu, s1evals, o);
         guard += __shfl_xor_sync(0xffffffffu, guard, o);
+        band += __shfl_xor_sync(0xffffffffu, band, o);
     }
     if ((tid & 31) == 0) {
         if (!EMIT) {
             stat_add(st, ST_PAIRS, pairs);
             stat_add(st, ST_TRAV, s1evals);
             stat_add(st, ST_GUARD, guard);
+            stat_add(st, ST_BAND, band);
             if (tid == 0) stat_add(st, ST_ROWS, rows_ld);
         } else {
             stat_add(st, ST_EMIT, pairs);
@@ -1264,78 +1288,97 @@ __global__ void k_ovf_scatter(int64_t used, const int32_t *__restrict__ orow, co
 //   with a few ulps per addition, generously).
 // A pair is kept iff d^2 <= (eps + 2^-8 (|x~| + |y~|))^2 + 2^-12 (|x~|^2 + |y~|^2),
 // which keeps every edge.  Kept pairs are decided like the FP32 path: the
-// canonical fp32 direct-difference sum outside the guard band, FP64 inside it.
+// canonical fp32 direct-difference sum (decide32), the pinned FP64 sum where
+// that cannot decide.
 // The emit pass is the FP32 path's, driven by the same per-block edge masks.
+//
+// Pipeline (one CTA of 8 warps per work item, one item's candidate blocks in
+// one batch): the fp32 rows of tile t + 1 are in flight -- 16-byte
+// asynchronous copies by all threads into a padded shared-memory stage --
+// while tile t is converted to bf16 from shared memory, multiplied, and
+// checked; the FP32 rechecks read both rows from shared memory.  (One bulk
+// copy per 512-byte row through the TMA engine was measured at about 12 SM
+// cycles per row, twice the time of the whole tile with these copies.)
 constexpr int TC_ROWS = 128;
+constexpr int TC_T = 256;           // threads per CTA
+constexpr int TC_NB = kItem;        // candidate blocks of one item
+constexpr int TC_RS4 = 33;          // fp32 row stride in float4 (odd: conflict-free row-per-thread reads)
 constexpr float TC_REL = 0x1p-8f, TC_ABS2 = 0x1p-12f;
+constexpr uint32_t TC_WAIT = 1u << 22;  // mbarrier polls before a wait gives up
+constexpr int TC_EB = 1024;             // edge buffer entries (one-pass emit)
 
 struct __align__(1024) TcShared {
     unsigned char A[TC_ROWS * 256];  // bf16 candidate rows, core-matrix layout
     unsigned char B[32 * 256];       // bf16 query rows
-    float4 Qf[32 * KS4];             // fp32 query rows (recheck)
+    float4 P[2][TC_ROWS * TC_RS4];   // fp32 candidate rows, two stages
+    float4 Qf[32 * TC_RS4];          // fp32 query rows
     float4 cen[32];                  // group centre
     float qn2[32], qabs[32];
-    float pn2[TC_ROWS], pabs[TC_ROWS];
-    int rpos[TC_ROWS];
-    uint8_t rli[TC_ROWS];
-    int bbeg[NB], bcnt[NB], bpre[NB + 1];
-    uint32_t bem[NB];
+    float pn2[2][TC_ROWS], pa2[2][TC_ROWS];  // per half row: bf16 and fp32 squared norms
+    int rpos[2][TC_ROWS];
+    uint16_t rli[2][TC_ROWS];
+    int npos[TC_ROWS];               // mapping of the tile being prepared
+    uint16_t nli[TC_ROWS];
+    int bbeg[TC_NB], bcnt[TC_NB], bpre[TC_NB + 1];
+    uint32_t bem[TC_NB];
     int qcnt[32], orig[32];
-    int gpos[GQ_CAP];
-    uint8_t gq[GQ_CAP], gb[GQ_CAP];
-    int gn;
+    // one-pass emit: edges of the current stretch, written out per query in
+    // one slot reservation each
+    int ecol[TC_EB];
+    float edist[TC_EB];
+    uint8_t eq[TC_EB];
+    uint16_t erank[TC_EB];
+    int en, qfill[32], qbase[32];
+    int wsum[TC_T / 32];
     uint32_t tslot;
-    uint64_t mbar;
+    uint64_t mma;
 };
 constexpr size_t kTcSmem = sizeof(TcShared) + 1024;
+static_assert(kTcSmem <= 227 * 1024, "k_leaf_tc shared memory above the per-block limit");
+static_assert(TC_NB == 2 * TC_T, "block prefix assumes two candidate blocks per thread");
 
-// Thread-per-row conversion of a whole row (dp4 float4, zero beyond) to
-// centred bf16 in the core-matrix layout; returns both squared norms.  Eight
-// loads are kept in flight.
-__device__ __forceinline__ void tc_convert_row_thread(unsigned char *tile, int r, const float4 *__restrict__ row,
-                                                      const float4 *cen, int dp4, bool valid, float &n2, float &a2) {
+// Converts float4 columns [k0, k1) of one row (fp32, shared memory; columns
+// at or past dp4 and rows that are not valid give zeros) to centred bf16 in
+// the core-matrix layout; returns the partial squared norms of the bf16 and
+// the fp32 centred values.  k0 and k1 are even.
+__device__ __forceinline__ void tc_convert_part(unsigned char *tile, int r, const float4 *row, const float4 *cen,
+                                                int k0, int k1, int dp4, bool valid, float &n2, float &a2) {
     float bn = 0.f, an = 0.f;
-#pragma unroll
-    for (int k0 = 0; k0 < 32; k0 += 8) {
-        float4 v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int k = k0 + u;
-            v[u] = (valid && k < dp4) ? __ldg(row + k) : cen[k];
+    for (int k = k0; k < k1; k += 2) {
+        float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+        if (valid && k < dp4) {
+            const float4 u = row[k], c = cen[k];
+            v0 = make_float4(u.x - c.x, u.y - c.y, u.z - c.z, u.w - c.w);
         }
-#pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-            const int k = k0 + u;
-            const float4 c0 = cen[k], c1 = cen[k + 1];
-            const float x0 = v[u].x - c0.x, x1 = v[u].y - c0.y, x2 = v[u].z - c0.z, x3 = v[u].w - c0.w;
-            const float x4 = v[u + 1].x - c1.x, x5 = v[u + 1].y - c1.y, x6 = v[u + 1].z - c1.z,
-                        x7 = v[u + 1].w - c1.w;
-            const __nv_bfloat162 b01 = __floats2bfloat162_rn(x0, x1), b23 = __floats2bfloat162_rn(x2, x3);
-            const __nv_bfloat162 b45 = __floats2bfloat162_rn(x4, x5), b67 = __floats2bfloat162_rn(x6, x7);
-            uint4 pk;
-            pk.x = *reinterpret_cast<const uint32_t *>(&b01);
-            pk.y = *reinterpret_cast<const uint32_t *>(&b23);
-            pk.z = *reinterpret_cast<const uint32_t *>(&b45);
-            pk.w = *reinterpret_cast<const uint32_t *>(&b67);
-            *reinterpret_cast<uint4 *>(tile + tc::core_offset(r, k >> 1)) = pk;
-            const float2 f01 = __bfloat1622float2(b01), f23 = __bfloat1622float2(b23);
-            const float2 f45 = __bfloat1622float2(b45), f67 = __bfloat1622float2(b67);
-            bn = fmaf(f01.x, f01.x, bn); bn = fmaf(f01.y, f01.y, bn);
-            bn = fmaf(f23.x, f23.x, bn); bn = fmaf(f23.y, f23.y, bn);
-            bn = fmaf(f45.x, f45.x, bn); bn = fmaf(f45.y, f45.y, bn);
-            bn = fmaf(f67.x, f67.x, bn); bn = fmaf(f67.y, f67.y, bn);
-            an = fmaf(x0, x0, an); an = fmaf(x1, x1, an); an = fmaf(x2, x2, an); an = fmaf(x3, x3, an);
-            an = fmaf(x4, x4, an); an = fmaf(x5, x5, an); an = fmaf(x6, x6, an); an = fmaf(x7, x7, an);
+        if (valid && k + 1 < dp4) {
+            const float4 u = row[k + 1], c = cen[k + 1];
+            v1 = make_float4(u.x - c.x, u.y - c.y, u.z - c.z, u.w - c.w);
         }
+        const __nv_bfloat162 b01 = __floats2bfloat162_rn(v0.x, v0.y), b23 = __floats2bfloat162_rn(v0.z, v0.w);
+        const __nv_bfloat162 b45 = __floats2bfloat162_rn(v1.x, v1.y), b67 = __floats2bfloat162_rn(v1.z, v1.w);
+        uint4 pk;
+        pk.x = *reinterpret_cast<const uint32_t *>(&b01);
+        pk.y = *reinterpret_cast<const uint32_t *>(&b23);
+        pk.z = *reinterpret_cast<const uint32_t *>(&b45);
+        pk.w = *reinterpret_cast<const uint32_t *>(&b67);
+        *reinterpret_cast<uint4 *>(tile + tc::core_offset(r, k >> 1)) = pk;
+        const float2 f01 = __bfloat1622float2(b01), f23 = __bfloat1622float2(b23);
+        const float2 f45 = __bfloat1622float2(b45), f67 = __bfloat1622float2(b67);
+        bn = fmaf(f01.x, f01.x, bn); bn = fmaf(f01.y, f01.y, bn);
+        bn = fmaf(f23.x, f23.x, bn); bn = fmaf(f23.y, f23.y, bn);
+        bn = fmaf(f45.x, f45.x, bn); bn = fmaf(f45.y, f45.y, bn);
+        bn = fmaf(f67.x, f67.x, bn); bn = fmaf(f67.y, f67.y, bn);
+        an = fmaf(v0.x, v0.x, an); an = fmaf(v0.y, v0.y, an); an = fmaf(v0.z, v0.z, an); an = fmaf(v0.w, v0.w, an);
+        an = fmaf(v1.x, v1.x, an); an = fmaf(v1.y, v1.y, an); an = fmaf(v1.z, v1.z, an); an = fmaf(v1.w, v1.w, an);
     }
     n2 = bn;
     a2 = an;
 }
 
-__global__ void __launch_bounds__(LEAF_T, 3) k_leaf_tc(TreeView tv, QParams qp, Items items,
-                                                    const uint32_t *__restrict__ cand, uint32_t *__restrict__ emask,
-                                                    int32_t *__restrict__ deg, unsigned long long *__restrict__ st,
-                                                    int32_t *__restrict__ err, CapOut co) {
+__global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(TreeView tv, QParams qp, Items items,
+                                                   const uint32_t *__restrict__ cand, uint32_t *__restrict__ emask,
+                                                   int32_t *__restrict__ deg, unsigned long long *__restrict__ st,
+                                                   int32_t *__restrict__ err, CapOut co) {
     extern __shared__ unsigned char tc_raw[];
     TcShared &S = *reinterpret_cast<TcShared *>(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
     const int it = blockIdx.x;
@@ -1344,243 +1387,282 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_tc(TreeView tv, QParams qp, 
     const int g = items.group[it];
     const int dp = tv.dp, dim = tv.dim, dp4 = dp >> 2;
     const int ksteps = (dp + 15) >> 4;
+    const int K4 = 4 * ksteps;                       // float4 columns of the MMA's K
+    const int kh = ((K4 >> 1) + 1) & ~1;             // split of a row between two threads (even)
     const int qb = tv.group_begin[g], qn = tv.group_count[g];
-    const int64_t c0 = items.begin[it], c1 = items.end[it];
-    unsigned long long pairs = 0, kept = 0, guard = 0, rows_ld = 0;  // rows_ld: thread 0
+    const int64_t c0 = items.begin[it];
+    const int nb = (int)(items.end[it] - c0);        // <= TC_NB
+    unsigned long long pairs = 0, kept = 0, guard = 0, band = 0, rows_ld = 0;  // rows_ld: thread 0
     bool failed = false;
+    uint32_t mph = 0u;
+    bool mma_out = false;
 
     if (warp == 0) tc::tmem_alloc(&S.tslot, 32);
-    if (tid == 0) tc::mbar_init(&S.mbar, 1);
+    if (tid == 0) {
+        tc::mbar_init(&S.mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
     if (tid < 32) S.cen[tid] = tid < dp4 ? __ldg(reinterpret_cast<const float4 *>(tv.pts + (size_t)qb * dp) + tid)
                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+    // candidate blocks of the item and their row prefix
+    {
+        int loc[2], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int i = 2 * tid + k;
+            int beg = 0, cnt = 0;
+            if (i < nb) {
+                const int v = (int)cand[c0 + i];
+                beg = tv.node_begin[v];
+                cnt = tv.node_count[v];
+            }
+            if (i < TC_NB) {
+                S.bbeg[i] = beg;
+                S.bcnt[i] = cnt;
+                S.bem[i] = 0u;
+            }
+            loc[k] = cnt;
+            sum += cnt;
+        }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) S.wsum[warp] = incl;
+        __syncthreads();
+        int base = 0;
+#pragma unroll
+        for (int w = 0; w < TC_T / 32; ++w)
+            if (w < warp) base += S.wsum[w];
+        int run = base + incl - sum;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            S.bpre[2 * tid + k] = run;
+            run += loc[k];
+        }
+        if (tid == TC_T - 1) S.bpre[TC_NB] = run;
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = S.tslot;
     const uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, 32);
-    uint32_t phase = 0;
+    const int T = S.bpre[TC_NB];
+    const int ntiles = (T + TC_ROWS - 1) / TC_ROWS;
+
+    // rows of tile tn -> (position, block) in npos / nli, by threads t0 and up
+    auto prep_map = [&](int tn, int t0) {
+        const int R0 = tn * TC_ROWS;
+        for (int r = tid - t0; r >= 0 && r < TC_ROWS; r += TC_T - t0) {
+            const int R = R0 + r;
+            if (R < T) {
+                int lo = 0, hi = TC_NB;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (S.bpre[mid] <= R) lo = mid; else hi = mid;
+                }
+                S.npos[r] = S.bbeg[lo] + (R - S.bpre[lo]);
+                S.nli[r] = (uint16_t)lo;
+            }
+        }
+    };
+    // all threads: take the prepared mapping for stage sg, start the row
+    // copies and commit them as one group (an empty group when tn is past the
+    // last tile, so that every iteration commits exactly one)
+    auto issue = [&](int tn, int sg) {
+        if (tn < ntiles) {
+            const int rows = min(TC_ROWS, T - tn * TC_ROWS);
+            for (int r = tid; r < rows; r += TC_T) {
+                S.rpos[sg][r] = S.npos[r];
+                S.rli[sg][r] = S.nli[r];
+            }
+            for (int r = warp; r < rows; r += TC_T / 32)  // warp per row, lane per 16 bytes
+                if (lane < dp4) cp_async16(&S.P[sg][r * TC_RS4 + lane], tv.pts + (size_t)S.npos[r] * dp + 4 * lane, true);
+        }
+        cp_async_commit();
+    };
 
     for (int q0 = 0; q0 < qn && !failed; q0 += 32) {
         const int nqr = min(32, qn - q0);
         const int qfirst = qb + q0;
         __syncthreads();
-        // queries: fp32 copy (recheck) by all threads, bf16 conversion by thread q
-        for (int i = tid; i < 32 * 32; i += LEAF_T) {
-            const int q = i >> 5, k = i & 31;
+        // queries: fp32 rows, then bf16 conversion (two threads per row)
+        for (int i = tid; i < 32 * TC_RS4; i += TC_T) {
+            const int q = i / TC_RS4, k = i - q * TC_RS4;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (q < nqr && k < dp4) v = __ldg(reinterpret_cast<const float4 *>(tv.pts + (size_t)(qfirst + q) * dp) + k);
-            S.Qf[q * KS4 + k] = v;
+            S.Qf[i] = v;
         }
         if (tid < 32) {
-            const int q = tid;
-            float n2, a2;
-            tc_convert_row_thread(S.B, q, reinterpret_cast<const float4 *>(tv.pts + (size_t)(qfirst + min(q, nqr - 1)) * dp),
-                                  S.cen, dp4, q < nqr, n2, a2);
-            S.qn2[q] = n2;
-            S.qabs[q] = sqrtf(a2);
-            S.qcnt[q] = 0;
-            S.orig[q] = q < nqr ? tv.perm[qfirst + q] : 0;
+            S.qcnt[tid] = 0;
+            S.orig[tid] = tid < nqr ? tv.perm[qfirst + tid] : 0;
         }
-        if (tid == 0) S.gn = 0;
+        for (int i = tid; i < nb; i += TC_T) S.bem[i] = 0u;
+        if (tid < 32) S.qfill[tid] = 0;
+        if (tid == 0) S.en = 0;
+        __syncthreads();
+        if (tid < 64) {
+            const int q = tid & 31, half = tid >> 5;
+            float n2, a2;
+            tc_convert_part(S.B, q, S.Qf + q * TC_RS4, S.cen, half ? kh : 0, half ? K4 : kh, dp4, q < nqr, n2, a2);
+            S.pn2[half][q] = n2;
+            S.pa2[half][q] = a2;
+        }
+        __syncthreads();
+        if (tid < 32) {
+            S.qn2[tid] = S.pn2[0][tid] + S.pn2[1][tid];
+            S.qabs[tid] = sqrtf(S.pa2[0][tid] + S.pa2[1][tid]);
+        }
 
-        auto drain = [&](bool all) {
+        // one-pass emit: reserves each query's slots once and writes the
+        // buffered edges (all threads; between barriers)
+        auto flush = [&]() {
+            if (tid < 32 && S.qfill[tid]) S.qbase[tid] = atomicAdd(&co.fill[S.orig[tid]], S.qfill[tid]);
             __syncthreads();
-            const int n = S.gn;
-            const int m = all ? n : (n & ~31);
-            for (int i = tid; i < m; i += LEAF_T) {
-                const int q = S.gq[i], ppos = S.gpos[i], li = S.gb[i];
-                ++guard;
-                const double s64 = sq_l2_exact(tv.pts + (size_t)(qfirst + q) * dp, tv.pts + (size_t)ppos * dp, dim);
-                if (s64 <= qp.eps2_64) {
-                    atomicAdd(&S.qcnt[q], 1);
-                    atomicOr(&S.bem[li], 1u << q);
-                    if (co.off) cap_put(co, S.orig[q], tv.perm[ppos], (float)sqrt(s64));
-                }
+            const int n = min(S.en, TC_EB);
+            for (int i = tid; i < n; i += TC_T) {
+                const int q = S.eq[i];
+                cap_place(co, S.orig[q], S.qbase[q] + S.erank[i], tv.perm[S.ecol[i]], S.edist[i]);
             }
             __syncthreads();
-            const int rest = n - m;
-            int rp = 0, rq = 0, rb = 0;
-            if (tid < rest) {
-                rp = S.gpos[m + tid];
-                rq = S.gq[m + tid];
-                rb = S.gb[m + tid];
-            }
-            __syncthreads();
-            if (tid < rest) {
-                S.gpos[tid] = rp;
-                S.gq[tid] = (uint8_t)rq;
-                S.gb[tid] = (uint8_t)rb;
-            }
-            if (tid == 0) S.gn = rest;
+            if (tid < 32) S.qfill[tid] = 0;
+            if (tid == 0) S.en = 0;
             __syncthreads();
         };
+        // an edge of query q: counted, marked in its block, buffered for the
+        // one-pass emit (written at once when the buffer is full)
+        auto edge_found = [&](int q, int li, int ppos, float d) {
+            atomicAdd(&S.qcnt[q], 1);
+            atomicOr(&S.bem[li], 1u << q);
+            if (co.off) {
+                const int slot = atomicAdd(&S.en, 1);
+                if (slot < TC_EB) {
+                    S.eq[slot] = (uint8_t)q;
+                    S.ecol[slot] = ppos;  // tree position; the original id is looked up at the flush
+                    S.edist[slot] = d;
+                    S.erank[slot] = (uint16_t)atomicAdd(&S.qfill[q], 1);
+                } else {
+                    cap_put(co, S.orig[q], tv.perm[ppos], d);
+                }
+            }
+        };
 
-        for (int64_t b0 = c0; b0 < c1 && !failed; b0 += NB) {
-            const int bn = (int)((c1 - b0) < NB ? (c1 - b0) : NB);
+        // prologue: tiles 0 and 1 in flight
+        for (int tn = 0; tn < 2; ++tn) {
+            if (tn < ntiles) prep_map(tn, 0);
             __syncthreads();
-            for (int i = tid; i < NB; i += LEAF_T) {
-                int beg = 0, cnt = 0;
-                if (i < bn) {
-                    const int v = (int)cand[b0 + i];
-                    beg = tv.node_begin[v];
-                    cnt = tv.node_count[v];
-                }
-                S.bbeg[i] = beg;
-                S.bcnt[i] = cnt;
-                S.bem[i] = 0u;
+            issue(tn, tn);
+            __syncthreads();
+        }
+        for (int t = 0; t < ntiles; ++t) {
+            const int sg = t & 1;
+            const int rows = min(TC_ROWS, T - t * TC_ROWS);
+            if (tid == 0) rows_ld += rows;
+            cp_async_wait<1>();  // this thread's copies of tile t have landed
+            __syncthreads();
+            // bf16 tile from the staged rows (two threads per row)
+            {
+                const int r = tid & (TC_ROWS - 1), half = tid >> 7;
+                float n2, a2;
+                tc_convert_part(S.A, r, S.P[sg] + r * TC_RS4, S.cen, half ? kh : 0, half ? K4 : kh, dp4, r < rows,
+                                n2, a2);
+                S.pn2[half][r] = n2;
+                S.pa2[half][r] = a2;
             }
+            tc::fence_smem_to_async();
+            tc::fence_before_sync();
             __syncthreads();
-            if (warp == 0) {
-                int loc[4], sum = 0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    loc[k] = S.bcnt[4 * lane + k];
-                    sum += loc[k];
+            tc::fence_after_sync();
+            if (tid == 0) {
+                for (int ks = 0; ks < ksteps; ++ks) {
+                    const uint64_t ad = tc::smem_desc(tc::smem_u32(S.A) + ks * 256, tc::kLBO, tc::kSBO);
+                    const uint64_t bd = tc::smem_desc(tc::smem_u32(S.B) + ks * 256, tc::kLBO, tc::kSBO);
+                    tc::mma_bf16(tmem, ad, bd, idesc, ks > 0);
                 }
-                int incl = sum;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                int run = incl - sum;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    S.bpre[4 * lane + k] = run;
-                    run += loc[k];
-                }
-                if (lane == 31) S.bpre[NB] = incl;
+                tc::mma_commit(&S.mma);
             }
-            __syncthreads();
-            const int T = S.bpre[NB];
-            for (int R0 = 0; R0 < T && !failed; R0 += TC_ROWS) {
-                const int rows = min(TC_ROWS, T - R0);
-                if (tid == 0) rows_ld += rows;
-                // row -> (position, block) for this tile
-                {
-                    const int r = tid;
-                    if (r < rows) {
-                        const int R = R0 + r;
-                        int lo = 0, hi = NB;
-                        while (hi - lo > 1) {
-                            const int mid = (lo + hi) >> 1;
-                            if (S.bpre[mid] <= R) lo = mid; else hi = mid;
-                        }
-                        S.rpos[r] = S.bbeg[lo] + (R - S.bpre[lo]);
-                        S.rli[r] = (uint8_t)lo;
-                    }
-                }
-                __syncthreads();
-                // A tile: thread r converts row r
-                {
-                    const int r = tid;
-                    const bool valid = r < rows;
-                    float n2, a2;
-                    tc_convert_row_thread(S.A, r,
-                                          reinterpret_cast<const float4 *>(tv.pts + (size_t)(valid ? S.rpos[r] : qb) * dp),
-                                          S.cen, dp4, valid, n2, a2);
-                    S.pn2[r] = n2;
-                    S.pabs[r] = sqrtf(a2);
-                }
-                tc::fence_smem_to_async();
-                tc::fence_before_sync();
-                __syncthreads();
-                tc::fence_after_sync();
-                if (tid == 0) {
-                    for (int ks = 0; ks < ksteps; ++ks) {
-                        const uint64_t ad = tc::smem_desc(tc::smem_u32(S.A) + ks * 256, tc::kLBO, tc::kSBO);
-                        const uint64_t bd = tc::smem_desc(tc::smem_u32(S.B) + ks * 256, tc::kLBO, tc::kSBO);
-                        tc::mma_bf16(tmem, ad, bd, idesc, ks > 0);
-                    }
-                    tc::mma_commit(&S.mbar);
-                }
-                const bool ok = tc::mbar_wait(&S.mbar, phase, 1u << 22);
-                phase ^= 1u;
-                if (!__syncthreads_and(ok)) {
-                    if (tid == 0) atomicOr(err, 32);
-                    failed = true;
-                    break;
-                }
-                tc::fence_after_sync();
-                float dot[32];
-                tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), dot);
-                const int r = 32 * warp + lane;
+            mma_out = true;
+            if (t + 2 < ntiles) prep_map(t + 2, 32);  // warp 0 issues the MMAs meanwhile
+            const bool mok = tc::mbar_wait(&S.mma, mph, TC_WAIT);
+            if (!__syncthreads_and(mok)) {
+                if (tid == 0) atomicOr(err, 32);
+                failed = true;
+                break;
+            }
+            mph ^= 1u;
+            mma_out = false;
+            tc::fence_after_sync();
+            // epilogue: warp w reads rows 32 (w % 4) .. + 31, queries 16 (w / 4) .. + 15
+            {
+                const int quarter = warp & 3, qh = warp >> 2;
+                float dot[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(16 * qh), dot);
+                const int r = 32 * quarter + lane;
                 if (r < rows) {
-                    const int ppos = S.rpos[r], li = S.rli[r];
-                    const float pa = S.pabs[r], pn = S.pn2[r];
+                    const int ppos = S.rpos[sg][r], li = S.rli[sg][r];
+                    const float pn = S.pn2[0][r] + S.pn2[1][r];
+                    const float pa = sqrtf(S.pa2[0][r] + S.pa2[1][r]);
                     uint32_t keepm = 0u, validm = 0u;
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
+                    for (int j = 0; j < 16; ++j) {
+                        const int q = 16 * qh + j;
                         if (q >= nqr) continue;
                         if (qfirst + q == ppos && !qp.include_self) continue;
-                        validm |= 1u << q;
+                        validm |= 1u << j;
                         const float qa = S.qabs[q];
-                        const float d2 = fmaf(-2.0f, dot[q], S.qn2[q] + pn);
+                        const float d2 = fmaf(-2.0f, dot[j], S.qn2[q] + pn);
                         const float e = fmaf(TC_REL, qa + pa, qp.eps_up);
                         const float bound = fmaf(e, e, TC_ABS2 * fmaf(qa, qa, pa * pa)) + 0x1p-60f;
-                        if (!(d2 > bound)) keepm |= 1u << q;  // NaN keeps the pair
+                        if (!(d2 > bound)) keepm |= 1u << j;  // NaN keeps the pair
                     }
                     pairs += __popc(validm);
                     kept += __popc(keepm);
+                    const float4 *prow = S.P[sg] + r * TC_RS4;
                     while (keepm) {
-                        const int q = __ffs(keepm) - 1;
+                        const int q = 16 * qh + __ffs(keepm) - 1;
                         keepm &= keepm - 1u;
-                        const float sv = pair_sqdist(S.Qf + q * KS4,
-                                                     reinterpret_cast<const float4 *>(tv.pts + (size_t)ppos * dp), dp4);
-                        int edge;
-                        if (qp.mode == 0) edge = sv < qp.lo2 ? 1 : (sv > qp.hi2 ? 0 : -1);
-                        else if (qp.mode == 1) edge = sv == 0.0f;
-                        else if (qp.mode == 3) edge = 1;
-                        else edge = -1;
-                        if (edge < 0) {
-                            const int slot = atomicAdd(&S.gn, 1);
-                            if (slot < GQ_CAP) {
-                                S.gpos[slot] = ppos;
-                                S.gq[slot] = (uint8_t)q;
-                                S.gb[slot] = (uint8_t)li;
-                            } else {  // queue full (many pairs at eps): decide here
-                                atomicSub(&S.gn, 1);
-                                ++guard;
-                                const double s64 = sq_l2_exact(tv.pts + (size_t)(qfirst + q) * dp,
-                                                               tv.pts + (size_t)ppos * dp, dim);
-                                if (s64 <= qp.eps2_64) {
-                                    atomicAdd(&S.qcnt[q], 1);
-                                    atomicOr(&S.bem[li], 1u << q);
-                                    if (co.off) cap_put(co, S.orig[q], tv.perm[ppos], (float)sqrt(s64));
-                                }
-                            }
+                        const float sv = pair_sqdist_smem(S.Qf + q * TC_RS4, prow, dp4);
+                        const int edge = decide32(qp, sv, band);
+                        if (edge < 0) {  // undecided in fp32: the pinned FP64 sum, rows from shared memory
+                            ++guard;
+                            const double s64 = sq_l2_exact4(S.Qf + q * TC_RS4, prow, dim);
+                            if (s64 <= qp.eps2_64) edge_found(q, li, ppos, (float)sqrt(s64));
                         } else if (edge) {
-                            atomicAdd(&S.qcnt[q], 1);
-                            atomicOr(&S.bem[li], 1u << q);
-                            if (co.off) cap_put(co, S.orig[q], tv.perm[ppos], sqrtf(sv));
+                            edge_found(q, li, ppos, sqrtf(sv));
                         }
                     }
                 }
-                tc::fence_before_sync();
-                __syncthreads();
-                tc::fence_after_sync();
-                if (S.gn >= 64) drain(false);
             }
-            if (failed) break;
-            drain(true);
-            if (emask)
-                for (int i = tid; i < bn; i += LEAF_T) emask[b0 + i] = qn <= 32 ? S.bem[i] : ~0u;
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            issue(t + 2, sg);
+            if (co.off && S.en >= TC_EB / 2) flush();
         }
+        if (failed) break;
+        if (co.off) flush();
         __syncthreads();
-        if (!failed && tid < nqr && S.qcnt[tid]) atomicAdd(&deg[S.orig[tid]], S.qcnt[tid]);
+        if (tid < nqr && S.qcnt[tid]) atomicAdd(&deg[S.orig[tid]], S.qcnt[tid]);
     }
+    if (!failed && emask)
+        for (int i = tid; i < nb; i += TC_T) emask[c0 + i] = qn <= 32 ? S.bem[i] : ~0u;
     for (int o = 16; o > 0; o >>= 1) {
         pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
         kept += __shfl_xor_sync(0xffffffffu, kept, o);
         guard += __shfl_xor_sync(0xffffffffu, guard, o);
+        band += __shfl_xor_sync(0xffffffffu, band, o);
     }
     if (lane == 0) {
         stat_add(st, ST_PAIRS, pairs);
         stat_add(st, ST_RECHECK, kept);
         stat_add(st, ST_GUARD, guard);
+        stat_add(st, ST_BAND, band);
         if (tid == 0) stat_add(st, ST_ROWS, rows_ld);
     }
-    if (failed) tc::mbar_wait(&S.mbar, phase ^ 1u, 1u << 22);  // let an outstanding MMA finish
+    cp_async_wait<0>();  // no copy into this CTA's shared memory outlives it
+    if (failed && mma_out) tc::mbar_wait(&S.mma, mph, TC_WAIT);  // let an outstanding MMA finish
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -1952,6 +2034,16 @@ QParams make_qparams(const ct_tree *t, double eps, int include_self) {
         if ((double)h < hi2) h = nextafterf(h, INFINITY);
         q.lo2 = l;
         q.hi2 = h;
+        // error bound of the canonical fp32 sum: one rounding per FMA of a
+        // 16-float chunk (8), the chunk sum, one per chunk of the running
+        // total, the rounded differences; doubled
+        const double m = 2.0 * ((double)(t->dp / 16) + 16.0) * 0x1p-24;
+        const double cl = e2 * (1.0 - m), ch = e2 * (1.0 + m);
+        float a = (float)cl, b = (float)ch;
+        if ((double)a > cl) a = nextafterf(a, 0.0f);
+        if ((double)b < ch) b = nextafterf(b, INFINITY);
+        q.c_lo = a;
+        q.c_hi = b;
     }
     return q;
 }
@@ -2192,7 +2284,7 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
             tc_ready = true;
         }
         if (G && nseg) {
-            k_leaf_tc<<<(unsigned)max_items, LEAF_T, kTcSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, st.p, err, co);
+            k_leaf_tc<<<(unsigned)max_items, TC_T, kTcSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, st.p, err, co);
             CT_COUNT_LAUNCH();
             CT_LAUNCH_CHECK();
         }
@@ -2212,6 +2304,7 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
         out.stats.recheck_fp32 = (int64_t)hs[ST_RECHECK];
         out.stats.emit_pairs = (int64_t)hs[ST_EMIT];
         out.stats.leaf_rows = (int64_t)hs[ST_ROWS];
+        out.stats.guard_band = (int64_t)hs[ST_BAND];
         out.stats.candidates = n_cand;
     };
 

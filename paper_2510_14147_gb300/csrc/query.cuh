@@ -8,15 +8,17 @@ struct ct_predictor;
 namespace ct {
 
 // Decision parameters of the L2 predicate d(q, p) <= eps.
-//  mode 0: fp32 decides outside the guard band |d - eps| <= 1e-3 eps, FP64
-//          (the pinned sequential sum) inside it;
-//  mode 1: eps == 0: an edge iff the fp32 sum is exactly 0 (iff x == y);
+//  mode 0: fp32 decides outside the guard band |d - eps| <= 1e-3 eps; inside
+//          it fp32 still decides where its error bound certifies the side of
+//          eps^2, else FP64 (the pinned sequential sum);
+//  mode 1: eps == 0: no edge if the fp32 sum is positive (x != y), else FP64;
 //  mode 2: every pair in FP64 (eps^2 outside [2^-100, 2^100]);
 //  mode 3: every pair is an edge (eps^2 above any representable sum).
 struct QParams {
     double eps64 = 0, eps2_64 = 0;
     float eps_up = 0;      // eps rounded up to fp32 (traversal bound)
     float lo2 = 0, hi2 = 0;  // guard band in squared distance, rounded outwards
+    float c_lo = 0, c_hi = 0;  // inside it: fp32 sums outside [c_lo, c_hi] decide alone
     int mode = 0;
     int include_self = 0;
     int lev_k = 0;         // edit distance: floor(eps)
@@ -60,6 +62,6 @@ void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int
                cudaStream_t s);
 
 // Stats slots accumulated on the device.
-enum { ST_TRAV = 0, ST_PAIRS, ST_GUARD, ST_RECHECK, ST_CAND, ST_OVERFLOW, ST_ERR, ST_EMIT, ST_ROWS, ST_N };
+enum { ST_TRAV = 0, ST_PAIRS, ST_GUARD, ST_RECHECK, ST_CAND, ST_OVERFLOW, ST_ERR, ST_EMIT, ST_ROWS, ST_BAND, ST_N };
 
 }  // namespace ct

@@ -60,7 +60,7 @@ class ct_query_stats(C.Structure):
     _fields_ = [(f, C.c_int64) for f in ("traversal_evals", "leaf_pairs", "guard_fp64",
                                            "recheck_fp32", "candidates", "overflow_rows",
                                            "kernel_launches", "emit_pairs", "reemit_rows",
-                                           "leaf_rows")]
+                                           "leaf_rows", "guard_band")]
 
 
 class ct_fit_opts(C.Structure):

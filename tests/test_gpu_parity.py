@@ -88,6 +88,22 @@ def test_duplicates_above_leaf_size_and_eps_zero():
     _check_tree(sp, out)
 
 
+def test_eps_zero_with_tiny_coordinates():
+    """eps = 0: only exact duplicates are neighbours, also where the fp32
+    square of a nonzero difference underflows to zero (|x - y| < 2^-75)."""
+    rng = np.random.default_rng(8)
+    base = (rng.random((300, 3)) * 1e-30).astype(np.float32)
+    base[:10, 0] = np.float32(3e-39)                # subnormal coordinates
+    base[10:20] = 0.0
+    base[20:30, 1] = np.float32(1e-38)
+    x = np.concatenate([base, base[:60]])          # duplicates of the first 60
+    x = x[rng.permutation(x.shape[0])]
+    sp = oracle.Space(points=x)
+    for precision in (0, 1):
+        out = gpu_graph(points=x, eps=0.0, leaf_size=8, precision=precision)
+        assert_csr_matches(out, oracle.brute_force(sp, 0.0))
+
+
 def test_complete_graph_and_include_self():
     x = I.uniform_cube(700, 4, seed=1)
     sp = oracle.Space(points=x)
