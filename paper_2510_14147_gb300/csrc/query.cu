@@ -476,6 +476,9 @@ __device__ __forceinline__ unsigned long long f2_sqacc(unsigned long long d, uns
     asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(d), "l"(acc));
     return r;
 }
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    return ((unsigned long long)__float_as_uint(hi) << 32) | (unsigned long long)__float_as_uint(lo);
+}
 __device__ __forceinline__ float f2_sum(unsigned long long v) {
     return __uint_as_float((uint32_t)v) + __uint_as_float((uint32_t)(v >> 32));
 }
@@ -1329,6 +1332,8 @@ struct __align__(1024) TcShared {
     uint8_t eq[TC_EB];
     uint16_t erank[TC_EB];
     int en, qfill[32], qbase[32];
+    uint16_t kl[TC_ROWS * 32];       // kept pairs of the tile: (query << 7) | row
+    int kn;
     int wsum[TC_T / 32];
     uint32_t tslot;
     uint64_t mma;
@@ -1340,20 +1345,27 @@ static_assert(TC_NB == 2 * TC_T, "block prefix assumes two candidate blocks per 
 // Converts float4 columns [k0, k1) of one row (fp32, shared memory; columns
 // at or past dp4 and rows that are not valid give zeros) to centred bf16 in
 // the core-matrix layout; returns the partial squared norms of the bf16 and
-// the fp32 centred values.  k0 and k1 are even.
+// the fp32 centred values.  k0 and k1 are even, k1 - k0 <= 16.  All loads
+// are issued before the first store.
 __device__ __forceinline__ void tc_convert_part(unsigned char *tile, int r, const float4 *row, const float4 *cen,
                                                 int k0, int k1, int dp4, bool valid, float &n2, float &a2) {
-    float bn = 0.f, an = 0.f;
-    for (int k = k0; k < k1; k += 2) {
-        float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-        if (valid && k < dp4) {
-            const float4 u = row[k], c = cen[k];
-            v0 = make_float4(u.x - c.x, u.y - c.y, u.z - c.z, u.w - c.w);
+    float4 v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int k = k0 + u;
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid && k < k1 && k < dp4) {
+            const float4 x = row[k], c = cen[k];
+            v[u] = make_float4(x.x - c.x, x.y - c.y, x.z - c.z, x.w - c.w);
         }
-        if (valid && k + 1 < dp4) {
-            const float4 u = row[k + 1], c = cen[k + 1];
-            v1 = make_float4(u.x - c.x, u.y - c.y, u.z - c.z, u.w - c.w);
-        }
+    }
+    // norms in packed pairs (f32x2): two partial sums each, added at the end
+    unsigned long long bn = 0ull, an = 0ull;
+#pragma unroll
+    for (int u = 0; u < 16; u += 2) {
+        const int k = k0 + u;
+        if (k >= k1) break;
+        const float4 v0 = v[u], v1 = v[u + 1];
         const __nv_bfloat162 b01 = __floats2bfloat162_rn(v0.x, v0.y), b23 = __floats2bfloat162_rn(v0.z, v0.w);
         const __nv_bfloat162 b45 = __floats2bfloat162_rn(v1.x, v1.y), b67 = __floats2bfloat162_rn(v1.z, v1.w);
         uint4 pk;
@@ -1364,15 +1376,17 @@ __device__ __forceinline__ void tc_convert_part(unsigned char *tile, int r, cons
         *reinterpret_cast<uint4 *>(tile + tc::core_offset(r, k >> 1)) = pk;
         const float2 f01 = __bfloat1622float2(b01), f23 = __bfloat1622float2(b23);
         const float2 f45 = __bfloat1622float2(b45), f67 = __bfloat1622float2(b67);
-        bn = fmaf(f01.x, f01.x, bn); bn = fmaf(f01.y, f01.y, bn);
-        bn = fmaf(f23.x, f23.x, bn); bn = fmaf(f23.y, f23.y, bn);
-        bn = fmaf(f45.x, f45.x, bn); bn = fmaf(f45.y, f45.y, bn);
-        bn = fmaf(f67.x, f67.x, bn); bn = fmaf(f67.y, f67.y, bn);
-        an = fmaf(v0.x, v0.x, an); an = fmaf(v0.y, v0.y, an); an = fmaf(v0.z, v0.z, an); an = fmaf(v0.w, v0.w, an);
-        an = fmaf(v1.x, v1.x, an); an = fmaf(v1.y, v1.y, an); an = fmaf(v1.z, v1.z, an); an = fmaf(v1.w, v1.w, an);
+        bn = f2_sqacc(f2_pack(f01.x, f01.y), bn);
+        bn = f2_sqacc(f2_pack(f23.x, f23.y), bn);
+        bn = f2_sqacc(f2_pack(f45.x, f45.y), bn);
+        bn = f2_sqacc(f2_pack(f67.x, f67.y), bn);
+        an = f2_sqacc(f2_pack(v0.x, v0.y), an);
+        an = f2_sqacc(f2_pack(v0.z, v0.w), an);
+        an = f2_sqacc(f2_pack(v1.x, v1.y), an);
+        an = f2_sqacc(f2_pack(v1.z, v1.w), an);
     }
-    n2 = bn;
-    a2 = an;
+    n2 = f2_sum(bn);
+    a2 = f2_sum(an);
 }
 
 __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(TreeView tv, QParams qp, Items items,
@@ -1501,7 +1515,10 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(TreeView tv, QParams qp, It
         }
         for (int i = tid; i < nb; i += TC_T) S.bem[i] = 0u;
         if (tid < 32) S.qfill[tid] = 0;
-        if (tid == 0) S.en = 0;
+        if (tid == 0) {
+            S.en = 0;
+            S.kn = 0;
+        }
         __syncthreads();
         if (tid < 64) {
             const int q = tid & 31, half = tid >> 5;
@@ -1531,24 +1548,6 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(TreeView tv, QParams qp, It
             if (tid == 0) S.en = 0;
             __syncthreads();
         };
-        // an edge of query q: counted, marked in its block, buffered for the
-        // one-pass emit (written at once when the buffer is full)
-        auto edge_found = [&](int q, int li, int ppos, float d) {
-            atomicAdd(&S.qcnt[q], 1);
-            atomicOr(&S.bem[li], 1u << q);
-            if (co.off) {
-                const int slot = atomicAdd(&S.en, 1);
-                if (slot < TC_EB) {
-                    S.eq[slot] = (uint8_t)q;
-                    S.ecol[slot] = ppos;  // tree position; the original id is looked up at the flush
-                    S.edist[slot] = d;
-                    S.erank[slot] = (uint16_t)atomicAdd(&S.qfill[q], 1);
-                } else {
-                    cap_put(co, S.orig[q], tv.perm[ppos], d);
-                }
-            }
-        };
-
         // prologue: tiles 0 and 1 in flight
         for (int tn = 0; tn < 2; ++tn) {
             if (tn < ntiles) prep_map(tn, 0);
@@ -1594,17 +1593,19 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(TreeView tv, QParams qp, It
             mph ^= 1u;
             mma_out = false;
             tc::fence_after_sync();
-            // epilogue: warp w reads rows 32 (w % 4) .. + 31, queries 16 (w / 4) .. + 15
+            // epilogue, filter: warp w reads rows 32 (w % 4) .. + 31, queries
+            // 16 (w / 4) .. + 15; kept pairs go to the tile's list
             {
                 const int quarter = warp & 3, qh = warp >> 2;
                 float dot[16];
                 tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(16 * qh), dot);
                 const int r = 32 * quarter + lane;
+                uint32_t keepm = 0u;
                 if (r < rows) {
-                    const int ppos = S.rpos[sg][r], li = S.rli[sg][r];
+                    const int ppos = S.rpos[sg][r];
                     const float pn = S.pn2[0][r] + S.pn2[1][r];
                     const float pa = sqrtf(S.pa2[0][r] + S.pa2[1][r]);
-                    uint32_t keepm = 0u, validm = 0u;
+                    uint32_t validm = 0u;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int q = 16 * qh + j;
@@ -1618,19 +1619,61 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(TreeView tv, QParams qp, It
                         if (!(d2 > bound)) keepm |= 1u << j;  // NaN keeps the pair
                     }
                     pairs += __popc(validm);
-                    kept += __popc(keepm);
+                }
+                const int c = __popc(keepm);
+                int incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                int base = 0;
+                if (lane == 31 && incl) base = atomicAdd(&S.kn, incl);
+                base = __shfl_sync(0xffffffffu, base, 31) + incl - c;
+                while (keepm) {
+                    const int j = __ffs(keepm) - 1;
+                    keepm &= keepm - 1u;
+                    S.kl[base++] = (uint16_t)(((16 * qh + j) << 7) | r);
+                }
+            }
+            __syncthreads();
+            // epilogue, recheck: the tile's kept pairs spread over all threads,
+            // one pair per thread (canonical fp32 sum, rows in shared memory)
+            {
+                const int n = S.kn;
+                if (tid == 0) kept += n;
+                for (int i = tid; i < n; i += TC_T) {
+                    const int e = S.kl[i];
+                    const int q = e >> 7, r = e & 127;
                     const float4 *prow = S.P[sg] + r * TC_RS4;
-                    while (keepm) {
-                        const int q = 16 * qh + __ffs(keepm) - 1;
-                        keepm &= keepm - 1u;
-                        const float sv = pair_sqdist_smem(S.Qf + q * TC_RS4, prow, dp4);
-                        const int edge = decide32(qp, sv, band);
-                        if (edge < 0) {  // undecided in fp32: the pinned FP64 sum, rows from shared memory
-                            ++guard;
-                            const double s64 = sq_l2_exact4(S.Qf + q * TC_RS4, prow, dim);
-                            if (s64 <= qp.eps2_64) edge_found(q, li, ppos, (float)sqrt(s64));
-                        } else if (edge) {
-                            edge_found(q, li, ppos, sqrtf(sv));
+                    const float4 *qrow = S.Qf + q * TC_RS4;
+                    const float sv = pair_sqdist_smem(qrow, prow, dp4);
+                    const int edge = decide32(qp, sv, band);
+                    bool is_edge;
+                    float d;
+                    if (edge < 0) {  // undecided in fp32: the pinned FP64 sum, rows from shared memory
+                        ++guard;
+                        const double s64 = sq_l2_exact4(qrow, prow, dim);
+                        is_edge = s64 <= qp.eps2_64;
+                        d = (float)sqrt(s64);
+                    } else {
+                        is_edge = edge != 0;
+                        d = sqrtf(sv);
+                    }
+                    if (is_edge) {
+                        const int ppos = S.rpos[sg][r], li = S.rli[sg][r];
+                        atomicAdd(&S.qcnt[q], 1);
+                        atomicOr(&S.bem[li], 1u << q);
+                        if (co.off) {
+                            const int slot = atomicAdd(&S.en, 1);
+                            if (slot < TC_EB) {
+                                S.eq[slot] = (uint8_t)q;
+                                S.ecol[slot] = ppos;  // tree position; the original id is looked up at the flush
+                                S.edist[slot] = d;
+                                S.erank[slot] = (uint16_t)atomicAdd(&S.qfill[q], 1);
+                            } else {
+                                cap_put(co, S.orig[q], tv.perm[ppos], d);
+                            }
                         }
                     }
                 }
@@ -1638,6 +1681,7 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(TreeView tv, QParams qp, It
             tc::fence_before_sync();
             __syncthreads();
             tc::fence_after_sync();
+            if (tid == 0) S.kn = 0;
             issue(t + 2, sg);
             if (co.off && S.en >= TC_EB / 2) flush();
         }
