@@ -215,6 +215,111 @@ def run_reference(args, wl):
 FORMS = {"plain": (0, False), "tc": (1, False), "learned": (0, True), "tc+learned": (1, True)}
 
 
+def run_clouds(args, wl, world, rank, dist):
+    """Many clouds per step: every cloud's tree is built, then one batched
+    query over all of them; value = all clouds' edges / step time."""
+    import torch
+    from paper_2510_14147_gb300 import ctgraph as cg
+    precision, learned = FORMS[args.form]
+    specs = wl["specs"]
+    xs = [torch.from_numpy(I.cloud_points(sp)).cuda() for sp in specs]
+    eps = [sp["eps"] for sp in specs]
+    zeta = wl.get("zeta", 32)
+    stream = torch.cuda.Stream()
+    pred = None
+    if learned:
+        raise SystemExit("the learned form of the many-cloud batch is not available yet")
+    last = {}
+
+    def step(prec):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        trees = [cg.ct_build(points=x, leaf_size=zeta, stream=stream) for x in xs]
+        e[1].record(stream)
+        csrs = cg.eps_graph_query_batched(trees, eps, precision=prec, stream=stream,
+                                          use_predictor=pred is not None, predictor=pred)
+        e[2].record(stream)
+        nnz = sum(c.nnz for c in csrs)
+        last["stats"] = [c.stats() for c in csrs]
+        last["events"] = e
+        for c in csrs:
+            c.free()
+        for t in trees:
+            t.free()
+        return nnz
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(precision)
+    barrier()
+    sampler = ClockSampler(gpu_identifier(torch, torch.cuda.current_device()))
+    if rank == 0:
+        sampler.start()
+    l0 = cg.ct_kernel_launches()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    build_ms = query_ms = 0.0
+    barrier()
+    a.record(stream)
+    tot = 0
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            tot += step(precision)
+            ev = last["events"]
+            ev[2].synchronize()
+            build_ms += ev[0].elapsed_time(ev[1])
+            query_ms += ev[1].elapsed_time(ev[2])
+    b.record(stream)
+    barrier()
+    launches = cg.ct_kernel_launches() - l0
+    clocks = sampler.stop() if rank == 0 else None
+    t_ms = a.elapsed_time(b)
+    if dist:
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+        tot *= world
+    value = tot / (t_ms / 1e3)
+    st = last["stats"]
+    plain = None
+    if args.form != "plain" and not args.no_compare:
+        with torch.cuda.stream(stream):
+            step(0)
+        barrier()
+        a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a2.record(stream)
+        tp = 0
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                tp += step(0)
+        b2.record(stream)
+        barrier()
+        tpm = a2.elapsed_time(b2)
+        plain = {"form": "plain", "value": tp * world / (tpm / 1e3), "ms_per_step": tpm / args.steps,
+                 "speedup_of_form": value / (tp * world / (tpm / 1e3))}
+    agg = {k: sum(x[k] for x in st) for k in st[0]}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "clouds": len(specs), "points": sum(sp["n"] for sp in specs),
+                       "dims": sorted(set(sp["dim"] for sp in specs)), "form": args.form,
+                       "precision": precision, "learned": learned, "zeta": zeta,
+                       "parallelism": "replicas%d" % world if world > 1 else "single",
+                       "step": "ct_build of every cloud + eps_graph_query_batched + csr_free"},
+            "nnz": tot // max(args.steps, 1) // world, "query_stats": agg,
+            "stage_ms": {"build_all": build_ms / args.steps, "query_batched": query_ms / args.steps},
+            "gpu_launches": launches, "clocks": clocks, "plain": plain, "roofline": None, "e2e": None}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+
 def config_of(args, wl, world):
     prec, learned = FORMS[args.form]
     return {"workload": args.workload, "n": wl["n"], "dim": wl["dim"], "eps": wl["eps"],
@@ -264,6 +369,12 @@ def main():
     if dist:
         dist.barrier()
     from paper_2510_14147_gb300 import ctgraph as cg
+
+    if wl["kind"] == "clouds":
+        rc = run_clouds(args, wl, world, rank, dist)
+        if dist:
+            dist.destroy_process_group()
+        return rc
 
     x = load_points(wl)
     xd = torch.from_numpy(x).cuda()

@@ -152,8 +152,14 @@ ct_status eps_graph_query(const ct_tree *tree, double eps, const ct_query_opts *
                           ct_stream stream, ct_csr *out);
 
 /* Many point clouds in one call: outs[c] is the ε-graph of trees[c] with
- * radius eps[c] (host array).  Work items of all clouds share one persistent
- * launch per stage.  Same output as n_clouds calls of eps_graph_query. */
+ * radius eps[c] (host array); the same output as n_clouds calls of
+ * eps_graph_query.  L2 clouds go in batches of up to 64 that share every
+ * launch: one walk over all their groups (in one global order), one leaf
+ * launch over all their work items, one scan, one row sort.  Edit-distance
+ * clouds run one at a time.  The CSRs of one batch view shared allocations,
+ * released when the last of them is freed (each csr_free as usual); the
+ * counters ct_csr_stats returns for them are those of the whole batch.
+ * Errors: as eps_graph_query, for any cloud. */
 ct_status eps_graph_query_batched(int32_t n_clouds, const ct_tree *const *trees,
                                   const double *eps, const ct_query_opts *opts,
                                   ct_stream stream, ct_csr *outs);

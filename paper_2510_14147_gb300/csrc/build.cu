@@ -670,8 +670,10 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
                 int burst = 1;
                 int64_t iters = 0;
                 for (;;) {
-                    // every iteration adds a distinct centre to some hub
-                    if (iters > n + 2) CT_FAIL(CT_ECUDA, "split loop did not terminate");
+                    // every iteration adds a distinct centre to some hub, so
+                    // no hub is active after n + 1 of them; a burst of up to
+                    // 16 may run past the last useful iteration
+                    if (iters > n + 2 + 16) CT_FAIL(CT_ECUDA, "split loop did not terminate");
                     iters += burst;
                     CT_CHECK_CUDA(cudaMemsetAsync(active.p, 0, sizeof(int32_t), s));
                     for (int it = 0; it < burst; ++it) {

@@ -24,6 +24,7 @@ namespace {
 struct CsrPriv {
     cudaStream_t stream;
     ct_query_stats stats;
+    std::shared_ptr<ct::SharedBlocks> shared;  // batch allocations this CSR views (or null)
 };
 
 template <class F>
@@ -68,6 +69,7 @@ void fill_csr(ct_csr *out, int64_t n, ct::QueryOut &q, cudaStream_t s) {
     CsrPriv *p = new CsrPriv();
     p->stream = s;
     p->stats = q.stats;
+    p->shared = q.shared;
     out->n_rows = n;
     out->nnz = q.nnz;
     out->row_ptr = q.row_ptr;
@@ -77,9 +79,12 @@ void fill_csr(ct_csr *out, int64_t n, ct::QueryOut &q, cudaStream_t s) {
 }
 
 void release_query_out(ct::QueryOut &q, cudaStream_t s) {
-    ct::dfree(q.row_ptr, s);
-    ct::dfree(q.col, s);
-    ct::dfree(q.dist, s);
+    if (!q.shared) {
+        ct::dfree(q.row_ptr, s);
+        ct::dfree(q.col, s);
+        ct::dfree(q.dist, s);
+    }
+    q.shared.reset();
     q.row_ptr = nullptr;
     q.col = nullptr;
     q.dist = nullptr;
@@ -199,9 +204,11 @@ void csr_free(ct_csr *csr) {
     if (!csr) return;
     CsrPriv *p = (CsrPriv *)csr->priv;
     cudaStream_t s = p ? p->stream : (cudaStream_t)0;
-    if (csr->row_ptr) cudaFreeAsync(csr->row_ptr, s);
-    if (csr->col) cudaFreeAsync(csr->col, s);
-    if (csr->dist) cudaFreeAsync(csr->dist, s);
+    if (!(p && p->shared)) {  // a batch's views are released with its last CSR
+        if (csr->row_ptr) cudaFreeAsync(csr->row_ptr, s);
+        if (csr->col) cudaFreeAsync(csr->col, s);
+        if (csr->dist) cudaFreeAsync(csr->dist, s);
+    }
     delete p;
     std::memset(csr, 0, sizeof(*csr));
 }

@@ -86,6 +86,11 @@ inline void to_host(T *h, const T *d, size_t count, cudaStream_t s) {
     CT_CHECK_CUDA(cudaMemcpyAsync(h, d, count * sizeof(T), cudaMemcpyDeviceToHost, s));
     CT_CHECK_CUDA(cudaStreamSynchronize(s));
 }
+// The copy only; the caller synchronises before reading h.
+template <class T>
+inline void to_host_async(T *h, const T *d, size_t count, cudaStream_t s) {
+    if (count) CT_CHECK_CUDA(cudaMemcpyAsync(h, d, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+}
 
 int num_sms();
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

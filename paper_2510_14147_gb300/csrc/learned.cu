@@ -202,15 +202,15 @@ __global__ void k_capacity(int64_t n, const float *__restrict__ y, const int32_t
 // Traversal order: per group the mean predicted walk length of its queries;
 // sort key larger first.
 __global__ void k_group_keys(int G, const int32_t *__restrict__ group_begin, const int32_t *__restrict__ group_count,
-                             const float *__restrict__ y, TargetNorm tn, uint32_t *__restrict__ keys,
+                             const float *__restrict__ y, TargetNorm tn, int gbase, uint32_t *__restrict__ keys,
                              uint32_t *__restrict__ vals) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G) return;
     const int qb = group_begin[g], qn = group_count[g];
     float s = 0.f;
     for (int q = 0; q < qn; ++q) s += predicted(y, qb + q, 1, tn);
-    keys[g] = ~__float_as_uint(fmaxf(s / (float)max(qn, 1), 0.f));
-    vals[g] = (uint32_t)g;
+    keys[gbase + g] = ~__float_as_uint(fmaxf(s / (float)max(qn, 1), 0.f));
+    vals[gbase + g] = (uint32_t)(gbase + g);
 }
 
 Norm make_norm(const float *mean, const float *std_, int d, bool on) {
@@ -299,7 +299,7 @@ double predictor_fit(ct_predictor *P, const ct_tree *t, double eps, const ct_fit
     pr.deg = deg.p;
     pr.gvisit = gvisit.p;
     QueryOut tmp;
-    query_impl(t, qp, s, tmp, 0, nullptr, &pr);
+    query_multi(1, &t, &qp, s, &tmp, 0, nullptr, &pr);
     predictor_features(t, eps, nullptr, x.p, s);
     k_pos_group<<<grid_of(n, 256), 256, 0, s>>>(n, G, t->group_begin, gof.p);
     CT_COUNT_LAUNCH();
@@ -353,27 +353,39 @@ void predictor_predict(const ct_predictor *P, const ct_tree *t, double eps, floa
     CT_LAUNCH_CHECK();
 }
 
-void learned_plan(const ct_predictor *P, const ct_tree *t, const QParams &qp, cudaStream_t s, LearnedPlan &lp) {
+// The plan of a batch of C clouds (rows and groups concatenated).
+void learned_plan(const ct_predictor *P, int C, const ct_tree *const *trees, const QParams *qps,
+                  const int64_t *rbase, const int32_t *gbase, cudaStream_t s, LearnedPlan &lp) {
     if (!P->fitted) CT_FAIL(CT_EINVAL, "the predictor has not been fitted");
-    const int64_t n = t->n;
-    const int G = t->n_groups;
+    const int64_t n = rbase[C];
+    const int G = gbase[C];
     DBuf<float> x(n * MLP_IN, s), y(n * MLP_OUT, s);
-    predictor_features(t, qp.eps64, P, x.p, s);
+    for (int c = 0; c < C; ++c) predictor_features(trees[c], qps[c].eps64, P, x.p + rbase[c] * MLP_IN, s);
     mlp_predict(P->wh, x.p, n, y.p, s);
     x.reset();
     const TargetNorm tn{{P->tmean[0], P->tmean[1]}, {P->tstd[0], P->tstd[1]}};
-    // row capacities and their offsets
+    // row capacities (rows of cloud c from rbase[c]) and their offsets
     DBuf<int32_t> cap(n + 1, s);
     lp.cap_off = DBuf<int64_t>(n + 1, s);
-    k_capacity<<<grid_of(n, 256), 256, 0, s>>>(n, y.p, t->perm, tn, P->margin, P->pad, cap.p, nullptr, nullptr);
-    CT_COUNT_LAUNCH();
+    for (int c = 0; c < C; ++c) {
+        const int64_t nc = trees[c]->n;
+        if (!nc) continue;
+        k_capacity<<<grid_of(nc, 256), 256, 0, s>>>(nc, y.p + MLP_OUT * rbase[c], trees[c]->perm, tn, P->margin,
+                                                    P->pad, cap.p + rbase[c], nullptr, nullptr);
+        CT_COUNT_LAUNCH();
+    }
     CT_LAUNCH_CHECK();
     exclusive_scan_i32_to_i64(cap.p, lp.cap_off.p, n + 1, nullptr, s);
     // groups by decreasing predicted walk length
     if (G > 1 && P->order_by_work) {
         DBuf<uint32_t> keys(G, s), vals(G, s), tk(G, s), tv(G, s);
-        k_group_keys<<<grid_of(G, 256), 256, 0, s>>>(G, t->group_begin, t->group_count, y.p, tn, keys.p, vals.p);
-        CT_COUNT_LAUNCH();
+        for (int c = 0; c < C; ++c) {
+            const int Gc = trees[c]->n_groups;
+            if (!Gc) continue;
+            k_group_keys<<<grid_of(Gc, 256), 256, 0, s>>>(Gc, trees[c]->group_begin, trees[c]->group_count,
+                                                          y.p + MLP_OUT * rbase[c], tn, gbase[c], keys.p, vals.p);
+            CT_COUNT_LAUNCH();
+        }
         CT_LAUNCH_CHECK();
         radix_sort_pairs(keys.p, vals.p, tk.p, tv.p, G, 32, s);
         lp.group_order = DBuf<int32_t>(G, s);
@@ -399,7 +411,7 @@ void query_predicted(const ct_tree *t, const QParams &qp, const void *predictor,
     const ct_predictor *P = static_cast<const ct_predictor *>(predictor);
     if (!P->fitted) CT_FAIL(CT_EINVAL, "the predictor has not been fitted");
     if (P->device != t->device) CT_FAIL(CT_EINVAL, "predictor and tree live on different devices");
-    query_impl(t, qp, s, out, precision, P, nullptr);
+    query_multi(1, &t, &qp, s, &out, precision, P, nullptr);
 }
 
 }  // namespace ct

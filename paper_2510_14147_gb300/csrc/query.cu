@@ -20,6 +20,7 @@
 #include <cfloat>
 #include <climits>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 
 #include "lev.cuh"
@@ -112,6 +113,26 @@ TreeView view_of(const ct_tree *t) {
     v.group_order = t->group_order;
     v.n_groups = t->n_groups;
     return v;
+}
+
+// Up to kMaxClouds trees queried by the same launches (in the kernel parameter
+// bank): global group gg of cloud c is gbase[c] + g, global row rbase[c] + o.
+// A single query is the case nc = 1.
+constexpr int kMaxClouds = kBatchClouds;
+struct Views {
+    int nc;
+    int32_t gbase[kMaxClouds + 1];
+    int64_t rbase[kMaxClouds + 1];
+    TreeView tv[kMaxClouds];
+    QParams qp[kMaxClouds];
+};
+__device__ __forceinline__ int cloud_of_group(const Views &V, int gg) {
+    int lo = 0, hi = V.nc;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (V.gbase[mid] <= gg) lo = mid; else hi = mid;
+    }
+    return lo;
 }
 
 // ------------------------------------------------------------ traversal
@@ -288,14 +309,15 @@ __device__ __forceinline__ bool l2_keep(const TreeView &tv, const float4 *cen, i
     return !(sqrtf(mine) > bound);
 }
 
-template <int TPD>
+// Warp per group over all clouds' groups, taken dynamically in `order`
+// (global group ids); the lanes per vertex test follow the cloud's row length.
 __global__ void __launch_bounds__(TRAV_WARPS * 32) k_traverse_l2(
-    TreeView tv, QParams qp, Pool P, int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st,
-    int32_t *__restrict__ err, int32_t *__restrict__ next_group, int32_t *__restrict__ gvisit) {
-    extern __shared__ float4 sc[];  // TRAV_WARPS x (dp/4)
-    const int nq4 = tv.dp >> 2;
+    const __grid_constant__ Views V, const int32_t *__restrict__ order, int n_order, Pool P,
+    int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st, int32_t *__restrict__ err,
+    int32_t *__restrict__ next_group, int32_t *__restrict__ gvisit, int max_nq4) {
+    extern __shared__ float4 sc[];  // TRAV_WARPS x (largest dp / 4)
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4 *cen = sc + wib * nq4;
+    float4 *cen = sc + wib * max_nq4;
     const int gw = blockIdx.x * TRAV_WARPS + wib;
     int2 *stack = stacks + (int64_t)gw * cap;
     unsigned long long evals = 0;
@@ -305,16 +327,28 @@ __global__ void __launch_bounds__(TRAV_WARPS * 32) k_traverse_l2(
         int gi = 0;
         if (lane == 0) gi = atomicAdd(next_group, 1);
         gi = __shfl_sync(0xffffffffu, gi, 0);
-        if (gi >= tv.n_groups) break;
-        const int g = tv.group_order[gi];
+        if (gi >= n_order) break;
+        const int gg = order[gi];
+        const int c = cloud_of_group(V, gg);
+        const TreeView &tv = V.tv[c];
+        const int g = gg - V.gbase[c];
+        const int nq4 = tv.dp >> 2;
+        const int tpd = nq4 >= 16 ? 8 : nq4 >= 8 ? 4 : nq4 >= 4 ? 2 : 1;
         const float4 *crow = reinterpret_cast<const float4 *>(tv.pts + (size_t)tv.group_begin[g] * tv.dp);
         for (int k = lane; k < nq4; k += 32) cen[k] = crow[k];
         __syncwarp();
-        const float add = qp.eps_up + tv.group_radius[g];
-        auto tester = [&](int first, int take) { return l2_keep<TPD>(tv, cen, nq4, first, take, add); };
+        const float add = V.qp[c].eps_up + tv.group_radius[g];
+        auto tester = [&](int first, int take) {
+            switch (tpd) {
+                case 8: return l2_keep<8>(tv, cen, nq4, first, take, add);
+                case 4: return l2_keep<4>(tv, cen, nq4, first, take, add);
+                case 2: return l2_keep<2>(tv, cen, nq4, first, take, add);
+                default: return l2_keep<1>(tv, cen, nq4, first, take, add);
+            }
+        };
         const unsigned long long e0 = evals;
-        if (walk_group(tv, stack, cap, g, P, pc, evals, err, tester) < 0) return;
-        if (gvisit) group_visits(gvisit, g, evals - e0);
+        if (walk_group(tv, stack, cap, gg, P, pc, evals, err, tester) < 0) return;
+        if (gvisit) group_visits(gvisit, gg, evals - e0);
         __syncwarp();
     }
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
@@ -731,7 +765,7 @@ __device__ __forceinline__ void cap_put(const CapOut &co, int o, int32_t c, floa
 
 template <bool EMIT>
 __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
-    TreeView tv, QParams qp, Items items, const uint32_t *__restrict__ cand,
+    const __grid_constant__ Views V, Items items, const uint32_t *__restrict__ cand,
     uint32_t *__restrict__ emask, int32_t *__restrict__ deg, const int64_t *__restrict__ row_ptr,
     int32_t *__restrict__ rowcur, int32_t *__restrict__ col, float *__restrict__ dist,
     unsigned long long *__restrict__ st, int32_t *__restrict__ err, CapOut co, const uint8_t *__restrict__ rowsel) {
@@ -739,7 +773,12 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
     LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
     const int it = blockIdx.x;
     if (it >= *items.count) return;
-    const int g = items.group[it];
+    const int gg = items.group[it];
+    const int cloud = cloud_of_group(V, gg);
+    const TreeView &tv = V.tv[cloud];
+    const QParams &qp = V.qp[cloud];
+    const int g = gg - V.gbase[cloud];
+    const int64_t rbase = V.rbase[cloud];  // CSR rows of this cloud start here
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int qi = tid >> 3, pj = tid & 7;
     const int dp = tv.dp, dim = tv.dim;
@@ -758,8 +797,8 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
             S.qcnt[tid] = 0;
             bool sel = false;
             if (tid < nqr) {
-                int o = tv.perm[qfirst + tid];
-                S.cursor[tid] = o;  // original id of the query (row of the CSR)
+                const int64_t o = rbase + tv.perm[qfirst + tid];
+                S.cursor[tid] = (int)o;  // row of the query in the (concatenated) CSR
                 if (EMIT) {
                     S.rowb[tid] = row_ptr[o];
                     S.rowe[tid] = row_ptr[o + 1];
@@ -1389,7 +1428,7 @@ __device__ __forceinline__ void tc_convert_part(unsigned char *tile, int r, cons
     a2 = f2_sum(an);
 }
 
-__global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(TreeView tv, QParams qp, Items items,
+__global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Views V, Items items,
                                                    const uint32_t *__restrict__ cand, uint32_t *__restrict__ emask,
                                                    int32_t *__restrict__ deg, unsigned long long *__restrict__ st,
                                                    int32_t *__restrict__ err, CapOut co) {
@@ -1398,7 +1437,12 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(TreeView tv, QParams qp, It
     const int it = blockIdx.x;
     if (it >= *items.count) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = items.group[it];
+    const int gg = items.group[it];
+    const int cloud = cloud_of_group(V, gg);
+    const TreeView &tv = V.tv[cloud];
+    const QParams &qp = V.qp[cloud];
+    const int g = gg - V.gbase[cloud];
+    const int64_t rbase = V.rbase[cloud];  // CSR rows of this cloud start here
     const int dp = tv.dp, dim = tv.dim, dp4 = dp >> 2;
     const int ksteps = (dp + 15) >> 4;
     const int K4 = 4 * ksteps;                       // float4 columns of the MMA's K
@@ -1511,7 +1555,7 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(TreeView tv, QParams qp, It
         }
         if (tid < 32) {
             S.qcnt[tid] = 0;
-            S.orig[tid] = tid < nqr ? tv.perm[qfirst + tid] : 0;
+            S.orig[tid] = tid < nqr ? (int)(rbase + tv.perm[qfirst + tid]) : 0;
         }
         for (int i = tid; i < nb; i += TC_T) S.bem[i] = 0u;
         if (tid < 32) S.qfill[tid] = 0;
@@ -2097,10 +2141,9 @@ QParams make_qparams(const ct_tree *t, double eps, int include_self) {
 struct TravLaunch {
     int blocks, warps;
 };
-TravLaunch trav_launch_config(const ct_tree *t) {
-    const int G = t->n_groups;
+TravLaunch trav_launch_config(bool l2, int64_t G) {
     TravLaunch tl;
-    if (t->metric == CT_L2_F32) {
+    if (l2) {
         tl.blocks = (int)std::min<int64_t>(ceil_div(G, TRAV_WARPS), (int64_t)num_sms() * 8);
         tl.blocks = std::max(tl.blocks, 1);
         tl.warps = tl.blocks * TRAV_WARPS;
@@ -2113,8 +2156,8 @@ TravLaunch trav_launch_config(const ct_tree *t) {
 
 // First pool size: 256 candidate blocks per point (or 512 per group), at most
 // a quarter of the free device memory, plus one chunk per warp.
-int64_t pool_capacity_guess(const ct_tree *t, const TravLaunch &tl) {
-    int64_t want = std::max<int64_t>(256 * t->n, (int64_t)t->n_groups * 512);
+int64_t pool_capacity_guess(int64_t n, int64_t G, const TravLaunch &tl) {
+    int64_t want = std::max<int64_t>(256 * n, G * 512);
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
         int64_t lim = (int64_t)(fr / 4 / sizeof(uint32_t));
@@ -2125,32 +2168,27 @@ int64_t pool_capacity_guess(const ct_tree *t, const TravLaunch &tl) {
     return want + (int64_t)(tl.warps + 1) * POOL_CHUNK;
 }
 
-// Clears the pool counters and launches the traversal (allocates nothing).
-void launch_traversal(const ct_tree *t, const TreeView &tv, const QParams &qp, const Pool &P, int2 *stacks, int cap,
-                      const TravLaunch &tl, unsigned long long *st, int32_t *err, int32_t *next_group,
-                      cudaStream_t s, int32_t *gvisit = nullptr) {
+// Clears the pool counters and launches the traversal over `order` (global
+// group ids; allocates nothing).  Edit distance: a single cloud.
+void launch_traversal(const Views &V, int64_t G, int max_dp, int max_len, bool l2, const int32_t *order,
+                      const Pool &P, int2 *stacks, int cap, const TravLaunch &tl, unsigned long long *st,
+                      int32_t *err, int32_t *next_group, cudaStream_t s, int32_t *gvisit = nullptr) {
     // P.next .. P.overflow are the four 64-bit words of one counter block
     CT_CHECK_CUDA(cudaMemsetAsync(next_group, 0, sizeof(int32_t), s));
     CT_CHECK_CUDA(cudaMemsetAsync(P.next, 0, 4 * sizeof(unsigned long long), s));
-    if (t->n_groups == 0) return;
-    if (t->metric == CT_L2_F32) {
-        const int nq4 = t->dp >> 2;
-        const size_t tsm = (size_t)TRAV_WARPS * t->dp * sizeof(float);
-        const int tpd = nq4 >= 16 ? 8 : nq4 >= 8 ? 4 : nq4 >= 4 ? 2 : 1;
-        switch (tpd) {
-#define CT_TRL(T)                                                                                               \
-    case T:                                                                                                     \
-        if (tsm > 48 * 1024)                                                                                    \
-            CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)); \
-        k_traverse_l2<T><<<tl.blocks, TRAV_WARPS * 32, tsm, s>>>(tv, qp, P, stacks, cap, st, err, next_group, gvisit); \
-        break;
-            CT_TRL(1) CT_TRL(2) CT_TRL(4) CT_TRL(8)
-#undef CT_TRL
-        }
+    if (G == 0) return;
+    if (l2) {
+        const size_t tsm = (size_t)TRAV_WARPS * max_dp * sizeof(float);
+        if (tsm > 48 * 1024)
+            CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+        k_traverse_l2<<<tl.blocks, TRAV_WARPS * 32, tsm, s>>>(V, order, (int)G, P, stacks, cap, st, err, next_group,
+                                                               gvisit, max_dp >> 2);
     } else {
-        switch (lev_words_for(t->max_len)) {
+        TreeView tv = V.tv[0];
+        tv.group_order = order;
+        switch (lev_words_for(max_len)) {
 #define CT_TL(WW) \
-    case WW: k_traverse_lev<WW><<<tl.blocks, 32, 0, s>>>(tv, qp, P, stacks, cap, st, err, next_group, gvisit); break;
+    case WW: k_traverse_lev<WW><<<tl.blocks, 32, 0, s>>>(tv, V.qp[0], P, stacks, cap, st, err, next_group, gvisit); break;
             CT_TL(1) CT_TL(2) CT_TL(4) CT_TL(8) CT_TL(16)
 #undef CT_TL
         }
@@ -2159,33 +2197,87 @@ void launch_traversal(const ct_tree *t, const TreeView &tv, const QParams &qp, c
     CT_LAUNCH_CHECK();
 }
 
-void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out, int precision,
-                const ct_predictor *pred, Probe *probe) {
-    const int64_t n = t->n;
-    const int G = t->n_groups;
-    const bool l2 = t->metric == CT_L2_F32;
-    TreeView tv = view_of(t);
+// Global walk order of several clouds: groups by decreasing radius relative
+// to their cloud's eps.
+__global__ void k_radius_keys(int G, const float *__restrict__ group_radius, float inv_eps, int gbase,
+                              uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    keys[gbase + g] = ~__float_as_uint(fmaxf(group_radius[g] * inv_eps, 0.f));
+    vals[gbase + g] = (uint32_t)(gbase + g);
+}
+
+// Relative row_ptr of one cloud from the concatenated one.
+__global__ void k_rel_rows(int64_t n1, const int64_t *__restrict__ grow, int64_t *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n1) out[i] = grow[i] - grow[0];
+}
+
+void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStream_t s, QueryOut *outs,
+                 int precision, const ct_predictor *pred, Probe *probe) {
+    if (C < 1 || C > kMaxClouds) CT_FAIL(CT_EINVAL, "between 1 and %d clouds per batch", kMaxClouds);
+    const bool l2 = trees[0]->metric == CT_L2_F32;
+    if (C > 1 && !l2) CT_FAIL(CT_EINVAL, "edit-distance trees are queried one at a time");
+    // the clouds' groups and rows, concatenated
+    Views V;
+    std::memset(&V, 0, sizeof(V));
+    V.nc = C;
+    int max_dp = 4, max_depth = 0, max_len = 0;
+    for (int c = 0; c < C; ++c) {
+        const ct_tree *tc = trees[c];
+        if ((tc->metric == CT_L2_F32) != l2) CT_FAIL(CT_EINVAL, "a batch mixes metrics");
+        V.tv[c] = view_of(tc);
+        V.qp[c] = qps[c];
+        V.gbase[c + 1] = V.gbase[c] + tc->n_groups;
+        V.rbase[c + 1] = V.rbase[c] + tc->n;
+        max_dp = std::max(max_dp, tc->dp);
+        max_depth = std::max(max_depth, tc->depth);
+        max_len = std::max(max_len, tc->max_len);
+    }
+    if (V.rbase[C] >= 0x7fffffffLL) CT_FAIL(CT_EOVERFLOW, "a batch above 2^31 points");
+    const int64_t n = V.rbase[C];
+    const int G = V.gbase[C];
+    const ct_tree *t = trees[0];  // edit distance: the only cloud
     DBuf<unsigned long long> st(ST_N, s);
     CT_CHECK_CUDA(cudaMemsetAsync(st.p, 0, ST_N * sizeof(unsigned long long), s));
     int32_t *err = reinterpret_cast<int32_t *>(st.p + ST_ERR);
+    QueryOut all;  // the concatenated CSR of all clouds
 
     // learned form: row capacities and the traversal order from the predictor
     LearnedPlan lp;
     if (pred && !probe && n > 0) {
         ProfScope ps("predict", s);
-        learned_plan(pred, t, qp, s, lp);
-        if (lp.group_order.p) tv.group_order = lp.group_order.p;
+        learned_plan(pred, C, trees, qps, V.rbase, V.gbase, s, lp);
+    }
+    // walk order: predicted walk length, else decreasing radius (relative to eps)
+    DBuf<uint32_t> okeys, ovals;
+    const int32_t *order = lp.group_order.p;
+    if (!order && C == 1) order = t->group_order;
+    if (!order && G > 0) {
+        okeys = DBuf<uint32_t>(G, s);
+        ovals = DBuf<uint32_t>(G, s);
+        for (int c = 0; c < C; ++c) {
+            const int Gc = trees[c]->n_groups;
+            if (!Gc) continue;
+            k_radius_keys<<<grid_for(Gc, 256), 256, 0, s>>>(Gc, trees[c]->group_radius,
+                                                            (float)(1.0 / std::max(qps[c].eps64, 1e-30)),
+                                                            V.gbase[c], okeys.p, ovals.p);
+            CT_COUNT_LAUNCH();
+        }
+        DBuf<uint32_t> tk(G, s), tvv(G, s);
+        radix_sort_pairs(okeys.p, ovals.p, tk.p, tvv.p, G, 32, s);
+        order = reinterpret_cast<const int32_t *>(ovals.p);
     }
     int32_t *gvisit = probe ? probe->gvisit : nullptr;
 
     const int W = l2 ? 1 : lev_words_for(t->max_len);
     // 1. traversal: one pass into the candidate pool (rerun once if it overflows)
-    const int cap = 32 * (t->depth + 2);
-    TravLaunch tl = trav_launch_config(t);
+    const int cap = 32 * (max_depth + 2);
+    TravLaunch tl = trav_launch_config(l2, G);
     DBuf<int2> stacks((size_t)tl.warps * cap, s);
     DBuf<unsigned long long> ctr(4, s);
     DBuf<int32_t> next_group(1, s);
-    int64_t pool_cap = pool_capacity_guess(t, tl);
+    int64_t pool_cap = pool_capacity_guess(n, G, tl);
     DBuf<uint32_t> pool;
     DBuf<int32_t> seg_group, seg_count;
     DBuf<int64_t> seg_begin;
@@ -2201,7 +2293,8 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
                  reinterpret_cast<int32_t *>(ctr.p + 1), seg_cap, ctr.p + 2, reinterpret_cast<int32_t *>(ctr.p + 3)};
         {
             ProfScope ps("traverse", s);
-            launch_traversal(t, tv, qp, P, stacks.p, cap, tl, st.p, err, next_group.p, s, gvisit);
+            launch_traversal(V, G, max_dp, max_len, l2, order, P, stacks.p, cap, tl, st.p, err, next_group.p, s,
+                             gvisit);
         }
         to_host(hc, ctr.p, 4, s);
         if (!(uint32_t)hc[3]) break;
@@ -2296,9 +2389,9 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
         if (l2) {
             leaf_l2_prepare();
             if (emit)
-                k_leaf_l2<true><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel);
+                k_leaf_l2<true><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(V, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel);
             else
-                k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel);
+                k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(V, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel);
         } else {
             switch (W) {
 #define CT_LL(WW)                                                                                                      \
@@ -2307,8 +2400,8 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
             CT_CHECK_CUDA(cudaFuncSetAttribute(k_leaf_lev<true, WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm)); \
             CT_CHECK_CUDA(cudaFuncSetAttribute(k_leaf_lev<false, WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm)); \
         }                                                                                                              \
-        if (emit) k_leaf_lev<true, WW><<<(unsigned)max_items, LEAF_T, lsm, s>>>(tv, qp, amap.p, A, qchunk, items, cand_p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel); \
-        else k_leaf_lev<false, WW><<<(unsigned)max_items, LEAF_T, lsm, s>>>(tv, qp, amap.p, A, qchunk, items, cand_p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel);    \
+        if (emit) k_leaf_lev<true, WW><<<(unsigned)max_items, LEAF_T, lsm, s>>>(V.tv[0], V.qp[0], amap.p, A, qchunk, items, cand_p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel); \
+        else k_leaf_lev<false, WW><<<(unsigned)max_items, LEAF_T, lsm, s>>>(V.tv[0], V.qp[0], amap.p, A, qchunk, items, cand_p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel);    \
         break;
                 CT_LL(1) CT_LL(2) CT_LL(4) CT_LL(8) CT_LL(16)
 #undef CT_LL
@@ -2319,7 +2412,7 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
     };
     // the tensor-core filter applies to L2 rows of at most 128 floats; wider
     // rows use the FP32 tiles (same output)
-    const bool use_tc = precision == 1 && l2 && t->dp <= 128;
+    const bool use_tc = precision == 1 && l2 && max_dp <= 128;
     if (use_tc) {
         ProfScope ps("leaf_count_tc", s);
         static bool tc_ready = false;
@@ -2328,7 +2421,7 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
             tc_ready = true;
         }
         if (G && nseg) {
-            k_leaf_tc<<<(unsigned)max_items, TC_T, kTcSmem, s>>>(tv, qp, items, cand_p, emask.p, deg.p, st.p, err, co);
+            k_leaf_tc<<<(unsigned)max_items, TC_T, kTcSmem, s>>>(V, items, cand_p, emask.p, deg.p, st.p, err, co);
             CT_COUNT_LAUNCH();
             CT_LAUNCH_CHECK();
         }
@@ -2342,14 +2435,14 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
         to_host(hs, st.p, ST_N, s);
         prof_flush();
         if (hs[ST_ERR]) CT_FAIL(CT_ECUDA, "internal consistency check failed in the query (code %llu)", hs[ST_ERR]);
-        out.stats.traversal_evals = (int64_t)hs[ST_TRAV];
-        out.stats.leaf_pairs = (int64_t)hs[ST_PAIRS];
-        out.stats.guard_fp64 = (int64_t)hs[ST_GUARD];
-        out.stats.recheck_fp32 = (int64_t)hs[ST_RECHECK];
-        out.stats.emit_pairs = (int64_t)hs[ST_EMIT];
-        out.stats.leaf_rows = (int64_t)hs[ST_ROWS];
-        out.stats.guard_band = (int64_t)hs[ST_BAND];
-        out.stats.candidates = n_cand;
+        all.stats.traversal_evals = (int64_t)hs[ST_TRAV];
+        all.stats.leaf_pairs = (int64_t)hs[ST_PAIRS];
+        all.stats.guard_fp64 = (int64_t)hs[ST_GUARD];
+        all.stats.recheck_fp32 = (int64_t)hs[ST_RECHECK];
+        all.stats.emit_pairs = (int64_t)hs[ST_EMIT];
+        all.stats.leaf_rows = (int64_t)hs[ST_ROWS];
+        all.stats.guard_band = (int64_t)hs[ST_BAND];
+        all.stats.candidates = n_cand;
     };
 
     if (probe) {  // labels for fitting the predictor
@@ -2360,13 +2453,13 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
 
     // 3. scan -> row_ptr, then emit
     int64_t *row_ptr = (int64_t *)dmalloc((size_t)(n + 1) * sizeof(int64_t), s);
-    out.row_ptr = row_ptr;
+    all.row_ptr = row_ptr;
     exclusive_scan_i32_to_i64(deg.p, row_ptr, n + 1, nullptr, s);
     int64_t nnz = 0;
     to_host(&nnz, row_ptr + n, 1, s);
-    out.nnz = nnz;
-    out.col = (int32_t *)dmalloc((size_t)(nnz ? nnz : 1) * sizeof(int32_t), s);
-    out.dist = (float *)dmalloc((size_t)(nnz ? nnz : 1) * sizeof(float), s);
+    all.nnz = nnz;
+    all.col = (int32_t *)dmalloc((size_t)(nnz ? nnz : 1) * sizeof(int32_t), s);
+    all.dist = (float *)dmalloc((size_t)(nnz ? nnz : 1) * sizeof(float), s);
     if (capmode) {
         // one-pass emit: move the capacity region and the arena into the CSR;
         // rows that lost entries are emitted again, exactly
@@ -2377,7 +2470,7 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
                 k_cap_rows<<<grid_for(n, 256), 256, 0, s>>>(n, row_ptr, lp.cap_off.p, c_fill.p, lost.p, o_n.p + 1, err);
                 CT_COUNT_LAUNCH();
                 k_compact<<<grid_for(n * 32, 256), 256, 0, s>>>(n, row_ptr, lp.cap_off.p, lost.p, c_col.p, c_dist.p,
-                                                                out.col, out.dist);
+                                                                all.col, all.dist);
                 CT_COUNT_LAUNCH();
                 CT_LAUNCH_CHECK();
             }
@@ -2385,42 +2478,70 @@ void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &o
             const int64_t used = std::min<int64_t>((int64_t)hv[0], co.ovf_cap);
             if (used > 0) {
                 k_ovf_scatter<<<grid_for(used, 256), 256, 0, s>>>(used, o_row.p, o_slot.p, o_col.p, o_dist.p, lost.p,
-                                                                  row_ptr, out.col, out.dist, err);
+                                                                  row_ptr, all.col, all.dist, err);
                 CT_COUNT_LAUNCH();
                 CT_LAUNCH_CHECK();
             }
         }
-        out.stats.overflow_rows = (int64_t)hv[1];
-        out.stats.reemit_rows = (int64_t)hv[2];
+        all.stats.overflow_rows = (int64_t)hv[1];
+        all.stats.reemit_rows = (int64_t)hv[2];
         c_col.reset();
         c_dist.reset();
         if (hv[2]) {
             ProfScope ps("reemit", s);
             CT_CHECK_CUDA(cudaMemsetAsync(rowcur.p, 0, (n + 1) * sizeof(int32_t), s));
-            leaf(true, row_ptr, out.col, out.dist, lost.p);
+            leaf(true, row_ptr, all.col, all.dist, lost.p);
             k_check_rows_sel<<<grid_for(n, 256), 256, 0, s>>>(n, row_ptr, rowcur.p, lost.p, err);
             CT_COUNT_LAUNCH();
         }
     } else if (nnz) {
         ProfScope ps("leaf_emit", s);
         CT_CHECK_CUDA(cudaMemsetAsync(rowcur.p, 0, (n + 1) * sizeof(int32_t), s));
-        leaf(true, row_ptr, out.col, out.dist, nullptr);
+        leaf(true, row_ptr, all.col, all.dist, nullptr);
         k_check_rows<<<grid_for(n, 256), 256, 0, s>>>(n, row_ptr, rowcur.p, err);
         CT_COUNT_LAUNCH();
     }
     {
         ProfScope ps("row_sort", s);
-        sort_rows(row_ptr, n, out.col, out.dist, nnz, s);
+        sort_rows(row_ptr, n, all.col, all.dist, nnz, s);
     }
     finish_stats();
+    if (C == 1) {
+        outs[0] = all;
+        return;
+    }
+    // several clouds: CSRs that view one shared allocation each of row
+    // offsets (relative to the cloud), columns and distances
+    std::vector<int64_t> hb(C + 1);
+    for (int c = 0; c <= C; ++c) to_host_async(&hb[c], row_ptr + V.rbase[c], 1, s);
+    CT_CHECK_CUDA(cudaStreamSynchronize(s));
+    int64_t *rel = (int64_t *)dmalloc((size_t)(n + C) * sizeof(int64_t), s);
+    auto blocks = std::make_shared<SharedBlocks>(s);
+    blocks->p[0] = rel;
+    blocks->p[1] = all.col;
+    blocks->p[2] = all.dist;
+    for (int c = 0; c < C; ++c) {
+        const int64_t nc1 = trees[c]->n + 1, o = V.rbase[c] + c;
+        k_rel_rows<<<grid_for(nc1, 256), 256, 0, s>>>(nc1, row_ptr + V.rbase[c], rel + o);
+        CT_COUNT_LAUNCH();
+        QueryOut &q = outs[c];
+        q.row_ptr = rel + o;
+        q.col = all.col + hb[c];
+        q.dist = all.dist + hb[c];
+        q.nnz = hb[c + 1] - hb[c];
+        q.stats = all.stats;
+        q.shared = blocks;
+    }
+    CT_LAUNCH_CHECK();
+    dfree(row_ptr, s);  // stream ordered: after the relative copies
 }
 
 void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out) {
-    query_impl(t, qp, s, out, 0, nullptr, nullptr);
+    query_multi(1, &t, &qp, s, &out, 0, nullptr, nullptr);
 }
 
 void query_tc(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out) {
-    query_impl(t, qp, s, out, 1, nullptr, nullptr);
+    query_multi(1, &t, &qp, s, &out, 1, nullptr, nullptr);
 }
 
 }  // namespace ct
@@ -2482,7 +2603,7 @@ void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cuda
     unsigned long long *ctr = (unsigned long long *)take(4 * sizeof(unsigned long long));
     int32_t *next_group = (int32_t *)take(sizeof(int32_t));
     int32_t *nitems = (int32_t *)take(sizeof(int32_t));
-    TravLaunch tl = trav_launch_config(t);
+    TravLaunch tl = trav_launch_config(true, t->n_groups);
     const size_t stack_per_block = (size_t)TRAV_WARPS * cap * sizeof(int2);
     if (off + stack_per_block > cap_bytes / 2)
         CT_FAIL(CT_EUNSUPPORTED, "a tree of depth %d needs more than the fixed %zu-byte scratch", t->depth, cap_bytes);
@@ -2505,11 +2626,17 @@ void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cuda
     Pool P{pool, pool_cap, ctr, seg_group, seg_count, seg_begin, reinterpret_cast<int32_t *>(ctr + 1), seg_cap,
            ctr + 2, reinterpret_cast<int32_t *>(ctr + 3)};
 
-    TreeView tv = view_of(t);
+    Views V;
+    std::memset(&V, 0, sizeof(V));
+    V.nc = 1;
+    V.tv[0] = view_of(t);
+    V.qp[0] = qp;
+    V.gbase[1] = t->n_groups;
+    V.rbase[1] = n;
     int32_t *err = reinterpret_cast<int32_t *>(st + ST_ERR);
     // the array keeps the previous call's contents: clear what must start at zero
     CT_CHECK_CUDA(cudaMemsetAsync(st, 0, ST_N * sizeof(unsigned long long), s));
-    launch_traversal(t, tv, qp, P, stacks, cap, tl, st, err, next_group, s);
+    launch_traversal(V, t->n_groups, t->dp, 0, true, t->group_order, P, stacks, cap, tl, st, err, next_group, s);
     unsigned long long hc[4] = {0, 0, 0, 0};
     CT_CHECK_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
     CT_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -2546,7 +2673,7 @@ void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cuda
         CT_COUNT_LAUNCH();
         Items items{igroup, ibeg, iend, nitems};
         leaf_l2_prepare();
-        k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(tv, qp, items, pool, nullptr, degrees, nullptr,
+        k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(V, items, pool, nullptr, degrees, nullptr,
                                                                           nullptr, nullptr, nullptr, st, err, CapOut{},
                                                                           nullptr);
         CT_COUNT_LAUNCH();

@@ -1,6 +1,8 @@
 // query.cuh -- shared declarations of the query stages.
 #pragma once
 
+#include <memory>
+
 #include "common.cuh"
 
 struct ct_predictor;
@@ -26,13 +28,29 @@ struct QParams {
 
 QParams make_qparams(const ct_tree *t, double eps, int include_self);
 
-// Per-query output and counters of one query.
+// Device allocations shared by the CSRs of one batch; released (stream
+// ordered) when the last of them is released.
+struct SharedBlocks {
+    explicit SharedBlocks(cudaStream_t st) : s(st) {}
+    ~SharedBlocks() {
+        for (void *q : p)
+            if (q) cudaFreeAsync(q, s);
+    }
+    SharedBlocks(const SharedBlocks &) = delete;
+    SharedBlocks &operator=(const SharedBlocks &) = delete;
+    cudaStream_t s;
+    void *p[3] = {nullptr, nullptr, nullptr};
+};
+
+// Per-query output and counters of one query.  With `shared` set the three
+// arrays are views into a batch's shared allocations.
 struct QueryOut {
     int64_t nnz = 0;
     int64_t *row_ptr = nullptr;
     int32_t *col = nullptr;
     float *dist = nullptr;
     ct_query_stats stats{};
+    std::shared_ptr<SharedBlocks> shared;
 };
 
 // The plain FP32 path (precision 0) and the edit-distance path.
@@ -53,9 +71,13 @@ struct LearnedPlan {
     DBuf<int32_t> group_order;  // groups by decreasing predicted walk length
     bool one_pass = false;
 };
-void query_impl(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out, int precision,
-                const ct_predictor *P, Probe *probe);
-void learned_plan(const ct_predictor *P, const ct_tree *t, const QParams &qp, cudaStream_t s, LearnedPlan &lp);
+// The query of C clouds (1 <= C <= 64) in shared launches: outs[c] is the
+// CSR of trees[c].  Several clouds must all be L2; a probe needs C = 1.
+void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStream_t s, QueryOut *outs,
+                 int precision, const ct_predictor *P, Probe *probe);
+constexpr int kBatchClouds = 64;
+void learned_plan(const ct_predictor *P, int C, const ct_tree *const *trees, const QParams *qps,
+                  const int64_t *rbase, const int32_t *gbase, cudaStream_t s, LearnedPlan &lp);
 
 // Sorts every CSR row by column, moving dist along.
 void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int64_t nnz,
