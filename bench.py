@@ -212,7 +212,8 @@ def run_reference(args, wl):
     return 0
 
 
-FORMS = {"plain": (0, False), "tc": (1, False), "learned": (0, True), "tc+learned": (1, True)}
+FORMS = {"plain": (0, False), "tc": (1, False), "learned": (0, True), "tc+learned": (1, True),
+         "auto": (2, False), "auto+learned": (2, True)}
 
 
 def run_clouds(args, wl, world, rank, dist):
@@ -254,6 +255,16 @@ def run_clouds(args, wl, world, rank, dist):
             dist.barrier()
         torch.cuda.synchronize()
 
+    tuned = None
+    if precision == 2:  # autotune the count kernels on these clouds, outside the timed region
+        with torch.cuda.stream(stream):
+            trees = [cg.ct_build(points=x, leaf_size=zeta, stream=stream) for x in xs]
+            t0 = time.perf_counter()
+            ch = cg.ct_autotune(trees, eps, stream=stream)
+            tuned = {"bf16_clouds": int(sum(ch)), "fp32_clouds": len(ch) - int(sum(ch)),
+                     "tune_s": time.perf_counter() - t0}
+            for t in trees:
+                t.free()
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step(precision)
@@ -313,7 +324,8 @@ def run_clouds(args, wl, world, rank, dist):
                        "step": "ct_build of every cloud + eps_graph_query_batched + csr_free"},
             "nnz": tot // max(args.steps, 1) // world, "query_stats": agg,
             "stage_ms": {"build_all": build_ms / args.steps, "query_batched": query_ms / args.steps},
-            "gpu_launches": launches, "clocks": clocks, "plain": plain, "roofline": None, "e2e": None}
+            "gpu_launches": launches, "clocks": clocks, "plain": plain, "roofline": None, "e2e": None,
+            "autotune": tuned}
     if rank == 0:
         print(json.dumps(line))
     return 0

@@ -83,8 +83,12 @@ typedef struct {
 
 /* Query options.
  *  precision:     0 = plain FP32 direct-difference leaf tiles;
- *                 1 = BF16 tensor-core filter (tcgen05) with FP32 recheck.
- *                 Both give the same edge set.
+ *                 1 = BF16 tensor-core filter (tcgen05) with FP32 recheck
+ *                     (L2 only; rows above 128 floats use the FP32 tiles);
+ *                 2 = per cloud, the count kernel and work-item length that
+ *                     ct_autotune measured fastest for its row length (before
+ *                     tuning: BF16 tiles from 32 floats per row up).
+ *                 All give the same edge set and distances.
  *  use_predictor: 0 = two-pass count -> scan -> emit;
  *                 1 = one-pass emit into row capacities predicted by
  *                     `predictor` (a fitted ct_predictor on the tree's
@@ -163,6 +167,19 @@ ct_status eps_graph_query(const ct_tree *tree, double eps, const ct_query_opts *
 ct_status eps_graph_query_batched(int32_t n_clouds, const ct_tree *const *trees,
                                   const double *eps, const ct_query_opts *opts,
                                   ct_stream stream, ct_csr *outs);
+
+/* Autotuner of precision 2.  For each class of row length present among the
+ * L2 trees (dp = dim rounded up to 4: <= 4, 16, 32, 64, 128), times the
+ * batched query of that class's clouds (eps_graph_query_batched with
+ * `opts`, twice per candidate, outputs discarded) with each candidate --
+ * count kernel (BF16 or FP32 tiles) x work-item length (512 or 256
+ * candidate blocks) -- and keeps the fastest in a process-wide table.
+ * choices (host int32[n_clouds], may be NULL) receives each cloud's kernel
+ * (1 BF16, 0 FP32).  Synchronises `stream`.  ct_autotune_reset clears the
+ * table.  Errors: as eps_graph_query_batched. */
+ct_status ct_autotune(int32_t n_clouds, const ct_tree *const *trees, const double *eps,
+                      const ct_query_opts *opts, ct_stream stream, int32_t *choices);
+void ct_autotune_reset(void);
 
 /* Size of the fixed device array used by eps_graph_degrees_noalloc. */
 #define CT_NOALLOC_SCRATCH_BYTES (16u << 20)

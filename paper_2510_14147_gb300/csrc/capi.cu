@@ -15,6 +15,8 @@ void query_predicted(const ct_tree *t, const QParams &qp, const void *predictor,
                      cudaStream_t s, QueryOut &out);
 void query_batched(int n_clouds, const ct_tree *const *trees, const QParams *qps, const ct_query_opts *opts,
                    cudaStream_t s, QueryOut *outs);
+void autotune(int n_clouds, const ct_tree *const *trees, const QParams *qps, const ct_query_opts *opts,
+              cudaStream_t s, int32_t *choices);
 void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cudaStream_t s);
 void tc_selftest(const void *A, const void *B, float *D, cudaStream_t s);
 }  // namespace ct
@@ -58,7 +60,7 @@ ct_query_opts default_query_opts() {
 void validate_query(const ct_tree *tree, double eps, const ct_query_opts &o) {
     if (!tree) CT_FAIL(CT_EINVAL, "tree is NULL");
     if (!(eps >= 0.0)) CT_FAIL(CT_EINVAL, "eps must be >= 0 (got %g)", eps);
-    if (o.precision != 0 && o.precision != 1) CT_FAIL(CT_EINVAL, "precision must be 0 or 1");
+    if (o.precision < 0 || o.precision > 2) CT_FAIL(CT_EINVAL, "precision must be 0, 1 or 2");
     if (o.precision == 1 && tree->metric != CT_L2_F32)
         CT_FAIL(CT_EINVAL, "the BF16 filter applies to L2 trees only");
     if (o.use_predictor && !o.predictor) CT_FAIL(CT_EINVAL, "use_predictor set without a predictor");
@@ -133,10 +135,8 @@ ct_status eps_graph_query(const ct_tree *tree, double eps, const ct_query_opts *
         ct::QParams qp = ct::make_qparams(tree, eps, o.include_self);
         if (o.use_predictor)
             ct::query_predicted(tree, qp, o.predictor, o.precision, s, q);
-        else if (o.precision == 1)
-            ct::query_tc(tree, qp, s, q);
         else
-            ct::query_plain(tree, qp, s, q);
+            ct::query_multi(1, &tree, &qp, s, &q, o.precision, nullptr, nullptr);
         q.stats.kernel_launches = ct::g_launches;
         fill_csr(out, tree->n, q, s);
     });
@@ -179,6 +179,25 @@ ct_status eps_graph_query_batched(int32_t n_clouds, const ct_tree *const *trees,
     }
     return st;
 }
+
+ct_status ct_autotune(int32_t n_clouds, const ct_tree *const *trees, const double *eps, const ct_query_opts *opts,
+                      ct_stream stream, int32_t *choices) {
+    return guarded([&] {
+        if (n_clouds < 0) CT_FAIL(CT_EINVAL, "n_clouds must be >= 0");
+        if (n_clouds == 0) return;
+        if (!trees || !eps) CT_FAIL(CT_EINVAL, "trees and eps must not be NULL");
+        ct_query_opts o = opts ? *opts : default_query_opts();
+        std::vector<ct::QParams> qps((size_t)n_clouds);
+        for (int c = 0; c < n_clouds; ++c) {
+            validate_query(trees[c], eps[c], o);
+            check_device(trees[c]);
+            qps[c] = ct::make_qparams(trees[c], eps[c], o.include_self);
+        }
+        ct::autotune(n_clouds, trees, qps.data(), &o, (cudaStream_t)stream, choices);
+    });
+}
+
+void ct_autotune_reset(void) { ct::tune_reset(); }
 
 ct_status eps_graph_degrees_noalloc(const ct_tree *tree, double eps, int32_t include_self, int32_t *degrees,
                                     ct_stream stream) {

@@ -125,6 +125,8 @@ struct Views {
     int64_t rbase[kMaxClouds + 1];
     TreeView tv[kMaxClouds];
     QParams qp[kMaxClouds];
+    int16_t item_len[kMaxClouds];  // candidate blocks per work item
+    uint8_t use_tc[kMaxClouds];    // leaf kernel of the count pass: BF16 tiles (1) or FP32 tiles (0)
 };
 __device__ __forceinline__ int cloud_of_group(const Views &V, int gg) {
     int lo = 0, hi = V.nc;
@@ -1230,26 +1232,49 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
 }
 
 // Work items: every pool segment split into slices of at most kItem blocks.
-__global__ void k_item_counts(int nseg, const int32_t *__restrict__ seg_count, int32_t *__restrict__ icnt) {
+__global__ void k_item_counts(const __grid_constant__ Views V, int nseg, const int32_t *__restrict__ seg_group,
+                              const int32_t *__restrict__ seg_count, int32_t *__restrict__ icnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nseg) icnt[i] = (seg_count[i] + kItem - 1) / kItem;
+    if (i >= nseg) return;
+    const int len = V.item_len[cloud_of_group(V, seg_group[i])];
+    icnt[i] = (seg_count[i] + len - 1) / len;
 }
-__global__ void k_item_fill(int nseg, const int32_t *__restrict__ seg_group, const int64_t *__restrict__ seg_begin,
-                            const int32_t *__restrict__ seg_count, const int64_t *__restrict__ ioff,
-                            int32_t *__restrict__ ig, int64_t *__restrict__ ib, int64_t *__restrict__ ie,
-                            int32_t *__restrict__ nitems) {
+__global__ void k_item_fill(const __grid_constant__ Views V, int nseg, const int32_t *__restrict__ seg_group,
+                            const int64_t *__restrict__ seg_begin, const int32_t *__restrict__ seg_count,
+                            const int64_t *__restrict__ ioff, int32_t *__restrict__ ig, int64_t *__restrict__ ib,
+                            int64_t *__restrict__ ie, int32_t *__restrict__ nitems) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) *nitems = (int32_t)ioff[nseg];
     if (i >= nseg) return;
+    const int len = V.item_len[cloud_of_group(V, seg_group[i])];
     const int64_t a = seg_begin[i], b = a + seg_count[i];
     int64_t k = ioff[i];
-    for (int64_t c = a; c < b; c += kItem, ++k) {
+    for (int64_t c = a; c < b; c += len, ++k) {
         ig[k] = seg_group[i];
         ib[k] = c;
-        ie[k] = c + kItem < b ? c + kItem : b;
+        ie[k] = c + len < b ? c + len : b;
     }
 }
-// Every row received exactly its counted number of entries.
+// Splits the items between the two count kernels by their cloud's choice.
+__global__ void k_item_split(const __grid_constant__ Views V, Items all, int32_t *__restrict__ tg,
+                             int64_t *__restrict__ tb, int64_t *__restrict__ te, int32_t *__restrict__ tn,
+                             int32_t *__restrict__ fg, int64_t *__restrict__ fb, int64_t *__restrict__ fe,
+                             int32_t *__restrict__ fn) {
+    const int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= *all.count) return;
+    const int gg = all.group[it];
+    if (V.use_tc[cloud_of_group(V, gg)]) {
+        const int k = atomicAdd(tn, 1);
+        tg[k] = gg;
+        tb[k] = all.begin[it];
+        te[k] = all.end[it];
+    } else {
+        const int k = atomicAdd(fn, 1);
+        fg[k] = gg;
+        fb[k] = all.begin[it];
+        fe[k] = all.end[it];
+    }
+}
 __global__ void k_check_rows(int64_t n, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ rowcur,
                              int32_t *__restrict__ err) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2197,6 +2222,36 @@ void launch_traversal(const Views &V, int64_t G, int max_dp, int max_len, bool l
     CT_LAUNCH_CHECK();
 }
 
+// Leaf kernel and item length per cloud.  precision 0: FP32 tiles; 1: BF16
+// tiles where the rows allow (L2, at most 128 floats); 2: the autotuned
+// choice of the cloud's row-length class (a default until tuned).
+std::mutex g_tune_mu;
+LeafChoice g_tune[kDpClasses] = {{-1, kItem}, {-1, kItem}, {-1, kItem}, {-1, kItem}, {-1, kItem}, {-1, kItem}};
+
+int dp_class(int dp) { return dp <= 4 ? 0 : dp <= 16 ? 1 : dp <= 32 ? 2 : dp <= 64 ? 3 : dp <= 128 ? 4 : 5; }
+
+LeafChoice tuned_choice(int dp) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    LeafChoice e = g_tune[dp_class(dp)];
+    if (e.use_tc < 0) e.use_tc = dp >= 32;
+    return e;
+}
+void tune_set(int cls, LeafChoice c) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[cls] = c;
+}
+void tune_reset() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &e : g_tune) e = LeafChoice{-1, kItem};
+}
+LeafChoice leaf_choice(const ct_tree *t, int precision) {
+    if (t->metric != CT_L2_F32 || t->dp > 128 || precision == 0) return LeafChoice{0, kItem};
+    if (precision == 1) return LeafChoice{1, kItem};
+    LeafChoice c = tuned_choice(t->dp);
+    if (c.item_len < 32 || c.item_len > kItem) c.item_len = kItem;
+    return c;
+}
+
 // Global walk order of several clouds: groups by decreasing radius relative
 // to their cloud's eps.
 __global__ void k_radius_keys(int G, const float *__restrict__ group_radius, float inv_eps, int gbase,
@@ -2222,12 +2277,19 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     Views V;
     std::memset(&V, 0, sizeof(V));
     V.nc = C;
-    int max_dp = 4, max_depth = 0, max_len = 0;
+    int max_dp = 4, max_depth = 0, max_len = 0, min_len = kItem;
+    bool any_tc = false, any_fp = false;
     for (int c = 0; c < C; ++c) {
         const ct_tree *tc = trees[c];
         if ((tc->metric == CT_L2_F32) != l2) CT_FAIL(CT_EINVAL, "a batch mixes metrics");
         V.tv[c] = view_of(tc);
         V.qp[c] = qps[c];
+        const LeafChoice ch = leaf_choice(tc, precision);
+        V.use_tc[c] = (uint8_t)ch.use_tc;
+        V.item_len[c] = (int16_t)ch.item_len;
+        any_tc |= ch.use_tc != 0;
+        any_fp |= ch.use_tc == 0;
+        min_len = std::min(min_len, ch.item_len);
         V.gbase[c + 1] = V.gbase[c] + tc->n_groups;
         V.rbase[c + 1] = V.rbase[c] + tc->n;
         max_dp = std::max(max_dp, tc->dp);
@@ -2307,17 +2369,17 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     const int nseg = (int)(uint32_t)hc[1];
     const int64_t pool_used = (int64_t)hc[0] < pool_cap ? (int64_t)hc[0] : pool_cap;
     DBuf<uint32_t> emask(l2 ? (pool_used ? pool_used : 1) : 0, s);
-    // work items: pool segments in slices of at most kItem candidate blocks
-    const int64_t max_items = nseg + n_cand / kItem + 1;
+    // work items: pool segments in slices of the clouds' item lengths
+    const int64_t max_items = nseg + n_cand / min_len + 1;
     DBuf<int32_t> icnt(nseg + 1, s), igroup(max_items, s), nitems(1, s);
     DBuf<int64_t> ioff(nseg + 1, s), ibeg(max_items, s), iend(max_items, s);
     Items items{igroup.p, ibeg.p, iend.p, nitems.p};
     CT_CHECK_CUDA(cudaMemsetAsync(nitems.p, 0, sizeof(int32_t), s));
     if (nseg) {
-        k_item_counts<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_count.p, icnt.p);
+        k_item_counts<<<grid_for(nseg, 256), 256, 0, s>>>(V, nseg, seg_group.p, seg_count.p, icnt.p);
         CT_COUNT_LAUNCH();
         exclusive_scan_i32_to_i64(icnt.p, ioff.p, nseg, ioff.p + nseg, s);
-        k_item_fill<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_group.p, seg_begin.p, seg_count.p, ioff.p,
+        k_item_fill<<<grid_for(nseg, 256), 256, 0, s>>>(V, nseg, seg_group.p, seg_begin.p, seg_count.p, ioff.p,
                                                        igroup.p, ibeg.p, iend.p, nitems.p);
         CT_COUNT_LAUNCH();
         CT_LAUNCH_CHECK();
@@ -2383,7 +2445,8 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     // 2. count pass
     DBuf<int32_t> deg(n + 1, s);
     CT_CHECK_CUDA(cudaMemsetAsync(deg.p, 0, (n + 1) * sizeof(int32_t), s));
-    auto leaf = [&](bool emit, int64_t *row_ptr, int32_t *col, float *dist, const uint8_t *rowsel) {
+    auto leaf = [&](bool emit, int64_t *row_ptr, int32_t *col, float *dist, const uint8_t *rowsel,
+                    const Items &items) {
         if (G == 0 || nseg == 0) return;
         const CapOut cw = emit ? CapOut{} : co;
         if (l2) {
@@ -2412,8 +2475,10 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     };
     // the tensor-core filter applies to L2 rows of at most 128 floats; wider
     // rows use the FP32 tiles (same output)
-    const bool use_tc = precision == 1 && l2 && max_dp <= 128;
-    if (use_tc) {
+    // each cloud's count kernel: BF16 tensor-core tiles (L2 rows of at most
+    // 128 floats) or FP32 tiles -- the same output; a mixed batch splits its
+    // work items between the two launches
+    auto count_tc = [&](const Items &its) {
         ProfScope ps("leaf_count_tc", s);
         static bool tc_ready = false;
         if (!tc_ready) {
@@ -2421,13 +2486,29 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
             tc_ready = true;
         }
         if (G && nseg) {
-            k_leaf_tc<<<(unsigned)max_items, TC_T, kTcSmem, s>>>(V, items, cand_p, emask.p, deg.p, st.p, err, co);
+            k_leaf_tc<<<(unsigned)max_items, TC_T, kTcSmem, s>>>(V, its, cand_p, emask.p, deg.p, st.p, err, co);
             CT_COUNT_LAUNCH();
             CT_LAUNCH_CHECK();
         }
-    } else {
+    };
+    if (!l2 || !any_tc) {
         ProfScope ps("leaf_count", s);
-        leaf(false, nullptr, nullptr, nullptr, nullptr);
+        leaf(false, nullptr, nullptr, nullptr, nullptr, items);
+    } else if (!any_fp) {
+        count_tc(items);
+    } else {
+        DBuf<int32_t> tg(max_items, s), fg(max_items, s), cnt2(2, s);
+        DBuf<int64_t> tb(max_items, s), te(max_items, s), fb(max_items, s), fe(max_items, s);
+        CT_CHECK_CUDA(cudaMemsetAsync(cnt2.p, 0, 2 * sizeof(int32_t), s));
+        if (nseg) {
+            k_item_split<<<grid_for(max_items, 256), 256, 0, s>>>(V, items, tg.p, tb.p, te.p, cnt2.p, fg.p, fb.p, fe.p,
+                                                                   cnt2.p + 1);
+            CT_COUNT_LAUNCH();
+            CT_LAUNCH_CHECK();
+        }
+        count_tc(Items{tg.p, tb.p, te.p, cnt2.p});
+        ProfScope ps("leaf_count", s);
+        leaf(false, nullptr, nullptr, nullptr, nullptr, Items{fg.p, fb.p, fe.p, cnt2.p + 1});
     }
 
     auto finish_stats = [&]() {
@@ -2490,14 +2571,14 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
         if (hv[2]) {
             ProfScope ps("reemit", s);
             CT_CHECK_CUDA(cudaMemsetAsync(rowcur.p, 0, (n + 1) * sizeof(int32_t), s));
-            leaf(true, row_ptr, all.col, all.dist, lost.p);
+            leaf(true, row_ptr, all.col, all.dist, lost.p, items);
             k_check_rows_sel<<<grid_for(n, 256), 256, 0, s>>>(n, row_ptr, rowcur.p, lost.p, err);
             CT_COUNT_LAUNCH();
         }
     } else if (nnz) {
         ProfScope ps("leaf_emit", s);
         CT_CHECK_CUDA(cudaMemsetAsync(rowcur.p, 0, (n + 1) * sizeof(int32_t), s));
-        leaf(true, row_ptr, all.col, all.dist, nullptr);
+        leaf(true, row_ptr, all.col, all.dist, nullptr, items);
         k_check_rows<<<grid_for(n, 256), 256, 0, s>>>(n, row_ptr, rowcur.p, err);
         CT_COUNT_LAUNCH();
     }
@@ -2633,6 +2714,7 @@ void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cuda
     V.qp[0] = qp;
     V.gbase[1] = t->n_groups;
     V.rbase[1] = n;
+    V.item_len[0] = kItem;
     int32_t *err = reinterpret_cast<int32_t *>(st + ST_ERR);
     // the array keeps the previous call's contents: clear what must start at zero
     CT_CHECK_CUDA(cudaMemsetAsync(st, 0, ST_N * sizeof(unsigned long long), s));
@@ -2665,10 +2747,10 @@ void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cuda
     CT_CHECK_CUDA(cudaMemsetAsync(degrees, 0, (size_t)n * sizeof(int32_t), s));
     CT_CHECK_CUDA(cudaMemsetAsync(nitems, 0, sizeof(int32_t), s));
     if (nseg) {
-        k_item_counts<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_count, icnt);
+        k_item_counts<<<grid_for(nseg, 256), 256, 0, s>>>(V, nseg, seg_group, seg_count, icnt);
         CT_COUNT_LAUNCH();
         exclusive_scan_i32_to_i64_into(icnt, ioff, nseg, ioff + nseg, sums, s);
-        k_item_fill<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_group, seg_begin, seg_count, ioff, igroup, ibeg,
+        k_item_fill<<<grid_for(nseg, 256), 256, 0, s>>>(V, nseg, seg_group, seg_begin, seg_count, ioff, igroup, ibeg,
                                                        iend, nitems);
         CT_COUNT_LAUNCH();
         Items items{igroup, ibeg, iend, nitems};

@@ -76,6 +76,18 @@ struct LearnedPlan {
 void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStream_t s, QueryOut *outs,
                  int precision, const ct_predictor *P, Probe *probe);
 constexpr int kBatchClouds = 64;
+// Count-pass kernel (1: BF16 tensor-core tiles, 0: FP32 tiles) and work-item
+// length of a cloud; autotuned per class of row length (dp <= 4, 16, 32, 64,
+// 128, wider).
+struct LeafChoice {
+    int use_tc;
+    int item_len;
+};
+constexpr int kDpClasses = 6;
+int dp_class(int dp);
+LeafChoice leaf_choice(const ct_tree *t, int precision);
+void tune_set(int cls, LeafChoice c);
+void tune_reset();
 void learned_plan(const ct_predictor *P, int C, const ct_tree *const *trees, const QParams *qps,
                   const int64_t *rbase, const int32_t *gbase, cudaStream_t s, LearnedPlan &lp);
 

@@ -42,4 +42,67 @@ void query_batched(int n_clouds, const ct_tree *const *trees, const QParams *qps
     }
 }
 
+namespace {
+void release(QueryOut &q, cudaStream_t s) {
+    if (!q.shared) {
+        dfree(q.row_ptr, s);
+        dfree(q.col, s);
+        dfree(q.dist, s);
+    }
+    q = QueryOut();
+}
+}  // namespace
+
+// Autotuner: for every row-length class present among the L2 clouds, times
+// the whole batched query of that class's clouds with each candidate (count
+// kernel x work-item length) and keeps the fastest for precision 2.
+void autotune(int n_clouds, const ct_tree *const *trees, const QParams *qps, const ct_query_opts *opts,
+              cudaStream_t s, int32_t *choices) {
+    static const LeafChoice cands[] = {{0, 512}, {0, 256}, {1, 512}, {1, 256}};
+    ct_query_opts o = *opts;
+    o.precision = 2;
+    cudaEvent_t e0, e1;
+    CT_CHECK_CUDA(cudaEventCreate(&e0));
+    CT_CHECK_CUDA(cudaEventCreate(&e1));
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } ev{e0, e1};
+    for (int cls = 0; cls < kDpClasses; ++cls) {
+        std::vector<const ct_tree *> ts;
+        std::vector<QParams> qs;
+        for (int c = 0; c < n_clouds; ++c)
+            if (trees[c]->metric == CT_L2_F32 && trees[c]->dp <= 128 && dp_class(trees[c]->dp) == cls) {
+                ts.push_back(trees[c]);
+                qs.push_back(qps[c]);
+            }
+        if (ts.empty()) continue;
+        float best = 1e30f;
+        LeafChoice pick = cands[0];
+        for (const LeafChoice &cd : cands) {
+            tune_set(cls, cd);
+            std::vector<QueryOut> outs(ts.size());
+            for (int rep = 0; rep < 2; ++rep) {  // the first run warms up
+                CT_CHECK_CUDA(cudaEventRecord(ev.a, s));
+                query_batched((int)ts.size(), ts.data(), qs.data(), &o, s, outs.data());
+                CT_CHECK_CUDA(cudaEventRecord(ev.b, s));
+                for (auto &q : outs) release(q, s);
+            }
+            CT_CHECK_CUDA(cudaEventSynchronize(ev.b));
+            float ms = 0.f;
+            CT_CHECK_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
+            if (ms < best) {
+                best = ms;
+                pick = cd;
+            }
+        }
+        tune_set(cls, pick);
+    }
+    if (choices)
+        for (int c = 0; c < n_clouds; ++c) choices[c] = leaf_choice(trees[c], 2).use_tc;
+}
+
 }  // namespace ct

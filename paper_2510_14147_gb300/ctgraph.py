@@ -120,6 +120,11 @@ def _load():
         lib.ct_selftest_tc_gemm.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.ct_kernel_launches.restype = C.c_int64
         lib.ct_kernel_launches.argtypes = []
+        lib.ct_autotune.restype = C.c_int
+        lib.ct_autotune.argtypes = [C.c_int32, P(C.c_void_p), P(C.c_double), P(ct_query_opts), C.c_void_p,
+                                    C.c_void_p]
+        lib.ct_autotune_reset.restype = None
+        lib.ct_autotune_reset.argtypes = []
         lib.ct_predictor_create.restype = C.c_int
         lib.ct_predictor_create.argtypes = [C.c_uint64, P(C.c_void_p)]
         lib.ct_predictor_free.restype = None
@@ -324,6 +329,23 @@ def eps_graph_query_batched(trees, eps, precision: int = 0, use_predictor: bool 
     o = _opts(precision, use_predictor, include_self, predictor)
     _check(lib.eps_graph_query_batched(k, arr, ea, C.byref(o), C.c_void_p(_stream(stream)), outs))
     return [CSR(outs[i]) for i in range(k)]
+
+
+def ct_autotune(trees, eps, use_predictor: bool = False, include_self: bool = False, predictor=None,
+                stream=None):
+    """Tunes precision 2 on these clouds; returns each cloud's count kernel
+    (1: BF16 tensor-core tiles, 0: FP32 tiles)."""
+    k = len(trees)
+    arr = (C.c_void_p * max(k, 1))(*[t.handle.value for t in trees])
+    ea = (C.c_double * max(k, 1))(*[float(e) for e in eps])
+    ch = np.zeros(max(k, 1), np.int32)
+    o = _opts(2, use_predictor, include_self, predictor)
+    _check(_load().ct_autotune(k, arr, ea, C.byref(o), C.c_void_p(_stream(stream)), ch.ctypes.data))
+    return [int(v) for v in ch[:k]]
+
+
+def ct_autotune_reset():
+    _load().ct_autotune_reset()
 
 
 def eps_graph_degrees_noalloc(tree: Tree, eps: float, degrees, include_self: bool = False, stream=None):

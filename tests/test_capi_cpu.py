@@ -62,6 +62,9 @@ def test_invalid_arguments_without_gpu():
     lib.ct_tree_free(None)
     assert lib.eps_graph_query_batched(-1, None, None, None, None, None) == cg.CT_EINVAL
     assert lib.eps_graph_query_batched(0, None, None, None, None, None) == cg.CT_OK
+    assert lib.ct_autotune(-1, None, None, None, None, None) == cg.CT_EINVAL
+    assert lib.ct_autotune(0, None, None, None, None, None) == cg.CT_OK
+    lib.ct_autotune_reset()
     st = cg.ct_query_stats()
     assert lib.ct_csr_stats(C.byref(csr), C.byref(st)) == cg.CT_EINVAL
     # predictor entry points

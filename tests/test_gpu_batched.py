@@ -166,3 +166,28 @@ def test_many_cloud_workload_sample():
         o.free()
     for t in trees:
         t.free()
+
+
+def test_autotuned_precision_keeps_the_output():
+    """precision 2 before and after tuning, on a batch spanning four row-length
+    classes, equals precision 0 cloud by cloud."""
+    cg = _cg()
+    cg.ct_autotune_reset()
+    xs, eps = _clouds(3)
+    trees = [_tree(points=x, leaf_size=16) for x in xs]
+    ref = [o.to_numpy() for o in cg.eps_graph_query_batched(trees, eps, precision=0)]
+    before = cg.eps_graph_query_batched(trees, eps, precision=2)
+    choices = cg.ct_autotune(trees, eps)
+    assert len(choices) == len(trees) and set(choices) <= {0, 1}
+    after = cg.eps_graph_query_batched(trees, eps, precision=2)
+    for r, a, b in zip(ref, before, after):
+        for out in (a.to_numpy(), b.to_numpy()):
+            for k in ("row_ptr", "col", "dist"):
+                assert np.array_equal(out[k], r[k]), k
+    for o in before + after:
+        o.free()
+    single = cg.eps_graph_query(trees[0], eps[0], precision=2).to_numpy()
+    assert np.array_equal(single["col"], ref[0]["col"])
+    cg.ct_autotune_reset()
+    for t in trees:
+        t.free()
