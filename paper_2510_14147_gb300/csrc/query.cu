@@ -283,14 +283,17 @@ __device__ __forceinline__ void group_visits(int32_t *gvisit, int g, unsigned lo
 template <int TPD>
 __device__ __forceinline__ bool l2_keep(const TreeView &tv, const float4 *cen, int nq4, int first, int take,
                                         float add) {
-    constexpr int NPR = 32 / TPD;
+    constexpr int NPR = 32 / TPD;  // vertices per round; TPD rounds cover a step of 32
     const int lane = threadIdx.x & 31, sub = lane / TPD, j = lane % TPD;
-    float mine = 0.f;
-    for (int r0 = 0; r0 < take; r0 += NPR) {
-        const int i = r0 + sub;
+    // all rounds' partial sums first (their loads overlap), then the reductions
+    float part[TPD];
+#pragma unroll
+    for (int u = 0; u < TPD; ++u) {
+        const int i = u * NPR + sub;
         float acc = 0.f;
-        if (i < take) {
+        if (u * NPR < take && i < take) {
             const float4 *row = reinterpret_cast<const float4 *>(tv.node_ctr) + (size_t)(first + i) * nq4;
+#pragma unroll 4
             for (int k = j; k < nq4; k += TPD) {
                 const float4 a = cen[k], b = __ldg(row + k);
                 const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
@@ -300,8 +303,16 @@ __device__ __forceinline__ bool l2_keep(const TreeView &tv, const float4 *cen, i
                 acc = fmaf(dw, dw, acc);
             }
         }
+        part[u] = acc;
+    }
+    float mine = 0.f;
+#pragma unroll
+    for (int u = 0; u < TPD; ++u) {
+        if (u * NPR >= take) break;  // warp-uniform
+        float acc = part[u];
 #pragma unroll
         for (int o = TPD / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const int r0 = u * NPR;
         const int src = ((lane - r0) & (NPR - 1)) * TPD;
         const float v = __shfl_sync(0xffffffffu, acc, src);
         if (lane >= r0 && lane < r0 + NPR) mine = v;
