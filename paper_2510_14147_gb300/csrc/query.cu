@@ -1365,7 +1365,9 @@ __global__ void k_ovf_scatter(int64_t used, const int32_t *__restrict__ orow, co
 //   sums, |d^2 - ||x^ - y^||^2| <= 2^-12 (|x~|^2 + |y~|^2) (sums of 128 terms
 //   with a few ulps per addition, generously).
 // A pair is kept iff d^2 <= (eps + 2^-8 (|x~| + |y~|))^2 + 2^-12 (|x~|^2 + |y~|^2),
-// which keeps every edge.  Kept pairs are decided like the FP32 path: the
+// which keeps every edge; the kernel uses upper bounds of |x~| and |y~| taken
+// from the bf16 norms (TC_NORM_UP), which only widen the test.  Kept pairs are
+// decided like the FP32 path: the
 // canonical fp32 direct-difference sum (decide32), the pinned FP64 sum where
 // that cannot decide.
 // The emit pass is the FP32 path's, driven by the same per-block edge masks.
@@ -1382,6 +1384,9 @@ constexpr int TC_T = 256;           // threads per CTA
 constexpr int TC_NB = kItem;        // candidate blocks of one item
 constexpr int TC_RS4 = 33;          // fp32 row stride in float4 (odd: conflict-free row-per-thread reads)
 constexpr float TC_REL = 0x1p-8f, TC_ABS2 = 0x1p-12f;
+// |x~| <= |x^| / (1 - 2^-9) and the fp32 sum of the bf16 squares loses at
+// most 2^-18 of |x^|^2: sqrt of that sum times 1 + 2^-7 bounds |x~|
+constexpr float TC_NORM_UP = 1.0f + 0x1p-7f;
 constexpr uint32_t TC_WAIT = 1u << 22;  // mbarrier polls before a wait gives up
 constexpr int TC_EB = 1024;             // edge buffer entries (one-pass emit)
 
@@ -1392,7 +1397,7 @@ struct __align__(1024) TcShared {
     float4 Qf[32 * TC_RS4];          // fp32 query rows
     float4 cen[32];                  // group centre
     float qn2[32], qabs[32];
-    float pn2[2][TC_ROWS], pa2[2][TC_ROWS];  // per half row: bf16 and fp32 squared norms
+    float pn2[2][TC_ROWS];           // per half row: squared norm of the bf16 values
     int rpos[2][TC_ROWS];
     uint16_t rli[2][TC_ROWS];
     int npos[TC_ROWS];               // mapping of the tile being prepared
@@ -1419,11 +1424,11 @@ static_assert(TC_NB == 2 * TC_T, "block prefix assumes two candidate blocks per 
 
 // Converts float4 columns [k0, k1) of one row (fp32, shared memory; columns
 // at or past dp4 and rows that are not valid give zeros) to centred bf16 in
-// the core-matrix layout; returns the partial squared norms of the bf16 and
-// the fp32 centred values.  k0 and k1 are even, k1 - k0 <= 16.  All loads
-// are issued before the first store.
+// the core-matrix layout; returns the partial squared norm of the bf16
+// values.  k0 and k1 are even, k1 - k0 <= 16.  All loads are issued before
+// the first store.
 __device__ __forceinline__ void tc_convert_part(unsigned char *tile, int r, const float4 *row, const float4 *cen,
-                                                int k0, int k1, int dp4, bool valid, float &n2, float &a2) {
+                                                int k0, int k1, int dp4, bool valid, float &n2) {
     float4 v[16];
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
@@ -1434,8 +1439,8 @@ __device__ __forceinline__ void tc_convert_part(unsigned char *tile, int r, cons
             v[u] = make_float4(x.x - c.x, x.y - c.y, x.z - c.z, x.w - c.w);
         }
     }
-    // norms in packed pairs (f32x2): two partial sums each, added at the end
-    unsigned long long bn = 0ull, an = 0ull;
+    // norm in packed pairs (f32x2): two partial sums, added at the end
+    unsigned long long bn = 0ull;
 #pragma unroll
     for (int u = 0; u < 16; u += 2) {
         const int k = k0 + u;
@@ -1455,13 +1460,8 @@ __device__ __forceinline__ void tc_convert_part(unsigned char *tile, int r, cons
         bn = f2_sqacc(f2_pack(f23.x, f23.y), bn);
         bn = f2_sqacc(f2_pack(f45.x, f45.y), bn);
         bn = f2_sqacc(f2_pack(f67.x, f67.y), bn);
-        an = f2_sqacc(f2_pack(v0.x, v0.y), an);
-        an = f2_sqacc(f2_pack(v0.z, v0.w), an);
-        an = f2_sqacc(f2_pack(v1.x, v1.y), an);
-        an = f2_sqacc(f2_pack(v1.z, v1.w), an);
     }
     n2 = f2_sum(bn);
-    a2 = f2_sum(an);
 }
 
 __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Views V, Items items,
@@ -1543,6 +1543,8 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Vie
     tc::fence_after_sync();
     const uint32_t tmem = S.tslot;
     const uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, 32);
+    const uint64_t adesc0 = tc::smem_desc(tc::smem_u32(S.A), tc::kLBO, tc::kSBO);
+    const uint64_t bdesc0 = tc::smem_desc(tc::smem_u32(S.B), tc::kLBO, tc::kSBO);
     const int T = S.bpre[TC_NB];
     const int ntiles = (T + TC_ROWS - 1) / TC_ROWS;
 
@@ -1602,15 +1604,14 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Vie
         __syncthreads();
         if (tid < 64) {
             const int q = tid & 31, half = tid >> 5;
-            float n2, a2;
-            tc_convert_part(S.B, q, S.Qf + q * TC_RS4, S.cen, half ? kh : 0, half ? K4 : kh, dp4, q < nqr, n2, a2);
+            float n2;
+            tc_convert_part(S.B, q, S.Qf + q * TC_RS4, S.cen, half ? kh : 0, half ? K4 : kh, dp4, q < nqr, n2);
             S.pn2[half][q] = n2;
-            S.pa2[half][q] = a2;
         }
         __syncthreads();
         if (tid < 32) {
             S.qn2[tid] = S.pn2[0][tid] + S.pn2[1][tid];
-            S.qabs[tid] = sqrtf(S.pa2[0][tid] + S.pa2[1][tid]);
+            S.qabs[tid] = sqrtf(S.qn2[tid]) * TC_NORM_UP;
         }
 
         // one-pass emit: reserves each query's slots once and writes the
@@ -1644,22 +1645,19 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Vie
             // bf16 tile from the staged rows (two threads per row)
             {
                 const int r = tid & (TC_ROWS - 1), half = tid >> 7;
-                float n2, a2;
+                float n2;
                 tc_convert_part(S.A, r, S.P[sg] + r * TC_RS4, S.cen, half ? kh : 0, half ? K4 : kh, dp4, r < rows,
-                                n2, a2);
+                                n2);
                 S.pn2[half][r] = n2;
-                S.pa2[half][r] = a2;
             }
             tc::fence_smem_to_async();
             tc::fence_before_sync();
             __syncthreads();
             tc::fence_after_sync();
             if (tid == 0) {
-                for (int ks = 0; ks < ksteps; ++ks) {
-                    const uint64_t ad = tc::smem_desc(tc::smem_u32(S.A) + ks * 256, tc::kLBO, tc::kSBO);
-                    const uint64_t bd = tc::smem_desc(tc::smem_u32(S.B) + ks * 256, tc::kLBO, tc::kSBO);
-                    tc::mma_bf16(tmem, ad, bd, idesc, ks > 0);
-                }
+                // one K step is 256 bytes further along both tiles (address field in 16-byte units)
+                for (int ks = 0; ks < ksteps; ++ks)
+                    tc::mma_bf16(tmem, adesc0 + (uint64_t)(ks * 16), bdesc0 + (uint64_t)(ks * 16), idesc, ks > 0);
                 tc::mma_commit(&S.mma);
             }
             mma_out = true;
@@ -1684,7 +1682,7 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Vie
                 if (r < rows) {
                     const int ppos = S.rpos[sg][r];
                     const float pn = S.pn2[0][r] + S.pn2[1][r];
-                    const float pa = sqrtf(S.pa2[0][r] + S.pa2[1][r]);
+                    const float pa = sqrtf(pn) * TC_NORM_UP;
                     uint32_t validm = 0u;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
