@@ -1969,15 +1969,66 @@ __global__ void k_alphabet(const uint8_t *__restrict__ s, int64_t nbytes, int32_
 
 constexpr int SORT_MID = 4096;  // rows up to this length are sorted in one CTA
 
+// Row classes by length: 0 <= 32, 1 <= 128, 2 <= 512, 3 <= 1024, 4 <= SORT_MID, 5 longer.
+constexpr int kSortClasses = 6;
 __global__ void k_row_classes(const int64_t *__restrict__ row_ptr, int64_t n, int32_t *__restrict__ lists,
                               int32_t *__restrict__ counts) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t len = row_ptr[i + 1] - row_ptr[i];
-    int cls = len <= 1 ? -1 : len <= 32 ? 0 : len <= SORT_MID ? 1 : 2;
+    int cls = len <= 1 ? -1 : len <= 32 ? 0 : len <= 128 ? 1 : len <= 512 ? 2 : len <= 1024 ? 3
+                                                              : len <= SORT_MID ? 4 : 5;
     if (cls < 0) return;
     int slot = atomicAdd(&counts[cls], 1);
     lists[(int64_t)cls * n + slot] = (int32_t)i;
+}
+
+// CTA of P threads per row (P a power of two, rows of at most P entries):
+// bitonic network with one element per thread; strides below 32 exchange by
+// shuffles, wider strides through shared memory.
+template <int P>
+__global__ void __launch_bounds__(P) k_sort_pow2(const int32_t *__restrict__ rows, const int32_t *__restrict__ count,
+                                                 const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col,
+                                                 float *__restrict__ dist) {
+    __shared__ int sk[P];
+    __shared__ float sv[P];
+    const int i = threadIdx.x;
+    for (int w = blockIdx.x; w < *count; w += gridDim.x) {
+        const int r = rows[w];
+        const int64_t b = row_ptr[r];
+        const int len = (int)(row_ptr[r + 1] - b);
+        int key = i < len ? col[b + i] : INT_MAX;
+        float val = i < len ? dist[b + i] : 0.f;
+#pragma unroll
+        for (int k = 2; k <= P; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                int ok;
+                float ov;
+                if (j >= 32) {
+                    __syncthreads();
+                    sk[i] = key;
+                    sv[i] = val;
+                    __syncthreads();
+                    ok = sk[i ^ j];
+                    ov = sv[i ^ j];
+                } else {
+                    ok = __shfl_xor_sync(0xffffffffu, key, j);
+                    ov = __shfl_xor_sync(0xffffffffu, val, j);
+                }
+                const bool up = (i & k) == 0, lower = (i & j) == 0;
+                const bool swap = (lower == up) ? (ok < key) : (ok > key);
+                if (swap) {
+                    key = ok;
+                    val = ov;
+                }
+            }
+        }
+        if (i < len) {
+            col[b + i] = key;
+            dist[b + i] = val;
+        }
+    }
 }
 
 // Warp per row, <= 32 entries: bitonic network across lanes.
@@ -2008,7 +2059,7 @@ __global__ void k_sort_small(const int32_t *__restrict__ rows, const int32_t *__
     }
 }
 
-// CTA per row, 33..SORT_MID entries: bitonic sort in shared memory.
+// CTA per row, 1025..SORT_MID entries: bitonic sort in shared memory.
 __global__ void __launch_bounds__(512) k_sort_mid(const int32_t *__restrict__ rows, const int32_t *__restrict__ count,
                                                   const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col,
                                                   float *__restrict__ dist) {
@@ -2089,24 +2140,33 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)ceil_div(n > 0 ? n
 
 void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int64_t nnz, cudaStream_t s) {
     if (n <= 0 || nnz <= 0) return;
-    DBuf<int32_t> lists(3 * n, s), counts(3, s);
-    CT_CHECK_CUDA(cudaMemsetAsync(counts.p, 0, 3 * sizeof(int32_t), s));
+    DBuf<int32_t> lists(kSortClasses * n, s), counts(kSortClasses, s);
+    CT_CHECK_CUDA(cudaMemsetAsync(counts.p, 0, kSortClasses * sizeof(int32_t), s));
     k_row_classes<<<grid_for(n, 256), 256, 0, s>>>(row_ptr, n, lists.p, counts.p);
     CT_COUNT_LAUNCH();
-    int32_t hc[3];
-    to_host(hc, counts.p, 3, s);
+    int32_t hc[kSortClasses];
+    to_host(hc, counts.p, kSortClasses, s);
     if (hc[0]) {
         k_sort_small<<<grid_for((int64_t)hc[0] * 32, 256), 256, 0, s>>>(lists.p, counts.p, row_ptr, col, dist);
         CT_COUNT_LAUNCH();
     }
-    if (hc[1]) {
-        int blocks = (int)std::min<int64_t>(hc[1], (int64_t)num_sms() * 8);
-        k_sort_mid<<<blocks, 512, 0, s>>>(lists.p + n, counts.p + 1, row_ptr, col, dist);
+    auto pow2 = [&](int cls, auto kern, int P) {
+        if (!hc[cls]) return;
+        const int blocks = (int)std::min<int64_t>(hc[cls], (int64_t)num_sms() * (2048 / P));
+        kern<<<blocks, P, 0, s>>>(lists.p + (int64_t)cls * n, counts.p + cls, row_ptr, col, dist);
+        CT_COUNT_LAUNCH();
+    };
+    pow2(1, k_sort_pow2<128>, 128);
+    pow2(2, k_sort_pow2<512>, 512);
+    pow2(3, k_sort_pow2<1024>, 1024);
+    if (hc[4]) {
+        int blocks = (int)std::min<int64_t>(hc[4], (int64_t)num_sms() * 8);
+        k_sort_mid<<<blocks, 512, 0, s>>>(lists.p + 4 * n, counts.p + 4, row_ptr, col, dist);
         CT_COUNT_LAUNCH();
     }
-    if (hc[2]) {
-        int nb = hc[2];
-        const int32_t *big = lists.p + 2 * n;
+    if (hc[5]) {
+        int nb = hc[5];
+        const int32_t *big = lists.p + 5 * n;
         DBuf<int64_t> lens(nb, s), off(nb, s), tot(1, s);
         k_big_lengths<<<grid_for(nb, 256), 256, 0, s>>>(big, nb, row_ptr, lens.p);
         CT_COUNT_LAUNCH();

@@ -104,6 +104,24 @@ def test_eps_zero_with_tiny_coordinates():
         assert_csr_matches(out, oracle.brute_force(sp, 0.0))
 
 
+def test_row_lengths_in_every_sort_class():
+    """Tight clusters of 20..5000 points give rows of every length class of
+    the row sort (<= 32, 128, 512, 1024, 4096, longer)."""
+    rng = np.random.default_rng(12)
+    parts = []
+    for k, size in enumerate((20, 100, 400, 900, 3000, 5000)):
+        centre = rng.random(4) * 100.0
+        parts.append(centre + rng.random((size, 4)) * 0.1)
+    x = np.concatenate(parts).astype(np.float32)
+    x = x[rng.permutation(x.shape[0])]
+    sp = oracle.Space(points=x)
+    for precision in (0, 1):
+        out = gpu_graph(points=x, eps=0.5, precision=precision)
+        assert_csr_matches(out, oracle.brute_force(sp, 0.5))
+        deg = np.diff(out["row_ptr"])
+        assert sorted(set(deg.tolist())) == [19, 99, 399, 899, 2999, 4999]
+
+
 def test_complete_graph_and_include_self():
     x = I.uniform_cube(700, 4, seed=1)
     sp = oracle.Space(points=x)
