@@ -56,6 +56,8 @@ __device__ __forceinline__ float round_radius_up(float r, int metric) {
 
 // ---- L2 distance of a point row to a centre row held in shared memory.
 // TPD threads cooperate on one distance; lane j reads float4s j, j+TPD, ...
+// The shuffles name only the TPD lanes of the caller's group, so groups of
+// one warp may take different branches around the call.
 template <int TPD>
 __device__ __forceinline__ float group_sqdist(const float4 *__restrict__ row, const float4 *cen,
                                               int nq, int j) {
@@ -69,8 +71,9 @@ __device__ __forceinline__ float group_sqdist(const float4 *__restrict__ row, co
         acc = fmaf(dz, dz, acc);
         acc = fmaf(dw, dw, acc);
     }
+    const unsigned mask = TPD == 32 ? 0xffffffffu : (((1u << TPD) - 1u) << ((threadIdx.x & 31) & ~(TPD - 1)));
 #pragma unroll
-    for (int o = TPD / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPD);
+    for (int o = TPD / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, TPD);
     return acc;
 }
 
@@ -80,17 +83,22 @@ struct Hubs {
     unsigned long long *key;
 };
 
+// Pruning (L2): a point labelled L cannot come closer to the new centre c
+// than D when d(c, centre L) >= 2 D (triangle inequality); such points keep D
+// and L without reading their row.  dcc[begin + L] = d(c, centre L) of the
+// hub (nullptr: no pruning).
 template <int TPD>
 __global__ void __launch_bounds__(BT) k_dist_update_l2(
     const float *__restrict__ X, int dp, const int32_t *__restrict__ ids, float *__restrict__ D,
     int32_t *__restrict__ lab, const int32_t *__restrict__ chunk_hub,
-    const int32_t *__restrict__ chunk_start, int chunk_len, Hubs hb) {
+    const int32_t *__restrict__ chunk_start, int chunk_len, Hubs hb, const float *__restrict__ dcc) {
     extern __shared__ float4 cen[];
     int c = blockIdx.x;
     int h = chunk_hub[c];
     if (hb.done[h]) return;
     int start = chunk_start[c];
-    int end = min(start + chunk_len, hb.begin[h] + hb.count[h]);
+    const int hbeg = hb.begin[h];
+    int end = min(start + chunk_len, hbeg + hb.count[h]);
     int cpos = hb.cur[h];
     int lbl = hb.nc[h] - 1;
     int nq = dp >> 2;
@@ -103,17 +111,21 @@ __global__ void __launch_bounds__(BT) k_dist_update_l2(
     for (int base = start; base < end; base += G) {
         int pos = base + g;
         bool valid = pos < end;
-        int row_id = valid ? ids[pos] : ids[start];
-        float s = group_sqdist<TPD>(reinterpret_cast<const float4 *>(X + (size_t)row_id * dp), cen,
-                                    nq, j);
-        if (valid && j == 0) {
-            float d = sqrtf(s);
-            float cur = D[pos];
-            if (d < cur) {
-                D[pos] = d;
-                lab[pos] = lbl;
-                cur = d;
+        float cur = valid ? D[pos] : 0.f;
+        bool far = !valid;
+        if (valid && dcc) far = dcc[hbeg + lab[pos]] >= 2.0f * cur * (1.0f + 0x1p-12f) + 0x1p-60f;
+        if (!far) {  // the same for the group's TPD lanes
+            float s = group_sqdist<TPD>(reinterpret_cast<const float4 *>(X + (size_t)ids[pos] * dp), cen, nq, j);
+            if (j == 0) {
+                float d = sqrtf(s);
+                if (d < cur) {
+                    D[pos] = d;
+                    lab[pos] = lbl;
+                    cur = d;
+                }
             }
+        }
+        if (valid && j == 0) {
             unsigned long long k = pack_max_key(cur, (uint32_t)pos);
             best = k > best ? k : best;
         }
@@ -170,8 +182,9 @@ __global__ void __launch_bounds__(BT) k_dist_update_lev(
     if ((threadIdx.x & 31) == 0 && best) atomicMax(&hb.key[h], best);
 }
 
-// One thread per hub: decide termination or choose the next centre.
-__global__ void k_hub_step(int nh, Hubs hb, int32_t *__restrict__ active_out) {
+// One thread per hub: decide termination or choose the next centre (its
+// position goes to cpos[begin + label] when cpos is given).
+__global__ void k_hub_step(int nh, Hubs hb, int32_t *__restrict__ active_out, int32_t *__restrict__ cpos) {
     int h = blockIdx.x * blockDim.x + threadIdx.x;
     int act = 0;
     if (h < nh && !hb.done[h]) {
@@ -181,6 +194,10 @@ __global__ void k_hub_step(int nh, Hubs hb, int32_t *__restrict__ active_out) {
             hb.done[h] = 1;
         } else {
             hb.cur[h] = (int32_t)key_pos(k);
+            if (cpos) {
+                cpos[hb.begin[h]] = hb.begin[h];  // label 0: the hub's own centre
+                cpos[hb.begin[h] + hb.nc[h]] = hb.cur[h];
+            }
             hb.nc[h] += 1;
             hb.key[h] = 0ull;
             act = 1;
@@ -188,6 +205,27 @@ __global__ void k_hub_step(int nh, Hubs hb, int32_t *__restrict__ active_out) {
     }
     unsigned b = __ballot_sync(0xffffffffu, act);
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(active_out, __popc(b));
+}
+
+// Per hub that took a new centre: its distance to each of the hub's centres
+// (TPD lanes per distance, warps over the labels).
+template <int TPD>
+__global__ void __launch_bounds__(BT) k_centre_dists(const float *__restrict__ X, int dp,
+                                                     const int32_t *__restrict__ ids, Hubs hb,
+                                                     const int32_t *__restrict__ cpos, float *__restrict__ dcc) {
+    const int h = blockIdx.x;
+    if (hb.done[h]) return;
+    const int b = hb.begin[h], nc = hb.nc[h], nq = dp >> 2;
+    const float4 *crow = reinterpret_cast<const float4 *>(X + (size_t)ids[hb.cur[h]] * dp);
+    constexpr int G = BT / TPD;
+    const int g = threadIdx.x / TPD, j = threadIdx.x % TPD;
+    for (int L0 = 0; L0 < nc; L0 += G) {  // every group runs the same number of steps
+        const int L = L0 + g;
+        const int pos = cpos[b + (L < nc ? L : 0)];
+        const float dd = sqrtf(group_sqdist<TPD>(reinterpret_cast<const float4 *>(X + (size_t)ids[pos] * dp), crow,
+                                                 nq, j));
+        if (L < nc && j == 0) dcc[b + L] = dd;
+    }
 }
 
 // Chunk table of a round: chunk -> (hub, first position).
@@ -588,12 +626,16 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
         // one pass of the update kernel with the root as the only centre
         const int tpd = l2 ? (dp >= 128 ? 32 : dp >= 64 ? 16 : dp >= 32 ? 8 : dp >= 16 ? 4 : dp >= 8 ? 2 : 1) : 1;
         const int chunk_len = l2 ? 32 * (BT / tpd) : 4 * BT;
+        // pruned updates (L2): centre positions and centre-to-new-centre distances per hub label
+        DBuf<int32_t> cpos(l2 ? n : 1, s);
+        DBuf<float> dcc(l2 ? n : 1, s);
+        bool prune = false;  // off for the root's first pass (no labels yet)
         auto update = [&](Hubs &hb, int64_t nchunks, const int32_t *chub, const int32_t *cst) {
             if (!nchunks) return;
             if (l2) {
                 size_t sm = (size_t)dp * sizeof(float);
                 switch (tpd) {
-#define CT_UPD(T) case T: k_dist_update_l2<T><<<(unsigned)nchunks, BT, sm, s>>>(Xp.p, dp, ids.p, D.p, lab.p, chub, cst, chunk_len, hb); break;
+#define CT_UPD(T) case T: k_dist_update_l2<T><<<(unsigned)nchunks, BT, sm, s>>>(Xp.p, dp, ids.p, D.p, lab.p, chub, cst, chunk_len, hb, prune ? dcc.p : nullptr); break;
                     CT_UPD(1) CT_UPD(2) CT_UPD(4) CT_UPD(8) CT_UPD(16) CT_UPD(32)
 #undef CT_UPD
                 }
@@ -677,8 +719,17 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
                     iters += burst;
                     CT_CHECK_CUDA(cudaMemsetAsync(active.p, 0, sizeof(int32_t), s));
                     for (int it = 0; it < burst; ++it) {
-                        k_hub_step<<<grid_for(nh), BT, 0, s>>>((int)nh, H, active.p);
+                        k_hub_step<<<grid_for(nh), BT, 0, s>>>((int)nh, H, active.p, l2 ? cpos.p : nullptr);
                         CT_COUNT_LAUNCH();
+                        if (l2) {
+                            switch (tpd) {
+#define CT_CD(T) case T: k_centre_dists<T><<<(unsigned)nh, BT, 0, s>>>(Xp.p, dp, ids.p, H, cpos.p, dcc.p); break;
+                                CT_CD(1) CT_CD(2) CT_CD(4) CT_CD(8) CT_CD(16) CT_CD(32)
+#undef CT_CD
+                            }
+                            CT_COUNT_LAUNCH();
+                            prune = true;
+                        }
                         update(H, nchunks, chub.p, cst.p);
                     }
                     int32_t act = 0;
