@@ -68,7 +68,13 @@ __device__ __forceinline__ int decide32(const QParams &qp, float sv, unsigned lo
 // nearest and never contracted.
 // Rows start on 16-byte boundaries (global or shared memory): the loads go
 // four floats at a time, the sum stays in ascending index order.
+template <bool INL>
+__device__ __forceinline__ double sq_l2_exact4_t(const float4 *x, const float4 *y, int dim);
 __device__ __noinline__ double sq_l2_exact4(const float4 *x, const float4 *y, int dim) {
+    return sq_l2_exact4_t<true>(x, y, dim);
+}
+template <bool INL>
+__device__ __forceinline__ double sq_l2_exact4_t(const float4 *x, const float4 *y, int dim) {
     double s = 0.0;
     const int n4 = dim >> 2;
 #pragma unroll 4
@@ -1372,94 +1378,122 @@ __global__ void k_ovf_scatter(int64_t used, const int32_t *__restrict__ orow, co
 // that cannot decide.
 // The emit pass is the FP32 path's, driven by the same per-block edge masks.
 //
-// Pipeline (one CTA of 8 warps per work item, one item's candidate blocks in
-// one batch): the fp32 rows of tile t + 1 are in flight -- 16-byte
-// asynchronous copies by all threads into a padded shared-memory stage --
-// while tile t is converted to bf16 from shared memory, multiplied, and
-// checked; the FP32 rechecks read both rows from shared memory.  (One bulk
-// copy per 512-byte row through the TMA engine was measured at about 12 SM
-// cycles per row, twice the time of the whole tile with these copies.)
+// Pipeline (one CTA of two 8-warp groups per work item, one item's candidate
+// blocks in one batch): the groups take alternate 128-row tiles, each with its
+// own fp32 stage, bf16 tile, 32 tensor-memory columns, MMA barrier, kept-pair
+// list and edge buffer, synchronised by its own named barrier, so that one
+// group's copies, conversion and MMA overlap the other's filter and rechecks.
+// A group's fp32 rows of tile t + 2 are copied (16-byte asynchronous copies)
+// into its stage as soon as tile t is converted; the FP32 rechecks read both
+// rows from global memory (L1/L2).  (One bulk copy per 512-byte row through
+// the TMA engine was measured at about 12 SM cycles per row, twice the time
+// of the whole tile with these copies.)
 constexpr int TC_ROWS = 128;
-constexpr int TC_T = 256;           // threads per CTA
+constexpr int TC_GT = 256;          // threads per group
+constexpr int TC_T = 2 * TC_GT;     // threads per CTA
 constexpr int TC_NB = kItem;        // candidate blocks of one item
-constexpr int TC_RS4 = 33;          // fp32 row stride in float4 (odd: conflict-free row-per-thread reads)
 constexpr float TC_REL = 0x1p-8f, TC_ABS2 = 0x1p-12f;
 // |x~| <= |x^| / (1 - 2^-9) and the fp32 sum of the bf16 squares loses at
 // most 2^-18 of |x^|^2: sqrt of that sum times 1 + 2^-7 bounds |x~|
 constexpr float TC_NORM_UP = 1.0f + 0x1p-7f;
 constexpr uint32_t TC_WAIT = 1u << 22;  // mbarrier polls before a wait gives up
-constexpr int TC_EB = 1024;             // edge buffer entries (one-pass emit)
+constexpr int TC_KL = 1024;             // kept pairs rechecked per round
+constexpr int TC_EB = 384;              // edge buffer entries per group (one-pass emit)
 
-struct __align__(1024) TcShared {
+struct __align__(128) TcGroup {
     unsigned char A[TC_ROWS * 256];  // bf16 candidate rows, core-matrix layout
-    unsigned char B[32 * 256];       // bf16 query rows
-    float4 P[2][TC_ROWS * TC_RS4];   // fp32 candidate rows, two stages
-    float4 Qf[32 * TC_RS4];          // fp32 query rows
-    float4 cen[32];                  // group centre
-    float qn2[32], qabs[32];
+    float4 P[TC_ROWS * 32];          // fp32 candidate rows: float4 k of row r at r * 32 + (k ^ (r & 7))
     float pn2[2][TC_ROWS];           // per half row: squared norm of the bf16 values
-    int rpos[2][TC_ROWS];
-    uint16_t rli[2][TC_ROWS];
-    int npos[TC_ROWS];               // mapping of the tile being prepared
-    uint16_t nli[TC_ROWS];
-    int bbeg[TC_NB], bcnt[TC_NB], bpre[TC_NB + 1];
-    uint32_t bem[TC_NB];
-    int qcnt[32], orig[32];
+    int pos[2][TC_ROWS];             // two map slots (tile t, tile t + 2): tree position of each row
+    uint16_t li[2][TC_ROWS];         //   and its candidate block
+    uint16_t kl[TC_KL];              // kept pairs of the tile: (query << 7) | row
     // one-pass emit: edges of the current stretch, written out per query in
     // one slot reservation each
     int ecol[TC_EB];
     float edist[TC_EB];
-    uint8_t eq[TC_EB];
     uint16_t erank[TC_EB];
-    int en, qfill[32], qbase[32];
-    uint16_t kl[TC_ROWS * 32];       // kept pairs of the tile: (query << 7) | row
-    int kn;
-    int wsum[TC_T / 32];
-    uint32_t tslot;
+    uint8_t eq[TC_EB];
+    int qfill[32], qbase[32];
+    int kn, en;
     uint64_t mma;
 };
-constexpr size_t kTcSmem = sizeof(TcShared) + 1024;
+struct __align__(128) TcShared {
+    TcGroup grp[2];
+    unsigned char B[32 * 256];       // bf16 query rows
+    float4 cen[32];                  // group centre
+    float2 qhg[32];                  // per query: threshold terms (h_q, g_q) of the filter
+    float qpn2[2][32];
+    int bbeg[TC_NB], bpre[TC_NB + 1];
+    uint32_t bem[TC_NB];
+    int qcnt[32], orig[32];
+    int wsum[TC_T / 32];
+    uint32_t tslot;
+};
+constexpr size_t kTcSmem = sizeof(TcShared) + 128;
 static_assert(kTcSmem <= 227 * 1024, "k_leaf_tc shared memory above the per-block limit");
-static_assert(TC_NB == 2 * TC_T, "block prefix assumes two candidate blocks per thread");
+static_assert(TC_NB == TC_T, "block prefix assumes one candidate block per thread");
+static_assert(sizeof(TcGroup) % 128 == 0, "bf16 tiles of both groups stay aligned");
 
-// Converts float4 columns [k0, k1) of one row (fp32, shared memory; columns
-// at or past dp4 and rows that are not valid give zeros) to centred bf16 in
-// the core-matrix layout; returns the partial squared norm of the bf16
-// values.  k0 and k1 are even, k1 - k0 <= 16.  All loads are issued before
-// the first store.
-__device__ __forceinline__ void tc_convert_part(unsigned char *tile, int r, const float4 *row, const float4 *cen,
-                                                int k0, int k1, int dp4, bool valid, float &n2) {
-    float4 v[16];
+// Named barrier of one 8-warp group (ids 1 and 2; id 0 is __syncthreads).
+__device__ __forceinline__ void tc_gbar(int id) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "n"(TC_GT) : "memory");
+}
+__device__ __forceinline__ bool tc_gbar_and(int id, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n"
+        ".reg .pred pi, po;\n"
+        "setp.ne.u32 pi, %1, 0;\n"
+        "bar.red.and.pred po, %2, %3, pi;\n"
+        "selp.u32 %0, 1, 0, po;\n"
+        "}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "n"(TC_GT)
+        : "memory");
+    return r != 0;
+}
+
+// Converts float4 columns [k0, k1) of one row (fp32; float4 k at row[k ^ sw];
+// columns at or past dp4 and rows that are not valid give zeros) to centred
+// bf16 in the core-matrix layout; returns the partial squared norm of the
+// bf16 values.  k0 and k1 are even, k1 - k0 <= 16.  Loads go eight float4 at a
+// time, each batch's loads before its stores.
+__device__ __forceinline__ void tc_convert_part(unsigned char *tile, int r, const float4 *row, int sw,
+                                                const float4 *cen, int k0, int k1, int dp4, bool valid, float &n2) {
+    unsigned long long bn = 0ull;  // norm in packed pairs (f32x2)
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-        const int k = k0 + u;
-        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (valid && k < k1 && k < dp4) {
-            const float4 x = row[k], c = cen[k];
-            v[u] = make_float4(x.x - c.x, x.y - c.y, x.z - c.z, x.w - c.w);
+    for (int b = 0; b < 16; b += 4) {
+        if (k0 + b >= k1) break;
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = k0 + b + u;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (valid && k < k1 && k < dp4) {
+                const float4 x = row[k ^ sw], c = cen[k];
+                v[u] = make_float4(x.x - c.x, x.y - c.y, x.z - c.z, x.w - c.w);
+            }
         }
-    }
-    // norm in packed pairs (f32x2): two partial sums, added at the end
-    unsigned long long bn = 0ull;
 #pragma unroll
-    for (int u = 0; u < 16; u += 2) {
-        const int k = k0 + u;
-        if (k >= k1) break;
-        const float4 v0 = v[u], v1 = v[u + 1];
-        const __nv_bfloat162 b01 = __floats2bfloat162_rn(v0.x, v0.y), b23 = __floats2bfloat162_rn(v0.z, v0.w);
-        const __nv_bfloat162 b45 = __floats2bfloat162_rn(v1.x, v1.y), b67 = __floats2bfloat162_rn(v1.z, v1.w);
-        uint4 pk;
-        pk.x = *reinterpret_cast<const uint32_t *>(&b01);
-        pk.y = *reinterpret_cast<const uint32_t *>(&b23);
-        pk.z = *reinterpret_cast<const uint32_t *>(&b45);
-        pk.w = *reinterpret_cast<const uint32_t *>(&b67);
-        *reinterpret_cast<uint4 *>(tile + tc::core_offset(r, k >> 1)) = pk;
-        const float2 f01 = __bfloat1622float2(b01), f23 = __bfloat1622float2(b23);
-        const float2 f45 = __bfloat1622float2(b45), f67 = __bfloat1622float2(b67);
-        bn = f2_sqacc(f2_pack(f01.x, f01.y), bn);
-        bn = f2_sqacc(f2_pack(f23.x, f23.y), bn);
-        bn = f2_sqacc(f2_pack(f45.x, f45.y), bn);
-        bn = f2_sqacc(f2_pack(f67.x, f67.y), bn);
+        for (int u = 0; u < 4; u += 2) {
+            const int k = k0 + b + u;
+            if (k >= k1) break;
+            const float4 v0 = v[u], v1 = v[u + 1];
+            const __nv_bfloat162 b01 = __floats2bfloat162_rn(v0.x, v0.y), b23 = __floats2bfloat162_rn(v0.z, v0.w);
+            const __nv_bfloat162 b45 = __floats2bfloat162_rn(v1.x, v1.y), b67 = __floats2bfloat162_rn(v1.z, v1.w);
+            uint4 pk;
+            pk.x = *reinterpret_cast<const uint32_t *>(&b01);
+            pk.y = *reinterpret_cast<const uint32_t *>(&b23);
+            pk.z = *reinterpret_cast<const uint32_t *>(&b45);
+            pk.w = *reinterpret_cast<const uint32_t *>(&b67);
+            *reinterpret_cast<uint4 *>(tile + tc::core_offset(r, k >> 1)) = pk;
+            const float2 f01 = __bfloat1622float2(b01), f23 = __bfloat1622float2(b23);
+            const float2 f45 = __bfloat1622float2(b45), f67 = __bfloat1622float2(b67);
+            bn = f2_sqacc(f2_pack(f01.x, f01.y), bn);
+            bn = f2_sqacc(f2_pack(f23.x, f23.y), bn);
+            bn = f2_sqacc(f2_pack(f45.x, f45.y), bn);
+            bn = f2_sqacc(f2_pack(f67.x, f67.y), bn);
+        }
     }
     n2 = f2_sum(bn);
 }
@@ -1469,10 +1503,13 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Vie
                                                    int32_t *__restrict__ deg, unsigned long long *__restrict__ st,
                                                    int32_t *__restrict__ err, CapOut co) {
     extern __shared__ unsigned char tc_raw[];
-    TcShared &S = *reinterpret_cast<TcShared *>(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+    TcShared &S = *reinterpret_cast<TcShared *>(((uintptr_t)tc_raw + 127) & ~(uintptr_t)127);
     const int it = blockIdx.x;
     if (it >= *items.count) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int grp = tid / TC_GT, gt = tid - grp * TC_GT, gw = gt >> 5;  // group, thread and warp in it
+    const int bar = 1 + grp;
+    TcGroup &G = S.grp[grp];
     const int gg = items.group[it];
     const int cloud = cloud_of_group(V, gg);
     const TreeView &tv = V.tv[cloud];
@@ -1480,45 +1517,37 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Vie
     const int g = gg - V.gbase[cloud];
     const int64_t rbase = V.rbase[cloud];  // CSR rows of this cloud start here
     const int dp = tv.dp, dim = tv.dim, dp4 = dp >> 2;
+    const float4 *pts4 = reinterpret_cast<const float4 *>(tv.pts);
     const int ksteps = (dp + 15) >> 4;
     const int K4 = 4 * ksteps;                       // float4 columns of the MMA's K
     const int kh = ((K4 >> 1) + 1) & ~1;             // split of a row between two threads (even)
     const int qb = tv.group_begin[g], qn = tv.group_count[g];
     const int64_t c0 = items.begin[it];
     const int nb = (int)(items.end[it] - c0);        // <= TC_NB
-    unsigned long long pairs = 0, kept = 0, guard = 0, band = 0, rows_ld = 0;  // rows_ld: thread 0
+    // per-thread counters (32-bit: at most 16 pairs per thread and tile)
+    uint32_t pairs = 0, kept = 0, guard = 0, band = 0, rows_ld = 0;  // rows_ld, kept: gt == 0
     bool failed = false;
     uint32_t mph = 0u;
     bool mma_out = false;
 
-    if (warp == 0) tc::tmem_alloc(&S.tslot, 32);
+    if (warp == 0) tc::tmem_alloc(&S.tslot, 64);
     if (tid == 0) {
-        tc::mbar_init(&S.mma, 1);
+        tc::mbar_init(&S.grp[0].mma, 1);
+        tc::mbar_init(&S.grp[1].mma, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (tid < 32) S.cen[tid] = tid < dp4 ? __ldg(reinterpret_cast<const float4 *>(tv.pts + (size_t)qb * dp) + tid)
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
-    // candidate blocks of the item and their row prefix
+    if (tid < 32) S.cen[tid] = tid < dp4 ? __ldg(pts4 + (size_t)qb * dp4 + tid) : make_float4(0.f, 0.f, 0.f, 0.f);
+    // candidate blocks of the item and their row prefix (one block per thread)
     {
-        int loc[2], sum = 0;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int i = 2 * tid + k;
-            int beg = 0, cnt = 0;
-            if (i < nb) {
-                const int v = (int)cand[c0 + i];
-                beg = tv.node_begin[v];
-                cnt = tv.node_count[v];
-            }
-            if (i < TC_NB) {
-                S.bbeg[i] = beg;
-                S.bcnt[i] = cnt;
-                S.bem[i] = 0u;
-            }
-            loc[k] = cnt;
-            sum += cnt;
+        int beg = 0, cnt = 0;
+        if (tid < nb) {
+            const int v = (int)cand[c0 + tid];
+            beg = tv.node_begin[v];
+            cnt = tv.node_count[v];
         }
-        int incl = sum;
+        S.bbeg[tid] = beg;
+        S.bem[tid] = 0u;
+        int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -1530,52 +1559,45 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Vie
 #pragma unroll
         for (int w = 0; w < TC_T / 32; ++w)
             if (w < warp) base += S.wsum[w];
-        int run = base + incl - sum;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            S.bpre[2 * tid + k] = run;
-            run += loc[k];
-        }
-        if (tid == TC_T - 1) S.bpre[TC_NB] = run;
+        S.bpre[tid] = base + incl - cnt;
+        if (tid == TC_T - 1) S.bpre[TC_NB] = base + incl;
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = S.tslot;
-    const uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, 32);
-    const uint64_t adesc0 = tc::smem_desc(tc::smem_u32(S.A), tc::kLBO, tc::kSBO);
-    const uint64_t bdesc0 = tc::smem_desc(tc::smem_u32(S.B), tc::kLBO, tc::kSBO);
+    const uint32_t tmem = S.tslot + (uint32_t)(32 * grp);  // this group's accumulator columns
     const int T = S.bpre[TC_NB];
     const int ntiles = (T + TC_ROWS - 1) / TC_ROWS;
 
-    // rows of tile tn -> (position, block) in npos / nli, by threads t0 and up
-    auto prep_map = [&](int tn, int t0) {
-        const int R0 = tn * TC_ROWS;
-        for (int r = tid - t0; r >= 0 && r < TC_ROWS; r += TC_T - t0) {
-            const int R = R0 + r;
-            if (R < T) {
-                int lo = 0, hi = TC_NB;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (S.bpre[mid] <= R) lo = mid; else hi = mid;
-                }
-                S.npos[r] = S.bbeg[lo] + (R - S.bpre[lo]);
-                S.nli[r] = (uint16_t)lo;
+    // rows of tile tn -> (position, block) in map slot sl (warps 1-4 of the
+    // group: warp 0 issues the MMAs meanwhile)
+    auto prep_map = [&](int tn, int sl) {
+        const int r = gt - 32, R = tn * TC_ROWS + r;
+        if (r >= 0 && r < TC_ROWS && R < T) {
+            int lo = 0, hi = TC_NB;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (S.bpre[mid] <= R) lo = mid; else hi = mid;
             }
+            G.pos[sl][r] = S.bbeg[lo] + (R - S.bpre[lo]);
+            G.li[sl][r] = (uint16_t)lo;
         }
     };
-    // all threads: take the prepared mapping for stage sg, start the row
-    // copies and commit them as one group (an empty group when tn is past the
-    // last tile, so that every iteration commits exactly one)
-    auto issue = [&](int tn, int sg) {
+    // the group's row copies of tile tn (map slot sl) into its stage,
+    // committed as one group (an empty group past the last tile)
+    // (warp w copies rows w, w + 8, ..., lane per 16 bytes; lane i < 16 reads
+    // the position of the warp's row i)
+    auto issue = [&](int tn, int sl) {
         if (tn < ntiles) {
             const int rows = min(TC_ROWS, T - tn * TC_ROWS);
-            for (int r = tid; r < rows; r += TC_T) {
-                S.rpos[sg][r] = S.npos[r];
-                S.rli[sg][r] = S.nli[r];
+            const int mine = gw + 8 * (lane & 15);
+            const int mpos = mine < rows ? G.pos[sl][mine] : 0;
+#pragma unroll
+            for (int i = 0; i < TC_ROWS / 8; ++i) {
+                const int r = gw + 8 * i;
+                const int pos = __shfl_sync(0xffffffffu, mpos, i);
+                if (r < rows && lane < dp4) cp_async16(&G.P[r * 32 + (lane ^ gw)], pts4 + (size_t)pos * dp4 + lane, true);
             }
-            for (int r = warp; r < rows; r += TC_T / 32)  // warp per row, lane per 16 bytes
-                if (lane < dp4) cp_async16(&S.P[sg][r * TC_RS4 + lane], tv.pts + (size_t)S.npos[r] * dp + 4 * lane, true);
         }
         cp_async_commit();
     };
@@ -1584,118 +1606,199 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Vie
         const int nqr = min(32, qn - q0);
         const int qfirst = qb + q0;
         __syncthreads();
-        // queries: fp32 rows, then bf16 conversion (two threads per row)
-        for (int i = tid; i < 32 * TC_RS4; i += TC_T) {
-            const int q = i / TC_RS4, k = i - q * TC_RS4;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (q < nqr && k < dp4) v = __ldg(reinterpret_cast<const float4 *>(tv.pts + (size_t)(qfirst + q) * dp) + k);
-            S.Qf[i] = v;
-        }
         if (tid < 32) {
             S.qcnt[tid] = 0;
             S.orig[tid] = tid < nqr ? (int)(rbase + tv.perm[qfirst + tid]) : 0;
         }
-        for (int i = tid; i < nb; i += TC_T) S.bem[i] = 0u;
-        if (tid < 32) S.qfill[tid] = 0;
-        if (tid == 0) {
-            S.en = 0;
-            S.kn = 0;
+        if (tid < nb) S.bem[tid] = 0u;
+        if (gt < 32) G.qfill[gt] = 0;
+        if (gt == 0) {
+            G.en = 0;
+            G.kn = 0;
         }
-        __syncthreads();
+        // queries: bf16 conversion from global memory (two threads per row)
         if (tid < 64) {
             const int q = tid & 31, half = tid >> 5;
             float n2;
-            tc_convert_part(S.B, q, S.Qf + q * TC_RS4, S.cen, half ? kh : 0, half ? K4 : kh, dp4, q < nqr, n2);
-            S.pn2[half][q] = n2;
+            tc_convert_part(S.B, q, pts4 + (size_t)(qfirst + min(q, nqr - 1)) * dp4, 0, S.cen, half ? kh : 0,
+                            half ? K4 : kh, dp4, q < nqr, n2);
+            S.qpn2[half][q] = n2;
+            tc::fence_smem_to_async();  // B is read by both groups' MMAs
         }
         __syncthreads();
         if (tid < 32) {
-            S.qn2[tid] = S.pn2[0][tid] + S.pn2[1][tid];
-            S.qabs[tid] = sqrtf(S.qn2[tid]) * TC_NORM_UP;
+            // filter test, rearranged per query: keep iff dot >= h_q + g_q |p~| + w_p
+            // (see the kernel's filter)
+            const float qn2 = S.qpn2[0][tid] + S.qpn2[1][tid];
+            const float qa = sqrtf(qn2) * TC_NORM_UP;
+            const float E = fmaf(TC_REL, qa, qp.eps_up);
+            const float h = 0.5f * (qn2 - fmaf(E, E, fmaf(TC_ABS2 * qa, qa, 0x1p-60f))) - 0x1p-20f * (E * E);
+            S.qhg[tid] = make_float2(h, -TC_REL * E);
         }
+        __syncthreads();
 
         // one-pass emit: reserves each query's slots once and writes the
-        // buffered edges (all threads; between barriers)
+        // group's buffered edges (the group's threads, between its barriers)
         auto flush = [&]() {
-            if (tid < 32 && S.qfill[tid]) S.qbase[tid] = atomicAdd(&co.fill[S.orig[tid]], S.qfill[tid]);
-            __syncthreads();
-            const int n = min(S.en, TC_EB);
-            for (int i = tid; i < n; i += TC_T) {
-                const int q = S.eq[i];
-                cap_place(co, S.orig[q], S.qbase[q] + S.erank[i], tv.perm[S.ecol[i]], S.edist[i]);
+            if (gt < 32 && G.qfill[gt]) G.qbase[gt] = atomicAdd(&co.fill[S.orig[gt]], G.qfill[gt]);
+            tc_gbar(bar);
+            const int n = min(G.en, TC_EB);
+            for (int i = gt; i < n; i += TC_GT) {
+                const int q = G.eq[i];
+                cap_place(co, S.orig[q], G.qbase[q] + G.erank[i], tv.perm[G.ecol[i]], G.edist[i]);
             }
-            __syncthreads();
-            if (tid < 32) S.qfill[tid] = 0;
-            if (tid == 0) S.en = 0;
-            __syncthreads();
+            tc_gbar(bar);
+            if (gt < 32) G.qfill[gt] = 0;
+            if (gt == 0) G.en = 0;
         };
-        // prologue: tiles 0 and 1 in flight
-        for (int tn = 0; tn < 2; ++tn) {
-            if (tn < ntiles) prep_map(tn, 0);
-            __syncthreads();
-            issue(tn, tn);
-            __syncthreads();
-        }
-        for (int t = 0; t < ntiles; ++t) {
-            const int sg = t & 1;
+        // pair e = (query << 7) | row of the tile in map slot sl, by the eight
+        // lanes of an octet: lane j sums coordinate chunk j (16 floats, both rows
+        // from global memory) in the canonical order and the chunk sums are
+        // added in ascending order -- the canonical fp32 sum; the octet's first
+        // lane decides (FP64 where fp32 cannot) and records the edge
+        auto recheck8 = [&](int e, int sl) {
+            const int q = e >> 7, r = e & 127, sub = lane & 7;
+            const unsigned omask = 0xffu << (lane & 24);
+            const int ppos = G.pos[sl][r];
+            const float4 *prow = pts4 + (size_t)ppos * dp4;
+            const float4 *qrow = pts4 + (size_t)(qfirst + q) * dp4;
+            const int k0 = 4 * sub;
+            float lo = 0.f, hi = 0.f;
+            if (k0 < dp4) {
+                float4 a[4], b[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool in = k0 + u < dp4;
+                    a[u] = in ? qrow[k0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    b[u] = in ? __ldg(prow + k0 + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (k0 + u < dp4) {
+                        const float dx = a[u].x - b[u].x, dy = a[u].y - b[u].y, dz = a[u].z - b[u].z,
+                                    dw = a[u].w - b[u].w;
+                        lo = fmaf(dx, dx, lo);
+                        hi = fmaf(dy, dy, hi);
+                        lo = fmaf(dz, dz, lo);
+                        hi = fmaf(dw, dw, hi);
+                    }
+            }
+            const float chunk = lo + hi;
+            const int nch = (dp4 + 3) >> 2;
+            float sv = __shfl_sync(omask, chunk, 0, 8);
+#pragma unroll
+            for (int j = 1; j < 8; ++j) {
+                const float cj = __shfl_sync(omask, chunk, j, 8);
+                if (j < nch) sv += cj;
+            }
+            if (sub) return;
+            unsigned long long in_band = 0;
+            const int edge = decide32(qp, sv, in_band);
+            band += (uint32_t)in_band;
+            bool is_edge;
+            float d;
+            if (edge < 0) {
+                ++guard;
+                const double s64 = sq_l2_exact4(qrow, prow, dim);
+                is_edge = s64 <= qp.eps2_64;
+                d = (float)sqrt(s64);
+            } else {
+                is_edge = edge != 0;
+                d = sqrtf(sv);
+            }
+            if (is_edge) {
+                atomicAdd(&S.qcnt[q], 1);
+                atomicOr(&S.bem[G.li[sl][r]], 1u << q);
+                if (co.off) {
+                    const int slot = atomicAdd(&G.en, 1);
+                    if (slot < TC_EB) {
+                        G.eq[slot] = (uint8_t)q;
+                        G.ecol[slot] = ppos;  // tree position; the original id is looked up at the flush
+                        G.edist[slot] = d;
+                        G.erank[slot] = (uint16_t)atomicAdd(&G.qfill[q], 1);
+                    } else {
+                        cap_put(co, S.orig[q], tv.perm[ppos], d);
+                    }
+                }
+            }
+        };
+
+        // this group's tiles: grp, grp + 2, ...
+        if (grp < ntiles) prep_map(grp, 0);
+        tc_gbar(bar);
+        issue(grp, 0);
+        for (int t = grp; t < ntiles; t += 2) {
+            const int sl = (t >> 1) & 1;
             const int rows = min(TC_ROWS, T - t * TC_ROWS);
-            if (tid == 0) rows_ld += rows;
-            cp_async_wait<1>();  // this thread's copies of tile t have landed
-            __syncthreads();
+            if (gt == 0) rows_ld += rows;
+            cp_async_wait<0>();  // this thread's copies of tile t have landed
+            tc_gbar(bar);
             // bf16 tile from the staged rows (two threads per row)
             {
-                const int r = tid & (TC_ROWS - 1), half = tid >> 7;
+                const int r = gt & (TC_ROWS - 1), half = gt >> 7;
                 float n2;
-                tc_convert_part(S.A, r, S.P[sg] + r * TC_RS4, S.cen, half ? kh : 0, half ? K4 : kh, dp4, r < rows,
+                tc_convert_part(G.A, r, G.P + r * 32, r & 7, S.cen, half ? kh : 0, half ? K4 : kh, dp4, r < rows,
                                 n2);
-                S.pn2[half][r] = n2;
+                G.pn2[half][r] = n2;
             }
             tc::fence_smem_to_async();
             tc::fence_before_sync();
-            __syncthreads();
+            tc_gbar(bar);
             tc::fence_after_sync();
-            if (tid == 0) {
+            if (gt == 0) {
+                constexpr uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, 32);
+                const uint64_t adesc0 = tc::smem_desc(tc::smem_u32(G.A), tc::kLBO, tc::kSBO);
+                const uint64_t bdesc0 = tc::smem_desc(tc::smem_u32(S.B), tc::kLBO, tc::kSBO);
                 // one K step is 256 bytes further along both tiles (address field in 16-byte units)
                 for (int ks = 0; ks < ksteps; ++ks)
                     tc::mma_bf16(tmem, adesc0 + (uint64_t)(ks * 16), bdesc0 + (uint64_t)(ks * 16), idesc, ks > 0);
-                tc::mma_commit(&S.mma);
+                tc::mma_commit(&G.mma);
             }
             mma_out = true;
-            if (t + 2 < ntiles) prep_map(t + 2, 32);  // warp 0 issues the MMAs meanwhile
-            const bool mok = tc::mbar_wait(&S.mma, mph, TC_WAIT);
-            if (!__syncthreads_and(mok)) {
-                if (tid == 0) atomicOr(err, 32);
+            if (t + 2 < ntiles) prep_map(t + 2, sl ^ 1);
+            tc_gbar(bar);   // stage consumed, map of tile t + 2 ready
+            issue(t + 2, sl ^ 1);
+            bool mok = true;  // warp 0 of the group waits, the barrier releases the others
+            if (gw == 0) mok = tc::mbar_wait(&G.mma, mph, TC_WAIT);
+            if (!tc_gbar_and(bar, mok)) {
+                if (gt == 0) atomicOr(err, 32);
                 failed = true;
                 break;
             }
             mph ^= 1u;
             mma_out = false;
             tc::fence_after_sync();
-            // epilogue, filter: warp w reads rows 32 (w % 4) .. + 31, queries
-            // 16 (w / 4) .. + 15; kept pairs go to the tile's list
+            // epilogue, filter: warp w of the group reads rows 32 (w % 4) .. + 31,
+            // queries 16 (w / 4) .. + 15; kept pairs go to the tile's list
+            uint32_t keepm = 0u;
+            int kb = 0;
             {
-                const int quarter = warp & 3, qh = warp >> 2;
+                const int quarter = gw & 3, qh = gw >> 2;
                 float dot[16];
                 tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(16 * qh), dot);
                 const int r = 32 * quarter + lane;
-                uint32_t keepm = 0u;
                 if (r < rows) {
-                    const int ppos = S.rpos[sg][r];
-                    const float pn = S.pn2[0][r] + S.pn2[1][r];
+                    // kept iff d^2 = |q^|^2 + |p^|^2 - 2 dot <= (E_q + 2^-8 |p~|)^2
+                    // + 2^-12 (|q~|^2 + |p~|^2) + 2^-60 with E_q = eps + 2^-8 |q~|, i.e.
+                    // iff dot >= h_q + g_q |p~| + w_p with h_q = (|q^|^2 - E_q^2 - 2^-12 |q~|^2
+                    // - 2^-60) / 2, g_q = -2^-8 E_q, w_p = (|p^|^2 - (2^-16 + 2^-12) |p~|^2) / 2.
+                    // The rounding of this form stays below 2^-21 (|q^|^2 + |p^|^2 + 2 E_q^2):
+                    // the first part is inside the 2^-12 term's slack over the MMA's
+                    // accumulation error (below 2^-17 (|q^|^2 + |p^|^2)), the second is
+                    // covered by the 2^-20 E_q^2 taken off h_q.  NaN keeps the pair.
+                    const int ppos = G.pos[sl][r];
+                    const float pn = G.pn2[0][r] + G.pn2[1][r];
                     const float pa = sqrtf(pn) * TC_NORM_UP;
-                    uint32_t validm = 0u;
+                    const float wp = 0.5f * fmaf(-(TC_REL * TC_REL + TC_ABS2) * pa, pa, pn);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const int q = 16 * qh + j;
-                        if (q >= nqr) continue;
-                        if (qfirst + q == ppos && !qp.include_self) continue;
-                        validm |= 1u << j;
-                        const float qa = S.qabs[q];
-                        const float d2 = fmaf(-2.0f, dot[j], S.qn2[q] + pn);
-                        const float e = fmaf(TC_REL, qa + pa, qp.eps_up);
-                        const float bound = fmaf(e, e, TC_ABS2 * fmaf(qa, qa, pa * pa)) + 0x1p-60f;
-                        if (!(d2 > bound)) keepm |= 1u << j;  // NaN keeps the pair
+                        const float2 hg = S.qhg[16 * qh + j];
+                        if (!(dot[j] < fmaf(hg.y, pa, hg.x) + wp)) keepm |= 1u << j;
                     }
+                    uint32_t validm = (nqr >= 16 * qh + 16 ? 0xffffu : (1u << max(nqr - 16 * qh, 0)) - 1u);
+                    const int self = ppos - qfirst - 16 * qh;
+                    if (!qp.include_self && (unsigned)self < 16u) validm &= ~(1u << self);
+                    keepm &= validm;
                     pairs += __popc(validm);
                 }
                 const int c = __popc(keepm);
@@ -1706,89 +1809,67 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Vie
                     if (lane >= o) incl += y;
                 }
                 int base = 0;
-                if (lane == 31 && incl) base = atomicAdd(&S.kn, incl);
-                base = __shfl_sync(0xffffffffu, base, 31) + incl - c;
-                while (keepm) {
-                    const int j = __ffs(keepm) - 1;
-                    keepm &= keepm - 1u;
-                    S.kl[base++] = (uint16_t)(((16 * qh + j) << 7) | r);
+                if (lane == 31 && incl) base = atomicAdd(&G.kn, incl);
+                kb = __shfl_sync(0xffffffffu, base, 31) + incl - c;
+                uint32_t m = keepm;
+                for (int idx = kb; m && idx < TC_KL; ++idx) {
+                    const int j = __ffs(m) - 1;
+                    m &= m - 1u;
+                    G.kl[idx] = (uint16_t)(((16 * qh + j) << 7) | r);
                 }
             }
-            __syncthreads();
-            // epilogue, recheck: the tile's kept pairs spread over all threads,
-            // one pair per thread (canonical fp32 sum, rows in shared memory)
+            tc_gbar(bar);
+            // epilogue, recheck: the kept pairs spread over the group's lane
+            // octets, one pair per octet, TC_KL at a time
             {
-                const int n = S.kn;
-                if (tid == 0) kept += n;
-                for (int i = tid; i < n; i += TC_T) {
-                    const int e = S.kl[i];
-                    const int q = e >> 7, r = e & 127;
-                    const float4 *prow = S.P[sg] + r * TC_RS4;
-                    const float4 *qrow = S.Qf + q * TC_RS4;
-                    const float sv = pair_sqdist_smem(qrow, prow, dp4);
-                    const int edge = decide32(qp, sv, band);
-                    bool is_edge;
-                    float d;
-                    if (edge < 0) {  // undecided in fp32: the pinned FP64 sum, rows from shared memory
-                        ++guard;
-                        const double s64 = sq_l2_exact4(qrow, prow, dim);
-                        is_edge = s64 <= qp.eps2_64;
-                        d = (float)sqrt(s64);
-                    } else {
-                        is_edge = edge != 0;
-                        d = sqrtf(sv);
+                const int n = G.kn;
+                if (gt == 0) kept += n;
+                for (int i = gt >> 3; i < min(n, TC_KL); i += TC_GT / 8) recheck8(G.kl[i], sl);
+                for (int lo = TC_KL; lo < n; lo += TC_KL) {
+                    tc_gbar(bar);
+                    uint32_t m = keepm;
+                    const int qc = 16 * (gw >> 2), r = 32 * (gw & 3) + lane;
+                    for (int idx = kb; m && idx < lo + TC_KL; ++idx) {
+                        const int j = __ffs(m) - 1;
+                        m &= m - 1u;
+                        if (idx >= lo) G.kl[idx - lo] = (uint16_t)(((qc + j) << 7) | r);
                     }
-                    if (is_edge) {
-                        const int ppos = S.rpos[sg][r], li = S.rli[sg][r];
-                        atomicAdd(&S.qcnt[q], 1);
-                        atomicOr(&S.bem[li], 1u << q);
-                        if (co.off) {
-                            const int slot = atomicAdd(&S.en, 1);
-                            if (slot < TC_EB) {
-                                S.eq[slot] = (uint8_t)q;
-                                S.ecol[slot] = ppos;  // tree position; the original id is looked up at the flush
-                                S.edist[slot] = d;
-                                S.erank[slot] = (uint16_t)atomicAdd(&S.qfill[q], 1);
-                            } else {
-                                cap_put(co, S.orig[q], tv.perm[ppos], d);
-                            }
-                        }
-                    }
+                    tc_gbar(bar);
+                    for (int i = gt >> 3; i < min(n - lo, TC_KL); i += TC_GT / 8) recheck8(G.kl[i], sl);
                 }
             }
             tc::fence_before_sync();
-            __syncthreads();
+            tc_gbar(bar);
             tc::fence_after_sync();
-            if (tid == 0) S.kn = 0;
-            issue(t + 2, sg);
-            if (co.off && S.en >= TC_EB / 2) flush();
+            if (gt == 0) G.kn = 0;
+            if (co.off && G.en >= TC_EB / 2) flush();
         }
+        if (!failed && co.off) flush();
+        failed = __syncthreads_or(failed);
         if (failed) break;
-        if (co.off) flush();
-        __syncthreads();
         if (tid < nqr && S.qcnt[tid]) atomicAdd(&deg[S.orig[tid]], S.qcnt[tid]);
     }
-    if (!failed && emask)
-        for (int i = tid; i < nb; i += TC_T) emask[c0 + i] = qn <= 32 ? S.bem[i] : ~0u;
+    if (!failed && emask && tid < nb) emask[c0 + tid] = qn <= 32 ? S.bem[tid] : ~0u;
+    unsigned long long pairs64 = pairs, kept64 = kept, guard64 = guard, band64 = band;
     for (int o = 16; o > 0; o >>= 1) {
-        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
-        kept += __shfl_xor_sync(0xffffffffu, kept, o);
-        guard += __shfl_xor_sync(0xffffffffu, guard, o);
-        band += __shfl_xor_sync(0xffffffffu, band, o);
+        pairs64 += __shfl_xor_sync(0xffffffffu, pairs64, o);
+        kept64 += __shfl_xor_sync(0xffffffffu, kept64, o);
+        guard64 += __shfl_xor_sync(0xffffffffu, guard64, o);
+        band64 += __shfl_xor_sync(0xffffffffu, band64, o);
     }
     if (lane == 0) {
-        stat_add(st, ST_PAIRS, pairs);
-        stat_add(st, ST_RECHECK, kept);
-        stat_add(st, ST_GUARD, guard);
-        stat_add(st, ST_BAND, band);
-        if (tid == 0) stat_add(st, ST_ROWS, rows_ld);
+        stat_add(st, ST_PAIRS, pairs64);
+        stat_add(st, ST_RECHECK, kept64);
+        stat_add(st, ST_GUARD, guard64);
+        stat_add(st, ST_BAND, band64);
+        if (gt == 0) stat_add(st, ST_ROWS, rows_ld);
     }
     cp_async_wait<0>();  // no copy into this CTA's shared memory outlives it
-    if (failed && mma_out) tc::mbar_wait(&S.mma, mph, TC_WAIT);  // let an outstanding MMA finish
+    if (failed && mma_out) tc::mbar_wait(&G.mma, mph, TC_WAIT);  // let an outstanding MMA finish
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, 32);
+    if (warp == 0) tc::tmem_dealloc(S.tslot, 64);
 }
 
 // Dynamic shared memory of the L2 leaf kernel (set once per process).
