@@ -10,7 +10,7 @@ sift eps=175 shape).  Prints ONE JSON line (rank 0).
                   [--workload gmm_1m_k70] [--form tc+learned|tc|learned|plain]
                   [--no-compare] [--no-cpu-baseline] [--no-e2e]
 
-The default form is the BF16-filtered, learned one; the plain FP32 two-pass
+The default form is the tensor-core-filtered, learned one; the plain FP32 two-pass
 form is timed beside it on the same input ("plain" in the JSON line).
 
 With N > 1 (torchrun) every rank runs an independent replica of the workload
@@ -261,7 +261,7 @@ def run_clouds(args, wl, world, rank, dist):
             trees = [cg.ct_build(points=x, leaf_size=zeta, stream=stream) for x in xs]
             t0 = time.perf_counter()
             ch = cg.ct_autotune(trees, eps, stream=stream)
-            tuned = {"bf16_clouds": int(sum(ch)), "fp32_clouds": len(ch) - int(sum(ch)),
+            tuned = {"tc_clouds": int(sum(ch)), "fp32_clouds": len(ch) - int(sum(ch)),
                      "tune_s": time.perf_counter() - t0}
             for t in trees:
                 t.free()
@@ -352,7 +352,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="gmm_1m_k70")
     ap.add_argument("--form", default="tc+learned", choices=sorted(FORMS),
-                    help="plain: FP32 two-pass; tc: BF16 tensor-core filter; learned: one-pass emit "
+                    help="plain: FP32 two-pass; tc: tensor-core filter (fp16 rows); learned: one-pass emit "
                          "sized by the predictor; tc+learned: both")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the plain form beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -545,19 +545,23 @@ def main():
     dom = max(kernel_stages, key=lambda k: kernel_stages[k][0]) if kernel_stages else None
     roof = None
     if "leaf_count_tc" in prof:
-        # BF16 form: 32 queries x 128 dims x 2 flops per 512-byte candidate row is
-        # 16 flop/B, far below the tensor ridge (~250 flop/B): the tiles are
-        # bound by streaming the candidate rows, so the roofline is HBM
+        # tensor-core form: 32 queries x 128 dims x 2 flops per 260-byte fp16
+        # candidate row (+ norm) is 32 flop/B, far below the tensor ridge
+        # (~250 flop/B): the tiles are bound by streaming the candidate rows
+        # (and the original rows of the kept pairs), so the roofline is HBM
         t_launch = prof["leaf_count_tc"][0] / prof["leaf_count_tc"][1] / 1e3
-        nbytes = st["leaf_rows"] * wl["dim"] * 4.0
+        kp = 16 * ((((wl["dim"] + 3) // 4) * 4 + 15) // 16)  # fp16 row length (dp rounded up to 16)
+        nbytes = st["leaf_rows"] * (2.0 * kp + 4.0) + st["recheck_fp32"] * 4.0 * wl["dim"]
         hbm = peaks.get("hbm_gbs", 6800.0)
         ach = nbytes / t_launch / 1e9
         roof = {"kernel": "k_leaf_tc", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": profile_traffic("k_leaf_tc", args.workload),
                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)" if peaks else "fallback 6.8 TB/s",
-                "bytes_per_launch": nbytes, "bytes_rule": "candidate point rows loaded x dim x 4 B",
-                "ms_per_launch": t_launch * 1e3, "tensor_flops_per_launch": st["leaf_pairs"] * 2.0 * wl["dim"],
-                "tensor_frac_of_sustained_bf16": st["leaf_pairs"] * 2.0 * wl["dim"] / t_launch / 1e12
+                "bytes_per_launch": nbytes,
+                "bytes_rule": "leaf_rows x (2 kp + 4) B (fp16 candidate rows and norms, kp = dim rounded "
+                              "up to 16) + recheck_fp32 x dim x 4 B (original candidate rows of kept pairs)",
+                "ms_per_launch": t_launch * 1e3, "tensor_flops_per_launch": st["leaf_pairs"] * 2.0 * kp,
+                "tensor_frac_of_sustained_f16": st["leaf_pairs"] * 2.0 * kp / t_launch / 1e12
                 / peaks.get("bf16_tflops_sustained", 1700.0),
                 "recheck_fp32_pairs": st["recheck_fp32"], "dominant_stage": dom}
     elif "leaf_count" in prof:

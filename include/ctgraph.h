@@ -83,11 +83,13 @@ typedef struct {
 
 /* Query options.
  *  precision:     0 = plain FP32 direct-difference leaf tiles;
- *                 1 = BF16 tensor-core filter (tcgen05) with FP32 recheck
- *                     (L2 only; rows above 128 floats use the FP32 tiles);
+ *                 1 = tensor-core filter (tcgen05, fp16 rows centred on
+ *                     the column means and scaled by a power of two,
+ *                     prepared once per query) with FP32 recheck (L2 only;
+ *                     rows above 128 floats use the FP32 tiles);
  *                 2 = per cloud, the count kernel and work-item length that
  *                     ct_autotune measured fastest for its row length (before
- *                     tuning: BF16 tiles from 32 floats per row up).
+ *                     tuning: tensor-core tiles from 32 floats per row up).
  *                 All give the same edge set and distances.
  *  use_predictor: 0 = two-pass count -> scan -> emit;
  *                 1 = one-pass emit into row capacities predicted by
@@ -124,7 +126,7 @@ typedef struct {
     int64_t traversal_evals;  /* distance evaluations in the tree walk (count pass) */
     int64_t leaf_pairs;       /* (query, candidate point) pairs decided (count pass) */
     int64_t guard_fp64;       /* pairs decided by the pinned FP64 sum */
-    int64_t recheck_fp32;     /* pairs re-evaluated in FP32 after the BF16 filter */
+    int64_t recheck_fp32;     /* pairs re-evaluated in FP32 after the tensor-core filter */
     int64_t candidates;       /* (group, candidate leaf block) entries */
     int64_t overflow_rows;    /* learned form: rows whose degree exceeded the predicted capacity */
     int64_t kernel_launches;  /* kernels this library launched for the query */
@@ -172,10 +174,10 @@ ct_status eps_graph_query_batched(int32_t n_clouds, const ct_tree *const *trees,
  * L2 trees (dp = dim rounded up to 4: <= 4, 16, 32, 64, 128), times the
  * batched query of that class's clouds (eps_graph_query_batched with
  * `opts`, twice per candidate, outputs discarded) with each candidate --
- * count kernel (BF16 or FP32 tiles) x work-item length (512 or 256
+ * count kernel (tensor-core or FP32 tiles) x work-item length (512 or 256
  * candidate blocks) -- and keeps the fastest in a process-wide table.
  * choices (host int32[n_clouds], may be NULL) receives each cloud's kernel
- * (1 BF16, 0 FP32).  Synchronises `stream`.  ct_autotune_reset clears the
+ * (1 tensor core, 0 FP32).  Synchronises `stream`.  ct_autotune_reset clears the
  * table.  Errors: as eps_graph_query_batched. */
 ct_status ct_autotune(int32_t n_clouds, const ct_tree *const *trees, const double *eps,
                       const ct_query_opts *opts, ct_stream stream, int32_t *choices);
@@ -342,12 +344,13 @@ ct_status ct_profile_entry(int32_t i, const char **name, double *total_ms, int64
 int64_t ct_kernel_launches(void);
 
 /* Tensor-core self-test (a diagnostic; the paper has none): D = A * B^T for
- * A (128 x 128) and B (32 x 128) bf16 row-major device matrices and D
- * (128 x 32) fp32 row-major device output, through one tcgen05 BF16 MMA chain
- * with the accumulator in tensor memory -- the primitive of the precision-1
- * leaf filter.  Synchronises `stream`.  CT_ETIMEOUT if the bounded wait for
- * the MMA's completion gives up. */
-ct_status ct_selftest_tc_gemm(const void *A, const void *B, float *D, ct_stream stream);
+ * A (128 x 128) and B (32 x 128) 16-bit row-major device matrices (fp16 = 0:
+ * bf16, 1: fp16; both the same type) and D (128 x 32) fp32 row-major device
+ * output, through one tcgen05 kind::f16 MMA chain with the accumulator in
+ * tensor memory -- the primitive of the precision-1 leaf filter (fp16).
+ * Synchronises `stream`.  CT_EINVAL for a NULL pointer or fp16 outside
+ * {0, 1}; CT_ETIMEOUT if the bounded wait for the MMA's completion gives up. */
+ct_status ct_selftest_tc_gemm(const void *A, const void *B, int32_t fp16, float *D, ct_stream stream);
 
 /* Thread-local message for the last non-OK status of this thread. */
 const char *ct_last_error(void);

@@ -18,7 +18,7 @@ void query_batched(int n_clouds, const ct_tree *const *trees, const QParams *qps
 void autotune(int n_clouds, const ct_tree *const *trees, const QParams *qps, const ct_query_opts *opts,
               cudaStream_t s, int32_t *choices);
 void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cudaStream_t s);
-void tc_selftest(const void *A, const void *B, float *D, cudaStream_t s);
+void tc_selftest(const void *A, const void *B, int fp16, float *D, cudaStream_t s);
 }  // namespace ct
 
 namespace {
@@ -62,7 +62,7 @@ void validate_query(const ct_tree *tree, double eps, const ct_query_opts &o) {
     if (!(eps >= 0.0)) CT_FAIL(CT_EINVAL, "eps must be >= 0 (got %g)", eps);
     if (o.precision < 0 || o.precision > 2) CT_FAIL(CT_EINVAL, "precision must be 0, 1 or 2");
     if (o.precision == 1 && tree->metric != CT_L2_F32)
-        CT_FAIL(CT_EINVAL, "the BF16 filter applies to L2 trees only");
+        CT_FAIL(CT_EINVAL, "the tensor-core filter applies to L2 trees only");
     if (o.use_predictor && !o.predictor) CT_FAIL(CT_EINVAL, "use_predictor set without a predictor");
     if (o.include_self != 0 && o.include_self != 1) CT_FAIL(CT_EINVAL, "include_self must be 0 or 1");
 }
@@ -212,10 +212,11 @@ ct_status eps_graph_degrees_noalloc(const ct_tree *tree, double eps, int32_t inc
     });
 }
 
-ct_status ct_selftest_tc_gemm(const void *A, const void *B, float *D, ct_stream stream) {
+ct_status ct_selftest_tc_gemm(const void *A, const void *B, int32_t fp16, float *D, ct_stream stream) {
     return guarded([&] {
         if (!A || !B || !D) CT_FAIL(CT_EINVAL, "NULL argument");
-        ct::tc_selftest(A, B, D, (cudaStream_t)stream);
+        if (fp16 != 0 && fp16 != 1) CT_FAIL(CT_EINVAL, "fp16 must be 0 or 1");
+        ct::tc_selftest(A, B, fp16, D, (cudaStream_t)stream);
     });
 }
 

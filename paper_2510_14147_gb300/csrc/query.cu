@@ -132,7 +132,11 @@ struct Views {
     TreeView tv[kMaxClouds];
     QParams qp[kMaxClouds];
     int16_t item_len[kMaxClouds];  // candidate blocks per work item
-    uint8_t use_tc[kMaxClouds];    // leaf kernel of the count pass: BF16 tiles (1) or FP32 tiles (0)
+    uint8_t use_tc[kMaxClouds];    // leaf kernel of the count pass: tensor-core tiles (1) or FP32 tiles (0)
+    // tensor-core filter rows (FP16 form): fp16 rows, their squared norms, {s, s eps_up}
+    const uint4 *h16[kMaxClouds];
+    const float *n16[kMaxClouds];
+    const float *s16[kMaxClouds];
 };
 __device__ __forceinline__ int cloud_of_group(const Views &V, int gg) {
     int lo = 0, hi = V.nc;
@@ -512,6 +516,11 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool va
     unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     int n = valid ? 16 : 0;  // 0: the 16 bytes are zero-filled, nothing is read
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
+}
+// 4-byte copy through L1 (cp.async.cg takes 16-byte copies only)
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
@@ -1359,195 +1368,200 @@ __global__ void k_ovf_scatter(int64_t used, const int32_t *__restrict__ orow, co
 }
 
 // ---------------------------------------------------------------------------
-// Precision 1: BF16 tensor-core filter, FP32 recheck, FP64 guard band.
+// Precision 1: tensor-core filter, FP32 recheck, FP64 guard band.
 //
 // Count pass per work item: the group's queries (B, N = 32) and 128-row tiles
-// of packed candidate points (A, M = 128) are centred on the group centre c,
-// rounded to bf16 and multiplied by tcgen05 MMAs (K = 16 per instruction) into
-// a 128 x 32 fp32 accumulator in tensor memory.  With x~ = x - c, y~ = y - c
-// (fp32) and x^ = bf16(x~), y^ = bf16(y~):
-//   |x^_k - x~_k| <= 2^-9 |x~_k|, so ||x^ - y^|| <= d(x, y) + 2^-8.9 (|x~| + |y~|);
-//   d^2 = |x^|^2 + |y^|^2 - 2 x^.y^ is formed from exact bf16 products with fp32
-//   sums, |d^2 - ||x^ - y^||^2| <= 2^-12 (|x~|^2 + |y~|^2) (sums of 128 terms
-//   with a few ulps per addition, generously).
-// A pair is kept iff d^2 <= (eps + 2^-8 (|x~| + |y~|))^2 + 2^-12 (|x~|^2 + |y~|^2),
-// which keeps every edge; the kernel uses upper bounds of |x~| and |y~| taken
-// from the bf16 norms (TC_NORM_UP), which only widen the test.  Kept pairs are
-// decided like the FP32 path: the
-// canonical fp32 direct-difference sum (decide32), the pinned FP64 sum where
-// that cannot decide.
-// The emit pass is the FP32 path's, driven by the same per-block edge masks.
-//
-// Pipeline (one CTA of two 8-warp groups per work item, one item's candidate
-// blocks in one batch): the groups take alternate 128-row tiles, each with its
-// own fp32 stage, bf16 tile, 32 tensor-memory columns, MMA barrier, kept-pair
-// list and edge buffer, synchronised by its own named barrier, so that one
-// group's copies, conversion and MMA overlap the other's filter and rechecks.
-// A group's fp32 rows of tile t + 2 are copied (16-byte asynchronous copies)
-// into its stage as soon as tile t is converted; the FP32 rechecks read both
-// rows from global memory (L1/L2).  (One bulk copy per 512-byte row through
-// the TMA engine was measured at about 12 SM cycles per row, twice the time
-// of the whole tile with these copies.)
+// of packed candidate points (A, M = 128), both as fp16 rows prepared once per
+// query (below), are multiplied by tcgen05 MMAs (K = 16 per instruction) into a
+// 128 x 32 fp32 accumulator in tensor memory.  The accumulator, the rows'
+// squared norms and a rigorous bound on the fp16 and fp32 rounding give a
+// filter that keeps every edge; kept pairs are decided like the FP32 path: the
+// canonical fp32 direct-difference sum of the original rows (decide32), the
+// pinned FP64 sum where that cannot decide.  The emit pass is the FP32 path's,
+// driven by the same per-block edge masks.
 constexpr int TC_ROWS = 128;
-constexpr int TC_GT = 256;          // threads per group
-constexpr int TC_T = 2 * TC_GT;     // threads per CTA
-constexpr int TC_NB = kItem;        // candidate blocks of one item
-constexpr float TC_REL = 0x1p-8f, TC_ABS2 = 0x1p-12f;
-// |x~| <= |x^| / (1 - 2^-9) and the fp32 sum of the bf16 squares loses at
-// most 2^-18 of |x^|^2: sqrt of that sum times 1 + 2^-7 bounds |x~|
-constexpr float TC_NORM_UP = 1.0f + 0x1p-7f;
+constexpr int TC_NB = kItem;            // candidate blocks of one item
 constexpr uint32_t TC_WAIT = 1u << 22;  // mbarrier polls before a wait gives up
 constexpr int TC_KL = 1024;             // kept pairs rechecked per round
-constexpr int TC_EB = 384;              // edge buffer entries per group (one-pass emit)
 
-struct __align__(128) TcGroup {
-    unsigned char A[TC_ROWS * 256];  // bf16 candidate rows, core-matrix layout
-    float4 P[TC_ROWS * 32];          // fp32 candidate rows: float4 k of row r at r * 32 + (k ^ (r & 7))
-    float pn2[2][TC_ROWS];           // per half row: squared norm of the bf16 values
-    int pos[2][TC_ROWS];             // two map slots (tile t, tile t + 2): tree position of each row
-    uint16_t li[2][TC_ROWS];         //   and its candidate block
-    uint16_t kl[TC_KL];              // kept pairs of the tile: (query << 7) | row
-    // one-pass emit: edges of the current stretch, written out per query in
-    // one slot reservation each
+// ---------------------------------------------------------------------------
+// FP16 rows for the tensor-core filter.  Each cloud's points are stored once
+// per query as x^ = fp16(s fl(x - m)) (m: the column means, s: a power of two
+// with s |x_k - m_k| < 2^14), rows of kp = 16 ceil(dp / 16) halves, zero
+// padded, with n^ = the fp32 sum of their squares.  Rounding to nearest gives
+// |x^_k - s (x_k - m_k)| <= 2^-11 (1 + 2^-10) |x^_k| + 2^-25 (the last for
+// subnormal halves), so with |x^| <= sqrt(n^) (1 + 2^-16) =: a_x
+//   ||x^ - y^|| <= s d(x, y) + rel (a_x + a_y) + 2^-20,  rel = 2^-11 (1 + 2^-8).
+// d^2 = n^_x + n^_y - 2 x^.y^ is formed from exact fp16 products with fp32
+// sums: the MMA's accumulation (K <= 128 terms, below 2^-17 (n^_x + n^_y)),
+// the norms (2^-17 each) and the formula (2^-22) stay below 2^-15.9 (n^_x +
+// n^_y).  A pair is kept iff
+//   d^2 <= (s eps + rel (a_x + a_y) + 2^-20)^2 + 2^-14 (a_x^2 + a_y^2) + 2^-60,
+// which keeps every edge with a 4x margin on the fp32 terms.  The slack
+// relative to eps grows with |x - m| / eps (about 2^-10 of it); rows are
+// copied into the MMA's layout unchanged, so the count pass converts nothing.
+constexpr int H16_MB = 1024;  // blocks of the column-mean partial sums
+constexpr float H16_REL = 0x1.01p-11f, H16_ABS = 0x1p-20f, H16_ABS2 = 0x1p-14f;
+constexpr float H16_NORM_UP = 1.0f + 0x1p-16f;
+
+// Partial column sums: block b adds points b, b + H16_MB, ...; thread k is
+// coordinate k (dp <= 128).
+__global__ void k_col_partial(const float *__restrict__ pts, int64_t n, int dp, float *__restrict__ partial) {
+    const int k = threadIdx.x;
+    if (k >= dp) return;
+    float acc = 0.f;
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) acc += __ldg(pts + i * dp + k);
+    partial[(size_t)blockIdx.x * dp + k] = acc;
+}
+
+// Column means (partials added in block order) and the scale: every point is
+// within r_root of the root centre, so |x_k - m_k| <= |x - m| <= 2 r_root;
+// s = 2^(14 - e) with max(2 r_root, eps) < 2^e.  scal = {s, s eps_up}.
+__global__ void k_col_final(const float *__restrict__ partial, int dp, int64_t n, const float *__restrict__ radius,
+                            float eps_up, float *__restrict__ mean, float *__restrict__ scal) {
+    const int k = threadIdx.x;
+    if (k < dp) {
+        double acc = 0.0;
+        for (int b = 0; b < H16_MB; ++b) acc += (double)partial[(size_t)b * dp + k];
+        mean[k] = n ? (float)(acc / (double)n) : 0.f;
+    }
+    if (k == 0) {
+        const float M = fmaxf(2.0f * radius[0] * (1.0f + 0x1p-10f), eps_up);
+        float s = 0x1p-100f;
+        if (M <= 0x1p100f) {
+            int e;
+            frexpf(fmaxf(M, 0x1p-100f), &e);  // M < 2^e
+            s = ldexpf(1.0f, 14 - e);
+        }
+        scal[0] = s;
+        scal[1] = s * eps_up;
+    }
+}
+
+// Rows in tree order -> fp16 rows and their squared norms; sixteen lanes per
+// row, lane j converts halves 8j .. 8j + 7 (one 16-byte chunk).
+__global__ void k_to_h16(const float *__restrict__ pts, int64_t n, int dp, int kp, const float *__restrict__ mean,
+                         const float *__restrict__ scal, uint4 *__restrict__ h16, float *__restrict__ n16) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = gid >> 4;
+    const int j = (int)(gid & 15), kc = kp >> 3;
+    const float s = scal[0];
+    float sq = 0.f;
+    if (row < n && j < kc) {
+        float v[8];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 8 * j + 4 * h;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f), m = x;
+            if (k < dp) {  // dp is a multiple of 4
+                x = __ldg(reinterpret_cast<const float4 *>(pts + row * dp + k));
+                m = __ldg(reinterpret_cast<const float4 *>(mean + k));
+            }
+            v[4 * h + 0] = (x.x - m.x) * s;
+            v[4 * h + 1] = (x.y - m.y) * s;
+            v[4 * h + 2] = (x.z - m.z) * s;
+            v[4 * h + 3] = (x.w - m.w) * s;
+        }
+        uint32_t w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const __half2 hh = __floats2half2_rn(v[2 * u], v[2 * u + 1]);
+            w[u] = *reinterpret_cast<const uint32_t *>(&hh);
+            const float2 f = __half22float2(hh);
+            sq = fmaf(f.x, f.x, sq);
+            sq = fmaf(f.y, f.y, sq);
+        }
+        h16[row * kc + j] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o, 16);
+    if (j == 0 && row < n) n16[row] = sq;
+}
+
+constexpr int TC_T = 256;   // threads per CTA (two CTAs per SM)
+constexpr int TC_EB = 768;  // edge buffer entries (one-pass emit)
+struct __align__(128) TcShared {
+    unsigned char A[2][TC_ROWS * 256];  // fp16 candidate rows, core-matrix layout, two buffers
+    unsigned char B[32 * 256];          // fp16 query rows
+    float pn[2][TC_ROWS];               // squared norms of the rows
+    int pos[3][TC_ROWS];                // three map slots (tiles t, t + 1, t + 2): tree positions
+    uint16_t li[3][TC_ROWS];            //   and candidate blocks
+    uint16_t kl[TC_KL];                 // kept pairs of the tile: (query << 7) | row
     int ecol[TC_EB];
     float edist[TC_EB];
     uint16_t erank[TC_EB];
     uint8_t eq[TC_EB];
-    int qfill[32], qbase[32];
-    int kn, en;
-    uint64_t mma;
-};
-struct __align__(128) TcShared {
-    TcGroup grp[2];
-    unsigned char B[32 * 256];       // bf16 query rows
-    float4 cen[32];                  // group centre
-    float2 qhg[32];                  // per query: threshold terms (h_q, g_q) of the filter
-    float qpn2[2][32];
+    float2 qhg[32];                     // per query: threshold terms (h_q, g_q) of the filter
     int bbeg[TC_NB], bpre[TC_NB + 1];
     uint32_t bem[TC_NB];
-    int qcnt[32], orig[32];
+    int qcnt[32], orig[32], qfill[32], qbase[32];
     int wsum[TC_T / 32];
+    int kn, en;
     uint32_t tslot;
+    uint64_t mma;
 };
 constexpr size_t kTcSmem = sizeof(TcShared) + 128;
-static_assert(kTcSmem <= 227 * 1024, "k_leaf_tc shared memory above the per-block limit");
-static_assert(TC_NB == TC_T, "block prefix assumes one candidate block per thread");
-static_assert(sizeof(TcGroup) % 128 == 0, "bf16 tiles of both groups stay aligned");
+static_assert(2 * (kTcSmem + 1024) <= 228 * 1024, "k_leaf_tc: two CTAs per SM");
+static_assert(TC_NB == 2 * TC_T, "block prefix assumes two candidate blocks per thread");
 
-// Named barrier of one 8-warp group (ids 1 and 2; id 0 is __syncthreads).
-__device__ __forceinline__ void tc_gbar(int id) {
-    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "n"(TC_GT) : "memory");
-}
-__device__ __forceinline__ bool tc_gbar_and(int id, bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n"
-        ".reg .pred pi, po;\n"
-        "setp.ne.u32 pi, %1, 0;\n"
-        "bar.red.and.pred po, %2, %3, pi;\n"
-        "selp.u32 %0, 1, 0, po;\n"
-        "}\n"
-        : "=r"(r)
-        : "r"((uint32_t)v), "r"(id), "n"(TC_GT)
-        : "memory");
-    return r != 0;
-}
-
-// Converts float4 columns [k0, k1) of one row (fp32; float4 k at row[k ^ sw];
-// columns at or past dp4 and rows that are not valid give zeros) to centred
-// bf16 in the core-matrix layout; returns the partial squared norm of the
-// bf16 values.  k0 and k1 are even, k1 - k0 <= 16.  Loads go eight float4 at a
-// time, each batch's loads before its stores.
-__device__ __forceinline__ void tc_convert_part(unsigned char *tile, int r, const float4 *row, int sw,
-                                                const float4 *cen, int k0, int k1, int dp4, bool valid, float &n2) {
-    unsigned long long bn = 0ull;  // norm in packed pairs (f32x2)
-#pragma unroll
-    for (int b = 0; b < 16; b += 4) {
-        if (k0 + b >= k1) break;
-        float4 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int k = k0 + b + u;
-            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (valid && k < k1 && k < dp4) {
-                const float4 x = row[k ^ sw], c = cen[k];
-                v[u] = make_float4(x.x - c.x, x.y - c.y, x.z - c.z, x.w - c.w);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u += 2) {
-            const int k = k0 + b + u;
-            if (k >= k1) break;
-            const float4 v0 = v[u], v1 = v[u + 1];
-            const __nv_bfloat162 b01 = __floats2bfloat162_rn(v0.x, v0.y), b23 = __floats2bfloat162_rn(v0.z, v0.w);
-            const __nv_bfloat162 b45 = __floats2bfloat162_rn(v1.x, v1.y), b67 = __floats2bfloat162_rn(v1.z, v1.w);
-            uint4 pk;
-            pk.x = *reinterpret_cast<const uint32_t *>(&b01);
-            pk.y = *reinterpret_cast<const uint32_t *>(&b23);
-            pk.z = *reinterpret_cast<const uint32_t *>(&b45);
-            pk.w = *reinterpret_cast<const uint32_t *>(&b67);
-            *reinterpret_cast<uint4 *>(tile + tc::core_offset(r, k >> 1)) = pk;
-            const float2 f01 = __bfloat1622float2(b01), f23 = __bfloat1622float2(b23);
-            const float2 f45 = __bfloat1622float2(b45), f67 = __bfloat1622float2(b67);
-            bn = f2_sqacc(f2_pack(f01.x, f01.y), bn);
-            bn = f2_sqacc(f2_pack(f23.x, f23.y), bn);
-            bn = f2_sqacc(f2_pack(f45.x, f45.y), bn);
-            bn = f2_sqacc(f2_pack(f67.x, f67.y), bn);
-        }
-    }
-    n2 = f2_sum(bn);
-}
-
-__global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Views V, Items items,
-                                                   const uint32_t *__restrict__ cand, uint32_t *__restrict__ emask,
-                                                   int32_t *__restrict__ deg, unsigned long long *__restrict__ st,
-                                                   int32_t *__restrict__ err, CapOut co) {
+// Count pass (and one-pass emit) with the FP16 filter.  One CTA of 8 warps per
+// work item, two CTAs per SM (one's setup and drain overlap the other's
+// tiles).  Tile t + 1 is copied (16-byte cp.async straight into the MMA's
+// core-matrix layout, no conversion) into the second buffer while tile t is
+// multiplied, filtered and rechecked; rechecks read the original fp32 rows
+// from global memory, eight lanes per pair.
+__global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Views V, Items items,
+                                                     const uint32_t *__restrict__ cand, uint32_t *__restrict__ emask,
+                                                     int32_t *__restrict__ deg, unsigned long long *__restrict__ st,
+                                                     int32_t *__restrict__ err, CapOut co) {
     extern __shared__ unsigned char tc_raw[];
     TcShared &S = *reinterpret_cast<TcShared *>(((uintptr_t)tc_raw + 127) & ~(uintptr_t)127);
     const int it = blockIdx.x;
     if (it >= *items.count) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int grp = tid / TC_GT, gt = tid - grp * TC_GT, gw = gt >> 5;  // group, thread and warp in it
-    const int bar = 1 + grp;
-    TcGroup &G = S.grp[grp];
     const int gg = items.group[it];
     const int cloud = cloud_of_group(V, gg);
     const TreeView &tv = V.tv[cloud];
     const QParams &qp = V.qp[cloud];
+    const uint4 *h16 = V.h16[cloud];
+    const float *n16 = V.n16[cloud];
     const int g = gg - V.gbase[cloud];
     const int64_t rbase = V.rbase[cloud];  // CSR rows of this cloud start here
     const int dp = tv.dp, dim = tv.dim, dp4 = dp >> 2;
     const float4 *pts4 = reinterpret_cast<const float4 *>(tv.pts);
     const int ksteps = (dp + 15) >> 4;
-    const int K4 = 4 * ksteps;                       // float4 columns of the MMA's K
-    const int kh = ((K4 >> 1) + 1) & ~1;             // split of a row between two threads (even)
+    const int kc = 2 * ksteps;                       // 16-byte chunks of an fp16 row
     const int qb = tv.group_begin[g], qn = tv.group_count[g];
     const int64_t c0 = items.begin[it];
     const int nb = (int)(items.end[it] - c0);        // <= TC_NB
-    // per-thread counters (32-bit: at most 16 pairs per thread and tile)
-    uint32_t pairs = 0, kept = 0, guard = 0, band = 0, rows_ld = 0;  // rows_ld, kept: gt == 0
+    uint32_t pairs = 0, kept = 0, guard = 0, band = 0, rows_ld = 0;  // rows_ld, kept: thread 0
     bool failed = false;
     uint32_t mph = 0u;
     bool mma_out = false;
 
-    if (warp == 0) tc::tmem_alloc(&S.tslot, 64);
+    if (warp == 0) tc::tmem_alloc(&S.tslot, 32);
     if (tid == 0) {
-        tc::mbar_init(&S.grp[0].mma, 1);
-        tc::mbar_init(&S.grp[1].mma, 1);
+        tc::mbar_init(&S.mma, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (tid < 32) S.cen[tid] = tid < dp4 ? __ldg(pts4 + (size_t)qb * dp4 + tid) : make_float4(0.f, 0.f, 0.f, 0.f);
-    // candidate blocks of the item and their row prefix (one block per thread)
+    // candidate blocks of the item and their row prefix (two blocks per thread)
     {
-        int beg = 0, cnt = 0;
-        if (tid < nb) {
-            const int v = (int)cand[c0 + tid];
-            beg = tv.node_begin[v];
-            cnt = tv.node_count[v];
+        int loc[2], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int i = 2 * tid + k;
+            int beg = 0, cnt = 0;
+            if (i < nb) {
+                const int v = (int)cand[c0 + i];
+                beg = tv.node_begin[v];
+                cnt = tv.node_count[v];
+            }
+            S.bbeg[i] = beg;
+            S.bem[i] = 0u;
+            loc[k] = cnt;
+            sum += cnt;
         }
-        S.bbeg[tid] = beg;
-        S.bem[tid] = 0u;
-        int incl = cnt;
+        int incl = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -1559,44 +1573,52 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Vie
 #pragma unroll
         for (int w = 0; w < TC_T / 32; ++w)
             if (w < warp) base += S.wsum[w];
-        S.bpre[tid] = base + incl - cnt;
-        if (tid == TC_T - 1) S.bpre[TC_NB] = base + incl;
+        int run = base + incl - sum;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            S.bpre[2 * tid + k] = run;
+            run += loc[k];
+        }
+        if (tid == TC_T - 1) S.bpre[TC_NB] = run;
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = S.tslot + (uint32_t)(32 * grp);  // this group's accumulator columns
+    const uint32_t tmem = S.tslot;
     const int T = S.bpre[TC_NB];
     const int ntiles = (T + TC_ROWS - 1) / TC_ROWS;
+    const float s_eps = V.s16[cloud][1];  // s eps_up
 
-    // rows of tile tn -> (position, block) in map slot sl (warps 1-4 of the
-    // group: warp 0 issues the MMAs meanwhile)
-    auto prep_map = [&](int tn, int sl) {
-        const int r = gt - 32, R = tn * TC_ROWS + r;
+    // rows of tile t -> (position, block) in map slot t % 3 (warps 1-4: warp
+    // 0 issues the MMAs meanwhile)
+    auto prep_map = [&](int t) {
+        const int r = tid - 32, R = t * TC_ROWS + r;
         if (r >= 0 && r < TC_ROWS && R < T) {
             int lo = 0, hi = TC_NB;
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
                 if (S.bpre[mid] <= R) lo = mid; else hi = mid;
             }
-            G.pos[sl][r] = S.bbeg[lo] + (R - S.bpre[lo]);
-            G.li[sl][r] = (uint16_t)lo;
+            S.pos[t % 3][r] = S.bbeg[lo] + (R - S.bpre[lo]);
+            S.li[t % 3][r] = (uint16_t)lo;
         }
     };
-    // the group's row copies of tile tn (map slot sl) into its stage,
-    // committed as one group (an empty group past the last tile)
-    // (warp w copies rows w, w + 8, ..., lane per 16 bytes; lane i < 16 reads
-    // the position of the warp's row i)
-    auto issue = [&](int tn, int sl) {
-        if (tn < ntiles) {
-            const int rows = min(TC_ROWS, T - tn * TC_ROWS);
-            const int mine = gw + 8 * (lane & 15);
-            const int mpos = mine < rows ? G.pos[sl][mine] : 0;
+    // tile t into buffer t & 1, committed as one copy group (an empty group
+    // past the last tile): warp w copies 8-row bands w and w + 8, lane l row
+    // (l & 7) of the band, chunks (l >> 3) + 4 i; lanes 0-7 also the norms
+    auto issue = [&](int t) {
+        if (t < ntiles) {
+            const int rows = min(TC_ROWS, T - t * TC_ROWS), sl = t % 3, bf = t & 1;
+            unsigned char *A = S.A[bf];
 #pragma unroll
-            for (int i = 0; i < TC_ROWS / 8; ++i) {
-                const int r = gw + 8 * i;
-                const int pos = __shfl_sync(0xffffffffu, mpos, i);
-                if (r < rows && lane < dp4) cp_async16(&G.P[r * 32 + (lane ^ gw)], pts4 + (size_t)pos * dp4 + lane, true);
+            for (int bnd = 0; bnd < 2; ++bnd) {
+                const int r = 8 * (warp + 8 * bnd) + (lane & 7);
+                if (r < rows) {
+                    const int pos = S.pos[sl][r];
+                    const uint4 *src = h16 + (size_t)pos * kc;
+                    for (int c = lane >> 3; c < kc; c += 4) cp_async16(A + tc::core_offset(r, c), src + c, true);
+                    if (lane < 8) cp_async4(&S.pn[bf][r], n16 + pos);
+                }
             }
         }
         cp_async_commit();
@@ -1608,58 +1630,53 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Vie
         __syncthreads();
         if (tid < 32) {
             S.qcnt[tid] = 0;
+            S.qfill[tid] = 0;
             S.orig[tid] = tid < nqr ? (int)(rbase + tv.perm[qfirst + tid]) : 0;
+            // filter test per query (see the filter)
+            const float qn2 = tid < nqr ? __ldg(n16 + qfirst + tid) : 0.f;
+            const float qa = sqrtf(qn2) * H16_NORM_UP;
+            const float E = fmaf(H16_REL, qa, s_eps) + H16_ABS;
+            const float h = 0.5f * (qn2 - fmaf(E, E, fmaf(H16_ABS2 * qa, qa, 0x1p-60f))) - 0x1p-20f * (E * E);
+            S.qhg[tid] = make_float2(h, -H16_REL * E);
         }
-        if (tid < nb) S.bem[tid] = 0u;
-        if (gt < 32) G.qfill[gt] = 0;
-        if (gt == 0) {
-            G.en = 0;
-            G.kn = 0;
+        for (int i = tid; i < nb; i += TC_T) S.bem[i] = 0u;
+        if (tid == 0) {
+            S.en = 0;
+            S.kn = 0;
         }
-        // queries: bf16 conversion from global memory (two threads per row)
-        if (tid < 64) {
-            const int q = tid & 31, half = tid >> 5;
-            float n2;
-            tc_convert_part(S.B, q, pts4 + (size_t)(qfirst + min(q, nqr - 1)) * dp4, 0, S.cen, half ? kh : 0,
-                            half ? K4 : kh, dp4, q < nqr, n2);
-            S.qpn2[half][q] = n2;
-            tc::fence_smem_to_async();  // B is read by both groups' MMAs
+        // query rows (fp16, zero rows past the group's queries): warp w < 4
+        // rows 8 w .., lane row (l & 7), chunks (l >> 3) + 4 i
+        if (warp < 4) {
+            const int q = 8 * warp + (lane & 7);
+            const uint4 *src = h16 + (size_t)(qfirst + min(q, nqr - 1)) * kc;
+            for (int c = lane >> 3; c < kc; c += 4) cp_async16(S.B + tc::core_offset(q, c), src + c, q < nqr);
         }
-        __syncthreads();
-        if (tid < 32) {
-            // filter test, rearranged per query: keep iff dot >= h_q + g_q |p~| + w_p
-            // (see the kernel's filter)
-            const float qn2 = S.qpn2[0][tid] + S.qpn2[1][tid];
-            const float qa = sqrtf(qn2) * TC_NORM_UP;
-            const float E = fmaf(TC_REL, qa, qp.eps_up);
-            const float h = 0.5f * (qn2 - fmaf(E, E, fmaf(TC_ABS2 * qa, qa, 0x1p-60f))) - 0x1p-20f * (E * E);
-            S.qhg[tid] = make_float2(h, -TC_REL * E);
-        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        tc::fence_smem_to_async();
         __syncthreads();
 
-        // one-pass emit: reserves each query's slots once and writes the
-        // group's buffered edges (the group's threads, between its barriers)
         auto flush = [&]() {
-            if (gt < 32 && G.qfill[gt]) G.qbase[gt] = atomicAdd(&co.fill[S.orig[gt]], G.qfill[gt]);
-            tc_gbar(bar);
-            const int n = min(G.en, TC_EB);
-            for (int i = gt; i < n; i += TC_GT) {
-                const int q = G.eq[i];
-                cap_place(co, S.orig[q], G.qbase[q] + G.erank[i], tv.perm[G.ecol[i]], G.edist[i]);
+            if (tid < 32 && S.qfill[tid]) S.qbase[tid] = atomicAdd(&co.fill[S.orig[tid]], S.qfill[tid]);
+            __syncthreads();
+            const int n = min(S.en, TC_EB);
+            for (int i = tid; i < n; i += TC_T) {
+                const int q = S.eq[i];
+                cap_place(co, S.orig[q], S.qbase[q] + S.erank[i], tv.perm[S.ecol[i]], S.edist[i]);
             }
-            tc_gbar(bar);
-            if (gt < 32) G.qfill[gt] = 0;
-            if (gt == 0) G.en = 0;
+            __syncthreads();
+            if (tid < 32) S.qfill[tid] = 0;
+            if (tid == 0) S.en = 0;
         };
-        // pair e = (query << 7) | row of the tile in map slot sl, by the eight
-        // lanes of an octet: lane j sums coordinate chunk j (16 floats, both rows
-        // from global memory) in the canonical order and the chunk sums are
-        // added in ascending order -- the canonical fp32 sum; the octet's first
-        // lane decides (FP64 where fp32 cannot) and records the edge
+        // pair e = (query << 7) | row in map slot sl, by the eight lanes of an
+        // octet: lane j sums coordinate chunk j (16 floats of both original
+        // rows) in the canonical order, the chunk sums are added in ascending
+        // order -- the canonical fp32 sum; the octet's first lane decides (FP64
+        // where fp32 cannot) and records the edge
         auto recheck8 = [&](int e, int sl) {
             const int q = e >> 7, r = e & 127, sub = lane & 7;
             const unsigned omask = 0xffu << (lane & 24);
-            const int ppos = G.pos[sl][r];
+            const int ppos = S.pos[sl][r];
             const float4 *prow = pts4 + (size_t)ppos * dp4;
             const float4 *qrow = pts4 + (size_t)(qfirst + q) * dp4;
             const int k0 = 4 * sub;
@@ -1708,14 +1725,14 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Vie
             }
             if (is_edge) {
                 atomicAdd(&S.qcnt[q], 1);
-                atomicOr(&S.bem[G.li[sl][r]], 1u << q);
+                atomicOr(&S.bem[S.li[sl][r]], 1u << q);
                 if (co.off) {
-                    const int slot = atomicAdd(&G.en, 1);
+                    const int slot = atomicAdd(&S.en, 1);
                     if (slot < TC_EB) {
-                        G.eq[slot] = (uint8_t)q;
-                        G.ecol[slot] = ppos;  // tree position; the original id is looked up at the flush
-                        G.edist[slot] = d;
-                        G.erank[slot] = (uint16_t)atomicAdd(&G.qfill[q], 1);
+                        S.eq[slot] = (uint8_t)q;
+                        S.ecol[slot] = ppos;  // tree position; the original id is looked up at the flush
+                        S.edist[slot] = d;
+                        S.erank[slot] = (uint16_t)atomicAdd(&S.qfill[q], 1);
                     } else {
                         cap_put(co, S.orig[q], tv.perm[ppos], d);
                     }
@@ -1723,73 +1740,62 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Vie
             }
         };
 
-        // this group's tiles: grp, grp + 2, ...
-        if (grp < ntiles) prep_map(grp, 0);
-        tc_gbar(bar);
-        issue(grp, 0);
-        for (int t = grp; t < ntiles; t += 2) {
-            const int sl = (t >> 1) & 1;
+        prep_map(0);
+        prep_map(1);
+        __syncthreads();
+        issue(0);
+        for (int t = 0; t < ntiles; ++t) {
+            const int sl = t % 3, bf = t & 1;
             const int rows = min(TC_ROWS, T - t * TC_ROWS);
-            if (gt == 0) rows_ld += rows;
-            cp_async_wait<0>();  // this thread's copies of tile t have landed
-            tc_gbar(bar);
-            // bf16 tile from the staged rows (two threads per row)
-            {
-                const int r = gt & (TC_ROWS - 1), half = gt >> 7;
-                float n2;
-                tc_convert_part(G.A, r, G.P + r * 32, r & 7, S.cen, half ? kh : 0, half ? K4 : kh, dp4, r < rows,
-                                n2);
-                G.pn2[half][r] = n2;
-            }
+            if (tid == 0) rows_ld += rows;
+            issue(t + 1);        // into the other buffer (its last MMA has completed)
+            cp_async_wait<1>();  // this thread's copies of tile t have landed
             tc::fence_smem_to_async();
             tc::fence_before_sync();
-            tc_gbar(bar);
+            __syncthreads();
             tc::fence_after_sync();
-            if (gt == 0) {
-                constexpr uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, 32);
-                const uint64_t adesc0 = tc::smem_desc(tc::smem_u32(G.A), tc::kLBO, tc::kSBO);
+            if (tid == 0) {
+                constexpr uint32_t idesc = tc::idesc_f16_f32(TC_ROWS, 32);
+                const uint64_t adesc0 = tc::smem_desc(tc::smem_u32(S.A[bf]), tc::kLBO, tc::kSBO);
                 const uint64_t bdesc0 = tc::smem_desc(tc::smem_u32(S.B), tc::kLBO, tc::kSBO);
                 // one K step is 256 bytes further along both tiles (address field in 16-byte units)
                 for (int ks = 0; ks < ksteps; ++ks)
-                    tc::mma_bf16(tmem, adesc0 + (uint64_t)(ks * 16), bdesc0 + (uint64_t)(ks * 16), idesc, ks > 0);
-                tc::mma_commit(&G.mma);
+                    tc::mma_f16(tmem, adesc0 + (uint64_t)(ks * 16), bdesc0 + (uint64_t)(ks * 16), idesc, ks > 0);
+                tc::mma_commit(&S.mma);
             }
             mma_out = true;
-            if (t + 2 < ntiles) prep_map(t + 2, sl ^ 1);
-            tc_gbar(bar);   // stage consumed, map of tile t + 2 ready
-            issue(t + 2, sl ^ 1);
-            bool mok = true;  // warp 0 of the group waits, the barrier releases the others
-            if (gw == 0) mok = tc::mbar_wait(&G.mma, mph, TC_WAIT);
-            if (!tc_gbar_and(bar, mok)) {
-                if (gt == 0) atomicOr(err, 32);
+            prep_map(t + 2);
+            bool mok = true;  // warp 0 waits, the barrier releases the others
+            if (warp == 0) mok = tc::mbar_wait(&S.mma, mph, TC_WAIT);
+            if (!__syncthreads_and(mok)) {
+                if (tid == 0) atomicOr(err, 32);
                 failed = true;
                 break;
             }
             mph ^= 1u;
             mma_out = false;
             tc::fence_after_sync();
-            // epilogue, filter: warp w of the group reads rows 32 (w % 4) .. + 31,
-            // queries 16 (w / 4) .. + 15; kept pairs go to the tile's list
+            // epilogue, filter: warp w reads rows 32 (w % 4) .. + 31, queries
+            // 16 (w / 4) .. + 15; kept pairs go to the tile's list
             uint32_t keepm = 0u;
             int kb = 0;
             {
-                const int quarter = gw & 3, qh = gw >> 2;
+                const int quarter = warp & 3, qh = warp >> 2;
                 float dot[16];
                 tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(16 * qh), dot);
                 const int r = 32 * quarter + lane;
                 if (r < rows) {
-                    // kept iff d^2 = |q^|^2 + |p^|^2 - 2 dot <= (E_q + 2^-8 |p~|)^2
-                    // + 2^-12 (|q~|^2 + |p~|^2) + 2^-60 with E_q = eps + 2^-8 |q~|, i.e.
-                    // iff dot >= h_q + g_q |p~| + w_p with h_q = (|q^|^2 - E_q^2 - 2^-12 |q~|^2
-                    // - 2^-60) / 2, g_q = -2^-8 E_q, w_p = (|p^|^2 - (2^-16 + 2^-12) |p~|^2) / 2.
-                    // The rounding of this form stays below 2^-21 (|q^|^2 + |p^|^2 + 2 E_q^2):
-                    // the first part is inside the 2^-12 term's slack over the MMA's
-                    // accumulation error (below 2^-17 (|q^|^2 + |p^|^2)), the second is
-                    // covered by the 2^-20 E_q^2 taken off h_q.  NaN keeps the pair.
-                    const int ppos = G.pos[sl][r];
-                    const float pn = G.pn2[0][r] + G.pn2[1][r];
-                    const float pa = sqrtf(pn) * TC_NORM_UP;
-                    const float wp = 0.5f * fmaf(-(TC_REL * TC_REL + TC_ABS2) * pa, pa, pn);
+                    // kept iff d^2 = n^_q + n^_p - 2 dot <= (E_q + rel |p^|)^2 + abs2 (|q^|^2 + |p^|^2)
+                    // + 2^-60 with E_q = s eps + rel |q^| + 2^-20, i.e. iff dot >= h_q + g_q |p^| + w_p
+                    // with h_q = (n^_q - E_q^2 - abs2 |q^|^2 - 2^-60) / 2, g_q = -rel E_q,
+                    // w_p = (n^_p - (rel^2 + abs2) |p^|^2) / 2.  The rounding of this form stays
+                    // below 2^-21 (n^_q + n^_p + 2 E_q^2): the first part is inside the abs2
+                    // term's slack over the other fp32 errors, the second is covered by the
+                    // 2^-20 E_q^2 taken off h_q.  NaN keeps the pair.
+                    const int ppos = S.pos[sl][r];
+                    const float pn = S.pn[bf][r];
+                    const float pa = sqrtf(pn) * H16_NORM_UP;
+                    const float wp = 0.5f * fmaf(-(H16_REL * H16_REL + H16_ABS2) * pa, pa, pn);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const float2 hg = S.qhg[16 * qh + j];
@@ -1809,47 +1815,48 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Vie
                     if (lane >= o) incl += y;
                 }
                 int base = 0;
-                if (lane == 31 && incl) base = atomicAdd(&G.kn, incl);
+                if (lane == 31 && incl) base = atomicAdd(&S.kn, incl);
                 kb = __shfl_sync(0xffffffffu, base, 31) + incl - c;
                 uint32_t m = keepm;
                 for (int idx = kb; m && idx < TC_KL; ++idx) {
                     const int j = __ffs(m) - 1;
                     m &= m - 1u;
-                    G.kl[idx] = (uint16_t)(((16 * qh + j) << 7) | r);
+                    S.kl[idx] = (uint16_t)(((16 * qh + j) << 7) | r);
                 }
             }
-            tc_gbar(bar);
-            // epilogue, recheck: the kept pairs spread over the group's lane
-            // octets, one pair per octet, TC_KL at a time
+            __syncthreads();
+            // epilogue, recheck: the kept pairs spread over the lane octets, one
+            // pair per octet, TC_KL at a time
             {
-                const int n = G.kn;
-                if (gt == 0) kept += n;
-                for (int i = gt >> 3; i < min(n, TC_KL); i += TC_GT / 8) recheck8(G.kl[i], sl);
+                const int n = S.kn;
+                if (tid == 0) kept += n;
+                for (int i = tid >> 3; i < min(n, TC_KL); i += TC_T / 8) recheck8(S.kl[i], sl);
                 for (int lo = TC_KL; lo < n; lo += TC_KL) {
-                    tc_gbar(bar);
+                    __syncthreads();
                     uint32_t m = keepm;
-                    const int qc = 16 * (gw >> 2), r = 32 * (gw & 3) + lane;
+                    const int qc = 16 * (warp >> 2), r = 32 * (warp & 3) + lane;
                     for (int idx = kb; m && idx < lo + TC_KL; ++idx) {
                         const int j = __ffs(m) - 1;
                         m &= m - 1u;
-                        if (idx >= lo) G.kl[idx - lo] = (uint16_t)(((qc + j) << 7) | r);
+                        if (idx >= lo) S.kl[idx - lo] = (uint16_t)(((qc + j) << 7) | r);
                     }
-                    tc_gbar(bar);
-                    for (int i = gt >> 3; i < min(n - lo, TC_KL); i += TC_GT / 8) recheck8(G.kl[i], sl);
+                    __syncthreads();
+                    for (int i = tid >> 3; i < min(n - lo, TC_KL); i += TC_T / 8) recheck8(S.kl[i], sl);
                 }
             }
             tc::fence_before_sync();
-            tc_gbar(bar);
+            __syncthreads();
             tc::fence_after_sync();
-            if (gt == 0) G.kn = 0;
-            if (co.off && G.en >= TC_EB / 2) flush();
+            if (tid == 0) S.kn = 0;
+            if (co.off && S.en >= TC_EB / 2) flush();
         }
-        if (!failed && co.off) flush();
-        failed = __syncthreads_or(failed);
         if (failed) break;
+        if (co.off) flush();
+        __syncthreads();
         if (tid < nqr && S.qcnt[tid]) atomicAdd(&deg[S.orig[tid]], S.qcnt[tid]);
     }
-    if (!failed && emask && tid < nb) emask[c0 + tid] = qn <= 32 ? S.bem[tid] : ~0u;
+    if (!failed && emask)
+        for (int i = tid; i < nb; i += TC_T) emask[c0 + i] = qn <= 32 ? S.bem[i] : ~0u;
     unsigned long long pairs64 = pairs, kept64 = kept, guard64 = guard, band64 = band;
     for (int o = 16; o > 0; o >>= 1) {
         pairs64 += __shfl_xor_sync(0xffffffffu, pairs64, o);
@@ -1862,14 +1869,14 @@ __global__ void __launch_bounds__(TC_T, 1) k_leaf_tc(const __grid_constant__ Vie
         stat_add(st, ST_RECHECK, kept64);
         stat_add(st, ST_GUARD, guard64);
         stat_add(st, ST_BAND, band64);
-        if (gt == 0) stat_add(st, ST_ROWS, rows_ld);
+        if (tid == 0) stat_add(st, ST_ROWS, rows_ld);
     }
     cp_async_wait<0>();  // no copy into this CTA's shared memory outlives it
-    if (failed && mma_out) tc::mbar_wait(&G.mma, mph, TC_WAIT);  // let an outstanding MMA finish
+    if (failed && mma_out) tc::mbar_wait(&S.mma, mph, TC_WAIT);  // let an outstanding MMA finish
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(S.tslot, 64);
+    if (warp == 0) tc::tmem_dealloc(tmem, 32);
 }
 
 // Dynamic shared memory of the L2 leaf kernel (set once per process).
@@ -2372,8 +2379,8 @@ void launch_traversal(const Views &V, int64_t G, int max_dp, int max_len, bool l
     CT_LAUNCH_CHECK();
 }
 
-// Leaf kernel and item length per cloud.  precision 0: FP32 tiles; 1: BF16
-// tiles where the rows allow (L2, at most 128 floats); 2: the autotuned
+// Leaf kernel and item length per cloud.  precision 0: FP32 tiles; 1: tensor-
+// core tiles where the rows allow (L2, at most 128 floats); 2: the autotuned
 // choice of the cloud's row-length class (a default until tuned).
 std::mutex g_tune_mu;
 LeafChoice g_tune[kDpClasses] = {{-1, kItem}, {-1, kItem}, {-1, kItem}, {-1, kItem}, {-1, kItem}, {-1, kItem}};
@@ -2447,6 +2454,36 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
         max_len = std::max(max_len, tc->max_len);
     }
     if (V.rbase[C] >= 0x7fffffffLL) CT_FAIL(CT_EOVERFLOW, "a batch above 2^31 points");
+    // fp16 rows of the clouds that take the tensor-core filter
+    std::vector<DBuf<uint4>> h16s;
+    std::vector<DBuf<float>> f16s;
+    if (any_tc) {
+        ProfScope ps("rows_f16", s);
+        DBuf<float> partial;
+        for (int c = 0; c < C; ++c) {
+            if (!V.use_tc[c]) continue;
+            const ct_tree *tc = trees[c];
+            const int64_t nc = tc->n;
+            if (nc == 0) continue;  // no work items
+            const int dp = tc->dp, kp = 16 * ((dp + 15) / 16);
+            h16s.emplace_back((size_t)nc * (kp / 8), s);
+            f16s.emplace_back((size_t)dp + 4 + nc, s);  // means (dp: a multiple of 4), {s, s eps_up}, norms
+            float *mean = f16s.back().p, *scal = mean + dp, *nrm = scal + 4;
+            partial.grow((size_t)H16_MB * dp);
+            k_col_partial<<<H16_MB, 128, 0, s>>>(tc->pts, nc, dp, partial.p);
+            CT_COUNT_LAUNCH();
+            CT_LAUNCH_CHECK();
+            k_col_final<<<1, 128, 0, s>>>(partial.p, dp, nc, tc->radius, V.qp[c].eps_up, mean, scal);
+            CT_COUNT_LAUNCH();
+            CT_LAUNCH_CHECK();
+            k_to_h16<<<grid_for(nc * 16, 256), 256, 0, s>>>(tc->pts, nc, dp, kp, mean, scal, h16s.back().p, nrm);
+            CT_COUNT_LAUNCH();
+            CT_LAUNCH_CHECK();
+            V.h16[c] = h16s.back().p;
+            V.n16[c] = nrm;
+            V.s16[c] = scal;
+        }
+    }
     const int64_t n = V.rbase[C];
     const int G = V.gbase[C];
     const ct_tree *t = trees[0];  // edit distance: the only cloud
@@ -2623,11 +2660,9 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
         CT_COUNT_LAUNCH();
         CT_LAUNCH_CHECK();
     };
-    // the tensor-core filter applies to L2 rows of at most 128 floats; wider
-    // rows use the FP32 tiles (same output)
-    // each cloud's count kernel: BF16 tensor-core tiles (L2 rows of at most
-    // 128 floats) or FP32 tiles -- the same output; a mixed batch splits its
-    // work items between the two launches
+    // each cloud's count kernel: tensor-core tiles (L2 rows of at most 128
+    // floats) or FP32 tiles -- the same output; a mixed batch splits its work
+    // items between the two launches
     auto count_tc = [&](const Items &its) {
         ProfScope ps("leaf_count_tc", s);
         static bool tc_ready = false;

@@ -76,7 +76,7 @@ struct LearnedPlan {
 void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStream_t s, QueryOut *outs,
                  int precision, const ct_predictor *P, Probe *probe);
 constexpr int kBatchClouds = 64;
-// Count-pass kernel (1: BF16 tensor-core tiles, 0: FP32 tiles) and work-item
+// Count-pass kernel (1: tensor-core tiles, 0: FP32 tiles) and work-item
 // length of a cloud; autotuned per class of row length (dp <= 4, 16, 32, 64,
 // 128, wider).
 struct LeafChoice {

@@ -1,6 +1,6 @@
-// tc.cu -- tensor-core self-test: one BF16 MMA chain (M = 128, N = 32,
-// K = 128) through shared-memory descriptors and tensor memory, the primitive
-// of the precision-1 leaf filter.
+// tc.cu -- tensor-core self-test: one kind::f16 MMA chain (M = 128, N = 32,
+// K = 128; bf16 or fp16 operands) through shared-memory descriptors and tensor
+// memory, the primitive of the precision-1 leaf filter.
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -8,7 +8,7 @@ namespace ct {
 namespace {
 
 __global__ void __launch_bounds__(128) k_tc_selftest(const uint16_t *__restrict__ A, const uint16_t *__restrict__ B,
-                                                     float *__restrict__ D, int32_t *__restrict__ status) {
+                                                     int fp16, float *__restrict__ D, int32_t *__restrict__ status) {
     __shared__ __align__(1024) unsigned char sA[128 * 256];
     __shared__ __align__(1024) unsigned char sB[32 * 256];
     __shared__ uint32_t tslot;
@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const uint16_t *__restrict_
     tc::fence_after_sync();
     const uint32_t tmem = tslot;
     if (tid == 0) {
-        const uint32_t idesc = tc::idesc_bf16_f32(128, 32);
+        const uint32_t idesc = fp16 ? tc::idesc_f16_f32(128, 32) : tc::idesc_bf16_f32(128, 32);
         for (int s = 0; s < 8; ++s) {
             const uint64_t ad = tc::smem_desc(tc::smem_u32(sA) + s * 256, tc::kLBO, tc::kSBO);
             const uint64_t bd = tc::smem_desc(tc::smem_u32(sB) + s * 256, tc::kLBO, tc::kSBO);
@@ -58,10 +58,10 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const uint16_t *__restrict_
 
 }  // namespace
 
-void tc_selftest(const void *A, const void *B, float *D, cudaStream_t s) {
+void tc_selftest(const void *A, const void *B, int fp16, float *D, cudaStream_t s) {
     DBuf<int32_t> status(1, s);
     CT_CHECK_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int32_t), s));
-    k_tc_selftest<<<1, 128, 0, s>>>((const uint16_t *)A, (const uint16_t *)B, D, status.p);
+    k_tc_selftest<<<1, 128, 0, s>>>((const uint16_t *)A, (const uint16_t *)B, fp16, D, status.p);
     CT_COUNT_LAUNCH();
     CT_LAUNCH_CHECK();
     int32_t h = 0;

@@ -41,6 +41,13 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
            | ((uint32_t)(M >> 4) << 24);    // M / 16
 }
 
+// Instruction descriptor of kind::f16: D fp32, A and B fp16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+    return (1u << 4)                        // D format: f32
+           | ((uint32_t)(N >> 3) << 17)     // N / 8 (A, B format 0: f16)
+           | ((uint32_t)(M >> 4) << 24);    // M / 16
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t *slot_smem, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(slot_smem)),
                  "r"(ncols));
@@ -65,6 +72,12 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
         "}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate));
+}
+
+// The same instruction with fp16 operands (the types are in the instruction descriptor).
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        bool accumulate) {
+    mma_bf16(d_tmem, adesc, bdesc, idesc, accumulate);
 }
 
 // Arrives on the mbarrier when the MMAs issued so far by this thread complete.

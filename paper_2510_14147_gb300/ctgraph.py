@@ -117,7 +117,7 @@ def _load():
         lib.eps_graph_degrees_noalloc.restype = C.c_int
         lib.eps_graph_degrees_noalloc.argtypes = [C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p]
         lib.ct_selftest_tc_gemm.restype = C.c_int
-        lib.ct_selftest_tc_gemm.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.ct_selftest_tc_gemm.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]
         lib.ct_kernel_launches.restype = C.c_int64
         lib.ct_kernel_launches.argtypes = []
         lib.ct_autotune.restype = C.c_int
@@ -334,7 +334,7 @@ def eps_graph_query_batched(trees, eps, precision: int = 0, use_predictor: bool 
 def ct_autotune(trees, eps, use_predictor: bool = False, include_self: bool = False, predictor=None,
                 stream=None):
     """Tunes precision 2 on these clouds; returns each cloud's count kernel
-    (1: BF16 tensor-core tiles, 0: FP32 tiles)."""
+    (1: tensor-core tiles, 0: FP32 tiles)."""
     k = len(trees)
     arr = (C.c_void_p * max(k, 1))(*[t.handle.value for t in trees])
     ea = (C.c_double * max(k, 1))(*[float(e) for e in eps])
@@ -410,15 +410,17 @@ def ct_kernel_launches() -> int:
 
 
 def ct_selftest_tc_gemm(A, B, stream=None):
-    """D = A @ B.T through one tcgen05 BF16 MMA chain: A (128, 128) and B (32, 128)
-    CUDA bfloat16 tensors; returns D (128, 32) float32."""
+    """D = A @ B.T through one tcgen05 kind::f16 MMA chain: A (128, 128) and
+    B (32, 128) CUDA tensors, both bfloat16 or both float16; returns D (128, 32)
+    float32."""
     import torch
-    if not (A.shape == (128, 128) and B.shape == (32, 128) and A.dtype == torch.bfloat16
-            and B.dtype == torch.bfloat16 and A.is_cuda and B.is_cuda):
-        raise ValueError("A must be (128, 128) and B (32, 128) CUDA bfloat16")
+    if not (A.shape == (128, 128) and B.shape == (32, 128) and A.dtype == B.dtype
+            and A.dtype in (torch.bfloat16, torch.float16) and A.is_cuda and B.is_cuda):
+        raise ValueError("A must be (128, 128) and B (32, 128) CUDA tensors, both bfloat16 or both float16")
     A, B = A.contiguous(), B.contiguous()
     D = torch.empty(128, 32, dtype=torch.float32, device=A.device)
-    _check(_load().ct_selftest_tc_gemm(A.data_ptr(), B.data_ptr(), D.data_ptr(), C.c_void_p(_stream(stream))))
+    f16 = 1 if A.dtype == torch.float16 else 0
+    _check(_load().ct_selftest_tc_gemm(A.data_ptr(), B.data_ptr(), f16, D.data_ptr(), C.c_void_p(_stream(stream))))
     return D
 
 

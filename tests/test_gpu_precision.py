@@ -1,4 +1,4 @@
-"""Precision form (precision=1): BF16 tensor-core filter, FP32 recheck, FP64
+"""Precision form (precision=1): tensor-core filter (fp16 rows), FP32 recheck, FP64
 guard band.  Same edge set as the oracle (and as precision 0), bit for bit."""
 import itertools
 import math
@@ -102,3 +102,30 @@ def test_precision1_full_size_sampled(key):
            "dist": np.concatenate([out["dist"][rp[r]:rp[r + 1]] for r in rows])}
     assert_csr_matches(sub, ref)
     assert out["stats"]["recheck_fp32"] < out["stats"]["leaf_pairs"] // 4
+
+
+@pytest.mark.parametrize("scale", [1e-12, 1.0, 1e12])
+def test_precision1_coordinate_scales(scale):
+    """The fp16 rows are centred on the column means and scaled by a power of
+    two chosen from the root radius and eps: tiny and huge coordinates give
+    the oracle's graph."""
+    base = I.gmm_embedded(1500, dim=40, intrinsic=5, n_centres=3, seed=21).astype(np.float64)
+    x = (base * scale + 7.0 * scale).astype(np.float32)
+    sp = oracle.Space(points=x)
+    sample = oracle.brute_rows(sp, 1e30, [0, 1, 2])["dist"]
+    eps = float(np.float32(np.quantile(sample[sample > 0], 0.03)))
+    assert_csr_matches(gpu_graph(points=x, eps=eps, precision=1), oracle.brute_force(sp, eps))
+
+
+def test_precision1_wide_extent():
+    """Points spread far beyond eps from the column means (the fp16 filter's
+    slack grows with |x - m| / eps): the filter keeps more pairs, the graph is
+    still the oracle's."""
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.uniform(-2000, 2000, (1500, 32)),
+                        rng.standard_normal((1500, 32)) * 0.05 + 1500.0]).astype(np.float32)
+    sp = oracle.Space(points=x)
+    for eps in (0.4, 2.0):
+        out = gpu_graph(points=x, eps=eps, precision=1)
+        assert_csr_matches(out, oracle.brute_force(sp, eps))
+        assert out["row_ptr"][-1] > 0
