@@ -550,7 +550,7 @@ def main():
         # (~250 flop/B): the tiles are bound by streaming the candidate rows
         # (and the original rows of the kept pairs), so the roofline is HBM
         t_launch = prof["leaf_count_tc"][0] / prof["leaf_count_tc"][1] / 1e3
-        kp = 16 * ((((wl["dim"] + 3) // 4) * 4 + 15) // 16)  # fp16 row length (dp rounded up to 16)
+        kp = 64 * ((((wl["dim"] + 3) // 4) * 4 + 63) // 64)  # fp16 row length (dp rounded up to 64)
         nbytes = st["leaf_rows"] * (2.0 * kp + 4.0) + st["recheck_fp32"] * 4.0 * wl["dim"]
         hbm = peaks.get("hbm_gbs", 6800.0)
         ach = nbytes / t_launch / 1e9
@@ -559,7 +559,7 @@ def main():
                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)" if peaks else "fallback 6.8 TB/s",
                 "bytes_per_launch": nbytes,
                 "bytes_rule": "leaf_rows x (2 kp + 4) B (fp16 candidate rows and norms, kp = dim rounded "
-                              "up to 16) + recheck_fp32 x dim x 4 B (original candidate rows of kept pairs)",
+                              "up to 64) + recheck_fp32 x dim x 4 B (original candidate rows of kept pairs)",
                 "ms_per_launch": t_launch * 1e3, "tensor_flops_per_launch": st["leaf_pairs"] * 2.0 * kp,
                 "tensor_frac_of_sustained_f16": st["leaf_pairs"] * 2.0 * kp / t_launch / 1e12
                 / peaks.get("bf16_tflops_sustained", 1700.0),

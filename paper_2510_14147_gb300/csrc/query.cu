@@ -21,6 +21,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <cuda.h>
 #include <mutex>
 
 #include "lev.cuh"
@@ -133,11 +134,12 @@ struct Views {
     QParams qp[kMaxClouds];
     int16_t item_len[kMaxClouds];  // candidate blocks per work item
     uint8_t use_tc[kMaxClouds];    // leaf kernel of the count pass: tensor-core tiles (1) or FP32 tiles (0)
-    // tensor-core filter rows (FP16 form): fp16 rows, their squared norms, {s, s eps_up}
-    const uint4 *h16[kMaxClouds];
+    // tensor-core filter rows: a TMA map of the fp16 rows, their squared norms, {s, s eps_up}
     const float *n16[kMaxClouds];
     const float *s16[kMaxClouds];
+    CUtensorMap tmap[kMaxClouds];  // (a 128-byte aligned type)
 };
+static_assert(sizeof(Views) <= 32000, "Views exceeds the kernel parameter space");
 __device__ __forceinline__ int cloud_of_group(const Views &V, int gg) {
     int lo = 0, hi = V.nc;
     while (hi - lo > 1) {
@@ -537,9 +539,6 @@ __device__ __forceinline__ unsigned long long f2_sqacc(unsigned long long d, uns
     unsigned long long r;
     asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(d), "l"(acc));
     return r;
-}
-__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
-    return ((unsigned long long)__float_as_uint(hi) << 32) | (unsigned long long)__float_as_uint(lo);
 }
 __device__ __forceinline__ float f2_sum(unsigned long long v) {
     return __uint_as_float((uint32_t)v) + __uint_as_float((uint32_t)(v >> 32));
@@ -1387,7 +1386,7 @@ constexpr int TC_KL = 1024;             // kept pairs rechecked per round
 // ---------------------------------------------------------------------------
 // FP16 rows for the tensor-core filter.  Each cloud's points are stored once
 // per query as x^ = fp16(s fl(x - m)) (m: the column means, s: a power of two
-// with s |x_k - m_k| < 2^14), rows of kp = 16 ceil(dp / 16) halves, zero
+// with s |x_k - m_k| < 2^14), rows of kp = 64 ceil(dp / 64) halves, zero
 // padded, with n^ = the fp32 sum of their squares.  Rounding to nearest gives
 // |x^_k - s (x_k - m_k)| <= 2^-11 (1 + 2^-10) |x^_k| + 2^-25 (the last for
 // subnormal halves), so with |x^| <= sqrt(n^) (1 + 2^-16) =: a_x
@@ -1480,42 +1479,43 @@ __global__ void k_to_h16(const float *__restrict__ pts, int64_t n, int dp, int k
 
 constexpr int TC_T = 256;   // threads per CTA (two CTAs per SM)
 constexpr int TC_EB = 768;  // edge buffer entries (one-pass emit)
-struct __align__(128) TcShared {
-    unsigned char A[2][TC_ROWS * 256];  // fp16 candidate rows, core-matrix layout, two buffers
-    unsigned char B[32 * 256];          // fp16 query rows
-    float pn[2][TC_ROWS];               // squared norms of the rows
-    int pos[3][TC_ROWS];                // three map slots (tiles t, t + 1, t + 2): tree positions
-    uint16_t li[3][TC_ROWS];            //   and candidate blocks
-    uint16_t kl[TC_KL];                 // kept pairs of the tile: (query << 7) | row
+struct __align__(1024) TcShared {
+    unsigned char A[2][2][TC_ROWS * 128];  // fp16 candidate rows: buffer, K half (64 halves), 128-byte swizzle
+    unsigned char B[2][32 * 128];          // fp16 query rows, the same layout
+    float pn[4][TC_ROWS];                  // squared norms of the rows, per map slot
+    int pos[4][TC_ROWS];                   // map slots of tiles t .. t + 3 (slot t & 3): tree positions
+    uint16_t li[4][TC_ROWS];               //   and candidate blocks
+    uint16_t kl[TC_KL];                    // kept pairs of the tile: (query << 7) | row
     int ecol[TC_EB];
     float edist[TC_EB];
     uint16_t erank[TC_EB];
     uint8_t eq[TC_EB];
-    float2 qhg[32];                     // per query: threshold terms (h_q, g_q) of the filter
+    float2 qhg[32];                        // per query: threshold terms (h_q, g_q) of the filter
     int bbeg[TC_NB], bpre[TC_NB + 1];
     uint32_t bem[TC_NB];
     int qcnt[32], orig[32], qfill[32], qbase[32];
     int wsum[TC_T / 32];
-    int kn, en;
+    int kn[2], en;
     uint32_t tslot;
-    uint64_t mma;
+    uint64_t lbar[2], mbar[2], bbar;       // tile loads, MMAs (per buffer), query rows
 };
-constexpr size_t kTcSmem = sizeof(TcShared) + 128;
+constexpr size_t kTcSmem = sizeof(TcShared) + 1024;
 static_assert(2 * (kTcSmem + 1024) <= 228 * 1024, "k_leaf_tc: two CTAs per SM");
 static_assert(TC_NB == 2 * TC_T, "block prefix assumes two candidate blocks per thread");
 
 // Count pass (and one-pass emit) with the FP16 filter.  One CTA of 8 warps per
 // work item, two CTAs per SM (one's setup and drain overlap the other's
-// tiles).  Tile t + 1 is copied (16-byte cp.async straight into the MMA's
-// core-matrix layout, no conversion) into the second buffer while tile t is
-// multiplied, filtered and rechecked; rechecks read the original fp32 rows
-// from global memory, eight lanes per pair.
+// tiles).  Candidate rows arrive by TMA gathers (four rows per instruction,
+// 128-byte swizzle, straight into the MMA's operand layout; lane 0 of each
+// warp issues its 16 rows) two tiles ahead; the MMA of tile t + 1 (second
+// accumulator) runs while tile t is filtered and rechecked.  Rechecks read
+// the original fp32 rows from global memory, eight lanes per pair.
 __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Views V, Items items,
                                                      const uint32_t *__restrict__ cand, uint32_t *__restrict__ emask,
                                                      int32_t *__restrict__ deg, unsigned long long *__restrict__ st,
                                                      int32_t *__restrict__ err, CapOut co) {
     extern __shared__ unsigned char tc_raw[];
-    TcShared &S = *reinterpret_cast<TcShared *>(((uintptr_t)tc_raw + 127) & ~(uintptr_t)127);
+    TcShared &S = *reinterpret_cast<TcShared *>(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
     const int it = blockIdx.x;
     if (it >= *items.count) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1523,25 +1523,33 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
     const int cloud = cloud_of_group(V, gg);
     const TreeView &tv = V.tv[cloud];
     const QParams &qp = V.qp[cloud];
-    const uint4 *h16 = V.h16[cloud];
+    const void *tmap = &V.tmap[cloud];
     const float *n16 = V.n16[cloud];
     const int g = gg - V.gbase[cloud];
     const int64_t rbase = V.rbase[cloud];  // CSR rows of this cloud start here
     const int dp = tv.dp, dim = tv.dim, dp4 = dp >> 2;
     const float4 *pts4 = reinterpret_cast<const float4 *>(tv.pts);
-    const int ksteps = (dp + 15) >> 4;
-    const int kc = 2 * ksteps;                       // 16-byte chunks of an fp16 row
+    const int halves = (dp + 63) >> 6;               // 64-half K blocks of an fp16 row (1 or 2)
+    const int ksteps = 4 * halves;                   // MMA K steps of 16
+    const uint32_t tile_bytes = (uint32_t)(TC_ROWS * 128 * halves), q_bytes = (uint32_t)(32 * 128 * halves);
     const int qb = tv.group_begin[g], qn = tv.group_count[g];
     const int64_t c0 = items.begin[it];
     const int nb = (int)(items.end[it] - c0);        // <= TC_NB
     uint32_t pairs = 0, kept = 0, guard = 0, band = 0, rows_ld = 0;  // rows_ld, kept: thread 0
     bool failed = false;
-    uint32_t mph = 0u;
-    bool mma_out = false;
+    // next phase parity of each barrier (bit b: buffer b): mph in every thread
+    // (warp 0 waits), lph and bph in thread 0 (it waits); thread 0 also tracks
+    // what is in flight, for a clean exit after a failure
+    uint32_t lph = 0u, mph = 0u, bph = 0u, lpend = 0u, mpend = 0u, bpend = 0u;
+    bool tok = true;  // thread 0: its own waits succeeded
 
-    if (warp == 0) tc::tmem_alloc(&S.tslot, 32);
+    if (warp == 0) tc::tmem_alloc(&S.tslot, 64);
     if (tid == 0) {
-        tc::mbar_init(&S.mma, 1);
+        tc::mbar_init(&S.lbar[0], 1);
+        tc::mbar_init(&S.lbar[1], 1);
+        tc::mbar_init(&S.mbar[0], 1);
+        tc::mbar_init(&S.mbar[1], 1);
+        tc::mbar_init(&S.bbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     // candidate blocks of the item and their row prefix (two blocks per thread)
@@ -1589,39 +1597,52 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
     const int ntiles = (T + TC_ROWS - 1) / TC_ROWS;
     const float s_eps = V.s16[cloud][1];  // s eps_up
 
-    // rows of tile t -> (position, block) in map slot t % 3 (warps 1-4: warp
-    // 0 issues the MMAs meanwhile)
+    // rows of tile t -> (position, block) in map slot t & 3 and the rows'
+    // norms (4-byte copies; each thread commits one copy group per call).
+    // Warps 1-4: warp 0 issues the MMAs.
     auto prep_map = [&](int t) {
         const int r = tid - 32, R = t * TC_ROWS + r;
-        if (r >= 0 && r < TC_ROWS && R < T) {
+        if (t < ntiles && r >= 0 && r < TC_ROWS && R < T) {
             int lo = 0, hi = TC_NB;
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
                 if (S.bpre[mid] <= R) lo = mid; else hi = mid;
             }
-            S.pos[t % 3][r] = S.bbeg[lo] + (R - S.bpre[lo]);
-            S.li[t % 3][r] = (uint16_t)lo;
-        }
-    };
-    // tile t into buffer t & 1, committed as one copy group (an empty group
-    // past the last tile): warp w copies 8-row bands w and w + 8, lane l row
-    // (l & 7) of the band, chunks (l >> 3) + 4 i; lanes 0-7 also the norms
-    auto issue = [&](int t) {
-        if (t < ntiles) {
-            const int rows = min(TC_ROWS, T - t * TC_ROWS), sl = t % 3, bf = t & 1;
-            unsigned char *A = S.A[bf];
-#pragma unroll
-            for (int bnd = 0; bnd < 2; ++bnd) {
-                const int r = 8 * (warp + 8 * bnd) + (lane & 7);
-                if (r < rows) {
-                    const int pos = S.pos[sl][r];
-                    const uint4 *src = h16 + (size_t)pos * kc;
-                    for (int c = lane >> 3; c < kc; c += 4) cp_async16(A + tc::core_offset(r, c), src + c, true);
-                    if (lane < 8) cp_async4(&S.pn[bf][r], n16 + pos);
-                }
-            }
+            const int pos = S.bbeg[lo] + (R - S.bpre[lo]);
+            S.pos[t & 3][r] = pos;
+            S.li[t & 3][r] = (uint16_t)lo;
+            cp_async4(&S.pn[t & 3][r], n16 + pos);
         }
         cp_async_commit();
+    };
+    // lane 0 of warp w: tile t's rows 16 w .. 16 w + 15 (past the last row of
+    // a short tile: row 0 again) into buffer t & 1, completing on lbar[t & 1]
+    auto issue_tile = [&](int t) {
+        if (lane == 0) {
+            const int rows = min(TC_ROWS, T - t * TC_ROWS), sl = t & 3, bf = t & 1;
+#pragma unroll
+            for (int gq = 0; gq < 4; ++gq) {
+                const int r = 16 * warp + 4 * gq;
+                int p[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) p[i] = S.pos[sl][r + i < rows ? r + i : 0];
+                for (int h = 0; h < halves; ++h)
+                    tc::tma_gather4(S.A[bf][h] + r * 128, tmap, 64 * h, p[0], p[1], p[2], p[3], &S.lbar[bf]);
+            }
+        }
+    };
+    // thread 0: tile t's MMA chain into accumulator columns 32 (t & 1)
+    auto mma_tile = [&](int t) {
+        const int bf = t & 1;
+        constexpr uint32_t idesc = tc::idesc_f16_f32(TC_ROWS, 32);
+        for (int ks = 0; ks < ksteps; ++ks) {
+            const int h = ks >> 2, j = ks & 3;  // K half, 16-half step inside it (32 bytes)
+            const uint64_t ad = tc::smem_desc_sw128(tc::smem_u32(S.A[bf][h]) + 32 * j);
+            const uint64_t bd = tc::smem_desc_sw128(tc::smem_u32(S.B[h]) + 32 * j);
+            tc::mma_f16(tmem + (uint32_t)(32 * bf), ad, bd, idesc, ks > 0);
+        }
+        tc::mma_commit(&S.mbar[bf]);
+        mpend |= 1u << bf;
     };
 
     for (int q0 = 0; q0 < qn && !failed; q0 += 32) {
@@ -1642,19 +1663,46 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
         for (int i = tid; i < nb; i += TC_T) S.bem[i] = 0u;
         if (tid == 0) {
             S.en = 0;
-            S.kn = 0;
+            S.kn[0] = S.kn[1] = 0;
         }
-        // query rows (fp16, zero rows past the group's queries): warp w < 4
-        // rows 8 w .., lane row (l & 7), chunks (l >> 3) + 4 i
-        if (warp < 4) {
-            const int q = 8 * warp + (lane & 7);
-            const uint4 *src = h16 + (size_t)(qfirst + min(q, nqr - 1)) * kc;
-            for (int c = lane >> 3; c < kc; c += 4) cp_async16(S.B + tc::core_offset(q, c), src + c, q < nqr);
+        prep_map(0);
+        prep_map(1);
+        prep_map(2);
+        if (tid == 0) {  // expectations before any gather of them is issued
+            tc::mbar_arrive_expect_tx(&S.bbar, q_bytes);
+            bpend = 1u;
+            for (int t = 0; t < 2 && t < ntiles; ++t) {
+                tc::mbar_arrive_expect_tx(&S.lbar[t], tile_bytes);
+                lpend |= 1u << t;
+            }
         }
-        cp_async_commit();
-        cp_async_wait<0>();
-        tc::fence_smem_to_async();
         __syncthreads();
+        // query rows (past the group's queries: its last query again) and tiles 0, 1
+        if (warp == 0 && lane < 8) {
+            const int q = 4 * lane;
+            const int r0 = qfirst + min(q, nqr - 1), r1 = qfirst + min(q + 1, nqr - 1);
+            const int r2 = qfirst + min(q + 2, nqr - 1), r3 = qfirst + min(q + 3, nqr - 1);
+            for (int h = 0; h < halves; ++h) tc::tma_gather4(S.B[h] + q * 128, tmap, 64 * h, r0, r1, r2, r3, &S.bbar);
+        }
+        for (int t = 0; t < 2 && t < ntiles; ++t) issue_tile(t);
+        if (tid == 0) {  // thread 0 alone tracks the load barriers' phases
+            const bool okb = tok && tc::mbar_wait(&S.bbar, bph, TC_WAIT);
+            if (okb) {
+                bpend = 0u;
+                bph ^= 1u;
+            }
+            bool okl = okb;
+            if (okb && ntiles > 0) {
+                okl = tc::mbar_wait(&S.lbar[0], lph & 1u, TC_WAIT);
+                if (okl) {
+                    lpend &= ~1u;
+                    lph ^= 1u;
+                    tc::fence_after_sync();
+                    mma_tile(0);
+                }
+            }
+            tok = okl;
+        }
 
         auto flush = [&]() {
             if (tid < 32 && S.qfill[tid]) S.qbase[tid] = atomicAdd(&co.fill[S.orig[tid]], S.qfill[tid]);
@@ -1740,41 +1788,30 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
             }
         };
 
-        prep_map(0);
-        prep_map(1);
-        __syncthreads();
-        issue(0);
         for (int t = 0; t < ntiles; ++t) {
-            const int sl = t % 3, bf = t & 1;
+            const int sl = t & 3, bf = t & 1;
             const int rows = min(TC_ROWS, T - t * TC_ROWS);
             if (tid == 0) rows_ld += rows;
-            issue(t + 1);        // into the other buffer (its last MMA has completed)
-            cp_async_wait<1>();  // this thread's copies of tile t have landed
-            tc::fence_smem_to_async();
-            tc::fence_before_sync();
-            __syncthreads();
-            tc::fence_after_sync();
-            if (tid == 0) {
-                constexpr uint32_t idesc = tc::idesc_f16_f32(TC_ROWS, 32);
-                const uint64_t adesc0 = tc::smem_desc(tc::smem_u32(S.A[bf]), tc::kLBO, tc::kSBO);
-                const uint64_t bdesc0 = tc::smem_desc(tc::smem_u32(S.B), tc::kLBO, tc::kSBO);
-                // one K step is 256 bytes further along both tiles (address field in 16-byte units)
-                for (int ks = 0; ks < ksteps; ++ks)
-                    tc::mma_f16(tmem, adesc0 + (uint64_t)(ks * 16), bdesc0 + (uint64_t)(ks * 16), idesc, ks > 0);
-                tc::mma_commit(&S.mma);
+            // tile t's MMA has completed (warp 0 waits) and its norms have landed
+            cp_async_wait<2>();
+            const bool tk = __shfl_sync(0xffffffffu, tok, 0);  // warp 0: thread 0's own waits
+            bool ok = true;
+            if (warp == 0) ok = tk && tc::mbar_wait(&S.mbar[bf], (mph >> bf) & 1u, TC_WAIT);
+            if (tid == 0 && ok && t + 2 < ntiles) {  // buffer bf takes tile t + 2 (gathers after the barrier)
+                tc::mbar_arrive_expect_tx(&S.lbar[bf], tile_bytes);
+                lpend |= 1u << bf;
             }
-            mma_out = true;
-            prep_map(t + 2);
-            bool mok = true;  // warp 0 waits, the barrier releases the others
-            if (warp == 0) mok = tc::mbar_wait(&S.mma, mph, TC_WAIT);
-            if (!__syncthreads_and(mok)) {
+            if (!__syncthreads_and(ok)) {
                 if (tid == 0) atomicOr(err, 32);
                 failed = true;
                 break;
             }
-            mph ^= 1u;
-            mma_out = false;
+            mph ^= 1u << bf;
+            if (tid == 0) mpend &= ~(1u << bf);
             tc::fence_after_sync();
+            if (co.off && S.en >= TC_EB / 2) flush();  // tile t - 1's rechecks are done
+            if (t + 2 < ntiles) issue_tile(t + 2);
+            prep_map(t + 3);
             // epilogue, filter: warp w reads rows 32 (w % 4) .. + 31, queries
             // 16 (w / 4) .. + 15; kept pairs go to the tile's list
             uint32_t keepm = 0u;
@@ -1782,7 +1819,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
             {
                 const int quarter = warp & 3, qh = warp >> 2;
                 float dot[16];
-                tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(16 * qh), dot);
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(32 * bf + 16 * qh), dot);
                 const int r = 32 * quarter + lane;
                 if (r < rows) {
                     // kept iff d^2 = n^_q + n^_p - 2 dot <= (E_q + rel |p^|)^2 + abs2 (|q^|^2 + |p^|^2)
@@ -1793,7 +1830,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
                     // term's slack over the other fp32 errors, the second is covered by the
                     // 2^-20 E_q^2 taken off h_q.  NaN keeps the pair.
                     const int ppos = S.pos[sl][r];
-                    const float pn = S.pn[bf][r];
+                    const float pn = S.pn[sl][r];
                     const float pa = sqrtf(pn) * H16_NORM_UP;
                     const float wp = 0.5f * fmaf(-(H16_REL * H16_REL + H16_ABS2) * pa, pa, pn);
 #pragma unroll
@@ -1815,7 +1852,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
                     if (lane >= o) incl += y;
                 }
                 int base = 0;
-                if (lane == 31 && incl) base = atomicAdd(&S.kn, incl);
+                if (lane == 31 && incl) base = atomicAdd(&S.kn[bf], incl);
                 kb = __shfl_sync(0xffffffffu, base, 31) + incl - c;
                 uint32_t m = keepm;
                 for (int idx = kb; m && idx < TC_KL; ++idx) {
@@ -1824,33 +1861,45 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
                     S.kl[idx] = (uint16_t)(((16 * qh + j) << 7) | r);
                 }
             }
-            __syncthreads();
-            // epilogue, recheck: the kept pairs spread over the lane octets, one
-            // pair per octet, TC_KL at a time
-            {
-                const int n = S.kn;
-                if (tid == 0) kept += n;
-                for (int i = tid >> 3; i < min(n, TC_KL); i += TC_T / 8) recheck8(S.kl[i], sl);
-                for (int lo = TC_KL; lo < n; lo += TC_KL) {
-                    __syncthreads();
-                    uint32_t m = keepm;
-                    const int qc = 16 * (warp >> 2), r = 32 * (warp & 3) + lane;
-                    for (int idx = kb; m && idx < lo + TC_KL; ++idx) {
-                        const int j = __ffs(m) - 1;
-                        m &= m - 1u;
-                        if (idx >= lo) S.kl[idx - lo] = (uint16_t)(((qc + j) << 7) | r);
-                    }
-                    __syncthreads();
-                    for (int i = tid >> 3; i < min(n - lo, TC_KL); i += TC_T / 8) recheck8(S.kl[i], sl);
+            tc::fence_before_sync();
+            // thread 0: tile t + 1's MMA into the other accumulator (its rows
+            // were gathered two iterations ago; its columns were last read by
+            // tile t - 1's filter, before the barrier above)
+            if (t + 1 < ntiles && tid == 0 && tok) {
+                if (tc::mbar_wait(&S.lbar[bf ^ 1], (lph >> (bf ^ 1)) & 1u, TC_WAIT)) {
+                    lpend &= ~(1u << (bf ^ 1));
+                    lph ^= 1u << (bf ^ 1);
+                    tc::fence_after_sync();
+                    mma_tile(t + 1);
+                } else {
+                    tok = false;
                 }
             }
-            tc::fence_before_sync();
             __syncthreads();
-            tc::fence_after_sync();
-            if (tid == 0) S.kn = 0;
-            if (co.off && S.en >= TC_EB / 2) flush();
+            const int n = S.kn[bf];
+            if (tid == 0) {
+                kept += n;
+                S.kn[bf ^ 1] = 0;  // tile t + 1's list (filled after the next barrier)
+            }
+            // recheck: the kept pairs spread over the lane octets, one pair per
+            // octet, TC_KL at a time (pairs past the list are re-derived from
+            // the filter's masks)
+            for (int i = tid >> 3; i < min(n, TC_KL); i += TC_T / 8) recheck8(S.kl[i], sl);
+            for (int lo = TC_KL; lo < n; lo += TC_KL) {
+                __syncthreads();
+                uint32_t m = keepm;
+                const int qc = 16 * (warp >> 2), r = 32 * (warp & 3) + lane;
+                for (int idx = kb; m && idx < lo + TC_KL; ++idx) {
+                    const int j = __ffs(m) - 1;
+                    m &= m - 1u;
+                    if (idx >= lo) S.kl[idx - lo] = (uint16_t)(((qc + j) << 7) | r);
+                }
+                __syncthreads();
+                for (int i = tid >> 3; i < min(n - lo, TC_KL); i += TC_T / 8) recheck8(S.kl[i], sl);
+            }
         }
         if (failed) break;
+        __syncthreads();
         if (co.off) flush();
         __syncthreads();
         if (tid < nqr && S.qcnt[tid]) atomicAdd(&deg[S.orig[tid]], S.qcnt[tid]);
@@ -1872,12 +1921,19 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
         if (tid == 0) stat_add(st, ST_ROWS, rows_ld);
     }
     cp_async_wait<0>();  // no copy into this CTA's shared memory outlives it
-    if (failed && mma_out) tc::mbar_wait(&S.mma, mph, TC_WAIT);  // let an outstanding MMA finish
+    if (tid == 0) {      // after a failure: let gathers and MMAs in flight finish (bounded)
+        for (int b = 0; b < 2; ++b) {
+            if (lpend >> b & 1u) tc::mbar_wait(&S.lbar[b], (lph >> b) & 1u, TC_WAIT);
+            if (mpend >> b & 1u) tc::mbar_wait(&S.mbar[b], (mph >> b) & 1u, TC_WAIT);
+        }
+        if (bpend) tc::mbar_wait(&S.bbar, bph, TC_WAIT);
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, 32);
+    if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
+
 
 // Dynamic shared memory of the L2 leaf kernel (set once per process).
 void leaf_l2_prepare() {
@@ -2425,6 +2481,29 @@ __global__ void k_rel_rows(int64_t n1, const int64_t *__restrict__ grow, int64_t
     if (i < n1) out[i] = grow[i] - grow[0];
 }
 
+// TMA map of n fp16 rows of kp halves (kp a multiple of 64): boxes of 64
+// halves x 1 row (gathered four rows at a time), 128-byte swizzle.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+void encode_rows_f16(CUtensorMap *m, const void *rows, int64_t n, int kp) {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        CT_CHECK_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !p) CT_FAIL(CT_ECUDA, "cuTensorMapEncodeTiled is not available");
+        fn = (EncodeTiledFn)p;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+    const cuuint32_t box[2] = {64, 1}, estr[2] = {1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(rows), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) CT_FAIL(CT_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+}
+
 void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStream_t s, QueryOut *outs,
                  int precision, const ct_predictor *pred, Probe *probe) {
     if (C < 1 || C > kMaxClouds) CT_FAIL(CT_EINVAL, "between 1 and %d clouds per batch", kMaxClouds);
@@ -2465,7 +2544,7 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
             const ct_tree *tc = trees[c];
             const int64_t nc = tc->n;
             if (nc == 0) continue;  // no work items
-            const int dp = tc->dp, kp = 16 * ((dp + 15) / 16);
+            const int dp = tc->dp, kp = 64 * ((dp + 63) / 64);  // rows of 64-half K blocks
             h16s.emplace_back((size_t)nc * (kp / 8), s);
             f16s.emplace_back((size_t)dp + 4 + nc, s);  // means (dp: a multiple of 4), {s, s eps_up}, norms
             float *mean = f16s.back().p, *scal = mean + dp, *nrm = scal + 4;
@@ -2479,7 +2558,7 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
             k_to_h16<<<grid_for(nc * 16, 256), 256, 0, s>>>(tc->pts, nc, dp, kp, mean, scal, h16s.back().p, nrm);
             CT_COUNT_LAUNCH();
             CT_LAUNCH_CHECK();
-            V.h16[c] = h16s.back().p;
+            encode_rows_f16(&V.tmap[c], h16s.back().p, nc, kp);
             V.n16[c] = nrm;
             V.s16[c] = scal;
         }

@@ -32,6 +32,22 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;         // layout type 0 (no swizzle) in bits 61-63
 }
 
+// Shared-memory matrix descriptor for the 128-byte swizzled K-major layout:
+// rows of 128 bytes (64 halves of K) in 8-row atoms of 1024 bytes, the 16-byte
+// chunks of row r XOR-permuted by r % 8 (the pattern TMA writes with
+// CU_TENSOR_MAP_SWIZZLE_128B).  Atoms 1024-byte aligned; stride byte offset =
+// 1024 (next 8 rows), leading byte offset unused; a K step of 16 halves
+// inside the atom advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;             // leading byte offset (ignored for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+    d |= 1ull << 46;                    // version
+    d |= 2ull << 61;                    // layout type: 128-byte swizzle
+    return d;
+}
+
 // Instruction descriptor of kind::f16: D fp32, A and B bf16, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4)                        // D format: f32
@@ -109,6 +125,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint3
         if (done) return true;
     }
     return false;
+}
+
+// One arrival on the mbarrier that also expects `bytes` of asynchronous
+// copies (TMA) to complete in the current phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// TMA gather of four rows r0..r3 (columns col .. col + box - 1 of a 2-D tensor
+// map whose box is one row high) into consecutive rows at dst, completing
+// their bytes on mbar.  col * element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_gather4(void *dst, const void *tmap, int col, int r0, int r1, int r2, int r3,
+                                            uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(col), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_u32(mbar))
+        : "memory");
 }
 
 // 16 consecutive fp32 columns of this warp's 32 tensor-memory lanes.
