@@ -170,6 +170,18 @@ struct Pool {
     int32_t *overflow;
 };
 
+// Walks stopped at a step limit leave their stack's ranges here, as items
+// (global group, first vertex, count, -) that the next round walks.
+struct Spill {
+    int4 *items;
+    int32_t *count;  // may exceed cap: ranges past cap were not stored
+    int cap;
+    int limit;       // steps before a walk stops
+};
+constexpr int TRAV_ROUNDS = 4;     // rounds after the groups' round; the last one has no step limit
+constexpr int TRAV_LIMIT0 = 256;   // step limit of the groups' round
+constexpr int TRAV_LIMIT = 128;    // step limit of the next rounds
+
 // Warp-uniform write cursor: current chunk, its fill, the open segment.
 struct PoolCursor {
     int64_t cur;
@@ -227,27 +239,48 @@ __device__ __forceinline__ void pool_append(const Pool &P, int g, PoolCursor &pc
     if (flag && rank >= room) P.data[pc.cur + rank - room] = v;
 }
 
-// DFS over ranges of sibling vertices: up to 32 vertices are tested per step,
-// vertex i of the step by lane i (`tester(first, take)` returns the lane's
-// keep flag); survivors are compacted with ballots -- leaf blocks are
-// appended to the pool, internal vertices push their child range.
+// DFS over ranges of sibling vertices from `start` (count 0: the root's
+// children): up to 32 vertices are tested per step, vertex i of the step by
+// lane i (`tester(first, take)` returns the lane's keep flag); survivors are
+// compacted with ballots -- leaf blocks are appended to the pool, internal
+// vertices push their child range.  The vertices' child ranges are loaded
+// before the test, so that their loads overlap the test's.  With `sp`, a walk
+// that reaches sp->limit steps stores the ranges left on its stack in
+// sp->items and stops (if they do not fit it goes on).
 template <class Tester>
-__device__ __forceinline__ int walk_group(const TreeView &tv, int2 *__restrict__ stack, int cap, int g,
+__device__ __forceinline__ int walk_group(const TreeView &tv, int2 *__restrict__ stack, int cap, int g, int2 start,
                                           const Pool &P, PoolCursor &pc, unsigned long long &evals,
-                                          int32_t *__restrict__ err, Tester tester) {
+                                          int32_t *__restrict__ err, const Spill *sp, Tester tester) {
     const int lane = threadIdx.x & 31;
     int n_cand = 0;
     pc.seg_begin = pc.cur + pc.fill;
     pc.seg_count = 0;
-    if (tv.child_count[0] == 0) {  // the root is a leaf block: it is the only candidate
+    if (start.y == 0 && tv.child_count[0] == 0) {  // the root is a leaf block: it is the only candidate
         pool_append(P, g, pc, lane == 0, 0u);
         n_cand = 1;
     } else {
         int top = 0;
-        if (lane == 0) stack[0] = make_int2(tv.child_begin[0], tv.child_count[0]);
+        if (lane == 0) stack[0] = start.y ? start : make_int2(tv.child_begin[0], tv.child_count[0]);
         top = 1;
         __syncwarp();
-        while (top > 0) {
+        int limit = sp ? sp->limit : INT_MAX;
+        for (int steps = 0; top > 0; ++steps) {
+            if (steps >= limit) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(sp->count, top);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (base + top <= sp->cap) {
+                    for (int i = lane; i < top; i += 32) {
+                        const int2 r = stack[i];
+                        sp->items[base + i] = make_int4(g, r.x, r.y, 0);
+                    }
+                    break;
+                }
+                // no room: the slots reserved below the end hold empty ranges
+                // (count 0, skipped), and the walk is finished here
+                for (int i = base + lane; i < sp->cap; i += 32) sp->items[i] = make_int4(g, 0, 0, 0);
+                limit = INT_MAX;
+            }
             int2 r = stack[top - 1];
             int take = r.y < 32 ? r.y : 32;
             __syncwarp();
@@ -256,9 +289,14 @@ __device__ __forceinline__ int walk_group(const TreeView &tv, int2 *__restrict__
             }
             if (r.y <= take) --top;
             if (lane < take) ++evals;
-            const bool keep = tester(r.x, take);
             const int v = r.x + lane;
-            const bool leaf = keep && tv.child_count[v] == 0;
+            int ccount = 0, cbegin = 0;
+            if (lane < take) {
+                ccount = tv.child_count[v];
+                cbegin = tv.child_begin[v];
+            }
+            const bool keep = tester(r.x, take);
+            const bool leaf = keep && ccount == 0;
             pool_append(P, g, pc, keep && leaf, (uint32_t)v);
             n_cand += __popc(__ballot_sync(0xffffffffu, keep && leaf));
             const unsigned mi = __ballot_sync(0xffffffffu, keep && !leaf);
@@ -270,7 +308,7 @@ __device__ __forceinline__ int walk_group(const TreeView &tv, int2 *__restrict__
             if (keep && !leaf) {
                 // reverse lane order so the lowest lane's children are on top (DFS order)
                 int slot = top + __popc(mi & ~lanemask_lt() & ~(1u << lane));
-                stack[slot] = make_int2(tv.child_begin[v], tv.child_count[v]);
+                stack[slot] = make_int2(cbegin, ccount);
             }
             top += np;
             __syncwarp();
@@ -281,11 +319,12 @@ __device__ __forceinline__ int walk_group(const TreeView &tv, int2 *__restrict__
     return 0;
 }
 
-// Vertices the warp tested for group g (for fitting the predictor).
+// Vertices the warp tested for group g (for fitting the predictor; the rounds
+// of one group's walk add up).
 __device__ __forceinline__ void group_visits(int32_t *gvisit, int g, unsigned long long mine) {
     unsigned long long v = mine;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) gvisit[g] = (int32_t)(v < 0x7fffffffull ? v : 0x7fffffffull);
+    if ((threadIdx.x & 31) == 0) atomicAdd(gvisit + g, (int32_t)(v < 0x7fffffffull ? v : 0x7fffffffull));
 }
 
 // L2 test of `take` consecutive vertices against the group centre (shared
@@ -297,6 +336,7 @@ __device__ __forceinline__ bool l2_keep(const TreeView &tv, const float4 *cen, i
                                         float add) {
     constexpr int NPR = 32 / TPD;  // vertices per round; TPD rounds cover a step of 32
     const int lane = threadIdx.x & 31, sub = lane / TPD, j = lane % TPD;
+    const float rad = lane < take ? tv.radius[first + lane] : 0.f;  // issued with the centre rows
     // all rounds' partial sums first (their loads overlap), then the reductions
     float part[TPD];
 #pragma unroll
@@ -330,30 +370,51 @@ __device__ __forceinline__ bool l2_keep(const TreeView &tv, const float4 *cen, i
         if (lane >= r0 && lane < r0 + NPR) mine = v;
     }
     if (lane >= take) return false;
-    const float bound = fmaf(tv.radius[first + lane] + add, PRUNE_REL, PRUNE_ABS);
+    const float bound = fmaf(rad + add, PRUNE_REL, PRUNE_ABS);
     return !(sqrtf(mine) > bound);
 }
 
 // Warp per group over all clouds' groups, taken dynamically in `order`
-// (global group ids); the lanes per vertex test follow the cloud's row length.
-__global__ void __launch_bounds__(TRAV_WARPS * 32) k_traverse_l2(
-    const __grid_constant__ Views V, const int32_t *__restrict__ order, int n_order, Pool P,
-    int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st, int32_t *__restrict__ err,
-    int32_t *__restrict__ next_group, int32_t *__restrict__ gvisit, int max_nq4) {
+// (global group ids), or -- in the later rounds -- per stored range of a
+// walk that reached the step limit; the lanes per vertex test follow the
+// cloud's row length.  Walks stop at out.limit steps (no limit without
+// out.items) and store the rest of their stack in `out`.
+__global__ void __launch_bounds__(TRAV_WARPS * 32, 8) k_traverse_l2(
+    const __grid_constant__ Views V, const int32_t *__restrict__ order, int n_order,
+    const int4 *__restrict__ in_items, const int32_t *__restrict__ in_count, int in_cap, Spill out, Pool P,
+    longlong2 *__restrict__ cursors, int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st,
+    int32_t *__restrict__ err, int32_t *__restrict__ next_group, int32_t *__restrict__ gvisit, int max_nq4) {
     extern __shared__ float4 sc[];  // TRAV_WARPS x (largest dp / 4)
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4 *cen = sc + wib * max_nq4;
     const int gw = blockIdx.x * TRAV_WARPS + wib;
     int2 *stack = stacks + (int64_t)gw * cap;
     unsigned long long evals = 0;
+    // the warp's pool chunk carries over from the previous round
     PoolCursor pc{-1, POOL_CHUNK, 0, 0};
+    if (in_items) {
+        const longlong2 c = cursors[gw];
+        pc.cur = c.x;
+        pc.fill = (int)c.y;
+    }
+    const int n_work = in_items ? min(*in_count, in_cap) : n_order;
+    const Spill *sp = out.items ? &out : nullptr;
     for (;;) {
-        // groups are taken dynamically: their walks differ widely in length
+        // work is taken dynamically: walks differ widely in length
         int gi = 0;
         if (lane == 0) gi = atomicAdd(next_group, 1);
         gi = __shfl_sync(0xffffffffu, gi, 0);
-        if (gi >= n_order) break;
-        const int gg = order[gi];
+        if (gi >= n_work) break;
+        int gg;
+        int2 start = make_int2(0, 0);
+        if (in_items) {
+            const int4 w = in_items[gi];
+            if (w.z <= 0) continue;  // an empty range (a stop that did not fit)
+            gg = w.x;
+            start = make_int2(w.y, w.z);
+        } else {
+            gg = order[gi];
+        }
         const int c = cloud_of_group(V, gg);
         const TreeView &tv = V.tv[c];
         const int g = gg - V.gbase[c];
@@ -372,10 +433,11 @@ __global__ void __launch_bounds__(TRAV_WARPS * 32) k_traverse_l2(
             }
         };
         const unsigned long long e0 = evals;
-        if (walk_group(tv, stack, cap, gg, P, pc, evals, err, tester) < 0) return;
+        if (walk_group(tv, stack, cap, gg, start, P, pc, evals, err, sp, tester) < 0) return;
         if (gvisit) group_visits(gvisit, gg, evals - e0);
         __syncwarp();
     }
+    if (lane == 0) cursors[gw] = make_longlong2(pc.cur, pc.fill);
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
     if (lane == 0) stat_add(st, ST_TRAV, evals);
 }
@@ -415,7 +477,7 @@ __global__ void __launch_bounds__(32) k_traverse_lev(
             return lev_myers<W>(peq, m, txt, n, k) <= k;
         };
         const unsigned long long e0 = evals;
-        if (walk_group(tv, stack, cap, g, P, pc, evals, err, tester) < 0) return;
+        if (walk_group(tv, stack, cap, g, make_int2(0, 0), P, pc, evals, err, nullptr, tester) < 0) return;
         if (gvisit) group_visits(gvisit, g, evals - e0);
     }
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
@@ -2407,20 +2469,44 @@ int64_t pool_capacity_guess(int64_t n, int64_t G, const TravLaunch &tl) {
 }
 
 // Clears the pool counters and launches the traversal over `order` (global
-// group ids; allocates nothing).  Edit distance: a single cloud.
+// group ids; allocates nothing).  L2: a round over the groups with a step
+// limit, then TRAV_ROUNDS rounds over the ranges the previous round stored
+// (`spill`: two buffers of spill_cap items and two counters; the last round
+// has no limit), so that no single long walk sets the time.  Each warp's
+// pool chunk carries over between rounds (`cursors`: one per warp of the
+// grid).  Edit distance: a single cloud, one round.
 void launch_traversal(const Views &V, int64_t G, int max_dp, int max_len, bool l2, const int32_t *order,
                       const Pool &P, int2 *stacks, int cap, const TravLaunch &tl, unsigned long long *st,
-                      int32_t *err, int32_t *next_group, cudaStream_t s, int32_t *gvisit = nullptr) {
+                      int32_t *err, int32_t *next_group, int4 *const spill[2], int32_t *spill_cnt, int spill_cap,
+                      longlong2 *cursors, cudaStream_t s, int32_t *gvisit = nullptr) {
     // P.next .. P.overflow are the four 64-bit words of one counter block
     CT_CHECK_CUDA(cudaMemsetAsync(next_group, 0, sizeof(int32_t), s));
     CT_CHECK_CUDA(cudaMemsetAsync(P.next, 0, 4 * sizeof(unsigned long long), s));
+    if (gvisit && G > 0) CT_CHECK_CUDA(cudaMemsetAsync(gvisit, 0, (size_t)G * sizeof(int32_t), s));
     if (G == 0) return;
     if (l2) {
         const size_t tsm = (size_t)TRAV_WARPS * max_dp * sizeof(float);
         if (tsm > 48 * 1024)
             CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
-        k_traverse_l2<<<tl.blocks, TRAV_WARPS * 32, tsm, s>>>(V, order, (int)G, P, stacks, cap, st, err, next_group,
-                                                               gvisit, max_dp >> 2);
+        CT_CHECK_CUDA(cudaMemsetAsync(spill_cnt, 0, 2 * sizeof(int32_t), s));
+        for (int r = 0; r <= TRAV_ROUNDS; ++r) {
+            const int4 *in = r ? spill[(r - 1) & 1] : nullptr;
+            const int32_t *in_cnt = r ? spill_cnt + ((r - 1) & 1) : nullptr;
+            Spill out{nullptr, spill_cnt + (r & 1), spill_cap, INT_MAX};
+            if (r < TRAV_ROUNDS) {
+                out.items = spill[r & 1];
+                out.limit = r ? TRAV_LIMIT : TRAV_LIMIT0;
+            }
+            if (r) {
+                CT_CHECK_CUDA(cudaMemsetAsync(next_group, 0, sizeof(int32_t), s));
+                CT_CHECK_CUDA(cudaMemsetAsync(spill_cnt + (r & 1), 0, sizeof(int32_t), s));
+            }
+            k_traverse_l2<<<tl.blocks, TRAV_WARPS * 32, tsm, s>>>(V, order, (int)G, in, in_cnt, spill_cap, out, P,
+                                                                   cursors, stacks, cap, st, err, next_group,
+                                                                   gvisit, max_dp >> 2);
+            CT_COUNT_LAUNCH();
+            CT_LAUNCH_CHECK();
+        }
     } else {
         TreeView tv = V.tv[0];
         tv.group_order = order;
@@ -2430,9 +2516,9 @@ void launch_traversal(const Views &V, int64_t G, int max_dp, int max_len, bool l
             CT_TL(1) CT_TL(2) CT_TL(4) CT_TL(8) CT_TL(16)
 #undef CT_TL
         }
+        CT_COUNT_LAUNCH();
+        CT_LAUNCH_CHECK();
     }
-    CT_COUNT_LAUNCH();
-    CT_LAUNCH_CHECK();
 }
 
 // Leaf kernel and item length per cloud.  precision 0: FP32 tiles; 1: tensor-
@@ -2605,6 +2691,12 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     DBuf<int2> stacks((size_t)tl.warps * cap, s);
     DBuf<unsigned long long> ctr(4, s);
     DBuf<int32_t> next_group(1, s);
+    // ranges of step-limited walks (L2): two buffers and their counters
+    const int spill_cap = l2 ? (int)std::min<int64_t>(std::max<int64_t>(4 * G, 1 << 16), 1 << 20) : 0;
+    DBuf<int4> spill_a(spill_cap, s), spill_b(spill_cap, s);
+    DBuf<int32_t> spill_cnt(2, s);
+    int4 *const spills[2] = {spill_a.p, spill_b.p};
+    DBuf<longlong2> cursors(l2 ? tl.warps : 0, s);
     int64_t pool_cap = pool_capacity_guess(n, G, tl);
     DBuf<uint32_t> pool;
     DBuf<int32_t> seg_group, seg_count;
@@ -2612,7 +2704,8 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     unsigned long long hc[4] = {0, 0, 0, 0};
     Pool P{};
     for (int attempt = 0;; ++attempt) {
-        const int64_t seg_cap = G + pool_cap / POOL_CHUNK + tl.warps + 16;
+        // a segment per walk (groups, stored ranges) and per chunk a walk crosses
+        const int64_t seg_cap = G + (int64_t)TRAV_ROUNDS * spill_cap + pool_cap / POOL_CHUNK + tl.warps + 16;
         pool = DBuf<uint32_t>(pool_cap, s);
         seg_group = DBuf<int32_t>(seg_cap, s);
         seg_count = DBuf<int32_t>(seg_cap, s);
@@ -2621,8 +2714,8 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
                  reinterpret_cast<int32_t *>(ctr.p + 1), seg_cap, ctr.p + 2, reinterpret_cast<int32_t *>(ctr.p + 3)};
         {
             ProfScope ps("traverse", s);
-            launch_traversal(V, G, max_dp, max_len, l2, order, P, stacks.p, cap, tl, st.p, err, next_group.p, s,
-                             gvisit);
+            launch_traversal(V, G, max_dp, max_len, l2, order, P, stacks.p, cap, tl, st.p, err, next_group.p, spills,
+                             spill_cnt.p, spill_cap, cursors.p, s, gvisit);
         }
         to_host(hc, ctr.p, 4, s);
         if (!(uint32_t)hc[3]) break;
@@ -2948,6 +3041,9 @@ void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cuda
     unsigned long long *ctr = (unsigned long long *)take(4 * sizeof(unsigned long long));
     int32_t *next_group = (int32_t *)take(sizeof(int32_t));
     int32_t *nitems = (int32_t *)take(sizeof(int32_t));
+    constexpr int kSpillCap = 1 << 15;  // ranges of step-limited walks per round (a full buffer only ends the limit)
+    int32_t *spill_cnt = (int32_t *)take(2 * sizeof(int32_t));
+    int4 *const spills[2] = {(int4 *)take(kSpillCap * sizeof(int4)), (int4 *)take(kSpillCap * sizeof(int4))};
     TravLaunch tl = trav_launch_config(true, t->n_groups);
     const size_t stack_per_block = (size_t)TRAV_WARPS * cap * sizeof(int2);
     if (off + stack_per_block > cap_bytes / 2)
@@ -2959,6 +3055,7 @@ void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cuda
         1, std::min<int64_t>(std::min<int64_t>(tl.blocks, (cap_bytes / 4) / stack_per_block), chunk_blocks));
     tl.warps = tl.blocks * TRAV_WARPS;
     int2 *stacks = (int2 *)take((size_t)tl.blocks * stack_per_block);
+    longlong2 *cursors = (longlong2 *)take((size_t)tl.warps * sizeof(longlong2));
     // the rest: segments (one third of it, at most one per group and chunk) and the pool
     const size_t rest = cap_bytes > off ? cap_bytes - off : 0;
     const int64_t seg_cap = (int64_t)(rest / 3 / (sizeof(int32_t) * 2 + sizeof(int64_t) + 16));
@@ -2982,7 +3079,8 @@ void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cuda
     int32_t *err = reinterpret_cast<int32_t *>(st + ST_ERR);
     // the array keeps the previous call's contents: clear what must start at zero
     CT_CHECK_CUDA(cudaMemsetAsync(st, 0, ST_N * sizeof(unsigned long long), s));
-    launch_traversal(V, t->n_groups, t->dp, 0, true, t->group_order, P, stacks, cap, tl, st, err, next_group, s);
+    launch_traversal(V, t->n_groups, t->dp, 0, true, t->group_order, P, stacks, cap, tl, st, err, next_group, spills,
+                     spill_cnt, kSpillCap, cursors, s);
     unsigned long long hc[4] = {0, 0, 0, 0};
     CT_CHECK_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
     CT_CHECK_CUDA(cudaStreamSynchronize(s));
