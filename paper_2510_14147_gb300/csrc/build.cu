@@ -184,10 +184,12 @@ __global__ void __launch_bounds__(BT) k_dist_update_lev(
 
 // One thread per hub: decide termination or choose the next centre (its
 // position goes to cpos[begin + label] when cpos is given).
-__global__ void k_hub_step(int nh, Hubs hb, int32_t *__restrict__ active_out, int32_t *__restrict__ cpos) {
-    int h = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_hub_step(int nh, const int32_t *__restrict__ hlist, Hubs hb, int32_t *__restrict__ active_out,
+                           int32_t *__restrict__ cpos) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int h = i < nh && hlist ? hlist[i] : i;
     int act = 0;
-    if (h < nh && !hb.done[h]) {
+    if (i < nh && !hb.done[h]) {
         unsigned long long k = hb.key[h];
         float v = key_value(k);
         if (k == 0ull || !(v > hb.thr[h])) {
@@ -212,8 +214,9 @@ __global__ void k_hub_step(int nh, Hubs hb, int32_t *__restrict__ active_out, in
 template <int TPD>
 __global__ void __launch_bounds__(BT) k_centre_dists(const float *__restrict__ X, int dp,
                                                      const int32_t *__restrict__ ids, Hubs hb,
+                                                     const int32_t *__restrict__ hlist,
                                                      const int32_t *__restrict__ cpos, float *__restrict__ dcc) {
-    const int h = blockIdx.x;
+    const int h = hlist ? hlist[blockIdx.x] : blockIdx.x;
     if (hb.done[h]) return;
     const int b = hb.begin[h], nc = hb.nc[h], nq = dp >> 2;
     const float4 *crow = reinterpret_cast<const float4 *>(X + (size_t)ids[hb.cur[h]] * dp);
@@ -234,6 +237,40 @@ __global__ void k_chunk_counts(int nh, const int32_t *__restrict__ count, int ch
     int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h < nh) out[h] = (count[h] + chunk_len - 1) / chunk_len;
 }
+// Hubs not yet done, and the chunks of those hubs (from the current chunk
+// list), for the next burst of split iterations: late iterations touch only
+// the few hubs still splitting.  The order within the lists is immaterial
+// (every hub and point is updated independently; keys combine by max).
+__global__ void k_active_hubs(int nh, const int32_t *__restrict__ done, int32_t *__restrict__ hlist,
+                              int32_t *__restrict__ cnt) {
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool a = h < nh && !done[h];
+    const unsigned m = __ballot_sync(0xffffffffu, a);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (a) hlist[base + __popc(m & ((1u << lane) - 1u))] = h;
+}
+__global__ void k_active_chunks(int64_t nchunks, const int32_t *__restrict__ chub, const int32_t *__restrict__ cst,
+                                const int32_t *__restrict__ done, int32_t *__restrict__ chub2,
+                                int32_t *__restrict__ cst2, int32_t *__restrict__ cnt) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool a = c < nchunks && !done[chub[c]];
+    const unsigned m = __ballot_sync(0xffffffffu, a);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (a) {
+        const int k = base + __popc(m & ((1u << lane) - 1u));
+        chub2[k] = chub[c];
+        cst2[k] = cst[c];
+    }
+}
+
 __global__ void k_chunk_fill(int nh, const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
                              const int64_t *__restrict__ coff, int chunk_len,
                              int32_t *__restrict__ chunk_hub, int32_t *__restrict__ chunk_start) {
@@ -687,7 +724,8 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
         DBuf<uint32_t> pk(n, s), pv(n, s), tk(n, s), tv(n, s);
         DBuf<int32_t> rpos(n, s), tids(n, s);
         DBuf<float> tD(n, s);
-        DBuf<int32_t> active(1, s);
+        DBuf<int32_t> active(3, s);  // hub activations of a burst, active hubs, active chunks
+        DBuf<int32_t> hlist(n, s), chub2(nchunks0, s), cst2(nchunks0, s);
         DBuf<int64_t> i64tmp(2, s);
 
         while (nh > 0) {
@@ -702,6 +740,8 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
             to_host(&nchunks, i64tmp.p, 1, s);
             chub.grow(nchunks);
             cst.grow(nchunks);
+            chub2.grow(nchunks);
+            cst2.grow(nchunks);
             k_chunk_fill<<<(unsigned)nh, 64, 0, s>>>((int)nh, H.begin, H.count, coff.p, chunk_len, chub.p, cst.p);
             CT_COUNT_LAUNCH();
             CT_LAUNCH_CHECK();
@@ -711,30 +751,48 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
                 ProfScope prof_split("build_split", s);
                 int burst = 1;
                 int64_t iters = 0;
+                // the hubs and chunks a burst visits: all at first, then those
+                // of the hubs still splitting after the previous burst
+                const int32_t *hl = nullptr;
+                int64_t nl = nh, nck = nchunks;
+                int32_t *cb = chub.p, *cs = cst.p, *cb2 = chub2.p, *cs2 = cst2.p;
                 for (;;) {
                     // every iteration adds a distinct centre to some hub, so
                     // no hub is active after n + 1 of them; a burst of up to
                     // 16 may run past the last useful iteration
                     if (iters > n + 2 + 16) CT_FAIL(CT_ECUDA, "split loop did not terminate");
                     iters += burst;
-                    CT_CHECK_CUDA(cudaMemsetAsync(active.p, 0, sizeof(int32_t), s));
+                    CT_CHECK_CUDA(cudaMemsetAsync(active.p, 0, 3 * sizeof(int32_t), s));
                     for (int it = 0; it < burst; ++it) {
-                        k_hub_step<<<grid_for(nh), BT, 0, s>>>((int)nh, H, active.p, l2 ? cpos.p : nullptr);
+                        k_hub_step<<<grid_for(nl), BT, 0, s>>>((int)nl, hl, H, active.p, l2 ? cpos.p : nullptr);
                         CT_COUNT_LAUNCH();
                         if (l2) {
                             switch (tpd) {
-#define CT_CD(T) case T: k_centre_dists<T><<<(unsigned)nh, BT, 0, s>>>(Xp.p, dp, ids.p, H, cpos.p, dcc.p); break;
+#define CT_CD(T) case T: k_centre_dists<T><<<(unsigned)nl, BT, 0, s>>>(Xp.p, dp, ids.p, H, hl, cpos.p, dcc.p); break;
                                 CT_CD(1) CT_CD(2) CT_CD(4) CT_CD(8) CT_CD(16) CT_CD(32)
 #undef CT_CD
                             }
                             CT_COUNT_LAUNCH();
                             prune = true;
                         }
-                        update(H, nchunks, chub.p, cst.p);
+                        update(H, nck, cb, cs);
                     }
-                    int32_t act = 0;
-                    to_host(&act, active.p, 1, s);
-                    if (act == 0) break;
+                    k_active_hubs<<<grid_for(nh), BT, 0, s>>>((int)nh, H.done, hlist.p, active.p + 1);
+                    CT_COUNT_LAUNCH();
+                    if (nck) {
+                        k_active_chunks<<<grid_for(nck), BT, 0, s>>>(nck, cb, cs, H.done, cb2, cs2, active.p + 2);
+                        CT_COUNT_LAUNCH();
+                    }
+                    CT_LAUNCH_CHECK();
+                    int32_t act[3] = {0, 0, 0};
+                    to_host(act, active.p, 3, s);
+                    if (act[0] == 0) break;
+                    hl = hlist.p;
+                    nl = act[1];
+                    nck = act[2];
+                    std::swap(cb, cb2);
+                    std::swap(cs, cs2);
+                    if (nl == 0) break;
                     burst = burst < 16 ? burst * 2 : 16;
                 }
             }
