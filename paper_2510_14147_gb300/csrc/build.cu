@@ -237,6 +237,118 @@ __global__ void k_chunk_counts(int nh, const int32_t *__restrict__ count, int ch
     int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h < nh) out[h] = (count[h] + chunk_len - 1) / chunk_len;
 }
+// The whole split (Algorithm 1) of one small hub (at most SPLIT_SMALL points)
+// in one CTA: the iterations of k_hub_step, k_centre_dists and
+// k_dist_update_l2 for that hub, with the same arithmetic (so the same
+// centres), its distances, labels and centres in shared memory, and no
+// launch per iteration.  One CTA per hub of the round (larger hubs exit);
+// the distances, labels and the number of children go back to global memory.
+constexpr int SPLIT_SMALL = 2048;
+template <int TPD>
+__global__ void __launch_bounds__(BT) k_split_small(const float *__restrict__ X, int dp,
+                                                    const int32_t *__restrict__ ids, float *__restrict__ D,
+                                                    int32_t *__restrict__ lab, Hubs hb, int32_t *__restrict__ err) {
+    __shared__ float Ds[SPLIT_SMALL], dccs[SPLIT_SMALL];
+    __shared__ int32_t labs[SPLIT_SMALL], cposs[SPLIT_SMALL];
+    __shared__ float4 cen[32];  // dp <= 128 (TPD is chosen for it)
+    __shared__ unsigned long long red[BT / 32];
+    __shared__ int s_nc, s_done;
+    __shared__ unsigned long long s_key;
+    const int h = blockIdx.x;
+    if (hb.done[h] || hb.count[h] > SPLIT_SMALL) return;  // a large hub: the level-wide iterations
+    const int b = hb.begin[h], cnt = hb.count[h], nq = dp >> 2;
+    const float thr = hb.thr[h];
+    for (int i = threadIdx.x; i < cnt; i += BT) {
+        Ds[i] = D[b + i];
+        labs[i] = lab[b + i];
+    }
+    if (threadIdx.x == 0) {
+        s_nc = hb.nc[h];
+        s_key = hb.key[h];
+        cposs[0] = b;  // label 0: the hub's own centre
+    }
+    __syncthreads();
+    constexpr int G = BT / TPD;
+    const int g = threadIdx.x / TPD, j = threadIdx.x % TPD;
+    for (;;) {
+        // k_hub_step: done, or the farthest point becomes the next centre
+        if (threadIdx.x == 0) {
+            const unsigned long long k = s_key;
+            const float v = key_value(k);
+            if (k == 0ull || !(v > thr) || s_nc >= cnt + 1) {
+                if (k != 0ull && v > thr) atomicOr(err, 4);  // cannot happen: every centre is a distinct point
+                s_done = 1;
+            } else {
+                cposs[s_nc] = (int32_t)key_pos(k);
+                s_nc += 1;
+                s_done = 0;
+            }
+            s_key = 0ull;
+        }
+        __syncthreads();
+        if (s_done) break;
+        const int nc = s_nc, cur = cposs[nc - 1];
+        const float4 *crow = reinterpret_cast<const float4 *>(X + (size_t)ids[cur] * dp);
+        for (int i = threadIdx.x; i < nq; i += BT) cen[i] = crow[i];
+        __syncthreads();
+        // k_centre_dists: the new centre against every centre of the hub
+        for (int L0 = 0; L0 < nc; L0 += G) {
+            const int L = L0 + g;
+            const int pos = cposs[L < nc ? L : 0];
+            const float dd = sqrtf(group_sqdist<TPD>(reinterpret_cast<const float4 *>(X + (size_t)ids[pos] * dp), cen,
+                                                     nq, j));
+            if (L < nc && j == 0) dccs[L] = dd;
+        }
+        __syncthreads();
+        // k_dist_update_l2 over the hub's points, with the same pruning
+        unsigned long long best = 0ull;
+        for (int base = 0; base < cnt; base += G) {
+            const int i = base + g;
+            const bool valid = i < cnt;
+            float curd = valid ? Ds[i] : 0.f;
+            bool far = !valid;
+            if (valid) far = dccs[labs[i]] >= 2.0f * curd * (1.0f + 0x1p-12f) + 0x1p-60f;
+            if (!far) {
+                const float sq = group_sqdist<TPD>(reinterpret_cast<const float4 *>(X + (size_t)ids[b + i] * dp), cen,
+                                                   nq, j);
+                if (j == 0) {
+                    const float d = sqrtf(sq);
+                    if (d < curd) {
+                        Ds[i] = d;
+                        labs[i] = nc - 1;
+                        curd = d;
+                    }
+                }
+            }
+            if (valid && j == 0) {
+                const unsigned long long k = pack_max_key(curd, (uint32_t)(b + i));
+                best = k > best ? k : best;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+            best = v > best ? v : best;
+        }
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long m = 0ull;
+            for (int w = 0; w < BT / 32; ++w) m = red[w] > m ? red[w] : m;
+            s_key = m;
+        }
+        // the next pass's reads of Ds / labs follow the barrier at its top
+    }
+    for (int i = threadIdx.x; i < cnt; i += BT) {
+        D[b + i] = Ds[i];
+        lab[b + i] = labs[i];
+    }
+    if (threadIdx.x == 0) {
+        hb.nc[h] = s_nc;
+        hb.done[h] = 1;
+        hb.key[h] = 0ull;
+    }
+}
+
 // Hubs not yet done, and the chunks of those hubs (from the current chunk
 // list), for the next burst of split iterations: late iterations touch only
 // the few hubs still splitting.  The order within the lists is immaterial
@@ -756,7 +868,29 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
                 const int32_t *hl = nullptr;
                 int64_t nl = nh, nck = nchunks;
                 int32_t *cb = chub.p, *cs = cst.p, *cb2 = chub2.p, *cs2 = cst2.p;
-                for (;;) {
+                if (l2 && dp <= 128 && prune) {
+                    // small hubs split whole in one CTA each; the loop below takes the rest
+                    switch (tpd) {
+#define CT_SS(T) case T: k_split_small<T><<<(unsigned)nh, BT, 0, s>>>(Xp.p, dp, ids.p, D.p, lab.p, H, err.p); break;
+                        CT_SS(1) CT_SS(2) CT_SS(4) CT_SS(8) CT_SS(16) CT_SS(32)
+#undef CT_SS
+                    }
+                    CT_COUNT_LAUNCH();
+                    CT_CHECK_CUDA(cudaMemsetAsync(active.p, 0, 3 * sizeof(int32_t), s));
+                    k_active_hubs<<<grid_for(nh), BT, 0, s>>>((int)nh, H.done, hlist.p, active.p + 1);
+                    CT_COUNT_LAUNCH();
+                    k_active_chunks<<<grid_for(nck), BT, 0, s>>>(nck, cb, cs, H.done, cb2, cs2, active.p + 2);
+                    CT_COUNT_LAUNCH();
+                    CT_LAUNCH_CHECK();
+                    int32_t cnt3[3] = {0, 0, 0};
+                    to_host(cnt3, active.p, 3, s);
+                    hl = hlist.p;
+                    nl = cnt3[1];
+                    nck = cnt3[2];
+                    std::swap(cb, cb2);
+                    std::swap(cs, cs2);
+                }
+                for (; nl > 0;) {
                     // every iteration adds a distinct centre to some hub, so
                     // no hub is active after n + 1 of them; a burst of up to
                     // 16 may run past the last useful iteration
