@@ -62,6 +62,7 @@ template <int TPD>
 __device__ __forceinline__ float group_sqdist(const float4 *__restrict__ row, const float4 *cen,
                                               int nq, int j) {
     float acc = 0.f;
+#pragma unroll 4
     for (int k = j; k < nq; k += TPD) {
         float4 a = __ldg(row + k);
         float4 b = cen[k];
@@ -239,8 +240,9 @@ __global__ void k_chunk_counts(int nh, const int32_t *__restrict__ count, int ch
 }
 // The whole split (Algorithm 1) of one small hub (at most SPLIT_SMALL points)
 // in one CTA: the iterations of k_hub_step, k_centre_dists and
-// k_dist_update_l2 for that hub, with the same arithmetic (so the same
-// centres), its distances, labels and centres in shared memory, and no
+// k_dist_update_l2 for that hub (the same steps and pruning; TPD lanes per
+// distance, four 16-byte loads each, so that a pass has many rows in
+// flight), its distances, labels and centres in shared memory, and no
 // launch per iteration.  One CTA per hub of the round (larger hubs exit);
 // the distances, labels and the number of children go back to global memory.
 constexpr int SPLIT_SMALL = 2048;
@@ -773,8 +775,11 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
         k_root_init<<<grid_for(n), BT, 0, s>>>(n, root, ids.p, D.p, lab.p);
         CT_COUNT_LAUNCH();
         // one pass of the update kernel with the root as the only centre
-        const int tpd = l2 ? (dp >= 128 ? 32 : dp >= 64 ? 16 : dp >= 32 ? 8 : dp >= 16 ? 4 : dp >= 8 ? 2 : 1) : 1;
-        const int chunk_len = l2 ? 32 * (BT / tpd) : 4 * BT;
+        // lanes per distance: four 16-byte loads each (a pass has many rows in
+        // flight); a chunk is eight passes of a block
+        int tpd = 1;  // a power of two
+        while (l2 && tpd < 32 && 2 * tpd * 16 <= dp) tpd *= 2;
+        const int chunk_len = l2 ? 8 * (BT / tpd) : 4 * BT;
         // pruned updates (L2): centre positions and centre-to-new-centre distances per hub label
         DBuf<int32_t> cpos(l2 ? n : 1, s);
         DBuf<float> dcc(l2 ? n : 1, s);
