@@ -1443,6 +1443,8 @@ __global__ void k_ovf_scatter(int64_t used, const int32_t *__restrict__ orow, co
 constexpr int TC_ROWS = 128;
 constexpr int TC_NB = kItem;            // candidate blocks of one item
 constexpr uint32_t TC_WAIT = 1u << 22;  // mbarrier polls before a wait gives up
+constexpr uint32_t TC_HINT = 1u << 16;  // ns a suspended poll may sleep (woken by the phase)
+constexpr uint32_t TC_SLEEPS = 1u << 14;  // suspended polls before a wait gives up (about a second)
 constexpr int TC_KL = 1024;             // kept pairs rechecked per round
 
 // ---------------------------------------------------------------------------
@@ -1541,6 +1543,7 @@ __global__ void k_to_h16(const float *__restrict__ pts, int64_t n, int dp, int k
 
 constexpr int TC_T = 256;   // threads per CTA (two CTAs per SM)
 constexpr int TC_EB = 768;  // edge buffer entries (one-pass emit)
+constexpr int TC_ISSUER = TC_T - 32;  // lane 0 of the last warp: issues the tiles' MMAs, tracks their loads
 struct __align__(1024) TcShared {
     unsigned char A[2][2][TC_ROWS * 128];  // fp16 candidate rows: buffer, K half (64 halves), 128-byte swizzle
     unsigned char B[2][32 * 128];          // fp16 query rows, the same layout
@@ -1569,8 +1572,10 @@ static_assert(TC_NB == 2 * TC_T, "block prefix assumes two candidate blocks per 
 // work item, two CTAs per SM (one's setup and drain overlap the other's
 // tiles).  Candidate rows arrive by TMA gathers (four rows per instruction,
 // 128-byte swizzle, straight into the MMA's operand layout; lane 0 of each
-// warp issues its 16 rows) two tiles ahead; the MMA of tile t + 1 (second
-// accumulator) runs while tile t is filtered and rechecked.  Rechecks read
+// warp issues its 16 rows, between the filter and its rechecks) two tiles
+// ahead; one thread issues the MMA of tile t + 1 (second accumulator) as the
+// iteration of tile t begins, so that it runs while tile t is filtered and
+// rechecked.  Rechecks read
 // the original fp32 rows from global memory, eight lanes per pair.
 __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Views V, Items items,
                                                      const uint32_t *__restrict__ cand, uint32_t *__restrict__ emask,
@@ -1600,10 +1605,10 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
     uint32_t pairs = 0, kept = 0, guard = 0, band = 0, rows_ld = 0;  // rows_ld, kept: thread 0
     bool failed = false;
     // next phase parity of each barrier (bit b: buffer b): mph in every thread
-    // (warp 0 waits), lph and bph in thread 0 (it waits); thread 0 also tracks
-    // what is in flight, for a clean exit after a failure
+    // (warp 0 waits), lph and bph in the issuing thread (it waits), which also
+    // tracks what is in flight, for a clean exit after a failure
     uint32_t lph = 0u, mph = 0u, bph = 0u, lpend = 0u, mpend = 0u, bpend = 0u;
-    bool tok = true;  // thread 0: its own waits succeeded
+    bool tok = true;  // the issuing thread (TC_ISSUER): its own waits succeeded
 
     if (warp == 0) tc::tmem_alloc(&S.tslot, 64);
     if (tid == 0) {
@@ -1693,7 +1698,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
             }
         }
     };
-    // thread 0: tile t's MMA chain into accumulator columns 32 (t & 1)
+    // the issuing thread: tile t's MMA chain into accumulator columns 32 (t & 1)
     auto mma_tile = [&](int t) {
         const int bf = t & 1;
         constexpr uint32_t idesc = tc::idesc_f16_f32(TC_ROWS, 32);
@@ -1730,7 +1735,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
         prep_map(0);
         prep_map(1);
         prep_map(2);
-        if (tid == 0) {  // expectations before any gather of them is issued
+        if (tid == TC_ISSUER) {  // expectations before any gather of them is issued
             tc::mbar_arrive_expect_tx(&S.bbar, q_bytes);
             bpend = 1u;
             for (int t = 0; t < 2 && t < ntiles; ++t) {
@@ -1747,15 +1752,15 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
             for (int h = 0; h < halves; ++h) tc::tma_gather4(S.B[h] + q * 128, tmap, 64 * h, r0, r1, r2, r3, &S.bbar);
         }
         for (int t = 0; t < 2 && t < ntiles; ++t) issue_tile(t);
-        if (tid == 0) {  // thread 0 alone tracks the load barriers' phases
-            const bool okb = tok && tc::mbar_wait(&S.bbar, bph, TC_WAIT);
+        if (tid == TC_ISSUER) {  // the issuing thread alone tracks the load barriers' phases
+            const bool okb = tok && tc::mbar_wait_sleep(&S.bbar, bph, TC_SLEEPS, TC_HINT);
             if (okb) {
                 bpend = 0u;
                 bph ^= 1u;
             }
             bool okl = okb;
             if (okb && ntiles > 0) {
-                okl = tc::mbar_wait(&S.lbar[0], lph & 1u, TC_WAIT);
+                okl = tc::mbar_wait_sleep(&S.lbar[0], lph & 1u, TC_SLEEPS, TC_HINT);
                 if (okl) {
                     lpend &= ~1u;
                     lph ^= 1u;
@@ -1856,10 +1861,9 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
             if (tid == 0) rows_ld += rows;
             // tile t's MMA has completed (warp 0 waits) and its norms have landed
             cp_async_wait<2>();
-            const bool tk = __shfl_sync(0xffffffffu, tok, 0);  // warp 0: thread 0's own waits
-            bool ok = true;
-            if (warp == 0) ok = tk && tc::mbar_wait(&S.mbar[bf], (mph >> bf) & 1u, TC_WAIT);
-            if (tid == 0 && ok && t + 2 < ntiles) {  // buffer bf takes tile t + 2 (gathers after the barrier)
+            bool ok = tid != TC_ISSUER || tok;  // the issuing thread's own waits so far
+            if (warp == 0) ok = tc::mbar_wait_sleep(&S.mbar[bf], (mph >> bf) & 1u, TC_SLEEPS, TC_HINT);
+            if (tid == TC_ISSUER && ok && t + 2 < ntiles) {  // buffer bf takes tile t + 2 (gathers later)
                 tc::mbar_arrive_expect_tx(&S.lbar[bf], tile_bytes);
                 lpend |= 1u << bf;
             }
@@ -1869,10 +1873,23 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
                 break;
             }
             mph ^= 1u << bf;
-            if (tid == 0) mpend &= ~(1u << bf);
+            if (tid == TC_ISSUER) mpend &= ~(1u << bf);
             tc::fence_after_sync();
             if (co.off && S.en >= TC_EB / 2) flush();  // tile t - 1's rechecks are done
-            if (t + 2 < ntiles) issue_tile(t + 2);
+            // the issuing thread: tile t + 1's MMA into the other accumulator now,
+            // so that it runs while tile t is filtered and rechecked (its rows
+            // were gathered an iteration ago; its columns were last read by tile
+            // t - 1's filter, before the barrier above)
+            if (t + 1 < ntiles && tid == TC_ISSUER && tok) {
+                if (tc::mbar_wait_sleep(&S.lbar[bf ^ 1], (lph >> (bf ^ 1)) & 1u, TC_SLEEPS, TC_HINT)) {
+                    lpend &= ~(1u << (bf ^ 1));
+                    lph ^= 1u << (bf ^ 1);
+                    tc::fence_after_sync();
+                    mma_tile(t + 1);
+                } else {
+                    tok = false;
+                }
+            }
             prep_map(t + 3);
             // epilogue, filter: warp w reads rows 32 (w % 4) .. + 31, queries
             // 16 (w / 4) .. + 15; kept pairs go to the tile's list
@@ -1924,20 +1941,8 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
                 }
             }
             tc::fence_before_sync();
-            // thread 0: tile t + 1's MMA into the other accumulator (its rows
-            // were gathered two iterations ago; its columns were last read by
-            // tile t - 1's filter, before the barrier above)
-            if (t + 1 < ntiles && tid == 0 && tok) {
-                if (tc::mbar_wait(&S.lbar[bf ^ 1], (lph >> (bf ^ 1)) & 1u, TC_WAIT)) {
-                    lpend &= ~(1u << (bf ^ 1));
-                    lph ^= 1u << (bf ^ 1);
-                    tc::fence_after_sync();
-                    mma_tile(t + 1);
-                } else {
-                    tok = false;
-                }
-            }
             __syncthreads();
+            if (t + 2 < ntiles) issue_tile(t + 2);  // lane 0 of each warp, before its recheck
             const int n = S.kn[bf];
             if (tid == 0) {
                 kept += n;
@@ -1983,12 +1988,12 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
         if (tid == 0) stat_add(st, ST_ROWS, rows_ld);
     }
     cp_async_wait<0>();  // no copy into this CTA's shared memory outlives it
-    if (tid == 0) {      // after a failure: let gathers and MMAs in flight finish (bounded)
+    if (tid == TC_ISSUER) {  // after a failure: let gathers and MMAs in flight finish (bounded)
         for (int b = 0; b < 2; ++b) {
             if (lpend >> b & 1u) tc::mbar_wait(&S.lbar[b], (lph >> b) & 1u, TC_WAIT);
             if (mpend >> b & 1u) tc::mbar_wait(&S.mbar[b], (mph >> b) & 1u, TC_WAIT);
         }
-        if (bpend) tc::mbar_wait(&S.bbar, bph, TC_WAIT);
+        if (bpend) tc::mbar_wait_sleep(&S.bbar, bph, TC_SLEEPS, TC_HINT);
     }
     tc::fence_before_sync();
     __syncthreads();

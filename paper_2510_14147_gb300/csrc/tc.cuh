@@ -146,6 +146,27 @@ __device__ __forceinline__ void tma_gather4(void *dst, const void *tmap, int col
         : "memory");
 }
 
+// mbar_wait with the thread suspended between polls (up to `hint_ns` per poll,
+// woken when the phase completes), so that a waiting warp takes no issue slots
+// from the others; gives up after `limit` polls and returns false.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *mbar, uint32_t parity, uint32_t limit, uint32_t hint_ns) {
+    const uint32_t a = smem_u32(mbar);
+    for (uint32_t i = 0; i < limit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n"
+            ".reg .pred p;\n"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            "selp.u32 %0, 1, 0, p;\n"
+            "}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity), "r"(hint_ns)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // 16 consecutive fp32 columns of this warp's 32 tensor-memory lanes.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
