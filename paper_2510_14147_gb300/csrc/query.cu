@@ -1319,6 +1319,33 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
 }
 
 // Work items: every pool segment split into slices of at most kItem blocks.
+// The walk rounds leave a group's candidates in several pool segments; these
+// copy them into one contiguous range per group (longer work items, fewer
+// CTAs in the leaf pass): counts per group, then a warp per segment copies it
+// to its group's range at a place taken from the group's fill counter.
+__global__ void k_group_cand_counts(int nseg, const int32_t *__restrict__ seg_group,
+                                    const int32_t *__restrict__ seg_count, int32_t *__restrict__ gcnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nseg && seg_count[i] > 0) atomicAdd(gcnt + seg_group[i], seg_count[i]);
+}
+__global__ void k_group_cand_copy(int nseg, const int32_t *__restrict__ seg_group,
+                                  const int64_t *__restrict__ seg_begin, const int32_t *__restrict__ seg_count,
+                                  const int64_t *__restrict__ goff, int32_t *__restrict__ gfill,
+                                  const uint32_t *__restrict__ pool, uint32_t *__restrict__ gcand) {
+    const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (i >= nseg) return;
+    const int g = seg_group[i], c = seg_count[i];
+    int64_t base = 0;
+    if (lane == 0) base = goff[g] + atomicAdd(gfill + g, c);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const uint32_t *src = pool + seg_begin[i];
+    for (int k = lane; k < c; k += 32) gcand[base + k] = src[k];
+}
+__global__ void k_iota(int n, int32_t *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = i;
+}
+
 __global__ void k_item_counts(const __grid_constant__ Views V, int nseg, const int32_t *__restrict__ seg_group,
                               const int32_t *__restrict__ seg_count, int32_t *__restrict__ icnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2730,26 +2757,51 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     }
     stacks.reset();
     const int64_t n_cand = (int64_t)hc[2];
-    const int nseg = (int)(uint32_t)hc[1];
-    const int64_t pool_used = (int64_t)hc[0] < pool_cap ? (int64_t)hc[0] : pool_cap;
-    DBuf<uint32_t> emask(l2 ? (pool_used ? pool_used : 1) : 0, s);
-    // work items: pool segments in slices of the clouds' item lengths
+    int nseg = (int)(uint32_t)hc[1];
+    // each group's candidates in one range (segments become one per group)
+    DBuf<uint32_t> gcand(n_cand ? n_cand : 1, s);
+    DBuf<int32_t> gseg_group, gseg_count;
+    DBuf<int64_t> gseg_begin;
+    if (nseg && G) {
+        gseg_group = DBuf<int32_t>(G, s);
+        gseg_count = DBuf<int32_t>(G, s);
+        gseg_begin = DBuf<int64_t>(G + 1, s);
+        DBuf<int32_t> gfill(G, s);
+        CT_CHECK_CUDA(cudaMemsetAsync(gseg_count.p, 0, G * sizeof(int32_t), s));
+        CT_CHECK_CUDA(cudaMemsetAsync(gfill.p, 0, G * sizeof(int32_t), s));
+        k_group_cand_counts<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_group.p, seg_count.p, gseg_count.p);
+        CT_COUNT_LAUNCH();
+        exclusive_scan_i32_to_i64(gseg_count.p, gseg_begin.p, G, gseg_begin.p + G, s);
+        k_group_cand_copy<<<grid_for((int64_t)nseg * 32, 256), 256, 0, s>>>(nseg, seg_group.p, seg_begin.p, seg_count.p,
+                                                                          gseg_begin.p, gfill.p, pool.p, gcand.p);
+        CT_COUNT_LAUNCH();
+        k_iota<<<grid_for(G, 256), 256, 0, s>>>(G, gseg_group.p);
+        CT_COUNT_LAUNCH();
+        CT_LAUNCH_CHECK();
+        nseg = G;
+    }
+    pool.reset();
+    seg_group.reset();
+    seg_count.reset();
+    seg_begin.reset();
+    DBuf<uint32_t> emask(l2 ? (n_cand ? n_cand : 1) : 0, s);
+    // work items: the groups' candidate ranges in slices of the clouds' item lengths
     const int64_t max_items = nseg + n_cand / min_len + 1;
     DBuf<int32_t> icnt(nseg + 1, s), igroup(max_items, s), nitems(1, s);
     DBuf<int64_t> ioff(nseg + 1, s), ibeg(max_items, s), iend(max_items, s);
     Items items{igroup.p, ibeg.p, iend.p, nitems.p};
     CT_CHECK_CUDA(cudaMemsetAsync(nitems.p, 0, sizeof(int32_t), s));
     if (nseg) {
-        k_item_counts<<<grid_for(nseg, 256), 256, 0, s>>>(V, nseg, seg_group.p, seg_count.p, icnt.p);
+        k_item_counts<<<grid_for(nseg, 256), 256, 0, s>>>(V, nseg, gseg_group.p, gseg_count.p, icnt.p);
         CT_COUNT_LAUNCH();
         exclusive_scan_i32_to_i64(icnt.p, ioff.p, nseg, ioff.p + nseg, s);
-        k_item_fill<<<grid_for(nseg, 256), 256, 0, s>>>(V, nseg, seg_group.p, seg_begin.p, seg_count.p, ioff.p,
+        k_item_fill<<<grid_for(nseg, 256), 256, 0, s>>>(V, nseg, gseg_group.p, gseg_begin.p, gseg_count.p, ioff.p,
                                                        igroup.p, ibeg.p, iend.p, nitems.p);
         CT_COUNT_LAUNCH();
         CT_LAUNCH_CHECK();
     }
     DBuf<int32_t> rowcur(n + 1, s);
-    uint32_t *cand_p = pool.p;
+    uint32_t *cand_p = gcand.p;
 
     // alphabet of the strings (edit distance)
     DBuf<uint8_t> amap;
