@@ -806,6 +806,7 @@ constexpr size_t kLeafSmem = sizeof(LeafShared);
 // A work item: a slice of at most kItem candidate blocks of one query group.
 // Heavy groups (large candidate lists) are spread over several CTAs.
 constexpr int kItem = 512;
+constexpr int kItemTC = 1024;  // the tensor-core leaf kernel's work items (precision 1)
 struct Items {
     const int32_t *group;
     const int64_t *begin, *end;
@@ -1468,7 +1469,7 @@ __global__ void k_ovf_scatter(int64_t used, const int32_t *__restrict__ orow, co
 // pinned FP64 sum where that cannot decide.  The emit pass is the FP32 path's,
 // driven by the same per-block edge masks.
 constexpr int TC_ROWS = 128;
-constexpr int TC_NB = kItem;            // candidate blocks of one item
+constexpr int TC_NB = kItemTC;          // candidate blocks of one item
 constexpr uint32_t TC_WAIT = 1u << 22;  // mbarrier polls before a wait gives up
 constexpr uint32_t TC_HINT = 1u << 16;  // ns a suspended poll may sleep (woken by the phase)
 constexpr uint32_t TC_SLEEPS = 1u << 14;  // suspended polls before a wait gives up (about a second)
@@ -1593,7 +1594,7 @@ struct __align__(1024) TcShared {
 };
 constexpr size_t kTcSmem = sizeof(TcShared) + 1024;
 static_assert(2 * (kTcSmem + 1024) <= 228 * 1024, "k_leaf_tc: two CTAs per SM");
-static_assert(TC_NB == 2 * TC_T, "block prefix assumes two candidate blocks per thread");
+static_assert(TC_NB % TC_T == 0, "block prefix takes TC_NB / TC_T candidate blocks per thread");
 
 // Count pass (and one-pass emit) with the FP16 filter.  One CTA of 8 warps per
 // work item, two CTAs per SM (one's setup and drain overlap the other's
@@ -1646,12 +1647,13 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
         tc::mbar_init(&S.bbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    // candidate blocks of the item and their row prefix (two blocks per thread)
+    // candidate blocks of the item and their row prefix (TC_NB / TC_T blocks per thread)
     {
-        int loc[2], sum = 0;
+        constexpr int BPT = TC_NB / TC_T;
+        int loc[BPT], sum = 0;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int i = 2 * tid + k;
+        for (int k = 0; k < BPT; ++k) {
+            const int i = BPT * tid + k;
             int beg = 0, cnt = 0;
             if (i < nb) {
                 const int v = (int)cand[c0 + i];
@@ -1677,8 +1679,8 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
             if (w < warp) base += S.wsum[w];
         int run = base + incl - sum;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            S.bpre[2 * tid + k] = run;
+        for (int k = 0; k < BPT; ++k) {
+            S.bpre[BPT * tid + k] = run;
             run += loc[k];
         }
         if (tid == TC_T - 1) S.bpre[TC_NB] = run;
@@ -2577,7 +2579,7 @@ void tune_reset() {
 }
 LeafChoice leaf_choice(const ct_tree *t, int precision) {
     if (t->metric != CT_L2_F32 || t->dp > 128 || precision == 0) return LeafChoice{0, kItem};
-    if (precision == 1) return LeafChoice{1, kItem};
+    if (precision == 1) return LeafChoice{1, kItemTC};
     LeafChoice c = tuned_choice(t->dp);
     if (c.item_len < 32 || c.item_len > kItem) c.item_len = kItem;
     return c;
@@ -2631,7 +2633,7 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     Views V;
     std::memset(&V, 0, sizeof(V));
     V.nc = C;
-    int max_dp = 4, max_depth = 0, max_len = 0, min_len = kItem;
+    int max_dp = 4, max_depth = 0, max_len = 0, min_len = kItemTC;
     bool any_tc = false, any_fp = false;
     for (int c = 0; c < C; ++c) {
         const ct_tree *tc = trees[c];
