@@ -245,7 +245,7 @@ __global__ void k_chunk_counts(int nh, const int32_t *__restrict__ count, int ch
 // flight), its distances, labels and centres in shared memory, and no
 // launch per iteration.  One CTA per hub of the round (larger hubs exit);
 // the distances, labels and the number of children go back to global memory.
-constexpr int SPLIT_SMALL = 2048;
+constexpr int SPLIT_SMALL = 512;
 template <int TPD>
 __global__ void __launch_bounds__(BT) k_split_small(const float *__restrict__ X, int dp,
                                                     const int32_t *__restrict__ ids, float *__restrict__ D,
@@ -415,22 +415,36 @@ __global__ void k_part_keys(int nh, const int32_t *__restrict__ begin, const int
 
 // Gather the round in sorted order into temporaries; per child: count, first
 // position, first zero-distance position (its centre or a duplicate of it).
+// The sorted keys put each child's points in one run, so a warp combines its
+// lanes of the same run (their destinations increase along the run) and one
+// lane per run updates the child's count, first position and zero point.
 __global__ void k_part_gather(int64_t R, const uint32_t *__restrict__ skeys, const uint32_t *__restrict__ svals,
                               const int32_t *__restrict__ rpos, const int32_t *__restrict__ ids,
                               const float *__restrict__ D, int32_t *__restrict__ tids,
                               float *__restrict__ tD, int32_t *__restrict__ ccount,
                               int32_t *__restrict__ cbegin, int32_t *__restrict__ czero) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= R) return;
-    int src = rpos[svals[i]];
-    int dst = rpos[i];
-    uint32_t gc = skeys[i];
-    float d = D[src];
-    tids[i] = ids[src];
-    tD[i] = d;
-    atomicAdd(&ccount[gc], 1);
-    atomicMin(&cbegin[gc], dst);
-    if (d == 0.0f) atomicMin(&czero[gc], dst);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < R;
+    uint32_t gc = 0xffffffffu;
+    int dst = 0;
+    int zero = INT_MAX;
+    if (valid) {
+        const int src = rpos[svals[i]];
+        dst = rpos[i];
+        gc = skeys[i];
+        const float d = D[src];
+        tids[i] = ids[src];
+        tD[i] = d;
+        if (d == 0.0f) zero = dst;
+    }
+    const unsigned same = __match_any_sync(0xffffffffu, gc);
+    const int lane = threadIdx.x & 31;
+    const int zmin = __reduce_min_sync(same, (unsigned)zero);
+    if (valid && lane == __ffs(same) - 1) {  // the run's first lane: the smallest destination
+        atomicAdd(&ccount[gc], __popc(same));
+        atomicMin(&cbegin[gc], dst);
+        if (zmin != INT_MAX) atomicMin(&czero[gc], zmin);
+    }
 }
 
 // Writes the sorted round back; every point starts the next round labelled 0
@@ -459,12 +473,28 @@ __global__ void k_centre_front(int64_t T, const int32_t *__restrict__ cbegin, co
     }
 }
 
+// Per child, the largest (distance, position) key: a prefix maximum along each
+// run of equal keys in the warp, then one atomic per run (its last lane).
 __global__ void k_child_keys(int64_t R, const uint32_t *__restrict__ skeys, const int32_t *__restrict__ rpos,
                              const float *__restrict__ D, unsigned long long *__restrict__ ckey) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= R) return;
-    int pos = rpos[i];
-    atomicMax(&ckey[skeys[i]], pack_max_key(D[pos], (uint32_t)pos));
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < R;
+    const int lane = threadIdx.x & 31;
+    uint32_t gc = 0xffffffffu;
+    unsigned long long v = 0ull;
+    if (valid) {
+        const int pos = rpos[i];
+        gc = skeys[i];
+        v = pack_max_key(D[pos], (uint32_t)pos);
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long ov = __shfl_up_sync(0xffffffffu, v, o);
+        const uint32_t og = __shfl_up_sync(0xffffffffu, gc, o);
+        if (lane >= o && og == gc && ov > v) v = ov;
+    }
+    const uint32_t next = __shfl_down_sync(0xffffffffu, gc, 1);
+    if (valid && (lane == 31 || next != gc)) atomicMax(&ckey[gc], v);
 }
 
 // Link every hub to its children (consecutive node ids).
