@@ -78,6 +78,8 @@ __device__ __forceinline__ float group_sqdist(const float4 *__restrict__ row, co
     return acc;
 }
 
+constexpr int UPD_PASSES = 8;  // passes of a block over its chunk in k_dist_update_l2
+
 struct Hubs {
     int32_t *begin, *count, *node, *nc, *cur, *done, *level;
     float *thr;
@@ -89,7 +91,7 @@ struct Hubs {
 // and L without reading their row.  dcc[begin + L] = d(c, centre L) of the
 // hub (nullptr: no pruning).
 template <int TPD>
-__global__ void __launch_bounds__(BT) k_dist_update_l2(
+__global__ void __launch_bounds__(BT, 4) k_dist_update_l2(
     const float *__restrict__ X, int dp, const int32_t *__restrict__ ids, float *__restrict__ D,
     int32_t *__restrict__ lab, const int32_t *__restrict__ chunk_hub,
     const int32_t *__restrict__ chunk_start, int chunk_len, Hubs hb, const float *__restrict__ dcc) {
@@ -105,29 +107,46 @@ __global__ void __launch_bounds__(BT) k_dist_update_l2(
     int nq = dp >> 2;
     const float4 *crow = reinterpret_cast<const float4 *>(X + (size_t)ids[cpos] * dp);
     for (int i = threadIdx.x; i < nq; i += blockDim.x) cen[i] = crow[i];
-    __syncthreads();
     constexpr int G = BT / TPD;
     int g = threadIdx.x / TPD, j = threadIdx.x % TPD;
+    // the chunk's passes (chunk_len = UPD_PASSES * G): distances, labels and
+    // ids of every pass first, then the pruning test, then the distances --
+    // three round trips to memory per chunk instead of three per pass
+    float cur[UPD_PASSES];
+    int lb[UPD_PASSES], pid[UPD_PASSES];
+    bool far[UPD_PASSES];
+#pragma unroll
+    for (int p = 0; p < UPD_PASSES; ++p) {
+        const int pos = start + p * G + g;
+        const bool valid = pos < end;
+        cur[p] = valid ? D[pos] : 0.f;
+        lb[p] = valid ? lab[pos] : 0;
+        pid[p] = valid ? ids[pos] : 0;
+        far[p] = !valid;
+    }
+    if (dcc) {
+#pragma unroll
+        for (int p = 0; p < UPD_PASSES; ++p)
+            if (!far[p]) far[p] = dcc[hbeg + lb[p]] >= 2.0f * cur[p] * (1.0f + 0x1p-12f) + 0x1p-60f;
+    }
+    __syncthreads();  // the centre row
     unsigned long long best = 0ull;
-    for (int base = start; base < end; base += G) {
-        int pos = base + g;
-        bool valid = pos < end;
-        float cur = valid ? D[pos] : 0.f;
-        bool far = !valid;
-        if (valid && dcc) far = dcc[hbeg + lab[pos]] >= 2.0f * cur * (1.0f + 0x1p-12f) + 0x1p-60f;
-        if (!far) {  // the same for the group's TPD lanes
-            float s = group_sqdist<TPD>(reinterpret_cast<const float4 *>(X + (size_t)ids[pos] * dp), cen, nq, j);
+#pragma unroll
+    for (int p = 0; p < UPD_PASSES; ++p) {
+        const int pos = start + p * G + g;
+        if (!far[p]) {  // the same for the group's TPD lanes
+            float s = group_sqdist<TPD>(reinterpret_cast<const float4 *>(X + (size_t)pid[p] * dp), cen, nq, j);
             if (j == 0) {
                 float d = sqrtf(s);
-                if (d < cur) {
+                if (d < cur[p]) {
                     D[pos] = d;
                     lab[pos] = lbl;
-                    cur = d;
+                    cur[p] = d;
                 }
             }
         }
-        if (valid && j == 0) {
-            unsigned long long k = pack_max_key(cur, (uint32_t)pos);
+        if (pos < end && j == 0) {
+            unsigned long long k = pack_max_key(cur[p], (uint32_t)pos);
             best = k > best ? k : best;
         }
     }
@@ -809,7 +828,7 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
         // flight); a chunk is eight passes of a block
         int tpd = 1;  // a power of two
         while (l2 && tpd < 32 && 2 * tpd * 16 <= dp) tpd *= 2;
-        const int chunk_len = l2 ? 8 * (BT / tpd) : 4 * BT;
+        const int chunk_len = l2 ? UPD_PASSES * (BT / tpd) : 4 * BT;
         // pruned updates (L2): centre positions and centre-to-new-centre distances per hub label
         DBuf<int32_t> cpos(l2 ? n : 1, s);
         DBuf<float> dcc(l2 ? n : 1, s);
