@@ -416,20 +416,25 @@ __global__ void k_chunk_fill(int nh, const int32_t *__restrict__ begin, const in
     }
 }
 
-// Partition keys for the round: key = child_base[hub] + label, value = round index.
-__global__ void k_part_keys(int nh, const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+// Partition keys for the round: key = child_base[hub] + label, value = round
+// index.  One thread per point of the round; its hub is the last one whose
+// round offset is at most the index (hubs without points share an offset with
+// the next hub and are skipped by the search).
+__global__ void k_part_keys(int64_t R, int nh, const int32_t *__restrict__ begin,
                             const int64_t *__restrict__ round_off, const int64_t *__restrict__ child_base,
                             const int32_t *__restrict__ lab, uint32_t *__restrict__ keys,
                             uint32_t *__restrict__ vals, int32_t *__restrict__ rpos) {
-    int h = blockIdx.x;
-    int b = begin[h], cnt = count[h];
-    int64_t ro = round_off[h], cb = child_base[h];
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        int64_t r = ro + i;
-        keys[r] = (uint32_t)(cb + lab[b + i]);
-        vals[r] = (uint32_t)r;
-        rpos[r] = b + i;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    int lo = 0, hi = nh;  // round_off[lo] <= r, and r < round_off[hi] unless hi = nh
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(round_off + mid) <= r) lo = mid; else hi = mid;
     }
+    const int pos = begin[lo] + (int)(r - round_off[lo]);
+    keys[r] = (uint32_t)(child_base[lo] + lab[pos]);
+    vals[r] = (uint32_t)r;
+    rpos[r] = pos;
 }
 
 // Gather the round in sorted order into temporaries; per child: count, first
@@ -995,8 +1000,8 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
             to_host(tot, i64tmp.p, 2, s);
             const int64_t T = tot[0], R = tot[1];
             if (n_nodes + T > cap) CT_FAIL(CT_ECUDA, "vertex capacity exceeded");
-            k_part_keys<<<(unsigned)nh, BT, 0, s>>>((int)nh, H.begin, H.count, round_off.p, child_base.p, lab.p,
-                                                    pk.p, pv.p, rpos.p);
+            k_part_keys<<<grid_for(R), BT, 0, s>>>(R, (int)nh, H.begin, round_off.p, child_base.p, lab.p, pk.p,
+                                                   pv.p, rpos.p);
             CT_COUNT_LAUNCH();
             radix_sort_pairs(pk.p, pv.p, tk.p, tv.p, R, bits_for(T), s);
             DBuf<int32_t> ccount(T, s), cbegin(T, s), czero(T, s), is_hub(T, s);
