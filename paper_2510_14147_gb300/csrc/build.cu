@@ -404,16 +404,21 @@ __global__ void k_active_chunks(int64_t nchunks, const int32_t *__restrict__ chu
     }
 }
 
-__global__ void k_chunk_fill(int nh, const int32_t *__restrict__ begin, const int32_t *__restrict__ count,
+// Chunk table of a round, one thread per chunk: its hub is the last one whose
+// chunk offset is at most the chunk's index (hubs without chunks share an
+// offset with the next hub and are skipped by the search).
+__global__ void k_chunk_fill(int64_t nchunks, int nh, const int32_t *__restrict__ begin,
                              const int64_t *__restrict__ coff, int chunk_len,
                              int32_t *__restrict__ chunk_hub, int32_t *__restrict__ chunk_start) {
-    int h = blockIdx.x;
-    if (h >= nh) return;
-    int nchunks = (count[h] + chunk_len - 1) / chunk_len;
-    for (int i = threadIdx.x; i < nchunks; i += blockDim.x) {
-        chunk_hub[coff[h] + i] = h;
-        chunk_start[coff[h] + i] = begin[h] + i * chunk_len;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nchunks) return;
+    int lo = 0, hi = nh;  // coff[lo] <= c, and c < coff[hi] unless hi = nh
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(coff + mid) <= c) lo = mid; else hi = mid;
     }
+    chunk_hub[c] = lo;
+    chunk_start[c] = begin[lo] + (int)(c - coff[lo]) * chunk_len;
 }
 
 // Partition keys for the round: key = child_base[hub] + label, value = round
@@ -877,7 +882,7 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
         {
             DBuf<int64_t> coff(1, s);
             CT_CHECK_CUDA(cudaMemsetAsync(coff.p, 0, sizeof(int64_t), s));
-            k_chunk_fill<<<1, BT, 0, s>>>(1, H.begin, H.count, coff.p, chunk_len, chub.p, cst.p);
+            k_chunk_fill<<<grid_for(nchunks0), BT, 0, s>>>(nchunks0, 1, H.begin, coff.p, chunk_len, chub.p, cst.p);
             CT_COUNT_LAUNCH();
             update(H, nchunks0, chub.p, cst.p);
         }
@@ -913,7 +918,7 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
             cst.grow(nchunks);
             chub2.grow(nchunks);
             cst2.grow(nchunks);
-            k_chunk_fill<<<(unsigned)nh, 64, 0, s>>>((int)nh, H.begin, H.count, coff.p, chunk_len, chub.p, cst.p);
+            k_chunk_fill<<<grid_for(nchunks), BT, 0, s>>>(nchunks, (int)nh, H.begin, coff.p, chunk_len, chub.p, cst.p);
             CT_COUNT_LAUNCH();
             CT_LAUNCH_CHECK();
 

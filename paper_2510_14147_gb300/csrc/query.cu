@@ -2223,50 +2223,80 @@ __global__ void k_row_classes(const int64_t *__restrict__ row_ptr, int64_t n, in
     lists[(int64_t)cls * n + slot] = (int32_t)i;
 }
 
-// CTA of P threads per row (P a power of two, rows of at most P entries):
-// bitonic network with one element per thread; strides below 32 exchange by
-// shuffles, wider strides through shared memory.
-template <int P>
-__global__ void __launch_bounds__(P) k_sort_pow2(const int32_t *__restrict__ rows, const int32_t *__restrict__ count,
-                                                 const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col,
-                                                 float *__restrict__ dist) {
-    __shared__ int sk[P];
-    __shared__ float sv[P];
-    const int i = threadIdx.x;
+// Bitonic network over the 32 lanes of a warp: (key, val) pairs ascending by
+// key, lane i ending with the i-th smallest.
+__device__ __forceinline__ void warp_sort32(int &key, float &val, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int ok = __shfl_xor_sync(0xffffffffu, key, j);
+            const float ov = __shfl_xor_sync(0xffffffffu, val, j);
+            const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+            if ((lower == up) ? (ok < key) : (ok > key)) {
+                key = ok;
+                val = ov;
+            }
+        }
+    }
+}
+
+// CTA of P threads per row of 33 .. CAP entries (16 CAP bytes of dynamic
+// shared memory): warps sort runs of 32
+// entries (warp_sort32), then runs are merged in pairs in shared memory until
+// one is left.  The columns of a row are distinct, so an entry's place in the
+// merged run is its index in its own run plus the number of smaller entries
+// in the partner run (a binary search) -- every entry moves independently,
+// one barrier per merge round.
+template <int P, int CAP>
+__global__ void __launch_bounds__(P) k_sort_merge(const int32_t *__restrict__ rows, const int32_t *__restrict__ count,
+                                                  const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col,
+                                                  float *__restrict__ dist) {
+    extern __shared__ int sort_smem[];  // 16 CAP bytes: keys, then values, two buffers each
+    int (*sk)[CAP] = reinterpret_cast<int (*)[CAP]>(sort_smem);
+    float (*sv)[CAP] = reinterpret_cast<float (*)[CAP]>(sort_smem + 2 * CAP);
+    const int tid = threadIdx.x, lane = tid & 31;
     for (int w = blockIdx.x; w < *count; w += gridDim.x) {
         const int r = rows[w];
         const int64_t b = row_ptr[r];
-        const int len = (int)(row_ptr[r + 1] - b);
-        int key = i < len ? col[b + i] : INT_MAX;
-        float val = i < len ? dist[b + i] : 0.f;
-#pragma unroll
-        for (int k = 2; k <= P; k <<= 1) {
-#pragma unroll
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                int ok;
-                float ov;
-                if (j >= 32) {
-                    __syncthreads();
-                    sk[i] = key;
-                    sv[i] = val;
-                    __syncthreads();
-                    ok = sk[i ^ j];
-                    ov = sv[i ^ j];
-                } else {
-                    ok = __shfl_xor_sync(0xffffffffu, key, j);
-                    ov = __shfl_xor_sync(0xffffffffu, val, j);
-                }
-                const bool up = (i & k) == 0, lower = (i & j) == 0;
-                const bool swap = (lower == up) ? (ok < key) : (ok > key);
-                if (swap) {
-                    key = ok;
-                    val = ov;
-                }
+        const int64_t len64 = row_ptr[r + 1] - b;
+        const int len = len64 < CAP ? (int)len64 : CAP;  // rows of this class have at most CAP entries
+        __syncthreads();  // the previous row's write-back has read sk / sv
+        for (int rs = tid & ~31; rs < len; rs += P) {
+            const int i = rs + lane;
+            int key = i < len ? col[b + i] : INT_MAX;
+            float val = i < len ? dist[b + i] : 0.f;
+            warp_sort32(key, val, lane);
+            if (i < len) {
+                sk[0][i] = key;
+                sv[0][i] = val;
             }
         }
-        if (i < len) {
-            col[b + i] = key;
-            dist[b + i] = val;
+        __syncthreads();
+        int cur = 0;
+        for (int run = 32; run < len; run <<= 1) {
+            for (int p = tid; p < len; p += P) {
+                const int start = p & ~(run - 1), pst = start ^ run;  // own run, partner run
+                const int key = sk[cur][p];
+                const float val = sv[cur][p];
+                int out = p;  // the last run without a partner keeps its place
+                if (pst < len) {
+                    int lo = pst, hi = min(pst + run, len);
+                    while (lo < hi) {  // partner entries below key
+                        const int mid = (lo + hi) >> 1;
+                        if (sk[cur][mid] < key) lo = mid + 1; else hi = mid;
+                    }
+                    out = min(start, pst) + (p - start) + (lo - pst);
+                }
+                sk[cur ^ 1][out] = key;
+                sv[cur ^ 1][out] = val;
+            }
+            __syncthreads();
+            cur ^= 1;
+        }
+        for (int i = tid; i < len; i += P) {
+            col[b + i] = sk[cur][i];
+            dist[b + i] = sv[cur][i];
         }
     }
 }
@@ -2282,64 +2312,12 @@ __global__ void k_sort_small(const int32_t *__restrict__ rows, const int32_t *__
     int len = (int)(row_ptr[r + 1] - b);
     int key = lane < len ? col[b + lane] : INT_MAX;
     float val = lane < len ? dist[b + lane] : 0.f;
-    for (int k = 2; k <= 32; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            int ok = __shfl_xor_sync(0xffffffffu, key, j);
-            float ov = __shfl_xor_sync(0xffffffffu, val, j);
-            bool up = (lane & k) == 0;
-            bool lower = (lane & j) == 0;
-            bool take_min = lower == up;
-            bool swap = take_min ? (ok < key) : (ok > key);
-            if (swap) { key = ok; val = ov; }
-        }
-    }
+    warp_sort32(key, val, lane);
     if (lane < len) {
         col[b + lane] = key;
         dist[b + lane] = val;
     }
 }
-
-// CTA per row, 1025..SORT_MID entries: bitonic sort in shared memory.
-__global__ void __launch_bounds__(512) k_sort_mid(const int32_t *__restrict__ rows, const int32_t *__restrict__ count,
-                                                  const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col,
-                                                  float *__restrict__ dist) {
-    __shared__ int sk[SORT_MID];
-    __shared__ float sv[SORT_MID];
-    for (int w = blockIdx.x; w < *count; w += gridDim.x) {
-        int r = rows[w];
-        int64_t b = row_ptr[r];
-        int len = (int)(row_ptr[r + 1] - b);
-        int P = 64;
-        while (P < len) P <<= 1;
-        __syncthreads();
-        for (int i = threadIdx.x; i < P; i += blockDim.x) {
-            sk[i] = i < len ? col[b + i] : INT_MAX;
-            sv[i] = i < len ? dist[b + i] : 0.f;
-        }
-        __syncthreads();
-        for (int k = 2; k <= P; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                    int ix = i ^ j;
-                    if (ix > i) {
-                        bool up = (i & k) == 0;
-                        int a = sk[i], c = sk[ix];
-                        if ((a > c) == up) {
-                            sk[i] = c; sk[ix] = a;
-                            float t = sv[i]; sv[i] = sv[ix]; sv[ix] = t;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        for (int i = threadIdx.x; i < len; i += blockDim.x) {
-            col[b + i] = sk[i];
-            dist[b + i] = sv[i];
-        }
-    }
-}
-
 // Long rows: gather (row rank, col) keys and sort them globally.
 __global__ void k_big_gather(const int32_t *__restrict__ rows, int nbig, const int64_t *__restrict__ row_ptr,
                              const int64_t *__restrict__ big_off, const int32_t *__restrict__ col,
@@ -2390,20 +2368,20 @@ void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int
         k_sort_small<<<grid_for((int64_t)hc[0] * 32, 256), 256, 0, s>>>(lists.p, counts.p, row_ptr, col, dist);
         CT_COUNT_LAUNCH();
     }
-    auto pow2 = [&](int cls, auto kern, int P) {
+    auto merge = [&](int cls, auto kern, int P, int cap) {
         if (!hc[cls]) return;
-        const int blocks = (int)std::min<int64_t>(hc[cls], (int64_t)num_sms() * (2048 / P));
-        kern<<<blocks, P, 0, s>>>(lists.p + (int64_t)cls * n, counts.p + cls, row_ptr, col, dist);
+        const int smem = 16 * cap;
+        if (smem > 48 * 1024)
+            CT_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        const int per_sm = std::min(2048 / P, (200 * 1024) / smem);
+        const int blocks = (int)std::min<int64_t>(hc[cls], (int64_t)num_sms() * per_sm);
+        kern<<<blocks, P, smem, s>>>(lists.p + (int64_t)cls * n, counts.p + cls, row_ptr, col, dist);
         CT_COUNT_LAUNCH();
     };
-    pow2(1, k_sort_pow2<128>, 128);
-    pow2(2, k_sort_pow2<512>, 512);
-    pow2(3, k_sort_pow2<1024>, 1024);
-    if (hc[4]) {
-        int blocks = (int)std::min<int64_t>(hc[4], (int64_t)num_sms() * 8);
-        k_sort_mid<<<blocks, 512, 0, s>>>(lists.p + 4 * n, counts.p + 4, row_ptr, col, dist);
-        CT_COUNT_LAUNCH();
-    }
+    merge(1, k_sort_merge<128, 128>, 128, 128);
+    merge(2, k_sort_merge<256, 512>, 256, 512);
+    merge(3, k_sort_merge<256, 1024>, 256, 1024);
+    merge(4, k_sort_merge<512, SORT_MID>, 512, SORT_MID);
     if (hc[5]) {
         int nb = hc[5];
         const int32_t *big = lists.p + 5 * n;

@@ -122,6 +122,22 @@ def test_row_lengths_in_every_sort_class():
         assert sorted(set(deg.tolist())) == [19, 99, 399, 899, 2999, 4999]
 
 
+def test_row_lengths_at_sort_class_boundaries():
+    """Rows one below, at and one above each length boundary of the row sort
+    (32, 128, 512, 1024, 4096) and at the merge runs' sizes (64, 65, 200):
+    the sorted rows equal brute force's."""
+    rng = np.random.default_rng(5)
+    degrees = (32, 33, 64, 65, 127, 128, 129, 200, 511, 512, 513, 1023, 1024, 1025, 4095, 4096, 4097)
+    parts = [rng.random(4) * 100.0 + rng.random((d + 1, 4)) * 0.1 for d in degrees]
+    x = np.concatenate(parts).astype(np.float32)
+    x = x[rng.permutation(x.shape[0])]
+    ref = oracle.brute_force(oracle.Space(points=x), 0.5)
+    for precision in (0, 1):
+        out = gpu_graph(points=x, eps=0.5, precision=precision)
+        assert_csr_matches(out, ref)
+        assert sorted(set(np.diff(out["row_ptr"]).tolist())) == list(degrees)
+
+
 def test_complete_graph_and_include_self():
     x = I.uniform_cube(700, 4, seed=1)
     sp = oracle.Space(points=x)
