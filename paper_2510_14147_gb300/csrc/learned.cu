@@ -34,7 +34,14 @@ __global__ void k_pos_group(int64_t n, int G, const int32_t *__restrict__ group_
     gof[i] = lo;
 }
 
-__device__ __forceinline__ float rel_log(float r, double eps) { return (float)log1p((double)r / eps); }
+// log1p(r / e) in fp32 with inv_e = fl(1 / e), log_e = fl(log e): the ratio
+// carries a relative error below 2^-22, which moves the logarithm by less
+// than 2^-22; past 2^100 the ratio takes log r - log e (log1p(q) and log q
+// agree far below fp32 resolution there, and fl(r inv_e) may overflow).
+__device__ __forceinline__ float rel_log(float r, float inv_e, float log_e) {
+    const float q = r * inv_e;
+    return q < 0x1p100f ? log1pf(q) : logf(r) - log_e;
+}
 
 // The 16 features of the query at tree position i (see
 // ct_predictor_features); e = max(eps, 1e-20):
@@ -48,7 +55,8 @@ __global__ void __launch_bounds__(256) k_features(
     const int32_t *__restrict__ leaf_ids, int n_leaves, const int32_t *__restrict__ node_begin,
     const int32_t *__restrict__ node_count, const float *__restrict__ radius, const int32_t *__restrict__ parent,
     const int32_t *__restrict__ group_begin, const int32_t *__restrict__ group_count,
-    const float *__restrict__ group_radius, const int32_t *__restrict__ gof, double e, Norm nm,
+    const float *__restrict__ group_radius, const int32_t *__restrict__ gof, double e, float inv_e, float log_e,
+    Norm nm,
     float *__restrict__ x) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -60,7 +68,7 @@ __global__ void __launch_bounds__(256) k_features(
     const int leaf = leaf_ids[lo];
     const int g = gof[i];
     float f[MLP_IN];
-    f[0] = rel_log(dcen[i], e);
+    f[0] = rel_log(dcen[i], inv_e, log_e);
     f[1] = 0.f;
     if (l2) {
         const float4 *a = reinterpret_cast<const float4 *>(pts + (size_t)i * dp);
@@ -74,15 +82,15 @@ __global__ void __launch_bounds__(256) k_features(
             s = fmaf(d2, d2, s);
             s = fmaf(d3, d3, s);
         }
-        f[1] = rel_log(sqrtf(s), e);
+        f[1] = rel_log(sqrtf(s), inv_e, log_e);
     }
-    f[2] = rel_log(group_radius[g], e);
+    f[2] = rel_log(group_radius[g], inv_e, log_e);
     f[3] = log2f((float)group_count[g]);
     int v = leaf;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         f[4 + 2 * k] = log1pf((float)node_count[v]);
-        f[5 + 2 * k] = rel_log(radius[v], e);
+        f[5 + 2 * k] = rel_log(radius[v], inv_e, log_e);
         if (k < 3 && parent[v] >= 0) v = parent[v];
     }
     const double mult[4] = {1.0, 2.0, 4.0, 16.0};
@@ -254,7 +262,8 @@ void predictor_features(const ct_tree *t, double eps, const ct_predictor *P, flo
     const double e = eps > 1e-20 ? eps : 1e-20;
     k_features<<<grid_of(n, 256), 256, 0, s>>>(n, t->dp, t->metric == CT_L2_F32, t->pts, t->dcen, t->leaf_ids,
                                                t->n_leaves, t->node_begin, t->node_count, t->radius, t->parent,
-                                               t->group_begin, t->group_count, t->group_radius, gof.p, e, nm, x);
+                                               t->group_begin, t->group_count, t->group_radius, gof.p, e, (float)(1.0 / e),
+                                               (float)std::log(e), nm, x);
     CT_COUNT_LAUNCH();
     CT_LAUNCH_CHECK();
 }
