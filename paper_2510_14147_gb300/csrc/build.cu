@@ -86,6 +86,61 @@ struct Hubs {
     unsigned long long *key;
 };
 
+// The next split step of a hub, taken inside the update pass by the hub's
+// last block to finish (its arrival completes the hub's count in `arrive`;
+// every other block of the hub has written its distances and its key by
+// then): k_hub_step for that hub, then k_centre_dists for its new centre.
+// One launch per split iteration instead of three; nothing waits -- the
+// blocks only count their arrivals.
+struct Step {
+    int32_t *arrive;      // per hub: blocks of the pass that have finished (reset by the last)
+    int32_t *active_out;  // hubs that took a new centre
+    int32_t *cpos;        // centre positions per hub label
+    float *dcc;           // distances of the new centre to the hub's centres (read by the pass, then rewritten)
+};
+
+template <int TPD>
+__device__ __noinline__ void step_tail(const float *__restrict__ X, int dp, const int32_t *__restrict__ ids,
+                                       Hubs hb, int h, float4 *cen, Step st) {
+    __shared__ int s_act, s_nc, s_cur;
+    if (threadIdx.x == 0) {
+        const unsigned long long k = atomicAdd(&hb.key[h], 0ull);  // every block's maximum has landed
+        const float v = key_value(k);
+        s_act = 0;
+        if (k == 0ull || !(v > hb.thr[h])) {
+            hb.done[h] = 1;
+        } else {
+            const int b = hb.begin[h], nc = hb.nc[h];
+            const int cur = (int32_t)key_pos(k);
+            hb.cur[h] = cur;
+            st.cpos[b] = b;  // label 0: the hub's own centre
+            st.cpos[b + nc] = cur;
+            hb.nc[h] = nc + 1;
+            hb.key[h] = 0ull;
+            atomicAdd(st.active_out, 1);
+            s_act = 1;
+            s_nc = nc + 1;
+            s_cur = cur;
+        }
+        st.arrive[h] = 0;
+    }
+    __syncthreads();
+    if (!s_act) return;
+    const int b = hb.begin[h], nc = s_nc, nq = dp >> 2;
+    const float4 *crow = reinterpret_cast<const float4 *>(X + (size_t)ids[s_cur] * dp);
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) cen[i] = crow[i];
+    __syncthreads();
+    constexpr int G = BT / TPD;
+    const int g = threadIdx.x / TPD, j = threadIdx.x % TPD;
+    for (int L0 = 0; L0 < nc; L0 += G) {  // every group runs the same number of steps
+        const int L = L0 + g;
+        const int pos = st.cpos[b + (L < nc ? L : 0)];
+        const float dd = sqrtf(group_sqdist<TPD>(reinterpret_cast<const float4 *>(X + (size_t)ids[pos] * dp), cen,
+                                                 nq, j));
+        if (L < nc && j == 0) st.dcc[b + L] = dd;
+    }
+}
+
 // Pruning (L2): a point labelled L cannot come closer to the new centre c
 // than D when d(c, centre L) >= 2 D (triangle inequality); such points keep D
 // and L without reading their row.  dcc[begin + L] = d(c, centre L) of the
@@ -94,7 +149,7 @@ template <int TPD>
 __global__ void __launch_bounds__(BT, 4) k_dist_update_l2(
     const float *__restrict__ X, int dp, const int32_t *__restrict__ ids, float *__restrict__ D,
     int32_t *__restrict__ lab, const int32_t *__restrict__ chunk_hub,
-    const int32_t *__restrict__ chunk_start, int chunk_len, Hubs hb, const float *__restrict__ dcc) {
+    const int32_t *__restrict__ chunk_start, int chunk_len, Hubs hb, const float *dcc, Step st) {
     extern __shared__ float4 cen[];
     int c = blockIdx.x;
     int h = chunk_hub[c];
@@ -155,6 +210,20 @@ __global__ void __launch_bounds__(BT, 4) k_dist_update_l2(
         best = v > best ? v : best;
     }
     if ((threadIdx.x & 31) == 0 && best) atomicMax(&hb.key[h], best);
+    if (st.arrive) {  // the hub's last block takes its next step
+        __shared__ int s_last;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int blocks = (hb.count[h] + chunk_len - 1) / chunk_len;  // all of the hub's chunks run
+            s_last = atomicAdd(&st.arrive[h], 1) == blocks - 1;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            step_tail<TPD>(X, dp, ids, hb, h, cen, st);
+        }
+    }
 }
 
 // Edit distance: one thread per point; the newest centre is the pattern of
@@ -843,12 +912,12 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
         DBuf<int32_t> cpos(l2 ? n : 1, s);
         DBuf<float> dcc(l2 ? n : 1, s);
         bool prune = false;  // off for the root's first pass (no labels yet)
-        auto update = [&](Hubs &hb, int64_t nchunks, const int32_t *chub, const int32_t *cst) {
+        auto update = [&](Hubs &hb, int64_t nchunks, const int32_t *chub, const int32_t *cst, Step st) {
             if (!nchunks) return;
             if (l2) {
                 size_t sm = (size_t)dp * sizeof(float);
                 switch (tpd) {
-#define CT_UPD(T) case T: k_dist_update_l2<T><<<(unsigned)nchunks, BT, sm, s>>>(Xp.p, dp, ids.p, D.p, lab.p, chub, cst, chunk_len, hb, prune ? dcc.p : nullptr); break;
+#define CT_UPD(T) case T: k_dist_update_l2<T><<<(unsigned)nchunks, BT, sm, s>>>(Xp.p, dp, ids.p, D.p, lab.p, chub, cst, chunk_len, hb, prune ? dcc.p : nullptr, st); break;
                     CT_UPD(1) CT_UPD(2) CT_UPD(4) CT_UPD(8) CT_UPD(16) CT_UPD(32)
 #undef CT_UPD
                 }
@@ -884,7 +953,7 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
             CT_CHECK_CUDA(cudaMemsetAsync(coff.p, 0, sizeof(int64_t), s));
             k_chunk_fill<<<grid_for(nchunks0), BT, 0, s>>>(nchunks0, 1, H.begin, coff.p, chunk_len, chub.p, cst.p);
             CT_COUNT_LAUNCH();
-            update(H, nchunks0, chub.p, cst.p);
+            update(H, nchunks0, chub.p, cst.p, Step{});
         }
         DBuf<int32_t> is_root_hub(1, s);
         k_root_node<<<1, 1, 0, s>>>(n, zeta, pts->metric, H.key, nb.p, ncnt.p, cbeg.p, ccnt.p, rad.p, lvl.p, H,
@@ -902,6 +971,7 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
         DBuf<float> tD(n, s);
         DBuf<int32_t> active(3, s);  // hub activations of a burst, active hubs, active chunks
         DBuf<int32_t> hlist(n, s), chub2(nchunks0, s), cst2(nchunks0, s);
+        DBuf<int32_t> arrive(l2 ? cap_h + 1 : 1, s);  // per hub: finished blocks of an update pass
         DBuf<int64_t> i64tmp(2, s);
 
         while (nh > 0) {
@@ -927,6 +997,7 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
                 ProfScope prof_split("build_split", s);
                 int burst = 1;
                 int64_t iters = 0;
+                bool first_step = true;
                 // the hubs and chunks a burst visits: all at first, then those
                 // of the hubs still splitting after the previous burst
                 const int32_t *hl = nullptr;
@@ -961,10 +1032,13 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
                     if (iters > n + 2 + 16) CT_FAIL(CT_ECUDA, "split loop did not terminate");
                     iters += burst;
                     CT_CHECK_CUDA(cudaMemsetAsync(active.p, 0, 3 * sizeof(int32_t), s));
-                    for (int it = 0; it < burst; ++it) {
-                        k_hub_step<<<grid_for(nl), BT, 0, s>>>((int)nl, hl, H, active.p, l2 ? cpos.p : nullptr);
-                        CT_COUNT_LAUNCH();
-                        if (l2) {
+                    if (l2) {
+                        // the level's first step by its own kernels; every later
+                        // step is taken inside the update pass by each hub's last block
+                        if (first_step) {
+                            CT_CHECK_CUDA(cudaMemsetAsync(arrive.p, 0, nh * sizeof(int32_t), s));
+                            k_hub_step<<<grid_for(nl), BT, 0, s>>>((int)nl, hl, H, active.p, cpos.p);
+                            CT_COUNT_LAUNCH();
                             switch (tpd) {
 #define CT_CD(T) case T: k_centre_dists<T><<<(unsigned)nl, BT, 0, s>>>(Xp.p, dp, ids.p, H, hl, cpos.p, dcc.p); break;
                                 CT_CD(1) CT_CD(2) CT_CD(4) CT_CD(8) CT_CD(16) CT_CD(32)
@@ -972,8 +1046,16 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
                             }
                             CT_COUNT_LAUNCH();
                             prune = true;
+                            first_step = false;
                         }
-                        update(H, nck, cb, cs);
+                        const Step st{arrive.p, active.p, cpos.p, dcc.p};
+                        for (int it = 0; it < burst; ++it) update(H, nck, cb, cs, st);
+                    } else {
+                        for (int it = 0; it < burst; ++it) {
+                            k_hub_step<<<grid_for(nl), BT, 0, s>>>((int)nl, hl, H, active.p, nullptr);
+                            CT_COUNT_LAUNCH();
+                            update(H, nck, cb, cs, Step{});
+                        }
                     }
                     k_active_hubs<<<grid_for(nh), BT, 0, s>>>((int)nh, H.done, hlist.p, active.p + 1);
                     CT_COUNT_LAUNCH();
