@@ -752,6 +752,60 @@ __global__ void k_gather_strings(int64_t n, const int32_t *__restrict__ perm, co
 }
 
 // Sort keys putting larger radii first (radii are non-negative floats).
+// Query groups: greedy runs of consecutive sibling leaf blocks of at most
+// kGroupSize points in total (a larger block is a group of its own).  The
+// leaf blocks are in position order; k_group_prep lays out each block's size
+// and parent in that order, a run of siblings starts where the parent
+// changes, and one thread walks each run (sequential reads), marking where
+// its groups start and recording each group's size there.
+__global__ void k_group_prep(int L, const int32_t *__restrict__ leaf_ids, const int32_t *__restrict__ node_count,
+                             const int32_t *__restrict__ parent, int32_t *__restrict__ lcount,
+                             int32_t *__restrict__ lpar) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L) return;
+    const int v = leaf_ids[i];
+    lcount[i] = node_count[v];
+    lpar[i] = parent[v];
+}
+
+__global__ void k_group_marks(int L, const int32_t *__restrict__ lcount, const int32_t *__restrict__ lpar,
+                              int32_t *__restrict__ gstart, int32_t *__restrict__ gsize,
+                              unsigned long long *__restrict__ maxc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L) return;
+    const int p = lpar[i];
+    if (i > 0 && lpar[i - 1] == p) return;  // not the first block of its sibling run
+    int first = i, acc = lcount[i], big = 0;
+    gstart[i] = 1;
+    for (int j = i + 1; j < L && lpar[j] == p; ++j) {
+        const int c = lcount[j];
+        if (acc + c <= kGroupSize) {
+            acc += c;
+            gstart[j] = 0;
+        } else {
+            gsize[first] = acc;
+            big = max(big, acc);
+            first = j;
+            acc = c;
+            gstart[j] = 1;
+        }
+    }
+    gsize[first] = acc;
+    big = max(big, acc);
+    atomicMax(maxc, (unsigned long long)big);
+}
+
+__global__ void k_group_scatter(int L, const int32_t *__restrict__ leaf_ids, const int32_t *__restrict__ node_begin,
+                                const int32_t *__restrict__ gstart, const int32_t *__restrict__ gsize,
+                                const int64_t *__restrict__ gidx, int32_t *__restrict__ group_begin,
+                                int32_t *__restrict__ group_count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L || !gstart[i]) return;
+    const int64_t g = gidx[i];
+    group_begin[g] = node_begin[leaf_ids[i]];
+    group_count[g] = gsize[i];
+}
+
 __global__ void k_radius_desc_keys(int ng, const float *__restrict__ r, uint32_t *__restrict__ keys,
                                    uint32_t *__restrict__ vals) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1212,38 +1266,34 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
         t->leaf_ids = (int32_t *)dmalloc(sizeof(int32_t) * (size_t)(hc[0] ? hc[0] : 1), s);
         if (hc[0]) CT_CHECK_CUDA(cudaMemcpyAsync(t->leaf_ids, v1.p, sizeof(int32_t) * hc[0], cudaMemcpyDeviceToDevice, s));
     }
-    // query groups: greedy runs of consecutive sibling leaf blocks (host side)
+    // query groups: greedy runs of consecutive sibling leaf blocks (k_group_marks)
     {
         const int L = t->n_leaves;
-        std::vector<int32_t> lid(L), nbh(n_nodes), nch(n_nodes), parh(n_nodes);
-        to_host(lid.data(), t->leaf_ids, L, s);
-        to_host(nbh.data(), t->node_begin, n_nodes, s);
-        to_host(nch.data(), t->node_count, n_nodes, s);
-        to_host(parh.data(), t->parent, n_nodes, s);
-        std::vector<int32_t> gb, gc;
-        gb.reserve(L);
-        gc.reserve(L);
-        int cur_par = -2, maxc = 0;
-        for (int i = 0; i < L; ++i) {
-            int v = lid[i], b = nbh[v], c = nch[v], p = parh[v];
-            if (!gc.empty() && p == cur_par && gc.back() + c <= kGroupSize) {
-                gc.back() += c;
-            } else {
-                gb.push_back(b);
-                gc.push_back(c);
-                cur_par = p;
-            }
-            maxc = std::max(maxc, gc.back());
+        DBuf<int32_t> gstart(L ? L : 1, s), gsize(L ? L : 1, s), lcount(L ? L : 1, s), lpar(L ? L : 1, s);
+        DBuf<int64_t> gidx(L ? L : 1, s), tot(2, s);  // tot: group count, largest group
+        CT_CHECK_CUDA(cudaMemsetAsync(tot.p, 0, 2 * sizeof(int64_t), s));
+        if (L) {
+            k_group_prep<<<grid_for(L), BT, 0, s>>>(L, t->leaf_ids, t->node_count, t->parent, lcount.p, lpar.p);
+            CT_COUNT_LAUNCH();
+            k_group_marks<<<grid_for(L), BT, 0, s>>>(L, lcount.p, lpar.p, gstart.p, gsize.p,
+                                                     reinterpret_cast<unsigned long long *>(tot.p + 1));
+            CT_COUNT_LAUNCH();
+            exclusive_scan_i32_to_i64(gstart.p, gidx.p, L, tot.p, s);
         }
-        const int G = (int)gb.size();
+        int64_t gh[2] = {0, 0};
+        to_host(gh, tot.p, 2, s);
+        const int G = (int)gh[0];
         t->n_groups = G;
-        t->max_group_count = maxc;
+        t->max_group_count = (int)gh[1];
         t->group_begin = (int32_t *)dmalloc(sizeof(int32_t) * (size_t)(G ? G : 1), s);
         t->group_count = (int32_t *)dmalloc(sizeof(int32_t) * (size_t)(G ? G : 1), s);
+        if (G) {
+            k_group_scatter<<<grid_for(L), BT, 0, s>>>(L, t->leaf_ids, t->node_begin, gstart.p, gsize.p, gidx.p,
+                                                       t->group_begin, t->group_count);
+            CT_COUNT_LAUNCH();
+        }
         t->group_radius = (float *)dmalloc(sizeof(float) * (size_t)(G ? G : 1), s);
         if (G) {
-            CT_CHECK_CUDA(cudaMemcpyAsync(t->group_begin, gb.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s));
-            CT_CHECK_CUDA(cudaMemcpyAsync(t->group_count, gc.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s));
             if (l2) {
                 k_group_radius_l2<<<grid_for((int64_t)G * 32), BT, 0, s>>>(G, t->group_begin, t->group_count, t->pts,
                                                                           dp, t->group_radius);
@@ -1266,7 +1316,6 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
             radix_sort_pairs(ok.p, ov.p, tk2.p, tv2.p, G, 32, s);
             CT_CHECK_CUDA(cudaMemcpyAsync(t->group_order, ov.p, sizeof(int32_t) * G, cudaMemcpyDeviceToDevice, s));
         }
-        CT_CHECK_CUDA(cudaStreamSynchronize(s));  // host vectors above must outlive the copies
     }
     CT_LAUNCH_CHECK();
     CT_CHECK_CUDA(cudaStreamSynchronize(s));
