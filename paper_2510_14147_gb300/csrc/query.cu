@@ -245,7 +245,9 @@ __device__ __forceinline__ void pool_append(const Pool &P, int g, PoolCursor &pc
 
 // DFS over ranges of sibling vertices from `start` (count 0: the root's
 // children): up to 32 vertices are tested per step, vertex i of the step by
-// lane i (`tester(first, take)` returns the lane's keep flag); survivors are
+// lane i (`tester(v, n)` returns the keep flag of the lane's vertex v, for
+// lanes below n); a top range shorter than 32 is completed from the range
+// below it, so that fewer lanes idle; survivors are
 // compacted with ballots -- leaf blocks are appended to the pool, internal
 // vertices push their child range.  The vertices' child ranges are loaded
 // before the test, so that their loads overlap the test's.  With `sp`, a walk
@@ -285,21 +287,36 @@ __device__ __forceinline__ int walk_group(const TreeView &tv, int2 *__restrict__
                 for (int i = base + lane; i < sp->cap; i += 32) sp->items[i] = make_int4(g, 0, 0, 0);
                 limit = INT_MAX;
             }
-            int2 r = stack[top - 1];
-            int take = r.y < 32 ? r.y : 32;
-            __syncwarp();
-            if (lane == 0) {
-                if (r.y > take) stack[top - 1] = make_int2(r.x + take, r.y - take);
+            const int2 r = stack[top - 1];
+            const int take = r.y < 32 ? r.y : 32;
+            int2 r2 = make_int2(0, 0);  // the range below, for the lanes the top range leaves idle
+            int take2 = 0;
+            if (take < 32 && top >= 2) {
+                r2 = stack[top - 2];
+                take2 = r2.y < 32 - take ? r2.y : 32 - take;
             }
-            if (r.y <= take) --top;
-            if (lane < take) ++evals;
-            const int v = r.x + lane;
+            __syncwarp();
+            if (r.y > take) {  // a long top range: its first 32 vertices
+                if (lane == 0) stack[top - 1] = make_int2(r.x + take, r.y - take);
+            } else {
+                --top;
+                if (take2 > 0) {
+                    if (r2.y > take2) {
+                        if (lane == 0) stack[top - 1] = make_int2(r2.x + take2, r2.y - take2);
+                    } else {
+                        --top;
+                    }
+                }
+            }
+            const int n = take + take2;
+            if (lane < n) ++evals;
+            const int v = lane < take ? r.x + lane : r2.x + (lane - take);
             int ccount = 0, cbegin = 0;
-            if (lane < take) {
+            if (lane < n) {
                 ccount = tv.child_count[v];
                 cbegin = tv.child_begin[v];
             }
-            const bool keep = tester(r.x, take);
+            const bool keep = tester(v, n);
             const bool leaf = keep && ccount == 0;
             pool_append(P, g, pc, keep && leaf, (uint32_t)v);
             n_cand += __popc(__ballot_sync(0xffffffffu, keep && leaf));
@@ -336,19 +353,20 @@ __device__ __forceinline__ void group_visits(int32_t *gvisit, int g, unsigned lo
 // 16-byte pieces; the partial sums are reduced by shuffles and lane i gets
 // vertex i's squared distance.  Keep v unless d > (r(v) + eps + r_g)(1 + 2^-10).
 template <int TPD>
-__device__ __forceinline__ bool l2_keep(const TreeView &tv, const float4 *cen, int nq4, int first, int take,
+__device__ __forceinline__ bool l2_keep(const TreeView &tv, const float4 *cen, int nq4, int vid, int take,
                                         float add) {
     constexpr int NPR = 32 / TPD;  // vertices per round; TPD rounds cover a step of 32
     const int lane = threadIdx.x & 31, sub = lane / TPD, j = lane % TPD;
-    const float rad = lane < take ? tv.radius[first + lane] : 0.f;  // issued with the centre rows
+    const float rad = lane < take ? tv.radius[vid] : 0.f;  // issued with the centre rows
     // all rounds' partial sums first (their loads overlap), then the reductions
     float part[TPD];
 #pragma unroll
     for (int u = 0; u < TPD; ++u) {
         const int i = u * NPR + sub;
+        const int vi = __shfl_sync(0xffffffffu, vid, i);  // vertex of lane i
         float acc = 0.f;
         if (u * NPR < take && i < take) {
-            const float4 *row = reinterpret_cast<const float4 *>(tv.node_ctr) + (size_t)(first + i) * nq4;
+            const float4 *row = reinterpret_cast<const float4 *>(tv.node_ctr) + (size_t)vi * nq4;
 #pragma unroll 4
             for (int k = j; k < nq4; k += TPD) {
                 const float4 a = cen[k], b = __ldg(row + k);
@@ -428,12 +446,12 @@ __global__ void __launch_bounds__(TRAV_WARPS * 32, 8) k_traverse_l2(
         for (int k = lane; k < nq4; k += 32) cen[k] = crow[k];
         __syncwarp();
         const float add = V.qp[c].eps_up + tv.group_radius[g];
-        auto tester = [&](int first, int take) {
+        auto tester = [&](int v, int take) {
             switch (tpd) {
-                case 8: return l2_keep<8>(tv, cen, nq4, first, take, add);
-                case 4: return l2_keep<4>(tv, cen, nq4, first, take, add);
-                case 2: return l2_keep<2>(tv, cen, nq4, first, take, add);
-                default: return l2_keep<1>(tv, cen, nq4, first, take, add);
+                case 8: return l2_keep<8>(tv, cen, nq4, v, take, add);
+                case 4: return l2_keep<4>(tv, cen, nq4, v, take, add);
+                case 2: return l2_keep<2>(tv, cen, nq4, v, take, add);
+                default: return l2_keep<1>(tv, cen, nq4, v, take, add);
             }
         };
         const unsigned long long e0 = evals;
@@ -471,9 +489,8 @@ __global__ void __launch_bounds__(32) k_traverse_lev(
         lev_build_peq<W>(peq, pat, m);
         __syncwarp();
         const int add = qp.lev_k + (int)tv.group_radius[g];
-        auto tester = [&](int first, int take) {
+        auto tester = [&](int v, int take) {
             if (lane >= take) return false;
-            const int v = first + lane;
             const int vp = tv.node_begin[v];
             const int k = add + (int)tv.radius[v];
             const uint8_t *txt = tv.sdata + tv.soff[vp];
