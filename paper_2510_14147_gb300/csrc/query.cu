@@ -2408,8 +2408,8 @@ void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int
         kern<<<blocks, P, smem, s>>>(lists.p + (int64_t)cls * n, counts.p + cls, row_ptr, col, dist);
         CT_COUNT_LAUNCH();
     };
-    merge(1, k_sort_merge<128, 128>, 128, 128);
-    merge(2, k_sort_merge<256, 512>, 256, 512);
+    merge(1, k_sort_merge<64, 128>, 64, 128);  // small CTAs: more rows in flight per SM
+    merge(2, k_sort_merge<128, 512>, 128, 512);
     merge(3, k_sort_merge<256, 1024>, 256, 1024);
     merge(4, k_sort_merge<512, SORT_MID>, 512, SORT_MID);
     if (hc[5]) {
