@@ -2410,7 +2410,7 @@ void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int
     };
     merge(1, k_sort_merge<64, 128>, 64, 128);  // small CTAs: more rows in flight per SM
     merge(2, k_sort_merge<128, 512>, 128, 512);
-    merge(3, k_sort_merge<256, 1024>, 256, 1024);
+    merge(3, k_sort_merge<128, 1024>, 128, 1024);
     merge(4, k_sort_merge<512, SORT_MID>, 512, SORT_MID);
     if (hc[5]) {
         int nb = hc[5];
