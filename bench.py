@@ -51,6 +51,20 @@ def dist_env():
     return rank, world, local
 
 
+def combine_ranks(t_ms: float, units: float, dist, device="cuda"):
+    """Whole-job figures of a timed region: the time is the slowest rank's,
+    the units (edges) are summed over the ranks (each rank runs its own
+    replica).  Without a process group the rank's own figures."""
+    if not dist:
+        return t_ms, units
+    import torch
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    uu = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+    return float(tt.item()), int(round(uu.item()))
+
+
 def load_points(wl: dict) -> np.ndarray:
     if wl["kind"] == "gmm":
         return I.gmm_embedded(wl["n"], dim=wl["dim"], seed=wl["seed"])
@@ -289,12 +303,7 @@ def run_clouds(args, wl, world, rank, dist):
     barrier()
     launches = cg.ct_kernel_launches() - l0
     clocks = sampler.stop() if rank == 0 else None
-    t_ms = a.elapsed_time(b)
-    if dist:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-        tot *= world
+    t_ms, tot = combine_ranks(a.elapsed_time(b), tot, dist)
     value = tot / (t_ms / 1e3)
     st = last["stats"]
     plain = None
@@ -455,14 +464,8 @@ def main():
     cg.ct_profile_enable(False)
     prof = cg.ct_profile_read()
     clocks = sampler.stop() if rank == 0 else None
-    t_ms = e0.elapsed_time(e1)
-    if dist:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-        nn = torch.tensor([float(nnz_total)], device="cuda")
-        dist.all_reduce(nn)
-        nnz_total = int(nn.item())
+    rank_nnz = nnz_total
+    t_ms, nnz_total = combine_ranks(e0.elapsed_time(e1), nnz_total, dist)
     value = nnz_total / (t_ms / 1e3)
     st = last["stats"]
     nnz = last["nnz"]
@@ -481,14 +484,9 @@ def main():
                 tot += step(xd, 0, False)
         b.record(stream)
         barrier()
-        tp = a.elapsed_time(b)
-        if dist:
-            tt = torch.tensor([tp], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            tp = float(tt.item())
-            tot *= world
-        if not dist and tot != nnz_total:
+        if tot != rank_nnz:
             raise RuntimeError("plain form produced a different edge count")
+        tp, tot = combine_ranks(a.elapsed_time(b), tot, dist)
         plain = {"form": "plain", "value": tot / (tp / 1e3), "ms_per_step": tp / args.steps,
                  "speedup_of_form": value / (tot / (tp / 1e3))}
 
@@ -525,12 +523,7 @@ def main():
                 tot += e2e_step()
             b.record(stream)
         barrier()
-        te = a.elapsed_time(b)
-        if dist:
-            tt = torch.tensor([te], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-            tot *= world
+        te, tot = combine_ranks(a.elapsed_time(b), tot, dist)
         e2e = {"value": tot / (te / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(x.nbytes),
                "d2h_bytes_per_step": int((wl["n"] + 1) * 8 + nnz * 8),
