@@ -198,8 +198,12 @@ void ct_autotune_reset(void);
  * All temporaries live in one fixed array of CT_NOALLOC_SCRATCH_BYTES bytes
  * inside the library (every GPU that loads the library holds it until the
  * process exits).  The first call on a device looks up that array's device
- * address; make that first call before any stream capture.  Calls never
- * allocate or free device memory; they synchronise `stream` twice.
+ * address.  Calls never allocate or free device memory; they synchronise
+ * `stream` twice and copy counters to host memory, so no call may be made
+ * while `stream` (or any stream, under global capture mode) is being captured
+ * into a CUDA graph.  The candidate list holds about 2.5 M (group, leaf
+ * block) entries, fewer for deep trees; the walk runs with at most 64 blocks
+ * of 4 warps.
  * Every call reuses the same array and clears what must start at zero; calls
  * whose work overlaps on the GPU (other streams, other host threads) race on
  * it and must be serialised by the caller.

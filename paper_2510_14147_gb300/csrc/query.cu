@@ -3116,16 +3116,19 @@ void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cuda
     if (off + stack_per_block > cap_bytes / 2)
         CT_FAIL(CT_EUNSUPPORTED, "a tree of depth %d needs more than the fixed %zu-byte scratch", t->depth, cap_bytes);
     // stacks take at most a quarter of the array, and the warps' partly filled
-    // pool chunks at most a quarter of it
+    // pool chunks (POOL_CHUNK entries each) at most a quarter of it: with a
+    // 16 MiB array that caps the walk at 64 blocks of TRAV_WARPS warps, fewer
+    // than the main path's resident grid (the walk is slower, not different)
     const int64_t chunk_blocks = (int64_t)(cap_bytes / 4 / sizeof(uint32_t)) / ((int64_t)TRAV_WARPS * POOL_CHUNK);
     tl.blocks = (int)std::max<int64_t>(
         1, std::min<int64_t>(std::min<int64_t>(tl.blocks, (cap_bytes / 4) / stack_per_block), chunk_blocks));
     tl.warps = tl.blocks * TRAV_WARPS;
     int2 *stacks = (int2 *)take((size_t)tl.blocks * stack_per_block);
     longlong2 *cursors = (longlong2 *)take((size_t)tl.warps * sizeof(longlong2));
-    // the rest: segments (one third of it, at most one per group and chunk) and the pool
+    // the rest: segments (a sixth of it: 16 bytes each, one per walk and per
+    // pool chunk a walk crosses) and the pool
     const size_t rest = cap_bytes > off ? cap_bytes - off : 0;
-    const int64_t seg_cap = (int64_t)(rest / 3 / (sizeof(int32_t) * 2 + sizeof(int64_t) + 16));
+    const int64_t seg_cap = (int64_t)(rest / 6 / (sizeof(int32_t) * 2 + sizeof(int64_t)));
     int32_t *seg_group = (int32_t *)take((size_t)seg_cap * sizeof(int32_t));
     int32_t *seg_count = (int32_t *)take((size_t)seg_cap * sizeof(int32_t));
     int64_t *seg_begin = (int64_t *)take((size_t)seg_cap * sizeof(int64_t));

@@ -34,21 +34,24 @@ def test_noalloc_degrees_equal_query_rows_twice():
     from paper_2510_14147_gb300 import build
     build.build()
     from paper_2510_14147_gb300 import ctgraph as cg
-    cases = [(I.uniform_cube(3000, 3, seed=0), 0.08),
-             (I.gmm_embedded(20000, dim=64, intrinsic=6, n_centres=4, seed=1), None)]
-    for x, eps in cases:
+    # the larger problem first, so that the smaller one runs over the array's
+    # leftovers (more segments, a longer pool, spill counts); then the
+    # larger one again, and both with include_self
+    big = I.gmm_embedded(20000, dim=64, intrinsic=6, n_centres=4, seed=1)
+    d = np.sqrt(((big[:200, None, :].astype(np.float64) - big[None, :2000, :]) ** 2).sum(-1))
+    big_eps = float(np.float32(np.quantile(d, 0.01)))
+    cases = [(big, big_eps, False), (I.uniform_cube(3000, 3, seed=0), 0.08, False),
+             (big, big_eps, True), (I.uniform_cube(3000, 3, seed=0), 0.08, True)]
+    for x, eps, include_self in cases:
         xd = torch.from_numpy(x).cuda()
         tree = cg.ct_build(points=xd)
-        if eps is None:
-            d = np.sqrt(((x[:200, None, :].astype(np.float64) - x[None, :2000, :]) ** 2).sum(-1))
-            eps = float(np.float32(np.quantile(d, 0.01)))
-        csr = cg.eps_graph_query(tree, eps)
+        csr = cg.eps_graph_query(tree, eps, include_self=include_self)
         ref = np.diff(csr.row_ptr.cpu().numpy())
         csr.free()
         deg = torch.empty(x.shape[0], dtype=torch.int32, device="cuda")
         for _ in range(2):
             deg.fill_(-7)
-            cg.eps_graph_degrees_noalloc(tree, eps, deg)
+            cg.eps_graph_degrees_noalloc(tree, eps, deg, include_self=include_self)
             torch.cuda.synchronize()
             assert np.array_equal(deg.cpu().numpy(), ref)
         tree.free()
