@@ -1,17 +1,20 @@
 #!/usr/bin/env python
 """ε-graph benchmark: one step = cover-tree build + exact ε query (count ->
-scan -> emit -> row sort) of one synthetic point cloud, resident in HBM.
+scan -> emit -> row sort) of one synthetic input resident in HBM.
 
 Default workload: 1,000,000 points, 128-D, 100-component Gaussian mixture in
 8-D embedded in 128-D, eps calibrated for ~70 mean neighbours (the paper's
 sift eps=175 shape).  Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                  [--workload gmm_1m_k70] [--form tc+learned|tc|learned|plain]
+                  [--workload gmm_1m_k70|gmm_1m_k500|dna_50k|clouds_64|small_3d]
+                  [--form tc+learned|tc|learned|plain|auto|auto+learned]
                   [--no-compare] [--no-cpu-baseline] [--no-e2e]
 
-The default form is the tensor-core-filtered, learned one; the plain FP32 two-pass
-form is timed beside it on the same input ("plain" in the JSON line).
+The default form is the tensor-core-filtered, learned one for L2 points and
+the learned one for edit distance.  Every other form is timed beside it on the
+same input ("forms" in the JSON line), and its whole CSR is compared with the
+default form's, entry for entry.
 
 With N > 1 (torchrun) every rank runs an independent replica of the workload
 (nothing is sharded; weak scaling) and the time is the max over ranks.
@@ -40,7 +43,7 @@ from paper_2510_14147_gb300 import inputs as I  # noqa: E402
 
 METRIC = "ε-graph edges/s"
 UNIT = "edges/s"
-SMS, FP32_LANES = 152, 128          # GB300: 152 SMs x 128 FP32 lanes
+SMS, FP32_LANES, INT32_LANES = 152, 128, 64   # GB300: 152 SMs; FP32 and INT32 lanes per SM
 PROFILES = os.path.join(ROOT, "profiles")
 
 
@@ -65,12 +68,31 @@ def combine_ranks(t_ms: float, units: float, dist, device="cuda"):
     return float(tt.item()), int(round(uu.item()))
 
 
+# ------------------------------------------------------------------ inputs
+
 def load_points(wl: dict) -> np.ndarray:
     if wl["kind"] == "gmm":
         return I.gmm_embedded(wl["n"], dim=wl["dim"], seed=wl["seed"])
     if wl["kind"] == "uniform":
         return I.uniform_cube(wl["n"], wl["dim"], seed=wl["seed"])
     raise ValueError("workload %s has no point cloud" % wl)
+
+
+def load_input(wl: dict):
+    """("points", x) for L2 workloads, ("strings", (data, offsets)) for edit distance."""
+    if wl["kind"] == "dna":
+        return "strings", I.dna_strings(n_seeds=wl["n_seeds"], per_seed=wl["per_seed"],
+                                        seed_len=wl["seed_len"], seed=wl["seed"])
+    return "points", load_points(wl)
+
+
+def n_of(kind, host) -> int:
+    return host.shape[0] if kind == "points" else host[1].size - 1
+
+
+def oracle_space(kind, host):
+    import oracle
+    return oracle.Space(points=host) if kind == "points" else oracle.Space(strings=host)
 
 
 # ------------------------------------------------------------------ clocks
@@ -160,13 +182,13 @@ def measured_peaks() -> dict:
     return {}
 
 
-def profile_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch of `kernel` from a committed ncu summary, or None."""
+def profile_value(kernel: str, workload: str, key: str):
+    """A figure (e.g. dram_bytes_per_launch) from a committed ncu summary, or None."""
     path = os.path.join(PROFILES, "%s__%s.txt" % (kernel, workload))
     if not os.path.exists(path):
         return None
     for line in open(path):
-        m = re.match(r"\s*dram_bytes_per_launch\s*[:=]\s*([0-9.eE+]+)", line)
+        m = re.match(r"\s*%s\s*[:=]\s*([0-9.eE+]+)" % re.escape(key), line)
         if m:
             return float(m.group(1))
     return None
@@ -174,42 +196,74 @@ def profile_traffic(kernel: str, workload: str):
 
 # --------------------------------------------------------------- CPU oracle
 
-def oracle_sample(x: np.ndarray, wl: dict, n_queries: int, seed: int = 7):
+def oracle_sample(kind, host, wl: dict, n_queries: int, seed: int = 7):
     """Oracle cover tree (Algorithms 1-3, FP64) built on every point, queried
     for a random sample of points; extrapolated to all n queries."""
     import oracle
     oracle.build()
-    sp = oracle.Space(points=x)
+    sp = oracle_space(kind, host)
+    n = n_of(kind, host)
     t0 = time.perf_counter()
     tree = oracle.build_tree(sp, zeta=wl.get("zeta", 32))
     t_build = time.perf_counter() - t0
     rng = np.random.default_rng(seed)
-    rows = np.sort(rng.choice(x.shape[0], size=min(n_queries, x.shape[0]), replace=False))
+    rows = np.sort(rng.choice(n, size=min(n_queries, n), replace=False))
     t0 = time.perf_counter()
     res = oracle.tree_query_rows(sp, tree, wl["eps"], rows)
     t_query = time.perf_counter() - t0
-    scale = x.shape[0] / rows.size
+    scale = n / rows.size
     edges = float(res["row_ptr"][-1]) * scale
     t_total = t_build + t_query * scale
     evals = (tree.dist_evals + res["dist_evals"] * scale)
     return {"value": edges / t_total, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": "oracle tree built on all %d points (%.1f s); %d random queries (%.1f s) "
-                      "extrapolated to %d queries" % (x.shape[0], t_build, rows.size, t_query, x.shape[0]),
+                      "extrapolated to %d queries" % (n, t_build, rows.size, t_query, n),
             "dist_evals_per_s": evals / t_total, "wall_s": t_build + t_query,
             "extrapolated_s": t_total}
+
+
+def oracle_clouds_sample(specs, per_cloud: int, seed: int = 7):
+    """Many clouds: the oracle's brute force (the ε-graph definition, FP64)
+    for a random sample of query rows of every cloud, each cloud extrapolated
+    to all its rows (a cover tree of the uniform 64-D clouds would take the
+    CPU minutes to build: their farthest-first levels are quadratic)."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    edges = t_total = wall = 0.0
+    for sp in specs:
+        x = I.cloud_points(sp)
+        s = oracle.Space(points=x)
+        rows = np.sort(rng.choice(x.shape[0], size=min(per_cloud, x.shape[0]), replace=False))
+        t0 = time.perf_counter()
+        res = oracle.brute_rows(s, sp["eps"], rows)
+        dt = time.perf_counter() - t0
+        scale = x.shape[0] / rows.size
+        edges += float(res["row_ptr"][-1]) * scale
+        t_total += dt * scale
+        wall += dt
+    return {"value": edges / t_total, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "oracle brute force (FP64) on %d random rows of each of %d clouds (%.1f s), each cloud "
+                      "extrapolated to all its rows" % (per_cloud, len(specs), wall),
+            "wall_s": wall, "extrapolated_s": t_total}
 
 
 def run_reference(args, wl):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    x = load_points(wl)
-    nq = args.ref_queries
+    if wl["kind"] == "clouds":
+        samp = lambda seed: oracle_clouds_sample(wl["specs"], args.ref_queries // 40, seed=seed)
+        cfg = clouds_config(args, wl, world)
+    else:
+        kind, host = load_input(wl)
+        samp = lambda seed: oracle_sample(kind, host, wl, args.ref_queries, seed=seed)
+        cfg = config_of(args, wl, world)
     for _ in range(args.warmup):
-        oracle_sample(x, wl, nq, seed=11)
+        samp(11)
     vals, walls, ext = [], [], []
     for k in range(args.steps):
-        r = oracle_sample(x, wl, nq, seed=100 + k)
+        r = samp(100 + k)
         vals.append(r["value"] * r["extrapolated_s"])
         walls.append(r["wall_s"])
         ext.append(r["extrapolated_s"])
@@ -217,8 +271,8 @@ def run_reference(args, wl):
     value = sum(vals) / sum(ext)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / len(walls),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_of(args, wl, world),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32" if wl["kind"] == "dna" else "f64", "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
                              "sample": last["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -230,187 +284,160 @@ FORMS = {"plain": (0, False), "tc": (1, False), "learned": (0, True), "tc+learne
          "auto": (2, False), "auto+learned": (2, True)}
 
 
-def run_clouds(args, wl, world, rank, dist):
-    """Many clouds per step: every cloud's tree is built, then one batched
-    query over all of them; value = all clouds' edges / step time."""
-    import torch
-    from paper_2510_14147_gb300 import ctgraph as cg
-    precision, learned = FORMS[args.form]
-    specs = wl["specs"]
-    xs = [torch.from_numpy(I.cloud_points(sp)).cuda() for sp in specs]
-    eps = [sp["eps"] for sp in specs]
-    zeta = wl.get("zeta", 32)
-    stream = torch.cuda.Stream()
-    pred = None
-    if learned:
-        raise SystemExit("the learned form of the many-cloud batch is not available yet")
-    last = {}
-
-    def step(prec):
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        e[0].record(stream)
-        trees = [cg.ct_build(points=x, leaf_size=zeta, stream=stream) for x in xs]
-        e[1].record(stream)
-        csrs = cg.eps_graph_query_batched(trees, eps, precision=prec, stream=stream,
-                                          use_predictor=pred is not None, predictor=pred)
-        e[2].record(stream)
-        nnz = sum(c.nnz for c in csrs)
-        last["stats"] = [c.stats() for c in csrs]
-        last["events"] = e
-        for c in csrs:
-            c.free()
-        for t in trees:
-            t.free()
-        return nnz
-
-    def barrier():
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    tuned = None
-    if precision == 2:  # autotune the count kernels on these clouds, outside the timed region
-        with torch.cuda.stream(stream):
-            trees = [cg.ct_build(points=x, leaf_size=zeta, stream=stream) for x in xs]
-            t0 = time.perf_counter()
-            ch = cg.ct_autotune(trees, eps, stream=stream)
-            tuned = {"tc_clouds": int(sum(ch)), "fp32_clouds": len(ch) - int(sum(ch)),
-                     "tune_s": time.perf_counter() - t0}
-            for t in trees:
-                t.free()
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step(precision)
-    barrier()
-    sampler = ClockSampler(gpu_identifier(torch, torch.cuda.current_device()))
-    if rank == 0:
-        sampler.start()
-    l0 = cg.ct_kernel_launches()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    build_ms = query_ms = 0.0
-    barrier()
-    a.record(stream)
-    tot = 0
-    with torch.cuda.stream(stream):
-        for _ in range(args.steps):
-            tot += step(precision)
-            ev = last["events"]
-            ev[2].synchronize()
-            build_ms += ev[0].elapsed_time(ev[1])
-            query_ms += ev[1].elapsed_time(ev[2])
-    b.record(stream)
-    barrier()
-    launches = cg.ct_kernel_launches() - l0
-    clocks = sampler.stop() if rank == 0 else None
-    t_ms, tot = combine_ranks(a.elapsed_time(b), tot, dist)
-    value = tot / (t_ms / 1e3)
-    st = last["stats"]
-    plain = None
-    if args.form != "plain" and not args.no_compare:
-        with torch.cuda.stream(stream):
-            step(0)
-        barrier()
-        a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a2.record(stream)
-        tp = 0
-        with torch.cuda.stream(stream):
-            for _ in range(args.steps):
-                tp += step(0)
-        b2.record(stream)
-        barrier()
-        tpm = a2.elapsed_time(b2)
-        plain = {"form": "plain", "value": tp * world / (tpm / 1e3), "ms_per_step": tpm / args.steps,
-                 "speedup_of_form": value / (tp * world / (tpm / 1e3))}
-    agg = {k: sum(x[k] for x in st) for k in st[0]}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "clouds": len(specs), "points": sum(sp["n"] for sp in specs),
-                       "dims": sorted(set(sp["dim"] for sp in specs)), "form": args.form,
-                       "precision": precision, "learned": learned, "zeta": zeta,
-                       "parallelism": "replicas%d" % world if world > 1 else "single",
-                       "step": "ct_build of every cloud + eps_graph_query_batched + csr_free"},
-            "nnz": tot // max(args.steps, 1) // world, "query_stats": agg,
-            "stage_ms": {"build_all": build_ms / args.steps, "query_batched": query_ms / args.steps},
-            "gpu_launches": launches, "clocks": clocks, "plain": plain, "roofline": None, "e2e": None,
-            "autotune": tuned}
-    if rank == 0:
-        print(json.dumps(line))
-    return 0
-
+def default_form(wl) -> str:
+    return "learned" if wl["kind"] == "dna" else "tc+learned"
 
 
 def config_of(args, wl, world):
     prec, learned = FORMS[args.form]
+    if wl["kind"] == "dna":
+        n = wl["n_seeds"] * wl["per_seed"]
+        return {"workload": args.workload, "n": n, "metric": "levenshtein", "eps": wl["eps"],
+                "zeta": wl.get("zeta", 32), "form": args.form, "precision": prec, "learned": learned,
+                "strings": "%d seeds of length %d, %d mutants each" % (wl["n_seeds"], wl["seed_len"],
+                                                                       wl["per_seed"]),
+                "parallelism": "replicas%d" % world if world > 1 else "single",
+                "l2": "edit distance is compute bound (strings 5 MB); no flush",
+                "step": "ct_build + eps_graph_query + csr_free"}
     return {"workload": args.workload, "n": wl["n"], "dim": wl["dim"], "eps": wl["eps"],
             "zeta": wl.get("zeta", 32), "target_degree": wl.get("target_degree"),
             "form": args.form, "precision": prec, "learned": learned,
             "parallelism": "replicas%d" % world if world > 1 else "single",
-            "l2": "inputs (%.0f MB) larger than L2 (129 MB); no flush" % (wl["n"] * wl["dim"] * 4 / 1e6),
+            "l2": "inputs (%.0f MB) larger than L2 (129 MB); no flush" % (wl["n"] * wl["dim"] * 4 / 1e6)
+            if wl["n"] * wl["dim"] * 4 > 129e6 else "inputs smaller than L2; no flush",
             "step": "ct_build + eps_graph_query + csr_free"}
+
+
+def clouds_config(args, wl, world):
+    prec, learned = FORMS[args.form]
+    specs = wl["specs"]
+    return {"workload": args.workload, "clouds": len(specs), "points": sum(sp["n"] for sp in specs),
+            "dims": sorted(set(sp["dim"] for sp in specs)), "form": args.form,
+            "precision": prec, "learned": learned, "zeta": wl.get("zeta", 32),
+            "parallelism": "replicas%d" % world if world > 1 else "single",
+            "l2": "inputs (%.0f MB) larger than L2 (129 MB); no flush"
+                  % (sum(sp["n"] * sp["dim"] * 4 for sp in specs) / 1e6),
+            "step": "ct_build of every cloud + eps_graph_query_batched + csr_free"}
+
+
+# ------------------------------------------------------------------ roofline
+
+def roofline(prof: dict, st: dict, wl: dict, workload: str, peaks: dict, dim: int, mean_len=None):
+    """Roofline of the count pass's leaf kernel, by the rules of each path:
+    tensor-core tiles: 2 D flops per candidate pair against the dense f16/bf16
+    tensor peak (sustained: the kernel runs inside a long step); FP32 tiles:
+    3 D flops per pair against the FP32 lanes; edit distance: 17 64-bit word
+    operations per pattern word per text character against the INT32 lanes
+    (two 32-bit operations per word operation)."""
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    stage = {k: v for k, v in prof.items() if k not in ("build",)}
+    dom = max(stage, key=lambda k: stage[k][0]) if stage else None
+    if "leaf_count_tc" in prof:
+        t = prof["leaf_count_tc"][0] / prof["leaf_count_tc"][1] / 1e3
+        flops = st["leaf_pairs"] * 2.0 * dim
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        ach = flops / t / 1e12
+        traffic = profile_value("k_leaf_tc", workload, "dram_bytes_per_launch")
+        kp = 64 * ((((dim + 3) // 4) * 4 + 63) // 64)
+        nbytes = st["leaf_rows"] * (2.0 * kp + 4.0) + st["recheck_fp32"] * 4.0 * dim
+        return {"kernel": "k_leaf_tc", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": traffic,
+                "peak_note": ("measured cuBLAS bf16 sustained (MEASURED_PEAKS.json); fp16 operands run at the "
+                              "same dense rate" if peaks else "fallback 1.7 PFLOP/s sustained"),
+                "flops_rule": "leaf_pairs x 2 x dim (every (query, candidate point) pair of the MMA tiles)",
+                "flops_per_launch": flops, "ms_per_launch": t * 1e3,
+                "dram_gbs": traffic / t / 1e9 if traffic else None,
+                "dram_frac": traffic / t / 1e9 / peaks.get("hbm_gbs", 6800.0) if traffic else None,
+                "l2_served_bytes_per_launch": nbytes,
+                "l2_served_rule": "leaf_rows x (2 kp + 4) B (fp16 rows and norms) + recheck_fp32 x 4 dim B",
+                "recheck_fp32_pairs": st["recheck_fp32"], "dominant_stage": dom}
+    if "leaf_count" in prof and wl.get("kind") != "dna":
+        t = prof["leaf_count"][0] / prof["leaf_count"][1] / 1e3
+        peak = 2.0 * SMS * FP32_LANES * sm_max * 1e6 / 1e12
+        flops = st["leaf_pairs"] * 3.0 * dim
+        ach = flops / t / 1e12
+        return {"kernel": "k_leaf_l2<count>", "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": profile_value("k_leaf_l2_count", workload, "dram_bytes_per_launch"),
+                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz; direct differences "
+                             "(sub+mul+add) can reach at most 0.75 of it" % sm_max,
+                "flops_rule": "leaf_pairs x 3 x dim", "flops_per_launch": flops, "ms_per_launch": t * 1e3,
+                "dominant_stage": dom}
+    if "leaf_count" in prof:
+        t = prof["leaf_count"][0] / prof["leaf_count"][1] / 1e3
+        words = math.ceil(mean_len / 64.0)
+        ops = st["leaf_pairs"] * 17.0 * words * mean_len          # 64-bit word operations
+        peak = SMS * INT32_LANES * sm_max * 1e6 / 2.0 / 1e12       # T word-ops/s
+        ach = ops / t / 1e12
+        return {"kernel": "k_leaf_lev<count>", "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "Tword-op/s", "frac": ach / peak,
+                "traffic": profile_value("k_leaf_lev_count", workload, "dram_bytes_per_launch"),
+                "peak_note": "derived: 152 SMs x 64 INT32 lanes x %.0f MHz / 2 (a 64-bit word operation is "
+                             "two 32-bit ones)" % sm_max,
+                "ops_rule": "leaf_pairs x 17 word-ops x ceil(mean length / 64) x mean length "
+                            "(the full bit-parallel recurrence; pairs that stop early count in full)",
+                "ops_per_launch": ops, "ms_per_launch": t * 1e3, "dominant_stage": dom}
+    return None
+
+
+def traversal_roofline(prof: dict, st: dict, n: int, dim: int, workload: str, peaks: dict):
+    """The walk's algorithmic bytes (per vertex test: 4 D of centre + 16 B of
+    vertex record; per query: 4 D to read it) per unit time, and its DRAM
+    bytes from the committed ncu summary, against the measured HBM copy
+    bandwidth."""
+    if "traverse" not in prof:
+        return None
+    t = prof["traverse"][0] / prof["traverse"][1] / 1e3
+    nbytes = st["traversal_evals"] * (4.0 * dim + 16.0) + n * 4.0 * dim
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    dram = profile_value("k_traverse_l2", workload, "dram_bytes_per_query")
+    return {"kernel": "k_traverse_l2", "bound": "hbm", "ms_per_query": t * 1e3,
+            "algorithmic_gbs": nbytes / t / 1e9, "algorithmic_frac": nbytes / t / 1e9 / hbm,
+            "dram_gbs": dram / t / 1e9 if dram else None, "dram_frac": dram / t / 1e9 / hbm if dram else None,
+            "peak": hbm, "unit": "GB/s", "bytes_rule": "traversal_evals x (4 dim + 16) B + n x 4 dim B"}
 
 
 # ------------------------------------------------------------------ native
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="gmm_1m_k70")
-    ap.add_argument("--form", default="tc+learned", choices=sorted(FORMS),
-                    help="plain: FP32 two-pass; tc: tensor-core filter (fp16 rows); learned: one-pass emit "
-                         "sized by the predictor; tc+learned: both")
-    ap.add_argument("--no-compare", action="store_true", help="skip timing the plain form beside it")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-queries", type=int, default=4000)
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--fit-steps", type=int, default=1500)
-    ap.add_argument("--order-radius", action="store_true",
-                    help="learned forms: walk groups by radius instead of predicted walk length")
-    args = ap.parse_args()
-    wl = I.load_workloads()[args.workload]
-    precision, learned = FORMS[args.form]
-
-    if args.impl == "reference":
-        return run_reference(args, wl)
-
+def csr_equal(a, b) -> bool:
+    """Exact equality of two device CSRs: row_ptr, col and dist bit for bit."""
     import torch
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    from paper_2510_14147_gb300 import build as libbuild
-    if rank == 0 or world == 1:
-        libbuild.build()
-    if dist:
-        dist.barrier()
+    return (a.nnz == b.nnz and torch.equal(a.row_ptr, b.row_ptr) and torch.equal(a.col, b.col)
+            and torch.equal(a.dist.view(torch.int32), b.dist.view(torch.int32)))
+
+
+def run_single(args, wl, world, rank, dist):
+    import torch
     from paper_2510_14147_gb300 import ctgraph as cg
-
-    if wl["kind"] == "clouds":
-        rc = run_clouds(args, wl, world, rank, dist)
-        if dist:
-            dist.destroy_process_group()
-        return rc
-
-    x = load_points(wl)
-    xd = torch.from_numpy(x).cuda()
+    kind, host = load_input(wl)
+    n = n_of(kind, host)
+    dim = host.shape[1] if kind == "points" else 0
+    mean_len = float(np.diff(host[1]).mean()) if kind == "strings" else None
+    if kind == "points":
+        dev = torch.from_numpy(host).cuda()
+        build = lambda stream, d=None: cg.ct_build(points=dev if d is None else d, leaf_size=zeta, stream=stream)
+    else:
+        dev = (torch.from_numpy(host[0]).cuda(), torch.from_numpy(host[1]).cuda())
+        build = lambda stream, d=None: cg.ct_build(strings=dev if d is None else d, leaf_size=zeta, stream=stream)
     stream = torch.cuda.Stream()
     eps, zeta = wl["eps"], wl.get("zeta", 32)
+    precision, learned = FORMS[args.form]
 
     last = {}
     pred = None
     fit_info = None
-    if learned:
+    need_pred = learned or (not args.no_compare)
+    if need_pred:
         # fitted once, outside the timed region, on another draw of the recipe
-        wl_fit = dict(wl, seed=wl["seed"] + 1)
-        xf = torch.from_numpy(load_points(wl_fit)).cuda()
+        kf, hf = load_input(dict(wl, seed=wl["seed"] + 1))
+        if kf == "points":
+            df = torch.from_numpy(hf).cuda()
+            mk = lambda: cg.ct_build(points=df, leaf_size=zeta, stream=stream)
+        else:
+            df = (torch.from_numpy(hf[0]).cuda(), torch.from_numpy(hf[1]).cuda())
+            mk = lambda: cg.ct_build(strings=df, leaf_size=zeta, stream=stream)
         with torch.cuda.stream(stream):
-            tf = cg.ct_build(points=xf, leaf_size=zeta, stream=stream)
+            tf = mk()
             pred = cg.ct_predictor_create(seed=1)
             t0 = time.perf_counter()
             loss = cg.ct_predictor_fit(pred, tf, eps, steps=args.fit_steps, seed=2, stream=stream)
@@ -418,19 +445,21 @@ def main():
             tf.free()
             if args.order_radius:
                 cg.ct_predictor_set_order(pred, False)
-        del xf
-        fit_info = {"fit_on": "another draw of the recipe (seed %d)" % wl_fit["seed"],
+        del df
+        fit_info = {"fit_on": "another draw of the recipe (seed %d)" % (wl["seed"] + 1),
                     "fit_steps": args.fit_steps, "final_loss": loss, "fit_s": fit_s,
                     "walk_order": "radius" if args.order_radius else "predicted walk length"}
 
-    def step(points, prec=precision, use_pred=learned):
-        t = cg.ct_build(points=points, leaf_size=zeta, stream=stream)
+    def step(prec=precision, use_pred=learned, keep=False):
+        t = build(stream)
         c = cg.eps_graph_query(t, eps, precision=prec, stream=stream, use_predictor=use_pred,
                                predictor=pred if use_pred else None)
         last["nnz"] = c.nnz
         last["stats"] = c.stats()
-        c.free()
         t.free()
+        if keep:
+            return c
+        c.free()
         return c.nnz
 
     def barrier():
@@ -438,12 +467,13 @@ def main():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
+
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            step(xd)
+            step()
     barrier()
 
-    sampler = ClockSampler(gpu_identifier(torch, local))
+    sampler = ClockSampler(gpu_identifier(torch, torch.cuda.current_device()))
     if rank == 0:
         sampler.start()
     cg.ct_profile_reset()
@@ -456,7 +486,7 @@ def main():
     nnz_total = 0
     with torch.cuda.stream(stream):
         for _ in range(args.steps):
-            nnz_total += step(xd)
+            nnz_total += step()
     e1.record(stream)
     barrier()
     sampler.mark("t1")
@@ -464,44 +494,66 @@ def main():
     cg.ct_profile_enable(False)
     prof = cg.ct_profile_read()
     clocks = sampler.stop() if rank == 0 else None
-    rank_nnz = nnz_total
     t_ms, nnz_total = combine_ranks(e0.elapsed_time(e1), nnz_total, dist)
     value = nnz_total / (t_ms / 1e3)
     st = last["stats"]
     nnz = last["nnz"]
 
-    # the plain form on the same input, for the comparison
-    plain = None
-    if args.form != "plain" and not args.no_compare:
+    # the other forms on the same input: time, stage times, and their whole
+    # CSR against the default form's
+    forms = None
+    if not args.no_compare:
+        forms = {}
         with torch.cuda.stream(stream):
-            step(xd, 0, False)
-        barrier()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        tot = 0
-        with torch.cuda.stream(stream):
-            for _ in range(args.steps):
-                tot += step(xd, 0, False)
-        b.record(stream)
-        barrier()
-        if tot != rank_nnz:
-            raise RuntimeError("plain form produced a different edge count")
-        tp, tot = combine_ranks(a.elapsed_time(b), tot, dist)
-        plain = {"form": "plain", "value": tot / (tp / 1e3), "ms_per_step": tp / args.steps,
-                 "speedup_of_form": value / (tot / (tp / 1e3))}
+            ref = step(keep=True)
+        names = ["plain", "learned"] if kind == "strings" else ["plain", "tc", "learned", "tc+learned"]
+        for name in names:
+            if name == args.form:
+                continue
+            pf, lf = FORMS[name]
+            with torch.cuda.stream(stream):
+                c = step(pf, lf, keep=True)
+                same = csr_equal(c, ref)
+                c.free()
+                step(pf, lf)
+            barrier()
+            cg.ct_profile_reset()
+            cg.ct_profile_enable(True)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tot = 0
+            with torch.cuda.stream(stream):
+                for _ in range(args.steps):
+                    tot += step(pf, lf)
+            b.record(stream)
+            barrier()
+            cg.ct_profile_enable(False)
+            fp = cg.ct_profile_read()
+            tp, tot = combine_ranks(a.elapsed_time(b), tot, dist)
+            forms[name] = {"value": tot / (tp / 1e3), "ms_per_step": tp / args.steps,
+                           "csr_identical_to_default_form": bool(same),
+                           "stage_ms": {k: v[0] / max(v[1], 1) for k, v in fp.items()},
+                           "speedup_of_default_form": value / (tot / (tp / 1e3))}
+            if not same:
+                raise RuntimeError("form %s produced a different CSR than %s" % (name, args.form))
+        ref.free()
 
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        xh = torch.from_numpy(x).pin_memory()
-        xdev = torch.empty_like(xd)
-        rp_h = torch.empty(wl["n"] + 1, dtype=torch.int64).pin_memory()
+        if kind == "points":
+            hin = [torch.from_numpy(host).pin_memory()]
+        else:
+            hin = [torch.from_numpy(host[0]).pin_memory(), torch.from_numpy(host[1]).pin_memory()]
+        din = [torch.empty_like(h, device="cuda") for h in hin]
+        rp_h = torch.empty(n + 1, dtype=torch.int64).pin_memory()
         col_h = torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory()
         dist_h = torch.empty(max(nnz, 1), dtype=torch.float32).pin_memory()
 
         def e2e_step():
-            xdev.copy_(xh, non_blocking=True)
-            t = cg.ct_build(points=xdev, leaf_size=zeta, stream=stream)
+            for d, h in zip(din, hin):
+                d.copy_(h, non_blocking=True)
+            t = build(stream, din[0] if kind == "points" else (din[0], din[1]))
             c = cg.eps_graph_query(t, eps, precision=precision, stream=stream,
                                    use_predictor=learned, predictor=pred)
             rp_h.copy_(c.row_ptr, non_blocking=True)
@@ -525,69 +577,280 @@ def main():
         barrier()
         te, tot = combine_ranks(a.elapsed_time(b), tot, dist)
         e2e = {"value": tot / (te / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": int(x.nbytes),
-               "d2h_bytes_per_step": int((wl["n"] + 1) * 8 + nnz * 8),
-               "ms_per_step": te / args.steps}
+               "h2d_bytes_per_step": int(sum(h.numel() * h.element_size() for h in hin)),
+               "d2h_bytes_per_step": int((n + 1) * 8 + nnz * 8), "ms_per_step": te / args.steps}
 
-    # roofline of the dominant kernel
     stage_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items()}
     peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 2.0 * SMS * FP32_LANES * sm_max * 1e6 / 1e12   # TFLOP/s, FMA = 2 flops
-    kernel_stages = {k: v for k, v in prof.items() if k not in ("build",)}
-    dom = max(kernel_stages, key=lambda k: kernel_stages[k][0]) if kernel_stages else None
-    roof = None
-    if "leaf_count_tc" in prof:
-        # tensor-core form: 32 queries x 128 dims x 2 flops per 260-byte fp16
-        # candidate row (+ norm) is 32 flop/B, far below the tensor ridge
-        # (~250 flop/B): the tiles are bound by streaming the candidate rows
-        # (and the original rows of the kept pairs), so the roofline is HBM
-        t_launch = prof["leaf_count_tc"][0] / prof["leaf_count_tc"][1] / 1e3
-        kp = 64 * ((((wl["dim"] + 3) // 4) * 4 + 63) // 64)  # fp16 row length (dp rounded up to 64)
-        nbytes = st["leaf_rows"] * (2.0 * kp + 4.0) + st["recheck_fp32"] * 4.0 * wl["dim"]
-        hbm = peaks.get("hbm_gbs", 6800.0)
-        ach = nbytes / t_launch / 1e9
-        roof = {"kernel": "k_leaf_tc", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": profile_traffic("k_leaf_tc", args.workload),
-                "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)" if peaks else "fallback 6.8 TB/s",
-                "bytes_per_launch": nbytes,
-                "bytes_rule": "leaf_rows x (2 kp + 4) B (fp16 candidate rows and norms, kp = dim rounded "
-                              "up to 64) + recheck_fp32 x dim x 4 B (original candidate rows of kept pairs)",
-                "ms_per_launch": t_launch * 1e3, "tensor_flops_per_launch": st["leaf_pairs"] * 2.0 * kp,
-                "tensor_frac_of_sustained_f16": st["leaf_pairs"] * 2.0 * kp / t_launch / 1e12
-                / peaks.get("bf16_tflops_sustained", 1700.0),
-                "recheck_fp32_pairs": st["recheck_fp32"], "dominant_stage": dom}
-    elif "leaf_count" in prof:
-        t_launch = prof["leaf_count"][0] / prof["leaf_count"][1] / 1e3
-        flops = st["leaf_pairs"] * 3.0 * wl["dim"]
-        ach = flops / t_launch / 1e12
-        roof = {"kernel": "k_leaf_l2<count>", "bound": "alu", "achieved": ach, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                "traffic": profile_traffic("k_leaf_l2_count", args.workload),
-                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz; direct "
-                             "differences (sub+mul+add) can reach at most 0.75 of it" % sm_max,
-                "flops_per_launch": flops, "ms_per_launch": t_launch * 1e3,
-                "dominant_stage": dom}
-
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_of(args, wl, world), "nnz": nnz, "edges_undirected": nnz // 2,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32" if kind == "strings" else "f32",
+            "data": "synthetic", "config": config_of(args, wl, world), "nnz": nnz, "edges_undirected": nnz // 2,
             "dist_evals_per_s": (st["traversal_evals"] + st["leaf_pairs"]) * world * args.steps / (t_ms / 1e3),
-            "query_stats": st, "stage_ms": stage_ms, "roofline": roof, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks, "library": cg.library_path(), "plain": plain}
+            "query_stats": st, "stage_ms": stage_ms,
+            "roofline": roofline(prof, st, wl, args.workload, peaks, dim, mean_len),
+            "traversal": traversal_roofline(prof, st, n, dim, args.workload, peaks) if kind == "points" else None,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "library": cg.library_path(),
+            "forms": forms}
     if fit_info:
         line["learned"] = fit_info
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = oracle_sample(x, wl, args.ref_queries)
+            line["cpu_baseline"] = oracle_sample(kind, host, wl, args.ref_queries)
         except Exception as e:  # reported, never silently replaced
             line["cpu_baseline"] = {"error": str(e)}
     if rank == 0:
         print(json.dumps(line))
+    return 0
+
+
+def run_clouds(args, wl, world, rank, dist):
+    """Many clouds per step: every cloud's tree is built, then one batched
+    query over all of them; value = all clouds' edges / step time."""
+    import torch
+    from paper_2510_14147_gb300 import ctgraph as cg
+    precision, learned = FORMS[args.form]
+    specs = wl["specs"]
+    hosts = [I.cloud_points(sp) for sp in specs]
+    xs = [torch.from_numpy(x).cuda() for x in hosts]
+    eps = [sp["eps"] for sp in specs]
+    zeta = wl.get("zeta", 32)
+    stream = torch.cuda.Stream()
+    pred = None
+    fit_info = None
+    if learned:
+        # one predictor for every cloud, fitted outside the timed region on
+        # another draw of three clouds of the recipe (a uniform and two mixtures)
+        fit_specs = [dict(sp, seed=sp["seed"] + 100000) for sp in specs[:3]]
+        with torch.cuda.stream(stream):
+            pred = cg.ct_predictor_create(seed=1)
+            t0 = time.perf_counter()
+            loss = None
+            for sp in fit_specs:
+                tf = cg.ct_build(points=torch.from_numpy(I.cloud_points(sp)).cuda(), leaf_size=zeta, stream=stream)
+                loss = cg.ct_predictor_fit(pred, tf, sp["eps"], steps=args.fit_steps // len(fit_specs) or 1,
+                                           seed=2, stream=stream)
+                tf.free()
+            fit_info = {"fit_on": "another draw of clouds 0-2 of the recipe", "final_loss": loss,
+                        "fit_s": time.perf_counter() - t0}
+    last = {}
+
+    def step(prec, use_pred, keep=False, src=None):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        trees = [cg.ct_build(points=x, leaf_size=zeta, stream=stream) for x in (src or xs)]
+        e[1].record(stream)
+        csrs = cg.eps_graph_query_batched(trees, eps, precision=prec, stream=stream,
+                                          use_predictor=use_pred, predictor=pred if use_pred else None)
+        e[2].record(stream)
+        nnz = sum(c.nnz for c in csrs)
+        last["stats"] = [c.stats() for c in csrs]
+        last["events"] = e
+        for t in trees:
+            t.free()
+        if keep:
+            return csrs
+        for c in csrs:
+            c.free()
+        return nnz
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    tuned = None
+    if precision == 2:  # autotune the count kernels on these clouds, outside the timed region
+        with torch.cuda.stream(stream):
+            trees = [cg.ct_build(points=x, leaf_size=zeta, stream=stream) for x in xs]
+            t0 = time.perf_counter()
+            ch = cg.ct_autotune(trees, eps, stream=stream)
+            tuned = {"tc_clouds": int(sum(ch)), "fp32_clouds": len(ch) - int(sum(ch)),
+                     "tune_s": time.perf_counter() - t0}
+            for t in trees:
+                t.free()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(precision, learned)
+    barrier()
+    sampler = ClockSampler(gpu_identifier(torch, torch.cuda.current_device()))
+    if rank == 0:
+        sampler.start()
+    cg.ct_profile_reset()
+    cg.ct_profile_enable(True)
+    l0 = cg.ct_kernel_launches()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    build_ms = query_ms = 0.0
+    barrier()
+    sampler.mark("t0")
+    a.record(stream)
+    tot = 0
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            tot += step(precision, learned)
+    b.record(stream)
+    barrier()
+    sampler.mark("t1")
+    launches = cg.ct_kernel_launches() - l0
+    cg.ct_profile_enable(False)
+    prof = cg.ct_profile_read()
+    clocks = sampler.stop() if rank == 0 else None
+    t_ms, tot = combine_ranks(a.elapsed_time(b), tot, dist)
+    value = tot / (t_ms / 1e3)
+    st = last["stats"][0]          # a batch reports its counters once, for all its clouds
+    ev = last["events"]
+    build_ms, query_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+
+    forms = None
+    if not args.no_compare:
+        forms = {}
+        with torch.cuda.stream(stream):
+            ref = step(precision, learned, keep=True)
+        for name in ("plain",):
+            if name == args.form:
+                continue
+            pf, lf = FORMS[name]
+            with torch.cuda.stream(stream):
+                cs = step(pf, lf, keep=True)
+                same = all(csr_equal(x, y) for x, y in zip(cs, ref))
+                for c in cs:
+                    c.free()
+            barrier()
+            a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a2.record(stream)
+            tp = 0
+            with torch.cuda.stream(stream):
+                for _ in range(args.steps):
+                    tp += step(pf, lf)
+            b2.record(stream)
+            barrier()
+            tpm, tp = combine_ranks(a2.elapsed_time(b2), tp, dist)
+            forms[name] = {"value": tp / (tpm / 1e3), "ms_per_step": tpm / args.steps,
+                           "csr_identical_to_default_form": bool(same),
+                           "speedup_of_default_form": value / (tp / (tpm / 1e3))}
+            if not same:
+                raise RuntimeError("form %s produced a different CSR than %s" % (name, args.form))
+        for c in ref:
+            c.free()
+
+    e2e = None
+    if not args.no_e2e:
+        hin = [torch.from_numpy(x).pin_memory() for x in hosts]
+        din = [torch.empty_like(h, device="cuda") for h in hin]
+        nn = [x.shape[0] for x in hosts]
+        caps = {}
+
+        def e2e_step():
+            for d, h in zip(din, hin):
+                d.copy_(h, non_blocking=True)
+            cs = step(precision, learned, keep=True, src=din)
+            outs = []
+            for i, c in enumerate(cs):
+                need = (c.nnz, nn[i])
+                if caps.get(i, (-1, -1))[0] < c.nnz:
+                    caps[i] = (c.nnz, torch.empty(max(c.nnz, 1), dtype=torch.int32).pin_memory(),
+                               torch.empty(max(c.nnz, 1), dtype=torch.float32).pin_memory(),
+                               torch.empty(nn[i] + 1, dtype=torch.int64).pin_memory())
+                _, ch, dh, rh = caps[i]
+                rh.copy_(c.row_ptr, non_blocking=True)
+                ch[:c.nnz].copy_(c.col, non_blocking=True)
+                dh[:c.nnz].copy_(c.dist, non_blocking=True)
+                outs.append(need)
+            stream.synchronize()
+            k = sum(c.nnz for c in cs)
+            for c in cs:
+                c.free()
+            return k
+
+        with torch.cuda.stream(stream):
+            e2e_step()
+            barrier()
+            a3, b3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a3.record(stream)
+            te_tot = 0
+            for _ in range(args.steps):
+                te_tot += e2e_step()
+            b3.record(stream)
+        barrier()
+        te, te_tot = combine_ranks(a3.elapsed_time(b3), te_tot, dist)
+        nnz_step = te_tot // max(args.steps, 1) // max(world, 1)
+        e2e = {"value": te_tot / (te / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(x.nbytes for x in hosts)),
+               "d2h_bytes_per_step": int(sum((m + 1) * 8 for m in nn) + nnz_step * 8),
+               "ms_per_step": te / args.steps}
+
+    peaks = measured_peaks()
+    roof = roofline(prof, st, wl, args.workload, peaks, max(sp["dim"] for sp in specs))
+    if roof:
+        roof["note"] = ("a batch mixes dims 3/16/64: the flop count takes the largest dim for every pair of the "
+                        "launch (an upper bound on the work)")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": clouds_config(args, wl, world),
+            "nnz": tot // max(args.steps, 1) // world, "query_stats": st,
+            "stage_ms": dict({k: v[0] / max(v[1], 1) for k, v in prof.items()},
+                             build_all=build_ms, query_batched=query_ms),
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "library": cg.library_path(), "forms": forms, "autotune": tuned}
+    if fit_info:
+        line["learned"] = fit_info
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = oracle_clouds_sample(specs, args.ref_queries // 40)
+        except Exception as e:
+            line["cpu_baseline"] = {"error": str(e)}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="gmm_1m_k70")
+    ap.add_argument("--form", default=None, choices=sorted(FORMS),
+                    help="plain: FP32 two-pass; tc: tensor-core filter (fp16 rows); learned: one-pass emit "
+                         "sized by the predictor; tc+learned: both; auto: the autotuned count kernel")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other forms beside it")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-queries", type=int, default=4000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fit-steps", type=int, default=1500)
+    ap.add_argument("--order-radius", action="store_true",
+                    help="learned forms: walk groups by radius instead of predicted walk length")
+    args = ap.parse_args()
+    wl = I.load_workloads()[args.workload]
+    if args.form is None:
+        args.form = "plain" if wl["kind"] == "clouds" else default_form(wl)
+
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2510_14147_gb300 import build as libbuild
+    if rank == 0 or world == 1:
+        libbuild.build()
+    if dist:
+        dist.barrier()
+
+    if wl["kind"] == "clouds":
+        rc = run_clouds(args, wl, world, rank, dist)
+    else:
+        rc = run_single(args, wl, world, rank, dist)
     if dist:
         dist.destroy_process_group()
-    return 0
+    return rc
 
 
 if __name__ == "__main__":

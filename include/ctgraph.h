@@ -249,8 +249,9 @@ ct_status ct_tree_export(const ct_tree *tree, int64_t *center, double *radius, i
  *          log1p(points below), log1p(radius/e)
  *    12..15 log1p(points below the lowest ancestor of the leaf block,
  *          itself included, with radius >= e, 2e, 4e, 16e; the root if none)
- * (the group: the query's run of sibling leaf blocks, at most 32 points or a
- * single larger block; its centre is its first point) to
+ * (the group: the query's run of sibling leaf blocks, at most 32 points, or
+ * a cut of 32 consecutive points of a larger block; its centre is its first
+ * point) to
  *    output 0: log(1 + degree of the query),
  *    output 1: log(1 + vertices tested by the tree walk of its group).
  * Output 0 sizes the rows of the one-pass emit; output 1, averaged over a

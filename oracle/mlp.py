@@ -83,8 +83,9 @@ GROUP_SIZE = 32
 def query_groups(tree):
     """Query groups of a tree in the flat export format: runs of consecutive
     sibling leaf blocks (in position order) holding at most 32 points in
-    total; a larger leaf block is a group of its own.  Returns (begin, count)
-    position arrays."""
+    total; a larger leaf block is cut into groups of 32 consecutive points
+    (the last one shorter), none shared with another block.  Returns
+    (begin, count) position arrays."""
     N = len(tree["center"])
     parent = np.full(N, -1, np.int64)
     for v in range(N):
@@ -95,7 +96,12 @@ def query_groups(tree):
     gb, gc, cur = [], [], None
     for v in leaves:
         b, c, p = int(tree["pts_begin"][v]), int(tree["pts_count"][v]), int(parent[v])
-        if gc and p == cur and gc[-1] + c <= GROUP_SIZE:
+        if c > GROUP_SIZE:
+            for k in range(0, c, GROUP_SIZE):
+                gb.append(b + k)
+                gc.append(min(GROUP_SIZE, c - k))
+            cur = None      # the next block starts a group of its own
+        elif gc and p == cur and gc[-1] + c <= GROUP_SIZE:
             gc[-1] += c
         else:
             gb.append(b)

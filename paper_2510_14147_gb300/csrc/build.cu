@@ -82,9 +82,24 @@ constexpr int UPD_PASSES = 8;  // passes of a block over its chunk in k_dist_upd
 
 struct Hubs {
     int32_t *begin, *count, *node, *nc, *cur, *done, *level;
+    int32_t *flat;     // 1: the split stopped early and every child is a leaf block
+    int32_t *covered;  // points within the split threshold after the last pass (L2)
     float *thr;
     unsigned long long *key;
 };
+
+// A split that has taken FLAT_MIN_CENTRES centres while they cover on average
+// fewer than 1 + 1/8 points each is making almost every point its own child
+// (in high-dimensional data where all distances lie above the threshold):
+// the triangle inequality can then prune nothing below this hub, and the
+// farthest-first iterations would grow quadratically with its size.  Such a
+// hub keeps the centres taken so far (a net of its own: separated, within
+// 2^l of the hub's centre) and its children become leaf blocks whatever their
+// size; their stored radii keep the query exact.
+constexpr int FLAT_MIN_CENTRES = 256;
+__device__ __forceinline__ bool flat_split(int nc, int covered) {
+    return nc >= FLAT_MIN_CENTRES && covered <= nc + (nc >> 3);
+}
 
 // The next split step of a hub, taken inside the update pass by the hub's
 // last block to finish (its arrival completes the hub's count in `arrive`;
@@ -106,9 +121,13 @@ __device__ __noinline__ void step_tail(const float *__restrict__ X, int dp, cons
     if (threadIdx.x == 0) {
         const unsigned long long k = atomicAdd(&hb.key[h], 0ull);  // every block's maximum has landed
         const float v = key_value(k);
+        const int covered = atomicExch(&hb.covered[h], 0);           // every block's count has landed
         s_act = 0;
         if (k == 0ull || !(v > hb.thr[h])) {
             hb.done[h] = 1;
+        } else if (flat_split(hb.nc[h], covered)) {
+            hb.done[h] = 1;
+            hb.flat[h] = 1;
         } else {
             const int b = hb.begin[h], nc = hb.nc[h];
             const int cur = (int32_t)key_pos(k);
@@ -210,6 +229,14 @@ __global__ void __launch_bounds__(BT, 4) k_dist_update_l2(
         best = v > best ? v : best;
     }
     if ((threadIdx.x & 31) == 0 && best) atomicMax(&hb.key[h], best);
+    {  // points now within the split threshold (the flat-split test)
+        const float thr = hb.thr[h];
+        int cov = 0;
+#pragma unroll
+        for (int p = 0; p < UPD_PASSES; ++p) cov += (j == 0 && start + p * G + g < end && cur[p] <= thr) ? 1 : 0;
+        for (int o = 16; o > 0; o >>= 1) cov += __shfl_xor_sync(0xffffffffu, cov, o);
+        if ((threadIdx.x & 31) == 0 && cov) atomicAdd(&hb.covered[h], cov);
+    }
     if (st.arrive) {  // the hub's last block takes its next step
         __shared__ int s_last;
         __threadfence();
@@ -274,15 +301,20 @@ __global__ void __launch_bounds__(BT) k_dist_update_lev(
 // One thread per hub: decide termination or choose the next centre (its
 // position goes to cpos[begin + label] when cpos is given).
 __global__ void k_hub_step(int nh, const int32_t *__restrict__ hlist, Hubs hb, int32_t *__restrict__ active_out,
-                           int32_t *__restrict__ cpos) {
+                           int32_t *__restrict__ cpos, int flat_check) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int h = i < nh && hlist ? hlist[i] : i;
     int act = 0;
     if (i < nh && !hb.done[h]) {
         unsigned long long k = hb.key[h];
         float v = key_value(k);
+        const int covered = hb.covered[h];
+        hb.covered[h] = 0;
         if (k == 0ull || !(v > hb.thr[h])) {
             hb.done[h] = 1;
+        } else if (flat_check && flat_split(hb.nc[h], covered)) {
+            hb.done[h] = 1;
+            hb.flat[h] = 1;
         } else {
             hb.cur[h] = (int32_t)key_pos(k);
             if (cpos) {
@@ -598,7 +630,8 @@ __global__ void k_child_keys(int64_t R, const uint32_t *__restrict__ skeys, cons
 // Link every hub to its children (consecutive node ids).
 __global__ void k_link_children(int nh, Hubs hb, const int64_t *__restrict__ child_base, int node_base,
                                 int32_t *__restrict__ child_begin, int32_t *__restrict__ child_count,
-                                int32_t *__restrict__ node_level, int32_t *__restrict__ parent) {
+                                int32_t *__restrict__ node_level, int32_t *__restrict__ parent,
+                                int32_t *__restrict__ leafy) {
     int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= nh) return;
     int u = hb.node[h];
@@ -606,7 +639,11 @@ __global__ void k_link_children(int nh, Hubs hb, const int64_t *__restrict__ chi
     child_begin[u] = first;
     child_count[u] = hb.nc[h];
     node_level[u] = hb.level[h];
-    for (int c = 0; c < hb.nc[h]; ++c) parent[first + c] = u;
+    const int fl = hb.flat[h];
+    for (int c = 0; c < hb.nc[h]; ++c) {
+        parent[first + c] = u;
+        leafy[child_base[h] + c] = fl;
+    }
 }
 
 // New vertices of the round; flags children that become next-round hubs.
@@ -615,7 +652,8 @@ __global__ void k_make_nodes(int64_t T, int node_base, int zeta, int metric,
                              const unsigned long long *__restrict__ ckey, int32_t *__restrict__ node_begin,
                              int32_t *__restrict__ node_count, int32_t *__restrict__ child_begin,
                              int32_t *__restrict__ child_count, float *__restrict__ radius,
-                             int32_t *__restrict__ level, int32_t *__restrict__ is_hub) {
+                             int32_t *__restrict__ level, const int32_t *__restrict__ leafy,
+                             int32_t *__restrict__ is_hub) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= T) return;
     int v = node_base + (int)c;
@@ -626,7 +664,7 @@ __global__ void k_make_nodes(int64_t T, int node_base, int zeta, int metric,
     child_count[v] = 0;
     radius[v] = round_radius_up(r, metric);
     level[v] = r > 0.0f ? ceil_log2f(r) : INT_MIN;
-    is_hub[c] = (ccount[c] > zeta && r > 0.0f) ? 1 : 0;
+    is_hub[c] = (ccount[c] > zeta && r > 0.0f && !leafy[c]) ? 1 : 0;
 }
 
 // Next round's hubs from the flagged children (order preserved).
@@ -644,6 +682,8 @@ __global__ void k_next_hubs(int64_t T, int node_base, const int32_t *__restrict_
     nh.nc[h] = 1;
     nh.cur[h] = cbegin[c];
     nh.done[h] = 0;
+    nh.flat[h] = 0;
+    nh.covered[h] = 0;
     nh.key[h] = ckey[c];
     int l = level[v];
     nh.level[h] = l;
@@ -681,6 +721,8 @@ __global__ void k_root_node(int64_t n, int zeta, int metric, const unsigned long
     hb.nc[0] = 1;
     hb.cur[0] = 0;
     hb.done[0] = 0;
+    hb.flat[0] = 0;
+    hb.covered[0] = 0;
     hb.key[0] = key[0];
     hb.level[0] = l;
     hb.thr[0] = hub ? ldexpf(1.0f, l - 1) : 0.0f;
@@ -751,13 +793,13 @@ __global__ void k_gather_strings(int64_t n, const int32_t *__restrict__ perm, co
     for (int64_t k = threadIdx.x; k < l; k += blockDim.x) out[o + k] = S[b + k];
 }
 
-// Sort keys putting larger radii first (radii are non-negative floats).
 // Query groups: greedy runs of consecutive sibling leaf blocks of at most
-// kGroupSize points in total (a larger block is a group of its own).  The
+// kGroupSize points in total; a larger block is cut into groups of kGroupSize
+// consecutive points (the last one shorter) that hold no other block.  The
 // leaf blocks are in position order; k_group_prep lays out each block's size
 // and parent in that order, a run of siblings starts where the parent
-// changes, and one thread walks each run (sequential reads), marking where
-// its groups start and recording each group's size there.
+// changes, and one thread walks each run (sequential reads), marking how many
+// groups start at each block and recording the size of a merged group there.
 __global__ void k_group_prep(int L, const int32_t *__restrict__ leaf_ids, const int32_t *__restrict__ node_count,
                              const int32_t *__restrict__ parent, int32_t *__restrict__ lcount,
                              int32_t *__restrict__ lpar) {
@@ -775,22 +817,28 @@ __global__ void k_group_marks(int L, const int32_t *__restrict__ lcount, const i
     if (i >= L) return;
     const int p = lpar[i];
     if (i > 0 && lpar[i - 1] == p) return;  // not the first block of its sibling run
-    int first = i, acc = lcount[i], big = 0;
-    gstart[i] = 1;
-    for (int j = i + 1; j < L && lpar[j] == p; ++j) {
+    int first = -1, acc = 0, big = 0;
+    for (int j = i; j < L && lpar[j] == p; ++j) {
         const int c = lcount[j];
-        if (acc + c <= kGroupSize) {
+        if (c > kGroupSize) {  // groups of its own
+            if (first >= 0) gsize[first] = acc;
+            gstart[j] = (c + kGroupSize - 1) / kGroupSize;
+            gsize[j] = c;
+            big = kGroupSize;
+            first = -1;
+            acc = 0;
+        } else if (first >= 0 && acc + c <= kGroupSize) {
             acc += c;
             gstart[j] = 0;
         } else {
-            gsize[first] = acc;
+            if (first >= 0) gsize[first] = acc;
             big = max(big, acc);
             first = j;
             acc = c;
             gstart[j] = 1;
         }
     }
-    gsize[first] = acc;
+    if (first >= 0) gsize[first] = acc;
     big = max(big, acc);
     atomicMax(maxc, (unsigned long long)big);
 }
@@ -802,10 +850,14 @@ __global__ void k_group_scatter(int L, const int32_t *__restrict__ leaf_ids, con
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= L || !gstart[i]) return;
     const int64_t g = gidx[i];
-    group_begin[g] = node_begin[leaf_ids[i]];
-    group_count[g] = gsize[i];
+    const int b = node_begin[leaf_ids[i]], c = gsize[i];
+    for (int k = 0; k < gstart[i]; ++k) {  // one group, or the cuts of a large block
+        group_begin[g + k] = b + k * kGroupSize;
+        group_count[g + k] = min(kGroupSize, c - k * kGroupSize);
+    }
 }
 
+// Sort keys putting larger radii first (radii are non-negative floats).
 __global__ void k_radius_desc_keys(int ng, const float *__restrict__ r, uint32_t *__restrict__ keys,
                                    uint32_t *__restrict__ vals) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -938,10 +990,10 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
         if (root < 0 || root >= n) CT_FAIL(CT_EINVAL, "root %d out of range", root);
         // ---- round 0: distances to the root
         const int64_t cap_h = n;  // hubs per round never exceed n / (zeta+1) + 1
-        DBuf<int32_t> hbuf(7 * (cap_h + 1), s);
+        DBuf<int32_t> hbuf(9 * (cap_h + 1), s);
         DBuf<float> hthr(cap_h + 1, s);
         DBuf<unsigned long long> hkey(cap_h + 1, s);
-        DBuf<int32_t> hbuf2(7 * (cap_h + 1), s);
+        DBuf<int32_t> hbuf2(9 * (cap_h + 1), s);
         DBuf<float> hthr2(cap_h + 1, s);
         DBuf<unsigned long long> hkey2(cap_h + 1, s);
         auto make_hubs = [&](DBuf<int32_t> &b, DBuf<float> &th, DBuf<unsigned long long> &k) {
@@ -949,6 +1001,7 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
             int64_t st = cap_h + 1;
             h.begin = b.p; h.count = b.p + st; h.node = b.p + 2 * st; h.nc = b.p + 3 * st;
             h.cur = b.p + 4 * st; h.done = b.p + 5 * st; h.level = b.p + 6 * st;
+            h.flat = b.p + 7 * st; h.covered = b.p + 8 * st;
             h.thr = th.p; h.key = k.p;
             return h;
         };
@@ -997,6 +1050,8 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
             CT_CHECK_CUDA(cudaMemcpyAsync(H.nc, &one, 4, cudaMemcpyHostToDevice, s));
             CT_CHECK_CUDA(cudaMemcpyAsync(H.cur, &zero, 4, cudaMemcpyHostToDevice, s));
             CT_CHECK_CUDA(cudaMemcpyAsync(H.done, &zero, 4, cudaMemcpyHostToDevice, s));
+            CT_CHECK_CUDA(cudaMemcpyAsync(H.flat, &zero, 4, cudaMemcpyHostToDevice, s));
+            CT_CHECK_CUDA(cudaMemcpyAsync(H.covered, &zero, 4, cudaMemcpyHostToDevice, s));
             CT_CHECK_CUDA(cudaMemcpyAsync(H.key, &z, 8, cudaMemcpyHostToDevice, s));
             CT_CHECK_CUDA(cudaStreamSynchronize(s));  // host values above are on the stack
         }
@@ -1091,7 +1146,7 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
                         // step is taken inside the update pass by each hub's last block
                         if (first_step) {
                             CT_CHECK_CUDA(cudaMemsetAsync(arrive.p, 0, nh * sizeof(int32_t), s));
-                            k_hub_step<<<grid_for(nl), BT, 0, s>>>((int)nl, hl, H, active.p, cpos.p);
+                            k_hub_step<<<grid_for(nl), BT, 0, s>>>((int)nl, hl, H, active.p, cpos.p, 1);
                             CT_COUNT_LAUNCH();
                             switch (tpd) {
 #define CT_CD(T) case T: k_centre_dists<T><<<(unsigned)nl, BT, 0, s>>>(Xp.p, dp, ids.p, H, hl, cpos.p, dcc.p); break;
@@ -1106,7 +1161,7 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
                         for (int it = 0; it < burst; ++it) update(H, nck, cb, cs, st);
                     } else {
                         for (int it = 0; it < burst; ++it) {
-                            k_hub_step<<<grid_for(nl), BT, 0, s>>>((int)nl, hl, H, active.p, nullptr);
+                            k_hub_step<<<grid_for(nl), BT, 0, s>>>((int)nl, hl, H, active.p, nullptr, 0);
                             CT_COUNT_LAUNCH();
                             update(H, nck, cb, cs, Step{});
                         }
@@ -1145,7 +1200,7 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
                                                    pv.p, rpos.p);
             CT_COUNT_LAUNCH();
             radix_sort_pairs(pk.p, pv.p, tk.p, tv.p, R, bits_for(T), s);
-            DBuf<int32_t> ccount(T, s), cbegin(T, s), czero(T, s), is_hub(T, s);
+            DBuf<int32_t> ccount(T, s), cbegin(T, s), czero(T, s), is_hub(T, s), leafy(T, s);
             DBuf<unsigned long long> ckey(T, s);
             CT_CHECK_CUDA(cudaMemsetAsync(ccount.p, 0, T * sizeof(int32_t), s));
             CT_CHECK_CUDA(cudaMemsetAsync(cbegin.p, 0x7f, T * sizeof(int32_t), s));
@@ -1160,10 +1215,11 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
             CT_COUNT_LAUNCH();
             k_child_keys<<<grid_for(R), BT, 0, s>>>(R, pk.p, rpos.p, D.p, ckey.p);
             CT_COUNT_LAUNCH();
-            k_link_children<<<grid_for(nh), BT, 0, s>>>((int)nh, H, child_base.p, n_nodes, cbeg.p, ccnt.p, lvl.p, par.p);
+            k_link_children<<<grid_for(nh), BT, 0, s>>>((int)nh, H, child_base.p, n_nodes, cbeg.p, ccnt.p, lvl.p, par.p,
+                                                         leafy.p);
             CT_COUNT_LAUNCH();
             k_make_nodes<<<grid_for(T), BT, 0, s>>>(T, n_nodes, zeta, pts->metric, cbegin.p, ccount.p, ckey.p,
-                                                    nb.p, ncnt.p, cbeg.p, ccnt.p, rad.p, lvl.p, is_hub.p);
+                                                    nb.p, ncnt.p, cbeg.p, ccnt.p, rad.p, lvl.p, leafy.p, is_hub.p);
             CT_COUNT_LAUNCH();
             DBuf<int64_t> hub_off(T, s);
             exclusive_scan_i32_to_i64(is_hub.p, hub_off.p, T, i64tmp.p, s);

@@ -184,7 +184,8 @@ struct ct_tree {
     int32_t *parent = nullptr;       // parent vertex (-1 for the root)
 
     // query groups: runs of consecutive sibling leaf blocks with at most
-    // kGroupSize points in total (a larger leaf block is a group of its own);
+    // kGroupSize points in total (a larger leaf block is cut into groups of
+    // kGroupSize consecutive points, the last one shorter);
     // centre = first point, radius = max distance to it (rounded up)
     int32_t n_groups = 0, max_group_count = 0;
     int32_t *group_begin = nullptr;

@@ -63,6 +63,28 @@ def test_parity_dims_and_leaf_sizes(dim, n, zeta, seed):
             _check_tree(sp, out)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_flat_split_in_high_dimension(precision):
+    """Uniform points in 64-D: every pairwise distance lies above the split
+    threshold of the second level, so farthest-first splitting would make
+    every point its own child.  The split stops after its first centres and
+    their cells become leaf blocks larger than zeta (still a valid net with
+    exact stored radii); the graph stays exact."""
+    x = I.uniform_cube(6000, 64, seed=21)
+    sp = oracle.Space(points=x)
+    rng = np.random.default_rng(21)
+    sample = oracle.brute_rows(sp, 1e30, rng.integers(0, 6000, size=8))["dist"]
+    for q in (0.001, 0.02):
+        eps = float(np.float32(np.quantile(sample, q)))
+        out = gpu_graph(points=x, eps=eps, precision=precision, export=True)
+        assert_csr_matches(out, oracle.brute_force(sp, eps))
+        _check_tree(sp, out)
+        tr = out["tree"]
+        leaf = np.asarray(tr["child_count"]) == 0
+        big = leaf & (np.asarray(tr["pts_count"]) > 32) & (np.asarray(tr["radius"]) > 0)
+        assert big.any(), "no flat split happened"
+
+
 def test_degenerate_sizes():
     for n in (0, 1, 2, 3, 33):
         x = I.uniform_cube(n, 3, seed=n)

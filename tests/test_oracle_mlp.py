@@ -101,7 +101,9 @@ def test_features_hand_computed():
 
 def test_query_groups_split_at_32_points():
     """Sibling leaves are merged while the run stays at most 32 points; a
-    leaf of another parent starts a new group."""
+    leaf of another parent starts a new group; a leaf block above 32 points is
+    cut into groups of 32 (the last one shorter) of its own, and the sibling
+    after it starts a new group."""
     # root 0 -> children 1..5 (1..4 leaf blocks of 20, 12, 5, 40 points; 5
     # internal) and 5 -> leaf block 6 of 3 points
     tree = {"center": np.zeros(7, np.int64), "radius": np.ones(7),
@@ -110,4 +112,11 @@ def test_query_groups_split_at_32_points():
             "pts_begin": np.array([0, 0, 20, 32, 37, 0, 77]), "pts_count": np.array([0, 20, 12, 5, 40, 0, 3]),
             "leaf_pts": np.arange(80)}
     gb, gc, _ = mlp.query_groups(tree)
-    assert list(gb) == [0, 32, 37, 77] and list(gc) == [32, 5, 40, 3]
+    assert list(gb) == [0, 32, 37, 69, 77] and list(gc) == [32, 5, 32, 8, 3]
+    # a small sibling after the large block does not join its last group
+    tree2 = {"center": np.zeros(6, np.int64), "radius": np.ones(6), "level": np.zeros(6, np.int32),
+             "child_begin": np.array([1, 0, 0, 0, 0, 0]), "child_count": np.array([5, 0, 0, 0, 0, 0]),
+             "pts_begin": np.array([0, 0, 20, 32, 37, 77]), "pts_count": np.array([0, 20, 12, 5, 40, 3]),
+             "leaf_pts": np.arange(80)}
+    gb, gc, _ = mlp.query_groups(tree2)
+    assert list(gb) == [0, 32, 37, 69, 77] and list(gc) == [32, 5, 32, 8, 3]
