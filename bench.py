@@ -280,6 +280,10 @@ def run_reference(args, wl):
     return 0
 
 
+# the three radii of a sweep over one tree (sift's eps = 125, 175, 225 shapes)
+SWEEPS = {"gmm_1m_k70": ["gmm_1m_k10", "gmm_1m_k70", "gmm_1m_k500"],
+          "gmm_1m_k500": ["gmm_1m_k10", "gmm_1m_k70", "gmm_1m_k500"]}
+
 FORMS = {"plain": (0, False), "tc": (1, False), "learned": (0, True), "tc+learned": (1, True),
          "auto": (2, False), "auto+learned": (2, True)}
 
@@ -538,6 +542,51 @@ def run_single(args, wl, world, rank, dist):
                 raise RuntimeError("form %s produced a different CSR than %s" % (name, args.form))
         ref.free()
 
+    # several radii over one tree (Table I's three radii per dataset): three
+    # independent queries against one eps_graph_query_sweep, tree built once
+    sweep = None
+    radii = SWEEPS.get(args.workload)
+    if radii and not args.no_sweep:
+        wls = I.load_workloads()
+        reps = [wls[k]["eps"] for k in radii]
+        with torch.cuda.stream(stream):
+            t = build(stream)
+            ind = [cg.eps_graph_query(t, e, precision=precision, stream=stream, use_predictor=learned,
+                                      predictor=pred) for e in reps]
+            sw = cg.eps_graph_query_sweep(t, reps, precision=precision, stream=stream, use_predictor=learned,
+                                          predictor=pred)
+            same = all(csr_equal(a, b) for a, b in zip(ind, sw))
+            sw_nnz = [c.nnz for c in sw]
+            for c in ind + sw:
+                c.free()
+        if not same:
+            raise RuntimeError("the radius sweep differs from independent queries")
+        times = {}
+        for mode in ("independent", "sweep"):
+            barrier()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            with torch.cuda.stream(stream):
+                for _ in range(args.steps):
+                    if mode == "sweep":
+                        cs = cg.eps_graph_query_sweep(t, reps, precision=precision, stream=stream,
+                                                      use_predictor=learned, predictor=pred)
+                    else:
+                        cs = [cg.eps_graph_query(t, e, precision=precision, stream=stream, use_predictor=learned,
+                                                 predictor=pred) for e in reps]
+                    for c in cs:
+                        c.free()
+            b.record(stream)
+            barrier()
+            times[mode] = a.elapsed_time(b) / args.steps
+        t.free()
+        sweep = {"radii": dict(zip(radii, reps)), "nnz": dict(zip(radii, sw_nnz)),
+                 "csr_identical_to_independent_queries": bool(same),
+                 "ms_independent": times["independent"], "ms_sweep": times["sweep"],
+                 "edges_per_s_sweep": sum(sw_nnz) / (times["sweep"] / 1e3),
+                 "speedup": times["independent"] / times["sweep"],
+                 "note": "one tree, built once outside the timed region; queries of the form above"}
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -591,7 +640,7 @@ def run_single(args, wl, world, rank, dist):
             "roofline": roofline(prof, st, wl, args.workload, peaks, dim, mean_len),
             "traversal": traversal_roofline(prof, st, n, dim, args.workload, peaks) if kind == "points" else None,
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "library": cg.library_path(),
-            "forms": forms}
+            "forms": forms, "sweep": sweep}
     if fit_info:
         line["learned"] = fit_info
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -820,6 +869,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-queries", type=int, default=4000)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip timing the three-radius sweep")
     ap.add_argument("--fit-steps", type=int, default=1500)
     ap.add_argument("--order-radius", action="store_true",
                     help="learned forms: walk groups by radius instead of predicted walk length")

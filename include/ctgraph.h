@@ -170,6 +170,37 @@ ct_status eps_graph_query_batched(int32_t n_clouds, const ct_tree *const *trees,
                                   const double *eps, const ct_query_opts *opts,
                                   ct_stream stream, ct_csr *outs);
 
+/* The ε-graph of one tree at several radii (the paper queries each dataset at
+ * three radii, Table I; the tree does not depend on eps, so one build serves
+ * them all).  outs[k] is exactly the CSR eps_graph_query(tree, eps[k], opts)
+ * returns (the same entries and distances, bit for bit), each released with
+ * csr_free.  The largest radius is queried in full; each smaller one is
+ * derived from the CSR of the next larger one: an entry is decided again
+ * from its stored distance when that distance lies outside the guard band
+ * |d - r| <= 1e-3 r of both radii (the stored value is within 1e-6 of the
+ * exact one), and from the points, by the query's own decision, inside it.
+ * eps (host array of n_eps) may be in any order.  The counters of outs[k]
+ * are the full query's for the largest radius; for the others leaf_pairs
+ * counts the entries evaluated again from the points.  Synchronises
+ * `stream` once per radius.  Errors: as eps_graph_query for any radius. */
+ct_status eps_graph_query_sweep(const ct_tree *tree, int32_t n_eps, const double *eps,
+                                const ct_query_opts *opts, ct_stream stream, ct_csr *outs);
+
+/* Writes a tree to a file at `path` (a header with the sizes, every device
+ * array of the tree, and a 64-bit FNV-1a checksum), so that a later process
+ * can query it without building it again.  Synchronises the tree's stream.
+ * Errors: CT_EINVAL (NULL argument, the file cannot be written), CT_ECUDA. */
+ct_status ct_tree_save(const ct_tree *tree, const char *path);
+
+/* Reads a tree written by ct_tree_save onto the current device (allocated
+ * stream-ordered on `stream`, released with ct_tree_free).  Queries of the
+ * loaded tree return what queries of the saved one return.  The header is
+ * checked, the checksum compared and every index of the tree range-checked
+ * on the device before the call returns.  Synchronises `stream`.
+ * Errors: CT_EINVAL (NULL argument, unreadable, truncated or inconsistent
+ * file, checksum mismatch), CT_ENOMEM, CT_ECUDA. */
+ct_status ct_tree_load(const char *path, ct_stream stream, ct_tree **out);
+
 /* Autotuner of precision 2.  For each class of row length present among the
  * L2 trees (dp = dim rounded up to 4: <= 4, 16, 32, 64, 128), times the
  * batched query of that class's clouds (eps_graph_query_batched with

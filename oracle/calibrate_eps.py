@@ -29,6 +29,24 @@ PROFILE_SIZE = {"kind": "gmm", "n": 300_000, "dim": 128, "seed": 0, "target_degr
                 "note": "profiling size of the 1M generator (154 MB of points, above the 129 MB L2)"}
 
 
+BASE = {
+    "small_3d": {"kind": "uniform", "n": 2000, "dim": 3, "seed": 0, "eps": 0.08,
+                 "zeta": 32, "note": "uniform [0,1]^3, eps=0.08"},
+    "gmm_1m_k10": {"kind": "gmm", "n": 1_000_000, "dim": 128, "seed": 0,
+                   "target_degree": 10.0, "zeta": 32,
+                   "note": "same generator; sift eps=125 stand-in (the smallest radius of the sweep)"},
+    "gmm_1m_k70": {"kind": "gmm", "n": 1_000_000, "dim": 128, "seed": 0,
+                   "target_degree": 70.0, "zeta": 32,
+                   "note": "100-component 8-D GMM embedded in 128-D; sift eps=175 stand-in"},
+    "gmm_1m_k500": {"kind": "gmm", "n": 1_000_000, "dim": 128, "seed": 0,
+                    "target_degree": 500.0, "zeta": 32,
+                    "note": "same generator; sift eps=225 stand-in"},
+    "dna_50k": {"kind": "dna", "n_seeds": 500, "per_seed": 100, "seed_len": 96,
+                "seed": 0, "eps": 8, "zeta": 32,
+                "note": "Levenshtein; 4% substitution, 0.5% insertion, 0.5% deletion per site"},
+}
+
+
 def calibrate(x: np.ndarray, target_degree: float, n_queries: int = 4096, seed: int = 12345) -> float:
     n = x.shape[0]
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -64,7 +82,7 @@ def main():
         with open(OUT) as f:
             wl = json.load(f)
         key = args.only
-        spec = dict(PROFILE_SIZE) if key == "gmm_300k_k70" else wl[key]
+        spec = dict(PROFILE_SIZE) if key == "gmm_300k_k70" else wl.get(key) or BASE[key]
         x = I.gmm_embedded(spec["n"], dim=spec["dim"], seed=spec["seed"])
         spec["eps"] = calibrate(x, spec["target_degree"])
         wl[key] = spec
@@ -72,25 +90,13 @@ def main():
         with open(OUT, "w") as f:
             json.dump(wl, f, indent=1)
         return
-    wl = {
-        "small_3d": {"kind": "uniform", "n": 2000, "dim": 3, "seed": 0, "eps": 0.08,
-                     "zeta": 32, "note": "uniform [0,1]^3, eps=0.08"},
-        "gmm_1m_k70": {"kind": "gmm", "n": 1_000_000, "dim": 128, "seed": 0,
-                       "target_degree": 70.0, "zeta": 32,
-                       "note": "100-component 8-D GMM embedded in 128-D; sift eps=175 stand-in"},
-        "gmm_1m_k500": {"kind": "gmm", "n": 1_000_000, "dim": 128, "seed": 0,
-                        "target_degree": 500.0, "zeta": 32,
-                        "note": "same generator; sift eps=225 stand-in"},
-        "dna_50k": {"kind": "dna", "n_seeds": 500, "per_seed": 100, "seed_len": 96,
-                    "seed": 0, "eps": 8, "zeta": 32,
-                    "note": "Levenshtein; 4% substitution, 0.5% insertion, 0.5% deletion per site"},
-    }
+    wl = {k: dict(v) for k, v in BASE.items()}
     wl["gmm_300k_k70"] = dict(PROFILE_SIZE)
     x3 = I.gmm_embedded(300_000, seed=0)
     wl["gmm_300k_k70"]["eps"] = calibrate(x3, 70.0)
     del x3
     x = I.gmm_embedded(1_000_000, seed=0)
-    for key in ("gmm_1m_k70", "gmm_1m_k500"):
+    for key in ("gmm_1m_k10", "gmm_1m_k70", "gmm_1m_k500"):
         wl[key]["eps"] = calibrate(x, wl[key]["target_degree"])
         print(key, wl[key]["eps"], flush=True)
     del x

@@ -1,8 +1,10 @@
 // capi.cu -- the C-ABI of include/ctgraph.h: argument checks, status codes,
 // ownership of trees and CSR outputs.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "mlp.cuh"
 #include "query.cuh"
@@ -19,6 +21,10 @@ void autotune(int n_clouds, const ct_tree *const *trees, const QParams *qps, con
               cudaStream_t s, int32_t *choices);
 void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cudaStream_t s);
 void tc_selftest(const void *A, const void *B, int fp16, float *D, cudaStream_t s);
+void save_tree(const ct_tree *t, const char *path);
+ct_tree *load_tree(const char *path, cudaStream_t s);
+void sweep_filter(const ct_tree *t, const QParams &qs, const QParams &qd, const QueryOut &src, cudaStream_t s,
+                  QueryOut &out);
 }  // namespace ct
 
 namespace {
@@ -145,6 +151,66 @@ ct_status eps_graph_query(const ct_tree *tree, double eps, const ct_query_opts *
         if (out) std::memset(out, 0, sizeof(*out));
     }
     return st;
+}
+
+ct_status eps_graph_query_sweep(const ct_tree *tree, int32_t n_eps, const double *eps, const ct_query_opts *opts,
+                                ct_stream stream, ct_csr *outs) {
+    if (outs && n_eps > 0) std::memset(outs, 0, sizeof(ct_csr) * (size_t)n_eps);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<ct::QueryOut> q((size_t)(n_eps > 0 ? n_eps : 0));
+    ct_status st = guarded([&] {
+        if (n_eps < 0) CT_FAIL(CT_EINVAL, "n_eps must be >= 0");
+        if (n_eps == 0) return;
+        if (!eps || !outs) CT_FAIL(CT_EINVAL, "eps and outs must not be NULL");
+        ct_query_opts o = opts ? *opts : default_query_opts();
+        for (int k = 0; k < n_eps; ++k) validate_query(tree, eps[k], o);
+        check_device(tree);
+        // radii in decreasing order; equal radii keep their input order
+        std::vector<int> ord((size_t)n_eps);
+        for (int k = 0; k < n_eps; ++k) ord[k] = k;
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return eps[a] > eps[b]; });
+        std::vector<ct::QParams> qps((size_t)n_eps);
+        for (int k = 0; k < n_eps; ++k) qps[k] = ct::make_qparams(tree, eps[k], o.include_self);
+        ct::g_launches = 0;
+        const int top = ord[0];
+        if (o.use_predictor)
+            ct::query_predicted(tree, qps[top], o.predictor, o.precision, s, q[top]);
+        else
+            ct::query_multi(1, &tree, &qps[top], s, &q[top], o.precision, nullptr, nullptr);
+        q[top].stats.kernel_launches = ct::g_launches;
+        for (size_t i = 1; i < ord.size(); ++i) {
+            const int a = ord[i - 1], b = ord[i];
+            ct::g_launches = 0;
+            ct::sweep_filter(tree, qps[a], qps[b], q[a], s, q[b]);
+            q[b].stats.kernel_launches = ct::g_launches;
+        }
+        for (int k = 0; k < n_eps; ++k) {
+            fill_csr(&outs[k], tree->n, q[k], s);
+            q[k] = ct::QueryOut();
+        }
+    });
+    if (st != CT_OK) {
+        for (auto &x : q) release_query_out(x, s);
+        if (outs && n_eps > 0) std::memset(outs, 0, sizeof(ct_csr) * (size_t)n_eps);
+    }
+    return st;
+}
+
+ct_status ct_tree_save(const ct_tree *tree, const char *path) {
+    return guarded([&] {
+        if (!tree || !path) CT_FAIL(CT_EINVAL, "tree and path must not be NULL");
+        check_device(tree);
+        ct::save_tree(tree, path);
+    });
+}
+
+ct_status ct_tree_load(const char *path, ct_stream stream, ct_tree **out) {
+    if (out) *out = nullptr;
+    return guarded([&] {
+        if (!path || !out) CT_FAIL(CT_EINVAL, "path and out must not be NULL");
+        ct::g_launches = 0;
+        *out = ct::load_tree(path, (cudaStream_t)stream);
+    });
 }
 
 ct_status eps_graph_query_batched(int32_t n_clouds, const ct_tree *const *trees, const double *eps,

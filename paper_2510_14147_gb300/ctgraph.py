@@ -150,6 +150,13 @@ def _load():
                                          P(C.c_double), C.c_void_p]
         lib.ct_mlp_forward_f16.restype = C.c_int
         lib.ct_mlp_forward_f16.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+        lib.eps_graph_query_sweep.restype = C.c_int
+        lib.eps_graph_query_sweep.argtypes = [C.c_void_p, C.c_int32, P(C.c_double), P(ct_query_opts), C.c_void_p,
+                                              P(ct_csr)]
+        lib.ct_tree_save.restype = C.c_int
+        lib.ct_tree_save.argtypes = [C.c_void_p, C.c_char_p]
+        lib.ct_tree_load.restype = C.c_int
+        lib.ct_tree_load.argtypes = [C.c_char_p, C.c_void_p, P(C.c_void_p)]
         _lib = lib
         return lib
 
@@ -329,6 +336,35 @@ def eps_graph_query_batched(trees, eps, precision: int = 0, use_predictor: bool 
     o = _opts(precision, use_predictor, include_self, predictor)
     _check(lib.eps_graph_query_batched(k, arr, ea, C.byref(o), C.c_void_p(_stream(stream)), outs))
     return [CSR(outs[i]) for i in range(k)]
+
+
+def eps_graph_query_sweep(tree: Tree, eps, precision: int = 0, use_predictor: bool = False,
+                          include_self: bool = False, predictor=None, stream=None):
+    """CSRs of one tree at several radii (eps: a sequence); csrs[k] equals
+    eps_graph_query(tree, eps[k], ...) bit for bit."""
+    lib = _load()
+    k = len(eps)
+    ea = (C.c_double * max(k, 1))(*[float(e) for e in eps])
+    outs = (ct_csr * max(k, 1))()
+    o = _opts(precision, use_predictor, include_self, predictor)
+    _check(lib.eps_graph_query_sweep(tree.handle, k, ea, C.byref(o), C.c_void_p(_stream(stream)), outs))
+    return [CSR(outs[i]) for i in range(k)]
+
+
+def ct_tree_save(tree: Tree, path: str):
+    """Writes the tree to a file (ct_tree_load reads it back)."""
+    _check(_load().ct_tree_save(tree.handle, os.fsencode(path)))
+
+
+def ct_tree_load(path: str, stream=None) -> Tree:
+    """A tree written by ct_tree_save, on the current device."""
+    lib = _load()
+    h = C.c_void_p()
+    _check(lib.ct_tree_load(os.fsencode(path), C.c_void_p(_stream(stream)), C.byref(h)))
+    n_nodes, n_pts = C.c_int64(), C.c_int64()
+    _check(lib.ct_tree_shape(h, C.byref(n_nodes), C.byref(n_pts)))
+    t = Tree(h.value, int(n_pts.value), -1)
+    return t
 
 
 def ct_autotune(trees, eps, use_predictor: bool = False, include_self: bool = False, predictor=None,
