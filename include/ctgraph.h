@@ -170,6 +170,54 @@ ct_status eps_graph_query_batched(int32_t n_clouds, const ct_tree *const *trees,
                                   const double *eps, const ct_query_opts *opts,
                                   ct_stream stream, ct_csr *outs);
 
+/* ------------------------------------------------------------------------
+ * Plans: one batch of L2 clouds (the batched form above) queried again and
+ * again over the same trees, with every buffer allocated once.  The paper's
+ * batching of queries (Sec. IV-B) is carried across clouds: a run is one
+ * sequence of launches with no host read-back and no allocation -- the walk
+ * over every cloud's query groups, each group's candidates gathered into one
+ * range, then the leaf stage as ONE persistent launch over all clouds'
+ * (cloud, group) work items: each CTA first produces the work items of a
+ * chunk of groups into a device work queue (groups in the walk order; item
+ * lengths per row-length class from ct_autotune with precision 2), then
+ * takes queue slots, waiting for a slot's producer with a bounded number of
+ * polls -- then the scan, the emit pass (the same persistent launch over the
+ * complete queue) and the in-place row sorts.  With use_graph the run is
+ * captured once into a CUDA graph and every launch replays it.  A plan's leaf
+ * tiles are the FP32 ones (precision 1 is taken as 0); use_predictor orders
+ * the walk by predicted work; the output equals eps_graph_query_batched's.
+ * The plan borrows the trees: they must outlive it and stay unchanged. */
+typedef struct ct_plan ct_plan;
+
+/* Runs the batch once with the exact query to size every buffer (candidate
+ * list, work queue, edges: each times 1 + margin, plus a constant), then
+ * allocates them (and captures the graph when use_graph != 0).  1 <= n_clouds
+ * <= 64, L2 trees on the current device.  Synchronises `stream`.
+ * Errors: CT_EINVAL (NULL arguments, a bad count, margin outside [0, 100],
+ * an edit-distance tree, options as eps_graph_query), CT_EUNSUPPORTED (a row
+ * longer than 4096 entries: plans sort rows in place), CT_ENOMEM, CT_ECUDA. */
+ct_status ct_plan_create(int32_t n_clouds, const ct_tree *const *trees, const double *eps,
+                         const ct_query_opts *opts, float margin, int32_t use_graph, ct_stream stream,
+                         ct_plan **out);
+/* Enqueues one run on `stream` (a graph launch with use_graph); returns at
+ * once.  Runs on one plan must not overlap (they share its buffers). */
+ct_status ct_plan_launch(ct_plan *plan, ct_stream stream);
+/* Synchronises `stream` and reports the last run: CT_OK with outs[c] (host
+ * array of n_clouds) the CSR of cloud c -- views into the plan's buffers,
+ * valid until the next launch or ct_plan_free (csr_free releases only the
+ * view) -- or CT_EOVERFLOW (the run outgrew a capacity: create a new plan),
+ * CT_ETIMEOUT (a work-queue wait gave up), CT_ECUDA; on error outs are
+ * zeroed. */
+ct_status ct_plan_result(ct_plan *plan, ct_stream stream, ct_csr *outs);
+/* Test control of the work queue's bounded waits, read by later runs
+ * (replays included): withhold_producers != 0 makes the producers take their
+ * groups and publish nothing, so that every consumer's wait runs out after
+ * max_polls polls (about 1 us each; default 2^20) and the run reports
+ * CT_ETIMEOUT.  Synchronises the device.  Errors: CT_EINVAL. */
+ct_status ct_plan_set_wait(ct_plan *plan, int32_t withhold_producers, int32_t max_polls);
+/* Releases a plan (synchronises its creation stream).  NULL-safe. */
+void ct_plan_free(ct_plan *plan);
+
 /* The ε-graph of one tree at several radii (the paper queries each dataset at
  * three radii, Table I; the tree does not depend on eps, so one build serves
  * them all).  outs[k] is exactly the CSR eps_graph_query(tree, eps[k], opts)

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -194,6 +195,78 @@ ct_status eps_graph_query_sweep(const ct_tree *tree, int32_t n_eps, const double
         if (outs && n_eps > 0) std::memset(outs, 0, sizeof(ct_csr) * (size_t)n_eps);
     }
     return st;
+}
+
+struct ct_plan {
+    ct::PlanImpl *impl;
+};
+
+ct_status ct_plan_create(int32_t n_clouds, const ct_tree *const *trees, const double *eps, const ct_query_opts *opts,
+                         float margin, int32_t use_graph, ct_stream stream, ct_plan **out) {
+    if (out) *out = nullptr;
+    return guarded([&] {
+        if (!out || !trees || !eps) CT_FAIL(CT_EINVAL, "trees, eps and out must not be NULL");
+        if (n_clouds < 1 || n_clouds > ct::kBatchClouds)
+            CT_FAIL(CT_EINVAL, "a plan takes 1 to %d clouds (got %d)", ct::kBatchClouds, n_clouds);
+        if (!(margin >= 0.0f) || margin > 100.0f) CT_FAIL(CT_EINVAL, "margin must be in [0, 100]");
+        ct_query_opts o = opts ? *opts : default_query_opts();
+        std::vector<ct::QParams> qps((size_t)n_clouds);
+        for (int c = 0; c < n_clouds; ++c) {
+            validate_query(trees[c], eps[c], o);
+            check_device(trees[c]);
+            if (trees[c]->metric != CT_L2_F32) CT_FAIL(CT_EINVAL, "plans take L2 trees only");
+            qps[c] = ct::make_qparams(trees[c], eps[c], o.include_self);
+        }
+        const ct_predictor *P = o.use_predictor ? static_cast<const ct_predictor *>(o.predictor) : nullptr;
+        ct::g_launches = 0;
+        std::unique_ptr<ct_plan> h(new ct_plan{nullptr});
+        h->impl = ct::plan_create(n_clouds, trees, qps.data(), o.precision, P, margin, use_graph != 0,
+                                  (cudaStream_t)stream);
+        *out = h.release();
+    });
+}
+
+ct_status ct_plan_launch(ct_plan *plan, ct_stream stream) {
+    return guarded([&] {
+        if (!plan || !plan->impl) CT_FAIL(CT_EINVAL, "plan is NULL");
+        ct::g_launches = 0;
+        ct::plan_launch(plan->impl, (cudaStream_t)stream);
+    });
+}
+
+ct_status ct_plan_result(ct_plan *plan, ct_stream stream, ct_csr *outs) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const int C = plan && plan->impl ? ct::plan_clouds(plan->impl) : 0;
+    if (outs && C > 0) std::memset(outs, 0, sizeof(ct_csr) * (size_t)C);
+    ct_status rs = CT_OK;
+    ct_status st = guarded([&] {
+        if (!plan || !plan->impl || !outs) CT_FAIL(CT_EINVAL, "plan and outs must not be NULL");
+        std::vector<ct::QueryOut> q((size_t)C);
+        rs = ct::plan_result(plan->impl, s, q.data());
+        if (rs != CT_OK) return;
+        const ct::PlanImpl *pi = plan->impl;
+        (void)pi;
+        for (int c = 0; c < C; ++c) fill_csr(&outs[c], ct::plan_rows(plan->impl, c), q[c], s);
+    });
+    if (st == CT_OK) st = rs;
+    if (st != CT_OK && outs && C > 0) {
+        for (int c = 0; c < C; ++c) csr_free(&outs[c]);
+    }
+    return st;
+}
+
+ct_status ct_plan_set_wait(ct_plan *plan, int32_t withhold_producers, int32_t max_polls) {
+    return guarded([&] {
+        if (!plan || !plan->impl) CT_FAIL(CT_EINVAL, "plan is NULL");
+        if (max_polls < 1) CT_FAIL(CT_EINVAL, "max_polls must be >= 1");
+        ct::plan_set_wait(plan->impl, withhold_producers, max_polls);
+    });
+}
+
+void ct_plan_free(ct_plan *plan) {
+    if (!plan) return;
+    ct::plan_free(plan->impl);
+    delete plan;
 }
 
 ct_status ct_tree_save(const ct_tree *tree, const char *path) {

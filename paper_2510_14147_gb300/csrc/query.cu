@@ -783,15 +783,14 @@ __device__ __forceinline__ void cap_put(const CapOut &co, int o, int32_t c, floa
     cap_place(co, o, atomicAdd(&co.fill[o], 1), c, d);
 }
 
+// One work item of the FP32 tiles (count or emit pass), by the whole CTA.
 template <bool EMIT>
-__global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
-    const __grid_constant__ Views V, Items items, const uint32_t *__restrict__ cand,
+__device__ __forceinline__ void leaf_l2_item(
+    const Views &V, const Items &items, const int it, const uint32_t *__restrict__ cand,
     uint32_t *__restrict__ emask, int32_t *__restrict__ deg, const int64_t *__restrict__ row_ptr,
     int32_t *__restrict__ rowcur, int32_t *__restrict__ col, float *__restrict__ dist,
-    unsigned long long *__restrict__ st, int32_t *__restrict__ err, CapOut co, const uint8_t *__restrict__ rowsel) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
-    const int it = blockIdx.x;
+    unsigned long long *__restrict__ st, int32_t *__restrict__ err, const CapOut &co,
+    const uint8_t *__restrict__ rowsel, LeafShared &S) {
     if (it >= *items.count) return;
     const int gg = items.group[it];
     const int cloud = cloud_of_group(V, gg);
@@ -1247,6 +1246,18 @@ __global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
             stat_add(st, ST_EMIT, pairs);
         }
     }
+}
+
+// One CTA per work item.
+template <bool EMIT>
+__global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2(
+    const __grid_constant__ Views V, Items items, const uint32_t *__restrict__ cand,
+    uint32_t *__restrict__ emask, int32_t *__restrict__ deg, const int64_t *__restrict__ row_ptr,
+    int32_t *__restrict__ rowcur, int32_t *__restrict__ col, float *__restrict__ dist,
+    unsigned long long *__restrict__ st, int32_t *__restrict__ err, CapOut co, const uint8_t *__restrict__ rowsel) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    leaf_l2_item<EMIT>(V, items, blockIdx.x, cand, emask, deg, row_ptr, rowcur, col, dist, st, err, co, rowsel,
+                       *reinterpret_cast<LeafShared *>(smem_raw));
 }
 
 // Work items: every pool segment split into slices of at most kItem blocks.
@@ -2956,6 +2967,557 @@ void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &
 
 void query_tc(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out) {
     query_multi(1, &t, &qp, s, &out, 1, nullptr, nullptr);
+}
+
+// ---------------------------------------------------------------- plans
+//
+// A batch of L2 clouds queried again and again over the same trees (a served
+// set of point clouds): every buffer is sized once, from a sizing query plus
+// a margin, so that a run enqueues the whole query -- walk, candidate ranges,
+// count pass, scan, emit, row sort -- without reading anything back to the
+// host.  A run can therefore be captured in a CUDA graph and replayed.  The
+// leaf stage is one persistent launch over every cloud's (cloud, group) work
+// items: each CTA first produces the items of a chunk of groups into a device
+// work queue (in the walk order, which the predictor sets when one is given),
+// then consumes queue slots; a slot is waited for, with a bounded number of
+// polls, until its producer has published it.  Sizes that outgrow the plan, a
+// wait that gives up, and rows too long for the in-place sorts are reported
+// by the run's status word.
+
+namespace {
+
+constexpr int32_t Q_ERR_OVERFLOW = 128;  // a run outgrew one of the plan's capacities
+constexpr int32_t Q_ERR_TIMEOUT = 256;   // a queue wait gave up
+
+__device__ __forceinline__ int ld_acquire_i32(const int32_t *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_i32(int32_t *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// The leaf stage's work queue.  Counters: claim (next group chunk to
+// produce), tail (slots reserved), head (next slot to consume), published
+// (groups whose items are all written).
+struct Queue {
+    int32_t *claim, *tail, *head, *published;
+    int32_t *ready;  // per slot: 1 once its item is written
+    int32_t *group;
+    int64_t *begin, *end;
+    const int32_t *order;   // production order (global group ids)
+    const int32_t *gcount;  // candidate blocks per group
+    const int64_t *gbegin;  // first candidate of each group
+    const int32_t *ctl;     // ctl[0] != 0: producers publish nothing (a test); ctl[1]: polls before a wait gives up
+    int64_t cand_cap;       // candidate ranges beyond it were not copied
+    int G, cap, produce;
+};
+
+// Producer: chunks of LEAF_T groups, one thread per group; a group's items
+// are its candidate range cut at its cloud's item length.
+__device__ __forceinline__ void queue_produce(const Views &V, const Queue &Q, int32_t *err) {
+    __shared__ int s_c0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_c0 = atomicAdd(Q.claim, LEAF_T);
+        __syncthreads();
+        const int c0 = s_c0;
+        if (c0 >= Q.G) break;
+        if (Q.ctl[0]) continue;  // withheld: the chunk is taken and nothing is published
+        const int i = c0 + threadIdx.x;
+        if (i < Q.G) {
+            const int gg = Q.order[i];
+            const int cnt = Q.gcount[gg];
+            const int len = V.item_len[cloud_of_group(V, gg)];
+            int k = (cnt + len - 1) / len;
+            if (Q.gbegin[gg] + cnt > Q.cand_cap) {  // its range was not copied: no items
+                atomicOr(err, Q_ERR_OVERFLOW);
+                k = 0;
+            }
+            if (k > 0) {
+                const int base = atomicAdd(Q.tail, k);
+                const int64_t b0 = Q.gbegin[gg];
+                for (int j = 0; j < k; ++j) {
+                    const int slot = base + j;
+                    if (slot >= Q.cap) {  // slots past the plan's capacity are never consumed
+                        atomicOr(err, Q_ERR_OVERFLOW);
+                        break;
+                    }
+                    Q.group[slot] = gg;
+                    Q.begin[slot] = b0 + (int64_t)j * len;
+                    Q.end[slot] = min(b0 + (int64_t)(j + 1) * len, b0 + cnt);
+                    __threadfence();
+                    st_release_i32(Q.ready + slot, 1);
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(Q.published, min(LEAF_T, Q.G - c0));
+        }
+    }
+}
+
+// Consumer: the next slot, once published; -1 when the queue is exhausted
+// (or a wait gave up: Q_ERR_TIMEOUT).
+__device__ __forceinline__ int queue_next(const Queue &Q, int32_t *err) {
+    __shared__ int s_it;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int slot = atomicAdd(Q.head, 1);
+        int it = -1;
+        if (slot < Q.cap) {
+            const unsigned limit = (unsigned)Q.ctl[1];
+            for (unsigned poll = 0;; ++poll) {
+                if (ld_acquire_i32(Q.ready + slot)) {
+                    it = slot;
+                    break;
+                }
+                if (ld_acquire_i32(Q.published) >= Q.G && slot >= ld_acquire_i32(Q.tail)) break;
+                if (poll >= limit) {
+                    atomicOr(err, Q_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(poll < 64 ? 64 : 1024);
+            }
+            __threadfence();
+        }
+        s_it = it;
+    }
+    __syncthreads();
+    return s_it;
+}
+
+// The FP32 tiles as one persistent launch over the queue (count pass:
+// produce, then consume; emit pass: consume the complete queue again).
+template <bool EMIT>
+__global__ void __launch_bounds__(LEAF_T, 3) k_leaf_l2_queue(
+    const __grid_constant__ Views V, Queue Q, const uint32_t *__restrict__ cand, uint32_t *__restrict__ emask,
+    int32_t *__restrict__ deg, const int64_t *__restrict__ row_ptr, int32_t *__restrict__ rowcur,
+    int32_t *__restrict__ col, float *__restrict__ dist, unsigned long long *__restrict__ st,
+    int32_t *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
+    if (Q.produce) queue_produce(V, Q, err);
+    const Items items{Q.group, Q.begin, Q.end, Q.tail};
+    for (;;) {
+        const int it = queue_next(Q, err);
+        if (it < 0) break;
+        leaf_l2_item<EMIT>(V, items, it, cand, emask, deg, row_ptr, rowcur, col, dist, st, err, CapOut{}, nullptr,
+                           S);
+    }
+}
+
+// Candidate ranges per group from the walk's segments (segment count read on
+// the device; destinations checked against the plan's capacity).
+__global__ void k_plan_cand_counts(const int32_t *__restrict__ nseg_dev, int64_t seg_cap,
+                                   const int32_t *__restrict__ seg_group, const int32_t *__restrict__ seg_count,
+                                   int32_t *__restrict__ gcnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nseg = min((int64_t)*nseg_dev, seg_cap);
+    if (i < nseg && seg_count[i] > 0) atomicAdd(gcnt + seg_group[i], seg_count[i]);
+}
+__global__ void k_plan_cand_copy(const int32_t *__restrict__ nseg_dev, int64_t seg_cap,
+                                 const int32_t *__restrict__ seg_group, const int64_t *__restrict__ seg_begin,
+                                 const int32_t *__restrict__ seg_count, const int64_t *__restrict__ goff,
+                                 int32_t *__restrict__ gfill, const uint32_t *__restrict__ pool,
+                                 uint32_t *__restrict__ gcand, int64_t cand_cap, int32_t *__restrict__ err) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t nseg = min((int64_t)*nseg_dev, seg_cap);
+    if (i >= nseg) return;
+    const int g = seg_group[i], c = seg_count[i];
+    int64_t base = 0;
+    if (lane == 0) base = goff[g] + atomicAdd(gfill + g, c);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base + c > cand_cap) {
+        if (lane == 0) atomicOr(err, Q_ERR_OVERFLOW);
+        return;
+    }
+    const uint32_t *src = pool + seg_begin[i];
+    for (int k = lane; k < c; k += 32) gcand[base + k] = src[k];
+}
+// The walk's own overflow flag, and the candidate total against the plan.
+__global__ void k_plan_walk_check(const int32_t *__restrict__ pool_ovf, const int64_t *__restrict__ total,
+                                  int64_t cand_cap, int32_t *__restrict__ err) {
+    if (*pool_ovf || *total > cand_cap) atomicOr(err, Q_ERR_OVERFLOW);
+}
+// Edges above the plan's capacity: flagged, and every row emptied so that the
+// emit pass writes nothing.
+__global__ void k_plan_nnz_check(const int64_t *__restrict__ row_ptr, int64_t n, int64_t nnz_cap,
+                                 int32_t *__restrict__ flag, int32_t *__restrict__ err) {
+    if (row_ptr[n] > nnz_cap) {
+        *flag = 1;
+        atomicOr(err, Q_ERR_OVERFLOW);
+    } else {
+        *flag = 0;
+    }
+}
+__global__ void k_plan_empty_rows(int64_t n1, const int32_t *__restrict__ flag, int64_t *__restrict__ row_ptr) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n1 && *flag) row_ptr[i] = 0;
+}
+// Rows longer than the in-place sorts take (the plan sorts no longer row).
+__global__ void k_plan_sort_check(const int32_t *__restrict__ counts, int32_t *__restrict__ err) {
+    if (counts[kSortClasses - 1] > 0) atomicOr(err, Q_ERR_OVERFLOW);
+}
+
+}  // namespace
+
+struct PlanImpl {
+    int C = 0;
+    std::vector<const ct_tree *> trees;
+    Views V;
+    int64_t n = 0;
+    int G = 0;
+    int max_dp = 4, cap_stack = 0, spill_cap = 0, leaf_grid = 1;
+    TravLaunch tl{1, 1};
+    int64_t pool_cap = 0, seg_cap = 0, cand_cap = 0, item_cap = 0, nnz_cap = 0;
+    cudaStream_t s0 = 0;
+    DBuf<int32_t> order;
+    DBuf<unsigned long long> st, ctr;
+    DBuf<int32_t> next_group, spill_cnt, ctl, qctr, ready, igroup, gcount, gfill, deg, rowcur, empty_flag;
+    DBuf<int2> stacks;
+    DBuf<int4> spill_a, spill_b;
+    DBuf<longlong2> cursors;
+    DBuf<uint32_t> pool, gcand, emask;
+    DBuf<int32_t> seg_group, seg_count, col, sort_lists, sort_counts;
+    DBuf<int64_t> seg_begin, gbegin, ibeg, iend, sums, row_ptr, rel;
+    DBuf<float> dist;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~PlanImpl() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
+namespace {
+// One run of a plan: every launch on `s`, nothing read back, nothing allocated.
+void plan_enqueue(PlanImpl &p, cudaStream_t s) {
+    const Views &V = p.V;
+    const int64_t n = p.n;
+    const int G = p.G;
+    unsigned long long *st = p.st.p;
+    int32_t *err = reinterpret_cast<int32_t *>(st + ST_ERR);
+    CT_CHECK_CUDA(cudaMemsetAsync(st, 0, ST_N * sizeof(unsigned long long), s));
+    if (G == 0) {  // empty clouds only
+        CT_CHECK_CUDA(cudaMemsetAsync(p.row_ptr.p, 0, (size_t)(n + 1) * sizeof(int64_t), s));
+        CT_CHECK_CUDA(cudaMemsetAsync(p.rel.p, 0, (size_t)(n + p.C) * sizeof(int64_t), s));
+        return;
+    }
+    Pool P{p.pool.p, p.pool_cap, p.ctr.p, p.seg_group.p, p.seg_count.p, p.seg_begin.p,
+           reinterpret_cast<int32_t *>(p.ctr.p + 1), p.seg_cap, p.ctr.p + 2, reinterpret_cast<int32_t *>(p.ctr.p + 3)};
+    int4 *const spills[2] = {p.spill_a.p, p.spill_b.p};
+    // 1. the walk over every cloud's groups
+    launch_traversal(V, G, p.max_dp, 0, true, p.order.p, P, p.stacks.p, p.cap_stack, p.tl, st, err, p.next_group.p,
+                     spills, p.spill_cnt.p, p.spill_cap, p.cursors.p, s);
+    k_plan_walk_check<<<1, 1, 0, s>>>(P.overflow, reinterpret_cast<const int64_t *>(P.total), p.cand_cap, err);
+    CT_COUNT_LAUNCH();
+    // 2. each group's candidates in one range
+    CT_CHECK_CUDA(cudaMemsetAsync(p.gcount.p, 0, (size_t)G * sizeof(int32_t), s));
+    CT_CHECK_CUDA(cudaMemsetAsync(p.gfill.p, 0, (size_t)G * sizeof(int32_t), s));
+    k_plan_cand_counts<<<grid_for(p.seg_cap, 256), 256, 0, s>>>(P.nseg, p.seg_cap, P.seg_group, P.seg_count,
+                                                              p.gcount.p);
+    CT_COUNT_LAUNCH();
+    exclusive_scan_i32_to_i64_into(p.gcount.p, p.gbegin.p, G, p.gbegin.p + G, p.sums.p, s);
+    k_plan_cand_copy<<<grid_for(p.seg_cap * 32, 256), 256, 0, s>>>(P.nseg, p.seg_cap, P.seg_group, P.seg_begin,
+                                                                  P.seg_count, p.gbegin.p, p.gfill.p, P.data,
+                                                                  p.gcand.p, p.cand_cap, err);
+    CT_COUNT_LAUNCH();
+    // 3. count pass: one persistent launch producing and consuming the work queue
+    CT_CHECK_CUDA(cudaMemsetAsync(p.qctr.p, 0, 4 * sizeof(int32_t), s));
+    CT_CHECK_CUDA(cudaMemsetAsync(p.ready.p, 0, (size_t)p.item_cap * sizeof(int32_t), s));
+    CT_CHECK_CUDA(cudaMemsetAsync(p.deg.p, 0, (size_t)(n + 1) * sizeof(int32_t), s));
+    Queue Q{p.qctr.p, p.qctr.p + 1, p.qctr.p + 2, p.qctr.p + 3, p.ready.p, p.igroup.p, p.ibeg.p, p.iend.p,
+            p.order.p, p.gcount.p, p.gbegin.p, p.ctl.p, p.cand_cap, G, (int)p.item_cap, 1};
+    k_leaf_l2_queue<false><<<p.leaf_grid, LEAF_T, kLeafSmem, s>>>(V, Q, p.gcand.p, p.emask.p, p.deg.p, nullptr,
+                                                                  nullptr, nullptr, nullptr, st, err);
+    CT_COUNT_LAUNCH();
+    // 4. scan; a run above the plan's edge capacity empties every row
+    exclusive_scan_i32_to_i64_into(p.deg.p, p.row_ptr.p, n + 1, nullptr, p.sums.p, s);
+    k_plan_nnz_check<<<1, 1, 0, s>>>(p.row_ptr.p, n, p.nnz_cap, p.empty_flag.p, err);
+    CT_COUNT_LAUNCH();
+    k_plan_empty_rows<<<grid_for(n + 1, 256), 256, 0, s>>>(n + 1, p.empty_flag.p, p.row_ptr.p);
+    CT_COUNT_LAUNCH();
+    // 5. emit pass over the complete queue
+    CT_CHECK_CUDA(cudaMemsetAsync(p.qctr.p + 2, 0, sizeof(int32_t), s));
+    CT_CHECK_CUDA(cudaMemsetAsync(p.rowcur.p, 0, (size_t)(n + 1) * sizeof(int32_t), s));
+    Q.produce = 0;
+    k_leaf_l2_queue<true><<<p.leaf_grid, LEAF_T, kLeafSmem, s>>>(V, Q, p.gcand.p, p.emask.p, p.deg.p, p.row_ptr.p,
+                                                                 p.rowcur.p, p.col.p, p.dist.p, st, err);
+    CT_COUNT_LAUNCH();
+    k_check_rows<<<grid_for(n, 256), 256, 0, s>>>(n, p.row_ptr.p, p.rowcur.p, err);
+    CT_COUNT_LAUNCH();
+    // 6. rows sorted in place (rows above the in-place sorts' length are reported)
+    CT_CHECK_CUDA(cudaMemsetAsync(p.sort_counts.p, 0, kSortClasses * sizeof(int32_t), s));
+    k_row_classes<<<grid_for(n, 256), 256, 0, s>>>(p.row_ptr.p, n, p.sort_lists.p, p.sort_counts.p);
+    CT_COUNT_LAUNCH();
+    k_plan_sort_check<<<1, 1, 0, s>>>(p.sort_counts.p, err);
+    CT_COUNT_LAUNCH();
+    k_sort_small<<<grid_for(n * 32, 256), 256, 0, s>>>(p.sort_lists.p, p.sort_counts.p, p.row_ptr.p, p.col.p,
+                                                       p.dist.p);
+    CT_COUNT_LAUNCH();
+    auto merge = [&](int cls, auto kern, int P_, int cap) {
+        const int smem = 16 * cap;
+        const int per_sm = std::min(2048 / P_, (200 * 1024) / smem);
+        kern<<<num_sms() * per_sm, P_, smem, s>>>(p.sort_lists.p + (int64_t)cls * n, p.sort_counts.p + cls,
+                                                   p.row_ptr.p, p.col.p, p.dist.p);
+        CT_COUNT_LAUNCH();
+    };
+    merge(1, k_sort_merge<64, 128>, 64, 128);
+    merge(2, k_sort_merge<128, 512>, 128, 512);
+    merge(3, k_sort_merge<128, 1024>, 128, 1024);
+    merge(4, k_sort_merge<512, SORT_MID>, 512, SORT_MID);
+    // 7. each cloud's row offsets relative to its first row
+    for (int c = 0; c < p.C; ++c) {
+        const int64_t nc1 = p.trees[c]->n + 1;
+        k_rel_rows<<<grid_for(nc1, 256), 256, 0, s>>>(nc1, p.row_ptr.p + V.rbase[c], p.rel.p + V.rbase[c] + c);
+        CT_COUNT_LAUNCH();
+    }
+    CT_LAUNCH_CHECK();
+}
+}  // namespace
+
+PlanImpl *plan_create(int C, const ct_tree *const *trees, const QParams *qps, int precision,
+                      const ct_predictor *pred, float margin, bool use_graph, cudaStream_t s) {
+    if (C < 1 || C > kMaxClouds) CT_FAIL(CT_EINVAL, "between 1 and %d clouds per plan", kMaxClouds);
+    std::unique_ptr<PlanImpl> pp(new PlanImpl());
+    PlanImpl &p = *pp;
+    p.C = C;
+    p.s0 = s;
+    std::memset(&p.V, 0, sizeof(p.V));
+    p.V.nc = C;
+    int max_depth = 0, min_len = kItem;
+    for (int c = 0; c < C; ++c) {
+        const ct_tree *t = trees[c];
+        if (t->metric != CT_L2_F32) CT_FAIL(CT_EINVAL, "plans take L2 trees only");
+        p.trees.push_back(t);
+        p.V.tv[c] = view_of(t);
+        p.V.qp[c] = qps[c];
+        p.V.use_tc[c] = 0;  // the persistent launch runs the FP32 tiles
+        const int len = precision == 2 ? leaf_choice(t, 2).item_len : kItem;
+        p.V.item_len[c] = (int16_t)len;
+        min_len = std::min(min_len, len);
+        p.V.gbase[c + 1] = p.V.gbase[c] + t->n_groups;
+        p.V.rbase[c + 1] = p.V.rbase[c] + t->n;
+        p.max_dp = std::max(p.max_dp, t->dp);
+        max_depth = std::max(max_depth, t->depth);
+    }
+    if (p.V.rbase[C] >= 0x7fffffffLL) CT_FAIL(CT_EOVERFLOW, "a plan above 2^31 points");
+    p.n = p.V.rbase[C];
+    p.G = p.V.gbase[C];
+    const int64_t n = p.n;
+    const int G = p.G;
+    // sizing query (the batch's own exact query, FP32 tiles)
+    std::vector<QueryOut> outs((size_t)C);
+    query_multi(C, trees, qps, s, outs.data(), 0, pred, nullptr);
+    const int64_t n_cand = outs[0].stats.candidates;
+    int64_t nnz = 0, longest = 0;
+    {
+        std::vector<int64_t> hrp;
+        for (int c = 0; c < C; ++c) {
+            nnz += outs[c].nnz;
+            hrp.resize((size_t)trees[c]->n + 1);
+            to_host(hrp.data(), outs[c].row_ptr, hrp.size(), s);
+            for (size_t i = 0; i + 1 < hrp.size(); ++i) longest = std::max(longest, hrp[i + 1] - hrp[i]);
+        }
+    }
+    for (auto &o : outs) {
+        if (!o.shared) {
+            dfree(o.row_ptr, s);
+            dfree(o.col, s);
+            dfree(o.dist, s);
+        }
+        o = QueryOut();
+    }
+    if (longest > SORT_MID)
+        CT_FAIL(CT_EUNSUPPORTED, "a row of %lld entries: plans sort rows of at most %d in place", (long long)longest,
+                SORT_MID);
+    const double m = std::max(0.0, (double)margin);
+    p.tl = trav_launch_config(true, G);
+    p.cap_stack = 32 * (max_depth + 2);
+    p.spill_cap = (int)std::min<int64_t>(std::max<int64_t>(4 * (int64_t)G, 1 << 16), 1 << 20);
+    p.cand_cap = (int64_t)std::ceil((double)n_cand * (1.0 + m)) + 4096;
+    p.pool_cap = p.cand_cap + (int64_t)(p.tl.warps + 1) * POOL_CHUNK;
+    p.seg_cap = G + (int64_t)TRAV_ROUNDS * p.spill_cap + p.pool_cap / POOL_CHUNK + p.tl.warps + 16;
+    p.item_cap = std::min<int64_t>(G + p.cand_cap / min_len + 1, 0x7fffffff);
+    p.nnz_cap = (int64_t)std::ceil((double)nnz * (1.0 + m)) + 4096;
+    // walk order: the predictor's (groups by decreasing predicted walk
+    // length), else decreasing radius relative to eps
+    p.order = DBuf<int32_t>(G ? G : 1, s);
+    if (G) {
+        LearnedPlan lp;
+        if (pred) learned_plan(pred, C, trees, qps, p.V.rbase, p.V.gbase, s, lp);
+        if (lp.group_order.p) {
+            CT_CHECK_CUDA(cudaMemcpyAsync(p.order.p, lp.group_order.p, (size_t)G * sizeof(int32_t),
+                                          cudaMemcpyDeviceToDevice, s));
+        } else {
+            DBuf<uint32_t> k1(G, s), v1(G, s), k2(G, s), v2(G, s);
+            for (int c = 0; c < C; ++c) {
+                const int Gc = trees[c]->n_groups;
+                if (!Gc) continue;
+                k_radius_keys<<<grid_for(Gc, 256), 256, 0, s>>>(Gc, trees[c]->group_radius,
+                                                                (float)(1.0 / std::max(qps[c].eps64, 1e-30)),
+                                                                p.V.gbase[c], k1.p, v1.p);
+                CT_COUNT_LAUNCH();
+            }
+            radix_sort_pairs(k1.p, v1.p, k2.p, v2.p, G, 32, s);
+            CT_CHECK_CUDA(cudaMemcpyAsync(p.order.p, v1.p, (size_t)G * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    // buffers
+    p.st = DBuf<unsigned long long>(ST_N, s);
+    p.ctr = DBuf<unsigned long long>(4, s);
+    p.next_group = DBuf<int32_t>(1, s);
+    p.spill_cnt = DBuf<int32_t>(2, s);
+    p.ctl = DBuf<int32_t>(2, s);
+    p.qctr = DBuf<int32_t>(4, s);
+    p.empty_flag = DBuf<int32_t>(1, s);
+    p.stacks = DBuf<int2>((size_t)p.tl.warps * p.cap_stack, s);
+    p.spill_a = DBuf<int4>(p.spill_cap, s);
+    p.spill_b = DBuf<int4>(p.spill_cap, s);
+    p.cursors = DBuf<longlong2>(p.tl.warps, s);
+    p.pool = DBuf<uint32_t>(p.pool_cap, s);
+    p.seg_group = DBuf<int32_t>(p.seg_cap, s);
+    p.seg_count = DBuf<int32_t>(p.seg_cap, s);
+    p.seg_begin = DBuf<int64_t>(p.seg_cap, s);
+    p.gcand = DBuf<uint32_t>(p.cand_cap, s);
+    p.emask = DBuf<uint32_t>(p.cand_cap, s);
+    p.gcount = DBuf<int32_t>(G ? G : 1, s);
+    p.gfill = DBuf<int32_t>(G ? G : 1, s);
+    p.gbegin = DBuf<int64_t>(G + 1, s);
+    p.sums = DBuf<int64_t>(std::max<int64_t>(scan_scratch_entries(std::max<int64_t>(n + 1, G)), 1), s);
+    p.ready = DBuf<int32_t>(p.item_cap, s);
+    p.igroup = DBuf<int32_t>(p.item_cap, s);
+    p.ibeg = DBuf<int64_t>(p.item_cap, s);
+    p.iend = DBuf<int64_t>(p.item_cap, s);
+    p.deg = DBuf<int32_t>(n + 1, s);
+    p.rowcur = DBuf<int32_t>(n + 1, s);
+    p.row_ptr = DBuf<int64_t>(n + 1, s);
+    p.rel = DBuf<int64_t>(n + C, s);
+    p.col = DBuf<int32_t>(p.nnz_cap, s);
+    p.dist = DBuf<float>(p.nnz_cap, s);
+    p.sort_lists = DBuf<int32_t>((size_t)kSortClasses * (n ? n : 1), s);
+    p.sort_counts = DBuf<int32_t>(kSortClasses, s);
+    const int32_t ctl0[2] = {0, 1 << 20};  // about a second of polls
+    CT_CHECK_CUDA(cudaMemcpyAsync(p.ctl.p, ctl0, sizeof(ctl0), cudaMemcpyHostToDevice, s));
+    // persistent grid: the FP32 tiles' resident CTAs on every SM
+    leaf_l2_prepare();
+    {
+        int per_sm = 0;
+        CT_CHECK_CUDA(cudaFuncSetAttribute(k_leaf_l2_queue<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kLeafSmem));
+        CT_CHECK_CUDA(cudaFuncSetAttribute(k_leaf_l2_queue<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kLeafSmem));
+        CT_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_l2_queue<false>, LEAF_T,
+                                                                    kLeafSmem));
+        p.leaf_grid = std::max(1, num_sms() * std::max(per_sm, 1));
+    }
+    {
+        const size_t tsm = (size_t)TRAV_WARPS * p.max_dp * sizeof(float);
+        if (tsm > 48 * 1024)
+            CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+        auto attr = [&](auto kern, int cap) {
+            if (16 * cap > 48 * 1024)
+                CT_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * cap));
+        };
+        attr(k_sort_merge<64, 128>, 128);
+        attr(k_sort_merge<128, 512>, 512);
+        attr(k_sort_merge<128, 1024>, 1024);
+        attr(k_sort_merge<512, SORT_MID>, SORT_MID);
+    }
+    CT_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (use_graph) {
+        // captured on a private stream (the caller's may be the legacy
+        // default stream, which cannot be captured); launched on any stream
+        cudaStream_t cs = nullptr;
+        CT_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        struct StreamGuard {
+            cudaStream_t s;
+            ~StreamGuard() { cudaStreamDestroy(s); }
+        } sg{cs};
+        CT_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+        try {
+            plan_enqueue(p, cs);
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(cs, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            throw;
+        }
+        CT_CHECK_CUDA(cudaStreamEndCapture(cs, &p.graph));
+        CT_CHECK_CUDA(cudaGraphInstantiate(&p.exec, p.graph, 0));
+    }
+    return pp.release();
+}
+
+void plan_launch(PlanImpl *p, cudaStream_t s) {
+    if (p->exec)
+        CT_CHECK_CUDA(cudaGraphLaunch(p->exec, s));
+    else
+        plan_enqueue(*p, s);
+}
+
+void plan_set_wait(PlanImpl *p, int withhold, int max_polls) {
+    const int32_t v[2] = {withhold ? 1 : 0, max_polls};
+    CT_CHECK_CUDA(cudaDeviceSynchronize());  // no run of the plan is in flight
+    CT_CHECK_CUDA(cudaMemcpy(p->ctl.p, v, sizeof(v), cudaMemcpyHostToDevice));
+}
+
+int plan_clouds(const PlanImpl *p) { return p->C; }
+int64_t plan_rows(const PlanImpl *p, int c) { return p->trees[c]->n; }
+
+// Status of the last run (synchronises `s`): CT_OK and the clouds' CSR views
+// into the plan's buffers, or the failure.
+ct_status plan_result(PlanImpl *p, cudaStream_t s, QueryOut *outs) {
+    unsigned long long hs[ST_N];
+    to_host(hs, p->st.p, ST_N, s);
+    const int32_t e = (int32_t)hs[ST_ERR];
+    if (e & Q_ERR_TIMEOUT) {
+        set_error("a work-queue wait of the plan's leaf stage gave up (its producer never published)");
+        return CT_ETIMEOUT;
+    }
+    if (e & Q_ERR_OVERFLOW) {
+        set_error("the run outgrew the plan's capacities (candidates, work items, edges or row length); "
+                  "create a new plan");
+        return CT_EOVERFLOW;
+    }
+    if (e) {
+        set_error("internal consistency check failed in the plan's run (code %d)", e);
+        return CT_ECUDA;
+    }
+    std::vector<int64_t> hb((size_t)p->C + 1);
+    for (int c = 0; c <= p->C; ++c) to_host_async(&hb[c], p->row_ptr.p + p->V.rbase[c], 1, s);
+    CT_CHECK_CUDA(cudaStreamSynchronize(s));
+    auto blocks = std::make_shared<SharedBlocks>(s);  // views: the plan keeps the memory
+    for (int c = 0; c < p->C; ++c) {
+        QueryOut &q = outs[c];
+        q.row_ptr = p->rel.p + p->V.rbase[c] + c;
+        q.col = p->col.p + hb[c];
+        q.dist = p->dist.p + hb[c];
+        q.nnz = hb[c + 1] - hb[c];
+        q.stats = ct_query_stats{};
+        q.stats.traversal_evals = (int64_t)hs[ST_TRAV];
+        q.stats.leaf_pairs = (int64_t)hs[ST_PAIRS];
+        q.stats.guard_fp64 = (int64_t)hs[ST_GUARD];
+        q.stats.emit_pairs = (int64_t)hs[ST_EMIT];
+        q.stats.leaf_rows = (int64_t)hs[ST_ROWS];
+        q.stats.guard_band = (int64_t)hs[ST_BAND];
+        q.shared = blocks;
+    }
+    return CT_OK;
+}
+
+void plan_free(PlanImpl *p) {
+    if (!p) return;
+    cudaStream_t s = p->s0;
+    cudaStreamSynchronize(s);
+    delete p;
+    cudaStreamSynchronize(s);
 }
 
 }  // namespace ct

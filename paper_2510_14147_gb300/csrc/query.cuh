@@ -91,6 +91,19 @@ void tune_reset();
 void learned_plan(const ct_predictor *P, int C, const ct_tree *const *trees, const QParams *qps,
                   const int64_t *rbase, const int32_t *gbase, cudaStream_t s, LearnedPlan &lp);
 
+// Plans: a batch of L2 clouds with every buffer allocated up front, so that a
+// run (one graph-capturable sequence of launches, the leaf stage one
+// persistent launch over a device work queue) needs no host read-back.
+struct PlanImpl;
+PlanImpl *plan_create(int C, const ct_tree *const *trees, const QParams *qps, int precision,
+                      const ct_predictor *pred, float margin, bool use_graph, cudaStream_t s);
+void plan_launch(PlanImpl *p, cudaStream_t s);
+void plan_set_wait(PlanImpl *p, int withhold, int max_polls);
+int plan_clouds(const PlanImpl *p);
+int64_t plan_rows(const PlanImpl *p, int c);
+ct_status plan_result(PlanImpl *p, cudaStream_t s, QueryOut *outs);
+void plan_free(PlanImpl *p);
+
 // Sorts every CSR row by column, moving dist along.
 void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int64_t nnz,
                cudaStream_t s);

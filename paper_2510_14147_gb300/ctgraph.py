@@ -153,6 +153,17 @@ def _load():
         lib.eps_graph_query_sweep.restype = C.c_int
         lib.eps_graph_query_sweep.argtypes = [C.c_void_p, C.c_int32, P(C.c_double), P(ct_query_opts), C.c_void_p,
                                               P(ct_csr)]
+        lib.ct_plan_create.restype = C.c_int
+        lib.ct_plan_create.argtypes = [C.c_int32, P(C.c_void_p), P(C.c_double), P(ct_query_opts), C.c_float,
+                                       C.c_int32, C.c_void_p, P(C.c_void_p)]
+        lib.ct_plan_launch.restype = C.c_int
+        lib.ct_plan_launch.argtypes = [C.c_void_p, C.c_void_p]
+        lib.ct_plan_result.restype = C.c_int
+        lib.ct_plan_result.argtypes = [C.c_void_p, C.c_void_p, P(ct_csr)]
+        lib.ct_plan_set_wait.restype = C.c_int
+        lib.ct_plan_set_wait.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
+        lib.ct_plan_free.restype = None
+        lib.ct_plan_free.argtypes = [C.c_void_p]
         lib.ct_tree_save.restype = C.c_int
         lib.ct_tree_save.argtypes = [C.c_void_p, C.c_char_p]
         lib.ct_tree_load.restype = C.c_int
@@ -349,6 +360,56 @@ def eps_graph_query_sweep(tree: Tree, eps, precision: int = 0, use_predictor: bo
     o = _opts(precision, use_predictor, include_self, predictor)
     _check(lib.eps_graph_query_sweep(tree.handle, k, ea, C.byref(o), C.c_void_p(_stream(stream)), outs))
     return [CSR(outs[i]) for i in range(k)]
+
+
+class Plan:
+    """Owning handle of a plan: a batch of L2 clouds with its buffers allocated
+    once, run by ct_plan_launch (a CUDA-graph replay with use_graph)."""
+
+    def __init__(self, handle: int, n_clouds: int, trees):
+        self.handle = C.c_void_p(handle)
+        self.n_clouds = n_clouds
+        self._trees = list(trees)   # the plan borrows them
+
+    def free(self):
+        if self.handle and self.handle.value:
+            _load().ct_plan_free(self.handle)
+            self.handle = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def ct_plan_create(trees, eps, precision: int = 0, use_predictor: bool = False, include_self: bool = False,
+                   predictor=None, margin: float = 0.1, use_graph: bool = True, stream=None) -> Plan:
+    lib = _load()
+    k = len(trees)
+    arr = (C.c_void_p * max(k, 1))(*[t.handle.value for t in trees])
+    ea = (C.c_double * max(k, 1))(*[float(e) for e in eps])
+    o = _opts(precision, use_predictor, include_self, predictor)
+    h = C.c_void_p()
+    _check(lib.ct_plan_create(k, arr, ea, C.byref(o), float(margin), int(bool(use_graph)),
+                              C.c_void_p(_stream(stream)), C.byref(h)))
+    return Plan(h.value, k, trees)
+
+
+def ct_plan_launch(plan: Plan, stream=None):
+    _check(_load().ct_plan_launch(plan.handle, C.c_void_p(_stream(stream))))
+
+
+def ct_plan_result(plan: Plan, stream=None):
+    """The CSRs of the last run (views into the plan's buffers, valid until the
+    next launch); raises CtError with CT_EOVERFLOW / CT_ETIMEOUT on failure."""
+    outs = (ct_csr * max(plan.n_clouds, 1))()
+    _check(_load().ct_plan_result(plan.handle, C.c_void_p(_stream(stream)), outs))
+    return [CSR(outs[i]) for i in range(plan.n_clouds)]
+
+
+def ct_plan_set_wait(plan: Plan, withhold_producers: bool = False, max_polls: int = 1 << 20):
+    _check(_load().ct_plan_set_wait(plan.handle, int(bool(withhold_producers)), int(max_polls)))
 
 
 def ct_tree_save(tree: Tree, path: str):
