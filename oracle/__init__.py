@@ -13,6 +13,8 @@ Functions and the paper passages they follow:
                            of squared differences compared with fl(eps*eps)
   lev / lev_banded      -- edit distance (named in Sec. I and Sec. III), unit
                            costs; banded cutoff after Ukkonen
+  hamming               -- Hamming distance of bit strings (the binary
+                           datasets of Sec. V-A, Table I), bit by bit
   build_tree            -- Algorithm 1 (SplitVertex) + Algorithm 2 (BuildLevel)
   tree_query            -- Algorithm 3 (stack query with vertex-triple radii)
   check_tree            -- cover-tree invariants (Sec. III) + radius bound
@@ -33,7 +35,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-ORC_L2, ORC_LEV = 0, 1
+ORC_L2, ORC_LEV, ORC_HAM = 0, 1, 2
 LEVEL_NONE = -(2 ** 31)   # level of a radius-0 vertex
 
 
@@ -81,6 +83,8 @@ def _load():
             lib.orc_sq_l2.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
             lib.orc_lev_full.restype = C.c_int32
             lib.orc_lev_full.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32]
+            lib.orc_hamming.restype = C.c_int32
+            lib.orc_hamming.argtypes = [C.c_void_p, C.c_void_p, C.c_int32]
             lib.orc_lev_banded.restype = C.c_int32
             lib.orc_lev_banded.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32]
             lib.orc_brute_force.restype = C.POINTER(_Csr)
@@ -109,13 +113,25 @@ def num_threads() -> int:
 
 
 class Space:
-    """A point set with its metric: L2 over fp32 rows or Levenshtein over uint8
-    strings.  Keeps the numpy buffers alive for the C side."""
+    """A point set with its metric: L2 over fp32 rows, Levenshtein over uint8
+    strings, or Hamming over bit rows (``bits=(rows, dim)``: uint8 array of
+    shape (n, ceil(dim/8)), bit j of a row = bit j % 8 of its byte j // 8).
+    Keeps the numpy buffers alive for the C side."""
 
-    def __init__(self, points=None, strings=None):
-        if (points is None) == (strings is None):
-            raise ValueError("give exactly one of points= or strings=")
-        if points is not None:
+    def __init__(self, points=None, strings=None, bits=None):
+        if sum(a is not None for a in (points, strings, bits)) != 1:
+            raise ValueError("give exactly one of points=, strings= or bits=")
+        if bits is not None:
+            rows, dim = bits
+            rows = np.ascontiguousarray(rows, dtype=np.uint8)
+            if rows.ndim != 2 or rows.shape[1] != (int(dim) + 7) // 8:
+                raise ValueError("bits rows must be (n, ceil(dim/8)) uint8")
+            keep = rows if rows.size else np.zeros((1, 1), np.uint8)
+            self.metric, self.n, self.dim = ORC_HAM, rows.shape[0], int(dim)
+            self._keep = (keep,)
+            self.c = _Space(ORC_HAM, self.n, self.dim, None, keep.ctypes.data, None)
+            self.rows = rows
+        elif points is not None:
             x = np.ascontiguousarray(points, dtype=np.float32)
             if x.ndim != 2:
                 raise ValueError("points must be (n, dim)")
@@ -143,6 +159,13 @@ def sq_l2(x, y) -> float:
     x = np.ascontiguousarray(x, dtype=np.float32)
     y = np.ascontiguousarray(y, dtype=np.float32)
     return float(_load().orc_sq_l2(x.ctypes.data, y.ctypes.data, x.size))
+
+
+def hamming(a, b, dim: int) -> int:
+    """Hamming distance of two rows of `dim` bits (uint8, ceil(dim/8) bytes)."""
+    x = np.ascontiguousarray(a, dtype=np.uint8)
+    y = np.ascontiguousarray(b, dtype=np.uint8)
+    return int(_load().orc_hamming(x.ctypes.data, y.ctypes.data, int(dim)))
 
 
 def _bytes(s):

@@ -12,6 +12,8 @@
  *     s = sum_k (x_k - y_k)^2 in FP64, ascending k, edge iff s <= fl(eps*eps);
  *   - Levenshtein distance (edit distance, named in Sec. I and Sec. III) by the
  *     Wagner-Fischer dynamic programme, and a banded cutoff variant (Ukkonen);
+ *   - Hamming distance of bit strings (the binary datasets of Sec. V-A,
+ *     Table I): the number of positions whose bits differ, bit by bit;
  *   - brute-force all-pairs ε-graph (the ground truth, Sec. III "ε-graph");
  *   - the plain cover tree: batch construction by vertex splitting
  *     (Algorithm 1, SplitVertex) applied level by level (Algorithm 2,
@@ -31,13 +33,15 @@
 
 #define ORC_L2 0
 #define ORC_LEV 1
+#define ORC_HAM 2
 
 typedef struct {
-    int32_t metric;        /* ORC_L2 or ORC_LEV */
+    int32_t metric;        /* ORC_L2, ORC_LEV or ORC_HAM */
     int64_t n;
-    int32_t dim;           /* L2 only */
+    int32_t dim;           /* L2: coordinates per point; Hamming: bits per row */
     const float *X;        /* L2: n*dim row-major */
-    const uint8_t *S;      /* Lev: concatenated strings */
+    const uint8_t *S;      /* Lev: concatenated strings; Hamming: n rows of ceil(dim/8) bytes,
+                              bit j of a row = bit (j mod 8) of its byte j/8 */
     const int64_t *off;    /* Lev: n+1 offsets */
 } orc_space;
 
@@ -119,6 +123,24 @@ int32_t orc_lev_banded(const uint8_t *a, int32_t la, const uint8_t *b, int32_t l
     return r;
 }
 
+/* Hamming distance of two rows of `dim` bits: the number of positions j <
+ * dim whose bits differ, counted one bit at a time (the definition). */
+int32_t orc_hamming(const uint8_t *a, const uint8_t *b, int32_t dim)
+{
+    int32_t d = 0;
+    for (int32_t j = 0; j < dim; ++j) {
+        int32_t x = (a[j >> 3] >> (j & 7)) & 1;
+        int32_t y = (b[j >> 3] >> (j & 7)) & 1;
+        d += x != y;
+    }
+    return d;
+}
+
+static inline const uint8_t *bits_at(const orc_space *sp, int64_t i)
+{
+    return sp->S + (size_t)i * (size_t)((sp->dim + 7) / 8);
+}
+
 static inline const uint8_t *str_at(const orc_space *sp, int64_t i, int32_t *len)
 {
     *len = (int32_t)(sp->off[i + 1] - sp->off[i]);
@@ -126,18 +148,21 @@ static inline const uint8_t *str_at(const orc_space *sp, int64_t i, int32_t *len
 }
 
 /* Metric value as a double: sqrt of the pinned sum for L2, the exact integer
- * for Levenshtein. */
+ * for Levenshtein and Hamming. */
 static double metric_dist(const orc_space *sp, int64_t i, int64_t j)
 {
     if (sp->metric == ORC_L2)
         return sqrt(orc_sq_l2(sp->X + (size_t)i * sp->dim, sp->X + (size_t)j * sp->dim, sp->dim));
+    if (sp->metric == ORC_HAM)
+        return (double)orc_hamming(bits_at(sp, i), bits_at(sp, j), sp->dim);
     int32_t la, lb;
     const uint8_t *a = str_at(sp, i, &la), *b = str_at(sp, j, &lb);
     return (double)orc_lev_full(a, la, b, lb);
 }
 
 /* Edge predicate d(i,j) <= eps, with its distance.  L2 compares the pinned sum
- * against fl(eps*eps); Levenshtein uses the banded cutoff at floor(eps). */
+ * against fl(eps*eps); Levenshtein uses the banded cutoff at floor(eps);
+ * Hamming compares the integer distance with floor(eps). */
 static int edge_pred(const orc_space *sp, int64_t i, int64_t j, double eps, double eps2,
                      double *dist)
 {
@@ -145,6 +170,11 @@ static int edge_pred(const orc_space *sp, int64_t i, int64_t j, double eps, doub
         double s = orc_sq_l2(sp->X + (size_t)i * sp->dim, sp->X + (size_t)j * sp->dim, sp->dim);
         *dist = sqrt(s);
         return s <= eps2;
+    }
+    if (sp->metric == ORC_HAM) {
+        int32_t v = orc_hamming(bits_at(sp, i), bits_at(sp, j), sp->dim);
+        *dist = (double)v;
+        return (double)v <= floor(eps);
     }
     int32_t la, lb;
     const uint8_t *a = str_at(sp, i, &la), *b = str_at(sp, j, &lb);
@@ -509,6 +539,9 @@ orc_csr *orc_tree_query_rows(const orc_space *sp, const orc_tree *t, double eps,
                         if (sp->metric == ORC_L2) {
                             dv = metric_dist(sp, q, t->center[v]);
                             if (!(dv <= (t->radius[v] + eps) * (1.0 + PRUNE_SLACK))) continue;
+                        } else if (sp->metric == ORC_HAM) {
+                            dv = metric_dist(sp, q, t->center[v]);
+                            if (!(dv <= floor(t->radius[v] + eps))) continue;
                         } else {
                             int32_t la, lb;
                             const uint8_t *a = str_at(sp, q, &la);

@@ -139,6 +139,25 @@ def random_strings(n: int, min_len: int, max_len: int, alphabet: bytes = b"ACGT"
     return data.astype(np.uint8), offsets
 
 
+def binary_codes(n: int, bits: int = 256, n_centres: int = 1000, flip: float = 0.05, seed: int = 0,
+                 chunk: int = 1 << 16) -> np.ndarray:
+    """Bit strings clustered around random centres: ``n_centres`` uniform
+    random codes of ``bits`` bits; each point picks a centre uniformly at
+    random and flips each of its bits independently with probability
+    ``flip``.  Returned as uint8 rows of ceil(bits/8) bytes, bit j of a row =
+    bit j % 8 of byte j // 8, bits past ``bits`` zero."""
+    rng = _rng(seed)
+    centres = rng.random((n_centres, bits)) < 0.5
+    labels = rng.integers(0, n_centres, size=n)
+    nb = (bits + 7) // 8
+    out = np.empty((n, nb), dtype=np.uint8)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        x = centres[labels[s:e]] ^ (rng.random((e - s, bits)) < flip)
+        out[s:e] = np.packbits(x, axis=1, bitorder="little")
+    return out
+
+
 def cloud_specs(n_clouds: int = 64, seed: int = 0, min_n: int = 10_000,
                 max_n: int = 500_000, dims=(3, 16, 64), min_deg: float = 20.0,
                 max_deg: float = 300.0):
