@@ -783,6 +783,63 @@ def run_clouds(args, wl, world, rank, dist):
         for c in ref:
             c.free()
 
+    # the same batch as a plan (buffers sized once, one persistent leaf launch
+    # over a device work queue, replayed from a CUDA graph) against the batched
+    # query and the sum of the single-cloud queries, on the same trees
+    plan_info = None
+    if not args.no_plan:
+        with torch.cuda.stream(stream):
+            trees = [cg.ct_build(points=x, leaf_size=zeta, stream=stream) for x in xs]
+        opts = dict(precision=precision, use_predictor=learned, predictor=pred if learned else None, stream=stream)
+
+        def timed(fn, reps):
+            barrier()
+            a4, b4 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a4.record(stream)
+            with torch.cuda.stream(stream):
+                for _ in range(reps):
+                    fn()
+            b4.record(stream)
+            barrier()
+            return a4.elapsed_time(b4) / reps
+
+        def singles():
+            for t, e in zip(trees, eps):
+                cg.eps_graph_query(t, e, **opts).free()
+
+        def batched():
+            for c in cg.eps_graph_query_batched(trees, eps, **opts):
+                c.free()
+
+        t0 = time.perf_counter()
+        plan = cg.ct_plan_create(trees, eps, margin=0.05, use_graph=True, **opts)
+        t_plan = time.perf_counter() - t0
+        with torch.cuda.stream(stream):
+            ref = cg.eps_graph_query_batched(trees, eps, **opts)
+            cg.ct_plan_launch(plan, stream=stream)
+            outs = cg.ct_plan_result(plan, stream=stream)
+            same = all(csr_equal(x, y) for x, y in zip(outs, ref))
+            for c in ref:
+                c.free()
+        if not same:
+            raise RuntimeError("the plan's CSRs differ from the batched query's")
+        reps = max(1, min(args.steps, 3))
+        l1 = cg.ct_kernel_launches()
+        ms_plan = timed(lambda: cg.ct_plan_launch(plan, stream=stream), reps)
+        with torch.cuda.stream(stream):
+            cg.ct_plan_result(plan, stream=stream)
+        plan_launches = (cg.ct_kernel_launches() - l1) // reps
+        ms_batched = timed(batched, reps)
+        ms_singles = timed(singles, 1)
+        plan_info = {"ms_graph_replay": ms_plan, "ms_batched_query": ms_batched,
+                     "ms_sum_of_single_cloud_queries": ms_singles, "create_s": t_plan,
+                     "csr_identical_to_batched_query": bool(same),
+                     "host_launch_calls_per_replay": plan_launches,
+                     "note": "query only (trees built once outside); the plan's leaf tiles are the FP32 ones"}
+        plan.free()
+        for t in trees:
+            t.free()
+
     e2e = None
     if not args.no_e2e:
         hin = [torch.from_numpy(x).pin_memory() for x in hosts]
@@ -842,7 +899,7 @@ def run_clouds(args, wl, world, rank, dist):
             "stage_ms": dict({k: v[0] / max(v[1], 1) for k, v in prof.items()},
                              build_all=build_ms, query_batched=query_ms),
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "library": cg.library_path(), "forms": forms, "autotune": tuned}
+            "library": cg.library_path(), "forms": forms, "autotune": tuned, "plan": plan_info}
     if fit_info:
         line["learned"] = fit_info
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -870,13 +927,14 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=4000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip timing the three-radius sweep")
+    ap.add_argument("--no-plan", action="store_true", help="clouds: skip timing the plan (graph replay)")
     ap.add_argument("--fit-steps", type=int, default=1500)
     ap.add_argument("--order-radius", action="store_true",
                     help="learned forms: walk groups by radius instead of predicted walk length")
     args = ap.parse_args()
     wl = I.load_workloads()[args.workload]
     if args.form is None:
-        args.form = "plain" if wl["kind"] == "clouds" else default_form(wl)
+        args.form = "auto+learned" if wl["kind"] == "clouds" else default_form(wl)
 
     if args.impl == "reference":
         return run_reference(args, wl)

@@ -49,7 +49,8 @@ typedef enum {
 
 typedef enum {
     CT_L2_F32 = 0,        /* Euclidean distance over fp32 coordinates */
-    CT_LEVENSHTEIN_U8 = 1 /* edit distance, unit costs, over byte strings */
+    CT_LEVENSHTEIN_U8 = 1, /* edit distance, unit costs, over byte strings */
+    CT_HAMMING_B1 = 2     /* Hamming distance over bit strings (the number of differing bits) */
 } ct_metric;
 
 /* A cudaStream_t, passed as an opaque pointer so this header needs no CUDA headers. */
@@ -62,6 +63,12 @@ typedef void *ct_stream;
  *                     offsets = device, n+1 int64, string i is
  *                     data[offsets[i] .. offsets[i+1]); dim ignored;
  *                     every string at most CT_MAX_STRING_LEN bytes.
+ *  CT_HAMMING_B1:     data    = device, n rows of ceil(dim/8) bytes, rows
+ *                     contiguous; bit j of a row is bit (j mod 8) of its
+ *                     byte j/8 (bits past dim are ignored); offsets = NULL;
+ *                     1 <= dim <= 4096 bits.  Distances are integers; an
+ *                     edge iff d <= floor(eps) (the binary datasets of the
+ *                     paper's Sec. V-A, Table I).
  *  n may be 0.  n must be below 2^31 - 1. */
 typedef struct {
     int32_t metric;
@@ -182,7 +189,8 @@ ct_status eps_graph_query_batched(int32_t n_clouds, const ct_tree *const *trees,
  * lengths per row-length class from ct_autotune with precision 2), then
  * takes queue slots, waiting for a slot's producer with a bounded number of
  * polls -- then the scan, the emit pass (the same persistent launch over the
- * complete queue) and the in-place row sorts.  With use_graph the run is
+ * complete queue) and the row sorts (rows above 4096 entries by one radix
+ * sort over a capacity sized like the others).  With use_graph the run is
  * captured once into a CUDA graph and every launch replays it.  A plan's leaf
  * tiles are the FP32 ones (precision 1 is taken as 0); use_predictor orders
  * the walk by predicted work; the output equals eps_graph_query_batched's.
@@ -194,8 +202,8 @@ typedef struct ct_plan ct_plan;
  * allocates them (and captures the graph when use_graph != 0).  1 <= n_clouds
  * <= 64, L2 trees on the current device.  Synchronises `stream`.
  * Errors: CT_EINVAL (NULL arguments, a bad count, margin outside [0, 100],
- * an edit-distance tree, options as eps_graph_query), CT_EUNSUPPORTED (a row
- * longer than 4096 entries: plans sort rows in place), CT_ENOMEM, CT_ECUDA. */
+ * a tree of another metric, options as eps_graph_query), CT_ENOMEM,
+ * CT_ECUDA. */
 ct_status ct_plan_create(int32_t n_clouds, const ct_tree *const *trees, const double *eps,
                          const ct_query_opts *opts, float margin, int32_t use_graph, ct_stream stream,
                          ct_plan **out);

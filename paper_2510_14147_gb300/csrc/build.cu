@@ -298,6 +298,106 @@ __global__ void __launch_bounds__(BT) k_dist_update_lev(
     if ((threadIdx.x & 31) == 0 && best) atomicMax(&hb.key[h], best);
 }
 
+// ---- Hamming distance: rows of wp 32-bit words (wp a multiple of 4),
+// compared four words at a time.
+__device__ __forceinline__ int ham_dist4(const uint4 *__restrict__ a, const uint4 *b, int nq) {
+    int d = 0;
+    for (int k = 0; k < nq; ++k) {
+        const uint4 x = a[k], y = b[k];
+        d += __popc(x.x ^ y.x) + __popc(x.y ^ y.y) + __popc(x.z ^ y.z) + __popc(x.w ^ y.w);
+    }
+    return d;
+}
+
+// Input rows of ceil(dim/8) bytes (bit j = bit j % 8 of byte j / 8) into
+// words of 32 bits (bit j = bit j % 32 of word j / 32); bits past dim cleared.
+__global__ void k_pack_bits(const uint8_t *__restrict__ src, int64_t n, int dim, int wp, uint32_t *__restrict__ dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * wp) return;
+    const int64_t r = i / wp;
+    const int w = (int)(i - r * wp);
+    const int nbytes = (dim + 7) >> 3;
+    uint32_t v = 0u;
+    for (int b = 0; b < 4; ++b) {
+        const int byte = 4 * w + b;
+        if (byte < nbytes) v |= (uint32_t)src[r * nbytes + byte] << (8 * b);
+    }
+    const int lo = 32 * w;
+    if (lo >= dim) v = 0u;
+    else if (dim - lo < 32) v &= (1u << (dim - lo)) - 1u;
+    dst[i] = v;
+}
+
+// Hamming: one thread per point against the newest centre (its row in shared
+// memory); also counts the hub's points within the split threshold.
+__global__ void __launch_bounds__(BT) k_dist_update_ham(
+    const uint32_t *__restrict__ X, int wp, const int32_t *__restrict__ ids, float *__restrict__ D,
+    int32_t *__restrict__ lab, const int32_t *__restrict__ chunk_hub, const int32_t *__restrict__ chunk_start,
+    int chunk_len, Hubs hb) {
+    extern __shared__ uint4 hcen[];
+    const int c = blockIdx.x;
+    const int h = chunk_hub[c];
+    if (hb.done[h]) return;
+    const int start = chunk_start[c];
+    const int end = min(start + chunk_len, hb.begin[h] + hb.count[h]);
+    const int nq = wp >> 2;
+    const uint4 *crow = reinterpret_cast<const uint4 *>(X + (size_t)ids[hb.cur[h]] * wp);
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) hcen[i] = crow[i];
+    __syncthreads();
+    const int lbl = hb.nc[h] - 1;
+    const float thr = hb.thr[h];
+    unsigned long long best = 0ull;
+    int cov = 0;
+    for (int base = start; base < end; base += blockDim.x) {
+        const int pos = base + threadIdx.x;
+        if (pos < end) {
+            float cur = D[pos];
+            const int d = ham_dist4(reinterpret_cast<const uint4 *>(X + (size_t)ids[pos] * wp), hcen, nq);
+            if ((float)d < cur) {
+                D[pos] = (float)d;
+                lab[pos] = lbl;
+                cur = (float)d;
+            }
+            cov += cur <= thr;
+            const unsigned long long k = pack_max_key(cur, (uint32_t)pos);
+            best = k > best ? k : best;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+        best = v > best ? v : best;
+        cov += __shfl_xor_sync(0xffffffffu, cov, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (best) atomicMax(&hb.key[h], best);
+        if (cov) atomicAdd(&hb.covered[h], cov);
+    }
+}
+
+__global__ void k_gather_bits(const uint32_t *__restrict__ Xb, int wp, const int32_t *__restrict__ perm, int64_t n,
+                              uint32_t *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nq = wp >> 2;
+    if (i >= n * nq) return;
+    const int64_t r = i / nq;
+    const int k = (int)(i - r * nq);
+    reinterpret_cast<uint4 *>(out)[r * nq + k] = reinterpret_cast<const uint4 *>(Xb)[(int64_t)perm[r] * nq + k];
+}
+
+// Radius of each query group (Hamming): warp per group, lane per point.
+__global__ void k_group_radius_ham(int ng, const int32_t *__restrict__ gbeg, const int32_t *__restrict__ gcnt,
+                                   const uint32_t *__restrict__ bits, int wp, float *__restrict__ grad) {
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (g >= ng) return;
+    const int nq = wp >> 2;
+    const uint4 *c = reinterpret_cast<const uint4 *>(bits + (size_t)gbeg[g] * wp);
+    int r = 0;
+    for (int i = lane; i < gcnt[g]; i += 32)
+        r = max(r, ham_dist4(reinterpret_cast<const uint4 *>(bits + (size_t)(gbeg[g] + i) * wp), c, nq));
+    for (int o = 16; o > 0; o >>= 1) r = max(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (lane == 0) grad[g] = (float)r;
+}
+
 // One thread per hub: decide termination or choose the next centre (its
 // position goes to cpos[begin + label] when cpos is given).
 __global__ void k_hub_step(int nh, const int32_t *__restrict__ hlist, Hubs hb, int32_t *__restrict__ active_out,
@@ -943,17 +1043,27 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
     t->stream = s;
     CT_CHECK_CUDA(cudaGetDevice(&t->device));
     const bool l2 = pts->metric == CT_L2_F32;
-    t->dim = l2 ? pts->dim : 0;
+    const bool ham = pts->metric == CT_HAMMING_B1;
+    const bool lev = pts->metric == CT_LEVENSHTEIN_U8;
+    t->dim = l2 || ham ? pts->dim : 0;
     t->dp = l2 ? (int)ceil_div(pts->dim, 4) * 4 : 0;
-    const int dp = t->dp;
+    t->wp = ham ? (int)ceil_div(pts->dim, 128) * 4 : 0;
+    const int dp = t->dp, wp = t->wp;
 
     DBuf<int32_t> err(2, s);
     CT_CHECK_CUDA(cudaMemsetAsync(err.p, 0, 2 * sizeof(int32_t), s));
 
     // padded copy of the input (original order) / string lengths
     DBuf<float> Xp;
+    DBuf<uint32_t> Xb;
     int W = 1;
-    if (l2) {
+    if (ham) {
+        Xb = DBuf<uint32_t>((size_t)(n ? n : 1) * wp, s);
+        if (n) {
+            k_pack_bits<<<grid_for(n * wp), BT, 0, s>>>((const uint8_t *)pts->data, n, pts->dim, wp, Xb.p);
+            CT_COUNT_LAUNCH();
+        }
+    } else if (l2) {
         Xp = DBuf<float>((size_t)n * dp, s);
         if (n) {
             k_pad_rows<<<grid_for(n * dp), BT, 0, s>>>((const float *)pts->data, n, pts->dim, dp, Xp.p, err.p);
@@ -970,7 +1080,7 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
     int32_t herr[2] = {0, 0};
     to_host(herr, err.p, 2, s);
     if (herr[0]) CT_FAIL(CT_EUNSUPPORTED, "coordinates must be finite with |x| <= 2^50");
-    if (!l2) {
+    if (lev) {
         if (herr[1] > CT_MAX_STRING_LEN)
             CT_FAIL(CT_EUNSUPPORTED, "string of length %d above the limit %d", herr[1], CT_MAX_STRING_LEN);
         t->max_len = herr[1];
@@ -1028,6 +1138,9 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
                     CT_UPD(1) CT_UPD(2) CT_UPD(4) CT_UPD(8) CT_UPD(16) CT_UPD(32)
 #undef CT_UPD
                 }
+            } else if (ham) {
+                k_dist_update_ham<<<(unsigned)nchunks, BT, (size_t)wp * sizeof(uint32_t), s>>>(
+                    Xb.p, wp, ids.p, D.p, lab.p, chub, cst, chunk_len, hb);
             } else {
                 const uint8_t *S = (const uint8_t *)pts->data;
                 switch (W) {
@@ -1161,7 +1274,7 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
                         for (int it = 0; it < burst; ++it) update(H, nck, cb, cs, st);
                     } else {
                         for (int it = 0; it < burst; ++it) {
-                            k_hub_step<<<grid_for(nl), BT, 0, s>>>((int)nl, hl, H, active.p, nullptr, 0);
+                            k_hub_step<<<grid_for(nl), BT, 0, s>>>((int)nl, hl, H, active.p, nullptr, ham ? 1 : 0);
                             CT_COUNT_LAUNCH();
                             update(H, nck, cb, cs, Step{});
                         }
@@ -1257,6 +1370,13 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
             CT_COUNT_LAUNCH();
         }
         Xp.reset();
+    } else if (ham) {
+        t->bits = (uint32_t *)dmalloc((size_t)(n ? n : 1) * wp * sizeof(uint32_t) + 16, s);
+        if (n) {
+            k_gather_bits<<<grid_for(n * (wp / 4)), BT, 0, s>>>(Xb.p, wp, t->perm, n, t->bits);
+            CT_COUNT_LAUNCH();
+        }
+        Xb.reset();
     } else {
         DBuf<int64_t> lens(n + 1, s);
         DBuf<int32_t> ml(1, s);
@@ -1350,7 +1470,10 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
         }
         t->group_radius = (float *)dmalloc(sizeof(float) * (size_t)(G ? G : 1), s);
         if (G) {
-            if (l2) {
+            if (ham) {
+                k_group_radius_ham<<<grid_for((int64_t)G * 32), BT, 0, s>>>(G, t->group_begin, t->group_count,
+                                                                           t->bits, wp, t->group_radius);
+            } else if (l2) {
                 k_group_radius_l2<<<grid_for((int64_t)G * 32), BT, 0, s>>>(G, t->group_begin, t->group_count, t->pts,
                                                                           dp, t->group_radius);
             } else {
@@ -1382,7 +1505,7 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
 void free_tree(ct_tree *t) {
     if (!t) return;
     cudaStream_t s = t->stream;
-    void *ptrs[] = {t->pts, t->sdata, t->soff, t->perm, t->dcen, t->node_begin, t->node_count,
+    void *ptrs[] = {t->pts, t->bits, t->sdata, t->soff, t->perm, t->dcen, t->node_begin, t->node_count,
                     t->child_begin, t->child_count, t->radius, t->level, t->node_ctr, t->leaf_ids,
                     t->parent, t->group_begin, t->group_count, t->group_radius, t->group_order};
     for (void *p : ptrs)

@@ -117,6 +117,9 @@ ct_status ct_build(const ct_points *points, const ct_build_opts *opts, ct_stream
                 CT_FAIL(CT_EOVERFLOW, "n * dim too large");
         } else if (p.metric == CT_LEVENSHTEIN_U8) {
             if (p.n > 0 && (!p.data || !p.offsets)) CT_FAIL(CT_EINVAL, "data and offsets must not be NULL");
+        } else if (p.metric == CT_HAMMING_B1) {
+            if (p.dim < 1 || p.dim > 4096) CT_FAIL(CT_EINVAL, "dim must be in [1, 4096] bits (got %d)", p.dim);
+            if (p.n > 0 && !p.data) CT_FAIL(CT_EINVAL, "data is NULL");
         } else {
             CT_FAIL(CT_EINVAL, "unknown metric %d", p.metric);
         }

@@ -167,6 +167,11 @@ struct ct_tree {
     int32_t max_len = 0;
     int64_t sbytes = 0;
 
+    // Hamming bit rows in tree order, n x wp 32-bit words (wp a multiple of
+    // 4, bits past dim zero); dim is the number of bits
+    uint32_t *bits = nullptr;
+    int32_t wp = 0;
+
     int32_t *perm = nullptr;      // position -> original id
     float *dcen = nullptr;        // position -> distance to its leaf block's centre
 

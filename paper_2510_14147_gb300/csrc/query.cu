@@ -52,11 +52,12 @@ __device__ __forceinline__ void stat_add(unsigned long long *st, int slot, unsig
 
 struct TreeView {
     const float *pts, *node_ctr, *radius, *dcen, *group_radius;
+    const uint32_t *bits;  // Hamming rows (wp words each)
     const int32_t *perm, *node_begin, *node_count, *child_begin, *child_count, *leaf_ids;
     const int32_t *group_begin, *group_count, *group_order;
     const uint8_t *sdata;
     const int64_t *soff;
-    int dp, dim, n_leaves, n_groups;
+    int dp, dim, n_leaves, n_groups, wp;
 };
 
 TreeView view_of(const ct_tree *t) {
@@ -68,6 +69,8 @@ TreeView view_of(const ct_tree *t) {
     v.group_begin = t->group_begin; v.group_count = t->group_count; v.group_radius = t->group_radius;
     v.group_order = t->group_order;
     v.n_groups = t->n_groups;
+    v.bits = t->bits;
+    v.wp = t->wp;
     return v;
 }
 
@@ -441,6 +444,63 @@ __global__ void __launch_bounds__(32) k_traverse_lev(
             const uint8_t *txt = tv.sdata + tv.soff[vp];
             const int n = (int)(tv.soff[vp + 1] - tv.soff[vp]);
             return lev_myers<W>(peq, m, txt, n, k) <= k;
+        };
+        const unsigned long long e0 = evals;
+        if (walk_group(tv, stack, cap, g, make_int2(0, 0), P, pc, evals, err, nullptr, tester) < 0) return;
+        if (gvisit) group_visits(gvisit, g, evals - e0);
+    }
+    for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
+    if (lane == 0) stat_add(st, ST_TRAV, evals);
+}
+
+// Hamming: a vertex survives iff ham(c_g, v) <= r(v) + eps + r_g (integers,
+// exact).  One warp per block, lane i tests vertex i of a step against the
+// group centre's row in shared memory.
+// Distance of a row in shared memory (a) to a row in global memory (b, read
+// through the read-only path).
+__device__ __forceinline__ int ham_rows(const uint4 *a, const uint4 *__restrict__ b, int nq) {
+    int d = 0;
+    for (int k = 0; k < nq; ++k) {
+        const uint4 x = a[k], y = __ldg(b + k);
+        d += __popc(x.x ^ y.x) + __popc(x.y ^ y.y) + __popc(x.z ^ y.z) + __popc(x.w ^ y.w);
+    }
+    return d;
+}
+// Both rows in shared memory (plain loads).
+__device__ __forceinline__ int ham_rows_smem(const uint4 *a, const uint4 *b, int nq) {
+    int d = 0;
+    for (int k = 0; k < nq; ++k) {
+        const uint4 x = a[k], y = b[k];
+        d += __popc(x.x ^ y.x) + __popc(x.y ^ y.y) + __popc(x.z ^ y.z) + __popc(x.w ^ y.w);
+    }
+    return d;
+}
+
+__global__ void __launch_bounds__(32) k_traverse_ham(
+    TreeView tv, QParams qp, Pool P, int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st,
+    int32_t *__restrict__ err, int32_t *__restrict__ next_group, int32_t *__restrict__ gvisit) {
+    __shared__ uint4 cen[32];  // up to 4096 bits
+    const int lane = threadIdx.x;
+    const int nq = tv.wp >> 2;
+    int2 *stack = stacks + (int64_t)blockIdx.x * cap;
+    unsigned long long evals = 0;
+    PoolCursor pc{-1, POOL_CHUNK, 0, 0};
+    for (;;) {
+        int gi = 0;
+        if (lane == 0) gi = atomicAdd(next_group, 1);
+        gi = __shfl_sync(0xffffffffu, gi, 0);
+        if (gi >= tv.n_groups) break;
+        const int g = tv.group_order[gi];
+        const uint4 *crow = reinterpret_cast<const uint4 *>(tv.bits + (size_t)tv.group_begin[g] * tv.wp);
+        __syncwarp();
+        for (int k = lane; k < nq; k += 32) cen[k] = crow[k];
+        __syncwarp();
+        const int add = qp.lev_k + (int)tv.group_radius[g];
+        auto tester = [&](int v, int take) {
+            if (lane >= take) return false;
+            const int k = add + (int)tv.radius[v];
+            const uint4 *row = reinterpret_cast<const uint4 *>(tv.bits + (size_t)tv.node_begin[v] * tv.wp);
+            return ham_rows(cen, row, nq) <= k;
         };
         const unsigned long long e0 = evals;
         if (walk_group(tv, stack, cap, g, make_int2(0, 0), P, pc, evals, err, nullptr, tester) < 0) return;
@@ -2150,6 +2210,103 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf_lev(
     }
 }
 
+// Hamming leaf stage: one CTA per work item; the group's query rows and each
+// tile of up to 32 candidate rows in shared memory; thread t takes pairs
+// t, t + LEAF_T, ... of the tile (query-major), integer distances.
+template <bool EMIT>
+__global__ void __launch_bounds__(LEAF_T) k_leaf_ham(
+    TreeView tv, QParams qp, Items items, uint32_t *__restrict__ cand, int32_t *__restrict__ deg,
+    const int64_t *__restrict__ row_ptr, int32_t *__restrict__ rowcur, int32_t *__restrict__ col,
+    float *__restrict__ dist, unsigned long long *__restrict__ st, int32_t *__restrict__ err, CapOut co,
+    const uint8_t *__restrict__ rowsel) {
+    extern __shared__ uint4 hsm[];  // 32 query rows, then 32 candidate rows (wp / 4 uint4 each)
+    __shared__ int cnt[32], cursor[32], sel[32];
+    __shared__ int64_t rowb[32], rowe[32];
+    __shared__ int tpos[32];
+    __shared__ int64_t tcand[32];
+    __shared__ int64_t s_ci;
+    __shared__ int s_off, s_rows;
+    __shared__ unsigned s_hit;
+    const int tid = threadIdx.x;
+    const int it = blockIdx.x;
+    if (it >= *items.count) return;
+    const int g = items.group[it];
+    const int qb = tv.group_begin[g], qn = tv.group_count[g];  // at most 32 queries
+    const int64_t c0 = items.begin[it], c1 = items.end[it];
+    const int k = qp.lev_k, nq = tv.wp >> 2;
+    uint4 *Qs = hsm, *Ps = hsm + 32 * nq;
+    unsigned long long pairs = 0;
+    if (tid < 32) {
+        cnt[tid] = 0;
+        if (tid < qn) {
+            const int o = tv.perm[qb + tid];
+            cursor[tid] = o;
+            sel[tid] = rowsel == nullptr || rowsel[o] != 0;
+            if (EMIT) {
+                rowb[tid] = row_ptr[o];
+                rowe[tid] = row_ptr[o + 1];
+            }
+        }
+    }
+    for (int i = tid; i < qn * nq; i += LEAF_T)
+        Qs[i] = reinterpret_cast<const uint4 *>(tv.bits)[(size_t)(qb + i / nq) * nq + i % nq];
+    if (tid == 0) {
+        s_ci = c0;
+        s_off = 0;
+        s_hit = 0u;
+    }
+    for (;;) {
+        __syncthreads();
+        if (tid < 32) fill_tile(tv, cand, c1, EMIT, &s_ci, &s_off, &s_rows, tpos, tcand);
+        __syncthreads();
+        const int npr = s_rows;
+        const bool last = s_ci >= c1;
+        for (int i = tid; i < npr * nq; i += LEAF_T)
+            Ps[i] = reinterpret_cast<const uint4 *>(tv.bits)[(size_t)tpos[i / nq] * nq + i % nq];
+        __syncthreads();
+        if (npr > 0) {
+            unsigned hit = 0u;
+            for (int t = tid; t < qn * npr; t += LEAF_T) {
+                const int q = t / npr, p = t - q * npr;
+                const int qpos = qb + q, ppos = tpos[p];
+                if (qpos == ppos && !qp.include_self) continue;
+                if (EMIT && !sel[q]) continue;
+                if (!EMIT) ++pairs;
+                const int d = ham_rows_smem(Qs + q * nq, Ps + p * nq, nq);
+                if (d > k) continue;
+                if (!EMIT) {
+                    hit |= 1u << p;
+                    atomicAdd(&cnt[q], 1);
+                    if (co.off) cap_put(co, cursor[q], tv.perm[ppos], (float)d);
+                } else {
+                    const int slot = atomicAdd(&rowcur[cursor[q]], 1);
+                    const int64_t at = rowb[q] + slot;
+                    if (at < rowe[q]) {
+                        col[at] = tv.perm[ppos];
+                        dist[at] = (float)d;
+                    } else {
+                        atomicOr(err, 4);
+                    }
+                }
+            }
+            if (!EMIT) {
+                if (hit) atomicOr(&s_hit, hit);
+                __syncthreads();
+                if (tid < npr && ((s_hit >> tid) & 1u)) atomicOr(&cand[tcand[tid]], FLAG);
+                __syncthreads();
+                if (tid == 0) s_hit = 0u;
+            }
+        }
+        if (last) break;
+    }
+    __syncthreads();
+    if (!EMIT && tid < qn && cnt[tid]) atomicAdd(&deg[cursor[tid]], cnt[tid]);
+    if (!EMIT) {
+        for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        if ((tid & 31) == 0) stat_add(st, ST_PAIRS, pairs);
+    }
+}
+
 __global__ void k_alphabet(const uint8_t *__restrict__ s, int64_t nbytes, int32_t *__restrict__ present) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nbytes) present[s[i]] = 1;
@@ -2363,7 +2520,7 @@ QParams make_qparams(const ct_tree *t, double eps, int include_self) {
     float ef = (float)eps;
     if ((double)ef < eps) ef = nextafterf(ef, INFINITY);
     q.eps_up = ef;
-    if (t->metric == CT_LEVENSHTEIN_U8) {
+    if (t->metric == CT_LEVENSHTEIN_U8 || t->metric == CT_HAMMING_B1) {
         double fl = floor(eps);
         q.lev_k = fl > 1e9 ? 1000000000 : (int)fl;
         return q;
@@ -2469,6 +2626,12 @@ void launch_traversal(const Views &V, int64_t G, int max_dp, int max_len, bool l
             CT_COUNT_LAUNCH();
             CT_LAUNCH_CHECK();
         }
+    } else if (V.tv[0].wp) {
+        TreeView tv = V.tv[0];
+        tv.group_order = order;
+        k_traverse_ham<<<tl.blocks, 32, 0, s>>>(tv, V.qp[0], P, stacks, cap, st, err, next_group, gvisit);
+        CT_COUNT_LAUNCH();
+        CT_LAUNCH_CHECK();
     } else {
         TreeView tv = V.tv[0];
         tv.group_order = order;
@@ -2556,7 +2719,8 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
                  int precision, const ct_predictor *pred, Probe *probe) {
     if (C < 1 || C > kMaxClouds) CT_FAIL(CT_EINVAL, "between 1 and %d clouds per batch", kMaxClouds);
     const bool l2 = trees[0]->metric == CT_L2_F32;
-    if (C > 1 && !l2) CT_FAIL(CT_EINVAL, "edit-distance trees are queried one at a time");
+    const bool ham = trees[0]->metric == CT_HAMMING_B1;
+    if (C > 1 && !l2) CT_FAIL(CT_EINVAL, "edit-distance and Hamming trees are queried one at a time");
     // the clouds' groups and rows, concatenated
     Views V;
     std::memset(&V, 0, sizeof(V));
@@ -2646,7 +2810,7 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     }
     int32_t *gvisit = probe ? probe->gvisit : nullptr;
 
-    const int W = l2 ? 1 : lev_words_for(t->max_len);
+    const int W = l2 || ham ? 1 : lev_words_for(t->max_len);
     // 1. traversal: one pass into the candidate pool (rerun once if it overflows)
     const int cap = 32 * (max_depth + 2);
     TravLaunch tl = trav_launch_config(l2, G);
@@ -2736,7 +2900,7 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     // alphabet of the strings (edit distance)
     DBuf<uint8_t> amap;
     int A = 0, qchunk = 32;
-    if (!l2) {
+    if (!l2 && !ham) {
         DBuf<int32_t> present(256, s);
         CT_CHECK_CUDA(cudaMemsetAsync(present.p, 0, 256 * sizeof(int32_t), s));
         if (t->sbytes) {
@@ -2761,7 +2925,7 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
         size_t per_q = (size_t)A * W * sizeof(uint64_t);
         qchunk = (int)std::max<size_t>(1, std::min<size_t>(32, (96 * 1024) / per_q));
     }
-    size_t lsm = l2 ? 0 : (size_t)qchunk * A * W * sizeof(uint64_t);
+    size_t lsm = l2 || ham ? 0 : (size_t)qchunk * A * W * sizeof(uint64_t);
 
     // one-pass emit: capacity region and overflow arena
     const bool capmode = pred && !probe && lp.one_pass;
@@ -2801,6 +2965,12 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
                 k_leaf_l2<true><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(V, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel);
             else
                 k_leaf_l2<false><<<(unsigned)max_items, LEAF_T, kLeafSmem, s>>>(V, items, cand_p, emask.p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel);
+        } else if (ham) {
+            const size_t hsm = (size_t)64 * (t->wp / 4) * sizeof(uint4);  // 32 query rows + 32 candidate rows
+            if (emit)
+                k_leaf_ham<true><<<(unsigned)max_items, LEAF_T, hsm, s>>>(V.tv[0], V.qp[0], items, cand_p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel);
+            else
+                k_leaf_ham<false><<<(unsigned)max_items, LEAF_T, hsm, s>>>(V.tv[0], V.qp[0], items, cand_p, deg.p, row_ptr, rowcur.p, col, dist, st.p, err, cw, rowsel);
         } else {
             switch (W) {
 #define CT_LL(WW)                                                                                                      \
@@ -3159,9 +3329,52 @@ __global__ void k_plan_empty_rows(int64_t n1, const int32_t *__restrict__ flag, 
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n1 && *flag) row_ptr[i] = 0;
 }
-// Rows longer than the in-place sorts take (the plan sorts no longer row).
-__global__ void k_plan_sort_check(const int32_t *__restrict__ counts, int32_t *__restrict__ err) {
-    if (counts[kSortClasses - 1] > 0) atomicOr(err, Q_ERR_OVERFLOW);
+// Rows longer than the in-place sorts take: their count against the plan,
+// their lengths (zero past the count), then (after a scan) their entries
+// against the plan's capacity.
+__global__ void k_plan_big_lengths(const int32_t *__restrict__ rows, const int32_t *__restrict__ nbig_dev,
+                                   int cap_rows, const int64_t *__restrict__ row_ptr, int64_t *__restrict__ lens,
+                                   int32_t *__restrict__ err) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nbig = *nbig_dev;
+    if (w == 0 && nbig > cap_rows) atomicOr(err, Q_ERR_OVERFLOW);
+    if (w < cap_rows) lens[w] = w < nbig ? row_ptr[rows[w] + 1] - row_ptr[rows[w]] : 0;
+}
+__global__ void k_plan_big_check(const int64_t *__restrict__ total, int64_t big_cap, int32_t *__restrict__ err,
+                                 int32_t *__restrict__ skip) {
+    *skip = *total > big_cap;
+    if (*skip) atomicOr(err, Q_ERR_OVERFLOW);
+}
+// Keys (rank of the row in the list, column) of the long rows, in the
+// plan's buffer (prefilled with keys that sort last).
+__global__ void k_plan_big_gather(const int32_t *__restrict__ rows, const int32_t *__restrict__ nbig_dev, int cap_rows,
+                                  const int32_t *__restrict__ skip, const int64_t *__restrict__ row_ptr,
+                                  const int64_t *__restrict__ big_off, const int32_t *__restrict__ col,
+                                  uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const int w = blockIdx.x;
+    if (w >= min(*nbig_dev, cap_rows) || *skip) return;
+    const int r = rows[w];
+    const int64_t b = row_ptr[r], len = row_ptr[r + 1] - b, o = big_off[w];
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+        keys[o + i] = ((uint64_t)w << 32) | (uint32_t)col[b + i];
+        vals[o + i] = (uint32_t)i;
+    }
+}
+__global__ void k_plan_big_apply(const int32_t *__restrict__ rows, const int32_t *__restrict__ nbig_dev, int cap_rows,
+                                 const int32_t *__restrict__ skip, const int64_t *__restrict__ row_ptr,
+                                 const int64_t *__restrict__ big_off, const uint64_t *__restrict__ keys,
+                                 const uint32_t *__restrict__ vals, int32_t *__restrict__ col,
+                                 float *__restrict__ dist, float *__restrict__ tmpd) {
+    const int w = blockIdx.x;
+    if (w >= min(*nbig_dev, cap_rows) || *skip) return;
+    const int r = rows[w];
+    const int64_t b = row_ptr[r], len = row_ptr[r + 1] - b, o = big_off[w];
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) tmpd[o + i] = dist[b + vals[o + i]];
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+        col[b + i] = (int32_t)(uint32_t)(keys[o + i] & 0xffffffffull);
+        dist[b + i] = tmpd[o + i];
+    }
 }
 
 }  // namespace
@@ -3175,6 +3388,8 @@ struct PlanImpl {
     int max_dp = 4, cap_stack = 0, spill_cap = 0, leaf_grid = 1;
     TravLaunch tl{1, 1};
     int64_t pool_cap = 0, seg_cap = 0, cand_cap = 0, item_cap = 0, nnz_cap = 0;
+    int big_rows = 0;       // rows above the in-place sorts' length the plan sorts by radix
+    int64_t big_cap = 0;    // their entries
     cudaStream_t s0 = 0;
     DBuf<int32_t> order;
     DBuf<unsigned long long> st, ctr;
@@ -3185,7 +3400,11 @@ struct PlanImpl {
     DBuf<uint32_t> pool, gcand, emask;
     DBuf<int32_t> seg_group, seg_count, col, sort_lists, sort_counts;
     DBuf<int64_t> seg_begin, gbegin, ibeg, iend, sums, row_ptr, rel;
-    DBuf<float> dist;
+    DBuf<float> dist, big_tmpd;
+    DBuf<int64_t> big_lens, big_off;
+    DBuf<uint64_t> big_k1, big_k2;
+    DBuf<uint32_t> big_v1, big_v2;
+    DBuf<int32_t> big_skip;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     ~PlanImpl() {
@@ -3255,8 +3474,6 @@ void plan_enqueue(PlanImpl &p, cudaStream_t s) {
     CT_CHECK_CUDA(cudaMemsetAsync(p.sort_counts.p, 0, kSortClasses * sizeof(int32_t), s));
     k_row_classes<<<grid_for(n, 256), 256, 0, s>>>(p.row_ptr.p, n, p.sort_lists.p, p.sort_counts.p);
     CT_COUNT_LAUNCH();
-    k_plan_sort_check<<<1, 1, 0, s>>>(p.sort_counts.p, err);
-    CT_COUNT_LAUNCH();
     k_sort_small<<<grid_for(n * 32, 256), 256, 0, s>>>(p.sort_lists.p, p.sort_counts.p, p.row_ptr.p, p.col.p,
                                                        p.dist.p);
     CT_COUNT_LAUNCH();
@@ -3271,6 +3488,26 @@ void plan_enqueue(PlanImpl &p, cudaStream_t s) {
     merge(2, k_sort_merge<128, 512>, 128, 512);
     merge(3, k_sort_merge<128, 1024>, 128, 1024);
     merge(4, k_sort_merge<512, SORT_MID>, 512, SORT_MID);
+    {  // longer rows: one radix sort of (row rank, column) keys over the plan's capacity
+        const int32_t *big = p.sort_lists.p + (int64_t)(kSortClasses - 1) * n;
+        const int32_t *nbig = p.sort_counts.p + (kSortClasses - 1);
+        k_plan_big_lengths<<<grid_for(p.big_rows, 256), 256, 0, s>>>(big, nbig, p.big_rows, p.row_ptr.p,
+                                                                     p.big_lens.p, err);
+        CT_COUNT_LAUNCH();
+        exclusive_scan_i64(p.big_lens.p, p.big_off.p, p.big_rows, p.big_off.p + p.big_rows, s);
+        k_plan_big_check<<<1, 1, 0, s>>>(p.big_off.p + p.big_rows, p.big_cap, err, p.big_skip.p);
+        CT_COUNT_LAUNCH();
+        CT_CHECK_CUDA(cudaMemsetAsync(p.big_k1.p, 0xff, (size_t)p.big_cap * sizeof(uint64_t), s));
+        k_plan_big_gather<<<p.big_rows, 256, 0, s>>>(big, nbig, p.big_rows, p.big_skip.p, p.row_ptr.p, p.big_off.p,
+                                                     p.col.p, p.big_k1.p, p.big_v1.p);
+        CT_COUNT_LAUNCH();
+        int bits = 32;
+        while ((int64_t(1) << (bits - 32)) < p.big_rows) ++bits;
+        radix_sort_pairs64(p.big_k1.p, p.big_v1.p, p.big_k2.p, p.big_v2.p, p.big_cap, bits, s);
+        k_plan_big_apply<<<p.big_rows, 256, 0, s>>>(big, nbig, p.big_rows, p.big_skip.p, p.row_ptr.p, p.big_off.p,
+                                                    p.big_k1.p, p.big_v1.p, p.col.p, p.dist.p, p.big_tmpd.p);
+        CT_COUNT_LAUNCH();
+    }
     // 7. each cloud's row offsets relative to its first row
     for (int c = 0; c < p.C; ++c) {
         const int64_t nc1 = p.trees[c]->n + 1;
@@ -3315,14 +3552,20 @@ PlanImpl *plan_create(int C, const ct_tree *const *trees, const QParams *qps, in
     std::vector<QueryOut> outs((size_t)C);
     query_multi(C, trees, qps, s, outs.data(), 0, pred, nullptr);
     const int64_t n_cand = outs[0].stats.candidates;
-    int64_t nnz = 0, longest = 0;
+    int64_t nnz = 0, nbig = 0, big_entries = 0;
     {
         std::vector<int64_t> hrp;
         for (int c = 0; c < C; ++c) {
             nnz += outs[c].nnz;
             hrp.resize((size_t)trees[c]->n + 1);
             to_host(hrp.data(), outs[c].row_ptr, hrp.size(), s);
-            for (size_t i = 0; i + 1 < hrp.size(); ++i) longest = std::max(longest, hrp[i + 1] - hrp[i]);
+            for (size_t i = 0; i + 1 < hrp.size(); ++i) {
+                const int64_t len = hrp[i + 1] - hrp[i];
+                if (len > SORT_MID) {
+                    ++nbig;
+                    big_entries += len;
+                }
+            }
         }
     }
     for (auto &o : outs) {
@@ -3333,10 +3576,9 @@ PlanImpl *plan_create(int C, const ct_tree *const *trees, const QParams *qps, in
         }
         o = QueryOut();
     }
-    if (longest > SORT_MID)
-        CT_FAIL(CT_EUNSUPPORTED, "a row of %lld entries: plans sort rows of at most %d in place", (long long)longest,
-                SORT_MID);
     const double m = std::max(0.0, (double)margin);
+    p.big_rows = (int)std::min<int64_t>((int64_t)std::ceil((double)nbig * (1.0 + m)) + 16, 0x7fffffff);
+    p.big_cap = (int64_t)std::ceil((double)big_entries * (1.0 + m)) + 4096;
     p.tl = trav_launch_config(true, G);
     p.cap_stack = 32 * (max_depth + 2);
     p.spill_cap = (int)std::min<int64_t>(std::max<int64_t>(4 * (int64_t)G, 1 << 16), 1 << 20);
@@ -3402,6 +3644,14 @@ PlanImpl *plan_create(int C, const ct_tree *const *trees, const QParams *qps, in
     p.dist = DBuf<float>(p.nnz_cap, s);
     p.sort_lists = DBuf<int32_t>((size_t)kSortClasses * (n ? n : 1), s);
     p.sort_counts = DBuf<int32_t>(kSortClasses, s);
+    p.big_lens = DBuf<int64_t>(p.big_rows, s);
+    p.big_off = DBuf<int64_t>(p.big_rows + 1, s);
+    p.big_k1 = DBuf<uint64_t>(p.big_cap, s);
+    p.big_k2 = DBuf<uint64_t>(p.big_cap, s);
+    p.big_v1 = DBuf<uint32_t>(p.big_cap, s);
+    p.big_v2 = DBuf<uint32_t>(p.big_cap, s);
+    p.big_tmpd = DBuf<float>(p.big_cap, s);
+    p.big_skip = DBuf<int32_t>(1, s);
     const int32_t ctl0[2] = {0, 1 << 20};  // about a second of polls
     CT_CHECK_CUDA(cudaMemcpyAsync(p.ctl.p, ctl0, sizeof(ctl0), cudaMemcpyHostToDevice, s));
     // persistent grid: the FP32 tiles' resident CTAs on every SM

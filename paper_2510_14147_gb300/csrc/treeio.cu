@@ -53,6 +53,8 @@ std::vector<std::pair<void **, size_t>> arrays_of(ct_tree *t) {
     std::vector<std::pair<void **, size_t>> a;
     if (t->metric == CT_L2_F32) {
         a.push_back({(void **)&t->pts, n * (size_t)t->dp * sizeof(float)});
+    } else if (t->metric == CT_HAMMING_B1) {
+        a.push_back({(void **)&t->bits, n * (size_t)t->wp * sizeof(uint32_t)});
     } else {
         a.push_back({(void **)&t->sdata, (size_t)t->sbytes});
         a.push_back({(void **)&t->soff, (n + 1) * sizeof(int64_t)});
@@ -124,7 +126,7 @@ void save_tree(const ct_tree *tc, const char *path) {
     h.version = kVersion;
     h.metric = t->metric;
     h.dim = t->dim;
-    h.dp = t->dp;
+    h.dp = t->metric == CT_HAMMING_B1 ? t->wp : t->dp;  // Hamming: 32-bit words per row
     h.leaf_size = t->leaf_size;
     h.max_len = t->max_len;
     h.n = t->n;
@@ -158,11 +160,12 @@ ct_tree *load_tree(const char *path, cudaStream_t s) {
     if (fread(&h, sizeof(h), 1, f.get()) != 1) CT_FAIL(CT_EINVAL, "%s: truncated header", path);
     if (std::memcmp(h.magic, kMagic, 8) != 0) CT_FAIL(CT_EINVAL, "%s is not a tree file", path);
     if (h.version != kVersion) CT_FAIL(CT_EINVAL, "%s: version %u, expected %u", path, h.version, kVersion);
-    const bool l2 = h.metric == CT_L2_F32;
-    if ((h.metric != CT_L2_F32 && h.metric != CT_LEVENSHTEIN_U8) || h.n < 0 || h.n >= 0x7f7f7f00LL ||
+    const bool l2 = h.metric == CT_L2_F32, ham = h.metric == CT_HAMMING_B1;
+    if ((!l2 && !ham && h.metric != CT_LEVENSHTEIN_U8) || h.n < 0 || h.n >= 0x7f7f7f00LL ||
         h.n_nodes < 0 || h.n_nodes > 2 * h.n + 1 || h.n_leaves < 0 || h.n_leaves > h.n_nodes || h.n_groups < 0 ||
         h.n_groups > h.n || (l2 && (h.dp < 4 || h.dp > 4096 || h.dp % 4 || h.dim < 1 || h.dim > h.dp)) ||
-        (!l2 && (h.sbytes < 0 || h.max_len < 0 || h.max_len > CT_MAX_STRING_LEN)))
+        (ham && (h.dp < 4 || h.dp > 128 || h.dp % 4 || h.dim < 1 || h.dim > 32 * h.dp)) ||
+        (!l2 && !ham && (h.sbytes < 0 || h.max_len < 0 || h.max_len > CT_MAX_STRING_LEN)))
         CT_FAIL(CT_EINVAL, "%s: inconsistent header", path);
     Fnv sum;
     sum.add(&h, sizeof(h));
@@ -174,8 +177,9 @@ ct_tree *load_tree(const char *path, cudaStream_t s) {
     } g{new ct_tree()};
     ct_tree *t = g.t;
     t->metric = h.metric;
-    t->dim = l2 ? h.dim : 0;
+    t->dim = l2 || ham ? h.dim : 0;
     t->dp = l2 ? h.dp : 0;
+    t->wp = ham ? h.dp : 0;
     t->n = h.n;
     t->leaf_size = h.leaf_size;
     t->max_len = h.max_len;

@@ -25,7 +25,7 @@ from . import build as _buildmod
 CT_OK, CT_EINVAL, CT_ENOMEM, CT_ECUDA, CT_ETIMEOUT, CT_EOVERFLOW, CT_EUNSUPPORTED = range(7)
 STATUS_NAMES = {0: "CT_OK", 1: "CT_EINVAL", 2: "CT_ENOMEM", 3: "CT_ECUDA", 4: "CT_ETIMEOUT",
                 5: "CT_EOVERFLOW", 6: "CT_EUNSUPPORTED"}
-CT_L2_F32, CT_LEVENSHTEIN_U8 = 0, 1
+CT_L2_F32, CT_LEVENSHTEIN_U8, CT_HAMMING_B1 = 0, 1, 2
 
 _lock = threading.Lock()
 _lib = None
@@ -286,15 +286,26 @@ class CSR:
         self._owner.free()
 
 
-def ct_build(points=None, strings=None, leaf_size: int = 32, root: int = 0, stream=None) -> Tree:
+def ct_build(points=None, strings=None, bits=None, leaf_size: int = 32, root: int = 0, stream=None) -> Tree:
     """Cover-tree construction (Algorithms 1-2).  ``points``: CUDA fp32 tensor
-    (n, dim); or ``strings=(data, offsets)``: CUDA uint8 and int64 tensors."""
+    (n, dim); or ``strings=(data, offsets)``: CUDA uint8 and int64 tensors; or
+    ``bits=(rows, dim)``: CUDA uint8 tensor (n, ceil(dim/8)) of bit rows (bit j
+    = bit j % 8 of byte j // 8) under the Hamming distance."""
     import torch
     lib = _load()
-    if (points is None) == (strings is None):
-        raise ValueError("give exactly one of points= or strings=")
+    if sum(a is not None for a in (points, strings, bits)) != 1:
+        raise ValueError("give exactly one of points=, strings= or bits=")
     p = ct_points()
-    if points is not None:
+    if bits is not None:
+        rows, dim = bits
+        if not (rows.is_cuda and rows.dtype == torch.uint8 and rows.dim() == 2
+                and rows.shape[1] == (int(dim) + 7) // 8):
+            raise ValueError("bits must be (CUDA uint8 tensor (n, ceil(dim/8)), dim)")
+        rows = rows.contiguous()
+        p.metric, p.dim, p.n = CT_HAMMING_B1, int(dim), rows.shape[0]
+        p.data, p.offsets = rows.data_ptr() or None, None
+        keep = (rows,)
+    elif points is not None:
         if not (points.is_cuda and points.dtype == torch.float32 and points.dim() == 2):
             raise ValueError("points must be a CUDA float32 tensor of shape (n, dim)")
         points = points.contiguous()

@@ -148,3 +148,24 @@ def test_plan_rejects_bad_arguments():
     assert e.value.status == cg.CT_EINVAL
     st.free()
     t.free()
+
+
+def test_plan_rows_longer_than_the_in_place_sorts():
+    """A duplicate class of 5000 points makes rows of 4999 entries, above the
+    4096 the in-place sorts take: the plan sorts them by its radix pass."""
+    cg = _cg()
+    x = I.uniform_cube(9000, 3, seed=11)
+    x[:5000] = x[0]
+    y = I.gmm_embedded(3000, dim=16, intrinsic=4, n_centres=3, seed=12)
+    xs, eps = [x, y], [0.05, 1.0]
+    trees = _trees(xs)
+    plan = cg.ct_plan_create(trees, eps, use_graph=True)
+    for _ in range(2):
+        cg.ct_plan_launch(plan)
+        outs = cg.ct_plan_result(plan)
+        for xx, e, o in zip(xs, eps, outs):
+            assert_csr_matches(o.to_numpy(), oracle.brute_force(oracle.Space(points=xx), e))
+    assert int((outs[0].row_ptr[1:] - outs[0].row_ptr[:-1]).max()) > 4096
+    plan.free()
+    for t in trees:
+        t.free()
