@@ -79,7 +79,11 @@ def load_points(wl: dict) -> np.ndarray:
 
 
 def load_input(wl: dict):
-    """("points", x) for L2 workloads, ("strings", (data, offsets)) for edit distance."""
+    """("points", x) for L2 workloads, ("strings", (data, offsets)) for edit
+    distance, ("bits", (rows, bits)) for Hamming."""
+    if wl["kind"] == "bits":
+        return "bits", (I.binary_codes(wl["n"], wl["bits"], n_centres=wl["n_centres"], flip=wl["flip"],
+                                       seed=wl["seed"]), wl["bits"])
     if wl["kind"] == "dna":
         return "strings", I.dna_strings(n_seeds=wl["n_seeds"], per_seed=wl["per_seed"],
                                         seed_len=wl["seed_len"], seed=wl["seed"])
@@ -87,11 +91,15 @@ def load_input(wl: dict):
 
 
 def n_of(kind, host) -> int:
+    if kind == "bits":
+        return host[0].shape[0]
     return host.shape[0] if kind == "points" else host[1].size - 1
 
 
 def oracle_space(kind, host):
     import oracle
+    if kind == "bits":
+        return oracle.Space(bits=host)
     return oracle.Space(points=host) if kind == "points" else oracle.Space(strings=host)
 
 
@@ -222,6 +230,28 @@ def oracle_sample(kind, host, wl: dict, n_queries: int, seed: int = 7):
             "extrapolated_s": t_total}
 
 
+def oracle_rows_sample(kind, host, wl: dict, n_queries: int, seed: int = 7):
+    """The oracle's brute force (the Sec. III definition) for a random sample
+    of query rows, extrapolated to all n rows (used where the oracle's cover
+    tree would take the CPU too long to build: Hamming rows are compared bit
+    by bit, and farthest-first splits of 1000 clusters need 1000 centres per
+    pass over a million points)."""
+    import oracle
+    oracle.build()
+    sp = oracle_space(kind, host)
+    n = n_of(kind, host)
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(n, size=min(n_queries, n), replace=False))
+    t0 = time.perf_counter()
+    res = oracle.brute_rows(sp, wl["eps"], rows)
+    dt = time.perf_counter() - t0
+    scale = n / rows.size
+    return {"value": float(res["row_ptr"][-1]) * scale / (dt * scale), "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": "oracle brute force on %d random rows of %d (%.1f s), extrapolated to all "
+                                        "rows" % (rows.size, n, dt),
+            "wall_s": dt, "extrapolated_s": dt * scale}
+
+
 def oracle_clouds_sample(specs, per_cloud: int, seed: int = 7):
     """Many clouds: the oracle's brute force (the ε-graph definition, FP64)
     for a random sample of query rows of every cloud, each cloud extrapolated
@@ -255,6 +285,10 @@ def run_reference(args, wl):
     if wl["kind"] == "clouds":
         samp = lambda seed: oracle_clouds_sample(wl["specs"], args.ref_queries // 40, seed=seed)
         cfg = clouds_config(args, wl, world)
+    elif wl["kind"] == "bits":
+        kind, host = load_input(wl)
+        samp = lambda seed: oracle_rows_sample(kind, host, wl, args.ref_queries // 20, seed=seed)
+        cfg = config_of(args, wl, world)
     else:
         kind, host = load_input(wl)
         samp = lambda seed: oracle_sample(kind, host, wl, args.ref_queries, seed=seed)
@@ -272,7 +306,7 @@ def run_reference(args, wl):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / len(walls),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "int32" if wl["kind"] == "dna" else "f64", "data": "synthetic", "config": cfg,
+            "dtype": "int32" if wl["kind"] in ("dna", "bits") else "f64", "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
                              "sample": last["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -289,11 +323,20 @@ FORMS = {"plain": (0, False), "tc": (1, False), "learned": (0, True), "tc+learne
 
 
 def default_form(wl) -> str:
-    return "learned" if wl["kind"] == "dna" else "tc+learned"
+    return "learned" if wl["kind"] in ("dna", "bits") else "tc+learned"
 
 
 def config_of(args, wl, world):
     prec, learned = FORMS[args.form]
+    if wl["kind"] == "bits":
+        return {"workload": args.workload, "n": wl["n"], "bits": wl["bits"], "metric": "hamming", "eps": wl["eps"],
+                "zeta": wl.get("zeta", 32), "target_degree": wl.get("target_degree"), "form": args.form,
+                "precision": prec, "learned": learned,
+                "codes": "%d centres, bits flipped with probability %g" % (wl["n_centres"], wl["flip"]),
+                "parallelism": "replicas%d" % world if world > 1 else "single",
+                "l2": "inputs (%.0f MB) smaller than L2 (129 MB): a 256 MB buffer is written before every "
+                      "timed step" % (wl["n"] * wl["bits"] / 8e6),
+                "step": "ct_build + eps_graph_query + csr_free"}
     if wl["kind"] == "dna":
         n = wl["n_seeds"] * wl["per_seed"]
         return {"workload": args.workload, "n": n, "metric": "levenshtein", "eps": wl["eps"],
@@ -301,7 +344,8 @@ def config_of(args, wl, world):
                 "strings": "%d seeds of length %d, %d mutants each" % (wl["n_seeds"], wl["seed_len"],
                                                                        wl["per_seed"]),
                 "parallelism": "replicas%d" % world if world > 1 else "single",
-                "l2": "edit distance is compute bound (strings 5 MB); no flush",
+                "l2": "inputs (strings, 5 MB) smaller than L2 (129 MB): a 256 MB buffer is written before every "
+                      "timed step",
                 "step": "ct_build + eps_graph_query + csr_free"}
     return {"workload": args.workload, "n": wl["n"], "dim": wl["dim"], "eps": wl["eps"],
             "zeta": wl.get("zeta", 32), "target_degree": wl.get("target_degree"),
@@ -355,6 +399,19 @@ def roofline(prof: dict, st: dict, wl: dict, workload: str, peaks: dict, dim: in
                 "l2_served_bytes_per_launch": nbytes,
                 "l2_served_rule": "leaf_rows x (2 kp + 4) B (fp16 rows and norms) + recheck_fp32 x 4 dim B",
                 "recheck_fp32_pairs": st["recheck_fp32"], "dominant_stage": dom}
+    if "leaf_count" in prof and wl.get("kind") == "bits":
+        t = prof["leaf_count"][0] / prof["leaf_count"][1] / 1e3
+        words = 4 * ((wl["bits"] + 127) // 128)                   # 32-bit words per row (padded)
+        ops = st["leaf_pairs"] * float(words)                       # one population count per word
+        peak = SMS * 16 * sm_max * 1e6 / 1e12                      # T popc/s
+        ach = ops / t / 1e12
+        return {"kernel": "k_leaf_ham<count>", "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "Tpopc/s", "frac": ach / peak,
+                "traffic": profile_value("k_leaf_ham_count", workload, "dram_bytes_per_launch"),
+                "peak_note": "derived: 152 SMs x 16 32-bit population counts per clock x %.0f MHz (the "
+                             "population-count rate of the SM's integer pipe, 16 per clock)" % sm_max,
+                "ops_rule": "leaf_pairs x 32-bit words per row (%d)" % words,
+                "ops_per_launch": ops, "ms_per_launch": t * 1e3, "dominant_stage": dom}
     if "leaf_count" in prof and wl.get("kind") != "dna":
         t = prof["leaf_count"][0] / prof["leaf_count"][1] / 1e3
         peak = 2.0 * SMS * FP32_LANES * sm_max * 1e6 / 1e12
@@ -369,8 +426,7 @@ def roofline(prof: dict, st: dict, wl: dict, workload: str, peaks: dict, dim: in
                 "dominant_stage": dom}
     if "leaf_count" in prof:
         t = prof["leaf_count"][0] / prof["leaf_count"][1] / 1e3
-        words = math.ceil(mean_len / 64.0)
-        ops = st["leaf_pairs"] * 17.0 * words * mean_len          # 64-bit word operations
+        ops = st["lev_columns"] * 17.0                              # 64-bit word operations
         peak = SMS * INT32_LANES * sm_max * 1e6 / 2.0 / 1e12       # T word-ops/s
         ach = ops / t / 1e12
         return {"kernel": "k_leaf_lev<count>", "bound": "alu", "achieved": ach, "peak": peak,
@@ -378,8 +434,9 @@ def roofline(prof: dict, st: dict, wl: dict, workload: str, peaks: dict, dim: in
                 "traffic": profile_value("k_leaf_lev_count", workload, "dram_bytes_per_launch"),
                 "peak_note": "derived: 152 SMs x 64 INT32 lanes x %.0f MHz / 2 (a 64-bit word operation is "
                              "two 32-bit ones)" % sm_max,
-                "ops_rule": "leaf_pairs x 17 word-ops x ceil(mean length / 64) x mean length "
-                            "(the full bit-parallel recurrence; pairs that stop early count in full)",
+                "ops_rule": "lev_columns (text characters processed x pattern words, counted by the kernel: "
+                            "pairs that stop early count what they ran) x 17 word-ops per column",
+                "full_recurrence_ops_per_launch": st["leaf_pairs"] * 17.0 * math.ceil(mean_len / 64.0) * mean_len,
                 "ops_per_launch": ops, "ms_per_launch": t * 1e3, "dominant_stage": dom}
     return None
 
@@ -420,6 +477,10 @@ def run_single(args, wl, world, rank, dist):
     if kind == "points":
         dev = torch.from_numpy(host).cuda()
         build = lambda stream, d=None: cg.ct_build(points=dev if d is None else d, leaf_size=zeta, stream=stream)
+    elif kind == "bits":
+        dev = torch.from_numpy(host[0]).cuda()
+        build = lambda stream, d=None: cg.ct_build(bits=(dev if d is None else d, host[1]), leaf_size=zeta,
+                                                   stream=stream)
     else:
         dev = (torch.from_numpy(host[0]).cuda(), torch.from_numpy(host[1]).cuda())
         build = lambda stream, d=None: cg.ct_build(strings=dev if d is None else d, leaf_size=zeta, stream=stream)
@@ -437,6 +498,9 @@ def run_single(args, wl, world, rank, dist):
         if kf == "points":
             df = torch.from_numpy(hf).cuda()
             mk = lambda: cg.ct_build(points=df, leaf_size=zeta, stream=stream)
+        elif kf == "bits":
+            df = torch.from_numpy(hf[0]).cuda()
+            mk = lambda: cg.ct_build(bits=(df, hf[1]), leaf_size=zeta, stream=stream)
         else:
             df = (torch.from_numpy(hf[0]).cuda(), torch.from_numpy(hf[1]).cuda())
             mk = lambda: cg.ct_build(strings=df, leaf_size=zeta, stream=stream)
@@ -454,7 +518,13 @@ def run_single(args, wl, world, rank, dist):
                     "fit_steps": args.fit_steps, "final_loss": loss, "fit_s": fit_s,
                     "walk_order": "radius" if args.order_radius else "predicted walk length"}
 
+    flush = None
+    if kind in ("strings", "bits"):   # inputs smaller than L2: written over before every timed step
+        flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+
     def step(prec=precision, use_pred=learned, keep=False):
+        if flush is not None:
+            flush.fill_(1.0)
         t = build(stream)
         c = cg.eps_graph_query(t, eps, precision=prec, stream=stream, use_predictor=use_pred,
                                predictor=pred if use_pred else None)
@@ -510,7 +580,7 @@ def run_single(args, wl, world, rank, dist):
         forms = {}
         with torch.cuda.stream(stream):
             ref = step(keep=True)
-        names = ["plain", "learned"] if kind == "strings" else ["plain", "tc", "learned", "tc+learned"]
+        names = ["plain", "learned"] if kind in ("strings", "bits") else ["plain", "tc", "learned", "tc+learned"]
         for name in names:
             if name == args.form:
                 continue
@@ -592,6 +662,8 @@ def run_single(args, wl, world, rank, dist):
     if not args.no_e2e:
         if kind == "points":
             hin = [torch.from_numpy(host).pin_memory()]
+        elif kind == "bits":
+            hin = [torch.from_numpy(host[0]).pin_memory()]
         else:
             hin = [torch.from_numpy(host[0]).pin_memory(), torch.from_numpy(host[1]).pin_memory()]
         din = [torch.empty_like(h, device="cuda") for h in hin]
@@ -602,7 +674,7 @@ def run_single(args, wl, world, rank, dist):
         def e2e_step():
             for d, h in zip(din, hin):
                 d.copy_(h, non_blocking=True)
-            t = build(stream, din[0] if kind == "points" else (din[0], din[1]))
+            t = build(stream, din[0] if kind in ("points", "bits") else (din[0], din[1]))
             c = cg.eps_graph_query(t, eps, precision=precision, stream=stream,
                                    use_predictor=learned, predictor=pred)
             rp_h.copy_(c.row_ptr, non_blocking=True)
@@ -633,7 +705,7 @@ def run_single(args, wl, world, rank, dist):
     peaks = measured_peaks()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32" if kind == "strings" else "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32" if kind in ("strings", "bits") else "f32",
             "data": "synthetic", "config": config_of(args, wl, world), "nnz": nnz, "edges_undirected": nnz // 2,
             "dist_evals_per_s": (st["traversal_evals"] + st["leaf_pairs"]) * world * args.steps / (t_ms / 1e3),
             "query_stats": st, "stage_ms": stage_ms,
@@ -645,7 +717,10 @@ def run_single(args, wl, world, rank, dist):
         line["learned"] = fit_info
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = oracle_sample(kind, host, wl, args.ref_queries)
+            if kind == "bits":
+                line["cpu_baseline"] = oracle_rows_sample(kind, host, wl, args.ref_queries // 20)
+            else:
+                line["cpu_baseline"] = oracle_sample(kind, host, wl, args.ref_queries)
         except Exception as e:  # reported, never silently replaced
             line["cpu_baseline"] = {"error": str(e)}
     if rank == 0:

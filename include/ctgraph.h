@@ -105,12 +105,19 @@ typedef struct {
  *                     overflow arena, rows that overflow the arena too are
  *                     emitted again exactly.  Same output.
  *  include_self:  1 adds the pair (i, i) to every row (d(p, p) = 0 <= eps).
+ *  upper_triangle: 1 evaluates each pair of points of two different query
+ *                 groups once, from the group that comes first in tree
+ *                 order, and writes the edge into both rows (the symmetry
+ *                 d(p, q) = d(q, p) the paper's ring uses to halve its
+ *                 rounds, Sec. IV-C); pairs inside a group are evaluated
+ *                 from both ends as before.  Same output, about half the
+ *                 leaf pairs.
  *  predictor:     a ct_predictor* when use_predictor = 1, else NULL. */
 typedef struct {
     int32_t precision;
     int32_t use_predictor;
     int32_t include_self;
-    int32_t reserved;
+    int32_t upper_triangle;
     const void *predictor;
 } ct_query_opts;
 
@@ -143,6 +150,8 @@ typedef struct {
     int64_t guard_band;       /* pairs in the guard band |d - eps| <= 1e-3 eps (FP32 value); of
                                  these, only those the fp32 error bound cannot place on one side
                                  of eps go to FP64 */
+    int64_t lev_columns;      /* edit distance, count pass: text characters the bit-parallel
+                                 recurrence processed, times the pattern's 64-bit words */
 } ct_query_stats;
 
 typedef struct ct_tree ct_tree;           /* opaque, device-resident */

@@ -41,6 +41,9 @@ BASE = {
     "gmm_1m_k500": {"kind": "gmm", "n": 1_000_000, "dim": 128, "seed": 0,
                     "target_degree": 500.0, "zeta": 32,
                     "note": "same generator; sift eps=225 stand-in"},
+    "ham_1m_256": {"kind": "bits", "n": 1_000_000, "bits": 256, "n_centres": 1000, "flip": 0.05, "seed": 0,
+                   "target_degree": 70.0, "zeta": 32,
+                   "note": "1M clustered 256-bit codes (1000 centres, 5% bit flips); sift-hamming stand-in"},
     "dna_50k": {"kind": "dna", "n_seeds": 500, "per_seed": 100, "seed_len": 96,
                 "seed": 0, "eps": 8, "zeta": 32,
                 "note": "Levenshtein; 4% substitution, 0.5% insertion, 0.5% deletion per site"},
@@ -73,6 +76,25 @@ def calibrate(x: np.ndarray, target_degree: float, n_queries: int = 4096, seed: 
     return float(np.float32(math.sqrt(thr2)))
 
 
+def calibrate_bits(rows: np.ndarray, target_degree: float, n_queries: int = 1024, seed: int = 12345) -> int:
+    """Hamming workloads: the same rule on integer distances (exact popcounts
+    of the XOR of 64-bit words): eps = the ceil(k*Q)-th smallest non-self
+    distance of Q sampled queries."""
+    n = rows.shape[0]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    q = np.sort(rng.choice(n, size=min(n_queries, n), replace=False))
+    pad = (-rows.shape[1]) % 8
+    w = np.ascontiguousarray(np.pad(rows, ((0, 0), (0, pad)))).view(np.uint64)
+    rank = int(math.ceil(target_degree * q.size))
+    hist = np.zeros(rows.shape[1] * 8 + 1, np.int64)
+    for s in range(0, q.size, 16):
+        qb = q[s:s + 16]
+        d = np.bitwise_count(w[qb][:, None, :] ^ w[None, :, :]).sum(axis=2, dtype=np.int64)
+        d[np.arange(qb.size), qb] = -1                 # drop self pairs
+        hist += np.bincount(d[d >= 0].ravel(), minlength=hist.size)[:hist.size]
+    return int(np.searchsorted(np.cumsum(hist), rank))
+
+
 def main():
     import argparse
     ap = argparse.ArgumentParser()
@@ -83,8 +105,13 @@ def main():
             wl = json.load(f)
         key = args.only
         spec = dict(PROFILE_SIZE) if key == "gmm_300k_k70" else wl.get(key) or BASE[key]
-        x = I.gmm_embedded(spec["n"], dim=spec["dim"], seed=spec["seed"])
-        spec["eps"] = calibrate(x, spec["target_degree"])
+        if spec["kind"] == "bits":
+            rows = I.binary_codes(spec["n"], spec["bits"], n_centres=spec["n_centres"], flip=spec["flip"],
+                                  seed=spec["seed"])
+            spec["eps"] = calibrate_bits(rows, spec["target_degree"])
+        else:
+            x = I.gmm_embedded(spec["n"], dim=spec["dim"], seed=spec["seed"])
+            spec["eps"] = calibrate(x, spec["target_degree"])
         wl[key] = spec
         print(key, spec["eps"])
         with open(OUT, "w") as f:
@@ -95,6 +122,9 @@ def main():
     x3 = I.gmm_embedded(300_000, seed=0)
     wl["gmm_300k_k70"]["eps"] = calibrate(x3, 70.0)
     del x3
+    hb = wl["ham_1m_256"]
+    hb["eps"] = calibrate_bits(I.binary_codes(hb["n"], hb["bits"], n_centres=hb["n_centres"], flip=hb["flip"],
+                                              seed=hb["seed"]), hb["target_degree"])
     x = I.gmm_embedded(1_000_000, seed=0)
     for key in ("gmm_1m_k10", "gmm_1m_k70", "gmm_1m_k500"):
         wl[key]["eps"] = calibrate(x, wl[key]["target_degree"])

@@ -72,6 +72,7 @@ void validate_query(const ct_tree *tree, double eps, const ct_query_opts &o) {
         CT_FAIL(CT_EINVAL, "the tensor-core filter applies to L2 trees only");
     if (o.use_predictor && !o.predictor) CT_FAIL(CT_EINVAL, "use_predictor set without a predictor");
     if (o.include_self != 0 && o.include_self != 1) CT_FAIL(CT_EINVAL, "include_self must be 0 or 1");
+    if (o.upper_triangle != 0 && o.upper_triangle != 1) CT_FAIL(CT_EINVAL, "upper_triangle must be 0 or 1");
 }
 
 void fill_csr(ct_csr *out, int64_t n, ct::QueryOut &q, cudaStream_t s) {
@@ -143,6 +144,7 @@ ct_status eps_graph_query(const ct_tree *tree, double eps, const ct_query_opts *
         check_device(tree);
         ct::g_launches = 0;
         ct::QParams qp = ct::make_qparams(tree, eps, o.include_self);
+        qp.half = o.upper_triangle;
         if (o.use_predictor)
             ct::query_predicted(tree, qp, o.predictor, o.precision, s, q);
         else
@@ -174,7 +176,10 @@ ct_status eps_graph_query_sweep(const ct_tree *tree, int32_t n_eps, const double
         for (int k = 0; k < n_eps; ++k) ord[k] = k;
         std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return eps[a] > eps[b]; });
         std::vector<ct::QParams> qps((size_t)n_eps);
-        for (int k = 0; k < n_eps; ++k) qps[k] = ct::make_qparams(tree, eps[k], o.include_self);
+        for (int k = 0; k < n_eps; ++k) {
+            qps[k] = ct::make_qparams(tree, eps[k], o.include_self);
+            qps[k].half = o.upper_triangle;
+        }
         ct::g_launches = 0;
         const int top = ord[0];
         if (o.use_predictor)
@@ -219,6 +224,7 @@ ct_status ct_plan_create(int32_t n_clouds, const ct_tree *const *trees, const do
             check_device(trees[c]);
             if (trees[c]->metric != CT_L2_F32) CT_FAIL(CT_EINVAL, "plans take L2 trees only");
             qps[c] = ct::make_qparams(trees[c], eps[c], o.include_self);
+            qps[c].half = o.upper_triangle;
         }
         const ct_predictor *P = o.use_predictor ? static_cast<const ct_predictor *>(o.predictor) : nullptr;
         ct::g_launches = 0;
@@ -304,6 +310,7 @@ ct_status eps_graph_query_batched(int32_t n_clouds, const ct_tree *const *trees,
             validate_query(trees[c], eps[c], o);
             check_device(trees[c]);
             qps[c] = ct::make_qparams(trees[c], eps[c], o.include_self);
+            qps[c].half = o.upper_triangle;
         }
         ct::g_launches = 0;
         ct::query_batched(n_clouds, trees, qps.data(), &o, s, q.data());
@@ -334,6 +341,7 @@ ct_status ct_autotune(int32_t n_clouds, const ct_tree *const *trees, const doubl
             validate_query(trees[c], eps[c], o);
             check_device(trees[c]);
             qps[c] = ct::make_qparams(trees[c], eps[c], o.include_self);
+            qps[c].half = o.upper_triangle;
         }
         ct::autotune(n_clouds, trees, qps.data(), &o, (cudaStream_t)stream, choices);
     });

@@ -865,8 +865,31 @@ __device__ __forceinline__ void leaf_l2_item(
     const int kq = dp >> 2;  // float4 per row when nkc == 1
     const bool fp32_dist_ok = dp <= 128;
     const int qb = tv.group_begin[g], qn = tv.group_count[g];
+    const int qe = qb + qn;       // the group's positions: [qb, qe)
+    const bool half = qp.half != 0;
     const int64_t c0 = items.begin[it], c1 = items.end[it];
     unsigned long long pairs = 0, s1evals = 0, guard = 0, band = 0, rows_ld = 0;  // rows_ld: thread 0
+    // upper-triangle form: an edge (q, p) with p in a later group is also the
+    // edge (p, q) of p's row -- its degree (count pass, with the one-pass
+    // emit's entry) or its entry (emit pass; only a selected row when rows
+    // are emitted again)
+    auto mirror = [&](int qpos, int ppos, float d) {
+        const int64_t o = rbase + tv.perm[ppos];
+        if (!EMIT) {
+            atomicAdd(&deg[o], 1);
+            if (co.off) cap_put(co, (int)o, tv.perm[qpos], d);
+        } else {
+            if (rowsel && !rowsel[o]) return;
+            const int slot = atomicAdd(&rowcur[o], 1);
+            const int64_t at = row_ptr[o] + slot;
+            if (at < row_ptr[o + 1]) {
+                col[at] = tv.perm[qpos];
+                dist[at] = d;
+            } else {
+                atomicOr(err, 4);
+            }
+        }
+    };
 
     for (int q0 = 0; q0 < qn; q0 += 32) {
         const int nqr = min(32, qn - q0);
@@ -903,11 +926,12 @@ __device__ __forceinline__ void leaf_l2_item(
                 if (!EMIT) ++guard;
                 double s64 = sq_l2_exact(tv.pts + (size_t)(qfirst + q) * dp, tv.pts + (size_t)ppos * dp, dim);
                 if (s64 <= qp.eps2_64) {
+                    if (half && ppos >= qe) mirror(qfirst + q, ppos, (float)sqrt(s64));
                     if (!EMIT) {
                         atomicAdd(&S.qcnt[q], 1);
                         atomicOr(&S.bem[li], 1u << q);
                         if (co.off) cap_put(co, S.cursor[q], tv.perm[ppos], (float)sqrt(s64));
-                    } else {
+                    } else if ((S.selm >> q) & 1u) {
                         int slot = atomicAdd(&rowcur[S.cursor[q]], 1);
                         int64_t at = S.rowb[q] + slot;
                         if (at < S.rowe[q]) {
@@ -972,7 +996,9 @@ __device__ __forceinline__ void leaf_l2_item(
                     const int nf = S.nb_fill;
                     if (nf >= NB || ci >= c1) break;
                     const int64_t idx = ci + tid;
-                    const uint32_t m = idx < c1 ? (emask[idx] & S.selm) : 0u;
+                    // (rows emitted again in the upper-triangle form: every query, as a
+                    // selected row can be the mirror of another query's edge)
+                    const uint32_t m = idx < c1 ? (emask[idx] & (half && rowsel ? 0xffffffffu : S.selm)) : 0u;
                     const bool f = m != 0u;
                     const unsigned bal = __ballot_sync(0xffffffffu, f);
                     if (lane == 0) S.scan_tmp[warp] = __popc(bal);
@@ -1095,7 +1121,7 @@ __device__ __forceinline__ void leaf_l2_item(
                         const int qr = idx / cnt, pidx = idx - qr * cnt;
                         const int q = (int)__fns(S.bmask[lo] & qvalid, 0u, qr + 1);
                         const int qpos = qfirst + q, ppos = S.bbeg[lo] + pidx;
-                        if (qpos != ppos || qp.include_self) {
+                        if ((qpos != ppos || qp.include_self) && !(half && ppos < qb)) {
                             ++pairs;
                             const float4 *qrow = reinterpret_cast<const float4 *>(tv.pts + (size_t)qpos * dp);
                             const float sv = pair_sqdist(qrow, reinterpret_cast<const float4 *>(tv.pts + (size_t)ppos * dp),
@@ -1107,15 +1133,19 @@ __device__ __forceinline__ void leaf_l2_item(
                                 S.gq[slot] = (uint8_t)q;
                                 S.gb[slot] = (uint8_t)lo;
                             } else if (edge) {
-                                const int slot = atomicAdd(&rowcur[S.cursor[q]], 1);
-                                const int64_t at = S.rowb[q] + slot;
-                                if (at < S.rowe[q]) {
-                                    col[at] = tv.perm[ppos];
-                                    dist[at] = fp32_dist_ok ? sqrtf(sv)
-                                                            : (float)sqrt(sq_l2_exact(tv.pts + (size_t)qpos * dp,
-                                                                                      tv.pts + (size_t)ppos * dp, dim));
-                                } else {
-                                    atomicOr(err, 4);
+                                const float d = fp32_dist_ok ? sqrtf(sv)
+                                                             : (float)sqrt(sq_l2_exact(tv.pts + (size_t)qpos * dp,
+                                                                                       tv.pts + (size_t)ppos * dp, dim));
+                                if (half && ppos >= qe) mirror(qpos, ppos, d);
+                                if ((S.selm >> q) & 1u) {
+                                    const int slot = atomicAdd(&rowcur[S.cursor[q]], 1);
+                                    const int64_t at = S.rowb[q] + slot;
+                                    if (at < S.rowe[q]) {
+                                        col[at] = tv.perm[ppos];
+                                        dist[at] = d;
+                                    } else {
+                                        atomicOr(err, 4);
+                                    }
                                 }
                             }
                         }
@@ -1181,6 +1211,7 @@ __device__ __forceinline__ void leaf_l2_item(
                             const int q = (int)__fns(S.bmask[li] & qvalid, 0u, pi - S.tpre[lo] + 1);
                             const int qpos = qfirst + q, ppos = S.rpos[r];
                             if (qpos == ppos && !qp.include_self) continue;
+                            if (half && ppos < qb) continue;
                             ++pairs;
                             const float sv = pair_sqdist_smem(S.Qs + q * KS4, Pb + lo * KS4, kq);
                             const int edge = decide32(qp, sv, band);
@@ -1190,13 +1221,16 @@ __device__ __forceinline__ void leaf_l2_item(
                                 S.gq[slot] = (uint8_t)q;
                                 S.gb[slot] = (uint8_t)li;
                             } else if (edge) {
-                                const int slot = atomicAdd(&rowcur[S.cursor[q]], 1);
-                                const int64_t at = S.rowb[q] + slot;
-                                if (at < S.rowe[q]) {
-                                    col[at] = tv.perm[ppos];
-                                    dist[at] = sqrtf(sv);
-                                } else {
-                                    atomicOr(err, 4);
+                                if (half && ppos >= qe) mirror(qpos, ppos, sqrtf(sv));
+                                if ((S.selm >> q) & 1u) {
+                                    const int slot = atomicAdd(&rowcur[S.cursor[q]], 1);
+                                    const int64_t at = S.rowb[q] + slot;
+                                    if (at < S.rowe[q]) {
+                                        col[at] = tv.perm[ppos];
+                                        dist[at] = sqrtf(sv);
+                                    } else {
+                                        atomicOr(err, 4);
+                                    }
                                 }
                             }
                         }
@@ -1221,6 +1255,7 @@ __device__ __forceinline__ void leaf_l2_item(
                             if (q >= nqr || !((mask >> q) & 1u)) continue;
                             const int qpos = qfirst + q;
                             if (qpos == ppos && !qp.include_self) continue;
+                            if (half && ppos < qb) continue;
                             if (!EMIT) ++pairs;
                             const float sv = tot[i][j];
                             const int edge = decide32(qp, sv, band);
@@ -1232,22 +1267,22 @@ __device__ __forceinline__ void leaf_l2_item(
                                 continue;
                             }
                             if (!edge) continue;
+                            const bool want_d = co.off || EMIT || (half && ppos >= qe);
+                            const float d = !want_d ? 0.f
+                                            : fp32_dist_ok ? sqrtf(sv)
+                                                           : (float)sqrt(sq_l2_exact(tv.pts + (size_t)qpos * dp,
+                                                                                     tv.pts + (size_t)ppos * dp, dim));
+                            if (half && ppos >= qe) mirror(qpos, ppos, d);
                             if (!EMIT) {
                                 if (i == 0) ++cnt0; else ++cnt1;
                                 hitrow |= 1u << (4 * j + i);
-                                if (co.off)
-                                    cap_put(co, S.cursor[q], tv.perm[ppos],
-                                            fp32_dist_ok ? sqrtf(sv)
-                                                         : (float)sqrt(sq_l2_exact(tv.pts + (size_t)qpos * dp,
-                                                                                   tv.pts + (size_t)ppos * dp, dim)));
-                            } else {
+                                if (co.off) cap_put(co, S.cursor[q], tv.perm[ppos], d);
+                            } else if ((S.selm >> q) & 1u) {
                                 const int slot = atomicAdd(&rowcur[S.cursor[q]], 1);
                                 const int64_t at = S.rowb[q] + slot;
                                 if (at < S.rowe[q]) {
                                     col[at] = tv.perm[ppos];
-                                    dist[at] = fp32_dist_ok ? sqrtf(sv)
-                                                            : (float)sqrt(sq_l2_exact(tv.pts + (size_t)qpos * dp,
-                                                                                      tv.pts + (size_t)ppos * dp, dim));
+                                    dist[at] = d;
                                 } else {
                                     atomicOr(err, 4);
                                 }
@@ -1343,6 +1378,36 @@ __global__ void k_group_cand_copy(int nseg, const int32_t *__restrict__ seg_grou
     const uint32_t *src = pool + seg_begin[i];
     for (int k = lane; k < c; k += 32) gcand[base + k] = src[k];
 }
+// Upper-triangle form: each group keeps the candidate blocks that reach its
+// first position or beyond (the pairs with earlier points are evaluated by
+// their own groups); a warp per group compacts its range in place, in order.
+__global__ void k_half_cands(const __grid_constant__ Views V, int G, const int64_t *__restrict__ gbegin,
+                             int32_t *__restrict__ gcount, uint32_t *__restrict__ gcand, int64_t cap) {
+    const int gg = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (gg >= G) return;
+    const int c = cloud_of_group(V, gg);
+    if (!V.qp[c].half) return;
+    const TreeView &tv = V.tv[c];
+    const int qb = tv.group_begin[gg - V.gbase[c]];
+    const int64_t b = gbegin[gg];
+    const int n = gcount[gg];
+    if (b + n > cap) return;  // a range that was not copied (a plan's overflow, reported there)
+    int w = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        uint32_t v = 0u;
+        bool keep = false;
+        if (i < n) {
+            v = gcand[b + i];
+            keep = tv.node_begin[v] + tv.node_count[v] > qb;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);  // every lane has read before any writes
+        if (keep) gcand[b + w + __popc(m & lanemask_lt())] = v;
+        w += __popc(m);
+    }
+    if (lane == 0) gcount[gg] = w;
+}
+
 __global__ void k_iota(int n, int32_t *__restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = i;
@@ -1629,6 +1694,8 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
     const int ksteps = 4 * halves;                   // MMA K steps of 16
     const uint32_t tile_bytes = (uint32_t)(TC_ROWS * 128 * halves), q_bytes = (uint32_t)(32 * 128 * halves);
     const int qb = tv.group_begin[g], qn = tv.group_count[g];
+    const int qe = qb + qn;  // the group's positions; upper-triangle form: rows before qb are skipped, edges
+                             // with rows from qe on are mirrored into those rows
     const int64_t c0 = items.begin[it];
     const int nb = (int)(items.end[it] - c0);        // <= TC_NB
     uint32_t pairs = 0, kept = 0, guard = 0, band = 0, rows_ld = 0;  // rows_ld, kept: thread 0
@@ -1869,6 +1936,11 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
                 d = sqrtf(sv);
             }
             if (is_edge) {
+                if (qp.half && ppos >= qe) {
+                    const int64_t o = rbase + tv.perm[ppos];
+                    atomicAdd(&deg[o], 1);
+                    if (co.off) cap_put(co, (int)o, tv.perm[qfirst + q], d);
+                }
                 atomicAdd(&S.qcnt[q], 1);
                 atomicOr(&S.bem[S.li[sl][r]], 1u << q);
                 if (co.off) {
@@ -1950,6 +2022,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
                     uint32_t validm = (nqr >= 16 * qh + 16 ? 0xffffu : (1u << max(nqr - 16 * qh, 0)) - 1u);
                     const int self = ppos - qfirst - 16 * qh;
                     if (!qp.include_self && (unsigned)self < 16u) validm &= ~(1u << self);
+                    if (qp.half && ppos < qb) validm = 0u;
                     keepm &= validm;
                     pairs += __popc(validm);
                 }
@@ -2050,11 +2123,36 @@ void leaf_l2_prepare() {
     done = true;
 }
 
+// Upper-triangle form, integer metrics (one cloud): the edge (q, p) with p in
+// a later group is also the edge (p, q) of p's row: its degree and one-pass
+// entry (count pass) or its entry (emit pass; a selected row only when rows
+// are emitted again).
+__device__ __forceinline__ void mirror_int(const TreeView &tv, int32_t *deg, const int64_t *row_ptr, int32_t *rowcur,
+                                           int32_t *col, float *dist, int32_t *err, const CapOut &co,
+                                           const uint8_t *rowsel, bool emit, int qpos, int ppos, int d) {
+    const int o = tv.perm[ppos];
+    if (!emit) {
+        atomicAdd(&deg[o], 1);
+        if (co.off) cap_put(co, o, tv.perm[qpos], (float)d);
+        return;
+    }
+    if (rowsel && !rowsel[o]) return;
+    const int slot = atomicAdd(&rowcur[o], 1);
+    const int64_t at = row_ptr[o] + slot;
+    if (at < row_ptr[o + 1]) {
+        col[at] = tv.perm[qpos];
+        dist[at] = (float)d;
+    } else {
+        atomicOr(err, 4);
+    }
+}
+
 // Edit distance of one (pattern, text) pair over alphabet-mapped symbols;
 // the distance if <= k, else k + 1.
 template <int W>
 __device__ __forceinline__ int lev_mapped(const uint64_t *__restrict__ pq, const uint8_t *__restrict__ amap, int m,
-                                          const uint8_t *__restrict__ txt, int n, int k) {
+                                          const uint8_t *__restrict__ txt, int n, int k,
+                                          unsigned long long &cols) {
     if (k < 0) return (m == 0 && n == 0) ? 0 : k + 1;
     if ((m > n ? m - n : n - m) > k) return k + 1;
     if (m == 0) return n;
@@ -2094,8 +2192,12 @@ __device__ __forceinline__ int lev_mapped(const uint64_t *__restrict__ pq, const
                 Mv[w] = Ph & Xv;
             }
         }
-        if (score - (n - 1 - j) > k) return k + 1;
+        if (score - (n - 1 - j) > k) {
+            cols += (unsigned long long)(j + 1) * nw;
+            return k + 1;
+        }
     }
+    cols += (unsigned long long)n * nw;
     return score;
 }
 
@@ -2122,11 +2224,11 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf_lev(
     const int it = blockIdx.x;
     if (it >= *items.count) return;
     const int g = items.group[it];
-    const int qb = tv.group_begin[g], qn = tv.group_count[g];
+    const int qb = tv.group_begin[g], qn = tv.group_count[g], qe = qb + qn;
     const int64_t c0 = items.begin[it], c1 = items.end[it];
     const int k = qp.lev_k;
     for (int i = tid; i < 256; i += LEAF_T) amap[i] = amap_g[i];
-    unsigned long long pairs = 0;
+    unsigned long long pairs = 0, cols = 0;
     for (int q0 = 0; q0 < qn; q0 += qchunk) {
         const int nqr = min(qchunk, qn - q0);
         __syncthreads();
@@ -2170,17 +2272,20 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf_lev(
                     int q = t / npr, p = t - q * npr;
                     int qpos = qb + q0 + q, ppos = tpos[p];
                     if (qpos == ppos && !qp.include_self) continue;
-                    if (EMIT && !sel[q]) continue;
+                    if (qp.half && ppos < qb) continue;
+                    const bool mir = qp.half && ppos >= qe;
+                    if (EMIT && !sel[q] && !(mir && rowsel)) continue;
                     if (!EMIT) ++pairs;
                     const uint8_t *txt = tv.sdata + tv.soff[ppos];
                     int n = (int)(tv.soff[ppos + 1] - tv.soff[ppos]);
-                    int d = lev_mapped<W>(speq + (size_t)q * A * W, amap, qlen[q], txt, n, k);
+                    int d = lev_mapped<W>(speq + (size_t)q * A * W, amap, qlen[q], txt, n, k, cols);
                     if (d > k) continue;
+                    if (mir) mirror_int(tv, deg, row_ptr, rowcur, col, dist, err, co, rowsel, EMIT, qpos, ppos, d);
                     if (!EMIT) {
                         hit |= 1u << p;
                         atomicAdd(&cnt[q], 1);
                         if (co.off) cap_put(co, cursor[q], tv.perm[ppos], (float)d);
-                    } else {
+                    } else if (sel[q]) {
                         int slot = atomicAdd(&rowcur[cursor[q]], 1);
                         int64_t at = rowb[q] + slot;
                         if (at < rowe[q]) {
@@ -2205,8 +2310,14 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf_lev(
         if (!EMIT && tid < nqr && cnt[tid]) atomicAdd(&deg[cursor[tid]], cnt[tid]);
     }
     if (!EMIT) {
-        for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
-        if ((tid & 31) == 0) stat_add(st, ST_PAIRS, pairs);
+        for (int o = 16; o > 0; o >>= 1) {
+            pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+            cols += __shfl_xor_sync(0xffffffffu, cols, o);
+        }
+        if ((tid & 31) == 0) {
+            stat_add(st, ST_PAIRS, pairs);
+            stat_add(st, ST_COLS, cols);
+        }
     }
 }
 
@@ -2231,7 +2342,7 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf_ham(
     const int it = blockIdx.x;
     if (it >= *items.count) return;
     const int g = items.group[it];
-    const int qb = tv.group_begin[g], qn = tv.group_count[g];  // at most 32 queries
+    const int qb = tv.group_begin[g], qn = tv.group_count[g], qe = qb + qn;  // at most 32 queries
     const int64_t c0 = items.begin[it], c1 = items.end[it];
     const int k = qp.lev_k, nq = tv.wp >> 2;
     uint4 *Qs = hsm, *Ps = hsm + 32 * nq;
@@ -2270,15 +2381,18 @@ __global__ void __launch_bounds__(LEAF_T) k_leaf_ham(
                 const int q = t / npr, p = t - q * npr;
                 const int qpos = qb + q, ppos = tpos[p];
                 if (qpos == ppos && !qp.include_self) continue;
-                if (EMIT && !sel[q]) continue;
+                if (qp.half && ppos < qb) continue;
+                const bool mir = qp.half && ppos >= qe;
+                if (EMIT && !sel[q] && !(mir && rowsel)) continue;
                 if (!EMIT) ++pairs;
                 const int d = ham_rows_smem(Qs + q * nq, Ps + p * nq, nq);
                 if (d > k) continue;
+                if (mir) mirror_int(tv, deg, row_ptr, rowcur, col, dist, err, co, rowsel, EMIT, qpos, ppos, d);
                 if (!EMIT) {
                     hit |= 1u << p;
                     atomicAdd(&cnt[q], 1);
                     if (co.off) cap_put(co, cursor[q], tv.perm[ppos], (float)d);
-                } else {
+                } else if (sel[q]) {
                     const int slot = atomicAdd(&rowcur[cursor[q]], 1);
                     const int64_t at = rowb[q] + slot;
                     if (at < rowe[q]) {
@@ -2726,12 +2840,13 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     std::memset(&V, 0, sizeof(V));
     V.nc = C;
     int max_dp = 4, max_depth = 0, max_len = 0, min_len = kItemTC;
-    bool any_tc = false, any_fp = false;
+    bool any_tc = false, any_fp = false, any_half = false;
     for (int c = 0; c < C; ++c) {
         const ct_tree *tc = trees[c];
         if ((tc->metric == CT_L2_F32) != l2) CT_FAIL(CT_EINVAL, "a batch mixes metrics");
         V.tv[c] = view_of(tc);
         V.qp[c] = qps[c];
+        any_half |= qps[c].half != 0;
         const LeafChoice ch = leaf_choice(tc, precision);
         V.use_tc[c] = (uint8_t)ch.use_tc;
         V.item_len[c] = (int16_t)ch.item_len;
@@ -2871,6 +2986,10 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
         CT_COUNT_LAUNCH();
         k_iota<<<grid_for(G, 256), 256, 0, s>>>(G, gseg_group.p);
         CT_COUNT_LAUNCH();
+        if (any_half) {
+            k_half_cands<<<grid_for((int64_t)G * 32, 256), 256, 0, s>>>(V, G, gseg_begin.p, gseg_count.p, gcand.p, n_cand);
+            CT_COUNT_LAUNCH();
+        }
         CT_LAUNCH_CHECK();
         nseg = G;
     }
@@ -3037,6 +3156,7 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
         all.stats.emit_pairs = (int64_t)hs[ST_EMIT];
         all.stats.leaf_rows = (int64_t)hs[ST_ROWS];
         all.stats.guard_band = (int64_t)hs[ST_BAND];
+        all.stats.lev_columns = (int64_t)hs[ST_COLS];
         all.stats.candidates = n_cand;
     };
 
@@ -3388,6 +3508,7 @@ struct PlanImpl {
     int max_dp = 4, cap_stack = 0, spill_cap = 0, leaf_grid = 1;
     TravLaunch tl{1, 1};
     int64_t pool_cap = 0, seg_cap = 0, cand_cap = 0, item_cap = 0, nnz_cap = 0;
+    bool any_half = false;  // some cloud is queried in the upper-triangle form
     int big_rows = 0;       // rows above the in-place sorts' length the plan sorts by radix
     int64_t big_cap = 0;    // their entries
     cudaStream_t s0 = 0;
@@ -3446,6 +3567,10 @@ void plan_enqueue(PlanImpl &p, cudaStream_t s) {
                                                                   P.seg_count, p.gbegin.p, p.gfill.p, P.data,
                                                                   p.gcand.p, p.cand_cap, err);
     CT_COUNT_LAUNCH();
+    if (p.any_half) {  // (ranges past the plan's capacity are never read: the producer skips them)
+        k_half_cands<<<grid_for((int64_t)G * 32, 256), 256, 0, s>>>(V, G, p.gbegin.p, p.gcount.p, p.gcand.p, p.cand_cap);
+        CT_COUNT_LAUNCH();
+    }
     // 3. count pass: one persistent launch producing and consuming the work queue
     CT_CHECK_CUDA(cudaMemsetAsync(p.qctr.p, 0, 4 * sizeof(int32_t), s));
     CT_CHECK_CUDA(cudaMemsetAsync(p.ready.p, 0, (size_t)p.item_cap * sizeof(int32_t), s));
@@ -3534,6 +3659,7 @@ PlanImpl *plan_create(int C, const ct_tree *const *trees, const QParams *qps, in
         p.trees.push_back(t);
         p.V.tv[c] = view_of(t);
         p.V.qp[c] = qps[c];
+        p.any_half |= qps[c].half != 0;
         p.V.use_tc[c] = 0;  // the persistent launch runs the FP32 tiles
         const int len = precision == 2 ? leaf_choice(t, 2).item_len : kItem;
         p.V.item_len[c] = (int16_t)len;

@@ -23,7 +23,8 @@ struct QParams {
     float c_lo = 0, c_hi = 0;  // inside it: fp32 sums outside [c_lo, c_hi] decide alone
     int mode = 0;
     int include_self = 0;
-    int lev_k = 0;         // edit distance: floor(eps)
+    int lev_k = 0;         // edit distance, Hamming: floor(eps)
+    int half = 0;          // upper-triangle form: each pair of two query groups evaluated once, mirrored
 };
 
 QParams make_qparams(const ct_tree *t, double eps, int include_self);
@@ -109,6 +110,6 @@ void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int
                cudaStream_t s);
 
 // Stats slots accumulated on the device.
-enum { ST_TRAV = 0, ST_PAIRS, ST_GUARD, ST_RECHECK, ST_CAND, ST_OVERFLOW, ST_ERR, ST_EMIT, ST_ROWS, ST_BAND, ST_N };
+enum { ST_TRAV = 0, ST_PAIRS, ST_GUARD, ST_RECHECK, ST_CAND, ST_OVERFLOW, ST_ERR, ST_EMIT, ST_ROWS, ST_BAND, ST_COLS, ST_N };
 
 }  // namespace ct

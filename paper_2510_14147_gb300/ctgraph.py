@@ -48,7 +48,7 @@ class ct_build_opts(C.Structure):
 
 class ct_query_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("use_predictor", C.c_int32),
-                ("include_self", C.c_int32), ("reserved", C.c_int32), ("predictor", C.c_void_p)]
+                ("include_self", C.c_int32), ("upper_triangle", C.c_int32), ("predictor", C.c_void_p)]
 
 
 class ct_csr(C.Structure):
@@ -60,7 +60,7 @@ class ct_query_stats(C.Structure):
     _fields_ = [(f, C.c_int64) for f in ("traversal_evals", "leaf_pairs", "guard_fp64",
                                            "recheck_fp32", "candidates", "overflow_rows",
                                            "kernel_launches", "emit_pairs", "reemit_rows",
-                                           "leaf_rows", "guard_band")]
+                                           "leaf_rows", "guard_band", "lev_columns")]
 
 
 class ct_fit_opts(C.Structure):
@@ -328,47 +328,48 @@ def ct_build(points=None, strings=None, bits=None, leaf_size: int = 32, root: in
     return Tree(h.value, int(p.n), int(p.metric))
 
 
-def _opts(precision, use_predictor, include_self, predictor):
+def _opts(precision, use_predictor, include_self, predictor, upper_triangle=False):
     o = ct_query_opts()
     o.precision = int(precision)
     o.use_predictor = int(bool(use_predictor))
     o.include_self = int(bool(include_self))
+    o.upper_triangle = int(bool(upper_triangle))
     o.predictor = predictor.handle.value if predictor is not None else None
     return o
 
 
 def eps_graph_query(tree: Tree, eps: float, precision: int = 0, use_predictor: bool = False,
-                    include_self: bool = False, predictor=None, stream=None) -> CSR:
+                    include_self: bool = False, predictor=None, stream=None, upper_triangle: bool = False) -> CSR:
     """The exact ε-graph of the tree's points as a CSR (rows ascending)."""
     lib = _load()
     out = ct_csr()
-    o = _opts(precision, use_predictor, include_self, predictor)
+    o = _opts(precision, use_predictor, include_self, predictor, upper_triangle)
     _check(lib.eps_graph_query(tree.handle, float(eps), C.byref(o), C.c_void_p(_stream(stream)),
                                C.byref(out)))
     return CSR(out)
 
 
 def eps_graph_query_batched(trees, eps, precision: int = 0, use_predictor: bool = False,
-                            include_self: bool = False, predictor=None, stream=None):
+                            include_self: bool = False, predictor=None, stream=None, upper_triangle: bool = False):
     lib = _load()
     k = len(trees)
     arr = (C.c_void_p * max(k, 1))(*[t.handle.value for t in trees])
     ea = (C.c_double * max(k, 1))(*[float(e) for e in eps])
     outs = (ct_csr * max(k, 1))()
-    o = _opts(precision, use_predictor, include_self, predictor)
+    o = _opts(precision, use_predictor, include_self, predictor, upper_triangle)
     _check(lib.eps_graph_query_batched(k, arr, ea, C.byref(o), C.c_void_p(_stream(stream)), outs))
     return [CSR(outs[i]) for i in range(k)]
 
 
 def eps_graph_query_sweep(tree: Tree, eps, precision: int = 0, use_predictor: bool = False,
-                          include_self: bool = False, predictor=None, stream=None):
+                          include_self: bool = False, predictor=None, stream=None, upper_triangle: bool = False):
     """CSRs of one tree at several radii (eps: a sequence); csrs[k] equals
     eps_graph_query(tree, eps[k], ...) bit for bit."""
     lib = _load()
     k = len(eps)
     ea = (C.c_double * max(k, 1))(*[float(e) for e in eps])
     outs = (ct_csr * max(k, 1))()
-    o = _opts(precision, use_predictor, include_self, predictor)
+    o = _opts(precision, use_predictor, include_self, predictor, upper_triangle)
     _check(lib.eps_graph_query_sweep(tree.handle, k, ea, C.byref(o), C.c_void_p(_stream(stream)), outs))
     return [CSR(outs[i]) for i in range(k)]
 
@@ -395,12 +396,12 @@ class Plan:
 
 
 def ct_plan_create(trees, eps, precision: int = 0, use_predictor: bool = False, include_self: bool = False,
-                   predictor=None, margin: float = 0.1, use_graph: bool = True, stream=None) -> Plan:
+                   predictor=None, margin: float = 0.1, use_graph: bool = True, stream=None, upper_triangle: bool = False) -> Plan:
     lib = _load()
     k = len(trees)
     arr = (C.c_void_p * max(k, 1))(*[t.handle.value for t in trees])
     ea = (C.c_double * max(k, 1))(*[float(e) for e in eps])
-    o = _opts(precision, use_predictor, include_self, predictor)
+    o = _opts(precision, use_predictor, include_self, predictor, upper_triangle)
     h = C.c_void_p()
     _check(lib.ct_plan_create(k, arr, ea, C.byref(o), float(margin), int(bool(use_graph)),
                               C.c_void_p(_stream(stream)), C.byref(h)))
