@@ -8,11 +8,12 @@ sift eps=175 shape).  Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
                   [--workload gmm_1m_k70|gmm_1m_k500|dna_50k|clouds_64|small_3d]
-                  [--form tc+learned|tc|learned|plain|auto|auto+learned]
+                  [--form tc+learned+upper|tc+learned|tc|learned|plain|auto|auto+learned|...+upper]
                   [--no-compare] [--no-cpu-baseline] [--no-e2e]
 
-The default form is the tensor-core-filtered, learned one for L2 points and
-the learned one for edit distance.  Every other form is timed beside it on the
+The default form is the tensor-core-filtered, learned, upper-triangle one
+for L2 points and the learned, upper-triangle one for edit distance and
+Hamming codes.  Every other form is timed beside it on the
 same input ("forms" in the JSON line), and its whole CSR is compared with the
 default form's, entry for entry.
 
@@ -320,18 +321,26 @@ SWEEPS = {"gmm_1m_k70": ["gmm_1m_k10", "gmm_1m_k70", "gmm_1m_k500"],
 
 FORMS = {"plain": (0, False), "tc": (1, False), "learned": (0, True), "tc+learned": (1, True),
          "auto": (2, False), "auto+learned": (2, True)}
+# any form with "+upper": the upper-triangle query (each pair of two query
+# groups evaluated once, mirrored into both rows)
+FORMS.update({k + "+upper": v for k, v in list(FORMS.items())})
+
+
+def form_opts(name):
+    prec, learned = FORMS[name]
+    return prec, learned, name.endswith("+upper")
 
 
 def default_form(wl) -> str:
-    return "learned" if wl["kind"] in ("dna", "bits") else "tc+learned"
+    return "learned+upper" if wl["kind"] in ("dna", "bits") else "tc+learned+upper"
 
 
 def config_of(args, wl, world):
-    prec, learned = FORMS[args.form]
+    prec, learned, upper = form_opts(args.form)
     if wl["kind"] == "bits":
         return {"workload": args.workload, "n": wl["n"], "bits": wl["bits"], "metric": "hamming", "eps": wl["eps"],
                 "zeta": wl.get("zeta", 32), "target_degree": wl.get("target_degree"), "form": args.form,
-                "precision": prec, "learned": learned,
+                "precision": prec, "learned": learned, "upper_triangle": upper,
                 "codes": "%d centres, bits flipped with probability %g" % (wl["n_centres"], wl["flip"]),
                 "parallelism": "replicas%d" % world if world > 1 else "single",
                 "l2": "inputs (%.0f MB) smaller than L2 (129 MB): a 256 MB buffer is written before every "
@@ -341,7 +350,7 @@ def config_of(args, wl, world):
         n = wl["n_seeds"] * wl["per_seed"]
         return {"workload": args.workload, "n": n, "metric": "levenshtein", "eps": wl["eps"],
                 "zeta": wl.get("zeta", 32), "form": args.form, "precision": prec, "learned": learned,
-                "strings": "%d seeds of length %d, %d mutants each" % (wl["n_seeds"], wl["seed_len"],
+                "upper_triangle": upper, "strings": "%d seeds of length %d, %d mutants each" % (wl["n_seeds"], wl["seed_len"],
                                                                        wl["per_seed"]),
                 "parallelism": "replicas%d" % world if world > 1 else "single",
                 "l2": "inputs (strings, 5 MB) smaller than L2 (129 MB): a 256 MB buffer is written before every "
@@ -349,7 +358,7 @@ def config_of(args, wl, world):
                 "step": "ct_build + eps_graph_query + csr_free"}
     return {"workload": args.workload, "n": wl["n"], "dim": wl["dim"], "eps": wl["eps"],
             "zeta": wl.get("zeta", 32), "target_degree": wl.get("target_degree"),
-            "form": args.form, "precision": prec, "learned": learned,
+            "form": args.form, "precision": prec, "learned": learned, "upper_triangle": upper,
             "parallelism": "replicas%d" % world if world > 1 else "single",
             "l2": "inputs (%.0f MB) larger than L2 (129 MB); no flush" % (wl["n"] * wl["dim"] * 4 / 1e6)
             if wl["n"] * wl["dim"] * 4 > 129e6 else "inputs smaller than L2; no flush",
@@ -357,11 +366,11 @@ def config_of(args, wl, world):
 
 
 def clouds_config(args, wl, world):
-    prec, learned = FORMS[args.form]
+    prec, learned, upper = form_opts(args.form)
     specs = wl["specs"]
     return {"workload": args.workload, "clouds": len(specs), "points": sum(sp["n"] for sp in specs),
             "dims": sorted(set(sp["dim"] for sp in specs)), "form": args.form,
-            "precision": prec, "learned": learned, "zeta": wl.get("zeta", 32),
+            "precision": prec, "learned": learned, "upper_triangle": upper, "zeta": wl.get("zeta", 32),
             "parallelism": "replicas%d" % world if world > 1 else "single",
             "l2": "inputs (%.0f MB) larger than L2 (129 MB); no flush"
                   % (sum(sp["n"] * sp["dim"] * 4 for sp in specs) / 1e6),
@@ -486,7 +495,7 @@ def run_single(args, wl, world, rank, dist):
         build = lambda stream, d=None: cg.ct_build(strings=dev if d is None else d, leaf_size=zeta, stream=stream)
     stream = torch.cuda.Stream()
     eps, zeta = wl["eps"], wl.get("zeta", 32)
-    precision, learned = FORMS[args.form]
+    precision, learned, upper = form_opts(args.form)
 
     last = {}
     pred = None
@@ -522,12 +531,12 @@ def run_single(args, wl, world, rank, dist):
     if kind in ("strings", "bits"):   # inputs smaller than L2: written over before every timed step
         flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
 
-    def step(prec=precision, use_pred=learned, keep=False):
+    def step(prec=precision, use_pred=learned, keep=False, up=upper):
         if flush is not None:
             flush.fill_(1.0)
         t = build(stream)
         c = cg.eps_graph_query(t, eps, precision=prec, stream=stream, use_predictor=use_pred,
-                               predictor=pred if use_pred else None)
+                               predictor=pred if use_pred else None, upper_triangle=up)
         last["nnz"] = c.nnz
         last["stats"] = c.stats()
         t.free()
@@ -581,15 +590,16 @@ def run_single(args, wl, world, rank, dist):
         with torch.cuda.stream(stream):
             ref = step(keep=True)
         names = ["plain", "learned"] if kind in ("strings", "bits") else ["plain", "tc", "learned", "tc+learned"]
+        names = names + [nm + "+upper" for nm in names]
         for name in names:
             if name == args.form:
                 continue
-            pf, lf = FORMS[name]
+            pf, lf, uf = form_opts(name)
             with torch.cuda.stream(stream):
-                c = step(pf, lf, keep=True)
+                c = step(pf, lf, keep=True, up=uf)
                 same = csr_equal(c, ref)
                 c.free()
-                step(pf, lf)
+                step(pf, lf, up=uf)
             barrier()
             cg.ct_profile_reset()
             cg.ct_profile_enable(True)
@@ -598,7 +608,7 @@ def run_single(args, wl, world, rank, dist):
             tot = 0
             with torch.cuda.stream(stream):
                 for _ in range(args.steps):
-                    tot += step(pf, lf)
+                    tot += step(pf, lf, up=uf)
             b.record(stream)
             barrier()
             cg.ct_profile_enable(False)
@@ -622,9 +632,9 @@ def run_single(args, wl, world, rank, dist):
         with torch.cuda.stream(stream):
             t = build(stream)
             ind = [cg.eps_graph_query(t, e, precision=precision, stream=stream, use_predictor=learned,
-                                      predictor=pred) for e in reps]
+                                      predictor=pred, upper_triangle=upper) for e in reps]
             sw = cg.eps_graph_query_sweep(t, reps, precision=precision, stream=stream, use_predictor=learned,
-                                          predictor=pred)
+                                          predictor=pred, upper_triangle=upper)
             same = all(csr_equal(a, b) for a, b in zip(ind, sw))
             sw_nnz = [c.nnz for c in sw]
             for c in ind + sw:
@@ -640,10 +650,10 @@ def run_single(args, wl, world, rank, dist):
                 for _ in range(args.steps):
                     if mode == "sweep":
                         cs = cg.eps_graph_query_sweep(t, reps, precision=precision, stream=stream,
-                                                      use_predictor=learned, predictor=pred)
+                                                      use_predictor=learned, predictor=pred, upper_triangle=upper)
                     else:
                         cs = [cg.eps_graph_query(t, e, precision=precision, stream=stream, use_predictor=learned,
-                                                 predictor=pred) for e in reps]
+                                                 predictor=pred, upper_triangle=upper) for e in reps]
                     for c in cs:
                         c.free()
             b.record(stream)
@@ -676,7 +686,7 @@ def run_single(args, wl, world, rank, dist):
                 d.copy_(h, non_blocking=True)
             t = build(stream, din[0] if kind in ("points", "bits") else (din[0], din[1]))
             c = cg.eps_graph_query(t, eps, precision=precision, stream=stream,
-                                   use_predictor=learned, predictor=pred)
+                                   use_predictor=learned, predictor=pred, upper_triangle=upper)
             rp_h.copy_(c.row_ptr, non_blocking=True)
             col_h[:c.nnz].copy_(c.col, non_blocking=True)
             dist_h[:c.nnz].copy_(c.dist, non_blocking=True)
@@ -733,7 +743,7 @@ def run_clouds(args, wl, world, rank, dist):
     query over all of them; value = all clouds' edges / step time."""
     import torch
     from paper_2510_14147_gb300 import ctgraph as cg
-    precision, learned = FORMS[args.form]
+    precision, learned, upper = form_opts(args.form)
     specs = wl["specs"]
     hosts = [I.cloud_points(sp) for sp in specs]
     xs = [torch.from_numpy(x).cuda() for x in hosts]
@@ -759,13 +769,14 @@ def run_clouds(args, wl, world, rank, dist):
                         "fit_s": time.perf_counter() - t0}
     last = {}
 
-    def step(prec, use_pred, keep=False, src=None):
+    def step(prec, use_pred, keep=False, src=None, up=upper):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         e[0].record(stream)
         trees = [cg.ct_build(points=x, leaf_size=zeta, stream=stream) for x in (src or xs)]
         e[1].record(stream)
         csrs = cg.eps_graph_query_batched(trees, eps, precision=prec, stream=stream,
-                                          use_predictor=use_pred, predictor=pred if use_pred else None)
+                                          use_predictor=use_pred, predictor=pred if use_pred else None,
+                                          upper_triangle=up)
         e[2].record(stream)
         nnz = sum(c.nnz for c in csrs)
         last["stats"] = [c.stats() for c in csrs]
@@ -834,9 +845,9 @@ def run_clouds(args, wl, world, rank, dist):
         for name in ("plain",):
             if name == args.form:
                 continue
-            pf, lf = FORMS[name]
+            pf, lf, uf = form_opts(name)
             with torch.cuda.stream(stream):
-                cs = step(pf, lf, keep=True)
+                cs = step(pf, lf, keep=True, up=uf)
                 same = all(csr_equal(x, y) for x, y in zip(cs, ref))
                 for c in cs:
                     c.free()
@@ -846,7 +857,7 @@ def run_clouds(args, wl, world, rank, dist):
             tp = 0
             with torch.cuda.stream(stream):
                 for _ in range(args.steps):
-                    tp += step(pf, lf)
+                    tp += step(pf, lf, up=uf)
             b2.record(stream)
             barrier()
             tpm, tp = combine_ranks(a2.elapsed_time(b2), tp, dist)
@@ -865,7 +876,8 @@ def run_clouds(args, wl, world, rank, dist):
     if not args.no_plan:
         with torch.cuda.stream(stream):
             trees = [cg.ct_build(points=x, leaf_size=zeta, stream=stream) for x in xs]
-        opts = dict(precision=precision, use_predictor=learned, predictor=pred if learned else None, stream=stream)
+        opts = dict(precision=precision, use_predictor=learned, predictor=pred if learned else None, stream=stream,
+                    upper_triangle=upper)
 
         def timed(fn, reps):
             barrier()
@@ -1009,7 +1021,7 @@ def main():
     args = ap.parse_args()
     wl = I.load_workloads()[args.workload]
     if args.form is None:
-        args.form = "auto+learned" if wl["kind"] == "clouds" else default_form(wl)
+        args.form = "auto+learned+upper" if wl["kind"] == "clouds" else default_form(wl)
 
     if args.impl == "reference":
         return run_reference(args, wl)

@@ -444,6 +444,15 @@ ct_status ct_profile_entry(int32_t i, const char **name, double *total_ms, int64
 /* Number of kernels this library has launched in this process so far. */
 int64_t ct_kernel_launches(void);
 
+/* Diagnostic for tests (the paper has none): while `rows` is set, every
+ * count pass of later queries (L2, FP32 and tensor-core tiles) appends the
+ * CSR rows of both ends of each pair it decides by the pinned FP64 sum --
+ * the pairs nearest eps -- to rows (device int32[cap]), counting them in
+ * *count (device uint64, zeroed by the caller; entries past cap are counted,
+ * not written).  Process-wide; rows = NULL turns it off.  Synchronises the
+ * device.  Errors: CT_EINVAL (rows without count, cap < 0), CT_ECUDA. */
+ct_status ct_debug_guard_rows(int32_t *rows, uint64_t *count, int64_t cap);
+
 /* Tensor-core self-test (a diagnostic; the paper has none): D = A * B^T for
  * A (128 x 128) and B (32 x 128) 16-bit row-major device matrices (fp16 = 0:
  * bf16, 1: fp16; both the same type) and D (128 x 32) fp32 row-major device

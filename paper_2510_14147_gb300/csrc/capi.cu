@@ -26,6 +26,7 @@ void save_tree(const ct_tree *t, const char *path);
 ct_tree *load_tree(const char *path, cudaStream_t s);
 void sweep_filter(const ct_tree *t, const QParams &qs, const QParams &qd, const QueryOut &src, cudaStream_t s,
                   QueryOut &out);
+void set_guard_rows(int32_t *rows, unsigned long long *count, int64_t cap);
 }  // namespace ct
 
 namespace {
@@ -359,6 +360,13 @@ ct_status eps_graph_degrees_noalloc(const ct_tree *tree, double eps, int32_t inc
         check_device(tree);
         ct::QParams qp = ct::make_qparams(tree, eps, include_self);
         ct::degrees_noalloc(tree, qp, degrees, (cudaStream_t)stream);
+    });
+}
+
+ct_status ct_debug_guard_rows(int32_t *rows, uint64_t *count, int64_t cap) {
+    return guarded([&] {
+        if (rows && (!count || cap < 0)) CT_FAIL(CT_EINVAL, "count must be given and cap >= 0");
+        ct::set_guard_rows(rows, reinterpret_cast<unsigned long long *>(count), cap);
     });
 }
 

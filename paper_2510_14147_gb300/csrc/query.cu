@@ -46,6 +46,22 @@ __device__ __forceinline__ void prefetch_l1(const void *p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
+// Diagnostic (off unless a test sets it): the CSR rows of both ends of every
+// pair a count pass decides by the FP64 sum, appended to a caller's buffer.
+__device__ int32_t *g_guard_rows = nullptr;
+__device__ unsigned long long *g_guard_n = nullptr;
+__device__ long long g_guard_cap = 0;
+
+__device__ __forceinline__ void note_guard_rows(int32_t a, int32_t b) {
+    int32_t *r = g_guard_rows;
+    if (!r) return;
+    const unsigned long long k = atomicAdd(g_guard_n, 2ull);
+    if ((long long)k + 1 < g_guard_cap) {
+        r[k] = a;
+        r[k + 1] = b;
+    }
+}
+
 __device__ __forceinline__ void stat_add(unsigned long long *st, int slot, unsigned long long v) {
     if (v) atomicAdd(st + slot, v);
 }
@@ -923,7 +939,10 @@ __device__ __forceinline__ void leaf_l2_item(
             const int m = all ? n : (n & ~31);
             for (int i = tid; i < m; i += LEAF_T) {
                 const int q = S.gq[i], ppos = S.gpos[i], li = S.gb[i];
-                if (!EMIT) ++guard;
+                if (!EMIT) {
+                    ++guard;
+                    note_guard_rows(S.cursor[q], (int32_t)(rbase + tv.perm[ppos]));
+                }
                 double s64 = sq_l2_exact(tv.pts + (size_t)(qfirst + q) * dp, tv.pts + (size_t)ppos * dp, dim);
                 if (s64 <= qp.eps2_64) {
                     if (half && ppos >= qe) mirror(qfirst + q, ppos, (float)sqrt(s64));
@@ -1928,6 +1947,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
             float d;
             if (edge < 0) {
                 ++guard;
+                note_guard_rows(S.orig[q], (int32_t)(rbase + tv.perm[ppos]));
                 const double s64 = sq_l2_exact4(qrow, prow, dim);
                 is_edge = s64 <= qp.eps2_64;
                 d = (float)sqrt(s64);
@@ -3257,6 +3277,16 @@ void query_plain(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &
 
 void query_tc(const ct_tree *t, const QParams &qp, cudaStream_t s, QueryOut &out) {
     query_multi(1, &t, &qp, s, &out, 1, nullptr, nullptr);
+}
+
+void set_guard_rows(int32_t *rows, unsigned long long *count, int64_t cap) {
+    long long c = rows ? (long long)cap : 0;
+    int32_t *r = rows;
+    unsigned long long *n = rows ? count : nullptr;
+    CT_CHECK_CUDA(cudaDeviceSynchronize());
+    CT_CHECK_CUDA(cudaMemcpyToSymbol(g_guard_rows, &r, sizeof(r)));
+    CT_CHECK_CUDA(cudaMemcpyToSymbol(g_guard_n, &n, sizeof(n)));
+    CT_CHECK_CUDA(cudaMemcpyToSymbol(g_guard_cap, &c, sizeof(c)));
 }
 
 // ---------------------------------------------------------------- plans

@@ -164,6 +164,8 @@ def _load():
         lib.ct_plan_set_wait.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
         lib.ct_plan_free.restype = None
         lib.ct_plan_free.argtypes = [C.c_void_p]
+        lib.ct_debug_guard_rows.restype = C.c_int
+        lib.ct_debug_guard_rows.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
         lib.ct_tree_save.restype = C.c_int
         lib.ct_tree_save.argtypes = [C.c_void_p, C.c_char_p]
         lib.ct_tree_load.restype = C.c_int
@@ -422,6 +424,16 @@ def ct_plan_result(plan: Plan, stream=None):
 
 def ct_plan_set_wait(plan: Plan, withhold_producers: bool = False, max_polls: int = 1 << 20):
     _check(_load().ct_plan_set_wait(plan.handle, int(bool(withhold_producers)), int(max_polls)))
+
+
+def ct_debug_guard_rows(rows=None, count=None):
+    """Diagnostic: record the CSR rows of both ends of every pair later count
+    passes decide by the FP64 sum into `rows` (CUDA int32 tensor), counting
+    into `count` (CUDA int64 tensor of one zeroed entry); rows=None stops."""
+    if rows is None:
+        _check(_load().ct_debug_guard_rows(None, None, 0))
+    else:
+        _check(_load().ct_debug_guard_rows(rows.data_ptr(), count.data_ptr(), rows.numel()))
 
 
 def ct_tree_save(tree: Tree, path: str):
