@@ -462,6 +462,22 @@ ct_status ct_debug_guard_rows(int32_t *rows, uint64_t *count, int64_t cap);
  * {0, 1}; CT_ETIMEOUT if the bounded wait for the MMA's completion gives up. */
 ct_status ct_selftest_tc_gemm(const void *A, const void *B, int32_t fp16, float *D, ct_stream stream);
 
+/* The same self-test with the MMA withheld (a test of the failure path: no
+ * MMA and no commit are issued, so the bounded wait for the completion runs
+ * out, about a second): returns CT_ETIMEOUT and leaves the context usable. */
+ct_status ct_selftest_tc_timeout(ct_stream stream);
+
+/* Host-side fault injection for tests: the k-th next device allocation made
+ * by the library (k >= 1, counted process-wide) fails as an out-of-memory
+ * error would (the call returns CT_ENOMEM); k = 0 turns it off.
+ * Errors: CT_EINVAL (k < 0). */
+ct_status ct_debug_fail_alloc(int64_t k);
+
+/* Bytes of the current device's default memory pool in use (the pool the
+ * library allocates from), after synchronising the device: a test's check
+ * that a failed call leaked nothing.  Errors: CT_EINVAL, CT_ECUDA. */
+ct_status ct_debug_pool_used(uint64_t *bytes);
+
 /* Thread-local message for the last non-OK status of this thread. */
 const char *ct_last_error(void);
 

@@ -21,7 +21,7 @@ void query_batched(int n_clouds, const ct_tree *const *trees, const QParams *qps
 void autotune(int n_clouds, const ct_tree *const *trees, const QParams *qps, const ct_query_opts *opts,
               cudaStream_t s, int32_t *choices);
 void degrees_noalloc(const ct_tree *t, const QParams &qp, int32_t *degrees, cudaStream_t s);
-void tc_selftest(const void *A, const void *B, int fp16, float *D, cudaStream_t s);
+void tc_selftest(const void *A, const void *B, int fp16, float *D, cudaStream_t s, int withhold);
 void save_tree(const ct_tree *t, const char *path);
 ct_tree *load_tree(const char *path, cudaStream_t s);
 void sweep_filter(const ct_tree *t, const QParams &qs, const QParams &qd, const QueryOut &src, cudaStream_t s,
@@ -374,7 +374,39 @@ ct_status ct_selftest_tc_gemm(const void *A, const void *B, int32_t fp16, float 
     return guarded([&] {
         if (!A || !B || !D) CT_FAIL(CT_EINVAL, "NULL argument");
         if (fp16 != 0 && fp16 != 1) CT_FAIL(CT_EINVAL, "fp16 must be 0 or 1");
-        ct::tc_selftest(A, B, fp16, D, (cudaStream_t)stream);
+        ct::tc_selftest(A, B, fp16, D, (cudaStream_t)stream, 0);
+    });
+}
+
+ct_status ct_selftest_tc_timeout(ct_stream stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    return guarded([&] {
+        ct::DBuf<uint16_t> a(128 * 128, s), b(32 * 128, s);
+        ct::DBuf<float> d(128 * 32, s);
+        CT_CHECK_CUDA(cudaMemsetAsync(a.p, 0, 128 * 128 * sizeof(uint16_t), s));
+        CT_CHECK_CUDA(cudaMemsetAsync(b.p, 0, 32 * 128 * sizeof(uint16_t), s));
+        ct::tc_selftest(a.p, b.p, 1, d.p, s, 1);
+    });
+}
+
+ct_status ct_debug_fail_alloc(int64_t k) {
+    return guarded([&] {
+        if (k < 0) CT_FAIL(CT_EINVAL, "k must be >= 0");
+        ct::set_fail_alloc(k);
+    });
+}
+
+ct_status ct_debug_pool_used(uint64_t *bytes) {
+    return guarded([&] {
+        if (!bytes) CT_FAIL(CT_EINVAL, "bytes is NULL");
+        int dev = 0;
+        CT_CHECK_CUDA(cudaGetDevice(&dev));
+        CT_CHECK_CUDA(cudaDeviceSynchronize());
+        cudaMemPool_t pool;
+        CT_CHECK_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+        uint64_t used = 0;
+        CT_CHECK_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+        *bytes = used;
     });
 }
 

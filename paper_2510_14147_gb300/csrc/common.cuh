@@ -47,6 +47,8 @@ struct Error {
 // next call instead of being returned to the driver.
 void *dmalloc(size_t bytes, cudaStream_t s);
 void dfree(void *p, cudaStream_t s);
+// Test hook: the k-th next dmalloc (k >= 1) fails with CT_ENOMEM; 0 turns it off.
+void set_fail_alloc(int64_t k);
 
 // Owning buffer freed stream-ordered when it goes out of scope.
 template <class T>

@@ -2917,6 +2917,17 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     CT_CHECK_CUDA(cudaMemsetAsync(st.p, 0, ST_N * sizeof(unsigned long long), s));
     int32_t *err = reinterpret_cast<int32_t *>(st.p + ST_ERR);
     QueryOut all;  // the concatenated CSR of all clouds
+    struct AllGuard {  // releases its arrays unless they were handed to the caller
+        QueryOut &q;
+        cudaStream_t s;
+        bool armed = true;
+        ~AllGuard() {
+            if (!armed) return;
+            dfree(q.row_ptr, s);
+            dfree(q.col, s);
+            dfree(q.dist, s);
+        }
+    } all_guard{all, s};
 
     // learned form: row capacities and the traversal order from the predictor
     LearnedPlan lp;
@@ -3168,6 +3179,8 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
         unsigned long long hs[ST_N];
         to_host(hs, st.p, ST_N, s);
         prof_flush();
+        if (hs[ST_ERR] & 32)
+            CT_FAIL(CT_ETIMEOUT, "a bounded wait of the tensor-core leaf kernel gave up (code %llu)", hs[ST_ERR]);
         if (hs[ST_ERR]) CT_FAIL(CT_ECUDA, "internal consistency check failed in the query (code %llu)", hs[ST_ERR]);
         all.stats.traversal_evals = (int64_t)hs[ST_TRAV];
         all.stats.leaf_pairs = (int64_t)hs[ST_PAIRS];
@@ -3243,6 +3256,7 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     finish_stats();
     if (C == 1) {
         outs[0] = all;
+        all_guard.armed = false;
         return;
     }
     // several clouds: CSRs that view one shared allocation each of row
@@ -3250,24 +3264,30 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     std::vector<int64_t> hb(C + 1);
     for (int c = 0; c <= C; ++c) to_host_async(&hb[c], row_ptr + V.rbase[c], 1, s);
     CT_CHECK_CUDA(cudaStreamSynchronize(s));
-    int64_t *rel = (int64_t *)dmalloc((size_t)(n + C) * sizeof(int64_t), s);
     auto blocks = std::make_shared<SharedBlocks>(s);
-    blocks->p[0] = rel;
-    blocks->p[1] = all.col;
-    blocks->p[2] = all.dist;
+    blocks->p[0] = dmalloc((size_t)(n + C) * sizeof(int64_t), s);
+    int64_t *rel = (int64_t *)blocks->p[0];
+    int32_t *colp = all.col;
+    float *distp = all.dist;
+    blocks->p[1] = colp;
+    blocks->p[2] = distp;
+    all.col = nullptr;  // the blocks own them now
+    all.dist = nullptr;
     for (int c = 0; c < C; ++c) {
         const int64_t nc1 = trees[c]->n + 1, o = V.rbase[c] + c;
         k_rel_rows<<<grid_for(nc1, 256), 256, 0, s>>>(nc1, row_ptr + V.rbase[c], rel + o);
         CT_COUNT_LAUNCH();
         QueryOut &q = outs[c];
         q.row_ptr = rel + o;
-        q.col = all.col + hb[c];
-        q.dist = all.dist + hb[c];
+        q.col = colp + hb[c];
+        q.dist = distp + hb[c];
         q.nnz = hb[c + 1] - hb[c];
         q.stats = all.stats;
         q.shared = blocks;
     }
     CT_LAUNCH_CHECK();
+    all.row_ptr = nullptr;
+    all_guard.armed = false;
     dfree(row_ptr, s);  // stream ordered: after the relative copies
 }
 
@@ -3706,6 +3726,20 @@ PlanImpl *plan_create(int C, const ct_tree *const *trees, const QParams *qps, in
     const int G = p.G;
     // sizing query (the batch's own exact query, FP32 tiles)
     std::vector<QueryOut> outs((size_t)C);
+    struct OutsGuard {  // the sizing query's CSRs are released on every path
+        std::vector<QueryOut> &o;
+        cudaStream_t s;
+        ~OutsGuard() {
+            for (auto &q : o) {
+                if (!q.shared) {
+                    dfree(q.row_ptr, s);
+                    dfree(q.col, s);
+                    dfree(q.dist, s);
+                }
+                q = QueryOut();
+            }
+        }
+    } outs_guard{outs, s};
     query_multi(C, trees, qps, s, outs.data(), 0, pred, nullptr);
     const int64_t n_cand = outs[0].stats.candidates;
     int64_t nnz = 0, nbig = 0, big_entries = 0;
@@ -3723,14 +3757,6 @@ PlanImpl *plan_create(int C, const ct_tree *const *trees, const QParams *qps, in
                 }
             }
         }
-    }
-    for (auto &o : outs) {
-        if (!o.shared) {
-            dfree(o.row_ptr, s);
-            dfree(o.col, s);
-            dfree(o.dist, s);
-        }
-        o = QueryOut();
     }
     const double m = std::max(0.0, (double)margin);
     p.big_rows = (int)std::min<int64_t>((int64_t)std::ceil((double)nbig * (1.0 + m)) + 16, 0x7fffffff);

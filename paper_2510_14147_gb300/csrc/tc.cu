@@ -8,7 +8,8 @@ namespace ct {
 namespace {
 
 __global__ void __launch_bounds__(128) k_tc_selftest(const uint16_t *__restrict__ A, const uint16_t *__restrict__ B,
-                                                     int fp16, float *__restrict__ D, int32_t *__restrict__ status) {
+                                                     int fp16, float *__restrict__ D, int32_t *__restrict__ status,
+                                                     int withhold) {
     __shared__ __align__(1024) unsigned char sA[128 * 256];
     __shared__ __align__(1024) unsigned char sB[32 * 256];
     __shared__ uint32_t tslot;
@@ -31,7 +32,7 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const uint16_t *__restrict_
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tslot;
-    if (tid == 0) {
+    if (tid == 0 && !withhold) {  // withheld (a test): no MMA and no commit, so the wait below runs out
         const uint32_t idesc = fp16 ? tc::idesc_f16_f32(128, 32) : tc::idesc_bf16_f32(128, 32);
         for (int s = 0; s < 8; ++s) {
             const uint64_t ad = tc::smem_desc(tc::smem_u32(sA) + s * 256, tc::kLBO, tc::kSBO);
@@ -58,10 +59,10 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const uint16_t *__restrict_
 
 }  // namespace
 
-void tc_selftest(const void *A, const void *B, int fp16, float *D, cudaStream_t s) {
+void tc_selftest(const void *A, const void *B, int fp16, float *D, cudaStream_t s, int withhold) {
     DBuf<int32_t> status(1, s);
     CT_CHECK_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int32_t), s));
-    k_tc_selftest<<<1, 128, 0, s>>>((const uint16_t *)A, (const uint16_t *)B, fp16, D, status.p);
+    k_tc_selftest<<<1, 128, 0, s>>>((const uint16_t *)A, (const uint16_t *)B, fp16, D, status.p, withhold);
     CT_COUNT_LAUNCH();
     CT_LAUNCH_CHECK();
     int32_t h = 0;

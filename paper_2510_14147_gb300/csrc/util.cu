@@ -22,6 +22,11 @@ const char *get_error() { return g_err; }
 static std::mutex g_pool_mu;
 static bool g_pool_ready[64] = {false};
 
+// Test hook: when positive, the allocation that brings it to zero fails as if
+// the device were out of memory (host-side fault injection).
+static std::atomic<int64_t> g_fail_alloc{0};
+void set_fail_alloc(int64_t k) { g_fail_alloc.store(k > 0 ? k : 0); }
+
 void *dmalloc(size_t bytes, cudaStream_t s) {
     int dev = 0;
     CT_CHECK_CUDA(cudaGetDevice(&dev));
@@ -37,6 +42,10 @@ void *dmalloc(size_t bytes, cudaStream_t s) {
     }
     void *p = nullptr;
     if (!bytes) return nullptr;
+    if (g_fail_alloc.load(std::memory_order_relaxed) > 0 && g_fail_alloc.fetch_sub(1) == 1) {
+        set_error("device allocation of %zu bytes failed (injected)", bytes);
+        throw Error{CT_ENOMEM};
+    }
     cudaError_t e = cudaMallocAsync(&p, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();

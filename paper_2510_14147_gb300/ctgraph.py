@@ -164,6 +164,12 @@ def _load():
         lib.ct_plan_set_wait.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
         lib.ct_plan_free.restype = None
         lib.ct_plan_free.argtypes = [C.c_void_p]
+        lib.ct_selftest_tc_timeout.restype = C.c_int
+        lib.ct_selftest_tc_timeout.argtypes = [C.c_void_p]
+        lib.ct_debug_fail_alloc.restype = C.c_int
+        lib.ct_debug_fail_alloc.argtypes = [C.c_int64]
+        lib.ct_debug_pool_used.restype = C.c_int
+        lib.ct_debug_pool_used.argtypes = [P(C.c_uint64)]
         lib.ct_debug_guard_rows.restype = C.c_int
         lib.ct_debug_guard_rows.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
         lib.ct_tree_save.restype = C.c_int
@@ -434,6 +440,24 @@ def ct_debug_guard_rows(rows=None, count=None):
         _check(_load().ct_debug_guard_rows(None, None, 0))
     else:
         _check(_load().ct_debug_guard_rows(rows.data_ptr(), count.data_ptr(), rows.numel()))
+
+
+def ct_selftest_tc_timeout(stream=None):
+    """The tensor-core self-test with its MMA withheld: raises CtError with
+    CT_ETIMEOUT once the bounded completion wait runs out."""
+    _check(_load().ct_selftest_tc_timeout(C.c_void_p(_stream(stream))))
+
+
+def ct_debug_fail_alloc(k: int):
+    """Test hook: the k-th next device allocation of the library fails (0: off)."""
+    _check(_load().ct_debug_fail_alloc(int(k)))
+
+
+def ct_debug_pool_used() -> int:
+    """Bytes in use in the device's default memory pool (after a device sync)."""
+    b = C.c_uint64()
+    _check(_load().ct_debug_pool_used(C.byref(b)))
+    return int(b.value)
 
 
 def ct_tree_save(tree: Tree, path: str):
