@@ -19,6 +19,8 @@ Functions and the paper passages they follow:
   tree_query            -- Algorithm 3 (stack query with vertex-triple radii)
   check_tree            -- cover-tree invariants (Sec. III) + radius bound
                            (Sec. IV-A vertex triple)
+  voronoi / landmark_graph -- Voronoi cells of landmark centres and the
+                           ε-graph through ε-ghosts (Sec. IV-D, Lemma 1)
 """
 from __future__ import annotations
 
@@ -98,6 +100,11 @@ def _load():
             lib.orc_tree_query_rows.restype = C.POINTER(_Csr)
             lib.orc_tree_query_rows.argtypes = [C.POINTER(_Space), C.POINTER(_Tree), C.c_double, C.c_int32,
                                                 C.c_void_p, C.c_int64]
+            lib.orc_voronoi.restype = None
+            lib.orc_voronoi.argtypes = [C.POINTER(_Space), C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]
+            lib.orc_landmark_graph.restype = C.POINTER(_Csr)
+            lib.orc_landmark_graph.argtypes = [C.POINTER(_Space), C.c_void_p, C.c_int32, C.c_double, C.c_int32,
+                                               C.c_double]
             lib.orc_check_tree.restype = C.c_int32
             lib.orc_check_tree.argtypes = [C.POINTER(_Space), C.POINTER(_Tree), C.c_double,
                                            C.c_char_p, C.c_int32]
@@ -208,6 +215,24 @@ def brute_rows(space: Space, eps: float, rows, include_self: bool = False) -> di
     r = np.ascontiguousarray(rows, dtype=np.int64)
     return _take_csr(_load().orc_brute_rows(C.byref(space.c), float(eps), int(include_self),
                                             r.ctypes.data, r.size))
+
+
+def voronoi(space: Space, centres):
+    """(cell, dmin): index of each point's nearest centre (lowest among
+    equals) and its distance, FP64 (landmark step 1, Sec. IV-D)."""
+    c = np.ascontiguousarray(centres, dtype=np.int64)
+    cell = np.zeros(max(space.n, 1), np.int32)
+    dmin = np.zeros(max(space.n, 1), np.float64)
+    _load().orc_voronoi(C.byref(space.c), c.ctypes.data, int(c.size), cell.ctypes.data, dmin.ctypes.data)
+    return cell[:space.n], dmin[:space.n]
+
+
+def landmark_graph(space: Space, centres, eps: float, include_self: bool = False, factor: float = 2.0) -> dict:
+    """The ε-graph by Voronoi cells and ε-ghosts (Sec. IV-D, Lemma 1): each
+    row by brute force over its cell's points and ghosts."""
+    c = np.ascontiguousarray(centres, dtype=np.int64)
+    return _take_csr(_load().orc_landmark_graph(C.byref(space.c), c.ctypes.data, int(c.size), float(eps),
+                                                int(include_self), float(factor)))
 
 
 class Tree:

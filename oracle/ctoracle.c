@@ -307,6 +307,74 @@ orc_csr *orc_brute_rows(const orc_space *sp, double eps, int32_t include_self, c
     return o;
 }
 
+/* --------------------------------------------------------- landmarks */
+
+/* Voronoi cells of the centres (point indices centres[0..m)): cell[i] is the
+ * index k of the nearest centre (the lowest k among equals) and dmin[i] its
+ * distance -- step (1) of the landmark construction (Sec. IV-D). */
+void orc_voronoi(const orc_space *sp, const int64_t *centres, int32_t m, int32_t *cell, double *dmin)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < sp->n; ++i) {
+        int32_t best = 0;
+        double bd = metric_dist(sp, i, centres[0]);
+        for (int32_t k = 1; k < m; ++k) {
+            double d = metric_dist(sp, i, centres[k]);
+            if (d < bd) { bd = d; best = k; }
+        }
+        cell[i] = best;
+        dmin[i] = bd;
+    }
+}
+
+/* The ε-graph by landmarks (Sec. IV-D, Algorithms 5 and 6 on one processor):
+ * Voronoi cells V_k of the centres; the ε-ghosts of V_k are the points p
+ * outside it with d(p, c_k) <= d(p, C) + factor * eps (Lemma 1: factor 2
+ * catches every p with a neighbour in V_k); each point's row is the brute
+ * force over its own cell and that cell's ghosts.  factor < 2 is for tests
+ * that show Lemma 1's bound is needed. */
+orc_csr *orc_landmark_graph(const orc_space *sp, const int64_t *centres, int32_t m, double eps,
+                            int32_t include_self, double factor)
+{
+    int64_t n = sp->n;
+    double eps2 = eps * eps;
+    int32_t *cell = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    double *dmin = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    if (n) orc_voronoi(sp, centres, m, cell, dmin);
+    /* members of every cell: its own points and its ghosts */
+    vec_t *mem = (vec_t *)calloc((size_t)m, sizeof(vec_t));
+    for (int64_t p = 0; p < n; ++p) {
+        for (int32_t k = 0; k < m; ++k) {
+            if (k == cell[p]) { vec_push(&mem[k], p, 0.0); continue; }
+            double d = metric_dist(sp, p, centres[k]);
+            if (d <= dmin[p] + factor * eps) vec_push(&mem[k], p, 1.0);
+        }
+    }
+    /* rows of each cell's own points, by brute force over the cell's members */
+    vec_t *rows = (vec_t *)calloc((size_t)(n ? n : 1), sizeof(vec_t));
+    int64_t evals = 0;
+    for (int32_t k = 0; k < m; ++k) {
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : evals)
+        for (int64_t a = 0; a < mem[k].len; ++a) {
+            int64_t p = mem[k].col[a];
+            if (mem[k].dist[a] != 0.0) continue;   /* a ghost: its row is made in its own cell */
+            for (int64_t b = 0; b < mem[k].len; ++b) {
+                int64_t q = mem[k].col[b];
+                if (q == p && !include_self) continue;
+                double d;
+                evals++;
+                if (edge_pred(sp, p, q, eps, eps2, &d)) vec_push(&rows[p], q, d);
+            }
+        }
+        free(mem[k].col);
+        free(mem[k].dist);
+    }
+    free(mem); free(cell); free(dmin);
+    orc_csr *o = assemble(n, rows);
+    o->dist_evals = evals;
+    return o;
+}
+
 /* ------------------------------------------------------------- cover tree */
 
 /* Flat tree export, shared format between this oracle and the GPU library's
