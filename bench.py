@@ -667,6 +667,40 @@ def run_single(args, wl, world, rank, dist):
                  "speedup": times["independent"] / times["sweep"],
                  "note": "one tree, built once outside the timed region; queries of the form above"}
 
+    # the landmark form (Voronoi cells of m random centres, Lemma 1 ghosts, a
+    # tree per cell, one batched query) against the step above, same form
+    landmark = None
+    if kind == "points" and not args.no_landmark:
+        m = args.landmark_m
+        centres = np.random.default_rng(60).choice(n, size=m, replace=False)
+        lm_kw = dict(points=dev, leaf_size=zeta, precision=precision, use_predictor=learned,
+                     predictor=pred if learned else None, upper_triangle=upper, stream=stream)
+        with torch.cuda.stream(stream):
+            ref = step(keep=True)
+            c, info = cg.eps_graph_query_landmark(centres, eps, **lm_kw)
+            same = csr_equal(c, ref)
+            c.free()
+            ref.free()
+        if not same:
+            raise RuntimeError("the landmark form's CSR differs from the query's")
+        barrier()
+        cg.ct_profile_reset()
+        cg.ct_profile_enable(True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                cg.eps_graph_query_landmark(centres, eps, **lm_kw)[0].free()
+        b.record(stream)
+        barrier()
+        cg.ct_profile_enable(False)
+        lp = cg.ct_profile_read()
+        tl = a.elapsed_time(b) / args.steps
+        landmark = {"m": m, "centres": "uniform random points (seed 60)", "ms_per_step": tl,
+                    "value": nnz / (tl / 1e3), "csr_identical_to_default_form": bool(same),
+                    "stage_ms": {k: v[0] / max(v[1], 1) for k, v in lp.items()}, "partition": info,
+                    "speedup_over_one_tree": (t_ms / args.steps) / tl}
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -722,7 +756,7 @@ def run_single(args, wl, world, rank, dist):
             "roofline": roofline(prof, st, wl, args.workload, peaks, dim, mean_len),
             "traversal": traversal_roofline(prof, st, n, dim, args.workload, peaks) if kind == "points" else None,
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "library": cg.library_path(),
-            "forms": forms, "sweep": sweep}
+            "forms": forms, "sweep": sweep, "landmark": landmark}
     if fit_info:
         line["learned"] = fit_info
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1015,6 +1049,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip timing the three-radius sweep")
     ap.add_argument("--no-plan", action="store_true", help="clouds: skip timing the plan (graph replay)")
+    ap.add_argument("--no-landmark", action="store_true", help="skip timing the landmark form")
+    ap.add_argument("--landmark-m", type=int, default=60, help="landmark centres (the paper's m = 60)")
     ap.add_argument("--fit-steps", type=int, default=1500)
     ap.add_argument("--order-radius", action="store_true",
                     help="learned forms: walk groups by radius instead of predicted walk length")

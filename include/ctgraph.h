@@ -251,6 +251,33 @@ void ct_plan_free(ct_plan *plan);
 ct_status eps_graph_query_sweep(const ct_tree *tree, int32_t n_eps, const double *eps,
                                 const ct_query_opts *opts, ct_stream stream, ct_csr *outs);
 
+/* Sizes of the landmark form's partition (eps_graph_query_landmark). */
+typedef struct {
+    int64_t cells;         /* m */
+    int64_t members;       /* points over all cells: each point in its own cell plus its ghost cells */
+    int64_t ghosts;        /* members - n */
+    int64_t largest_cell;  /* members of the largest cell */
+} ct_landmark_info;
+
+/* The ε-graph through landmarks (Sec. IV-D, the paper's Voronoi-cell and
+ * ghost-query algorithms on one GPU): the points' Voronoi cells of the m
+ * centres (host int64 point indices, e.g. drawn at random as the paper
+ * does); the ε-ghosts of every cell by Lemma 1 -- the points p outside it
+ * with d(p, c_k) <= d(p, C) + 2 eps -- so that every neighbour of a cell's
+ * point lies in the cell or among its ghosts; a cover tree per cell over its
+ * points and ghosts (`bopts`), all cells queried as one batch with `qopts`
+ * (the forms of eps_graph_query); each point's row from its own cell.  The
+ * output equals eps_graph_query's on the whole set (the same entries and
+ * distances), in library-owned memory (csr_free).  `points` as for ct_build
+ * (L2 or Hamming; device memory).  info (may be NULL) receives the sizes.
+ * n = 0 gives the empty graph.  Synchronises `stream`.  Errors: CT_EINVAL
+ * (NULL arguments, m outside [1, n], a centre out of range, options as
+ * eps_graph_query),
+ * CT_EUNSUPPORTED (edit distance), CT_ENOMEM, CT_ECUDA. */
+ct_status eps_graph_query_landmark(const ct_points *points, const int64_t *centres, int32_t m, double eps,
+                                  const ct_build_opts *bopts, const ct_query_opts *qopts, ct_stream stream,
+                                  ct_csr *out, ct_landmark_info *info);
+
 /* Writes a tree to a file at `path` (a header with the sizes, every device
  * array of the tree, and a 64-bit FNV-1a checksum), so that a later process
  * can query it without building it again.  Synchronises the tree's stream.

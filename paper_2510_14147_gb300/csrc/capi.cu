@@ -27,6 +27,8 @@ ct_tree *load_tree(const char *path, cudaStream_t s);
 void sweep_filter(const ct_tree *t, const QParams &qs, const QParams &qd, const QueryOut &src, cudaStream_t s,
                   QueryOut &out);
 void set_guard_rows(int32_t *rows, unsigned long long *count, int64_t cap);
+void landmark_query(const ct_points *pts, const int64_t *centres, int m, double eps, int zeta,
+                    const ct_query_opts *opts, cudaStream_t s, QueryOut &out, ct_landmark_info *info);
 }  // namespace ct
 
 namespace {
@@ -277,6 +279,41 @@ void ct_plan_free(ct_plan *plan) {
     if (!plan) return;
     ct::plan_free(plan->impl);
     delete plan;
+}
+
+ct_status eps_graph_query_landmark(const ct_points *points, const int64_t *centres, int32_t m, double eps,
+                                  const ct_build_opts *bopts, const ct_query_opts *qopts, ct_stream stream,
+                                  ct_csr *out, ct_landmark_info *info) {
+    if (out) std::memset(out, 0, sizeof(*out));
+    if (info) std::memset(info, 0, sizeof(*info));
+    cudaStream_t s = (cudaStream_t)stream;
+    ct::QueryOut q;
+    ct_status st = guarded([&] {
+        if (!points || !out || (m > 0 && !centres)) CT_FAIL(CT_EINVAL, "points, centres and out must not be NULL");
+        const ct_points &p = *points;
+        if (p.n < 0 || p.n >= 0x7f7f7f00LL) CT_FAIL(CT_EINVAL, "bad n");
+        if (p.metric != CT_L2_F32 && p.metric != CT_HAMMING_B1)
+            CT_FAIL(CT_EUNSUPPORTED, "the landmark form takes L2 points or Hamming rows");
+        if (p.dim < 1 || p.dim > 4096) CT_FAIL(CT_EINVAL, "dim must be in [1, 4096]");
+        if (p.n > 0 && !p.data) CT_FAIL(CT_EINVAL, "data is NULL");
+        if (!(eps >= 0.0)) CT_FAIL(CT_EINVAL, "eps must be >= 0 (got %g)", eps);
+        ct_query_opts o = qopts ? *qopts : default_query_opts();
+        if (o.precision < 0 || o.precision > 2) CT_FAIL(CT_EINVAL, "precision must be 0, 1 or 2");
+        if (o.precision == 1 && p.metric != CT_L2_F32) CT_FAIL(CT_EINVAL, "the tensor-core filter applies to L2 only");
+        if (o.use_predictor && !o.predictor) CT_FAIL(CT_EINVAL, "use_predictor set without a predictor");
+        if (o.include_self != 0 && o.include_self != 1) CT_FAIL(CT_EINVAL, "include_self must be 0 or 1");
+        if (o.upper_triangle != 0 && o.upper_triangle != 1) CT_FAIL(CT_EINVAL, "upper_triangle must be 0 or 1");
+        const int zeta = bopts && bopts->leaf_size > 0 ? bopts->leaf_size : 32;
+        ct::g_launches = 0;
+        ct::landmark_query(&p, centres, m, eps, zeta, &o, s, q, info);
+        q.stats.kernel_launches = ct::g_launches;
+        fill_csr(out, p.n, q, s);
+    });
+    if (st != CT_OK) {
+        release_query_out(q, s);
+        if (out) std::memset(out, 0, sizeof(*out));
+    }
+    return st;
 }
 
 ct_status ct_tree_save(const ct_tree *tree, const char *path) {

@@ -1397,34 +1397,46 @@ __global__ void k_group_cand_copy(int nseg, const int32_t *__restrict__ seg_grou
     const uint32_t *src = pool + seg_begin[i];
     for (int k = lane; k < c; k += 32) gcand[base + k] = src[k];
 }
-// Upper-triangle form: each group keeps the candidate blocks that reach its
-// first position or beyond (the pairs with earlier points are evaluated by
-// their own groups); a warp per group compacts its range in place, in order.
-__global__ void k_half_cands(const __grid_constant__ Views V, int G, const int64_t *__restrict__ gbegin,
-                             int32_t *__restrict__ gcount, uint32_t *__restrict__ gcand, int64_t cap) {
-    const int gg = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (gg >= G) return;
-    const int c = cloud_of_group(V, gg);
-    if (!V.qp[c].half) return;
-    const TreeView &tv = V.tv[c];
-    const int qb = tv.group_begin[gg - V.gbase[c]];
-    const int64_t b = gbegin[gg];
-    const int n = gcount[gg];
-    if (b + n > cap) return;  // a range that was not copied (a plan's overflow, reported there)
-    int w = 0;
-    for (int i0 = 0; i0 < n; i0 += 32) {
-        const int i = i0 + lane;
+// The copy in the upper-triangle form: a group keeps the candidate blocks
+// that reach its first position or beyond (the pairs with earlier points are
+// evaluated by their own groups); each warp ballots a segment's blocks 32 at
+// a time and appends the kept ones, so a group's kept count ends in gfill.
+// With nseg_dev (a plan) the segment count is read on the device and the
+// destinations are checked against cand_cap.
+__global__ void k_group_cand_copy_half(const __grid_constant__ Views V, int nseg, const int32_t *__restrict__ nseg_dev,
+                                       int64_t seg_cap, const int32_t *__restrict__ seg_group,
+                                       const int64_t *__restrict__ seg_begin, const int32_t *__restrict__ seg_count,
+                                       const int64_t *__restrict__ goff, int32_t *__restrict__ gfill,
+                                       const uint32_t *__restrict__ pool, uint32_t *__restrict__ gcand,
+                                       int64_t cand_cap, int32_t *__restrict__ err) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t ns = nseg_dev ? min((int64_t)*nseg_dev, seg_cap) : (int64_t)nseg;
+    if (i >= ns) return;
+    const int gg = seg_group[i], c = seg_count[i];
+    const int cl = cloud_of_group(V, gg);
+    const TreeView &tv = V.tv[cl];
+    const bool half = V.qp[cl].half != 0;
+    const int qb = tv.group_begin[gg - V.gbase[cl]];
+    const uint32_t *src = pool + seg_begin[i];
+    for (int k0 = 0; k0 < c; k0 += 32) {
+        const int k = k0 + lane;
         uint32_t v = 0u;
         bool keep = false;
-        if (i < n) {
-            v = gcand[b + i];
-            keep = tv.node_begin[v] + tv.node_count[v] > qb;
+        if (k < c) {
+            v = src[k];
+            keep = !half || tv.node_begin[v] + tv.node_count[v] > qb;
         }
-        const unsigned m = __ballot_sync(0xffffffffu, keep);  // every lane has read before any writes
-        if (keep) gcand[b + w + __popc(m & lanemask_lt())] = v;
-        w += __popc(m);
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        int64_t base = 0;
+        if (lane == 0 && m) base = goff[gg] + atomicAdd(gfill + gg, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base + __popc(m) > cand_cap) {  // a plan's overflow (reported; the producer skips the group)
+            if (lane == 0) atomicOr(err, 128);
+            return;
+        }
+        if (keep) gcand[base + __popc(m & lanemask_lt())] = v;
     }
-    if (lane == 0) gcount[gg] = w;
 }
 
 __global__ void k_iota(int n, int32_t *__restrict__ out) {
@@ -3012,15 +3024,19 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
         k_group_cand_counts<<<grid_for(nseg, 256), 256, 0, s>>>(nseg, seg_group.p, seg_count.p, gseg_count.p);
         CT_COUNT_LAUNCH();
         exclusive_scan_i32_to_i64(gseg_count.p, gseg_begin.p, G, gseg_begin.p + G, s);
-        k_group_cand_copy<<<grid_for((int64_t)nseg * 32, 256), 256, 0, s>>>(nseg, seg_group.p, seg_begin.p, seg_count.p,
-                                                                          gseg_begin.p, gfill.p, pool.p, gcand.p);
+        if (any_half)
+            k_group_cand_copy_half<<<grid_for((int64_t)nseg * 32, 256), 256, 0, s>>>(
+                V, nseg, nullptr, 0, seg_group.p, seg_begin.p, seg_count.p, gseg_begin.p, gfill.p, pool.p, gcand.p,
+                INT64_MAX, err);
+        else
+            k_group_cand_copy<<<grid_for((int64_t)nseg * 32, 256), 256, 0, s>>>(nseg, seg_group.p, seg_begin.p,
+                                                                              seg_count.p, gseg_begin.p, gfill.p,
+                                                                              pool.p, gcand.p);
         CT_COUNT_LAUNCH();
         k_iota<<<grid_for(G, 256), 256, 0, s>>>(G, gseg_group.p);
         CT_COUNT_LAUNCH();
-        if (any_half) {
-            k_half_cands<<<grid_for((int64_t)G * 32, 256), 256, 0, s>>>(V, G, gseg_begin.p, gseg_count.p, gcand.p, n_cand);
-            CT_COUNT_LAUNCH();
-        }
+        if (any_half)  // the groups' kept counts
+            CT_CHECK_CUDA(cudaMemcpyAsync(gseg_count.p, gfill.p, G * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
         CT_LAUNCH_CHECK();
         nseg = G;
     }
@@ -3613,12 +3629,17 @@ void plan_enqueue(PlanImpl &p, cudaStream_t s) {
                                                               p.gcount.p);
     CT_COUNT_LAUNCH();
     exclusive_scan_i32_to_i64_into(p.gcount.p, p.gbegin.p, G, p.gbegin.p + G, p.sums.p, s);
-    k_plan_cand_copy<<<grid_for(p.seg_cap * 32, 256), 256, 0, s>>>(P.nseg, p.seg_cap, P.seg_group, P.seg_begin,
-                                                                  P.seg_count, p.gbegin.p, p.gfill.p, P.data,
-                                                                  p.gcand.p, p.cand_cap, err);
-    CT_COUNT_LAUNCH();
-    if (p.any_half) {  // (ranges past the plan's capacity are never read: the producer skips them)
-        k_half_cands<<<grid_for((int64_t)G * 32, 256), 256, 0, s>>>(V, G, p.gbegin.p, p.gcount.p, p.gcand.p, p.cand_cap);
+    if (p.any_half) {
+        k_group_cand_copy_half<<<grid_for(p.seg_cap * 32, 256), 256, 0, s>>>(
+            V, 0, P.nseg, p.seg_cap, P.seg_group, P.seg_begin, P.seg_count, p.gbegin.p, p.gfill.p, P.data, p.gcand.p,
+            p.cand_cap, err);
+        CT_COUNT_LAUNCH();
+        // the groups' kept counts (ranges past the plan's capacity are never read: the producer skips them)
+        CT_CHECK_CUDA(cudaMemcpyAsync(p.gcount.p, p.gfill.p, (size_t)G * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    } else {
+        k_plan_cand_copy<<<grid_for(p.seg_cap * 32, 256), 256, 0, s>>>(P.nseg, p.seg_cap, P.seg_group, P.seg_begin,
+                                                                      P.seg_count, p.gbegin.p, p.gfill.p, P.data,
+                                                                      p.gcand.p, p.cand_cap, err);
         CT_COUNT_LAUNCH();
     }
     // 3. count pass: one persistent launch producing and consuming the work queue

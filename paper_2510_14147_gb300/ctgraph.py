@@ -63,6 +63,10 @@ class ct_query_stats(C.Structure):
                                            "leaf_rows", "guard_band", "lev_columns")]
 
 
+class ct_landmark_info(C.Structure):
+    _fields_ = [(f, C.c_int64) for f in ("cells", "members", "ghosts", "largest_cell")]
+
+
 class ct_fit_opts(C.Structure):
     _fields_ = [("steps", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("include_self", C.c_int32),
                 ("seed", C.c_uint64)]
@@ -172,6 +176,9 @@ def _load():
         lib.ct_debug_pool_used.argtypes = [P(C.c_uint64)]
         lib.ct_debug_guard_rows.restype = C.c_int
         lib.ct_debug_guard_rows.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+        lib.eps_graph_query_landmark.restype = C.c_int
+        lib.eps_graph_query_landmark.argtypes = [P(ct_points), C.c_void_p, C.c_int32, C.c_double, P(ct_build_opts),
+                                                 P(ct_query_opts), C.c_void_p, P(ct_csr), P(ct_landmark_info)]
         lib.ct_tree_save.restype = C.c_int
         lib.ct_tree_save.argtypes = [C.c_void_p, C.c_char_p]
         lib.ct_tree_load.restype = C.c_int
@@ -458,6 +465,36 @@ def ct_debug_pool_used() -> int:
     b = C.c_uint64()
     _check(_load().ct_debug_pool_used(C.byref(b)))
     return int(b.value)
+
+
+def eps_graph_query_landmark(centres, eps: float, points=None, bits=None, leaf_size: int = 32,
+                             precision: int = 0, use_predictor: bool = False, include_self: bool = False,
+                             predictor=None, upper_triangle: bool = False, stream=None):
+    """The ε-graph through Voronoi cells of `centres` (host sequence of point
+    indices) and their ε-ghosts; returns (CSR, info dict).  ``points``: CUDA
+    fp32 (n, dim); or ``bits=(rows, dim)`` as for ct_build."""
+    import torch
+    lib = _load()
+    p = ct_points()
+    if points is not None:
+        points = points.contiguous()
+        p.metric, p.dim, p.n, p.data, p.offsets = CT_L2_F32, points.shape[1], points.shape[0], \
+            points.data_ptr() or None, None
+        keep = points
+    else:
+        rows, dim = bits
+        rows = rows.contiguous()
+        p.metric, p.dim, p.n, p.data, p.offsets = CT_HAMMING_B1, int(dim), rows.shape[0], rows.data_ptr() or None, None
+        keep = rows
+    c = np.ascontiguousarray(centres, dtype=np.int64)
+    out, info = ct_csr(), ct_landmark_info()
+    b = ct_build_opts(leaf_size, 0)
+    o = _opts(precision, use_predictor, include_self, predictor, upper_triangle)
+    _check(lib.eps_graph_query_landmark(C.byref(p), c.ctypes.data if c.size else None, int(c.size), float(eps),
+                                        C.byref(b), C.byref(o), C.c_void_p(_stream(stream)), C.byref(out),
+                                        C.byref(info)))
+    del keep
+    return CSR(out), {f: int(getattr(info, f)) for f, _ in ct_landmark_info._fields_}
 
 
 def ct_tree_save(tree: Tree, path: str):
