@@ -18,6 +18,8 @@ namespace {
 struct Pending {
     std::string name;
     cudaEvent_t a, b;
+    bool closed = false;  // its end event is recorded
+    bool done = false;    // added to the table, events released
 };
 struct Acc {
     double ms = 0;
@@ -46,12 +48,22 @@ ProfScope::ProfScope(const char *name, cudaStream_t s) : s_(s), active_(prof_on(
 ProfScope::~ProfScope() {
     if (!active_) return;
     cudaEventRecord(t_pending[idx_].b, s_);
+    t_pending[idx_].closed = true;
 }
 
+// Scopes may nest (a stage that calls another entry point): only closed
+// scopes are added; entries stay in place (their indices are held by open
+// scopes) until every scope of the thread is closed.
 void prof_flush() {
     if (t_pending.empty()) return;
     std::lock_guard<std::mutex> lk(g_mu);
+    bool all_done = true;
     for (auto &p : t_pending) {
+        if (p.done) continue;
+        if (!p.closed) {
+            all_done = false;
+            continue;
+        }
         float ms = 0.f;
         if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
             Acc &a = g_acc[p.name];
@@ -60,8 +72,9 @@ void prof_flush() {
         }
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
+        p.done = true;
     }
-    t_pending.clear();
+    if (all_done) t_pending.clear();
 }
 
 }  // namespace ct

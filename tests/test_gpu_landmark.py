@@ -99,3 +99,30 @@ def test_landmark_rejects_bad_arguments():
     got, info = cg.eps_graph_query_landmark([0], 0.1, points=empty)      # n = 0: the empty graph
     assert got.nnz == 0 and got.row_ptr.cpu().tolist() == [0]
     got.free()
+
+
+def test_landmark_with_stage_timing_enabled():
+    """The landmark form's stages contain whole builds and queries (scopes
+    that nest): timing them must work and leave the results unchanged."""
+    import torch
+    cg = _cg()
+    x = I.gmm_embedded(3000, dim=16, intrinsic=4, n_centres=3, seed=8)
+    xd = torch.from_numpy(x).cuda()
+    eps = float(np.float32(np.quantile(oracle.brute_rows(oracle.Space(points=x), 1e30, [0])["dist"], 0.03)))
+    cg.ct_profile_reset()
+    cg.ct_profile_enable(True)
+    try:
+        for _ in range(2):
+            got, _ = cg.eps_graph_query_landmark(np.arange(0, 3000, 150), eps, points=xd)
+            got.free()
+    finally:
+        cg.ct_profile_enable(False)
+    prof = cg.ct_profile_read()
+    assert prof["landmark_build"][1] == 2 and prof["landmark_query"][1] == 2 and prof["build"][1] == 40
+    t = cg.ct_build(points=xd)
+    ref = cg.eps_graph_query(t, eps)
+    got, _ = cg.eps_graph_query_landmark(np.arange(0, 3000, 150), eps, points=xd)
+    _same(got, ref)
+    got.free()
+    ref.free()
+    t.free()
