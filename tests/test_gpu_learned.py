@@ -233,6 +233,49 @@ def test_learned_form_gains_over_two_pass():
         h.free()
 
 
+def test_learned_form_is_faster_than_two_pass():
+    """The network's gain in time: on a fixed 300k x 64 mixture (eps for about
+    60 neighbours, tensor-core filter), the one-pass emit's stages -- the
+    count pass writing the edges, the predictor's forward pass and the
+    compaction -- take less device time than the two-pass form's count and
+    emit passes.  Stage times are CUDA events around each stage's launches
+    (the library's stage timer), the median of five alternating runs of
+    each form, whose CSRs are equal."""
+    cg = _cg()
+    x = I.gmm_embedded(300000, dim=64, intrinsic=8, n_centres=60, seed=41)
+    xf = I.gmm_embedded(300000, dim=64, intrinsic=8, n_centres=60, seed=42)
+    d = oracle.brute_rows(oracle.Space(points=x), 1e30, [0, 1, 2, 3])["dist"]
+    eps = float(np.float32(np.quantile(d, 60.0 / 300000)))
+    t, tf = _tree(points=x), _tree(points=xf)
+    p = _fit(tf, eps, steps=1500)
+    one_stages = ("leaf_count_tc", "predict", "compact", "reemit")
+    two_stages = ("leaf_count_tc", "leaf_emit")
+    times = {True: [], False: []}
+    ref = None
+    try:
+        for rep in range(6):
+            for learned in (False, True):
+                cg.ct_profile_reset()
+                cg.ct_profile_enable(True)
+                try:
+                    got = _query(t, eps, precision=1, use_predictor=learned, predictor=p if learned else None)
+                finally:
+                    cg.ct_profile_enable(False)
+                prof = cg.ct_profile_read()
+                if ref is None:
+                    ref = got
+                _same(got, ref)
+                if rep:                                      # the first run of each form warms up
+                    times[learned].append(sum(prof.get(k, (0.0, 0))[0]
+                                              for k in (one_stages if learned else two_stages)))
+    finally:
+        cg.ct_profile_enable(False)
+    one, two = float(np.median(times[True])), float(np.median(times[False]))
+    assert one < two, "learned %.3f ms, two-pass %.3f ms" % (one, two)
+    for h in (p, t, tf):
+        h.free()
+
+
 def test_unfitted_predictor_is_rejected():
     cg = _cg()
     t = _tree(points=I.uniform_cube(100, 3, seed=0))
