@@ -102,7 +102,8 @@ struct Views {
     QParams qp[kMaxClouds];
     int16_t item_len[kMaxClouds];  // candidate blocks per work item
     uint8_t use_tc[kMaxClouds];    // leaf kernel of the count pass: tensor-core tiles (1) or FP32 tiles (0)
-    // tensor-core filter rows: a TMA map of the fp16 rows, their squared norms, {s, s eps_up}
+    // tensor-core filter rows: the fp16 rows, a TMA map of them, their squared norms, {s, s eps_up}
+    const uint4 *h16[kMaxClouds];
     const float *n16[kMaxClouds];
     const float *s16[kMaxClouds];
     CUtensorMap tmap[kMaxClouds];  // (a 128-byte aligned type)
@@ -1668,7 +1669,7 @@ __global__ void k_to_h16(const float *__restrict__ pts, int64_t n, int dp, int k
 
 constexpr int TC_T = 256;   // threads per CTA (two CTAs per SM)
 constexpr int TC_EB = 768;  // edge buffer entries (one-pass emit)
-constexpr int TC_ISSUER = TC_T - 32;  // lane 0 of the last warp: issues the tiles' MMAs, tracks their loads
+constexpr int TC_ISSUER = TC_T - 32;  // lane 0 of the last warp: issues the tiles' MMAs, tracks the query rows' load
 struct __align__(1024) TcShared {
     unsigned char A[2][2][TC_ROWS * 128];  // fp16 candidate rows: buffer, K half (64 halves), 128-byte swizzle
     unsigned char B[2][32 * 128];          // fp16 query rows, the same layout
@@ -1687,7 +1688,7 @@ struct __align__(1024) TcShared {
     int wsum[TC_T / 32];
     int kn[2], en;
     uint32_t tslot;
-    uint64_t lbar[2], mbar[2], bbar;       // tile loads, MMAs (per buffer), query rows
+    uint64_t mbar[2], bbar;                // MMAs (per buffer), query rows
 };
 constexpr size_t kTcSmem = sizeof(TcShared) + 1024;
 static_assert(2 * (kTcSmem + 1024) <= 228 * 1024, "k_leaf_tc: two CTAs per SM");
@@ -1695,13 +1696,12 @@ static_assert(TC_NB % TC_T == 0, "block prefix takes TC_NB / TC_T candidate bloc
 
 // Count pass (and one-pass emit) with the FP16 filter.  One CTA of 8 warps per
 // work item, two CTAs per SM (one's setup and drain overlap the other's
-// tiles).  Candidate rows arrive by TMA gathers (four rows per instruction,
-// 128-byte swizzle, straight into the MMA's operand layout; lane 0 of each
-// warp issues its 16 rows, between the filter and its rechecks) two tiles
-// ahead; one thread issues the MMA of tile t + 1 (second accumulator) as the
-// iteration of tile t begins, so that it runs while tile t is filtered and
-// rechecked.  Rechecks read
-// the original fp32 rows from global memory, eight lanes per pair.
+// tiles).  Candidate rows arrive by 16-byte cp.async copies of every thread
+// (half a row each), written in the MMA's 128-byte swizzled operand layout,
+// two tiles ahead; the 32 query rows by TMA gathers.  One thread issues the
+// MMA of tile t + 1 (second accumulator) as the iteration of tile t begins, so
+// that it runs while tile t is filtered and rechecked.  Rechecks read the
+// original fp32 rows from global memory, eight lanes per pair.
 __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Views V, Items items,
                                                      const uint32_t *__restrict__ cand, uint32_t *__restrict__ emask,
                                                      int32_t *__restrict__ deg, unsigned long long *__restrict__ st,
@@ -1716,6 +1716,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
     const TreeView &tv = V.tv[cloud];
     const QParams &qp = V.qp[cloud];
     const void *tmap = &V.tmap[cloud];
+    const uint4 *h16 = V.h16[cloud];
     const float *n16 = V.n16[cloud];
     const int g = gg - V.gbase[cloud];
     const int64_t rbase = V.rbase[cloud];  // CSR rows of this cloud start here
@@ -1723,7 +1724,8 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
     const float4 *pts4 = reinterpret_cast<const float4 *>(tv.pts);
     const int halves = (dp + 63) >> 6;               // 64-half K blocks of an fp16 row (1 or 2)
     const int ksteps = 4 * halves;                   // MMA K steps of 16
-    const uint32_t tile_bytes = (uint32_t)(TC_ROWS * 128 * halves), q_bytes = (uint32_t)(32 * 128 * halves);
+    const int kc = 8 * halves;                       // 16-byte chunks of an fp16 row
+    const uint32_t q_bytes = (uint32_t)(32 * 128 * halves);
     const int qb = tv.group_begin[g], qn = tv.group_count[g];
     const int qe = qb + qn;  // the group's positions; upper-triangle form: rows before qb are skipped, edges
                              // with rows from qe on are mirrored into those rows
@@ -1732,15 +1734,13 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
     uint32_t pairs = 0, kept = 0, guard = 0, band = 0, rows_ld = 0;  // rows_ld, kept: thread 0
     bool failed = false;
     // next phase parity of each barrier (bit b: buffer b): mph in every thread
-    // (warp 0 waits), lph and bph in the issuing thread (it waits), which also
-    // tracks what is in flight, for a clean exit after a failure
-    uint32_t lph = 0u, mph = 0u, bph = 0u, lpend = 0u, mpend = 0u, bpend = 0u;
+    // (warp 0 waits), bph in the issuing thread (it waits), which also tracks
+    // what is in flight, for a clean exit after a failure
+    uint32_t mph = 0u, bph = 0u, mpend = 0u, bpend = 0u;
     bool tok = true;  // the issuing thread (TC_ISSUER): its own waits succeeded
 
     if (warp == 0) tc::tmem_alloc(&S.tslot, 64);
     if (tid == 0) {
-        tc::mbar_init(&S.lbar[0], 1);
-        tc::mbar_init(&S.lbar[1], 1);
         tc::mbar_init(&S.mbar[0], 1);
         tc::mbar_init(&S.mbar[1], 1);
         tc::mbar_init(&S.bbar, 1);
@@ -1794,36 +1794,47 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
 
     // rows of tile t -> (position, block) in map slot t & 3 and the rows'
     // norms (4-byte copies; each thread commits one copy group per call).
-    // Warps 1-4: warp 0 issues the MMAs.
+    // Warp w in 1..4 maps rows 32 (w - 1) .. + 31 of the tile: the block b0
+    // holding the window's first row R0 comes from two 32-wide ballot
+    // searches over the block prefix (the largest b0 with bpre[b0] <= R0);
+    // blocks b0 + 1 .. b0 + 31 start inside the window or after it, and a
+    // row's block is b0 plus the number of block starts in (R0, R].
     auto prep_map = [&](int t) {
-        const int r = tid - 32, R = t * TC_ROWS + r;
-        if (t < ntiles && r >= 0 && r < TC_ROWS && R < T) {
-            int lo = 0, hi = TC_NB;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (S.bpre[mid] <= R) lo = mid; else hi = mid;
+        const int wq = warp - 1, R0 = t * TC_ROWS + 32 * wq;
+        if (t < ntiles && wq >= 0 && wq < 4 && R0 < T) {  // warp-uniform
+            const unsigned mc = __ballot_sync(0xffffffffu, S.bpre[32 * lane] <= R0);  // bit 0 set: bpre[0] = 0
+            const int c = 31 - __clz(mc);
+            const unsigned mf = __ballot_sync(0xffffffffu, S.bpre[32 * c + lane] <= R0);
+            const int b0 = 32 * c + 31 - __clz(mf);
+            const int j = b0 + 1 + lane;
+            const int v = j <= TC_NB ? S.bpre[j] : INT_MAX;
+            const unsigned m = __reduce_or_sync(0xffffffffu, v < R0 + 32 ? 1u << (v - R0) : 0u);  // v > R0
+            const int R = R0 + lane;
+            if (R < T) {
+                const int blk = b0 + __popc(m & (0xffffffffu >> (31 - lane)));
+                const int pos = S.bbeg[blk] + (R - S.bpre[blk]);
+                const int r = 32 * wq + lane;
+                S.pos[t & 3][r] = pos;
+                S.li[t & 3][r] = (uint16_t)blk;
+                cp_async4(&S.pn[t & 3][r], n16 + pos);
             }
-            const int pos = S.bbeg[lo] + (R - S.bpre[lo]);
-            S.pos[t & 3][r] = pos;
-            S.li[t & 3][r] = (uint16_t)lo;
-            cp_async4(&S.pn[t & 3][r], n16 + pos);
         }
         cp_async_commit();
     };
-    // lane 0 of warp w: tile t's rows 16 w .. 16 w + 15 (past the last row of
-    // a short tile: row 0 again) into buffer t & 1, completing on lbar[t & 1]
-    auto issue_tile = [&](int t) {
-        if (lane == 0) {
-            const int rows = min(TC_ROWS, T - t * TC_ROWS), sl = t & 3, bf = t & 1;
-#pragma unroll
-            for (int gq = 0; gq < 4; ++gq) {
-                const int r = 16 * warp + 4 * gq;
-                int p[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) p[i] = S.pos[sl][r + i < rows ? r + i : 0];
-                for (int h = 0; h < halves; ++h)
-                    tc::tma_gather4(S.A[bf][h] + r * 128, tmap, 64 * h, p[0], p[1], p[2], p[3], &S.lbar[bf]);
-            }
+    // every thread: rows of tile t (past the last row of a short tile: row 0
+    // again) into buffer t & 1 by 16-byte copies, consecutive threads taking
+    // consecutive chunks of a row (a warp's copy covers 2 or 4 whole rows), in
+    // the MMA's 128-byte swizzled K-major layout (chunk j of row r at chunk
+    // j ^ (r % 8) of the row's 128 bytes; 1024-byte atoms of 8 rows).
+    // Completed by the copy group wait, a proxy fence and the barrier at the
+    // top of the next iteration, before the MMA that reads them is issued.
+    auto load_tile = [&](int t) {
+        const int rows = min(TC_ROWS, T - t * TC_ROWS), sl = t & 3, bf = t & 1;
+        const int lkc = 2 + halves;  // log2 of kc (8 or 16 chunks per row)
+        for (int g = tid; g < TC_ROWS * kc; g += TC_T) {
+            const int r = g >> lkc, ch = g & (kc - 1), h = ch >> 3, j = ch & 7;
+            const int pos = S.pos[sl][r < rows ? r : 0];
+            cp_async16(S.A[bf][h] + r * 128 + ((j ^ (r & 7)) << 4), h16 + (size_t)pos * kc + ch, true);
         }
     };
     // the issuing thread: tile t's MMA chain into accumulator columns 32 (t & 1)
@@ -1863,13 +1874,9 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
         prep_map(0);
         prep_map(1);
         prep_map(2);
-        if (tid == TC_ISSUER) {  // expectations before any gather of them is issued
+        if (tid == TC_ISSUER) {  // the expectation before any gather of the query rows is issued
             tc::mbar_arrive_expect_tx(&S.bbar, q_bytes);
             bpend = 1u;
-            for (int t = 0; t < 2 && t < ntiles; ++t) {
-                tc::mbar_arrive_expect_tx(&S.lbar[t], tile_bytes);
-                lpend |= 1u << t;
-            }
         }
         __syncthreads();
         // query rows (past the group's queries: its last query again) and tiles 0, 1
@@ -1879,24 +1886,22 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
             const int r2 = qfirst + min(q + 2, nqr - 1), r3 = qfirst + min(q + 3, nqr - 1);
             for (int h = 0; h < halves; ++h) tc::tma_gather4(S.B[h] + q * 128, tmap, 64 * h, r0, r1, r2, r3, &S.bbar);
         }
-        for (int t = 0; t < 2 && t < ntiles; ++t) issue_tile(t);
-        if (tid == TC_ISSUER) {  // the issuing thread alone tracks the load barriers' phases
+        for (int t = 0; t < 2 && t < ntiles; ++t) load_tile(t);
+        cp_async_commit();
+        cp_async_wait<0>();
+        tc::fence_smem_to_async();
+        __syncthreads();
+        if (tid == TC_ISSUER) {  // the issuing thread alone tracks the query rows' barrier phase
             const bool okb = tok && tc::mbar_wait_sleep(&S.bbar, bph, TC_SLEEPS, TC_HINT);
             if (okb) {
                 bpend = 0u;
                 bph ^= 1u;
-            }
-            bool okl = okb;
-            if (okb && ntiles > 0) {
-                okl = tc::mbar_wait_sleep(&S.lbar[0], lph & 1u, TC_SLEEPS, TC_HINT);
-                if (okl) {
-                    lpend &= ~1u;
-                    lph ^= 1u;
+                if (ntiles > 0) {
                     tc::fence_after_sync();
                     mma_tile(0);
                 }
             }
-            tok = okl;
+            tok = okb;
         }
 
         auto flush = [&]() {
@@ -1905,7 +1910,10 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
             const int n = min(S.en, TC_EB);
             for (int i = tid; i < n; i += TC_T) {
                 const int q = S.eq[i];
-                cap_place(co, S.orig[q], S.qbase[q] + S.erank[i], tv.perm[S.ecol[i]], S.edist[i]);
+                if (q & 0x80)  // an edge mirrored into the row of tree position ecol (upper triangle)
+                    cap_put(co, (int)(rbase + tv.perm[S.ecol[i]]), tv.perm[qfirst + (q & 31)], S.edist[i]);
+                else
+                    cap_place(co, S.orig[q], S.qbase[q] + S.erank[i], tv.perm[S.ecol[i]], S.edist[i]);
             }
             __syncthreads();
             if (tid < 32) S.qfill[tid] = 0;
@@ -1971,7 +1979,16 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
                 if (qp.half && ppos >= qe) {
                     const int64_t o = rbase + tv.perm[ppos];
                     atomicAdd(&deg[o], 1);
-                    if (co.off) cap_put(co, (int)o, tv.perm[qfirst + q], d);
+                    if (co.off) {  // its slot is taken at the flush, off the recheck's path
+                        const int slot = atomicAdd(&S.en, 1);
+                        if (slot < TC_EB) {
+                            S.eq[slot] = (uint8_t)(0x80 | q);
+                            S.ecol[slot] = ppos;
+                            S.edist[slot] = d;
+                        } else {
+                            cap_put(co, (int)o, tv.perm[qfirst + q], d);
+                        }
+                    }
                 }
                 atomicAdd(&S.qcnt[q], 1);
                 atomicOr(&S.bem[S.li[sl][r]], 1u << q);
@@ -1993,14 +2010,12 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
             const int sl = t & 3, bf = t & 1;
             const int rows = min(TC_ROWS, T - t * TC_ROWS);
             if (tid == 0) rows_ld += rows;
-            // tile t's MMA has completed (warp 0 waits) and its norms have landed
-            cp_async_wait<2>();
+            // tile t's MMA has completed (warp 0 waits); the rows of tile t + 1
+            // (copied an iteration ago) and the norms have landed
+            cp_async_wait<0>();
+            tc::fence_smem_to_async();
             bool ok = tid != TC_ISSUER || tok;  // the issuing thread's own waits so far
             if (warp == 0) ok = tc::mbar_wait_sleep(&S.mbar[bf], (mph >> bf) & 1u, TC_SLEEPS, TC_HINT);
-            if (tid == TC_ISSUER && ok && t + 2 < ntiles) {  // buffer bf takes tile t + 2 (gathers later)
-                tc::mbar_arrive_expect_tx(&S.lbar[bf], tile_bytes);
-                lpend |= 1u << bf;
-            }
             if (!__syncthreads_and(ok)) {
                 if (tid == 0) atomicOr(err, 32);
                 failed = true;
@@ -2012,19 +2027,11 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
             if (co.off && S.en >= TC_EB / 2) flush();  // tile t - 1's rechecks are done
             // the issuing thread: tile t + 1's MMA into the other accumulator now,
             // so that it runs while tile t is filtered and rechecked (its rows
-            // were gathered an iteration ago; its columns were last read by tile
+            // were copied an iteration ago; its columns were last read by tile
             // t - 1's filter, before the barrier above)
-            if (t + 1 < ntiles && tid == TC_ISSUER && tok) {
-                if (tc::mbar_wait_sleep(&S.lbar[bf ^ 1], (lph >> (bf ^ 1)) & 1u, TC_SLEEPS, TC_HINT)) {
-                    lpend &= ~(1u << (bf ^ 1));
-                    lph ^= 1u << (bf ^ 1);
-                    tc::fence_after_sync();
-                    mma_tile(t + 1);
-                } else {
-                    tok = false;
-                }
-            }
-            prep_map(t + 3);
+            if (t + 1 < ntiles && tid == TC_ISSUER && tok) mma_tile(t + 1);
+            if (t + 2 < ntiles) load_tile(t + 2);  // buffer bf: tile t's MMA has completed
+            prep_map(t + 3);                       // commits the group (tile t + 2's rows, t + 3's norms)
             // epilogue, filter: warp w reads rows 32 (w % 4) .. + 31, queries
             // 16 (w / 4) .. + 15; kept pairs go to the tile's list
             uint32_t keepm = 0u;
@@ -2078,8 +2085,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
             tc::fence_before_sync();
             __syncthreads();
             const int n = S.kn[bf];
-            // the first recheck round's rows are prefetched into L1, so that
-            // their latency overlaps the gathers issued next
+            // the first recheck round's rows are prefetched into L1
             if ((tid >> 3) < min(n, TC_KL)) {
                 const int e = S.kl[tid >> 3], k0 = 4 * (lane & 7);
                 if (k0 < dp4) {
@@ -2087,7 +2093,6 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
                     prefetch_l1(pts4 + (size_t)S.pos[sl][e & 127] * dp4 + k0);
                 }
             }
-            if (t + 2 < ntiles) issue_tile(t + 2);  // lane 0 of each warp, before its recheck
             if (tid == 0) {
                 kept += n;
                 S.kn[bf ^ 1] = 0;  // tile t + 1's list (filled after the next barrier)
@@ -2132,11 +2137,9 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
         if (tid == 0) stat_add(st, ST_ROWS, rows_ld);
     }
     cp_async_wait<0>();  // no copy into this CTA's shared memory outlives it
-    if (tid == TC_ISSUER) {  // after a failure: let gathers and MMAs in flight finish (bounded)
-        for (int b = 0; b < 2; ++b) {
-            if (lpend >> b & 1u) tc::mbar_wait(&S.lbar[b], (lph >> b) & 1u, TC_WAIT);
+    if (tid == TC_ISSUER) {  // after a failure: let the query rows' gathers and MMAs in flight finish (bounded)
+        for (int b = 0; b < 2; ++b)
             if (mpend >> b & 1u) tc::mbar_wait(&S.mbar[b], (mph >> b) & 1u, TC_WAIT);
-        }
         if (bpend) tc::mbar_wait_sleep(&S.bbar, bph, TC_SLEEPS, TC_HINT);
     }
     tc::fence_before_sync();
@@ -2918,6 +2921,7 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
             CT_COUNT_LAUNCH();
             CT_LAUNCH_CHECK();
             encode_rows_f16(&V.tmap[c], h16s.back().p, nc, kp);
+            V.h16[c] = h16s.back().p;
             V.n16[c] = nrm;
             V.s16[c] = scal;
         }
