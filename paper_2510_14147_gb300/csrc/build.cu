@@ -23,6 +23,7 @@
 #include <climits>
 #include <cstdio>
 #include <memory>
+#include <mutex>
 #include <vector>
 #include <algorithm>
 
@@ -79,6 +80,39 @@ __device__ __forceinline__ float group_sqdist(const float4 *__restrict__ row, co
 }
 
 constexpr int UPD_PASSES = 8;  // passes of a block over its chunk in k_dist_update_l2
+
+// The same distance with the row staged in shared memory by the calling lane
+// (lane j copied float4s j, j + TPD, ... and reads only those): the same
+// operations in the same order, so the same value.
+template <int TPD>
+__device__ __forceinline__ float group_sqdist_staged(const float4 *row, const float4 *cen, int nq, int j) {
+    float acc = 0.f;
+#pragma unroll 4
+    for (int k = j; k < nq; k += TPD) {
+        float4 a = row[k];
+        float4 b = cen[k];
+        float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, dw = a.w - b.w;
+        acc = fmaf(dx, dx, acc);
+        acc = fmaf(dy, dy, acc);
+        acc = fmaf(dz, dz, acc);
+        acc = fmaf(dw, dw, acc);
+    }
+    const unsigned mask = TPD == 32 ? 0xffffffffu : (((1u << TPD) - 1u) << ((threadIdx.x & 31) & ~(TPD - 1)));
+#pragma unroll
+    for (int o = TPD / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, TPD);
+    return acc;
+}
+__device__ __forceinline__ void stage_copy16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void stage_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+// Staged passes keep UPD_STAGES buffers of G rows in shared memory: the rows
+// of passes p + 1 and p + 2 are in flight while pass p is computed.
+constexpr int UPD_STAGES = 3;
+constexpr int UPD_STAGE_F4 = 1024;  // float4s of one buffer (G rows of nq float4s) that allow staging
 
 struct Hubs {
     int32_t *begin, *count, *node, *nc, *cur, *done, *level;
@@ -151,20 +185,27 @@ __device__ __noinline__ void step_tail(const float *__restrict__ X, int dp, cons
     __syncthreads();
     constexpr int G = BT / TPD;
     const int g = threadIdx.x / TPD, j = threadIdx.x % TPD;
+    // the row of label L (its centre's point id), the next step's loaded
+    // while this step's distance is computed
+    auto row_of = [&](int L) { return ids[st.cpos[b + (L < nc ? L : 0)]]; };
+    int rid = row_of(g);
     for (int L0 = 0; L0 < nc; L0 += G) {  // every group runs the same number of steps
         const int L = L0 + g;
-        const int pos = st.cpos[b + (L < nc ? L : 0)];
-        const float dd = sqrtf(group_sqdist<TPD>(reinterpret_cast<const float4 *>(X + (size_t)ids[pos] * dp), cen,
-                                                 nq, j));
+        const int nrid = L0 + G < nc ? row_of(L + G) : 0;
+        const float dd = sqrtf(group_sqdist<TPD>(reinterpret_cast<const float4 *>(X + (size_t)rid * dp), cen, nq, j));
         if (L < nc && j == 0) st.dcc[b + L] = dd;
+        rid = nrid;
     }
 }
 
 // Pruning (L2): a point labelled L cannot come closer to the new centre c
 // than D when d(c, centre L) >= 2 D (triangle inequality); such points keep D
 // and L without reading their row.  dcc[begin + L] = d(c, centre L) of the
-// hub (nullptr: no pruning).
-template <int TPD>
+// hub (nullptr: no pruning).  STAGE: the rows of the chunk's passes are
+// copied into shared memory two passes ahead (cp.async), so that a group's
+// eight passes do not wait on memory one after another; otherwise each pass
+// reads its rows from global memory.
+template <int TPD, bool STAGE>
 __global__ void __launch_bounds__(BT, 4) k_dist_update_l2(
     const float *__restrict__ X, int dp, const int32_t *__restrict__ ids, float *__restrict__ D,
     int32_t *__restrict__ lab, const int32_t *__restrict__ chunk_hub,
@@ -203,13 +244,35 @@ __global__ void __launch_bounds__(BT, 4) k_dist_update_l2(
         for (int p = 0; p < UPD_PASSES; ++p)
             if (!far[p]) far[p] = dcc[hbeg + lb[p]] >= 2.0f * cur[p] * (1.0f + 0x1p-12f) + 0x1p-60f;
     }
+    // STAGE: buffer b holds G rows of nq float4s after the centre row; a lane
+    // copies (and later reads) only its own float4s of its group's row
+    float4 *stage = cen + nq;
+    auto issue = [&](int p) {
+        if (p < UPD_PASSES && !far[p]) {
+            const float4 *row = reinterpret_cast<const float4 *>(X + (size_t)pid[p] * dp);
+            float4 *dst = stage + ((size_t)(p % UPD_STAGES) * G + g) * nq;
+            for (int k = j; k < nq; k += TPD) stage_copy16(dst + k, row + k);
+        }
+        stage_commit();
+    };
+    if (STAGE) {
+        issue(0);
+        issue(1);
+    }
     __syncthreads();  // the centre row
     unsigned long long best = 0ull;
 #pragma unroll
     for (int p = 0; p < UPD_PASSES; ++p) {
         const int pos = start + p * G + g;
+        if (STAGE) issue(p + 2);
         if (!far[p]) {  // the same for the group's TPD lanes
-            float s = group_sqdist<TPD>(reinterpret_cast<const float4 *>(X + (size_t)pid[p] * dp), cen, nq, j);
+            float s;
+            if (STAGE) {
+                stage_wait<UPD_STAGES - 1>();  // this lane's copies of pass p have landed
+                s = group_sqdist_staged<TPD>(stage + ((size_t)(p % UPD_STAGES) * G + g) * nq, cen, nq, j);
+            } else {
+                s = group_sqdist<TPD>(reinterpret_cast<const float4 *>(X + (size_t)pid[p] * dp), cen, nq, j);
+            }
             if (j == 0) {
                 float d = sqrtf(s);
                 if (d < cur[p]) {
@@ -228,23 +291,41 @@ __global__ void __launch_bounds__(BT, 4) k_dist_update_l2(
         unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
         best = v > best ? v : best;
     }
-    if ((threadIdx.x & 31) == 0 && best) atomicMax(&hb.key[h], best);
-    {  // points now within the split threshold (the flat-split test)
-        const float thr = hb.thr[h];
-        int cov = 0;
+    // points now within the split threshold (the flat-split test)
+    const float thr = hb.thr[h];
+    int cov = 0;
 #pragma unroll
-        for (int p = 0; p < UPD_PASSES; ++p) cov += (j == 0 && start + p * G + g < end && cur[p] <= thr) ? 1 : 0;
-        for (int o = 16; o > 0; o >>= 1) cov += __shfl_xor_sync(0xffffffffu, cov, o);
-        if ((threadIdx.x & 31) == 0 && cov) atomicAdd(&hb.covered[h], cov);
+    for (int p = 0; p < UPD_PASSES; ++p) cov += (j == 0 && start + p * G + g < end && cur[p] <= thr) ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) cov += __shfl_xor_sync(0xffffffffu, cov, o);
+    // the block's maximum key and count go to the hub in one atomic each (a
+    // block's chunk lies in one hub); then, with pruning, the block arrives
+    // and the hub's last block takes its next step
+    __shared__ unsigned long long s_best[BT / 32];
+    __shared__ int s_cov[BT / 32];
+    __shared__ int s_last;
+    if ((threadIdx.x & 31) == 0) {
+        s_best[threadIdx.x >> 5] = best;
+        s_cov[threadIdx.x >> 5] = cov;
     }
-    if (st.arrive) {  // the hub's last block takes its next step
-        __shared__ int s_last;
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) {
+    if (st.arrive) __threadfence();  // this thread's D and lab writes, before the block's arrival
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long bk = 0ull;
+        int bc = 0;
+#pragma unroll
+        for (int w = 0; w < BT / 32; ++w) {
+            bk = s_best[w] > bk ? s_best[w] : bk;
+            bc += s_cov[w];
+        }
+        if (bk) atomicMax(&hb.key[h], bk);
+        if (bc) atomicAdd(&hb.covered[h], bc);
+        if (st.arrive) {
+            __threadfence();  // the key and the count, before the arrival
             const int blocks = (hb.count[h] + chunk_len - 1) / chunk_len;  // all of the hub's chunks run
             s_last = atomicAdd(&st.arrive[h], 1) == blocks - 1;
         }
+    }
+    if (st.arrive) {
         __syncthreads();
         if (s_last) {
             __threadfence();
@@ -1125,6 +1206,28 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
         int tpd = 1;  // a power of two
         while (l2 && tpd < 32 && 2 * tpd * 16 <= dp) tpd *= 2;
         const int chunk_len = l2 ? UPD_PASSES * (BT / tpd) : 4 * BT;
+        // staged update passes where the buffers fit (a pass's rows: BT / tpd
+        // rows of dp / 4 float4s), with their shared memory allowed once
+        const bool stage = l2 && (int64_t)(BT / tpd) * (dp / 4) <= UPD_STAGE_F4;
+        const size_t stage_sm = ((size_t)dp / 4 + (size_t)UPD_STAGES * (BT / tpd) * (dp / 4)) * sizeof(float4);
+        if (stage) {
+            static std::once_flag once[6];
+            auto allow = [&](int k, const void *fn) {
+                std::call_once(once[k], [&] {
+                    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float4) * (1 + UPD_STAGES) * UPD_STAGE_F4));
+                });
+            };
+            switch (tpd) {
+                case 1: allow(0, (const void *)k_dist_update_l2<1, true>); break;
+                case 2: allow(1, (const void *)k_dist_update_l2<2, true>); break;
+                case 4: allow(2, (const void *)k_dist_update_l2<4, true>); break;
+                case 8: allow(3, (const void *)k_dist_update_l2<8, true>); break;
+                case 16: allow(4, (const void *)k_dist_update_l2<16, true>); break;
+                case 32: allow(5, (const void *)k_dist_update_l2<32, true>); break;
+            }
+            CT_CHECK_CUDA(cudaGetLastError());
+        }
         // pruned updates (L2): centre positions and centre-to-new-centre distances per hub label
         DBuf<int32_t> cpos(l2 ? n : 1, s);
         DBuf<float> dcc(l2 ? n : 1, s);
@@ -1132,11 +1235,19 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
         auto update = [&](Hubs &hb, int64_t nchunks, const int32_t *chub, const int32_t *cst, Step st) {
             if (!nchunks) return;
             if (l2) {
-                size_t sm = (size_t)dp * sizeof(float);
-                switch (tpd) {
-#define CT_UPD(T) case T: k_dist_update_l2<T><<<(unsigned)nchunks, BT, sm, s>>>(Xp.p, dp, ids.p, D.p, lab.p, chub, cst, chunk_len, hb, prune ? dcc.p : nullptr, st); break;
-                    CT_UPD(1) CT_UPD(2) CT_UPD(4) CT_UPD(8) CT_UPD(16) CT_UPD(32)
+                if (stage) {
+                    switch (tpd) {
+#define CT_UPD(T) case T: k_dist_update_l2<T, true><<<(unsigned)nchunks, BT, stage_sm, s>>>(Xp.p, dp, ids.p, D.p, lab.p, chub, cst, chunk_len, hb, prune ? dcc.p : nullptr, st); break;
+                        CT_UPD(1) CT_UPD(2) CT_UPD(4) CT_UPD(8) CT_UPD(16) CT_UPD(32)
 #undef CT_UPD
+                    }
+                } else {
+                    const size_t sm = (size_t)dp * sizeof(float);
+                    switch (tpd) {
+#define CT_UPD(T) case T: k_dist_update_l2<T, false><<<(unsigned)nchunks, BT, sm, s>>>(Xp.p, dp, ids.p, D.p, lab.p, chub, cst, chunk_len, hb, prune ? dcc.p : nullptr, st); break;
+                        CT_UPD(1) CT_UPD(2) CT_UPD(4) CT_UPD(8) CT_UPD(16) CT_UPD(32)
+#undef CT_UPD
+                    }
                 }
             } else if (ham) {
                 k_dist_update_ham<<<(unsigned)nchunks, BT, (size_t)wp * sizeof(uint32_t), s>>>(
