@@ -1205,7 +1205,10 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
         // flight); a chunk is eight passes of a block
         int tpd = 1;  // a power of two
         while (l2 && tpd < 32 && 2 * tpd * 16 <= dp) tpd *= 2;
-        const int chunk_len = l2 ? UPD_PASSES * (BT / tpd) : 4 * BT;
+        // points per block of an update pass: L2, eight passes of the block's
+        // groups; Hamming, four per thread; edit distance, one per thread (a
+        // long recurrence each: more blocks share a pass)
+        const int chunk_len = l2 ? UPD_PASSES * (BT / tpd) : ham ? 4 * BT : BT;
         // staged update passes where the buffers fit (a pass's rows: BT / tpd
         // rows of dp / 4 float4s), with their shared memory allowed once
         const bool stage = l2 && (int64_t)(BT / tpd) * (dp / 4) <= UPD_STAGE_F4;
