@@ -51,38 +51,55 @@ CT_HD int lev_myers(const uint64_t *peq, int m, const uint8_t *txt, int n, int k
         Mv[w] = 0ull;
     }
     int score = m;
-    for (int j = 0; j < n; ++j) {
-        const uint64_t *eqr = peq + (int)txt[j] * W;
-        uint64_t carry = 0ull, hp_in = 1ull, hn_in = 0ull;
+    // the text is read a block of LEV_PF characters ahead of the recurrence:
+    // independent loads, so that a step does not wait on its own load
+    constexpr int LEV_PF = 8;
+    int nxt[LEV_PF];
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            if (w < nw) {
-                uint64_t Eq = eqr[w];
-                uint64_t pv = Pv[w], mv = Mv[w];
-                uint64_t Xv = Eq | mv;
-                uint64_t t = Eq & pv;
-                uint64_t s1 = t + pv;
-                uint64_t c1 = s1 < t ? 1ull : 0ull;
-                uint64_t s2 = s1 + carry;
-                uint64_t c2 = s2 < s1 ? 1ull : 0ull;
-                carry = c1 | c2;
-                uint64_t Xh = (s2 ^ pv) | Eq;
-                uint64_t Ph = mv | ~(Xh | pv);
-                uint64_t Mh = pv & Xh;
-                if (w == hw) {
-                    if (Ph & hbit) ++score;
-                    else if (Mh & hbit) --score;
-                }
-                uint64_t ph_out = Ph >> 63, mh_out = Mh >> 63;
-                Ph = (Ph << 1) | hp_in;
-                Mh = (Mh << 1) | hn_in;
-                hp_in = ph_out;
-                hn_in = mh_out;
-                Pv[w] = Mh | ~(Xv | Ph);
-                Mv[w] = Ph & Xv;
-            }
+    for (int u = 0; u < LEV_PF; ++u) nxt[u] = u < n ? (int)txt[u] : 0;
+    for (int j0 = 0; j0 < n; j0 += LEV_PF) {
+        int blk[LEV_PF];
+#pragma unroll
+        for (int u = 0; u < LEV_PF; ++u) {
+            blk[u] = nxt[u];
+            nxt[u] = j0 + LEV_PF + u < n ? (int)txt[j0 + LEV_PF + u] : 0;
         }
-        if (score - (n - 1 - j) > k) return k + 1;
+#pragma unroll
+        for (int u = 0; u < LEV_PF; ++u) {
+            const int j = j0 + u;
+            if (j >= n) break;
+            const uint64_t *eqr = peq + blk[u] * W;
+            uint64_t carry = 0ull, hp_in = 1ull, hn_in = 0ull;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                if (w < nw) {
+                    uint64_t Eq = eqr[w];
+                    uint64_t pv = Pv[w], mv = Mv[w];
+                    uint64_t Xv = Eq | mv;
+                    uint64_t t = Eq & pv;
+                    uint64_t s1 = t + pv;
+                    uint64_t c1 = s1 < t ? 1ull : 0ull;
+                    uint64_t s2 = s1 + carry;
+                    uint64_t c2 = s2 < s1 ? 1ull : 0ull;
+                    carry = c1 | c2;
+                    uint64_t Xh = (s2 ^ pv) | Eq;
+                    uint64_t Ph = mv | ~(Xh | pv);
+                    uint64_t Mh = pv & Xh;
+                    if (w == hw) {
+                        if (Ph & hbit) ++score;
+                        else if (Mh & hbit) --score;
+                    }
+                    uint64_t ph_out = Ph >> 63, mh_out = Mh >> 63;
+                    Ph = (Ph << 1) | hp_in;
+                    Mh = (Mh << 1) | hn_in;
+                    hp_in = ph_out;
+                    hn_in = mh_out;
+                    Pv[w] = Mh | ~(Xv | Ph);
+                    Mv[w] = Ph & Xv;
+                }
+            }
+            if (score - (n - 1 - j) > k) return k + 1;
+        }
     }
     return score;
 }

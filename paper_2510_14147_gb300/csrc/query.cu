@@ -150,6 +150,9 @@ struct Spill {
 constexpr int TRAV_ROUNDS = 4;     // rounds after the groups' round; the last one has no step limit
 constexpr int TRAV_LIMIT0 = 256;   // step limit of the groups' round
 constexpr int TRAV_LIMIT = 128;    // step limit of the next rounds
+// edit distance: a step (32 bit-parallel recurrences) costs about a hundred
+// L2 steps, so its walks stop much sooner
+constexpr int TRAV_LIMIT0_LEV = 8, TRAV_LIMIT_LEV = 8;
 
 // Warp-uniform write cursor: current chunk, its fill, the open segment.
 struct PoolCursor {
@@ -252,30 +255,37 @@ __device__ __forceinline__ int walk_group(const TreeView &tv, int2 *__restrict__
                 for (int i = base + lane; i < sp->cap; i += 32) sp->items[i] = make_int4(g, 0, 0, 0);
                 limit = INT_MAX;
             }
-            const int2 r = stack[top - 1];
-            const int take = r.y < 32 ? r.y : 32;
-            int2 r2 = make_int2(0, 0);  // the range below, for the lanes the top range leaves idle
-            int take2 = 0;
-            if (take < 32 && top >= 2) {
-                r2 = stack[top - 2];
-                take2 = r2.y < 32 - take ? r2.y : 32 - take;
+            // the step's vertices: the top ranges of the stack, newest first,
+            // until the 32 lanes are filled (lane i reads the i-th range from
+            // the top; ranges are never empty); the last range drawn on may be
+            // taken in part and keeps its rest on the stack.  A step reaches an
+            // older block of ranges only when the newer ones are used up, so
+            // the least deep vertex of each block on the stack is deeper than
+            // the block below's: at most depth + 1 blocks of at most 32 ranges.
+            const int nr = top < 32 ? top : 32;
+            const int2 ri = lane < nr ? stack[top - 1 - lane] : make_int2(0, 0);
+            int incl = ri.y;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
+            const int excl = incl - ri.y;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            const int n = total < 32 ? total : 32;
+            const int nfull = __popc(__ballot_sync(0xffffffffu, lane < nr && incl <= 32));
+            // the first lane of each range drawn on, then each lane's range
+            const unsigned smask = __reduce_or_sync(0xffffffffu, (lane < nr && excl < 32) ? 1u << excl : 0u);
+            const int k = __popc(smask & (0xffffffffu >> (31 - lane))) - 1;
+            const int kx = __shfl_sync(0xffffffffu, ri.x, k);
+            const int ke = __shfl_sync(0xffffffffu, excl, k);
+            const int px = __shfl_sync(0xffffffffu, ri.x, nfull & 31), py = __shfl_sync(0xffffffffu, ri.y, nfull & 31);
+            const int pe = __shfl_sync(0xffffffffu, excl, nfull & 31);
             __syncwarp();
-            if (r.y > take) {  // a long top range: its first 32 vertices
-                if (lane == 0) stack[top - 1] = make_int2(r.x + take, r.y - take);
-            } else {
-                --top;
-                if (take2 > 0) {
-                    if (r2.y > take2) {
-                        if (lane == 0) stack[top - 1] = make_int2(r2.x + take2, r2.y - take2);
-                    } else {
-                        --top;
-                    }
-                }
-            }
-            const int n = take + take2;
+            top -= nfull;
+            if (nfull < nr && pe < 32 && lane == 0) stack[top - 1] = make_int2(px + (32 - pe), py - (32 - pe));
             if (lane < n) ++evals;
-            const int v = lane < take ? r.x + lane : r2.x + (lane - take);
+            const int v = lane < n ? kx + (lane - ke) : 0;
             int ccount = 0, cbegin = 0;
             if (lane < n) {
                 ccount = tv.child_count[v];
@@ -287,7 +297,7 @@ __device__ __forceinline__ int walk_group(const TreeView &tv, int2 *__restrict__
             n_cand += __popc(__ballot_sync(0xffffffffu, keep && leaf));
             const unsigned mi = __ballot_sync(0xffffffffu, keep && !leaf);
             const int np = __popc(mi);
-            if (top + np > cap) {  // cannot happen for a stack of 32 * (depth + 2) ranges
+            if (top + np > cap) {  // cannot happen for a stack of 32 * (depth + 2) ranges (above)
                 if (lane == 0) atomicOr(err, 2);
                 return -1;
             }
@@ -434,19 +444,38 @@ __global__ void __launch_bounds__(TRAV_WARPS * 32, 8) k_traverse_l2(
 // in shared memory.
 template <int W>
 __global__ void __launch_bounds__(32) k_traverse_lev(
-    TreeView tv, QParams qp, Pool P, int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st,
-    int32_t *__restrict__ err, int32_t *__restrict__ next_group, int32_t *__restrict__ gvisit) {
+    TreeView tv, QParams qp, const int4 *__restrict__ in_items, const int32_t *__restrict__ in_count, int in_cap,
+    Spill out, Pool P, longlong2 *__restrict__ cursors, int2 *__restrict__ stacks, int cap,
+    unsigned long long *__restrict__ st, int32_t *__restrict__ err, int32_t *__restrict__ next_group,
+    int32_t *__restrict__ gvisit) {
     __shared__ uint64_t peq[256 * W];
     const int lane = threadIdx.x;
     int2 *stack = stacks + (int64_t)blockIdx.x * cap;
     unsigned long long evals = 0;
+    // the warp's pool chunk carries over from the previous round
     PoolCursor pc{-1, POOL_CHUNK, 0, 0};
+    if (in_items) {
+        const longlong2 c = cursors[blockIdx.x];
+        pc.cur = c.x;
+        pc.fill = (int)c.y;
+    }
+    const int n_work = in_items ? min(*in_count, in_cap) : tv.n_groups;
+    const Spill *sp = out.items ? &out : nullptr;
     for (;;) {
         int gi = 0;
         if (lane == 0) gi = atomicAdd(next_group, 1);
         gi = __shfl_sync(0xffffffffu, gi, 0);
-        if (gi >= tv.n_groups) break;
-        const int g = tv.group_order[gi];
+        if (gi >= n_work) break;
+        int g;
+        int2 start = make_int2(0, 0);
+        if (in_items) {
+            const int4 w = in_items[gi];
+            if (w.z <= 0) continue;  // an empty range (a stop that did not fit)
+            g = w.x;
+            start = make_int2(w.y, w.z);
+        } else {
+            g = tv.group_order[gi];
+        }
         int cpos = tv.group_begin[g];
         const uint8_t *pat = tv.sdata + tv.soff[cpos];
         int m = (int)(tv.soff[cpos + 1] - tv.soff[cpos]);
@@ -463,9 +492,11 @@ __global__ void __launch_bounds__(32) k_traverse_lev(
             return lev_myers<W>(peq, m, txt, n, k) <= k;
         };
         const unsigned long long e0 = evals;
-        if (walk_group(tv, stack, cap, g, make_int2(0, 0), P, pc, evals, err, nullptr, tester) < 0) return;
+        if (walk_group(tv, stack, cap, g, start, P, pc, evals, err, sp, tester) < 0) return;
         if (gvisit) group_visits(gvisit, g, evals - e0);
+        __syncwarp();
     }
+    if (lane == 0) cursors[blockIdx.x] = make_longlong2(pc.cur, pc.fill);
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
     if (lane == 0) stat_add(st, ST_TRAV, evals);
 }
@@ -494,20 +525,39 @@ __device__ __forceinline__ int ham_rows_smem(const uint4 *a, const uint4 *b, int
 }
 
 __global__ void __launch_bounds__(32) k_traverse_ham(
-    TreeView tv, QParams qp, Pool P, int2 *__restrict__ stacks, int cap, unsigned long long *__restrict__ st,
-    int32_t *__restrict__ err, int32_t *__restrict__ next_group, int32_t *__restrict__ gvisit) {
+    TreeView tv, QParams qp, const int4 *__restrict__ in_items, const int32_t *__restrict__ in_count, int in_cap,
+    Spill out, Pool P, longlong2 *__restrict__ cursors, int2 *__restrict__ stacks, int cap,
+    unsigned long long *__restrict__ st, int32_t *__restrict__ err, int32_t *__restrict__ next_group,
+    int32_t *__restrict__ gvisit) {
     __shared__ uint4 cen[32];  // up to 4096 bits
     const int lane = threadIdx.x;
     const int nq = tv.wp >> 2;
     int2 *stack = stacks + (int64_t)blockIdx.x * cap;
     unsigned long long evals = 0;
+    // the warp's pool chunk carries over from the previous round
     PoolCursor pc{-1, POOL_CHUNK, 0, 0};
+    if (in_items) {
+        const longlong2 c = cursors[blockIdx.x];
+        pc.cur = c.x;
+        pc.fill = (int)c.y;
+    }
+    const int n_work = in_items ? min(*in_count, in_cap) : tv.n_groups;
+    const Spill *sp = out.items ? &out : nullptr;
     for (;;) {
         int gi = 0;
         if (lane == 0) gi = atomicAdd(next_group, 1);
         gi = __shfl_sync(0xffffffffu, gi, 0);
-        if (gi >= tv.n_groups) break;
-        const int g = tv.group_order[gi];
+        if (gi >= n_work) break;
+        int g;
+        int2 start = make_int2(0, 0);
+        if (in_items) {
+            const int4 w = in_items[gi];
+            if (w.z <= 0) continue;  // an empty range (a stop that did not fit)
+            g = w.x;
+            start = make_int2(w.y, w.z);
+        } else {
+            g = tv.group_order[gi];
+        }
         const uint4 *crow = reinterpret_cast<const uint4 *>(tv.bits + (size_t)tv.group_begin[g] * tv.wp);
         __syncwarp();
         for (int k = lane; k < nq; k += 32) cen[k] = crow[k];
@@ -520,9 +570,11 @@ __global__ void __launch_bounds__(32) k_traverse_ham(
             return ham_rows(cen, row, nq) <= k;
         };
         const unsigned long long e0 = evals;
-        if (walk_group(tv, stack, cap, g, make_int2(0, 0), P, pc, evals, err, nullptr, tester) < 0) return;
+        if (walk_group(tv, stack, cap, g, start, P, pc, evals, err, sp, tester) < 0) return;
         if (gvisit) group_visits(gvisit, g, evals - e0);
+        __syncwarp();
     }
+    if (lane == 0) cursors[blockIdx.x] = make_longlong2(pc.cur, pc.fill);
     for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
     if (lane == 0) stat_add(st, ST_TRAV, evals);
 }
@@ -2716,7 +2768,9 @@ TravLaunch trav_launch_config(bool l2, int64_t G) {
         tl.blocks = std::max(tl.blocks, 1);
         tl.warps = tl.blocks * TRAV_WARPS;
     } else {
-        tl.blocks = (int)std::max<int64_t>(1, std::min<int64_t>(G, (int64_t)num_sms() * 16));
+        // a warp per block, as many as an SM holds: the later rounds' stored
+        // ranges can outnumber the groups
+        tl.blocks = (int)std::max<int64_t>(1, (int64_t)num_sms() * 32);
         tl.warps = tl.blocks;
     }
     return tl;
@@ -2742,7 +2796,8 @@ int64_t pool_capacity_guess(int64_t n, int64_t G, const TravLaunch &tl) {
 // (`spill`: two buffers of spill_cap items and two counters; the last round
 // has no limit), so that no single long walk sets the time.  Each warp's
 // pool chunk carries over between rounds (`cursors`: one per warp of the
-// grid).  Edit distance: a single cloud, one round.
+// grid).  Hamming and edit distance: a single cloud, the same rounds (one
+// warp per block; edit-distance walks stop sooner: their steps cost more).
 void launch_traversal(const Views &V, int64_t G, int max_dp, int max_len, bool l2, const int32_t *order,
                       const Pool &P, int2 *stacks, int cap, const TravLaunch &tl, unsigned long long *st,
                       int32_t *err, int32_t *next_group, int4 *const spill[2], int32_t *spill_cnt, int spill_cap,
@@ -2775,23 +2830,37 @@ void launch_traversal(const Views &V, int64_t G, int max_dp, int max_len, bool l
             CT_COUNT_LAUNCH();
             CT_LAUNCH_CHECK();
         }
-    } else if (V.tv[0].wp) {
+    } else {  // Hamming or edit distance: one cloud, the same rounds (a warp per block)
         TreeView tv = V.tv[0];
         tv.group_order = order;
-        k_traverse_ham<<<tl.blocks, 32, 0, s>>>(tv, V.qp[0], P, stacks, cap, st, err, next_group, gvisit);
-        CT_COUNT_LAUNCH();
-        CT_LAUNCH_CHECK();
-    } else {
-        TreeView tv = V.tv[0];
-        tv.group_order = order;
-        switch (lev_words_for(max_len)) {
+        const bool ham = tv.wp != 0;
+        CT_CHECK_CUDA(cudaMemsetAsync(spill_cnt, 0, 2 * sizeof(int32_t), s));
+        for (int r = 0; r <= TRAV_ROUNDS; ++r) {
+            const int4 *in = r ? spill[(r - 1) & 1] : nullptr;
+            const int32_t *in_cnt = r ? spill_cnt + ((r - 1) & 1) : nullptr;
+            Spill out{nullptr, spill_cnt + (r & 1), spill_cap, INT_MAX};
+            if (r < TRAV_ROUNDS) {
+                out.items = spill[r & 1];
+                out.limit = ham ? (r ? TRAV_LIMIT : TRAV_LIMIT0) : (r ? TRAV_LIMIT_LEV : TRAV_LIMIT0_LEV);
+            }
+            if (r) {
+                CT_CHECK_CUDA(cudaMemsetAsync(next_group, 0, sizeof(int32_t), s));
+                CT_CHECK_CUDA(cudaMemsetAsync(spill_cnt + (r & 1), 0, sizeof(int32_t), s));
+            }
+            if (ham) {
+                k_traverse_ham<<<tl.blocks, 32, 0, s>>>(tv, V.qp[0], in, in_cnt, spill_cap, out, P, cursors, stacks,
+                                                        cap, st, err, next_group, gvisit);
+            } else {
+                switch (lev_words_for(max_len)) {
 #define CT_TL(WW) \
-    case WW: k_traverse_lev<WW><<<tl.blocks, 32, 0, s>>>(tv, V.qp[0], P, stacks, cap, st, err, next_group, gvisit); break;
-            CT_TL(1) CT_TL(2) CT_TL(4) CT_TL(8) CT_TL(16)
+    case WW: k_traverse_lev<WW><<<tl.blocks, 32, 0, s>>>(tv, V.qp[0], in, in_cnt, spill_cap, out, P, cursors, stacks, cap, st, err, next_group, gvisit); break;
+                    CT_TL(1) CT_TL(2) CT_TL(4) CT_TL(8) CT_TL(16)
 #undef CT_TL
+                }
+            }
+            CT_COUNT_LAUNCH();
+            CT_LAUNCH_CHECK();
         }
-        CT_COUNT_LAUNCH();
-        CT_LAUNCH_CHECK();
     }
 }
 
@@ -2979,12 +3048,12 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     DBuf<int2> stacks((size_t)tl.warps * cap, s);
     DBuf<unsigned long long> ctr(4, s);
     DBuf<int32_t> next_group(1, s);
-    // ranges of step-limited walks (L2): two buffers and their counters
-    const int spill_cap = l2 ? (int)std::min<int64_t>(std::max<int64_t>(4 * G, 1 << 16), 1 << 20) : 0;
+    // ranges of step-limited walks: two buffers and their counters
+    const int spill_cap = (int)std::min<int64_t>(std::max<int64_t>(4 * G, 1 << 16), 1 << 20);
     DBuf<int4> spill_a(spill_cap, s), spill_b(spill_cap, s);
     DBuf<int32_t> spill_cnt(2, s);
     int4 *const spills[2] = {spill_a.p, spill_b.p};
-    DBuf<longlong2> cursors(l2 ? tl.warps : 0, s);
+    DBuf<longlong2> cursors(tl.warps, s);
     int64_t pool_cap = pool_capacity_guess(n, G, tl);
     DBuf<uint32_t> pool;
     DBuf<int32_t> seg_group, seg_count;
