@@ -334,13 +334,47 @@ __global__ void __launch_bounds__(BT, 4) k_dist_update_l2(
     }
 }
 
+// The hub step's decision in the hub's last block (thread 0; every block's
+// key and count have landed): the next centre from the hub's largest key, or
+// the hub is done (nothing above the split threshold, or a flat split where
+// `flat_check`).  The same decision as k_hub_step.
+__device__ __forceinline__ void step_decide(Hubs hb, int h, Step st, bool flat_check) {
+    const unsigned long long k = atomicAdd(&hb.key[h], 0ull);
+    const float v = key_value(k);
+    const int covered = atomicExch(&hb.covered[h], 0);
+    if (k == 0ull || !(v > hb.thr[h])) {
+        hb.done[h] = 1;
+    } else if (flat_check && flat_split(hb.nc[h], covered)) {
+        hb.done[h] = 1;
+        hb.flat[h] = 1;
+    } else {
+        hb.cur[h] = (int32_t)key_pos(k);
+        hb.nc[h] += 1;
+        hb.key[h] = 0ull;
+        atomicAdd(st.active_out, 1);
+    }
+    st.arrive[h] = 0;
+}
+
+// A block's arrival at the end of an update pass (its writes and atomics
+// fenced first): true in every thread of the hub's last block to arrive.
+__device__ __forceinline__ bool last_to_arrive(Step st, int h, int blocks) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st.arrive[h], 1) == blocks - 1;
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last;
+}
+
 // Edit distance: one thread per point; the newest centre is the pattern of
 // the bit-parallel recurrence, its match masks in shared memory.
 template <int W>
 __global__ void __launch_bounds__(BT) k_dist_update_lev(
     const uint8_t *__restrict__ S, const int64_t *__restrict__ off, const int32_t *__restrict__ ids,
     float *__restrict__ D, int32_t *__restrict__ lab, const int32_t *__restrict__ chunk_hub,
-    const int32_t *__restrict__ chunk_start, int chunk_len, Hubs hb) {
+    const int32_t *__restrict__ chunk_start, int chunk_len, Hubs hb, Step st) {
     __shared__ uint64_t peq[256 * W];
     int c = blockIdx.x;
     int h = chunk_hub[c];
@@ -377,6 +411,10 @@ __global__ void __launch_bounds__(BT) k_dist_update_lev(
         best = v > best ? v : best;
     }
     if ((threadIdx.x & 31) == 0 && best) atomicMax(&hb.key[h], best);
+    if (st.arrive) {  // the hub's last block takes its next step (no flat-split test: no counts here)
+        const int blocks = (hb.count[h] + chunk_len - 1) / chunk_len;  // all of the hub's chunks run
+        if (last_to_arrive(st, h, blocks) && threadIdx.x == 0) step_decide(hb, h, st, false);
+    }
 }
 
 // ---- Hamming distance: rows of wp 32-bit words (wp a multiple of 4),
@@ -414,7 +452,7 @@ __global__ void k_pack_bits(const uint8_t *__restrict__ src, int64_t n, int dim,
 __global__ void __launch_bounds__(BT) k_dist_update_ham(
     const uint32_t *__restrict__ X, int wp, const int32_t *__restrict__ ids, float *__restrict__ D,
     int32_t *__restrict__ lab, const int32_t *__restrict__ chunk_hub, const int32_t *__restrict__ chunk_start,
-    int chunk_len, Hubs hb) {
+    int chunk_len, Hubs hb, Step st) {
     extern __shared__ uint4 hcen[];
     const int c = blockIdx.x;
     const int h = chunk_hub[c];
@@ -452,6 +490,10 @@ __global__ void __launch_bounds__(BT) k_dist_update_ham(
     if ((threadIdx.x & 31) == 0) {
         if (best) atomicMax(&hb.key[h], best);
         if (cov) atomicAdd(&hb.covered[h], cov);
+    }
+    if (st.arrive) {  // the hub's last block takes its next step
+        const int blocks = (hb.count[h] + chunk_len - 1) / chunk_len;  // all of the hub's chunks run
+        if (last_to_arrive(st, h, blocks) && threadIdx.x == 0) step_decide(hb, h, st, true);
     }
 }
 
@@ -1254,11 +1296,11 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
                 }
             } else if (ham) {
                 k_dist_update_ham<<<(unsigned)nchunks, BT, (size_t)wp * sizeof(uint32_t), s>>>(
-                    Xb.p, wp, ids.p, D.p, lab.p, chub, cst, chunk_len, hb);
+                    Xb.p, wp, ids.p, D.p, lab.p, chub, cst, chunk_len, hb, st);
             } else {
                 const uint8_t *S = (const uint8_t *)pts->data;
                 switch (W) {
-#define CT_UPDL(WW) case WW: k_dist_update_lev<WW><<<(unsigned)nchunks, BT, 0, s>>>(S, pts->offsets, ids.p, D.p, lab.p, chub, cst, chunk_len, hb); break;
+#define CT_UPDL(WW) case WW: k_dist_update_lev<WW><<<(unsigned)nchunks, BT, 0, s>>>(S, pts->offsets, ids.p, D.p, lab.p, chub, cst, chunk_len, hb, st); break;
                     CT_UPDL(1) CT_UPDL(2) CT_UPDL(4) CT_UPDL(8) CT_UPDL(16)
 #undef CT_UPDL
                 }
@@ -1307,7 +1349,7 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
         DBuf<float> tD(n, s);
         DBuf<int32_t> active(3, s);  // hub activations of a burst, active hubs, active chunks
         DBuf<int32_t> hlist(n, s), chub2(nchunks0, s), cst2(nchunks0, s);
-        DBuf<int32_t> arrive(l2 ? cap_h + 1 : 1, s);  // per hub: finished blocks of an update pass
+        DBuf<int32_t> arrive(cap_h + 1, s);  // per hub: finished blocks of an update pass
         DBuf<int64_t> i64tmp(2, s);
 
         while (nh > 0) {
@@ -1387,11 +1429,16 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
                         const Step st{arrive.p, active.p, cpos.p, dcc.p};
                         for (int it = 0; it < burst; ++it) update(H, nck, cb, cs, st);
                     } else {
-                        for (int it = 0; it < burst; ++it) {
+                        // the level's first step by k_hub_step; every later step
+                        // is taken inside the update pass by each hub's last block
+                        if (first_step) {
+                            CT_CHECK_CUDA(cudaMemsetAsync(arrive.p, 0, nh * sizeof(int32_t), s));
                             k_hub_step<<<grid_for(nl), BT, 0, s>>>((int)nl, hl, H, active.p, nullptr, ham ? 1 : 0);
                             CT_COUNT_LAUNCH();
-                            update(H, nck, cb, cs, Step{});
+                            first_step = false;
                         }
+                        const Step st{arrive.p, active.p, nullptr, nullptr};
+                        for (int it = 0; it < burst; ++it) update(H, nck, cb, cs, st);
                     }
                     k_active_hubs<<<grid_for(nh), BT, 0, s>>>((int)nh, H.done, hlist.p, active.p + 1);
                     CT_COUNT_LAUNCH();
