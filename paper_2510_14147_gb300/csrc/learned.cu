@@ -207,6 +207,12 @@ __global__ void k_capacity(int64_t n, const float *__restrict__ y, const int32_t
     }
 }
 
+// Capacities scaled by f (the one-pass buffers over their memory budget).
+__global__ void k_scale_capacity(int64_t n, double f, int32_t *__restrict__ cap) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cap[i] = (int32_t)floor((double)cap[i] * f);
+}
+
 // Traversal order: per group the mean predicted walk length of its queries;
 // sort key larger first.
 __global__ void k_group_keys(int G, const int32_t *__restrict__ group_begin, const int32_t *__restrict__ group_count,
@@ -402,17 +408,36 @@ void learned_plan(const ct_predictor *P, int C, const ct_tree *const *trees, con
     }
     int64_t total = 0;
     to_host(&total, lp.cap_off.p + n, 1, s);
-    lp.cap_total = total;
     lp.arena = (int64_t)std::ceil((double)P->arena_frac * (double)total) + P->arena_min;
-    // the one-pass buffers must fit comfortably; else the two-pass form
+    // the one-pass buffers (capacities and arena) take at most a third of the
+    // free device memory: predictions that ask for more (a predictor far from
+    // its training data) are scaled down to that budget -- entries past a
+    // row's capacity go to the arena, rows past the arena are emitted again
+    // exactly -- and only a budget below the arena's minimum takes the
+    // two-pass form
     lp.one_pass = true;
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+        const double budget = (double)fr / 3.0;
         const double need = (double)total * 8.0 + (double)lp.arena * 16.0;
-        if (need > (double)fr / 3.0) lp.one_pass = false;
+        if (need > budget) {
+            const double room = budget - 16.0 * (double)P->arena_min;
+            if (room <= 0.0) {
+                lp.one_pass = false;
+            } else {
+                const double f = room / ((double)total * (8.0 + 16.0 * (double)P->arena_frac));
+                k_scale_capacity<<<grid_of(n, 256), 256, 0, s>>>(n, f, cap.p);
+                CT_COUNT_LAUNCH();
+                CT_LAUNCH_CHECK();
+                exclusive_scan_i32_to_i64(cap.p, lp.cap_off.p, n + 1, nullptr, s);
+                to_host(&total, lp.cap_off.p + n, 1, s);
+                lp.arena = (int64_t)std::ceil((double)P->arena_frac * (double)total) + P->arena_min;
+            }
+        }
     } else {
         cudaGetLastError();
     }
+    lp.cap_total = total;
 }
 
 void query_predicted(const ct_tree *t, const QParams &qp, const void *predictor, int precision, cudaStream_t s,
