@@ -42,9 +42,6 @@ constexpr uint32_t FLAG = 0x80000000u;     // candidate produced an edge
 constexpr float PRUNE_REL = 1.0f + 0x1p-10f;
 constexpr float PRUNE_ABS = 0x1p-60f;
 
-__device__ __forceinline__ void prefetch_l1(const void *p) {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
 
 // Diagnostic (off unless a test sets it): the CSR rows of both ends of every
 // pair a count pass decides by the FP64 sum, appended to a caller's buffer.
@@ -2137,14 +2134,6 @@ __global__ void __launch_bounds__(TC_T, 2) k_leaf_tc(const __grid_constant__ Vie
             tc::fence_before_sync();
             __syncthreads();
             const int n = S.kn[bf];
-            // the first recheck round's rows are prefetched into L1
-            if ((tid >> 3) < min(n, TC_KL)) {
-                const int e = S.kl[tid >> 3], k0 = 4 * (lane & 7);
-                if (k0 < dp4) {
-                    prefetch_l1(pts4 + (size_t)(qfirst + (e >> 7)) * dp4 + k0);
-                    prefetch_l1(pts4 + (size_t)S.pos[sl][e & 127] * dp4 + k0);
-                }
-            }
             if (tid == 0) {
                 kept += n;
                 S.kn[bf ^ 1] = 0;  // tile t + 1's list (filled after the next barrier)
