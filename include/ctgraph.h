@@ -505,6 +505,15 @@ ct_status ct_debug_fail_alloc(int64_t k);
  * that a failed call leaked nothing.  Errors: CT_EINVAL, CT_ECUDA. */
 ct_status ct_debug_pool_used(uint64_t *bytes);
 
+/* Test hook: the memory budget, in bytes, of the learned form's one-pass
+ * buffers (the capacity region and the overflow arena), process-wide, in
+ * place of the default -- a third of the free device memory; 0 restores the
+ * default.  Predicted capacities that need more are scaled down to the budget
+ * (entries past a row's capacity go to the arena, rows past the arena are
+ * emitted again exactly); a budget below the arena's minimum takes the
+ * two-pass emit.  Errors: CT_EINVAL (bytes < 0). */
+ct_status ct_debug_capacity_budget(int64_t bytes);
+
 /* Thread-local message for the last non-OK status of this thread. */
 const char *ct_last_error(void);
 

@@ -433,6 +433,13 @@ ct_status ct_debug_fail_alloc(int64_t k) {
     });
 }
 
+ct_status ct_debug_capacity_budget(int64_t bytes) {
+    return guarded([&] {
+        if (bytes < 0) CT_FAIL(CT_EINVAL, "bytes must be >= 0");
+        ct::set_capacity_budget(bytes);
+    });
+}
+
 ct_status ct_debug_pool_used(uint64_t *bytes) {
     return guarded([&] {
         if (!bytes) CT_FAIL(CT_EINVAL, "bytes is NULL");

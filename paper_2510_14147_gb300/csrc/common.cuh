@@ -49,6 +49,9 @@ void *dmalloc(size_t bytes, cudaStream_t s);
 void dfree(void *p, cudaStream_t s);
 // Test hook: the k-th next dmalloc (k >= 1) fails with CT_ENOMEM; 0 turns it off.
 void set_fail_alloc(int64_t k);
+// Budget of the learned form's one-pass buffers in bytes (0: a third of the
+// free device memory).
+void set_capacity_budget(int64_t bytes);
 
 // Owning buffer freed stream-ordered when it goes out of scope.
 template <class T>

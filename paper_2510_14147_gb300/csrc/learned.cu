@@ -4,6 +4,7 @@
 // walked in order of decreasing predicted walk length).  The paper has no
 // learned component; the output is the same edge set as the two-pass form
 // whatever the predictions are.
+#include <atomic>
 #include <cmath>
 #include <random>
 #include <vector>
@@ -206,6 +207,8 @@ __global__ void k_capacity(int64_t n, const float *__restrict__ y, const int32_t
         cap[o] = (int32_t)(c < n ? c : n);
     }
 }
+
+std::atomic<int64_t> g_capacity_budget{0};
 
 // Capacities scaled by f (the one-pass buffers over their memory budget).
 __global__ void k_scale_capacity(int64_t n, double f, int32_t *__restrict__ cap) {
@@ -417,8 +420,9 @@ void learned_plan(const ct_predictor *P, int C, const ct_tree *const *trees, con
     // two-pass form
     lp.one_pass = true;
     size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
-        const double budget = (double)fr / 3.0;
+    const int64_t fixed = g_capacity_budget.load();
+    if (fixed > 0 || cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+        const double budget = fixed > 0 ? (double)fixed : (double)fr / 3.0;
         const double need = (double)total * 8.0 + (double)lp.arena * 16.0;
         if (need > budget) {
             const double room = budget - 16.0 * (double)P->arena_min;
@@ -439,6 +443,8 @@ void learned_plan(const ct_predictor *P, int C, const ct_tree *const *trees, con
     }
     lp.cap_total = total;
 }
+
+void set_capacity_budget(int64_t bytes) { g_capacity_budget.store(bytes > 0 ? bytes : 0); }
 
 void query_predicted(const ct_tree *t, const QParams &qp, const void *predictor, int precision, cudaStream_t s,
                      QueryOut &out) {

@@ -174,6 +174,8 @@ def _load():
         lib.ct_debug_fail_alloc.argtypes = [C.c_int64]
         lib.ct_debug_pool_used.restype = C.c_int
         lib.ct_debug_pool_used.argtypes = [P(C.c_uint64)]
+        lib.ct_debug_capacity_budget.restype = C.c_int
+        lib.ct_debug_capacity_budget.argtypes = [C.c_int64]
         lib.ct_debug_guard_rows.restype = C.c_int
         lib.ct_debug_guard_rows.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
         lib.eps_graph_query_landmark.restype = C.c_int
@@ -458,6 +460,11 @@ def ct_selftest_tc_timeout(stream=None):
 def ct_debug_fail_alloc(k: int):
     """Test hook: the k-th next device allocation of the library fails (0: off)."""
     _check(_load().ct_debug_fail_alloc(int(k)))
+
+
+def ct_debug_capacity_budget(nbytes: int):
+    """Test hook: the learned form's one-pass buffers get this many bytes (0: the default)."""
+    _check(_load().ct_debug_capacity_budget(int(nbytes)))
 
 
 def ct_debug_pool_used() -> int:

@@ -276,6 +276,43 @@ def test_learned_form_is_faster_than_two_pass():
         h.free()
 
 
+def test_one_pass_under_a_memory_budget():
+    """The one-pass buffers under a memory budget below what the predicted
+    capacities ask for: the capacities are scaled down to the budget, entries
+    past them go to the overflow arena and rows past the arena are emitted
+    again exactly -- the CSR equals the two-pass form's, with the re-emit
+    taken when the budget is far too small.  A budget below the arena's
+    minimum takes the two-pass emit (the same CSR)."""
+    cg = _cg()
+    x = I.gmm_embedded(20000, dim=32, intrinsic=6, n_centres=8, seed=51)
+    d = oracle.brute_rows(oracle.Space(points=x), 1e30, [0, 1, 2, 3])["dist"]
+    eps = float(np.float32(np.quantile(d, 60.0 / 20000)))
+    t = _tree(points=x)
+    p = _fit(t, eps, steps=300)
+    two = _query(t, eps)
+    nnz = int(two["row_ptr"][-1])
+    arena_min_bytes = 65536 * 16
+    try:
+        # room for about the whole graph: scaled capacities, the arena takes the rest
+        cg.ct_debug_capacity_budget(arena_min_bytes + 12 * nnz)
+        one = _query(t, eps, use_predictor=True, predictor=p)
+        _same(one, two)
+        # room for an eighth of it: most rows lose entries and are emitted again
+        cg.ct_debug_capacity_budget(arena_min_bytes + 12 * (nnz // 8))
+        one = _query(t, eps, use_predictor=True, predictor=p)
+        _same(one, two)
+        assert one["stats"]["reemit_rows"] > 0
+        # below the arena's minimum: the two-pass emit
+        cg.ct_debug_capacity_budget(arena_min_bytes // 2)
+        one = _query(t, eps, use_predictor=True, predictor=p)
+        _same(one, two)
+        assert one["stats"]["emit_pairs"] > 0
+    finally:
+        cg.ct_debug_capacity_budget(0)
+    for h in (p, t):
+        h.free()
+
+
 def test_unfitted_predictor_is_rejected():
     cg = _cg()
     t = _tree(points=I.uniform_cube(100, 3, seed=0))
