@@ -2506,16 +2506,21 @@ __global__ void k_alphabet(const uint8_t *__restrict__ s, int64_t nbytes, int32_
 
 constexpr int SORT_MID = 4096;  // rows up to this length are sorted in one CTA
 
-// Row classes by length: 0 <= 32, 1 <= 128, 2 <= 512, 3 <= 1024, 4 <= SORT_MID, 5 longer.
-constexpr int kSortClasses = 6;
+// Row classes by length: 0 <= 32, 1 <= 64, 2 <= 128, 3 <= 256, 4 <= 512 (one
+// warp per row), 5 <= 1024, 6 <= 2048, 7 <= SORT_MID (one CTA per row), 8 longer.
+constexpr int kSortClasses = 9;
 __global__ void k_row_classes(const int64_t *__restrict__ row_ptr, int64_t n, int32_t *__restrict__ lists,
                               int32_t *__restrict__ counts) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t len = row_ptr[i + 1] - row_ptr[i];
-    int cls = len <= 1 ? -1 : len <= 32 ? 0 : len <= 128 ? 1 : len <= 512 ? 2 : len <= 1024 ? 3
-                                                              : len <= SORT_MID ? 4 : 5;
-    if (cls < 0) return;
+    if (len <= 1) return;
+    int cls = kSortClasses - 1;
+    for (int c = 0; c < kSortClasses - 1; ++c)
+        if (len <= (int64_t)32 << c) {
+            cls = c;
+            break;
+        }
     int slot = atomicAdd(&counts[cls], 1);
     lists[(int64_t)cls * n + slot] = (int32_t)i;
 }
@@ -2538,62 +2543,446 @@ __device__ __forceinline__ void warp_sort32(int &key, float &val, int lane) {
     }
 }
 
-// CTA of P threads per row of 33 .. CAP entries (16 CAP bytes of dynamic
-// shared memory): warps sort runs of 32
-// entries (warp_sort32), then runs are merged in pairs in shared memory until
-// one is left.  The columns of a row are distinct, so an entry's place in the
-// merged run is its index in its own run plus the number of smaller entries
-// in the partner run (a binary search) -- every entry moves independently,
-// one barrier per merge round.
-template <int P, int CAP>
-__global__ void __launch_bounds__(P) k_sort_merge(const int32_t *__restrict__ rows, const int32_t *__restrict__ count,
-                                                  const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col,
-                                                  float *__restrict__ dist) {
-    extern __shared__ int sort_smem[];  // 16 CAP bytes: keys, then values, two buffers each
+// A warp's 32 E entries in the blocked layout: lane l holds entries l E ..
+// l E + E - 1 in registers.  In shared memory entry i sits at swz<E>(i), its
+// low bits XORed with bits 5.., so that a warp's striped access (entries
+// c 32 + lane, coalesced in global memory) and its blocked access (entries
+// lane E + e) both hit 32 distinct banks.
+template <int E>
+__device__ __forceinline__ int swz(int i) {
+    return i ^ ((i >> 5) & (E - 1));
+}
+
+// Bitonic sorting network over 32 E (key, val) pairs in the blocked layout,
+// ascending by key.  Exchanges at distances below E pair entries of one lane
+// (registers only); the others pair lane l with lane l ^ (distance / E) at
+// the same register (one shuffle of key and of val).  The low distances,
+// which the network visits most often, are thus the register ones.
+template <int E>
+__device__ __forceinline__ void warp_sort_blocked(int (&key)[E], float (&val)[E], int lane) {
+    constexpr int N = 32 * E;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j < E) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if (e & j) continue;
+                    const int f = e | j;
+                    const bool up = ((lane * E + e) & k) == 0;
+                    // selects, not a branch: lanes disagree on the swap
+                    const int a = key[e], c = key[f];
+                    const float va = val[e], vc = val[f];
+                    const bool sw = (a > c) == up;
+                    key[e] = sw ? c : a;
+                    key[f] = sw ? a : c;
+                    val[e] = sw ? vc : va;
+                    val[f] = sw ? va : vc;
+                }
+            } else {
+                const int lj = j / E;
+                const bool keep_min = (((lane * E) & k) == 0) == ((lane & lj) == 0);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int ok = __shfl_xor_sync(0xffffffffu, key[e], lj);
+                    const float ov = __shfl_xor_sync(0xffffffffu, val[e], lj);
+                    const bool take = (ok < key[e]) == keep_min;  // equal keys: padding only
+                    key[e] = take ? ok : key[e];
+                    val[e] = take ? ov : val[e];
+                }
+            }
+        }
+    }
+}
+
+// One warp's blocked registers from / to its swizzled shared slice sh
+// (entries at or past len read as INT_MAX keys).
+template <int E>
+__device__ __forceinline__ void take_blocked(const int *sh, const float *sv, int len, int lane, int (&key)[E],
+                                             float (&val)[E]) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = lane * E + e;
+        key[e] = i < len ? sh[swz<E>(i)] : INT_MAX;
+        val[e] = i < len ? sv[swz<E>(i)] : 0.f;
+    }
+}
+template <int E>
+__device__ __forceinline__ void put_blocked(int *sh, float *sv, int lane, const int (&key)[E], const float (&val)[E]) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        sh[swz<E>(lane * E + e)] = key[e];
+        sv[swz<E>(lane * E + e)] = val[e];
+    }
+}
+
+constexpr int SORT_WARPS = 8;  // warps per CTA of k_sort_warp
+
+// Warp per row of 16 E + 1 .. 32 E entries (E = 2 .. 16): the row is read
+// coalesced into the warp's shared slice (all its loads issued before the
+// first store), taken into registers in the blocked layout, sorted by
+// warp_sort_blocked and written back the same way.
+template <int E>
+__global__ void __launch_bounds__(32 * SORT_WARPS, 3) k_sort_warp(const int32_t *__restrict__ rows,
+                                                               const int32_t *__restrict__ count,
+                                                               const int64_t *__restrict__ row_ptr,
+                                                               int32_t *__restrict__ col, float *__restrict__ dist) {
+    __shared__ int s_key[SORT_WARPS][32 * E];
+    __shared__ float s_val[SORT_WARPS][32 * E];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *sk = s_key[wib];
+    float *sv = s_val[wib];
+    const int nrows = *count;
+    for (int w = blockIdx.x * SORT_WARPS + wib; w < nrows; w += gridDim.x * SORT_WARPS) {
+        const int r = rows[w];
+        const int64_t b = row_ptr[r];
+        const int len = (int)min(row_ptr[r + 1] - b, (int64_t)(32 * E));  // rows of this class fit
+        int key[E];
+        float val[E];
+#pragma unroll
+        for (int c = 0; c < E; ++c) {
+            const int i = c * 32 + lane;
+            key[c] = i < len ? col[b + i] : 0;
+            val[c] = i < len ? dist[b + i] : 0.f;
+        }
+        __syncwarp();  // the previous row's write-back has read the slice
+#pragma unroll
+        for (int c = 0; c < E; ++c) {
+            const int i = c * 32 + lane;
+            if (i < len) {
+                sk[swz<E>(i)] = key[c];
+                sv[swz<E>(i)] = val[c];
+            }
+        }
+        __syncwarp();
+        take_blocked<E>(sk, sv, len, lane, key, val);
+        warp_sort_blocked<E>(key, val, lane);
+        __syncwarp();
+        put_blocked<E>(sk, sv, lane, key, val);
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < E; ++c) {
+            const int i = c * 32 + lane;
+            if (i < len) {
+                col[b + i] = sk[swz<E>(i)];
+                dist[b + i] = sv[swz<E>(i)];
+            }
+        }
+    }
+}
+
+// One merge round of a row's sorted runs of length run (the last may be
+// shorter or alone): the pair (A, B) = runs 2 m, 2 m + 1 goes to the outputs
+// [2 m run, ...) of buffers (kn, vn).  Thread tid writes the SEG outputs from
+// tid SEG: one binary search along its diagonal finds how many of them come
+// from A (merge path), then it merges them one by one.  SWZ: the source runs
+// are 512-entry runs in the swizzled layout (swz<16> within each run).
+template <int SEG, bool SWZ>
+__device__ __forceinline__ void merge_round(const int *__restrict__ kc, const float *__restrict__ vc,
+                                            int *__restrict__ kn, float *__restrict__ vn, int len, int run,
+                                            int tid) {
+    const int o = tid * SEG;
+    if (o >= len) return;
+    const int s0 = o & ~(2 * run - 1);
+    const int na = min(run, len - s0), nb = max(0, min(run, len - s0 - run));
+    const int *A = kc + s0, *B = A + run;
+    const float *Av = vc + s0, *Bv = Av + run;
+    auto at = [](int i) { return SWZ ? swz<16>(i) : i; };  // within a 512-entry run when SWZ
+    const int d = o - s0;  // outputs of the pair before this thread's
+    int lo = max(0, d - nb), hi = min(d, na);
+    while (lo < hi) {  // entries of A among the pair's d smallest
+        const int mid = (lo + hi) >> 1;
+        if (A[at(mid)] < B[at(d - 1 - mid)]) lo = mid + 1; else hi = mid;
+    }
+    // An exhausted run's head reads INT_MAX, above every column, so the other
+    // run is taken; each step selects, no branch.
+    int ia = lo, ib = d - lo;
+    int ka = ia < na ? A[at(ia)] : INT_MAX, kb = ib < nb ? B[at(ib)] : INT_MAX;
+    const int cnt = min(SEG, len - o);
+#pragma unroll 4
+    for (int t = 0; t < cnt; ++t) {
+        const bool ta = ka < kb;
+        kn[o + t] = ta ? ka : kb;
+        vn[o + t] = ta ? Av[at(ia)] : Bv[at(ib)];
+        ia += ta;
+        ib += !ta;
+        const int nx = ta ? ia : ib;
+        const int nk = nx < (ta ? na : nb) ? (ta ? A : B)[at(nx)] : INT_MAX;
+        ka = ta ? nk : ka;
+        kb = ta ? kb : nk;
+    }
+}
+
+// CTA of P = CAP / 16 threads per row of 513 .. CAP entries (16 CAP bytes of
+// dynamic shared memory: keys and values, two buffers each).  Each warp sorts
+// one 512-entry run in registers (warp_sort_blocked<16>) and leaves it in the
+// swizzled layout; then runs merge in pairs (merge_round) until one is left.
+// The columns of a row are distinct, so the merged order is unique.
+template <int CAP>
+__global__ void __launch_bounds__(CAP / 16, 12288 / CAP) k_sort_merge(const int32_t *__restrict__ rows,
+                                                                      const int32_t *__restrict__ count,
+                                                                      const int64_t *__restrict__ row_ptr,
+                                                                      int32_t *__restrict__ col,
+                                                                      float *__restrict__ dist) {
+    constexpr int P = CAP / 16, SEG = 16, RUN = 512;
+    extern __shared__ int sort_smem[];
     int (*sk)[CAP] = reinterpret_cast<int (*)[CAP]>(sort_smem);
     float (*sv)[CAP] = reinterpret_cast<float (*)[CAP]>(sort_smem + 2 * CAP);
     const int tid = threadIdx.x, lane = tid & 31;
-    for (int w = blockIdx.x; w < *count; w += gridDim.x) {
+    const int nrows = *count;
+    for (int w = blockIdx.x; w < nrows; w += gridDim.x) {
         const int r = rows[w];
         const int64_t b = row_ptr[r];
-        const int64_t len64 = row_ptr[r + 1] - b;
-        const int len = len64 < CAP ? (int)len64 : CAP;  // rows of this class have at most CAP entries
-        __syncthreads();  // the previous row's write-back has read sk / sv
-        for (int rs = tid & ~31; rs < len; rs += P) {
-            const int i = rs + lane;
-            int key = i < len ? col[b + i] : INT_MAX;
-            float val = i < len ? dist[b + i] : 0.f;
-            warp_sort32(key, val, lane);
-            if (i < len) {
-                sk[0][i] = key;
-                sv[0][i] = val;
+        const int len = (int)min(row_ptr[r + 1] - b, (int64_t)CAP);  // rows of this class fit
+        {  // coalesced read: SEG loads a thread, then the stores, each run swizzled
+            int key[SEG];
+            float val[SEG];
+#pragma unroll
+            for (int c = 0; c < SEG; ++c) {
+                const int i = c * P + tid;
+                key[c] = i < len ? col[b + i] : 0;
+                val[c] = i < len ? dist[b + i] : 0.f;
+            }
+            __syncthreads();  // the previous row's write-back has read sk / sv
+#pragma unroll
+            for (int c = 0; c < SEG; ++c) {
+                const int i = c * P + tid;
+                if (i < len) {
+                    const int p = (i & ~(RUN - 1)) | swz<16>(i & (RUN - 1));
+                    sk[0][p] = key[c];
+                    sv[0][p] = val[c];
+                }
             }
         }
         __syncthreads();
-        int cur = 0;
-        for (int run = 32; run < len; run <<= 1) {
-            for (int p = tid; p < len; p += P) {
-                const int start = p & ~(run - 1), pst = start ^ run;  // own run, partner run
-                const int key = sk[cur][p];
-                const float val = sv[cur][p];
-                int out = p;  // the last run without a partner keeps its place
-                if (pst < len) {
-                    int lo = pst, hi = min(pst + run, len);
-                    while (lo < hi) {  // partner entries below key
-                        const int mid = (lo + hi) >> 1;
-                        if (sk[cur][mid] < key) lo = mid + 1; else hi = mid;
-                    }
-                    out = min(start, pst) + (p - start) + (lo - pst);
-                }
-                sk[cur ^ 1][out] = key;
-                sv[cur ^ 1][out] = val;
-            }
+        const int base = (tid >> 5) * RUN;
+        if (base < len) {  // the warp's run, sorted in place
+            int key[16];
+            float val[16];
+            take_blocked<16>(sk[0] + base, sv[0] + base, len - base, lane, key, val);
+            warp_sort_blocked<16>(key, val, lane);
+            __syncwarp();
+            put_blocked<16>(sk[0] + base, sv[0] + base, lane, key, val);
+        }
+        __syncthreads();
+        merge_round<SEG, true>(sk[0], sv[0], sk[1], sv[1], len, RUN, tid);
+        __syncthreads();
+        int cur = 1;
+        for (int run = 2 * RUN; run < len; run <<= 1) {
+            merge_round<SEG, false>(sk[cur], sv[cur], sk[cur ^ 1], sv[cur ^ 1], len, run, tid);
             __syncthreads();
             cur ^= 1;
         }
-        for (int i = tid; i < len; i += P) {
-            col[b + i] = sk[cur][i];
-            dist[b + i] = sv[cur][i];
+#pragma unroll
+        for (int c = 0; c < SEG; ++c) {
+            const int i = c * P + tid;
+            if (i < len) {
+                col[b + i] = sk[cur][i];
+                dist[b + i] = sv[cur][i];
+            }
+        }
+    }
+}
+
+// Rows of a graph with fewer than 2^20 columns sort one 32-bit key per
+// entry, (column << PACK_BITS) | (the entry's position in the row, below
+// SORT_MID): a row's keys are distinct and order as its columns do, so the
+// network moves keys alone (min / max, no selects of values) and each value
+// is fetched by its position once the keys are sorted.
+constexpr int PACK_BITS = 12;
+constexpr uint32_t PACK_POS = (1u << PACK_BITS) - 1;
+constexpr int64_t PACK_MAX_COLS = int64_t(1) << (32 - PACK_BITS);  // packed when n (columns < n) is below
+static_assert(SORT_MID <= (1 << PACK_BITS), "positions must fit the packed keys");
+
+// warp_sort_blocked on keys alone (padding: 0xffffffff, above every key).
+template <int E>
+__device__ __forceinline__ void warp_sort_keys(uint32_t (&key)[E], int lane) {
+    constexpr int N = 32 * E;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j < E) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if (e & j) continue;
+                    const int f = e | j;
+                    const bool up = ((lane * E + e) & k) == 0;
+                    const uint32_t lo = min(key[e], key[f]), hi = max(key[e], key[f]);
+                    key[e] = up ? lo : hi;
+                    key[f] = up ? hi : lo;
+                }
+            } else {
+                const int lj = j / E;
+                const bool keep_min = (((lane * E) & k) == 0) == ((lane & lj) == 0);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const uint32_t o = __shfl_xor_sync(0xffffffffu, key[e], lj);
+                    key[e] = keep_min ? min(key[e], o) : max(key[e], o);
+                }
+            }
+        }
+    }
+}
+
+// merge_round on packed keys alone.
+template <int SEG, bool SWZ>
+__device__ __forceinline__ void merge_round_keys(const uint32_t *__restrict__ kc, uint32_t *__restrict__ kn,
+                                                 int len, int run, int tid) {
+    const int o = tid * SEG;
+    if (o >= len) return;
+    const int s0 = o & ~(2 * run - 1);
+    const int na = min(run, len - s0), nb = max(0, min(run, len - s0 - run));
+    const uint32_t *A = kc + s0, *B = A + run;
+    auto at = [](int i) { return SWZ ? swz<16>(i) : i; };
+    const int d = o - s0;
+    int lo = max(0, d - nb), hi = min(d, na);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (A[at(mid)] < B[at(d - 1 - mid)]) lo = mid + 1; else hi = mid;
+    }
+    int ia = lo, ib = d - lo;
+    uint32_t ka = ia < na ? A[at(ia)] : 0xffffffffu, kb = ib < nb ? B[at(ib)] : 0xffffffffu;
+    const int cnt = min(SEG, len - o);
+#pragma unroll 4
+    for (int t = 0; t < cnt; ++t) {
+        const bool ta = ka < kb;
+        kn[o + t] = min(ka, kb);
+        ia += ta;
+        ib += !ta;
+        const int nx = ta ? ia : ib;
+        const uint32_t nk = nx < (ta ? na : nb) ? (ta ? A : B)[at(nx)] : 0xffffffffu;
+        ka = ta ? nk : ka;
+        kb = ta ? kb : nk;
+    }
+}
+
+// k_sort_warp on packed keys: the values wait in shared memory in row order.
+template <int E>
+__global__ void __launch_bounds__(32 * SORT_WARPS, 4) k_sort_warp_packed(const int32_t *__restrict__ rows,
+                                                                         const int32_t *__restrict__ count,
+                                                                         const int64_t *__restrict__ row_ptr,
+                                                                         int32_t *__restrict__ col,
+                                                                         float *__restrict__ dist) {
+    __shared__ uint32_t s_key[SORT_WARPS][32 * E];
+    __shared__ float s_val[SORT_WARPS][32 * E];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *sk = s_key[wib];
+    float *sv = s_val[wib];
+    const int nrows = *count;
+    for (int w = blockIdx.x * SORT_WARPS + wib; w < nrows; w += gridDim.x * SORT_WARPS) {
+        const int r = rows[w];
+        const int64_t b = row_ptr[r];
+        const int len = (int)min(row_ptr[r + 1] - b, (int64_t)(32 * E));  // rows of this class fit
+        uint32_t key[E];
+        float val[E];
+#pragma unroll
+        for (int c = 0; c < E; ++c) {
+            const int i = c * 32 + lane;
+            key[c] = i < len ? ((uint32_t)col[b + i] << PACK_BITS) | (uint32_t)i : 0u;
+            val[c] = i < len ? dist[b + i] : 0.f;
+        }
+        __syncwarp();  // the previous row's write-back has read the slice
+#pragma unroll
+        for (int c = 0; c < E; ++c) {
+            const int i = c * 32 + lane;
+            if (i < len) {
+                sk[swz<E>(i)] = key[c];
+                sv[i] = val[c];
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = lane * E + e;
+            key[e] = i < len ? sk[swz<E>(i)] : 0xffffffffu;
+        }
+        warp_sort_keys<E>(key, lane);
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < E; ++e) sk[swz<E>(lane * E + e)] = key[e];
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < E; ++c) {
+            const int i = c * 32 + lane;
+            if (i < len) {
+                const uint32_t kk = sk[swz<E>(i)];
+                col[b + i] = (int32_t)(kk >> PACK_BITS);
+                dist[b + i] = sv[kk & PACK_POS];
+            }
+        }
+    }
+}
+
+// k_sort_merge on packed keys (12 CAP bytes of dynamic shared memory: two
+// key buffers and the values in row order).
+template <int CAP>
+__global__ void __launch_bounds__(CAP / 16, 16384 / CAP) k_sort_merge_packed(const int32_t *__restrict__ rows,
+                                                                             const int32_t *__restrict__ count,
+                                                                             const int64_t *__restrict__ row_ptr,
+                                                                             int32_t *__restrict__ col,
+                                                                             float *__restrict__ dist) {
+    constexpr int P = CAP / 16, SEG = 16, RUN = 512;
+    extern __shared__ uint32_t sort_smem_packed[];
+    uint32_t (*sk)[CAP] = reinterpret_cast<uint32_t (*)[CAP]>(sort_smem_packed);
+    float *sv = reinterpret_cast<float *>(sort_smem_packed + 2 * CAP);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nrows = *count;
+    for (int w = blockIdx.x; w < nrows; w += gridDim.x) {
+        const int r = rows[w];
+        const int64_t b = row_ptr[r];
+        const int len = (int)min(row_ptr[r + 1] - b, (int64_t)CAP);  // rows of this class fit
+        {
+            uint32_t key[SEG];
+            float val[SEG];
+#pragma unroll
+            for (int c = 0; c < SEG; ++c) {
+                const int i = c * P + tid;
+                key[c] = i < len ? ((uint32_t)col[b + i] << PACK_BITS) | (uint32_t)i : 0u;
+                val[c] = i < len ? dist[b + i] : 0.f;
+            }
+            __syncthreads();  // the previous row's write-back has read sk / sv
+#pragma unroll
+            for (int c = 0; c < SEG; ++c) {
+                const int i = c * P + tid;
+                if (i < len) {
+                    sk[0][(i & ~(RUN - 1)) | swz<16>(i & (RUN - 1))] = key[c];
+                    sv[i] = val[c];
+                }
+            }
+        }
+        __syncthreads();
+        const int base = (tid >> 5) * RUN;
+        if (base < len) {
+            uint32_t key[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int i = lane * 16 + e;
+                key[e] = base + i < len ? sk[0][base + swz<16>(i)] : 0xffffffffu;
+            }
+            warp_sort_keys<16>(key, lane);
+            __syncwarp();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) sk[0][base + swz<16>(lane * 16 + e)] = key[e];
+        }
+        __syncthreads();
+        merge_round_keys<SEG, true>(sk[0], sk[1], len, RUN, tid);
+        __syncthreads();
+        int cur = 1;
+        for (int run = 2 * RUN; run < len; run <<= 1) {
+            merge_round_keys<SEG, false>(sk[cur], sk[cur ^ 1], len, run, tid);
+            __syncthreads();
+            cur ^= 1;
+        }
+#pragma unroll
+        for (int c = 0; c < SEG; ++c) {
+            const int i = c * P + tid;
+            if (i < len) {
+                const uint32_t kk = sk[cur][i];
+                col[b + i] = (int32_t)(kk >> PACK_BITS);
+                dist[b + i] = sv[kk & PACK_POS];
+            }
         }
     }
 }
@@ -2651,6 +3040,87 @@ __global__ void k_big_lengths(const int32_t *__restrict__ rows, int nbig, const 
 
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)ceil_div(n > 0 ? n : 1, t); }
 
+// Row-sort kernels: dynamic shared memory allowed and CTAs resident per SM,
+// found once (before any capture) and kept.  [0]: (key, value) kernels, [1]:
+// packed keys.
+struct SortGrids {
+    int warp_per_sm[2][5] = {};   // k_sort_warp<2 .. 16> for classes 1 .. 4
+    int merge_per_sm[2][8] = {};  // k_sort_merge for classes 5 .. 7
+};
+const SortGrids &sort_grids() {
+    static const SortGrids g = [] {
+        SortGrids r;
+        auto warp = [&](int pk, int c, auto kern) {
+            CT_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r.warp_per_sm[pk][c], kern,
+                                                                        32 * SORT_WARPS, 0));
+            r.warp_per_sm[pk][c] = std::max(r.warp_per_sm[pk][c], 1);
+        };
+        auto merge = [&](int pk, int c, auto kern, int cap) {
+            const int smem = (pk ? 12 : 16) * cap;
+            if (smem > 48 * 1024)
+                CT_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            CT_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r.merge_per_sm[pk][c], kern, cap / 16, smem));
+            r.merge_per_sm[pk][c] = std::max(r.merge_per_sm[pk][c], 1);
+        };
+        warp(0, 1, k_sort_warp<2>);
+        warp(0, 2, k_sort_warp<4>);
+        warp(0, 3, k_sort_warp<8>);
+        warp(0, 4, k_sort_warp<16>);
+        merge(0, 5, k_sort_merge<1024>, 1024);
+        merge(0, 6, k_sort_merge<2048>, 2048);
+        merge(0, 7, k_sort_merge<SORT_MID>, SORT_MID);
+        warp(1, 1, k_sort_warp_packed<2>);
+        warp(1, 2, k_sort_warp_packed<4>);
+        warp(1, 3, k_sort_warp_packed<8>);
+        warp(1, 4, k_sort_warp_packed<16>);
+        merge(1, 5, k_sort_merge_packed<1024>, 1024);
+        merge(1, 6, k_sort_merge_packed<2048>, 2048);
+        merge(1, 7, k_sort_merge_packed<SORT_MID>, SORT_MID);
+        return r;
+    }();
+    return g;
+}
+
+// The sorts of the rows in classes 0 .. kSortClasses - 2 (class lists of
+// stride n, their counts on the device) of a graph whose columns are below n.
+// hc: the same counts on the host -- classes without rows are skipped and
+// grids sized to the rows; null: every class launched on a full grid (the
+// kernels loop over the rows the device counted).
+void launch_class_sorts(const int32_t *lists, const int32_t *counts, const int32_t *hc, int64_t n,
+                        const int64_t *row_ptr, int32_t *col, float *dist, cudaStream_t s) {
+    const SortGrids &g = sort_grids();
+    const int pk = n < PACK_MAX_COLS ? 1 : 0;
+    if (!hc || hc[0]) {
+        k_sort_small<<<grid_for((hc ? hc[0] : n) * 32, 256), 256, 0, s>>>(lists, counts, row_ptr, col, dist);
+        CT_COUNT_LAUNCH();
+    }
+    auto launch = [&](int c, auto kern, int threads, int smem, int per_sm, int rows_per_cta) {
+        if (hc && !hc[c]) return;
+        const int64_t full = (int64_t)num_sms() * per_sm;
+        const int64_t blocks = hc ? std::min<int64_t>(ceil_div((int64_t)hc[c], rows_per_cta), full) : full;
+        kern<<<(unsigned)blocks, threads, smem, s>>>(lists + (int64_t)c * n, counts + c, row_ptr, col, dist);
+        CT_COUNT_LAUNCH();
+    };
+    constexpr int WT = 32 * SORT_WARPS;
+    if (pk) {
+        launch(1, k_sort_warp_packed<2>, WT, 0, g.warp_per_sm[1][1], SORT_WARPS);
+        launch(2, k_sort_warp_packed<4>, WT, 0, g.warp_per_sm[1][2], SORT_WARPS);
+        launch(3, k_sort_warp_packed<8>, WT, 0, g.warp_per_sm[1][3], SORT_WARPS);
+        launch(4, k_sort_warp_packed<16>, WT, 0, g.warp_per_sm[1][4], SORT_WARPS);
+        launch(5, k_sort_merge_packed<1024>, 1024 / 16, 12 * 1024, g.merge_per_sm[1][5], 1);
+        launch(6, k_sort_merge_packed<2048>, 2048 / 16, 12 * 2048, g.merge_per_sm[1][6], 1);
+        launch(7, k_sort_merge_packed<SORT_MID>, SORT_MID / 16, 12 * SORT_MID, g.merge_per_sm[1][7], 1);
+    } else {
+        launch(1, k_sort_warp<2>, WT, 0, g.warp_per_sm[0][1], SORT_WARPS);
+        launch(2, k_sort_warp<4>, WT, 0, g.warp_per_sm[0][2], SORT_WARPS);
+        launch(3, k_sort_warp<8>, WT, 0, g.warp_per_sm[0][3], SORT_WARPS);
+        launch(4, k_sort_warp<16>, WT, 0, g.warp_per_sm[0][4], SORT_WARPS);
+        launch(5, k_sort_merge<1024>, 1024 / 16, 16 * 1024, g.merge_per_sm[0][5], 1);
+        launch(6, k_sort_merge<2048>, 2048 / 16, 16 * 2048, g.merge_per_sm[0][6], 1);
+        launch(7, k_sort_merge<SORT_MID>, SORT_MID / 16, 16 * SORT_MID, g.merge_per_sm[0][7], 1);
+    }
+}
+
 }  // namespace
 
 void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int64_t nnz, cudaStream_t s) {
@@ -2661,27 +3131,11 @@ void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int
     CT_COUNT_LAUNCH();
     int32_t hc[kSortClasses];
     to_host(hc, counts.p, kSortClasses, s);
-    if (hc[0]) {
-        k_sort_small<<<grid_for((int64_t)hc[0] * 32, 256), 256, 0, s>>>(lists.p, counts.p, row_ptr, col, dist);
-        CT_COUNT_LAUNCH();
-    }
-    auto merge = [&](int cls, auto kern, int P, int cap) {
-        if (!hc[cls]) return;
-        const int smem = 16 * cap;
-        if (smem > 48 * 1024)
-            CT_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        const int per_sm = std::min(2048 / P, (200 * 1024) / smem);
-        const int blocks = (int)std::min<int64_t>(hc[cls], (int64_t)num_sms() * per_sm);
-        kern<<<blocks, P, smem, s>>>(lists.p + (int64_t)cls * n, counts.p + cls, row_ptr, col, dist);
-        CT_COUNT_LAUNCH();
-    };
-    merge(1, k_sort_merge<64, 128>, 64, 128);  // small CTAs: more rows in flight per SM
-    merge(2, k_sort_merge<128, 512>, 128, 512);
-    merge(3, k_sort_merge<128, 1024>, 128, 1024);
-    merge(4, k_sort_merge<512, SORT_MID>, 512, SORT_MID);
-    if (hc[5]) {
-        int nb = hc[5];
-        const int32_t *big = lists.p + 5 * n;
+    launch_class_sorts(lists.p, counts.p, hc, n, row_ptr, col, dist, s);
+    constexpr int BIG = kSortClasses - 1;
+    if (hc[BIG]) {
+        int nb = hc[BIG];
+        const int32_t *big = lists.p + BIG * n;
         DBuf<int64_t> lens(nb, s), off(nb, s), tot(1, s);
         k_big_lengths<<<grid_for(nb, 256), 256, 0, s>>>(big, nb, row_ptr, lens.p);
         CT_COUNT_LAUNCH();
@@ -3732,20 +4186,7 @@ void plan_enqueue(PlanImpl &p, cudaStream_t s) {
     CT_CHECK_CUDA(cudaMemsetAsync(p.sort_counts.p, 0, kSortClasses * sizeof(int32_t), s));
     k_row_classes<<<grid_for(n, 256), 256, 0, s>>>(p.row_ptr.p, n, p.sort_lists.p, p.sort_counts.p);
     CT_COUNT_LAUNCH();
-    k_sort_small<<<grid_for(n * 32, 256), 256, 0, s>>>(p.sort_lists.p, p.sort_counts.p, p.row_ptr.p, p.col.p,
-                                                       p.dist.p);
-    CT_COUNT_LAUNCH();
-    auto merge = [&](int cls, auto kern, int P_, int cap) {
-        const int smem = 16 * cap;
-        const int per_sm = std::min(2048 / P_, (200 * 1024) / smem);
-        kern<<<num_sms() * per_sm, P_, smem, s>>>(p.sort_lists.p + (int64_t)cls * n, p.sort_counts.p + cls,
-                                                   p.row_ptr.p, p.col.p, p.dist.p);
-        CT_COUNT_LAUNCH();
-    };
-    merge(1, k_sort_merge<64, 128>, 64, 128);
-    merge(2, k_sort_merge<128, 512>, 128, 512);
-    merge(3, k_sort_merge<128, 1024>, 128, 1024);
-    merge(4, k_sort_merge<512, SORT_MID>, 512, SORT_MID);
+    launch_class_sorts(p.sort_lists.p, p.sort_counts.p, nullptr, n, p.row_ptr.p, p.col.p, p.dist.p, s);
     {  // longer rows: one radix sort of (row rank, column) keys over the plan's capacity
         const int32_t *big = p.sort_lists.p + (int64_t)(kSortClasses - 1) * n;
         const int32_t *nbig = p.sort_counts.p + (kSortClasses - 1);
@@ -3935,14 +4376,7 @@ PlanImpl *plan_create(int C, const ct_tree *const *trees, const QParams *qps, in
         const size_t tsm = (size_t)TRAV_WARPS * p.max_dp * sizeof(float);
         if (tsm > 48 * 1024)
             CT_CHECK_CUDA(cudaFuncSetAttribute(k_traverse_l2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
-        auto attr = [&](auto kern, int cap) {
-            if (16 * cap > 48 * 1024)
-                CT_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * cap));
-        };
-        attr(k_sort_merge<64, 128>, 128);
-        attr(k_sort_merge<128, 512>, 512);
-        attr(k_sort_merge<128, 1024>, 1024);
-        attr(k_sort_merge<512, SORT_MID>, SORT_MID);
+        sort_grids();  // row-sort attributes set outside the capture
     }
     CT_CHECK_CUDA(cudaStreamSynchronize(s));
     if (use_graph) {

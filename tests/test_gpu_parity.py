@@ -137,8 +137,8 @@ def test_eps_zero_with_tiny_coordinates():
 
 
 def test_row_lengths_in_every_sort_class():
-    """Tight clusters of 20..5000 points give rows of every length class of
-    the row sort (<= 32, 128, 512, 1024, 4096, longer)."""
+    """Tight clusters of 20..5000 points give rows in the row sort's classes
+    (<= 32, 128, 512, 1024, 4096, longer)."""
     rng = np.random.default_rng(12)
     parts = []
     for k, size in enumerate((20, 100, 400, 900, 3000, 5000)):
@@ -156,10 +156,12 @@ def test_row_lengths_in_every_sort_class():
 
 def test_row_lengths_at_sort_class_boundaries():
     """Rows one below, at and one above each length boundary of the row sort
-    (32, 128, 512, 1024, 4096) and at the merge runs' sizes (64, 65, 200):
-    the sorted rows equal brute force's."""
+    (32, 64, 128, 256, 512, 1024, 2048, 4096), and rows of 3 and 6 runs of
+    512 (1500, 2600: a run left without a partner in a merge round, a partial
+    last run): the sorted rows equal brute force's."""
     rng = np.random.default_rng(5)
-    degrees = (32, 33, 64, 65, 127, 128, 129, 200, 511, 512, 513, 1023, 1024, 1025, 4095, 4096, 4097)
+    degrees = (2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 200, 255, 256, 257, 511, 512, 513, 1023, 1024, 1025,
+               1500, 2047, 2048, 2049, 2600, 4095, 4096, 4097)
     parts = [rng.random(4) * 100.0 + rng.random((d + 1, 4)) * 0.1 for d in degrees]
     x = np.concatenate(parts).astype(np.float32)
     x = x[rng.permutation(x.shape[0])]
@@ -168,6 +170,46 @@ def test_row_lengths_at_sort_class_boundaries():
         out = gpu_graph(points=x, eps=0.5, precision=precision)
         assert_csr_matches(out, ref)
         assert sorted(set(np.diff(out["row_ptr"]).tolist())) == list(degrees)
+
+
+def test_row_sort_past_the_packed_keys():
+    """1.1M points: more columns than the row sort's packed keys (column << 12
+    | position, 32 bits) hold, so rows sort as (column, distance) pairs.
+    Tight clusters of 40..5000 points give rows in every length class;
+    sampled rows of every cluster and of the background equal brute force's,
+    and every row is strictly increasing."""
+    rng = np.random.default_rng(21)
+    sizes = (40, 70, 140, 300, 600, 1500, 3000, 5000)
+    n = 1_100_000
+    assert n > 1 << 20
+    parts = [rng.random(3) * 1000.0 + rng.random((s, 3)) * 0.2 for s in sizes]
+    parts.append(rng.random((n - sum(sizes), 3)) * 1000.0)
+    perm = rng.permutation(n)
+    x = np.concatenate(parts).astype(np.float32)[perm]
+    where = np.argsort(perm)                     # original index -> row
+    out = gpu_graph(points=x, eps=0.5)
+    rows, start = [], 0
+    for s in sizes:
+        rows += list(where[start + rng.choice(s, size=3, replace=False)])
+        start += s
+    rows += list(rng.choice(n, size=40, replace=False))
+    rows = np.unique(np.asarray(rows, np.int64))
+    ref = oracle.brute_rows(oracle.Space(points=x), 0.5, rows)
+    rp, col, dist = out["row_ptr"], out["col"], out["dist"]
+    deg = np.diff(rp)
+    for s in sizes:
+        assert (deg == s - 1).any() or (deg == s).any()
+    for k, r in enumerate(rows):
+        a, b = int(rp[r]), int(rp[r + 1])
+        ra, rb = int(ref["row_ptr"][k]), int(ref["row_ptr"][k + 1])
+        np.testing.assert_array_equal(np.asarray(col[a:b], np.int64), ref["col"][ra:rb], err_msg="row %d" % r)
+        rd = ref["dist"][ra:rb]
+        assert np.all(np.abs(np.asarray(dist[a:b], np.float64) - rd) <= 1e-6 * np.abs(rd)), "row %d" % r
+    step = np.diff(np.asarray(col, np.int64))
+    inner = np.ones(step.size, bool)
+    starts = rp[1:-1][(rp[1:-1] > 0) & (rp[1:-1] < col.size)] - 1
+    inner[starts] = False
+    assert np.all(step[inner] > 0)
 
 
 def test_complete_graph_and_include_self():
