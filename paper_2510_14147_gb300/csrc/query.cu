@@ -2672,13 +2672,15 @@ __global__ void __launch_bounds__(32 * SORT_WARPS, 3) k_sort_warp(const int32_t 
     }
 }
 
-// One merge round of a row's sorted runs of length run (the last may be
-// shorter or alone): the pair (A, B) = runs 2 m, 2 m + 1 goes to the outputs
-// [2 m run, ...) of buffers (kn, vn).  Thread tid writes the SEG outputs from
-// tid SEG: one binary search along its diagonal finds how many of them come
-// from A (merge path), then it merges them one by one.  SWZ: the source runs
-// are 512-entry runs in the swizzled layout (swz<16> within each run).
-template <int SEG, bool SWZ>
+// One merge round of a row's sorted runs of length run >= 512 (the last may
+// be shorter or alone): the pair (A, B) = runs 2 m, 2 m + 1 goes to the
+// outputs [2 m run, ...) of buffers (kn, vn).  Thread tid writes the SEG = 16
+// outputs from 16 tid: one binary search along its diagonal finds how many of
+// them come from A (merge path), then it merges them one by one.  Every
+// buffer holds entry i at swz<16>(i) (runs start at multiples of 512, so a
+// run's entry x sits at its start + swz<16>(x)): the warp's stores of its
+// 16 consecutive outputs then hit 32 distinct banks.
+template <int SEG>
 __device__ __forceinline__ void merge_round(const int *__restrict__ kc, const float *__restrict__ vc,
                                             int *__restrict__ kn, float *__restrict__ vn, int len, int run,
                                             int tid) {
@@ -2688,7 +2690,7 @@ __device__ __forceinline__ void merge_round(const int *__restrict__ kc, const fl
     const int na = min(run, len - s0), nb = max(0, min(run, len - s0 - run));
     const int *A = kc + s0, *B = A + run;
     const float *Av = vc + s0, *Bv = Av + run;
-    auto at = [](int i) { return SWZ ? swz<16>(i) : i; };  // within a 512-entry run when SWZ
+    auto at = [](int i) { return swz<16>(i); };
     const int d = o - s0;  // outputs of the pair before this thread's
     int lo = max(0, d - nb), hi = min(d, na);
     while (lo < hi) {  // entries of A among the pair's d smallest
@@ -2703,8 +2705,8 @@ __device__ __forceinline__ void merge_round(const int *__restrict__ kc, const fl
 #pragma unroll 4
     for (int t = 0; t < cnt; ++t) {
         const bool ta = ka < kb;
-        kn[o + t] = ta ? ka : kb;
-        vn[o + t] = ta ? Av[at(ia)] : Bv[at(ib)];
+        kn[swz<16>(o + t)] = ta ? ka : kb;
+        vn[swz<16>(o + t)] = ta ? Av[at(ia)] : Bv[at(ib)];
         ia += ta;
         ib += !ta;
         const int nx = ta ? ia : ib;
@@ -2717,7 +2719,8 @@ __device__ __forceinline__ void merge_round(const int *__restrict__ kc, const fl
 // CTA of P = CAP / 16 threads per row of 513 .. CAP entries (16 CAP bytes of
 // dynamic shared memory: keys and values, two buffers each).  Each warp sorts
 // one 512-entry run in registers (warp_sort_blocked<16>) and leaves it in the
-// swizzled layout; then runs merge in pairs (merge_round) until one is left.
+// swizzled layout (swz<16>, which every buffer keeps); then runs merge in
+// pairs (merge_round) until one is left.
 // The columns of a row are distinct, so the merged order is unique.
 template <int CAP>
 __global__ void __launch_bounds__(CAP / 16, 12288 / CAP) k_sort_merge(const int32_t *__restrict__ rows,
@@ -2735,7 +2738,7 @@ __global__ void __launch_bounds__(CAP / 16, 12288 / CAP) k_sort_merge(const int3
         const int r = rows[w];
         const int64_t b = row_ptr[r];
         const int len = (int)min(row_ptr[r + 1] - b, (int64_t)CAP);  // rows of this class fit
-        {  // coalesced read: SEG loads a thread, then the stores, each run swizzled
+        {  // coalesced read: SEG loads a thread, then the stores
             int key[SEG];
             float val[SEG];
 #pragma unroll
@@ -2749,9 +2752,8 @@ __global__ void __launch_bounds__(CAP / 16, 12288 / CAP) k_sort_merge(const int3
             for (int c = 0; c < SEG; ++c) {
                 const int i = c * P + tid;
                 if (i < len) {
-                    const int p = (i & ~(RUN - 1)) | swz<16>(i & (RUN - 1));
-                    sk[0][p] = key[c];
-                    sv[0][p] = val[c];
+                    sk[0][swz<16>(i)] = key[c];
+                    sv[0][swz<16>(i)] = val[c];
                 }
             }
         }
@@ -2766,11 +2768,9 @@ __global__ void __launch_bounds__(CAP / 16, 12288 / CAP) k_sort_merge(const int3
             put_blocked<16>(sk[0] + base, sv[0] + base, lane, key, val);
         }
         __syncthreads();
-        merge_round<SEG, true>(sk[0], sv[0], sk[1], sv[1], len, RUN, tid);
-        __syncthreads();
-        int cur = 1;
-        for (int run = 2 * RUN; run < len; run <<= 1) {
-            merge_round<SEG, false>(sk[cur], sv[cur], sk[cur ^ 1], sv[cur ^ 1], len, run, tid);
+        int cur = 0;
+        for (int run = RUN; run < len; run <<= 1) {
+            merge_round<SEG>(sk[cur], sv[cur], sk[cur ^ 1], sv[cur ^ 1], len, run, tid);
             __syncthreads();
             cur ^= 1;
         }
@@ -2778,8 +2778,8 @@ __global__ void __launch_bounds__(CAP / 16, 12288 / CAP) k_sort_merge(const int3
         for (int c = 0; c < SEG; ++c) {
             const int i = c * P + tid;
             if (i < len) {
-                col[b + i] = sk[cur][i];
-                dist[b + i] = sv[cur][i];
+                col[b + i] = sk[cur][swz<16>(i)];
+                dist[b + i] = sv[cur][swz<16>(i)];
             }
         }
     }
@@ -2795,27 +2795,52 @@ constexpr uint32_t PACK_POS = (1u << PACK_BITS) - 1;
 constexpr int64_t PACK_MAX_COLS = int64_t(1) << (32 - PACK_BITS);  // packed when n (columns < n) is below
 static_assert(SORT_MID <= (1 << PACK_BITS), "positions must fit the packed keys");
 
-// warp_sort_blocked on keys alone (padding: 0xffffffff, above every key).
+// Sorting network over 32 E packed keys in the blocked layout (padding:
+// 0xffffffff, above every key): bitonic merges in the form whose first step
+// of each merge compares entry i with its mirror i ^ (k - 1) in the block of
+// k, the rest comparing i with i ^ j -- every comparator puts the minimum at
+// the lower index, so a pair in one lane costs one min and one max.  Across
+// lanes (distances of E and more) each lane keeps the minimum or the maximum
+// of its key and its partner's, shuffled over.
 template <int E>
 __device__ __forceinline__ void warp_sort_keys(uint32_t (&key)[E], int lane) {
     constexpr int N = 32 * E;
 #pragma unroll
     for (int k = 2; k <= N; k <<= 1) {
+        if (k <= E) {  // the mirror step inside a lane
 #pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int e = 0; e < E; ++e) {
+                if (e & (k >> 1)) continue;
+                const int f = e ^ (k - 1);
+                const uint32_t lo = min(key[e], key[f]), hi = max(key[e], key[f]);
+                key[e] = lo;
+                key[f] = hi;
+            }
+        } else {  // mirror partner: lane ^ (k / E - 1), register E - 1 - e
+            const int m = k / E - 1;
+            const bool keep_min = (lane & (k / (2 * E))) == 0;
+#pragma unroll
+            for (int t = 0; t < E / 2; ++t) {
+                const uint32_t o1 = __shfl_xor_sync(0xffffffffu, key[E - 1 - t], m);
+                const uint32_t o2 = __shfl_xor_sync(0xffffffffu, key[t], m);
+                key[t] = keep_min ? min(key[t], o1) : max(key[t], o1);
+                key[E - 1 - t] = keep_min ? min(key[E - 1 - t], o2) : max(key[E - 1 - t], o2);
+            }
+        }
+#pragma unroll
+        for (int j = k >> 2; j > 0; j >>= 1) {
             if (j < E) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     if (e & j) continue;
                     const int f = e | j;
-                    const bool up = ((lane * E + e) & k) == 0;
                     const uint32_t lo = min(key[e], key[f]), hi = max(key[e], key[f]);
-                    key[e] = up ? lo : hi;
-                    key[f] = up ? hi : lo;
+                    key[e] = lo;
+                    key[f] = hi;
                 }
             } else {
                 const int lj = j / E;
-                const bool keep_min = (((lane * E) & k) == 0) == ((lane & lj) == 0);
+                const bool keep_min = (lane & lj) == 0;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const uint32_t o = __shfl_xor_sync(0xffffffffu, key[e], lj);
@@ -2827,7 +2852,7 @@ __device__ __forceinline__ void warp_sort_keys(uint32_t (&key)[E], int lane) {
 }
 
 // merge_round on packed keys alone.
-template <int SEG, bool SWZ>
+template <int SEG>
 __device__ __forceinline__ void merge_round_keys(const uint32_t *__restrict__ kc, uint32_t *__restrict__ kn,
                                                  int len, int run, int tid) {
     const int o = tid * SEG;
@@ -2835,7 +2860,7 @@ __device__ __forceinline__ void merge_round_keys(const uint32_t *__restrict__ kc
     const int s0 = o & ~(2 * run - 1);
     const int na = min(run, len - s0), nb = max(0, min(run, len - s0 - run));
     const uint32_t *A = kc + s0, *B = A + run;
-    auto at = [](int i) { return SWZ ? swz<16>(i) : i; };
+    auto at = [](int i) { return swz<16>(i); };
     const int d = o - s0;
     int lo = max(0, d - nb), hi = min(d, na);
     while (lo < hi) {
@@ -2848,7 +2873,7 @@ __device__ __forceinline__ void merge_round_keys(const uint32_t *__restrict__ kc
 #pragma unroll 4
     for (int t = 0; t < cnt; ++t) {
         const bool ta = ka < kb;
-        kn[o + t] = min(ka, kb);
+        kn[swz<16>(o + t)] = min(ka, kb);
         ia += ta;
         ib += !ta;
         const int nx = ta ? ia : ib;
@@ -2947,7 +2972,7 @@ __global__ void __launch_bounds__(CAP / 16, 16384 / CAP) k_sort_merge_packed(con
             for (int c = 0; c < SEG; ++c) {
                 const int i = c * P + tid;
                 if (i < len) {
-                    sk[0][(i & ~(RUN - 1)) | swz<16>(i & (RUN - 1))] = key[c];
+                    sk[0][swz<16>(i)] = key[c];
                     sv[i] = val[c];
                 }
             }
@@ -2967,11 +2992,9 @@ __global__ void __launch_bounds__(CAP / 16, 16384 / CAP) k_sort_merge_packed(con
             for (int e = 0; e < 16; ++e) sk[0][base + swz<16>(lane * 16 + e)] = key[e];
         }
         __syncthreads();
-        merge_round_keys<SEG, true>(sk[0], sk[1], len, RUN, tid);
-        __syncthreads();
-        int cur = 1;
-        for (int run = 2 * RUN; run < len; run <<= 1) {
-            merge_round_keys<SEG, false>(sk[cur], sk[cur ^ 1], len, run, tid);
+        int cur = 0;
+        for (int run = RUN; run < len; run <<= 1) {
+            merge_round_keys<SEG>(sk[cur], sk[cur ^ 1], len, run, tid);
             __syncthreads();
             cur ^= 1;
         }
@@ -2979,7 +3002,7 @@ __global__ void __launch_bounds__(CAP / 16, 16384 / CAP) k_sort_merge_packed(con
         for (int c = 0; c < SEG; ++c) {
             const int i = c * P + tid;
             if (i < len) {
-                const uint32_t kk = sk[cur][i];
+                const uint32_t kk = sk[cur][swz<16>(i)];
                 col[b + i] = (int32_t)(kk >> PACK_BITS);
                 dist[b + i] = sv[kk & PACK_POS];
             }
