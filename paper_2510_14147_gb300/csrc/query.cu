@@ -3105,14 +3105,14 @@ const SortGrids &sort_grids() {
 }
 
 // The sorts of the rows in classes 0 .. kSortClasses - 2 (class lists of
-// stride n, their counts on the device) of a graph whose columns are below n.
-// hc: the same counts on the host -- classes without rows are skipped and
-// grids sized to the rows; null: every class launched on a full grid (the
+// stride n, their counts on the device) of a graph whose columns are below
+// ncols.  hc: the same counts on the host -- classes without rows are skipped
+// and grids sized to the rows; null: every class launched on a full grid (the
 // kernels loop over the rows the device counted).
-void launch_class_sorts(const int32_t *lists, const int32_t *counts, const int32_t *hc, int64_t n,
+void launch_class_sorts(const int32_t *lists, const int32_t *counts, const int32_t *hc, int64_t n, int64_t ncols,
                         const int64_t *row_ptr, int32_t *col, float *dist, cudaStream_t s) {
     const SortGrids &g = sort_grids();
-    const int pk = n < PACK_MAX_COLS ? 1 : 0;
+    const int pk = ncols < PACK_MAX_COLS ? 1 : 0;
     if (!hc || hc[0]) {
         k_sort_small<<<grid_for((hc ? hc[0] : n) * 32, 256), 256, 0, s>>>(lists, counts, row_ptr, col, dist);
         CT_COUNT_LAUNCH();
@@ -3146,7 +3146,8 @@ void launch_class_sorts(const int32_t *lists, const int32_t *counts, const int32
 
 }  // namespace
 
-void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int64_t nnz, cudaStream_t s) {
+void sort_rows(const int64_t *row_ptr, int64_t n, int64_t ncols, int32_t *col, float *dist, int64_t nnz,
+               cudaStream_t s) {
     if (n <= 0 || nnz <= 0) return;
     DBuf<int32_t> lists(kSortClasses * n, s), counts(kSortClasses, s);
     CT_CHECK_CUDA(cudaMemsetAsync(counts.p, 0, kSortClasses * sizeof(int32_t), s));
@@ -3154,7 +3155,7 @@ void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int
     CT_COUNT_LAUNCH();
     int32_t hc[kSortClasses];
     to_host(hc, counts.p, kSortClasses, s);
-    launch_class_sorts(lists.p, counts.p, hc, n, row_ptr, col, dist, s);
+    launch_class_sorts(lists.p, counts.p, hc, n, ncols, row_ptr, col, dist, s);
     constexpr int BIG = kSortClasses - 1;
     if (hc[BIG]) {
         int nb = hc[BIG];
@@ -3806,7 +3807,9 @@ void query_multi(int C, const ct_tree *const *trees, const QParams *qps, cudaStr
     }
     {
         ProfScope ps("row_sort", s);
-        sort_rows(row_ptr, n, all.col, all.dist, nnz, s);
+        int64_t ncols = 0;  // columns index points of their own cloud
+        for (int c = 0; c < C; ++c) ncols = std::max<int64_t>(ncols, trees[c]->n);
+        sort_rows(row_ptr, n, ncols, all.col, all.dist, nnz, s);
     }
     finish_stats();
     if (C == 1) {
@@ -4108,7 +4111,7 @@ struct PlanImpl {
     int C = 0;
     std::vector<const ct_tree *> trees;
     Views V;
-    int64_t n = 0;
+    int64_t n = 0, max_cols = 0;  // rows of all clouds; points of the largest cloud
     int G = 0;
     int max_dp = 4, cap_stack = 0, spill_cap = 0, leaf_grid = 1;
     TravLaunch tl{1, 1};
@@ -4209,7 +4212,7 @@ void plan_enqueue(PlanImpl &p, cudaStream_t s) {
     CT_CHECK_CUDA(cudaMemsetAsync(p.sort_counts.p, 0, kSortClasses * sizeof(int32_t), s));
     k_row_classes<<<grid_for(n, 256), 256, 0, s>>>(p.row_ptr.p, n, p.sort_lists.p, p.sort_counts.p);
     CT_COUNT_LAUNCH();
-    launch_class_sorts(p.sort_lists.p, p.sort_counts.p, nullptr, n, p.row_ptr.p, p.col.p, p.dist.p, s);
+    launch_class_sorts(p.sort_lists.p, p.sort_counts.p, nullptr, n, p.max_cols, p.row_ptr.p, p.col.p, p.dist.p, s);
     {  // longer rows: one radix sort of (row rank, column) keys over the plan's capacity
         const int32_t *big = p.sort_lists.p + (int64_t)(kSortClasses - 1) * n;
         const int32_t *nbig = p.sort_counts.p + (kSortClasses - 1);
@@ -4263,6 +4266,7 @@ PlanImpl *plan_create(int C, const ct_tree *const *trees, const QParams *qps, in
         min_len = std::min(min_len, len);
         p.V.gbase[c + 1] = p.V.gbase[c] + t->n_groups;
         p.V.rbase[c + 1] = p.V.rbase[c] + t->n;
+        p.max_cols = std::max<int64_t>(p.max_cols, t->n);
         p.max_dp = std::max(p.max_dp, t->dp);
         max_depth = std::max(max_depth, t->depth);
     }

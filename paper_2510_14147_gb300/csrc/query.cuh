@@ -105,8 +105,9 @@ int64_t plan_rows(const PlanImpl *p, int c);
 ct_status plan_result(PlanImpl *p, cudaStream_t s, QueryOut *outs);
 void plan_free(PlanImpl *p);
 
-// Sorts every CSR row by column, moving dist along.
-void sort_rows(const int64_t *row_ptr, int64_t n, int32_t *col, float *dist, int64_t nnz,
+// Sorts every CSR row (n rows, columns below ncols) by column, moving dist
+// along.
+void sort_rows(const int64_t *row_ptr, int64_t n, int64_t ncols, int32_t *col, float *dist, int64_t nnz,
                cudaStream_t s);
 
 // Stats slots accumulated on the device.
