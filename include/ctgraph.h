@@ -322,9 +322,8 @@ void ct_autotune_reset(void);
  * inside the library (every GPU that loads the library holds it until the
  * process exits).  The first call on a device looks up that array's device
  * address.  Calls never allocate or free device memory; they synchronise
- * `stream` twice and copy counters to host memory, so no call may be made
- * while `stream` (or any stream, under global capture mode) is being captured
- * into a CUDA graph.  The candidate list holds about 2.5 M (group, leaf
+ * `stream` twice and copy counters to host memory.  The candidate list holds
+ * about 2.5 M (group, leaf
  * block) entries, fewer for deep trees; the walk runs with at most 64 blocks
  * of 4 warps.
  * Every call reuses the same array and clears what must start at zero; calls
