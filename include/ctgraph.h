@@ -323,9 +323,8 @@ void ct_autotune_reset(void);
  * process exits).  The first call on a device looks up that array's device
  * address.  Calls never allocate or free device memory; they synchronise
  * `stream` twice and copy counters to host memory.  The candidate list holds
- * about 2.5 M (group, leaf
- * block) entries, fewer for deep trees; the walk runs with at most 64 blocks
- * of 4 warps.
+ * about 2.5 M (group, leaf block) entries, fewer for deep trees; the walk
+ * runs with at most 64 blocks of 4 warps.
  * Every call reuses the same array and clears what must start at zero; calls
  * whose work overlaps on the GPU (other streams, other host threads) race on
  * it and must be serialised by the caller.
