@@ -951,6 +951,18 @@ __global__ void k_root_node(int64_t n, int zeta, int metric, const unsigned long
     hb.thr[0] = hub ? ldexpf(1.0f, l - 1) : 0.0f;
 }
 
+// Rows already of dp = dim floats (dim a multiple of 4, 16-byte aligned
+// source): a float4 copy with the same coordinate-range check.
+__global__ void k_copy_rows4(const float4 *__restrict__ src, int64_t nq, float4 *__restrict__ dst,
+                             int32_t *__restrict__ bad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    const float4 v = src[i];
+    if (!(fabsf(v.x) <= 0x1p50f && fabsf(v.y) <= 0x1p50f && fabsf(v.z) <= 0x1p50f && fabsf(v.w) <= 0x1p50f))
+        atomicOr(bad, 1);
+    dst[i] = v;
+}
+
 // Pad rows to dp floats (original order) and check the coordinate range.
 __global__ void k_pad_rows(const float *__restrict__ src, int64_t n, int dim, int dp,
                            float *__restrict__ dst, int32_t *__restrict__ bad) {
@@ -1188,7 +1200,11 @@ ct_tree *build_tree(const ct_points *pts, int zeta, int root, cudaStream_t s) {
         }
     } else if (l2) {
         Xp = DBuf<float>((size_t)n * dp, s);
-        if (n) {
+        if (n && dp == pts->dim && (reinterpret_cast<uintptr_t>(pts->data) & 15) == 0) {
+            const int64_t nq = n * dp / 4;
+            k_copy_rows4<<<grid_for(nq), BT, 0, s>>>((const float4 *)pts->data, nq, (float4 *)Xp.p, err.p);
+            CT_COUNT_LAUNCH();
+        } else if (n) {
             k_pad_rows<<<grid_for(n * dp), BT, 0, s>>>((const float *)pts->data, n, pts->dim, dp, Xp.p, err.p);
             CT_COUNT_LAUNCH();
         }

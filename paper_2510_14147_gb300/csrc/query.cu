@@ -2521,8 +2521,13 @@ __global__ void k_row_classes(const int64_t *__restrict__ row_ptr, int64_t n, in
             cls = c;
             break;
         }
-    int slot = atomicAdd(&counts[cls], 1);
-    lists[(int64_t)cls * n + slot] = (int32_t)i;
+    // one atomic per class present in the warp (the lanes still here)
+    const unsigned peers = __match_any_sync(__activemask(), cls);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&counts[cls], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    lists[(int64_t)cls * n + base + __popc(peers & ((1u << lane) - 1))] = (int32_t)i;
 }
 
 // Bitonic network over the 32 lanes of a warp: (key, val) pairs ascending by

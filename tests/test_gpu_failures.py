@@ -174,3 +174,23 @@ def test_selftest_wait_runs_out_and_context_survives():
     D = cg.ct_selftest_tc_gemm(A, B).cpu().numpy()
     ref = A.cpu().numpy().astype(np.float64) @ B.cpu().numpy().astype(np.float64).T
     assert np.allclose(D, ref, rtol=1e-5, atol=1e-3)
+
+
+@pytest.mark.parametrize("dim", [3, 4, 128])
+def test_build_rejects_coordinates_out_of_range(dim):
+    """A NaN, an infinity or a coordinate above 2^50 anywhere in the points
+    makes ct_build return CT_EUNSUPPORTED (dims 4 and 128 take the float4 row
+    copy, dim 3 the padded one); 2^50 itself is accepted."""
+    import torch
+    cg = _cg()
+    x = I.uniform_cube(257, dim, seed=3)
+    for bad in (np.nan, np.inf, -np.inf, 2.0 ** 51, -(2.0 ** 51)):
+        y = x.copy()
+        y[200, dim - 1] = bad
+        with pytest.raises(cg.CtError) as e:
+            cg.ct_build(points=torch.from_numpy(y).cuda())
+        assert e.value.status == cg.CT_EUNSUPPORTED
+    y = x.copy()
+    y[5, 0] = 2.0 ** 50
+    t = cg.ct_build(points=torch.from_numpy(y).cuda())
+    t.free()
